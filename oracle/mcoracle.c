@@ -1,0 +1,1657 @@
+/*
+ * mcoracle.c -- plain history-based CPU reference for event-based Monte Carlo
+ * neutral-particle transport.  TEST INFRASTRUCTURE: only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg use this file.
+ *
+ * What is computed follows the paper's description of the transport code
+ * (Sec. 1: multigroup and continuous-energy physics, CSG geometry with surface
+ * tracking, k-eigenvalue and fully dynamic/fixed-source runs, replicable
+ * random numbers; Sec. 2: particles advance, cross surfaces and collide).  The
+ * paper gives no formulas, so every step is the textbook one, taken one
+ * particle at a time (history-based), with secondaries deferred to the next
+ * cycle or generation.  Wherever the paper is silent the choice is stated in a
+ * comment beginning "Reading:".
+ *
+ * Arithmetic is plain IEEE double with no contraction (compile with
+ * -ffp-contract=off); each formula is evaluated in the order written.
+ */
+#include "mcoracle.h"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define INF HUGE_VAL
+#define MAX_EVENTS 1000000   /* events per history before it is cut (counted as capped) */
+#define MAX_TRIES 10000      /* source rejection attempts */
+#define MAX_GEN 200          /* fixed-source generations */
+
+/* ------------------------------------------------------------------------- */
+/* Random numbers.  The paper (Sec. 1) states only that streams are replicable
+ * on CPU and GPU.  Reading: the 63-bit multiplicative-congruential family
+ * generator s' = (g s + c) mod 2^63, g = 2806196910506780709, c = 1, with
+ * Brown's O(log n) skip-ahead ("Random number generation with arbitrary
+ * strides", 1994); stream i starts at skip(seed, i * 152917).  A draw advances
+ * the state and returns xi = ((s >> 10) + 1) 2^-53, in (0, 1].                */
+#define LCG_G 2806196910506780709ULL
+#define LCG_C 1ULL
+#define LCG_MASK 0x7FFFFFFFFFFFFFFFULL
+#define LCG_STRIDE 152917ULL
+
+uint64_t orc_rng_next(uint64_t s) { return (LCG_G * s + LCG_C) & LCG_MASK; }
+
+double orc_rng_xi(uint64_t s) { return (double)((s >> 10) + 1) * 0x1p-53; }
+
+uint64_t orc_rng_skip(uint64_t s, uint64_t n)
+{
+    /* compose the affine map s -> g s + c with itself n times by binary powers */
+    uint64_t G = 1, C = 0, h = LCG_G, f = LCG_C;
+    n &= LCG_MASK;
+    while (n) {
+        if (n & 1) {
+            G = G * h;
+            C = C * h + f;
+        }
+        f = f * (h + 1);
+        h = h * h;
+        n >>= 1;
+    }
+    return (G * (s & LCG_MASK) + C) & LCG_MASK;
+}
+
+uint64_t orc_rng_stream(uint64_t seed, uint64_t id) { return orc_rng_skip(seed, id * LCG_STRIDE); }
+
+static uint64_t draw_n(uint64_t *s)
+{
+    *s = orc_rng_next(*s);
+    return (*s >> 10) + 1;          /* the integer n of xi = n 2^-53 */
+}
+
+static double draw(uint64_t *s) { return (double)draw_n(s) * 0x1p-53; }
+
+/* ------------------------------------------------------------------------- */
+/* Natural logarithm of xi = n 2^-53 (n in [1, 2^53]) for the flight distance.
+ * Reading: both implementations evaluate ln with the same table-driven method
+ * (Tang, "Table-driven implementation of the logarithm function in IEEE
+ * floating-point arithmetic", ACM TOMS 1990): n = 2^e m, m in [1,2); c_j =
+ * 1 + j/256 from the top 8 fraction bits; r = (m - c_j) (1/c_j);
+ * ln xi = (e - 53) ln2 + ln c_j + log1p(r) with log1p by its Taylor series to
+ * r^6.  ln c_j comes from the series ln c = 2 atanh((c-1)/(c+1)).              */
+static double LOG_TAB[256], RINV_TAB[256];
+static int log_ready;
+static const double LN2 = 0x1.62e42fefa39efp-1;
+
+static double ln_series(double c)
+{
+    double s = (c - 1.0) / (c + 1.0);
+    double z = s * s;
+    double p = 1.0 / 79.0;
+    for (int k = 38; k >= 0; k--) p = p * z + 1.0 / (double)(2 * k + 1);
+    return 2.0 * s * p;
+}
+
+static void log_init(void)
+{
+    if (log_ready) return;
+    for (int j = 0; j < 256; j++) {
+        double c = 1.0 + (double)j / 256.0;
+        LOG_TAB[j] = ln_series(c);
+        RINV_TAB[j] = 1.0 / c;
+    }
+    log_ready = 1;
+}
+
+static int top_bit(uint64_t n)
+{
+    int e = 0;
+    while (n >> 1) {
+        n >>= 1;
+        e++;
+    }
+    return e;
+}
+
+static double log_n(uint64_t n)
+{
+    int e = top_bit(n);
+    double m = ldexp((double)n, -e);
+    int j = (int)(((n << (63 - e)) >> 55) & 0xFF);
+    double c = 1.0 + (double)j / 256.0;
+    double r = (m - c) * RINV_TAB[j];
+    double q = -1.0 / 6.0;
+    q = q * r + 1.0 / 5.0;
+    q = q * r + -0.25;
+    q = q * r + 1.0 / 3.0;
+    q = q * r + -0.5;
+    q = q * r + 1.0;
+    double p = q * r;
+    return (double)(e - 53) * LN2 + (LOG_TAB[j] + p);
+}
+
+double orc_log(double xi)
+{
+    log_init();
+    if (!(xi > 0.0) || xi > 1.0) return NAN;
+    return log_n((uint64_t)(xi * 0x1p53));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Isotropic direction (Marsaglia, "Choosing a point from the surface of a
+ * sphere", 1972): (a, b) uniform in the unit disk by rejection, S = a^2 + b^2,
+ * Omega = (2a sqrt(1-S), 2b sqrt(1-S), 1 - 2S).  No trigonometric function.   */
+static void iso_dir(uint64_t *s, double *u, double *v, double *w)
+{
+    for (int k = 0; k < 64; k++) {
+        double a = 2.0 * draw(s) - 1.0;
+        double b = 2.0 * draw(s) - 1.0;
+        double S = a * a + b * b;
+        if (S < 1.0) {
+            double t = 2.0 * sqrt(1.0 - S);
+            *u = a * t;
+            *v = b * t;
+            *w = 1.0 - 2.0 * S;
+            return;
+        }
+    }
+    *u = 0.0; *v = 0.0; *w = 1.0;
+}
+
+int orc_iso_dir(uint64_t *s, double out[3])
+{
+    iso_dir(s, &out[0], &out[1], &out[2]);
+    return 0;
+}
+
+/* Uniform azimuth as (cos phi, sin phi) without trigonometry: (a, b) uniform in
+ * the unit disk by rejection; the doubled angle of (a, b) is uniform, giving
+ * cos = (a^2 - b^2)/r2, sin = 2ab/r2.                                         */
+static void azimuth(uint64_t *s, double *cphi, double *sphi)
+{
+    for (int k = 0; k < 64; k++) {
+        double a = 2.0 * draw(s) - 1.0;
+        double b = 2.0 * draw(s) - 1.0;
+        double r2 = a * a + b * b;
+        if (r2 <= 1.0 && r2 > 0.0) {
+            *cphi = (a * a - b * b) / r2;
+            *sphi = 2.0 * a * b / r2;
+            return;
+        }
+    }
+    *cphi = 1.0; *sphi = 0.0;
+}
+
+/* Rotate direction (u,v,w) by polar cosine mu about itself, azimuth sampled
+ * (textbook rotation, polar axis z, or x when |w| is near 1).                 */
+static void rotate(double mu, uint64_t *s, double *u, double *v, double *w)
+{
+    double cphi, sphi;
+    azimuth(s, &cphi, &sphi);
+    double st2 = 1.0 - mu * mu;
+    double st = sqrt(st2 > 0.0 ? st2 : 0.0);
+    double u0 = *u, v0 = *v, w0 = *w;
+    double ww = 1.0 - w0 * w0;
+    if (ww > 1.0e-10) {
+        double q = sqrt(ww);
+        double f = st / q;
+        *u = mu * u0 + f * (u0 * w0 * cphi - v0 * sphi);
+        *v = mu * v0 + f * (v0 * w0 * cphi + u0 * sphi);
+        *w = mu * w0 - st * q * cphi;
+    } else {
+        double uu = 1.0 - u0 * u0;
+        double q = sqrt(uu);
+        double f = st / q;
+        *v = mu * v0 + f * (v0 * u0 * cphi - w0 * sphi);
+        *w = mu * w0 + f * (w0 * u0 * cphi + v0 * sphi);
+        *u = mu * u0 - st * q * cphi;
+    }
+}
+
+/* Elastic scattering off a target at rest (textbook two-body kinematics):
+ * mu_cm = 2 xi - 1, q = A^2 + 2 A mu_cm + 1, E' = E q / (A+1)^2,
+ * mu_lab = (1 + A mu_cm) / sqrt(q).
+ * Reading: E' is floored at 1e-5 eV (the paper's data start there).           */
+#define E_MIN 1.0e-5
+#define E_MAX 2.0e7
+static double elastic(double E, double A, uint64_t *s, double *u, double *v, double *w)
+{
+    double mucm = 2.0 * draw(s) - 1.0;
+    double q = A * A + 2.0 * A * mucm + 1.0;
+    double Ep = E * q / ((A + 1.0) * (A + 1.0));
+    double mul = (1.0 + A * mucm) / sqrt(q);
+    if (mul > 1.0) mul = 1.0;
+    if (mul < -1.0) mul = -1.0;
+    rotate(mul, s, u, v, w);
+    return Ep < E_MIN ? E_MIN : Ep;
+}
+
+int orc_elastic(double E, double A, const double dir[3], uint64_t *s, double out[4])
+{
+    double u = dir[0], v = dir[1], w = dir[2];
+    out[0] = elastic(E, A, s, &u, &v, &w);
+    out[1] = u; out[2] = v; out[3] = w;
+    return 0;
+}
+
+/* Fission spectrum.  Reading: Maxwellian with T = 1.33 MeV sampled by the
+ * Everett-Cashwell rule E = -T (ln xi1 + ln xi2 cos^2 theta) with theta uniform;
+ * cos^2 theta is taken as a^2 / (a^2 + b^2) of a point uniform in the unit disk
+ * (no trigonometry); energies above 20 MeV are resampled.                     */
+static double maxwell(uint64_t *s)
+{
+    log_init();
+    for (int k = 0; k < 64; k++) {
+        double L1 = log_n(draw_n(s));
+        double L2 = log_n(draw_n(s));
+        double a = 1.0, r2 = 1.0;
+        for (int t = 0; t < 64; t++) {
+            double aa = 2.0 * draw(s) - 1.0;
+            double bb = 2.0 * draw(s) - 1.0;
+            double rr = aa * aa + bb * bb;
+            if (rr <= 1.0 && rr > 0.0) { a = aa; r2 = rr; break; }
+        }
+        double c2 = a * a / r2;
+        double E = -1.33e6 * (L1 + L2 * c2);
+        if (E <= E_MAX) return E < E_MIN ? E_MIN : E;
+    }
+    return E_MAX;
+}
+
+double orc_maxwell(uint64_t *s) { return maxwell(s); }
+
+/* ------------------------------------------------------------------------- */
+/* problem description                                                        */
+typedef struct { int type, bc; double c[4]; double r2; } Surface;
+typedef struct { int universe, nhs, off, fill_kind, fill; } Cell;
+typedef struct { double x0, y0, pitch; int nx, ny; int *univ; } Lattice;
+typedef struct {
+    double *sigt, *sigs, *nusf, *chi;          /* input */
+    double *mfp, *mu, *mufl, *mufr, *ps, *stot, *scdf, *chicdf;   /* derived */
+    int fissile;
+} MatMG;
+typedef struct { double A, nu; int n; double *E, *s, *c, *f; } Nuclide;
+typedef struct { int n; int *nuc; double *dens; int fissile; } MatCE;
+typedef struct {
+    int kind, accept, ekind, dkind, ne;
+    double p[6], beam[3];
+    double *edata, *ecdf;
+} Source;
+typedef struct { int filter, nedges; double *edges; int nbins, ne; } Tally;
+
+typedef struct {
+    double x, y, z;
+    int cell, ix, iy, ucell, mat;
+    int64_t parent, root;
+    int32_t child;
+} Site;
+
+struct orc_ctx {
+    char err[256];
+    int ns, nc, nhs, nl, G, nm, nn, nmc, nt, ce, max_coll;
+    Surface *surf;
+    Cell *cell;
+    int *hs_surf, *hs_sense;
+    Lattice *lat;
+    int nuniv, *uoff, *ulist;
+    MatMG *mg;
+    Nuclide *nuc;
+    MatCE *mce;
+    Source src;
+    int src_set;
+    Tally *tally;
+    /* results */
+    double k[6];
+    int ncyc;
+    double *cyc_ktl, *cyc_kc;
+    int64_t *cyc_m;
+    double **t_sum, **t_sum2, **t_mean, **t_sd;
+    int64_t counters[7];
+    int64_t nhist;
+    int32_t *h_coll, *h_cross, *h_fis, *h_fate, *h_g;
+    uint64_t *h_rng;
+    int64_t nbank;
+    Site *bank;
+};
+
+static int fail(orc_ctx *c, int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof c->err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static void *xgrow(void *p, size_t n, size_t sz) { return realloc(p, (n ? n : 1) * sz); }
+
+static double *dup_d(const double *a, int n)
+{
+    double *r = malloc((size_t)(n ? n : 1) * sizeof(double));
+    if (n) memcpy(r, a, (size_t)n * sizeof(double));
+    return r;
+}
+
+orc_ctx *orc_create(void)
+{
+    log_init();
+    orc_ctx *c = calloc(1, sizeof(orc_ctx));
+    c->G = 0;
+    c->ce = -1;
+    return c;
+}
+
+static void free_results(orc_ctx *c)
+{
+    for (int t = 0; c->t_sum && t < c->nt; t++) {
+        free(c->t_sum[t]); free(c->t_sum2[t]); free(c->t_mean[t]); free(c->t_sd[t]);
+    }
+    free(c->t_sum); free(c->t_sum2); free(c->t_mean); free(c->t_sd);
+    c->t_sum = c->t_sum2 = c->t_mean = c->t_sd = NULL;
+    free(c->cyc_ktl); free(c->cyc_kc); free(c->cyc_m);
+    c->cyc_ktl = c->cyc_kc = NULL; c->cyc_m = NULL;
+    free(c->h_coll); free(c->h_cross); free(c->h_fis); free(c->h_rng);
+    free(c->h_fate); free(c->h_g);
+    c->h_coll = c->h_cross = c->h_fis = c->h_fate = c->h_g = NULL; c->h_rng = NULL;
+    free(c->bank); c->bank = NULL; c->nbank = 0; c->nhist = 0;
+}
+
+void orc_destroy(orc_ctx *c)
+{
+    if (!c) return;
+    free_results(c);
+    for (int i = 0; i < c->nl; i++) free(c->lat[i].univ);
+    for (int i = 0; i < c->nm; i++) {
+        MatMG *m = &c->mg[i];
+        free(m->sigt); free(m->sigs); free(m->nusf); free(m->chi); free(m->mfp); free(m->mu);
+        free(m->mufl); free(m->mufr); free(m->ps); free(m->stot); free(m->scdf); free(m->chicdf);
+    }
+    for (int i = 0; i < c->nn; i++) {
+        free(c->nuc[i].E); free(c->nuc[i].s); free(c->nuc[i].c); free(c->nuc[i].f);
+    }
+    for (int i = 0; i < c->nmc; i++) { free(c->mce[i].nuc); free(c->mce[i].dens); }
+    for (int i = 0; i < c->nt; i++) free(c->tally[i].edges);
+    free(c->src.edata); free(c->src.ecdf);
+    free(c->surf); free(c->cell); free(c->hs_surf); free(c->hs_sense); free(c->lat);
+    free(c->uoff); free(c->ulist); free(c->mg); free(c->nuc); free(c->mce); free(c->tally);
+    free(c);
+}
+
+const char *orc_error(const orc_ctx *c) { return c ? c->err : "null context"; }
+
+int orc_add_surface(orc_ctx *c, int type, const double coef[4], int bc)
+{
+    if (type < ORC_PX || type > ORC_SPHERE || bc < 0 || bc > 2)
+        return fail(c, ORC_EINVAL, "bad surface type/bc");
+    if (bc == ORC_BC_REFLECT && type > ORC_PLANE)
+        return fail(c, ORC_EINVAL, "reflective boundaries must be planes");
+    c->surf = xgrow(c->surf, c->ns + 1, sizeof(Surface));
+    Surface *s = &c->surf[c->ns];
+    s->type = type;
+    s->bc = bc;
+    memcpy(s->c, coef, sizeof s->c);
+    double R = type == ORC_CYLZ ? coef[2] : coef[3];
+    s->r2 = R * R;
+    return c->ns++;
+}
+
+int orc_add_cell(orc_ctx *c, int universe, int n, const int *surf, const int *sense,
+                 int fill_kind, int fill)
+{
+    if (universe < 0 || n < 0 || fill < 0) return fail(c, ORC_EINVAL, "bad cell");
+    for (int k = 0; k < n; k++)
+        if (surf[k] < 0 || surf[k] >= c->ns || (sense[k] != 1 && sense[k] != -1))
+            return fail(c, ORC_EINVAL, "bad half-space in cell %d", c->nc);
+    c->cell = xgrow(c->cell, c->nc + 1, sizeof(Cell));
+    c->hs_surf = xgrow(c->hs_surf, c->nhs + n, sizeof(int));
+    c->hs_sense = xgrow(c->hs_sense, c->nhs + n, sizeof(int));
+    Cell *e = &c->cell[c->nc];
+    e->universe = universe;
+    e->nhs = n;
+    e->off = c->nhs;
+    e->fill_kind = fill_kind;
+    e->fill = fill;
+    for (int k = 0; k < n; k++) {
+        c->hs_surf[c->nhs + k] = surf[k];
+        c->hs_sense[c->nhs + k] = sense[k];
+    }
+    c->nhs += n;
+    return c->nc++;
+}
+
+int orc_add_lattice(orc_ctx *c, double x0, double y0, double pitch, int nx, int ny,
+                    const int *universes)
+{
+    if (nx <= 0 || ny <= 0 || !(pitch > 0.0)) return fail(c, ORC_EINVAL, "bad lattice");
+    c->lat = xgrow(c->lat, c->nl + 1, sizeof(Lattice));
+    Lattice *L = &c->lat[c->nl];
+    L->x0 = x0; L->y0 = y0; L->pitch = pitch; L->nx = nx; L->ny = ny;
+    L->univ = malloc(sizeof(int) * (size_t)nx * ny);
+    memcpy(L->univ, universes, sizeof(int) * (size_t)nx * ny);
+    return c->nl++;
+}
+
+int orc_set_groups(orc_ctx *c, int G)
+{
+    if (G <= 0 || c->nm) return fail(c, ORC_EINVAL, "bad group count");
+    c->G = G;
+    c->ce = 0;
+    return 0;
+}
+
+/* cumulative distribution of non-negative weights: partial sums in order divided
+ * by the total; the last entry is exactly 1.  Sampling takes the first k with
+ * xi <= cdf[k].                                                              */
+static void make_cdf(const double *w, int n, double *cdf)
+{
+    double acc = 0.0;
+    for (int k = 0; k < n; k++) {
+        acc = acc + w[k];
+        cdf[k] = acc;
+    }
+    for (int k = 0; k < n; k++) cdf[k] = cdf[k] / acc;
+    cdf[n - 1] = 1.0;
+}
+
+static int sample_cdf(const double *cdf, int n, double xi)
+{
+    for (int k = 0; k < n; k++)
+        if (xi <= cdf[k]) return k;
+    return n - 1;
+}
+
+int orc_add_material_mg(orc_ctx *c, const double *sigma_t, const double *sigma_s,
+                        const double *nu_sigma_f, const double *chi)
+{
+    int G = c->G;
+    if (c->ce != 0 || G <= 0) return fail(c, ORC_ESTATE, "set groups first");
+    c->mg = xgrow(c->mg, c->nm + 1, sizeof(MatMG));
+    MatMG *m = &c->mg[c->nm];
+    m->sigt = dup_d(sigma_t, G);
+    m->sigs = dup_d(sigma_s, G * G);
+    m->nusf = dup_d(nu_sigma_f, G);
+    m->chi = dup_d(chi, G);
+    m->mfp = malloc(sizeof(double) * G);
+    m->mu = malloc(sizeof(double) * G);
+    m->mufl = malloc(sizeof(double) * G);
+    m->mufr = malloc(sizeof(double) * G);
+    m->ps = malloc(sizeof(double) * G);
+    m->stot = malloc(sizeof(double) * G);
+    m->scdf = malloc(sizeof(double) * G * G);
+    m->chicdf = malloc(sizeof(double) * G);
+    m->fissile = 0;
+    for (int g = 0; g < G; g++) {
+        if (sigma_t[g] < 0.0 || nu_sigma_f[g] < 0.0) return fail(c, ORC_EINVAL, "negative XS");
+        double acc = 0.0;
+        for (int h = 0; h < G; h++) {
+            if (sigma_s[g * G + h] < 0.0) return fail(c, ORC_EINVAL, "negative XS");
+            acc = acc + sigma_s[g * G + h];
+        }
+        if (acc > sigma_t[g]) return fail(c, ORC_EINVAL, "scattering exceeds total");
+        m->stot[g] = acc;
+        /* Reading: per-group constants are rounded once: mean free path 1/Sigma_t,
+         * fission yield mu = nuSigma_f/Sigma_t and scattering probability
+         * Sigma_s,tot/Sigma_t (all 0 in a void, Sigma_t = 0).                   */
+        m->mfp[g] = sigma_t[g] > 0.0 ? 1.0 / sigma_t[g] : INF;
+        m->mu[g] = sigma_t[g] > 0.0 ? nu_sigma_f[g] / sigma_t[g] : 0.0;
+        m->mufl[g] = floor(m->mu[g]);
+        m->mufr[g] = m->mu[g] - m->mufl[g];
+        m->ps[g] = sigma_t[g] > 0.0 ? acc / sigma_t[g] : 0.0;
+        if (acc > 0.0) make_cdf(&sigma_s[g * G], G, &m->scdf[g * G]);
+        else for (int h = 0; h < G; h++) m->scdf[g * G + h] = 1.0;
+        if (nu_sigma_f[g] > 0.0) m->fissile = 1;
+    }
+    double csum = 0.0;
+    for (int g = 0; g < G; g++) csum += chi[g];
+    if (csum > 0.0) make_cdf(chi, G, m->chicdf);
+    else for (int g = 0; g < G; g++) m->chicdf[g] = 1.0;
+    return c->nm++;
+}
+
+int orc_add_nuclide(orc_ctx *c, double A, int n, const double *E, const double *sig_s,
+                    const double *sig_c, const double *sig_f, double nu)
+{
+    if (c->ce == 0) return fail(c, ORC_ESTATE, "problem is multigroup");
+    if (n < 2 || !(A > 0.0)) return fail(c, ORC_EINVAL, "bad nuclide");
+    for (int k = 1; k < n; k++)
+        if (!(E[k] > E[k - 1])) return fail(c, ORC_EINVAL, "energy grid not increasing");
+    c->ce = 1;
+    c->nuc = xgrow(c->nuc, c->nn + 1, sizeof(Nuclide));
+    Nuclide *u = &c->nuc[c->nn];
+    u->A = A; u->nu = nu; u->n = n;
+    u->E = dup_d(E, n); u->s = dup_d(sig_s, n); u->c = dup_d(sig_c, n); u->f = dup_d(sig_f, n);
+    return c->nn++;
+}
+
+int orc_add_material_ce(orc_ctx *c, int n, const int *nuclides, const double *density)
+{
+    if (c->ce != 1) return fail(c, ORC_ESTATE, "add nuclides first");
+    c->mce = xgrow(c->mce, c->nmc + 1, sizeof(MatCE));
+    MatCE *m = &c->mce[c->nmc];
+    m->n = n;
+    m->nuc = malloc(sizeof(int) * (n ? n : 1));
+    m->dens = dup_d(density, n);
+    m->fissile = 0;
+    for (int k = 0; k < n; k++) {
+        if (nuclides[k] < 0 || nuclides[k] >= c->nn) return fail(c, ORC_EINVAL, "bad nuclide id");
+        m->nuc[k] = nuclides[k];
+        const Nuclide *u = &c->nuc[nuclides[k]];
+        if (u->nu > 0.0)
+            for (int j = 0; j < u->n; j++)
+                if (u->f[j] > 0.0) { m->fissile = 1; break; }
+    }
+    return c->nmc++;
+}
+
+int orc_set_source(orc_ctx *c, int kind, const double *params, int accept, int energy_kind,
+                   const double *energy, int n_energy, int dir_kind, const double *beam)
+{
+    Source *s = &c->src;
+    free(s->edata); free(s->ecdf);
+    memset(s, 0, sizeof *s);
+    s->kind = kind; s->accept = accept; s->ekind = energy_kind; s->dkind = dir_kind;
+    memcpy(s->p, params, sizeof(double) * (kind == ORC_SRC_BOX ? 6 : 3));
+    if (dir_kind == ORC_DIR_BEAM) memcpy(s->beam, beam, sizeof s->beam);
+    s->ne = n_energy;
+    s->edata = dup_d(energy, n_energy);
+    s->ecdf = malloc(sizeof(double) * (n_energy ? n_energy : 1));
+    if (energy_kind == ORC_E_PDF) make_cdf(energy, n_energy, s->ecdf);
+    c->src_set = 1;
+    return 0;
+}
+
+int orc_add_tally(orc_ctx *c, int filter, int n_edges, const double *edges)
+{
+    c->tally = xgrow(c->tally, c->nt + 1, sizeof(Tally));
+    Tally *t = &c->tally[c->nt];
+    t->filter = filter;
+    t->nedges = n_edges;
+    t->edges = dup_d(edges, n_edges);
+    return c->nt++;
+}
+
+int orc_set_max_collisions(orc_ctx *c, int max_collisions)
+{
+    c->max_coll = max_collisions;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* geometry                                                                   */
+static double surf_f(const Surface *s, double x, double y, double z)
+{
+    switch (s->type) {
+    case ORC_PX: return x - s->c[0];
+    case ORC_PY: return y - s->c[0];
+    case ORC_PZ: return z - s->c[0];
+    case ORC_PLANE: return s->c[0] * x + s->c[1] * y + s->c[2] * z - s->c[3];
+    case ORC_CYLZ: {
+        double dx = x - s->c[0], dy = y - s->c[1];
+        return dx * dx + dy * dy - s->r2;
+    }
+    default: {
+        double dx = x - s->c[0], dy = y - s->c[1], dz = z - s->c[2];
+        return dx * dx + dy * dy + dz * dz - s->r2;
+    }
+    }
+}
+
+/* gradient of the surface function dotted with the direction (sign only used) */
+static double surf_gdot(const Surface *s, double x, double y, double z, double u, double v,
+                        double w)
+{
+    switch (s->type) {
+    case ORC_PX: return u;
+    case ORC_PY: return v;
+    case ORC_PZ: return w;
+    case ORC_PLANE: return s->c[0] * u + s->c[1] * v + s->c[2] * w;
+    case ORC_CYLZ: return (x - s->c[0]) * u + (y - s->c[1]) * v;
+    default: return (x - s->c[0]) * u + (y - s->c[1]) * v + (z - s->c[2]) * w;
+    }
+}
+
+/* Distance along the direction to where the particle leaves the half-space of
+ * the given sense.  Reading (the paper names surface tracking, Sec. 1, without
+ * rules): the root is chosen from the sense, not from evaluating the position,
+ * so a particle sitting on a surface it just crossed never re-hits it; roots
+ * use the cancellation-free quadratic forms; a negative root from round-off is
+ * taken as 0.                                                                */
+static double surf_dist(const Surface *s, int sense, double x, double y, double z, double u,
+                        double v, double w)
+{
+    double t;
+    if (s->type <= ORC_PLANE) {
+        double dn, f;
+        switch (s->type) {
+        case ORC_PX: dn = u; f = x - s->c[0]; break;
+        case ORC_PY: dn = v; f = y - s->c[0]; break;
+        case ORC_PZ: dn = w; f = z - s->c[0]; break;
+        default:
+            dn = s->c[0] * u + s->c[1] * v + s->c[2] * w;
+            f = s->c[0] * x + s->c[1] * y + s->c[2] * z - s->c[3];
+        }
+        if ((sense > 0 && dn < 0.0) || (sense < 0 && dn > 0.0)) {
+            t = -f / dn;
+            return t < 0.0 ? 0.0 : t;
+        }
+        return INF;
+    }
+    double a, b, cc;
+    if (s->type == ORC_CYLZ) {
+        double dx = x - s->c[0], dy = y - s->c[1];
+        a = u * u + v * v;
+        b = dx * u + dy * v;
+        cc = dx * dx + dy * dy - s->r2;
+    } else {
+        double dx = x - s->c[0], dy = y - s->c[1], dz = z - s->c[2];
+        a = u * u + v * v + w * w;
+        b = dx * u + dy * v + dz * w;
+        cc = dx * dx + dy * dy + dz * dz - s->r2;
+    }
+    if (a == 0.0) return INF;
+    double disc = b * b - a * cc;
+    if (sense < 0) {
+        if (disc < 0.0) disc = 0.0;
+        if (b <= 0.0) t = (-b + sqrt(disc)) / a;
+        else t = -cc / (b + sqrt(disc));
+        return t < 0.0 ? 0.0 : t;
+    }
+    if (b >= 0.0 || disc < 0.0) return INF;
+    t = cc / (-b + sqrt(disc));
+    return t < 0.0 ? 0.0 : t;
+}
+
+static void build_universes(orc_ctx *c)
+{
+    int nu = 0;
+    for (int i = 0; i < c->nc; i++)
+        if (c->cell[i].universe + 1 > nu) nu = c->cell[i].universe + 1;
+    free(c->uoff); free(c->ulist);
+    c->nuniv = nu;
+    c->uoff = calloc((size_t)nu + 1, sizeof(int));
+    c->ulist = malloc(sizeof(int) * (c->nc ? c->nc : 1));
+    for (int i = 0; i < c->nc; i++) c->uoff[c->cell[i].universe + 1]++;
+    for (int u = 0; u < nu; u++) c->uoff[u + 1] += c->uoff[u];
+    int *fill = calloc((size_t)nu, sizeof(int));
+    for (int i = 0; i < c->nc; i++) {
+        int u = c->cell[i].universe;
+        c->ulist[c->uoff[u] + fill[u]++] = i;
+    }
+    free(fill);
+}
+
+/* The cell of universe U containing the point: every half-space must agree.
+ * The sense of a surface is the sign of its function; exactly on a surface the
+ * sign of (gradient . direction) decides, 0 counting as +.  `forced` (a
+ * surface just crossed) takes `forced_sense` instead.  Cells are scanned in
+ * definition order; the first match is returned (cells must partition space). */
+static int locate_univ(const orc_ctx *c, int U, double x, double y, double z, double u, double v,
+                       double w, int forced, int forced_sense)
+{
+    if (U < 0 || U >= c->nuniv) return -1;
+    for (int k = c->uoff[U]; k < c->uoff[U + 1]; k++) {
+        const Cell *e = &c->cell[c->ulist[k]];
+        int ok = 1;
+        for (int h = 0; h < e->nhs && ok; h++) {
+            int sid = c->hs_surf[e->off + h];
+            int sense;
+            if (sid == forced) {
+                sense = forced_sense;
+            } else {
+                const Surface *s = &c->surf[sid];
+                double f = surf_f(s, x, y, z);
+                if (f > 0.0) sense = 1;
+                else if (f < 0.0) sense = -1;
+                else sense = surf_gdot(s, x, y, z, u, v, w) >= 0.0 ? 1 : -1;
+            }
+            if (sense != c->hs_sense[e->off + h]) ok = 0;
+        }
+        if (ok) return c->ulist[k];
+    }
+    return -1;
+}
+
+typedef struct {
+    double x, y, z, u, v, w, E;
+    int g;
+    uint64_t s;
+    int cell, ix, iy, ucell, mat;
+    int64_t index, root;
+    int nfis, ncoll, ncross, alive, fate;
+} Particle;
+
+/* history fates */
+enum { FATE_ABSORBED = 0, FATE_LEAKED = 1, FATE_CUT = 2, FATE_LOST = 3, FATE_CAPPED = 4 };
+
+static void local_xy(const Lattice *L, int ix, int iy, double x, double y, double *xl, double *yl)
+{
+    *xl = x - (L->x0 + ((double)ix + 0.5) * L->pitch);
+    *yl = y - (L->y0 + ((double)iy + 0.5) * L->pitch);
+}
+
+/* Lattice element from a position: floor((x - x0)/pitch), clamped to the lattice. */
+static void lattice_index(const Lattice *L, double x, double y, int *ix, int *iy)
+{
+    int i = (int)floor((x - L->x0) / L->pitch);
+    int j = (int)floor((y - L->y0) / L->pitch);
+    *ix = i < 0 ? 0 : (i >= L->nx ? L->nx - 1 : i);
+    *iy = j < 0 ? 0 : (j >= L->ny ? L->ny - 1 : j);
+}
+
+/* Below the root cell: if it holds a lattice, find the element and the cell of
+ * the element's universe (in element-centred coordinates); set the material. */
+static int descend(const orc_ctx *c, Particle *p, int forced, int forced_sense)
+{
+    const Cell *rc = &c->cell[p->cell];
+    if (rc->fill_kind == ORC_FILL_LATTICE) {
+        const Lattice *L = &c->lat[rc->fill];
+        double xl, yl;
+        local_xy(L, p->ix, p->iy, p->x, p->y, &xl, &yl);
+        int U = L->univ[p->ix + L->nx * p->iy];
+        int uc = locate_univ(c, U, xl, yl, p->z, p->u, p->v, p->w, forced, forced_sense);
+        if (uc < 0) return -1;
+        p->ucell = uc;
+        p->mat = c->cell[uc].fill;
+    } else {
+        p->ucell = -1;
+        p->ix = p->iy = -1;
+        p->mat = rc->fill;
+    }
+    return 0;
+}
+
+static int locate_full(const orc_ctx *c, Particle *p)
+{
+    int rc = locate_univ(c, 0, p->x, p->y, p->z, p->u, p->v, p->w, -1, 0);
+    if (rc < 0) return -1;
+    p->cell = rc;
+    if (c->cell[rc].fill_kind == ORC_FILL_LATTICE)
+        lattice_index(&c->lat[c->cell[rc].fill], p->x, p->y, &p->ix, &p->iy);
+    return descend(c, p, -1, 0);
+}
+
+enum { B_NONE = 0, B_ROOT = 1, B_LATX = 2, B_LATY = 3, B_UNIV = 4 };
+
+/* Nearest boundary: the root cell's surfaces, then the lattice element walls
+ * (interior walls only), then the element universe cell's surfaces.  Reading:
+ * ties go to the earliest in that order (strict <).                          */
+static double boundary(const orc_ctx *c, const Particle *p, int *kind, int *which)
+{
+    double best = INF;
+    *kind = B_NONE;
+    *which = -1;
+    const Cell *rc = &c->cell[p->cell];
+    for (int h = 0; h < rc->nhs; h++) {
+        double t = surf_dist(&c->surf[c->hs_surf[rc->off + h]], c->hs_sense[rc->off + h], p->x,
+                             p->y, p->z, p->u, p->v, p->w);
+        if (t < best) { best = t; *kind = B_ROOT; *which = rc->off + h; }
+    }
+    if (rc->fill_kind == ORC_FILL_LATTICE) {
+        const Lattice *L = &c->lat[rc->fill];
+        double t = INF;
+        if (p->u > 0.0 && p->ix < L->nx - 1) t = (L->x0 + (double)(p->ix + 1) * L->pitch - p->x) / p->u;
+        else if (p->u < 0.0 && p->ix > 0) t = (L->x0 + (double)p->ix * L->pitch - p->x) / p->u;
+        if (t < 0.0) t = 0.0;
+        if (t < best) { best = t; *kind = B_LATX; }
+        t = INF;
+        if (p->v > 0.0 && p->iy < L->ny - 1) t = (L->y0 + (double)(p->iy + 1) * L->pitch - p->y) / p->v;
+        else if (p->v < 0.0 && p->iy > 0) t = (L->y0 + (double)p->iy * L->pitch - p->y) / p->v;
+        if (t < 0.0) t = 0.0;
+        if (t < best) { best = t; *kind = B_LATY; }
+        double xl, yl;
+        local_xy(L, p->ix, p->iy, p->x, p->y, &xl, &yl);
+        const Cell *uc = &c->cell[p->ucell];
+        for (int h = 0; h < uc->nhs; h++) {
+            double tt = surf_dist(&c->surf[c->hs_surf[uc->off + h]], c->hs_sense[uc->off + h], xl,
+                                  yl, p->z, p->u, p->v, p->w);
+            if (tt < best) { best = tt; *kind = B_UNIV; *which = uc->off + h; }
+        }
+    }
+    return best;
+}
+
+/* Surface crossing (Sec. 1, surface tracking).  Vacuum: the particle leaks.
+ * Reflective plane: Omega -= 2 (Omega.n) n / |n|^2, the cell is kept.
+ * Interior: the new cell is the one holding the point with the crossed
+ * surface's sense flipped.  Lattice wall: step the element index, relocate in
+ * the new element's universe.  Returns 0, 1 (leaked) or -1 (lost).           */
+static int cross(const orc_ctx *c, Particle *p, int kind, int which)
+{
+    if (kind == B_ROOT) {
+        int sid = c->hs_surf[which];
+        const Surface *s = &c->surf[sid];
+        if (s->bc == ORC_BC_VACUUM) return 1;
+        if (s->bc == ORC_BC_REFLECT) {
+            switch (s->type) {
+            case ORC_PX: p->u = -p->u; break;
+            case ORC_PY: p->v = -p->v; break;
+            case ORC_PZ: p->w = -p->w; break;
+            default: {
+                double dn = s->c[0] * p->u + s->c[1] * p->v + s->c[2] * p->w;
+                double nn = s->c[0] * s->c[0] + s->c[1] * s->c[1] + s->c[2] * s->c[2];
+                double k = 2.0 * dn / nn;
+                p->u = p->u - k * s->c[0];
+                p->v = p->v - k * s->c[1];
+                p->w = p->w - k * s->c[2];
+            }
+            }
+            return 0;
+        }
+        int nc = locate_univ(c, 0, p->x, p->y, p->z, p->u, p->v, p->w, sid, -c->hs_sense[which]);
+        if (nc < 0) return -1;
+        p->cell = nc;
+        if (c->cell[nc].fill_kind == ORC_FILL_LATTICE)
+            lattice_index(&c->lat[c->cell[nc].fill], p->x, p->y, &p->ix, &p->iy);
+        return descend(c, p, -1, 0);
+    }
+    if (kind == B_LATX || kind == B_LATY) {
+        if (kind == B_LATX) p->ix += p->u > 0.0 ? 1 : -1;
+        else p->iy += p->v > 0.0 ? 1 : -1;
+        return descend(c, p, -1, 0);
+    }
+    /* universe-level surface */
+    return descend(c, p, c->hs_surf[which], -c->hs_sense[which]);
+}
+
+int orc_probe(orc_ctx *c, const double pos[3], const double dir[3], int out_path[5],
+              double *dist, int *kind)
+{
+    build_universes(c);
+    Particle p;
+    memset(&p, 0, sizeof p);
+    p.x = pos[0]; p.y = pos[1]; p.z = pos[2];
+    p.u = dir[0]; p.v = dir[1]; p.w = dir[2];
+    if (locate_full(c, &p) < 0) return fail(c, ORC_ELOST, "point outside geometry");
+    out_path[0] = p.cell; out_path[1] = p.ix; out_path[2] = p.iy; out_path[3] = p.ucell;
+    out_path[4] = p.mat;
+    int which;
+    *dist = boundary(c, &p, kind, &which);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* continuous-energy lookup.  Reading: for each nuclide, the interval is the
+ * largest grid index j with E_j <= E (binary search, clamped to the last
+ * interval); cross sections are linear in E on it, with the interval's
+ * reciprocal width rounded once: f = (E - E_j) (1/(E_{j+1} - E_j)),
+ * sigma = sigma_j + f (sigma_{j+1} - sigma_j).  Macroscopic values are
+ * N_i sigma_i summed in the material's nuclide order; sigma_t,i =
+ * (sigma_s + sigma_c) + sigma_f.                                             */
+typedef struct {
+    double sigt, nusf;
+    double st[16], ss[16], sf[16];
+} CEXS;
+
+static int nuc_interval(const Nuclide *u, double E)
+{
+    int lo = 0, hi = u->n - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (u->E[mid] <= E) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+static void ce_lookup(const orc_ctx *c, int mat, double E, CEXS *x)
+{
+    const MatCE *m = &c->mce[mat];
+    x->sigt = 0.0;
+    x->nusf = 0.0;
+    for (int k = 0; k < m->n; k++) {
+        const Nuclide *u = &c->nuc[m->nuc[k]];
+        int j = nuc_interval(u, E);
+        double f = (E - u->E[j]) * (1.0 / (u->E[j + 1] - u->E[j]));
+        double ss = u->s[j] + f * (u->s[j + 1] - u->s[j]);
+        double sc = u->c[j] + f * (u->c[j + 1] - u->c[j]);
+        double sf = u->f[j] + f * (u->f[j + 1] - u->f[j]);
+        double st = ss + sc + sf;
+        x->st[k] = st; x->ss[k] = ss; x->sf[k] = sf;
+        x->sigt = x->sigt + m->dens[k] * st;
+        x->nusf = x->nusf + m->dens[k] * (u->nu * sf);
+    }
+}
+
+int orc_ce_lookup(orc_ctx *c, int material, double E, double out[4])
+{
+    if (c->ce != 1 || material < 0 || material >= c->nmc) return fail(c, ORC_EINVAL, "bad material");
+    CEXS x;
+    ce_lookup(c, material, E, &x);
+    out[0] = x.sigt; out[1] = x.nusf;
+    double ss = 0.0, sf = 0.0;
+    for (int k = 0; k < c->mce[material].n; k++) {
+        ss = ss + c->mce[material].dens[k] * x.ss[k];
+        sf = sf + c->mce[material].dens[k] * x.sf[k];
+    }
+    out[2] = ss; out[3] = sf;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* transport of one history                                                   */
+typedef struct {
+    double **acc;           /* per tally: [batch][bin * ne + e] */
+    double ktl, kc;
+    Site *bank;
+    int64_t nbank, capbank;
+    int64_t coll, crossn, leak, lost, capped;
+} Acc;
+
+typedef struct {            /* gradient records (one per score) */
+    int64_t n, cap;
+    int *param;
+    double *val, *ownb;
+    int *nfb;
+    int64_t *pid;
+    double *own;            /* own detector tally per particle (global index) */
+    int det_cell;
+    const double *weights;
+    int64_t pid_base;
+} Grad;
+
+static void bank_push(Acc *a, const Particle *p)
+{
+    if (a->nbank == a->capbank) {
+        a->capbank = a->capbank ? 2 * a->capbank : 1024;
+        a->bank = realloc(a->bank, sizeof(Site) * (size_t)a->capbank);
+    }
+    Site *s = &a->bank[a->nbank++];
+    s->x = p->x; s->y = p->y; s->z = p->z;
+    s->cell = p->cell; s->ix = p->ix; s->iy = p->iy; s->ucell = p->ucell; s->mat = p->mat;
+    s->parent = p->index; s->root = p->root; s->child = p->nfis;
+}
+
+static void grad_rec(Grad *gr, int param, double val, double ownb, int nfb, int64_t pid)
+{
+    if (gr->n == gr->cap) {
+        gr->cap = gr->cap ? 2 * gr->cap : 4096;
+        gr->param = realloc(gr->param, sizeof(int) * gr->cap);
+        gr->val = realloc(gr->val, sizeof(double) * gr->cap);
+        gr->ownb = realloc(gr->ownb, sizeof(double) * gr->cap);
+        gr->nfb = realloc(gr->nfb, sizeof(int) * gr->cap);
+        gr->pid = realloc(gr->pid, sizeof(int64_t) * gr->cap);
+    }
+    gr->param[gr->n] = param; gr->val[gr->n] = val; gr->ownb[gr->n] = ownb;
+    gr->nfb[gr->n] = nfb; gr->pid[gr->n] = pid;
+    gr->n++;
+}
+
+static int tally_bin(const orc_ctx *c, const Tally *t, const Particle *p, int *bin, int *e)
+{
+    switch (t->filter) {
+    case ORC_FILTER_CELL: *bin = p->ucell >= 0 ? p->ucell : p->cell; break;
+    case ORC_FILTER_LATTICE:
+        if (p->ucell < 0) return 0;
+        *bin = p->ix + c->lat[0].nx * p->iy;
+        break;
+    default: *bin = p->mat;
+    }
+    if (c->ce) {
+        /* energy bin: largest b with edges[b] <= E, the top edge closing the last bin */
+        if (p->E < t->edges[0] || p->E > t->edges[t->nedges - 1]) return 0;
+        int b = 0;
+        while (b + 1 < t->nedges - 1 && t->edges[b + 1] <= p->E) b++;
+        *e = b;
+    } else {
+        *e = p->g;
+    }
+    return 1;
+}
+
+static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr, int64_t pid)
+{
+    const int G = c->G;
+    double own = 0.0;
+    for (;;) {
+        if (p->ncoll + p->ncross >= MAX_EVENTS) { a->capped++; p->fate = FATE_CAPPED; break; }
+        /* cross sections at the particle's material and energy */
+        double sigt, mfp, nusf;
+        CEXS x;
+        const MatMG *m = NULL;
+        if (c->ce) {
+            ce_lookup(c, p->mat, p->E, &x);
+            sigt = x.sigt;
+            nusf = x.nusf;
+            mfp = sigt > 0.0 ? 1.0 / sigt : INF;
+        } else {
+            m = &c->mg[p->mat];
+            sigt = m->sigt[p->g];
+            nusf = m->nusf[p->g];
+            mfp = m->mfp[p->g];
+        }
+        /* distance to collision: d_c = -ln(xi) / Sigma_t (a draw is always taken) */
+        uint64_t n = draw_n(&p->s);
+        double dc = sigt > 0.0 ? -log_n(n) * mfp : INF;
+        int kind, which;
+        double ds = boundary(c, p, &kind, &which);
+        if (dc == INF && ds == INF) { a->lost++; p->fate = FATE_LOST; break; }
+        int coll = dc < ds;              /* ties: surface crossing */
+        double d = coll ? dc : ds;
+        p->x = p->x + d * p->u;
+        p->y = p->y + d * p->v;
+        p->z = p->z + d * p->w;
+        /* track-length estimators */
+        for (int t = 0; t < c->nt; t++) {
+            int bin, e;
+            if (tally_bin(c, &c->tally[t], p, &bin, &e)) {
+                a->acc[t][(size_t)batch * c->tally[t].nbins * c->tally[t].ne +
+                          (size_t)bin * c->tally[t].ne + e] += d;
+            }
+        }
+        a->ktl += d * nusf;
+        double ownb = own;
+        if (gr && (p->ucell >= 0 ? p->ucell : p->cell) == gr->det_cell)
+            own = own + gr->weights[p->g] * d;
+        if (!coll) {
+            p->ncross++;
+            if (gr && sigt != 0.0) grad_rec(gr, p->mat * G + p->g, -d, ownb, p->nfis, pid);
+            int r = cross(c, p, kind, which);
+            if (r == 1) { a->leak++; p->fate = FATE_LEAKED; break; }
+            if (r < 0) { a->lost++; p->fate = FATE_LOST; break; }
+            continue;
+        }
+        /* collision */
+        p->ncoll++;
+        int nfb = p->nfis;
+        if (!c->ce) {
+            int g = p->g;
+            a->kc += m->mu[g];
+            if (gr) grad_rec(gr, p->mat * G + g, mfp - d, ownb, nfb, pid);
+            /* fission sites: floor(mu) + [xi <= frac(mu)], mu = nuSigma_f/Sigma_t.
+             * Reading: no division by k; the population is controlled by resampling. */
+            double xi = draw(&p->s);
+            int nf = (int)m->mufl[g] + (xi <= m->mufr[g] ? 1 : 0);
+            if (gr && m->nusf[g] != 0.0 && m->mufr[g] != 0.0) {
+                double fac = nf > (int)m->mufl[g] ? 1.0 / m->mufr[g] : -1.0 / (1.0 - m->mufr[g]);
+                int nm = c->nm;
+                grad_rec(gr, nm * G + nm * G * G + p->mat * G + g, mfp * fac, ownb, nfb, pid);
+                grad_rec(gr, p->mat * G + g, -(m->mu[g] * mfp) * fac, ownb, nfb, pid);
+            }
+            for (int k = 0; k < nf; k++) { bank_push(a, p); p->nfis++; }
+            /* analog reaction: scatter with probability Sigma_s,tot / Sigma_t */
+            xi = draw(&p->s);
+            if (xi <= m->ps[g]) {
+                xi = draw(&p->s);
+                int gp = sample_cdf(&m->scdf[g * G], G, xi);
+                if (gr) {
+                    int nm = c->nm;
+                    grad_rec(gr, nm * G + (p->mat * G + g) * G + gp, 1.0 / m->sigs[g * G + gp], ownb,
+                             nfb, pid);
+                    grad_rec(gr, p->mat * G + g, -mfp, ownb, nfb, pid);
+                }
+                p->g = gp;
+                iso_dir(&p->s, &p->u, &p->v, &p->w);   /* isotropic (P0) scattering */
+            } else {
+                if (gr) {
+                    double sa = m->sigt[g] - m->stot[g];
+                    if (sa > 0.0) {
+                        int nm = c->nm;
+                        grad_rec(gr, p->mat * G + g, 1.0 / sa - mfp, ownb, nfb, pid);
+                        for (int h = 0; h < G; h++)
+                            if (m->sigs[g * G + h] != 0.0)
+                                grad_rec(gr, nm * G + (p->mat * G + g) * G + h, -1.0 / sa, ownb, nfb,
+                                         pid);
+                    }
+                }
+                p->alive = 0;
+            }
+        } else {
+            const MatCE *mc = &c->mce[p->mat];
+            a->kc += nusf / sigt;
+            /* nuclide by xi Sigma_t against the running sum of N_i sigma_t,i */
+            double target = draw(&p->s) * sigt;
+            double cum = 0.0;
+            int sel = mc->n - 1;
+            for (int k = 0; k < mc->n; k++) {
+                cum = cum + mc->dens[k] * x.st[k];
+                if (target <= cum) { sel = k; break; }
+            }
+            const Nuclide *u = &c->nuc[mc->nuc[sel]];
+            double mu = u->nu * x.sf[sel] / x.st[sel];
+            double fl = floor(mu);
+            double xi = draw(&p->s);
+            int nf = (int)fl + (xi <= mu - fl ? 1 : 0);
+            for (int k = 0; k < nf; k++) { bank_push(a, p); p->nfis++; }
+            /* scatter (elastic, target at rest) with probability sigma_s,i/sigma_t,i */
+            xi = draw(&p->s);
+            if (xi * x.st[sel] <= x.ss[sel]) p->E = elastic(p->E, u->A, &p->s, &p->u, &p->v, &p->w);
+            else p->alive = 0;
+        }
+        if (!p->alive) { p->fate = FATE_ABSORBED; break; }
+        if (c->max_coll && p->ncoll >= c->max_coll) { p->alive = 0; p->fate = FATE_CUT; break; }
+    }
+    if (gr) gr->own[pid] = own;
+    a->coll += p->ncoll;
+    a->crossn += p->ncross;
+}
+
+/* ------------------------------------------------------------------------- */
+/* sources                                                                    */
+static int birth_energy(const orc_ctx *c, Particle *p)
+{
+    if (c->ce) p->E = maxwell(&p->s);
+    else p->g = sample_cdf(c->mg[p->mat].chicdf, c->G, draw(&p->s));
+    return 0;
+}
+
+static int mat_fissile(const orc_ctx *c, int mat)
+{
+    return c->ce ? c->mce[mat].fissile : c->mg[mat].fissile;
+}
+
+/* Draw order: position (3 draws per rejection attempt for a box), energy
+ * (group or E), direction.  The point is located with a zero direction.     */
+static int sample_source(const orc_ctx *c, Particle *p)
+{
+    const Source *s = &c->src;
+    p->u = p->v = p->w = 0.0;
+    if (s->kind == ORC_SRC_BOX) {
+        int ok = 0;
+        for (int t = 0; t < MAX_TRIES && !ok; t++) {
+            p->x = s->p[0] + draw(&p->s) * (s->p[1] - s->p[0]);
+            p->y = s->p[2] + draw(&p->s) * (s->p[3] - s->p[2]);
+            p->z = s->p[4] + draw(&p->s) * (s->p[5] - s->p[4]);
+            if (locate_full(c, p) < 0) continue;
+            ok = s->accept == ORC_ACCEPT_ANY || mat_fissile(c, p->mat);
+        }
+        if (!ok) return -1;
+    } else {
+        p->x = s->p[0]; p->y = s->p[1]; p->z = s->p[2];
+        if (locate_full(c, p) < 0) return -1;
+    }
+    switch (s->ekind) {
+    case ORC_E_CHI: birth_energy(c, p); break;
+    case ORC_E_PDF: p->g = sample_cdf(s->ecdf, s->ne, draw(&p->s)); break;
+    case ORC_E_FIXED: p->E = s->edata[0]; break;
+    default: p->E = maxwell(&p->s);
+    }
+    if (s->dkind == ORC_DIR_BEAM) { p->u = s->beam[0]; p->v = s->beam[1]; p->w = s->beam[2]; }
+    else iso_dir(&p->s, &p->u, &p->v, &p->w);
+    return 0;
+}
+
+static void from_site(const orc_ctx *c, Particle *p, const Site *b)
+{
+    p->x = b->x; p->y = b->y; p->z = b->z;
+    p->cell = b->cell; p->ix = b->ix; p->iy = b->iy; p->ucell = b->ucell; p->mat = b->mat;
+    birth_energy(c, p);
+    iso_dir(&p->s, &p->u, &p->v, &p->w);
+}
+
+static int site_cmp(const void *a, const void *b)
+{
+    const Site *x = a, *y = b;
+    if (x->parent != y->parent) return x->parent < y->parent ? -1 : 1;
+    return x->child < y->child ? -1 : (x->child > y->child);
+}
+
+/* ------------------------------------------------------------------------- */
+static int prepare(orc_ctx *c)
+{
+    if (!c->src_set) return fail(c, ORC_ESTATE, "no source");
+    if (c->nc == 0) return fail(c, ORC_ESTATE, "no cells");
+    if (c->ce < 0) return fail(c, ORC_ESTATE, "no materials");
+    build_universes(c);
+    for (int t = 0; t < c->nt; t++) {
+        Tally *T = &c->tally[t];
+        T->nbins = T->filter == ORC_FILTER_CELL ? c->nc
+                 : T->filter == ORC_FILTER_LATTICE ? (c->nl ? c->lat[0].nx * c->lat[0].ny : 0)
+                 : (c->ce ? c->nmc : c->nm);
+        T->ne = c->ce ? T->nedges - 1 : c->G;
+        if (c->ce && T->nedges < 2) return fail(c, ORC_EINVAL, "CE tally needs energy edges");
+    }
+    free_results(c);
+    memset(c->counters, 0, sizeof c->counters);
+    c->t_sum = calloc(c->nt ? c->nt : 1, sizeof(double *));
+    c->t_sum2 = calloc(c->nt ? c->nt : 1, sizeof(double *));
+    c->t_mean = calloc(c->nt ? c->nt : 1, sizeof(double *));
+    c->t_sd = calloc(c->nt ? c->nt : 1, sizeof(double *));
+    for (int t = 0; t < c->nt; t++) {
+        size_t nb = (size_t)c->tally[t].nbins * c->tally[t].ne;
+        c->t_sum[t] = calloc(nb ? nb : 1, sizeof(double));
+        c->t_sum2[t] = calloc(nb ? nb : 1, sizeof(double));
+        c->t_mean[t] = calloc(nb ? nb : 1, sizeof(double));
+        c->t_sd[t] = calloc(nb ? nb : 1, sizeof(double));
+    }
+    return 0;
+}
+
+static Acc *make_accs(const orc_ctx *c, int nthr, int nbatch)
+{
+    Acc *A = calloc((size_t)nthr, sizeof(Acc));
+    for (int i = 0; i < nthr; i++) {
+        A[i].acc = calloc(c->nt ? c->nt : 1, sizeof(double *));
+        for (int t = 0; t < c->nt; t++)
+            A[i].acc[t] = calloc((size_t)nbatch * c->tally[t].nbins * c->tally[t].ne + 1,
+                                 sizeof(double));
+    }
+    return A;
+}
+
+static void free_accs(const orc_ctx *c, Acc *A, int nthr)
+{
+    for (int i = 0; i < nthr; i++) {
+        for (int t = 0; t < c->nt; t++) free(A[i].acc[t]);
+        free(A[i].acc);
+        free(A[i].bank);
+    }
+    free(A);
+}
+
+/* merge per-thread banks and sort them by (parent, child): the order is unique */
+static Site *merge_banks(Acc *A, int nthr, int64_t *M)
+{
+    int64_t tot = 0;
+    for (int i = 0; i < nthr; i++) tot += A[i].nbank;
+    Site *b = malloc(sizeof(Site) * (size_t)(tot ? tot : 1));
+    int64_t k = 0;
+    for (int i = 0; i < nthr; i++) {
+        memcpy(b + k, A[i].bank, sizeof(Site) * (size_t)A[i].nbank);
+        k += A[i].nbank;
+        A[i].nbank = 0;
+    }
+    qsort(b, (size_t)tot, sizeof(Site), site_cmp);
+    *M = tot;
+    return b;
+}
+
+static int nthreads(int threads)
+{
+#ifdef _OPENMP
+    return threads > 0 ? threads : omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
+}
+
+static void record_histories(orc_ctx *c, const Particle *P, int64_t n)
+{
+    free(c->h_coll); free(c->h_cross); free(c->h_fis); free(c->h_rng);
+    free(c->h_fate); free(c->h_g);
+    c->nhist = n;
+    c->h_fate = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    c->h_g = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    c->h_coll = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    c->h_cross = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    c->h_fis = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    c->h_rng = malloc(sizeof(uint64_t) * (size_t)(n ? n : 1));
+    for (int64_t j = 0; j < n; j++) {
+        c->h_coll[j] = P[j].ncoll; c->h_cross[j] = P[j].ncross;
+        c->h_fis[j] = P[j].nfis; c->h_rng[j] = P[j].s;
+        c->h_fate[j] = P[j].fate; c->h_g[j] = P[j].g;
+    }
+}
+
+static void sum_counters(orc_ctx *c, Acc *A, int nthr)
+{
+    for (int i = 0; i < nthr; i++) {
+        c->counters[1] += A[i].coll; c->counters[2] += A[i].crossn; c->counters[3] += A[i].leak;
+        c->counters[4] += A[i].lost; c->counters[5] += A[i].capped;
+        A[i].coll = A[i].crossn = A[i].leak = A[i].lost = A[i].capped = 0;
+    }
+}
+
+static void mean_sd(double sum, double sum2, int n, double *mean, double *sd)
+{
+    *mean = sum / n;
+    if (n > 1) {
+        double var = (sum2 - n * (*mean) * (*mean)) / (n - 1);
+        *sd = sqrt(var > 0.0 ? var / n : 0.0);
+    } else {
+        *sd = 0.0;
+    }
+}
+
+/* Power iteration (Sec. 4 runs 50 inactive + 100 active cycles).  Reading:
+ * cycle c's particle j uses stream c 2^32 + j; after a cycle the bank (sorted
+ * by parent and child) of M sites is resampled systematically to N:
+ * site j <- bank[floor((j + xi) M / N)], xi the first draw of stream
+ * c 2^32 + 2^32 - 1.  Per cycle k_analog = M/N, k_TL = sum d nuSigma_f / N,
+ * k_C = sum nuSigma_f/Sigma_t / N; k and tallies are means over active
+ * cycles with sd = s / sqrt(n_active).                                        */
+int orc_run_eigen(orc_ctx *c, int64_t n, int inactive, int active, uint64_t seed, int threads)
+{
+    int r = prepare(c);
+    if (r) return r;
+    if (n <= 0 || active < 1 || inactive < 0) return fail(c, ORC_EINVAL, "bad run size");
+    int nthr = nthreads(threads);
+    int ncyc = inactive + active;
+    Acc *A = make_accs(c, nthr, 1);
+    Particle *P = calloc((size_t)n, sizeof(Particle));
+    int64_t *site = malloc(sizeof(int64_t) * (size_t)n);
+    Site *bank = NULL;
+    int64_t M = 0;
+    c->ncyc = ncyc;
+    c->cyc_ktl = calloc((size_t)ncyc, sizeof(double));
+    c->cyc_kc = calloc((size_t)ncyc, sizeof(double));
+    c->cyc_m = calloc((size_t)ncyc, sizeof(int64_t));
+    double ks[3] = {0, 0, 0}, ks2[3] = {0, 0, 0};
+    int err = 0;
+    for (int cyc = 0; cyc < ncyc && !err; cyc++) {
+        int bad = 0;
+#pragma omp parallel for num_threads(nthr) schedule(static) reduction(+ : bad)
+        for (int64_t j = 0; j < n; j++) {
+            Particle *p = &P[j];
+            memset(p, 0, sizeof *p);
+            p->s = orc_rng_stream(seed, ((uint64_t)cyc << 32) + (uint64_t)j);
+            p->index = j;
+            p->root = j;
+            p->alive = 1;
+            if (cyc == 0) {
+                if (sample_source(c, p) < 0) { bad++; continue; }
+            } else {
+                from_site(c, p, &bank[site[j]]);
+            }
+#ifdef _OPENMP
+            Acc *a = &A[omp_get_thread_num()];
+#else
+            Acc *a = &A[0];
+#endif
+            transport(c, p, a, 0, NULL, j);
+        }
+        if (bad) { err = fail(c, ORC_ESTATE, "source sampling failed"); break; }
+        free(bank);
+        bank = merge_banks(A, nthr, &M);
+        double ktl = 0.0, kc = 0.0;
+        for (int i = 0; i < nthr; i++) { ktl += A[i].ktl; kc += A[i].kc; A[i].ktl = A[i].kc = 0.0; }
+        ktl /= (double)n;
+        kc /= (double)n;
+        double ka = (double)M / (double)n;
+        c->cyc_ktl[cyc] = ktl; c->cyc_kc[cyc] = kc; c->cyc_m[cyc] = M;
+        for (int t = 0; t < c->nt; t++) {
+            size_t nb = (size_t)c->tally[t].nbins * c->tally[t].ne;
+            for (size_t b = 0; b < nb; b++) {
+                double v = 0.0;
+                for (int i = 0; i < nthr; i++) { v += A[i].acc[t][b]; A[i].acc[t][b] = 0.0; }
+                v /= (double)n;
+                if (cyc >= inactive) { c->t_sum[t][b] += v; c->t_sum2[t][b] += v * v; }
+            }
+        }
+        if (cyc >= inactive) {
+            double kv[3] = {ktl, kc, ka};
+            for (int q = 0; q < 3; q++) { ks[q] += kv[q]; ks2[q] += kv[q] * kv[q]; }
+        }
+        sum_counters(c, A, nthr);
+        c->counters[0] += n;
+        if (cyc == ncyc - 1) record_histories(c, P, n);
+        if (M == 0) { err = fail(c, ORC_ESTATE, "fission bank empty after cycle %d", cyc); break; }
+        uint64_t rs = orc_rng_stream(seed, ((uint64_t)cyc << 32) + 0xFFFFFFFFULL);
+        double xi = draw(&rs);
+        for (int64_t j = 0; j < n; j++) {
+            double t = ((double)j + xi) * (double)M / (double)n;
+            int64_t idx = (int64_t)t;
+            site[j] = idx >= M ? M - 1 : idx;
+        }
+    }
+    if (!err) {
+        for (int q = 0; q < 3; q++) mean_sd(ks[q], ks2[q], active, &c->k[2 * q], &c->k[2 * q + 1]);
+        for (int t = 0; t < c->nt; t++) {
+            size_t nb = (size_t)c->tally[t].nbins * c->tally[t].ne;
+            for (size_t b = 0; b < nb; b++)
+                mean_sd(c->t_sum[t][b], c->t_sum2[t][b], active, &c->t_mean[t][b], &c->t_sd[t][b]);
+        }
+        c->nbank = M;
+        c->bank = bank;
+        bank = NULL;
+        if (c->counters[4] > 0 && (double)c->counters[4] > 1e-6 * (double)c->counters[0])
+            err = fail(c, ORC_ELOST, "lost particles: %lld", (long long)c->counters[4]);
+    }
+    c->counters[6] = ncyc;
+    free(bank); free(site); free(P);
+    free_accs(c, A, nthr);
+    return err;
+}
+
+/* Fixed source: generation 0 from the source (stream j), generation g+1 is the
+ * whole sorted bank of generation g (stream (g+1) 2^32 + j), until the bank is
+ * empty.  Reading: source particle j belongs to batch floor(j B / N) and its
+ * descendants inherit it; tallies are batch means per source particle.       */
+static int run_fixed(orc_ctx *c, int64_t n, int batches, uint64_t seed, int threads, Grad *gr)
+{
+    int r = prepare(c);
+    if (r) return r;
+    if (n <= 0 || batches < 1 || batches > n) return fail(c, ORC_EINVAL, "bad run size");
+    int nthr = gr ? 1 : nthreads(threads);
+    Acc *A = make_accs(c, nthr, batches);
+    Site *bank = NULL;
+    int64_t M = 0, ngen_n = n;
+    int err = 0, gen;
+    int64_t *gen_base = NULL, *gen_n = NULL;
+    int64_t **gen_off = NULL;   /* per generation: first child index of each particle */
+    for (gen = 0; gen < MAX_GEN; gen++) {
+        Particle *P = calloc((size_t)ngen_n, sizeof(Particle));
+        int bad = 0;
+        int64_t base = 0;
+        if (gr) {
+            gen_base = realloc(gen_base, sizeof(int64_t) * (gen + 1));
+            gen_n = realloc(gen_n, sizeof(int64_t) * (gen + 1));
+            gen_off = realloc(gen_off, sizeof(int64_t *) * (gen + 1));
+            base = gen ? gen_base[gen - 1] + gen_n[gen - 1] : 0;
+            gen_base[gen] = base;
+            gen_n[gen] = ngen_n;
+            gr->own = realloc(gr->own, sizeof(double) * (size_t)(base + ngen_n));
+        }
+#pragma omp parallel for num_threads(nthr) schedule(static) reduction(+ : bad)
+        for (int64_t j = 0; j < ngen_n; j++) {
+            Particle *p = &P[j];
+            p->s = orc_rng_stream(seed, ((uint64_t)gen << 32) + (uint64_t)j);
+            p->index = j;
+            p->alive = 1;
+            if (gen == 0) {
+                p->root = j;
+                if (sample_source(c, p) < 0) { bad++; continue; }
+            } else {
+                p->root = bank[j].root;
+                from_site(c, p, &bank[j]);
+            }
+#ifdef _OPENMP
+            Acc *a = &A[omp_get_thread_num()];
+#else
+            Acc *a = &A[0];
+#endif
+            int batch = (int)((p->root * (int64_t)batches) / n);
+            transport(c, p, a, batch, gr, gr ? base + j : j);
+        }
+        if (bad) { free(P); err = fail(c, ORC_ESTATE, "source sampling failed"); break; }
+        if (gen == 0) record_histories(c, P, ngen_n);
+        sum_counters(c, A, nthr);
+        c->counters[0] += ngen_n;
+        Site *nb = merge_banks(A, nthr, &M);
+        if (gen == 0) {
+            c->bank = malloc(sizeof(Site) * (size_t)(M ? M : 1));
+            memcpy(c->bank, nb, sizeof(Site) * (size_t)M);
+            c->nbank = M;
+        }
+        if (gr) {
+            int64_t *off = malloc(sizeof(int64_t) * (size_t)(ngen_n + 1));
+            for (int64_t j = 0; j <= ngen_n; j++) off[j] = 0;
+            for (int64_t k = 0; k < M; k++) off[nb[k].parent + 1]++;
+            for (int64_t j = 0; j < ngen_n; j++) off[j + 1] += off[j];
+            gen_off[gen] = off;
+        }
+        free(P);
+        free(bank);
+        bank = nb;
+        ngen_n = M;
+        if (M == 0) break;
+    }
+    if (!err && gen == MAX_GEN) err = fail(c, ORC_ETIMEOUT, "generation limit reached");
+    c->counters[6] = gen + 1;
+    if (!err) {
+        /* batch statistics */
+        int64_t *nb = calloc((size_t)batches, sizeof(int64_t));
+        for (int64_t j = 0; j < n; j++) nb[(j * batches) / n]++;
+        for (int t = 0; t < c->nt; t++) {
+            size_t ns = (size_t)c->tally[t].nbins * c->tally[t].ne;
+            for (size_t b = 0; b < ns; b++) {
+                double s = 0.0, s2 = 0.0;
+                for (int q = 0; q < batches; q++) {
+                    double v = 0.0;
+                    for (int i = 0; i < nthr; i++) v += A[i].acc[t][(size_t)q * ns + b];
+                    v /= (double)nb[q];
+                    s += v;
+                    s2 += v * v;
+                }
+                mean_sd(s, s2, batches, &c->t_mean[t][b], &c->t_sd[t][b]);
+            }
+        }
+        free(nb);
+        if (c->counters[4] > 0 && (double)c->counters[4] > 1e-6 * (double)c->counters[0])
+            err = fail(c, ORC_ELOST, "lost particles: %lld", (long long)c->counters[4]);
+    }
+    if (gr && !err) {
+        /* subtree totals, last generation first */
+        int ng = gen + 1 <= MAX_GEN ? gen + 1 : MAX_GEN;
+        int64_t tot = gen_base[ng - 1] + gen_n[ng - 1];
+        double *sub = malloc(sizeof(double) * (size_t)(tot ? tot : 1));
+        for (int g = ng - 1; g >= 0; g--) {
+            for (int64_t j = 0; j < gen_n[g]; j++) {
+                double s = gr->own[gen_base[g] + j];
+                if (g + 1 < ng)
+                    for (int64_t k = gen_off[g][j]; k < gen_off[g][j + 1]; k++)
+                        s += sub[gen_base[g + 1] + k];
+                sub[gen_base[g] + j] = s;
+            }
+        }
+        /* combine every score with its downstream tally D */
+        int npar = c->nm * c->G * (2 + c->G);
+        double *acc = calloc((size_t)npar, sizeof(double));
+        for (int64_t q = 0; q < gr->n; q++) {
+            int64_t pid = gr->pid[q];
+            int g = 0;
+            while (g + 1 < ng && pid >= gen_base[g + 1]) g++;
+            int64_t j = pid - gen_base[g];
+            double D = gr->own[pid] - gr->ownb[q];
+            if (g + 1 < ng)
+                for (int64_t k = gen_off[g][j] + gr->nfb[q]; k < gen_off[g][j + 1]; k++)
+                    D += sub[gen_base[g + 1] + k];
+            acc[gr->param[q]] += gr->val[q] * D;
+        }
+        for (int k = 0; k < npar; k++) acc[k] /= (double)n;
+        gr->val = realloc(gr->val, sizeof(double) * (size_t)(npar > gr->cap ? npar : gr->cap));
+        memcpy(gr->val, acc, sizeof(double) * (size_t)npar);
+        free(acc);
+        free(sub);
+    }
+    if (gr) {
+        for (int g = 0; g <= gen && g < MAX_GEN; g++) free(gen_off[g]);
+        free(gen_off); free(gen_base); free(gen_n);
+    }
+    free(bank);
+    free_accs(c, A, nthr);
+    return err;
+}
+
+int orc_run_fixed(orc_ctx *c, int64_t n, int batches, uint64_t seed, int threads)
+{
+    return run_fixed(c, n, batches, seed, threads, NULL);
+}
+
+/* Likelihood-ratio derivative of a cell's track-length tally (fixed source,
+ * multigroup).  The paper has no derivative; this is the textbook score
+ * function estimator: dE[T]/dtheta = E[sum_e s_e D_e], where s_e is the
+ * derivative of the log-probability of event e and D_e is the tally scored
+ * from the start of e's flight onward by the particle plus the full subtree
+ * tallies of the secondaries it banks at or after e.  Scores (weight 1):
+ *  flight ending at a surface        dSigma_t: -d
+ *  flight ending in a collision      dSigma_t: 1/Sigma_t - d
+ *  scatter g -> g'                   dSigma_s[g,g']: 1/Sigma_s[g,g'], dSigma_t: -1/Sigma_t
+ *  absorption (Sigma_a = Sigma_t - Sigma_s,tot)
+ *                                    dSigma_t: 1/Sigma_a - 1/Sigma_t, dSigma_s[g,*]: -1/Sigma_a
+ *  fission count, mu = nuSigma_f/Sigma_t, P(floor mu + 1) = frac mu
+ *                                    d log P = mu'/frac (n = floor+1) or -mu'/(1-frac),
+ *                                    mu'_nuSigma_f = 1/Sigma_t, mu'_Sigma_t = -mu/Sigma_t
+ * Parameters whose value is 0 (and fission counts with frac mu = 0) take no
+ * score.  This oracle stores every score with its context during the forward
+ * pass and combines them afterwards (no replay).                              */
+int orc_grad_fixed(orc_ctx *c, int64_t n, uint64_t seed, int cell, const double *weights,
+                   double *d_sigt, double *d_sigs, double *d_nusf, double *tally)
+{
+    if (c->ce) return fail(c, ORC_EINVAL, "derivatives are multigroup only");
+    Grad gr;
+    memset(&gr, 0, sizeof gr);
+    gr.det_cell = cell;
+    gr.weights = weights;
+    int mc = c->max_coll;
+    int r = run_fixed(c, n, 1, seed, 1, &gr);
+    c->max_coll = mc;
+    if (!r) {
+        int G = c->G, nm = c->nm;
+        memcpy(d_sigt, gr.val, sizeof(double) * nm * G);
+        memcpy(d_sigs, gr.val + nm * G, sizeof(double) * nm * G * G);
+        memcpy(d_nusf, gr.val + nm * G + nm * G * G, sizeof(double) * nm * G);
+        for (int t = 0; t < c->nt; t++)
+            if (c->tally[t].filter == ORC_FILTER_CELL) {
+                for (int g = 0; g < G; g++) tally[g] = c->t_mean[t][(size_t)cell * G + g];
+                break;
+            }
+    }
+    free(gr.param); free(gr.val); free(gr.ownb); free(gr.nfb); free(gr.pid); free(gr.own);
+    return r;
+}
+
+/* ------------------------------------------------------------------------- */
+int orc_get_k(const orc_ctx *c, double out[6])
+{
+    memcpy(out, c->k, sizeof c->k);
+    return 0;
+}
+
+int orc_get_cycle_k(const orc_ctx *c, int n_cycles, double *k_tl, double *k_c, int64_t *bank_size)
+{
+    for (int i = 0; i < n_cycles && i < c->ncyc; i++) {
+        k_tl[i] = c->cyc_ktl[i]; k_c[i] = c->cyc_kc[i]; bank_size[i] = c->cyc_m[i];
+    }
+    return 0;
+}
+
+int orc_tally_size(const orc_ctx *c, int tally, int *n_bins, int *n_ebins)
+{
+    if (tally < 0 || tally >= c->nt) return ORC_EINVAL;
+    *n_bins = c->tally[tally].nbins;
+    *n_ebins = c->tally[tally].ne;
+    return 0;
+}
+
+int orc_get_tally(const orc_ctx *c, int tally, double *mean, double *sd)
+{
+    if (tally < 0 || tally >= c->nt || !c->t_mean) return ORC_EINVAL;
+    size_t nb = (size_t)c->tally[tally].nbins * c->tally[tally].ne;
+    memcpy(mean, c->t_mean[tally], sizeof(double) * nb);
+    memcpy(sd, c->t_sd[tally], sizeof(double) * nb);
+    return 0;
+}
+
+int orc_get_counters(const orc_ctx *c, int64_t out[7])
+{
+    memcpy(out, c->counters, sizeof c->counters);
+    return 0;
+}
+
+int64_t orc_history_count(const orc_ctx *c) { return c->nhist; }
+
+int orc_get_histories(const orc_ctx *c, int32_t *n_coll, int32_t *n_cross, uint64_t *rng_end,
+                      int32_t *n_fis, int32_t *fate, int32_t *g_end)
+{
+    for (int64_t j = 0; j < c->nhist; j++) {
+        n_coll[j] = c->h_coll[j]; n_cross[j] = c->h_cross[j];
+        rng_end[j] = c->h_rng[j]; n_fis[j] = c->h_fis[j];
+        fate[j] = c->h_fate[j]; g_end[j] = c->h_g[j];
+    }
+    return 0;
+}
+
+int64_t orc_bank_count(const orc_ctx *c) { return c->nbank; }
+
+int orc_get_bank(const orc_ctx *c, double *xyz, int64_t *parent, int32_t *child, int32_t *mat)
+{
+    for (int64_t k = 0; k < c->nbank; k++) {
+        xyz[3 * k] = c->bank[k].x; xyz[3 * k + 1] = c->bank[k].y; xyz[3 * k + 2] = c->bank[k].z;
+        parent[k] = c->bank[k].parent; child[k] = c->bank[k].child; mat[k] = c->bank[k].mat;
+    }
+    return 0;
+}

@@ -1,0 +1,51 @@
+"""Stored fixtures: the paper's Table 1 (a worked example of Eq. 1) and the
+oracle's own regression record (written by tests/golden/make_golden.py)."""
+import json
+import os
+
+import numpy as np
+
+import workloads as W
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _load(name):
+    with open(os.path.join(HERE, name)) as f:
+        return json.load(f)
+
+
+def test_table1_core_equivalency():
+    from paper_2501_05440_gb300.report import core_equivalency
+    t = _load("table1_core_equivalency.json")
+    for row in t["rows"]:
+        for key, cpu in (("c5g7", t["cpu_runtime_s"]["c5g7"]), ("pin", t["cpu_runtime_s"]["pin_cell"])):
+            eq = core_equivalency(t["cpu_cores"], cpu, t["gpus_per_node"], row[f"{key}_runtime_s"])
+            assert abs(eq - row[f"{key}_equivalency"]) <= 0.5 + 1e-9, (row, key, eq)
+    # the text's 362 for the MI300A is not what Eq. 1 gives
+    mi300 = t["rows"][2]
+    assert abs(core_equivalency(112, 5080.0, 4, mi300["c5g7_runtime_s"]) - 362) > 30
+
+
+def test_oracle_regression_record(orc):
+    ref = _load("oracle_pin_cell_small.json")
+    o = orc.Oracle(W.pin_cell_mg(n=1000, inactive=2, active=3)).run(threads=1)
+    ktl, kc, m = o.cycle_k(5)
+    assert m.tolist() == ref["bank_size"]
+    assert ktl.tolist() == ref["k_tl"] and kc.tolist() == ref["k_col"]
+    h = o.histories()
+    assert [int(v) for v in h["rng_end"][:16]] == ref["rng_end_first16"]
+    assert h["n_coll"][:16].tolist() == ref["n_coll_first16"]
+    assert np.array_equal(o.bank()["xyz"][:4], np.array(ref["bank_xyz_first4"]))
+    # thread count changes only summation order, never histories or banks
+    o4 = orc.Oracle(W.pin_cell_mg(n=1000, inactive=2, active=3)).run(threads=4)
+    assert o4.cycle_k(5)[2].tolist() == ref["bank_size"]
+
+
+def test_oracle_rng_words(orc):
+    ref = _load("oracle_rng_words.json")
+    for st in ref["streams"]:
+        s = orc.rng_stream(1, st["stream"])
+        for w in st["words"]:
+            s = orc.rng_next(s)
+            assert s == w
