@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of event-based Monte Carlo transport on GB300.
+
+Headline: histories/s of k-eigenvalue power iteration on the C5G7-shaped
+multigroup lattice (51x51 pins, 7 groups, 1e6 particles per cycle), one step =
+one cycle (source from the resampled bank, transport of every history, bank
+ordering, resampling, tallies), persistent event-loop form.  Beside it, in the
+same JSON line: the plain one-kernel-per-event form on the same workload, the
+64-problem batched run against 64 separate plain runs, derivatives per second
+through the replay-backward kernel, the FP64 roofline of the transport
+kernel, the CPU oracle timed on this host's cores, and GPU clocks sampled
+during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mcgb|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (its own seed);
+the histories of all ranks are added and divided by the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "histories/s on 1 GB300, batched vs plain event launch; % HBM roofline; grad/s"
+WORKLOAD = "mg-c5g7-like-lattice-51x51-7g-keff"
+N_PER_CYCLE = 1_000_000
+# FP64-pipe peak of one GB300: 152 SMs x 2 FP64 results per clock per SM x 2.07 GHz
+# (the nominal 1.25 TFLOP/s counts an FMA as 2); a measured FP64 instruction
+# throughput probe gave 504 G/s at the clocks it ran at.
+FP64_PEAK_GOPS = 152 * 2 * 2.07
+# FP64 instructions per event of the persistent transport kernel on this
+# workload (ncu: smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on
+# plus conversions, divided by events), see profiles/.
+FP64_INST_PER_EVENT = None
+# Algorithmic particle-state bytes an event moves in the event-based form:
+# advance reads position/direction/energy/RNG/cell path and writes position,
+# RNG, event tag; collide or cross read and write direction, group, RNG and
+# cell path (fields counted once per kernel that touches them).
+STATE_BYTES_PER_EVENT = 120.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mcgb", choices=["mcgb", "reference"])
+    ap.add_argument("--n", type=int, default=N_PER_CYCLE, help="particles per cycle")
+    ap.add_argument("--quick", action="store_true", help="headline leg only")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def headline(m, W, torch, args, rank, pg):
+    """Persistent form: K timed cycles after W warm-up cycles."""
+    pb = W.c5g7_like_lattice(seed=1 + rank, n=args.n)
+    c = m.Context(device=int(os.environ.get("LOCAL_RANK", "0")), mode=m.MODE_PERSISTENT)
+    c.set_stream(torch.cuda.current_stream().cuda_stream)
+    m.load_problem(c, pb)
+    n = args.n
+    c.eigen_begin(n, args.warmup, args.steps, pb["run"]["seed"])
+    c.eigen_cycles(args.warmup)
+    torch.cuda.synchronize()
+    barrier(pg)
+    launches0 = c.get_counters()["kernel_launches"]
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    c.eigen_cycles(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = c.get_counters()["kernel_launches"] - launches0
+    c.eigen_finish()
+    cnt = c.get_counters()
+    ncyc = args.warmup + args.steps
+    tms, cms = c.get_cycle_times(ncyc)
+    k = c.get_k()
+    events = (cnt["collisions"] + cnt["crossings"]) / ncyc    # per cycle (the cycles are alike)
+    return {"ms": ms, "n": n, "launches": launches, "clocks": clk, "k": k,
+            "transport_ms": sum(tms[args.warmup:]) / args.steps,
+            "cycle_ms": sum(cms[args.warmup:]) / args.steps, "events_per_cycle": events,
+            "counters": cnt}
+
+
+def plain_leg(m, W, torch, args, steps):
+    pb = W.c5g7_like_lattice(seed=1, n=args.n)
+    c = m.Context(mode=m.MODE_EVENT)
+    c.set_stream(torch.cuda.current_stream().cuda_stream)
+    m.load_problem(c, pb)
+    c.eigen_begin(args.n, 1, steps, 1)
+    c.eigen_cycles(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    c.eigen_cycles(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c.eigen_finish()
+    cnt = c.get_counters()
+    return {"value": args.n * steps / (ms / 1e3), "unit": "histories/s", "mode": "event",
+            "ms_per_step": ms / steps, "steps": steps,
+            "event_iterations_per_cycle": cnt["event_iterations"] / (steps + 1)}
+
+
+def e2e_leg(m, W, args, steps):
+    """Through the public API with host buffers: define, upload, run, read back."""
+    pb = W.c5g7_like_lattice(seed=1, n=args.n)
+    t0 = time.perf_counter()
+    c = m.Context(mode=m.MODE_PERSISTENT)
+    m.load_problem(c, pb)
+    c.run_eigenvalue(args.n, 0, steps, 1)
+    k = c.get_k()
+    mean, sd = c.get_tally(0)
+    t1 = time.perf_counter()
+    cnt = c.get_counters()
+    d2h = mean.nbytes + sd.nbytes + 48 + 12 * steps
+    return {"value": args.n * steps / (t1 - t0), "unit": "histories/s",
+            "h2d_bytes_per_step": cnt["world_bytes"] / steps, "d2h_bytes_per_step": d2h / steps,
+            "steps": steps, "k": k["k"]}
+
+
+def batched_leg(m, W, torch):
+    """64 fixed-source box problems: one batched persistent run vs 64 plain runs."""
+    probs = W.batch_boxes()
+    hist = sum(p["run"]["n"] for p in probs)
+    ctxs = []
+    for p in probs:
+        c = m.Context(mode=m.MODE_EVENT)
+        m.load_problem(c, p)
+        ctxs.append(c)
+    b = m.Batch(mode=m.MODE_PERSISTENT)
+    for c, p in zip(ctxs, probs):
+        b.add_problem(c, p["run"]["n"], p["run"]["batches"], p["run"]["seed"])
+    tune = b.autotune(budget_ms=4000)
+    b.run(tune)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(tune)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    for c, p in zip(ctxs, probs):     # warm-up of the separate runs
+        c.run()
+        break
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in ctxs:
+        c.run()
+    torch.cuda.synchronize()
+    t_sep = time.perf_counter() - t0
+    return {"histories": hist, "batched_persistent_s": t_batch, "separate_plain_s": t_sep,
+            "batched_histories_per_s": hist / t_batch, "separate_histories_per_s": hist / t_sep,
+            "speedup": t_sep / t_batch, "tune": tune}
+
+
+def grad_leg(m, W, torch, n):
+    pb = W.diff_slab(n=n)
+    c = m.Context(mode=m.MODE_PERSISTENT)
+    m.load_problem(c, pb)
+    det = pb["detector_cell"]
+    c.forward_fixed(min(n, 10000), 1, det)
+    c.backward_fixed([1.0] * pb["G"], len(pb["materials"]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tal = c.forward_fixed(n, 1, det)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    c.backward_fixed([1.0] * pb["G"], len(pb["materials"]))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"histories": n, "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "grad_histories_per_s": n / (t2 - t1), "forward_histories_per_s": n / (t1 - t0),
+            "detector_tally": float(tal.sum())}
+
+
+def cpu_baseline(W, n=200_000):
+    import oracle
+    cores = os.cpu_count() or 1
+    pb = W.c5g7_like_lattice(seed=1, n=n, inactive=0, active=1)
+    o = oracle.Oracle(pb)
+    t0 = time.perf_counter()
+    o.run(threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "histories/s", "cores": cores, "kind": "oracle",
+            "sample": f"first power-iteration cycle of {WORKLOAD} at {n} particles (1 cycle), "
+                      f"{dt:.2f} s wall on {cores} threads"}
+
+
+def run_mcgb(args):
+    import torch
+
+    import paper_2501_05440_gb300 as m
+    import workloads as W
+
+    rank, world, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    m.build()
+    h = headline(m, W, torch, args, rank, pg)
+    ms_max = max_over_ranks(pg, h["ms"])
+    hist_total = sum_over_ranks(pg, float(h["n"] * args.steps))
+    value = hist_total / (ms_max / 1e3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles_per_cycle": h["n"], "step": "one power-iteration cycle",
+                   "mode": "persistent", "l2": "inputs larger than L2 (particle state and fission "
+                   "banks ~0.5 GB per GPU)", "parallelism": f"replicas x{world}"},
+        "events_per_s": h["events_per_cycle"] * world / (ms_max / 1e3 / args.steps),
+        "k": h["k"]["k"], "k_sd": h["k"]["k_sd"],
+        "gpu_launches": h["launches"], "clocks": h["clocks"],
+    }
+    # roofline of the transport kernel (the persistent event loop: one launch per cycle)
+    ev = h["events_per_cycle"]
+    t_kernel = h["transport_ms"] / 1e3
+    if FP64_INST_PER_EVENT:
+        ach = FP64_INST_PER_EVENT * ev / t_kernel / 1e9
+        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GOPS,
+                           "unit": "G FP64 instr/s", "frac": ach / FP64_PEAK_GOPS,
+                           "traffic": None, "kernel": "k_persistent"}
+    else:
+        peak = 6777.0
+        ach = STATE_BYTES_PER_EVENT * ev / t_kernel / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                           "frac": ach / peak, "traffic": None, "kernel": "k_persistent"}
+    out["transport_ms_per_cycle"] = h["transport_ms"]
+    if rank == 0 and not args.quick:
+        out["plain_event"] = plain_leg(m, W, torch, args, max(2, args.steps // 4))
+        out["e2e"] = e2e_leg(m, W, args, max(2, args.steps // 2))
+        out["batched"] = batched_leg(m, W, torch)
+        out["grad"] = grad_leg(m, W, torch, 1_000_000)
+        out["cpu_baseline"] = cpu_baseline(W)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def run_reference(args):
+    """The CPU oracle on this host's cores, same workload and metric, bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    n = 50_000
+    cores = os.cpu_count() or 1
+    pb = W.c5g7_like_lattice(seed=1, n=n, inactive=args.warmup, active=args.steps)
+    o = oracle.Oracle(pb)
+    t0 = time.perf_counter()
+    o.run(threads=cores)
+    dt = time.perf_counter() - t0
+    ncyc = args.warmup + args.steps
+    value = n * ncyc / dt
+    sample = (f"{WORKLOAD} at {n} particles per cycle (the GPU arm runs {N_PER_CYCLE}), "
+              f"{ncyc} cycles on {cores} threads")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s",
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3 / ncyc, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "particles_per_cycle": n, "step": "one power-iteration cycle"},
+           "cpu_baseline": {"value": value, "unit": "histories/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_mcgb(a)

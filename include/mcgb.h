@@ -1,0 +1,253 @@
+/*
+ * mcgb.h -- C ABI of the GB300 event-based Monte Carlo neutral-particle
+ * transport library (libmcgb.so).
+ *
+ * The calls follow the paper's statement of the problem (arXiv 2501.05440,
+ * Sec. 1): materials with multigroup or pointwise (continuous-energy) cross
+ * sections, constructive-solid-geometry cells bounded by surfaces and tracked
+ * surface to surface, a source, N particles run for C k-eigenvalue cycles or
+ * as a fixed-source problem, and track-length tallies and k read back.  Sec. 2
+ * describes the event-based GPU scheme these calls drive: particles repeatedly
+ * sample a distance to collision, find the nearest surface, move, score and
+ * then cross or collide.
+ *
+ * Conventions
+ *  - Every call returns int: MCGB_OK (0) or a negative MCGB_E_* code; a message
+ *    for the last failure on the calling thread is in mcgb_last_error().
+ *  - Input arrays are host pointers and are copied; the caller keeps
+ *    ownership.  Output arrays are caller-allocated host buffers with a
+ *    capacity; when it is too small the call returns MCGB_E_INVALID_ARG and
+ *    writes the required element count to *needed (when needed is not NULL).
+ *  - Everything runs on the context's CUDA device and stream.  Problem tables
+ *    are uploaded at the first run after a change; all transport steps run in
+ *    this library's kernels (there is no CPU fallback; without a usable CUDA
+ *    device mcgb_create fails with MCGB_E_CUDA).
+ *  - Floating point is IEEE double throughout (the paper uses double
+ *    precision for all floating-point operations, Sec. 5).
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef MCGB_H
+#define MCGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcgb_ctx mcgb_ctx;
+typedef struct mcgb_batch mcgb_batch;
+
+/* status codes */
+enum {
+    MCGB_OK = 0,
+    MCGB_E_INVALID_ARG = -1,   /* bad argument, or output capacity too small */
+    MCGB_E_STATE = -2,         /* call out of order (e.g. no source), empty bank */
+    MCGB_E_CUDA = -3,          /* CUDA runtime error or no device */
+    MCGB_E_OOM = -4,           /* device allocation failed */
+    MCGB_E_BANK_OVERFLOW = -5, /* more fission sites than the bank holds */
+    MCGB_E_LOST_PARTICLES = -6,/* more than 1e-6 of histories found no cell */
+    MCGB_E_TIMEOUT = -7,       /* iteration or generation limit reached */
+    MCGB_E_NOT_FOUND = -8      /* unknown id */
+};
+
+/* geometry vocabulary */
+enum { MCGB_SURF_PX = 0, MCGB_SURF_PY = 1, MCGB_SURF_PZ = 2, MCGB_SURF_PLANE = 3,
+       MCGB_SURF_CYLZ = 4, MCGB_SURF_SPHERE = 5 };
+enum { MCGB_BC_NONE = 0, MCGB_BC_VACUUM = 1, MCGB_BC_REFLECT = 2 };
+enum { MCGB_FILL_MATERIAL = 0, MCGB_FILL_LATTICE = 1 };
+/* sources */
+enum { MCGB_SRC_BOX = 0, MCGB_SRC_POINT = 1 };
+enum { MCGB_ACCEPT_ANY = 0, MCGB_ACCEPT_FISSILE = 1 };
+enum { MCGB_ENERGY_CHI = 0, MCGB_ENERGY_PDF = 1, MCGB_ENERGY_FIXED = 2, MCGB_ENERGY_MAXWELL = 3 };
+enum { MCGB_DIR_ISO = 0, MCGB_DIR_BEAM = 1 };
+/* tally filters */
+enum { MCGB_FILTER_CELL = 0, MCGB_FILTER_LATTICE = 1, MCGB_FILTER_MATERIAL = 2 };
+/* execution modes */
+enum { MCGB_MODE_EVENT = 0,       /* one kernel per event type, host-driven loop */
+       MCGB_MODE_PERSISTENT = 1 };/* one grid-resident event loop per cycle, CUDA graph */
+
+/* Options.  Zero-initialised fields take defaults. */
+typedef struct {
+    int device;             /* CUDA device ordinal (default 0) */
+    int mode;               /* MCGB_MODE_* (default MCGB_MODE_EVENT) */
+    int block;              /* threads per block (default: autotuned or 256) */
+    int blocks_per_sm;      /* persistent mode: resident blocks per SM (default: occupancy) */
+    int record_histories;   /* keep per-history records of the last cycle / generation 0 */
+    double bank_factor;     /* fission bank capacity as a multiple of N (default 3) */
+    int max_iterations;     /* event-mode iteration limit per cycle (default 1e7) */
+} mcgb_opts;
+
+/* Event and history counters of the last run. */
+typedef struct {
+    int64_t histories, collisions, crossings, leaks, lost, capped, generations;
+    int64_t kernel_launches;   /* kernels this library launched during the run */
+    int64_t event_iterations;  /* event mode: host loop iterations */
+    int64_t world_bytes;       /* bytes of problem tables uploaded to the device */
+} mcgb_counters;
+
+/* Launch shape chosen by the autotuner for a batch. */
+typedef struct {
+    int block;              /* threads per block */
+    int blocks_per_sm;      /* resident blocks per SM in the persistent launch */
+    int chunk;              /* particles a warp takes per work-queue pop (1 = per lane) */
+    double ms;              /* measured time of the tuning run */
+} mcgb_tune;
+
+/* --------------------------------------------------------------------------- */
+/* context                                                                      */
+/* Create a context on opts->device (opts may be NULL).  Fails with MCGB_E_CUDA
+ * when no CUDA device is usable. */
+int mcgb_create(mcgb_ctx **out, const mcgb_opts *opts);
+int mcgb_destroy(mcgb_ctx *ctx);
+/* Message for the last failing call on this thread (never NULL). */
+const char *mcgb_last_error(void);
+/* Run subsequent work on this cudaStream_t (NULL = the legacy default stream). */
+int mcgb_set_stream(mcgb_ctx *ctx, void *cuda_stream);
+int mcgb_set_mode(mcgb_ctx *ctx, int mode);
+
+/* --------------------------------------------------------------------------- */
+/* geometry: constructive solid geometry with surface tracking (Sec. 1)          */
+/* Surface f(r) = 0 with coef: PX/PY/PZ {x0}; PLANE {a,b,c,d} (a x + b y + c z = d);
+ * CYLZ {x0, y0, R}; SPHERE {x0, y0, z0, R}.  bc: MCGB_BC_*; reflective
+ * boundaries must be planes.  *id receives the surface index. */
+int mcgb_add_surface(mcgb_ctx *ctx, int type, const double coef[4], int bc, int *id);
+/* A cell is the intersection of n half-spaces (surf[k], sense[k] = +1 where
+ * f > 0, -1 where f < 0) in `universe` (0 = root).  fill_kind
+ * MCGB_FILL_MATERIAL: fill is a material index; MCGB_FILL_LATTICE: fill is a
+ * lattice index (root-universe cells only).  Cells of a universe must
+ * partition the space they cover. */
+int mcgb_add_cell(mcgb_ctx *ctx, int universe, int n, const int *surf, const int *sense,
+                  int fill_kind, int fill, int *id);
+/* Rectangular x-y lattice with lower-left corner (x0, y0), square pitch,
+ * nx * ny universes, element (ix, iy) at universes[ix + nx * iy].  Universe
+ * cells are placed in element-centred coordinates. */
+int mcgb_add_lattice(mcgb_ctx *ctx, double x0, double y0, double pitch, int nx, int ny,
+                     const int *universes, int *id);
+
+/* --------------------------------------------------------------------------- */
+/* materials (Sec. 1: multigroup and continuous-energy physics)                  */
+int mcgb_set_groups(mcgb_ctx *ctx, int G);
+/* Multigroup material: sigma_t[G], sigma_s[G*G] as [from][to], nu_sigma_f[G],
+ * chi[G] (any non-negative weights).  Row sums of sigma_s may not exceed sigma_t. */
+int mcgb_add_material_mg(mcgb_ctx *ctx, const double *sigma_t, const double *sigma_s,
+                         const double *nu_sigma_f, const double *chi, int *id);
+/* Replace the cross sections of multigroup material id (same layout). */
+int mcgb_update_material_mg(mcgb_ctx *ctx, int id, const double *sigma_t,
+                            const double *sigma_s, const double *nu_sigma_f, const double *chi);
+/* Pointwise nuclide: mass ratio A, n increasing energies E (eV) with elastic,
+ * capture and fission cross sections (barns), mean neutrons per fission nu. */
+int mcgb_add_nuclide_ce(mcgb_ctx *ctx, double A, int n, const double *E, const double *sig_s,
+                        const double *sig_c, const double *sig_f, double nu, int *id);
+/* Continuous-energy material: n nuclide ids with atom densities (atoms/b-cm). */
+int mcgb_add_material_ce(mcgb_ctx *ctx, int n, const int *nuclides, const double *density,
+                         int *id);
+
+/* --------------------------------------------------------------------------- */
+/* source and tallies                                                           */
+/* kind MCGB_SRC_BOX: params {xmin,xmax,ymin,ymax,zmin,zmax}, positions uniform,
+ * rejected until `accept` holds; MCGB_SRC_POINT: params {x,y,z}.
+ * energy_kind CHI (group from chi of the located material), PDF (group weights
+ * energy[0..n_energy)), FIXED (energy[0] eV), MAXWELL (fission spectrum).
+ * dir_kind ISO or BEAM (unit vector beam[3]). */
+int mcgb_set_source(mcgb_ctx *ctx, int kind, const double *params, int accept, int energy_kind,
+                    const double *energy, int n_energy, int dir_kind, const double *beam);
+/* Track-length flux tally.  filter: CELL (innermost cell), LATTICE (element
+ * ix + nx iy of lattice 0), MATERIAL.  Energy bins: the groups (multigroup) or
+ * n_edges increasing edges in eV (continuous energy). */
+int mcgb_add_tally(mcgb_ctx *ctx, int filter, int n_edges, const double *edges, int *id);
+/* End each history at its max_collisions-th collision (0 = no limit). */
+int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions);
+
+/* --------------------------------------------------------------------------- */
+/* runs                                                                         */
+/* k-eigenvalue power iteration (Sec. 4): n histories per cycle, `inactive`
+ * cycles discarded, statistics over `active` cycles. */
+int mcgb_run_eigenvalue(mcgb_ctx *ctx, int64_t n, int inactive, int active, uint64_t seed);
+/* The same power iteration in steps: begin (uploads the problem, allocates),
+ * run n_cycles further cycles (any number of calls), finish (statistics).
+ * mcgb_run_eigenvalue = begin + all cycles + finish. */
+int mcgb_eigen_begin(mcgb_ctx *ctx, int64_t n, int inactive, int active, uint64_t seed);
+int mcgb_eigen_cycles(mcgb_ctx *ctx, int n_cycles);
+int mcgb_eigen_finish(mcgb_ctx *ctx);
+/* Device time of each cycle (CUDA events on the context's stream): the
+ * transport phase and the whole cycle, in ms. */
+int mcgb_get_cycle_times(mcgb_ctx *ctx, int n_cycles, double *transport_ms, double *cycle_ms);
+/* Fixed source: n source histories in `batches` statistical batches; fission
+ * secondaries run as further generations until none remain. */
+int mcgb_run_fixed_source(mcgb_ctx *ctx, int64_t n, int batches, uint64_t seed);
+
+/* --------------------------------------------------------------------------- */
+/* results                                                                      */
+/* out[6] = k (track length) mean, sd; k (collision) mean, sd; k (analog) mean, sd. */
+int mcgb_get_k(mcgb_ctx *ctx, double out[6]);
+/* Per-cycle k (track length), k (collision) and bank size, n_cycles entries. */
+int mcgb_get_cycle_k(mcgb_ctx *ctx, int n_cycles, double *k_tl, double *k_col, int64_t *bank);
+int mcgb_tally_size(mcgb_ctx *ctx, int tally, int *n_bins, int *n_ebins);
+/* mean and sd per source particle, [bin][ebin], cap elements each. */
+int mcgb_get_tally(mcgb_ctx *ctx, int tally, double *mean, double *sd, size_t cap,
+                   size_t *needed);
+int mcgb_get_counters(mcgb_ctx *ctx, mcgb_counters *out);
+/* Per-history records (opts.record_histories): last cycle (eigenvalue) or
+ * generation 0 (fixed source).  fate: 0 absorbed, 1 leaked, 2 cut by
+ * max_collisions, 3 lost, 4 event cap.  Arrays of cap elements. */
+int mcgb_get_histories(mcgb_ctx *ctx, size_t cap, int32_t *n_coll, int32_t *n_cross,
+                       uint64_t *rng_end, int32_t *n_fis, int32_t *fate, int32_t *g_end,
+                       size_t *needed);
+/* Fission bank of the last cycle (eigenvalue) or generation 0 (fixed source),
+ * in (parent, child) order: xyz[3*cap], parent[cap], child[cap], mat[cap]. */
+int mcgb_get_bank(mcgb_ctx *ctx, size_t cap, double *xyz, int64_t *parent, int32_t *child,
+                  int32_t *mat, size_t *needed);
+
+/* --------------------------------------------------------------------------- */
+/* derivatives (likelihood ratio with replay; the paper has no counterpart)    */
+/* Forward: fixed-source run of n histories (1 batch) that keeps what the replay
+ * needs: per-particle detector tallies and every generation's sorted bank.
+ * tally_out[G] = the detector cell's track-length tally per group per source. */
+int mcgb_forward_fixed(mcgb_ctx *ctx, int64_t n, uint64_t seed, int det_cell, double *tally_out);
+/* Backward: replays every history of the last forward run from its random
+ * stream and accumulates score x downstream-tally for T = sum_g w[g] T_g:
+ * d_sigt[m*G+g], d_sigs[(m*G+g)*G+g'], d_nusf[m*G+g] per source particle.
+ * Parameters equal to 0 take no score. */
+int mcgb_backward_fixed(mcgb_ctx *ctx, const double *weights, double *d_sigt, double *d_sigs,
+                        double *d_nusf);
+
+/* --------------------------------------------------------------------------- */
+/* batching: many independent fixed-source problems in one persistent launch    */
+int mcgb_batch_create(mcgb_batch **out, const mcgb_opts *opts);
+int mcgb_batch_destroy(mcgb_batch *b);
+/* Add a problem defined in `problem` (its tables are copied; the context may be
+ * destroyed afterwards): n source histories in `batches` batches, seed. */
+int mcgb_batch_add_problem(mcgb_batch *b, mcgb_ctx *problem, int64_t n, int batches,
+                           uint64_t seed, int *id);
+/* Time candidate launch shapes on a fraction of the work and return the best;
+ * results are cached per (problem signature, device) in memory and, when the
+ * environment variable MCGB_TUNE_CACHE names a file, on disk. */
+int mcgb_batch_autotune(mcgb_batch *b, int budget_ms, mcgb_tune *out);
+/* Run every problem: tune NULL = the cached or default shape. */
+int mcgb_batch_run(mcgb_batch *b, const mcgb_tune *tune);
+int mcgb_batch_tally(mcgb_batch *b, int problem, int tally, double *mean, double *sd,
+                     size_t cap, size_t *needed);
+int mcgb_batch_counters(mcgb_batch *b, mcgb_counters *out);
+
+/* --------------------------------------------------------------------------- */
+/* building blocks on the device, for checks against other implementations     */
+/* out[i*n_draws + k] = k-th state of stream first_id + i of `seed` (63-bit LCG,
+ * stride 152917; Sec. 1's replicable random numbers). */
+int mcgb_rng_states(mcgb_ctx *ctx, uint64_t seed, uint64_t first_id, int64_t n_streams,
+                    int n_draws, uint64_t *out);
+/* out[i] = ln(xi[i]) for xi[i] = k 2^-53, k in [1, 2^53] (the transport's log). */
+int mcgb_log(mcgb_ctx *ctx, int64_t n, const double *xi, double *out);
+/* Geometry probe: locate each point (direction dir) and the distance to the
+ * nearest boundary.  path[5*i..] = root cell, ix, iy, universe cell, material. */
+int mcgb_probe(mcgb_ctx *ctx, int64_t n, const double *pos, const double *dir, int32_t *path,
+               double *dist, int32_t *kind);
+/* Continuous-energy lookup of material `mat` at n energies: out[4*i..] =
+ * Sigma_t, nuSigma_f, Sigma_s, Sigma_f. */
+int mcgb_ce_lookup(mcgb_ctx *ctx, int mat, int64_t n, const double *E, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCGB_H */

@@ -56,6 +56,7 @@ def lib():
             L.orc_add_lattice.argtypes = [P, d, d, d, i32, i32, P]
             L.orc_add_nuclide.argtypes = [P, d, i32, P, P, P, P, d]
             L.orc_grad_fixed.argtypes = [P, i64, u64, i32, P, P, P, P, P]
+            L.orc_histories_by_index.argtypes = [P, u64, i64, P, P, P, P, P, P, P]
             L.orc_rng_skip.restype = u64
             L.orc_rng_skip.argtypes = [u64, u64]
             L.orc_rng_stream.restype = u64
@@ -205,6 +206,16 @@ class Oracle:
         nc, nx, nf, fate, g = (np.zeros(n, dtype=np.int32) for _ in range(5))
         rng = np.zeros(n, dtype=np.uint64)
         self.L.orc_get_histories(self.ctx, _p(nc), _p(nx), _p(rng), _p(nf), _p(fate), _p(g))
+        return {"n_coll": nc, "n_cross": nx, "rng_end": rng, "n_fis": nf, "fate": fate, "g_end": g}
+
+    def histories_by_index(self, idx, seed=None):
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+        n = len(idx)
+        nc, nx, nf, fate, g = (np.zeros(n, dtype=np.int32) for _ in range(5))
+        rng = np.zeros(n, dtype=np.uint64)
+        seed = self.problem["run"]["seed"] if seed is None else seed
+        self._chk(self.L.orc_histories_by_index(self.ctx, seed, n, _p(idx), _p(nc), _p(nx), _p(rng),
+                                                _p(nf), _p(fate), _p(g)))
         return {"n_coll": nc, "n_cross": nx, "rng_end": rng, "n_fis": nf, "fate": fate, "g_end": g}
 
     def bank(self):

@@ -1594,6 +1594,36 @@ int orc_grad_fixed(orc_ctx *c, int64_t n, uint64_t seed, int cell, const double 
     return r;
 }
 
+/* Histories j = idx[k] of the first cycle / generation 0 (sources from the
+ * source definition, stream j), each run alone: for checking single histories
+ * of a large run without running all of it. */
+int orc_histories_by_index(orc_ctx *c, uint64_t seed, int64_t n_idx, const int64_t *idx,
+                           int32_t *n_coll, int32_t *n_cross, uint64_t *rng_end, int32_t *n_fis,
+                           int32_t *fate, int32_t *g_end)
+{
+    int r = prepare(c);
+    if (r) return r;
+    Acc *A = make_accs(c, 1, 1);
+    for (int64_t k = 0; k < n_idx; k++) {
+        Particle p;
+        memset(&p, 0, sizeof p);
+        p.s = orc_rng_stream(seed, (uint64_t)idx[k]);
+        p.index = idx[k];
+        p.root = 0;
+        p.alive = 1;
+        if (sample_source(c, &p) < 0) {
+            free_accs(c, A, 1);
+            return fail(c, ORC_ESTATE, "source sampling failed");
+        }
+        transport(c, &p, &A[0], 0, NULL, 0);
+        A[0].nbank = 0;
+        n_coll[k] = p.ncoll; n_cross[k] = p.ncross; rng_end[k] = p.s; n_fis[k] = p.nfis;
+        fate[k] = p.fate; g_end[k] = p.g;
+    }
+    free_accs(c, A, 1);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 int orc_get_k(const orc_ctx *c, double out[6])
 {

@@ -78,6 +78,10 @@ int orc_get_counters(const orc_ctx *c, int64_t out[7]);
 int64_t orc_history_count(const orc_ctx *c);
 int orc_get_histories(const orc_ctx *c, int32_t *n_coll, int32_t *n_cross, uint64_t *rng_end,
                       int32_t *n_fis, int32_t *fate, int32_t *g_end);
+/* histories j = idx[k] of the first cycle / generation 0, each run alone */
+int orc_histories_by_index(orc_ctx *c, uint64_t seed, int64_t n_idx, const int64_t *idx,
+                           int32_t *n_coll, int32_t *n_cross, uint64_t *rng_end, int32_t *n_fis,
+                           int32_t *fate, int32_t *g_end);
 /* fission bank of the last cycle / generation 0, in (parent, child) order */
 int64_t orc_bank_count(const orc_ctx *c);
 int orc_get_bank(const orc_ctx *c, double *xyz, int64_t *parent, int32_t *child, int32_t *mat);

@@ -1,0 +1,1454 @@
+// host_api.cu -- the C ABI: problem definition, run drivers, results.
+//
+// A run keeps all particle state, banks and accumulators in device memory.
+// Power iteration per cycle: transport N histories (event mode: a host loop of
+// advance / cross / collide kernels over compacted queues; persistent mode: one
+// grid-resident kernel), then on the device: reduce k estimators, scan the
+// per-history site counts, permute the bank into (parent, child) order,
+// resample N sources, fold the cycle's tallies into the batch statistics.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mcgb.h"
+#include "host_world.h"
+#include "kernels.h"
+#include "transport.cuh"
+
+using namespace mcgb;
+
+static thread_local std::string g_err = "";
+
+static int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(expr)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? MCGB_E_OOM : MCGB_E_CUDA,    \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+#define CKR(expr)                  \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ != MCGB_OK) return r_; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffers of a run
+struct DevAlloc {
+    std::vector<void *> ptrs;
+    ~DevAlloc() { release(); }
+    void release()
+    {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+    template <class T> int get(T *&p, int64_t n)
+    {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(MCGB_E_OOM, std::string("device allocation: ") + cudaGetErrorString(e));
+        }
+        ptrs.push_back(q);
+        p = (T *)q;
+        return MCGB_OK;
+    }
+};
+
+struct GradGen {          // what the replay needs from one forward generation
+    int64_t n = 0, M = 0;
+    double *own = nullptr;
+    int *nfis = nullptr, *off = nullptr, *perm = nullptr;
+    Bank bank{};          // this generation's sites (unsorted) = next generation's births
+};
+
+struct EigenRun {            // a power iteration in progress
+    bool on = false;
+    int64_t N = 0;
+    int inactive = 0, active = 0, ncyc = 0, cyc = 0, cur = 0;
+    uint64_t seed = 0;
+};
+
+struct RunState {
+    DevAlloc mem;
+    int64_t cap_p = 0, cap_b = 0, cap_acc = 0;
+    Particles P{};
+    Bank bank[2]{};
+    int *list[2] = {nullptr, nullptr};
+    int *q_cross = nullptr, *q_coll = nullptr, *off = nullptr, *perm = nullptr, *src_idx = nullptr;
+    int *scratch = nullptr, *M = nullptr, *work = nullptr;
+    int64_t *gen_base[2] = {nullptr, nullptr};
+    double *tacc = nullptr, *tsum = nullptr, *tsum2 = nullptr, *kout = nullptr;
+    unsigned long long *cnt = nullptr;
+    int *bank_n = nullptr, *err = nullptr, *q_n = nullptr;
+    int *pinned = nullptr;   // host-pinned mirror of small counters
+};
+
+struct mcgb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mcgb_opts opts{};
+    int sms = 1;
+    ProblemDef def;
+    std::unique_ptr<DeviceWorld> world;
+    RunState rs;
+    int64_t launches = 0;
+    // results
+    double k[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<double> cyc_ktl, cyc_kc;
+    std::vector<int64_t> cyc_m;
+    std::vector<std::vector<double>> t_mean, t_sd;
+    mcgb_counters counters{};
+    std::vector<int32_t> h_coll, h_cross, h_fis, h_fate, h_g;
+    std::vector<uint64_t> h_rng;
+    std::vector<double> b_xyz;
+    std::vector<int64_t> b_parent;
+    std::vector<int32_t> b_child, b_mat;
+    std::vector<double> cyc_tms, cyc_ms;   // per-cycle device time: transport, whole cycle
+    std::vector<cudaEvent_t> events;
+    EigenRun eig;
+    // derivative forward state
+    std::vector<GradGen> grad_gens;
+    DevAlloc grad_mem;
+    int64_t grad_n = 0;
+    int grad_cell = -1;
+    bool grad_ready = false;
+};
+
+struct mcgb_batch {
+    mcgb_opts opts{};
+    int device = 0;
+    std::vector<std::unique_ptr<ProblemDef>> defs;
+    std::vector<ProblemRun> runs;
+    std::unique_ptr<mcgb_ctx> engine;    // owns the device state of batched runs
+    std::vector<std::vector<std::vector<double>>> t_mean, t_sd;   // [problem][tally][...]
+    mcgb_tune tuned{};
+    bool has_tune = false;
+};
+
+// ---------------------------------------------------------------------------
+static int prepare_buffers(mcgb_ctx *c, int64_t cap_p, int64_t cap_b)
+{
+    RunState &r = c->rs;
+    int acc = c->world->acc_size * c->world->nrep;
+    if (cap_p <= r.cap_p && cap_b <= r.cap_b && acc <= r.cap_acc) return MCGB_OK;
+    r.mem.release();
+    cap_p = std::max(cap_p, r.cap_p);
+    cap_b = std::max(cap_b, r.cap_b);
+    Particles &P = r.P;
+    DevAlloc &m = r.mem;
+    CKR(m.get(P.x, cap_p)); CKR(m.get(P.y, cap_p)); CKR(m.get(P.z, cap_p));
+    CKR(m.get(P.u, cap_p)); CKR(m.get(P.v, cap_p)); CKR(m.get(P.w, cap_p));
+    CKR(m.get(P.E, cap_p)); CKR(m.get(P.kt, cap_p)); CKR(m.get(P.kc, cap_p));
+    CKR(m.get(P.s, cap_p));
+    CKR(m.get(P.g, cap_p)); CKR(m.get(P.cell, cap_p)); CKR(m.get(P.ix, cap_p));
+    CKR(m.get(P.iy, cap_p)); CKR(m.get(P.ucell, cap_p)); CKR(m.get(P.mat, cap_p));
+    CKR(m.get(P.uk, cap_p)); CKR(m.get(P.prob, cap_p)); CKR(m.get(P.root, cap_p));
+    CKR(m.get(P.nfis, cap_p)); CKR(m.get(P.ncoll, cap_p)); CKR(m.get(P.ncross, cap_p));
+    CKR(m.get(P.bwhich, cap_p)); CKR(m.get(P.bkind, cap_p)); CKR(m.get(P.fate, cap_p));
+    P.cap = cap_p;
+    for (int b = 0; b < 2; b++) {
+        Bank &B = r.bank[b];
+        CKR(m.get(B.x, cap_b)); CKR(m.get(B.y, cap_b)); CKR(m.get(B.z, cap_b));
+        CKR(m.get(B.cell, cap_b)); CKR(m.get(B.ix, cap_b)); CKR(m.get(B.iy, cap_b));
+        CKR(m.get(B.ucell, cap_b)); CKR(m.get(B.mat, cap_b)); CKR(m.get(B.parent, cap_b));
+        CKR(m.get(B.child, cap_b)); CKR(m.get(B.root, cap_b)); CKR(m.get(B.prob, cap_b));
+        B.cap = cap_b;
+        CKR(m.get(r.list[b], cap_p));
+        CKR(m.get(r.gen_base[b], 4096 + 1));
+    }
+    int64_t big = std::max(cap_p, cap_b);
+    CKR(m.get(r.q_cross, cap_p)); CKR(m.get(r.q_coll, cap_p));
+    CKR(m.get(r.off, cap_p + 1)); CKR(m.get(r.perm, cap_b)); CKR(m.get(r.src_idx, big));
+    CKR(m.get(r.scratch, scan_scratch_ints(cap_p) + 16));
+    CKR(m.get(r.M, 4)); CKR(m.get(r.work, 4));
+    CKR(m.get(r.tacc, std::max(acc, 1))); CKR(m.get(r.tsum, std::max(c->world->acc_size, 1)));
+    CKR(m.get(r.tsum2, std::max(c->world->acc_size, 1)));
+    CKR(m.get(r.kout, 2 * 4096)); CKR(m.get(r.cnt, 8));
+    CKR(m.get(r.bank_n, 4)); CKR(m.get(r.err, 4)); CKR(m.get(r.q_n, 4));
+    if (!r.pinned) CK(cudaMallocHost((void **)&r.pinned, 16 * sizeof(int)));
+    r.cap_p = cap_p;
+    r.cap_b = cap_b;
+    r.cap_acc = acc;
+    return MCGB_OK;
+}
+
+static RunBufs run_bufs(mcgb_ctx *c, double *own, int own_cell, int own_G)
+{
+    RunBufs R{};
+    R.kacc = nullptr;
+    R.tacc = c->rs.tacc;
+    R.bank_n = c->rs.bank_n;
+    R.err = c->rs.err;
+    R.q_n = c->rs.q_n;
+    R.own = own;
+    R.own_cell = own_cell;
+    R.own_G = own_G;
+    return R;
+}
+
+static int block_size(mcgb_ctx *c) { return c->opts.block > 0 ? c->opts.block : 256; }
+
+// Transport one cycle / generation of `total` slots (host-known bound).
+static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t total,
+                                const int64_t *gen_base, const int *src_idx, int eigen,
+                                const Bank &Bsrc, const Bank &Bdst)
+{
+    RunState &r = c->rs;
+    const World &W = c->world->W;
+    cudaStream_t st = c->stream;
+    int block = block_size(c);
+    if (c->opts.mode == MCGB_MODE_PERSISTENT) {
+        CK(cudaMemsetAsync(r.work, 0, sizeof(int), st));
+        PersistentArgs a{};
+        a.gen = gen;
+        a.total = total;
+        a.gen_n = nullptr;
+        a.gen_base = gen_base;
+        a.src_idx = src_idx;
+        a.eigen = eigen;
+        a.work = r.work;
+        a.chunk = 1;
+        int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
+                                             : std::max(1, persistent_max_blocks_per_sm(block));
+        int64_t want = (total + block - 1) / block;
+        int grid = (int)std::min<int64_t>((int64_t)c->sms * bps, std::max<int64_t>(want, 1));
+        launch_persistent(W, r.P, Bsrc, Bdst, R, a, grid, block, st);
+        c->launches += 1;
+        CK(cudaGetLastError());
+        return MCGB_OK;
+    }
+    launch_source(W, r.P, Bsrc, R, gen, total, gen_base, src_idx, eigen, block, st);
+    c->launches += 1;
+    int64_t n_act = total;
+    int cur = 0;
+    const int *list = nullptr;   // identity for the first iteration
+    int64_t maxit = c->opts.max_iterations > 0 ? c->opts.max_iterations : 10000000;
+    for (int64_t it = 0; n_act > 0; it++) {
+        if (it >= maxit) return fail(MCGB_E_TIMEOUT, "event iteration limit reached");
+        CK(cudaMemsetAsync(r.q_n, 0, 3 * sizeof(int), st));
+        int *next = r.list[cur];
+        launch_advance(W, r.P, R, list, (int)n_act, r.q_cross, r.q_coll, block, st);
+        launch_cross(W, r.P, R, r.q_cross, (int)n_act, next, block, st);
+        launch_collide(W, r.P, Bdst, R, r.q_coll, (int)n_act, next, block, st);
+        c->launches += 3;
+        CK(cudaMemcpyAsync(r.pinned, r.q_n + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        n_act = r.pinned[0];
+        list = next;
+        cur ^= 1;
+        c->counters.event_iterations++;
+    }
+    CK(cudaGetLastError());
+    return MCGB_OK;
+}
+
+static void mean_sd(double sum, double sum2, int n, double &mean, double &sd)
+{
+    mean = sum / n;
+    if (n > 1) {
+        double var = (sum2 - n * mean * mean) / (n - 1);
+        sd = std::sqrt(var > 0.0 ? var / n : 0.0);
+    } else {
+        sd = 0.0;
+    }
+}
+
+static double draw_host(uint64_t &s)
+{
+    s = rng_next(s);
+    return (double)((s >> 10) + 1) * 0x1p-53;
+}
+
+static int fetch_counters(mcgb_ctx *c)
+{
+    unsigned long long h[8];
+    CK(cudaMemcpyAsync(h, c->rs.cnt, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->counters.collisions = (int64_t)h[0];
+    c->counters.crossings = (int64_t)h[1];
+    c->counters.leaks = (int64_t)h[2];
+    c->counters.lost = (int64_t)h[3];
+    c->counters.capped = (int64_t)h[4];
+    c->counters.kernel_launches = c->launches;
+    c->counters.world_bytes = c->world ? (int64_t)c->world->bytes : 0;
+    return MCGB_OK;
+}
+
+static int copy_records(mcgb_ctx *c, int64_t n)
+{
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    c->h_coll.resize(n); c->h_cross.resize(n); c->h_fis.resize(n);
+    c->h_fate.resize(n); c->h_g.resize(n); c->h_rng.resize(n);
+    std::vector<signed char> fate(n);
+    CK(cudaMemcpyAsync(c->h_coll.data(), r.P.ncoll, n * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_cross.data(), r.P.ncross, n * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_fis.data(), r.P.nfis, n * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_g.data(), r.P.g, n * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_rng.data(), r.P.s, n * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(fate.data(), r.P.fate, n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int64_t j = 0; j < n; j++) c->h_fate[j] = fate[j];
+    return MCGB_OK;
+}
+
+// the bank `B` of M sites with permutation perm, copied in (parent, child) order
+static int copy_bank(mcgb_ctx *c, const Bank &B, int64_t M)
+{
+    cudaStream_t st = c->stream;
+    std::vector<int> perm(M), par(M), ch(M), mat(M);
+    std::vector<double> x(M), y(M), z(M);
+    if (M > 0) {
+        CK(cudaMemcpyAsync(perm.data(), c->rs.perm, M * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(par.data(), B.parent, M * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ch.data(), B.child, M * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(mat.data(), B.mat, M * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(x.data(), B.x, M * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(y.data(), B.y, M * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(z.data(), B.z, M * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    c->b_xyz.resize(3 * M); c->b_parent.resize(M); c->b_child.resize(M); c->b_mat.resize(M);
+    for (int64_t k = 0; k < M; k++) {
+        int b = perm[k];
+        c->b_xyz[3 * k] = x[b]; c->b_xyz[3 * k + 1] = y[b]; c->b_xyz[3 * k + 2] = z[b];
+        c->b_parent[k] = par[b]; c->b_child[k] = ch[b]; c->b_mat[k] = mat[b];
+    }
+    return MCGB_OK;
+}
+
+static int read_flags(mcgb_ctx *c, int64_t &M, int &err)
+{
+    CK(cudaMemcpyAsync(c->rs.pinned + 4, c->rs.M, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->rs.pinned + 5, c->rs.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->rs.pinned + 6, c->rs.bank_n, sizeof(int), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    M = c->rs.pinned[4];
+    err = c->rs.pinned[5];
+    if (c->rs.pinned[6] > c->rs.cap_b) err |= ERR_BANK_OVERFLOW;
+    return MCGB_OK;
+}
+
+static int build_single(mcgb_ctx *c, int64_t n, int batches, uint64_t seed)
+{
+    if (!c->world) c->world.reset(new DeviceWorld());
+    std::vector<ProblemRun> runs{{&c->def, n, batches, seed}};
+    std::string e = build_world(runs, *c->world, c->stream);
+    if (!e.empty()) return fail(MCGB_E_STATE, e);
+    return MCGB_OK;
+}
+
+static int check_lost(mcgb_ctx *c)
+{
+    if (c->counters.lost > 0 && (double)c->counters.lost > 1e-6 * (double)c->counters.histories)
+        return fail(MCGB_E_LOST_PARTICLES, "lost particles: " + std::to_string(c->counters.lost));
+    return MCGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// k-eigenvalue power iteration, stepwise: begin, any number of cycles, finish.
+static int eigen_begin(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_t seed)
+{
+    if (N <= 0 || N > (int64_t)1 << 30 || active < 1 || inactive < 0 || inactive + active > 4096)
+        return fail(MCGB_E_INVALID_ARG, "bad run size");
+    c->eig.on = false;
+    CKR(build_single(c, N, 1, seed));
+    double bf = c->opts.bank_factor > 0 ? c->opts.bank_factor : 3.0;
+    int64_t cap_b = (int64_t)(bf * (double)N) + 1024;
+    CKR(prepare_buffers(c, N, cap_b));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const World &W = c->world->W;
+    int acc = W.acc_size;
+    CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)acc * W.nrep, st));
+    CK(cudaMemsetAsync(r.tsum, 0, sizeof(double) * std::max(acc, 1), st));
+    CK(cudaMemsetAsync(r.tsum2, 0, sizeof(double) * std::max(acc, 1), st));
+    CK(cudaMemsetAsync(r.kout, 0, sizeof(double) * 2 * 4096, st));
+    CK(cudaMemsetAsync(r.cnt, 0, sizeof(unsigned long long) * 8, st));
+    CK(cudaMemsetAsync(r.err, 0, sizeof(int), st));
+    int64_t base[2] = {0, N};
+    CK(cudaMemcpyAsync(r.gen_base[0], base, sizeof base, cudaMemcpyHostToDevice, st));
+    int ncyc = inactive + active;
+    c->counters = mcgb_counters{};
+    c->counters.world_bytes = (int64_t)c->world->bytes;
+    c->launches = 0;
+    c->cyc_ktl.assign(ncyc, 0.0);
+    c->cyc_kc.assign(ncyc, 0.0);
+    c->cyc_m.assign(ncyc, 0);
+    c->cyc_tms.assign(ncyc, 0.0);
+    c->cyc_ms.assign(ncyc, 0.0);
+    EigenRun &e = c->eig;
+    e.on = true;
+    e.N = N;
+    e.inactive = inactive;
+    e.active = active;
+    e.ncyc = ncyc;
+    e.cyc = 0;
+    e.cur = 0;
+    e.seed = c->world->probs[0].seed;
+    if (c->events.size() < (size_t)3 * ncyc + 3) {
+        size_t old = c->events.size();
+        c->events.resize(3 * ncyc + 3);
+        for (size_t i = old; i < c->events.size(); i++) CK(cudaEventCreate(&c->events[i]));
+    }
+    return MCGB_OK;
+}
+
+static int eigen_cycles(mcgb_ctx *c, int k)
+{
+    EigenRun &e = c->eig;
+    if (!e.on) return fail(MCGB_E_STATE, "no eigenvalue run in progress");
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const World &W = c->world->W;
+    RunBufs R = run_bufs(c, nullptr, -1, 0);
+    int64_t N = e.N;
+    for (int q = 0; q < k && e.cyc < e.ncyc; q++) {
+        int cyc = e.cyc;
+        int nxt = e.cur ^ 1;
+        cudaEvent_t ev0 = c->events[3 * cyc], ev1 = c->events[3 * cyc + 1], ev2 = c->events[3 * cyc + 2];
+        CK(cudaEventRecord(ev0, st));
+        CK(cudaMemsetAsync(r.bank_n, 0, sizeof(int), st));
+        CKR(transport_generation(c, R, cyc, N, r.gen_base[0], cyc == 0 ? nullptr : r.src_idx, 1,
+                                 r.bank[e.cur], r.bank[nxt]));
+        CK(cudaEventRecord(ev1, st));
+        launch_reduce_gen(r.P, N, nullptr, r.kout + 2 * cyc, r.cnt, st);
+        scan_exclusive(r.P.nfis, r.off, N, r.M, r.scratch, st);
+        launch_perm(r.bank[nxt], r.off, r.M, r.perm, c->sms * 4, st);
+        uint64_t rs = rng_stream(e.seed, ((uint64_t)cyc << 32) + 0xFFFFFFFFULL);
+        double xi = draw_host(rs);
+        launch_resample(r.perm, r.M, N, xi, r.src_idx, r.err, r.bank[nxt].cap, st);
+        launch_tally_cycle(r.tacc, W.acc_size, W.nrep, (double)N, cyc >= e.inactive, r.tsum, r.tsum2, st);
+        c->launches += 7;
+        CK(cudaEventRecord(ev2, st));
+        CK(cudaGetLastError());
+        int64_t M;
+        int err;
+        CKR(read_flags(c, M, err));
+        c->cyc_m[cyc] = M;
+        float t1 = 0.f, t2 = 0.f;
+        cudaEventElapsedTime(&t1, ev0, ev1);
+        cudaEventElapsedTime(&t2, ev0, ev2);
+        c->cyc_tms[cyc] = t1;
+        c->cyc_ms[cyc] = t2;
+        e.cyc++;
+        if (err & ERR_BANK_OVERFLOW) {
+            e.on = false;
+            return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow in cycle " + std::to_string(cyc));
+        }
+        if (err & ERR_SOURCE) {
+            e.on = false;
+            return fail(MCGB_E_STATE, "source sampling failed");
+        }
+        if (cyc == e.ncyc - 1 && c->opts.record_histories) {
+            CKR(copy_records(c, N));
+            CKR(copy_bank(c, r.bank[nxt], M));
+        }
+        if (M == 0) {
+            e.on = false;
+            return fail(MCGB_E_STATE, "fission bank empty after cycle " + std::to_string(cyc));
+        }
+        e.cur = nxt;
+    }
+    return MCGB_OK;
+}
+
+static int eigen_finish(mcgb_ctx *c)
+{
+    EigenRun &e = c->eig;
+    if (!e.on) return fail(MCGB_E_STATE, "no eigenvalue run in progress");
+    if (e.cyc < e.ncyc) return fail(MCGB_E_STATE, "cycles remain to be run");
+    e.on = false;
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    int acc = c->world->W.acc_size;
+    int ncyc = e.ncyc, inactive = e.inactive, active = e.active;
+    int64_t N = e.N;
+    std::vector<double> kout(2 * ncyc);
+    CK(cudaMemcpyAsync(kout.data(), r.kout, sizeof(double) * 2 * ncyc, cudaMemcpyDeviceToHost, st));
+    std::vector<double> ts(std::max(acc, 1)), ts2(std::max(acc, 1));
+    CK(cudaMemcpyAsync(ts.data(), r.tsum, sizeof(double) * acc, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ts2.data(), r.tsum2, sizeof(double) * acc, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double ks[3] = {0, 0, 0}, ks2[3] = {0, 0, 0};
+    for (int cyc = 0; cyc < ncyc; cyc++) {
+        c->cyc_ktl[cyc] = kout[2 * cyc] / (double)N;
+        c->cyc_kc[cyc] = kout[2 * cyc + 1] / (double)N;
+        if (cyc >= inactive) {
+            double kv[3] = {c->cyc_ktl[cyc], c->cyc_kc[cyc], (double)c->cyc_m[cyc] / (double)N};
+            for (int q = 0; q < 3; q++) {
+                ks[q] += kv[q];
+                ks2[q] += kv[q] * kv[q];
+            }
+        }
+    }
+    for (int q = 0; q < 3; q++) mean_sd(ks[q], ks2[q], active, c->k[2 * q], c->k[2 * q + 1]);
+    DeviceWorld &dw = *c->world;
+    c->t_mean.assign(c->def.tallies.size(), {});
+    c->t_sd.assign(c->def.tallies.size(), {});
+    for (size_t t = 0; t < c->def.tallies.size(); t++) {
+        int gt = dw.tally_first[0] + (int)t;
+        int nb = dw.t_nbins[gt] * dw.t_ne[gt];
+        c->t_mean[t].resize(nb);
+        c->t_sd[t].resize(nb);
+        for (int b = 0; b < nb; b++)
+            mean_sd(ts[dw.t_off[gt] + b], ts2[dw.t_off[gt] + b], active, c->t_mean[t][b],
+                    c->t_sd[t][b]);
+    }
+    c->counters.histories = N * ncyc;
+    c->counters.generations = ncyc;
+    CKR(fetch_counters(c));
+    return check_lost(c);
+}
+
+static int run_eigen(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_t seed)
+{
+    CKR(eigen_begin(c, N, inactive, active, seed));
+    CKR(eigen_cycles(c, inactive + active));
+    return eigen_finish(c);
+}
+
+// Fixed source over the problems of the current world (one or a batch).
+// With `grad`, keeps every generation's own detector tallies and banks.
+static int run_fixed_world(mcgb_ctx *c, bool grad, int det_cell)
+{
+    DeviceWorld &dw = *c->world;
+    const World &W = dw.W;
+    int nprob = W.nprob;
+    int64_t N = 0;
+    std::vector<int64_t> base(nprob + 1, 0);
+    for (int p = 0; p < nprob; p++) base[p + 1] = base[p] + dw.probs[p].n;
+    N = base[nprob];
+    if (N <= 0 || N > (int64_t)1 << 30) return fail(MCGB_E_INVALID_ARG, "bad run size");
+    double bf = c->opts.bank_factor > 0 ? c->opts.bank_factor : 3.0;
+    int64_t cap_b = (int64_t)(bf * (double)N) + 1024;
+    CKR(prepare_buffers(c, std::max(N, cap_b), cap_b));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    int acc = W.acc_size;
+    CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)acc * W.nrep, st));
+    CK(cudaMemsetAsync(r.kout, 0, sizeof(double) * 2 * 4096, st));
+    CK(cudaMemsetAsync(r.cnt, 0, sizeof(unsigned long long) * 8, st));
+    CK(cudaMemsetAsync(r.err, 0, sizeof(int), st));
+    CK(cudaMemcpyAsync(r.gen_base[0], base.data(), sizeof(int64_t) * (nprob + 1),
+                       cudaMemcpyHostToDevice, st));
+    c->counters = mcgb_counters{};
+    c->counters.world_bytes = (int64_t)dw.bytes;
+    c->launches = 0;
+    if (grad) {
+        c->grad_gens.clear();
+        c->grad_mem.release();
+        c->grad_ready = false;
+    }
+    int G = dw.probs[0].G;
+    int cur = 0, gb = 0;
+    int64_t total = N;
+    const int *src = nullptr;
+    int gen;
+    const int MAX_GEN = 200;
+    for (gen = 0; gen < MAX_GEN; gen++) {
+        int nxt = cur ^ 1;
+        double *own = nullptr;
+        if (grad) {
+            CKR(c->grad_mem.get(own, total * G));
+            CK(cudaMemsetAsync(own, 0, sizeof(double) * total * G, st));
+        }
+        RunBufs R = run_bufs(c, own, det_cell, G);
+        CK(cudaMemsetAsync(r.bank_n, 0, sizeof(int), st));
+        CKR(transport_generation(c, R, gen, total, r.gen_base[gb], src, 0, r.bank[cur], r.bank[nxt]));
+        launch_reduce_gen(r.P, total, nullptr, r.kout, r.cnt, st);
+        scan_exclusive(r.P.nfis, r.off, total, r.M, r.scratch, st);
+        launch_perm(r.bank[nxt], r.off, r.M, r.perm, c->sms * 4, st);
+        launch_gen_base(r.gen_base[gb], nprob, r.off, r.M, r.gen_base[gb ^ 1], st);
+        c->launches += 6;
+        CK(cudaGetLastError());
+        int64_t M;
+        int err;
+        CKR(read_flags(c, M, err));
+        c->counters.histories += total;
+        if (err & ERR_BANK_OVERFLOW)
+            return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow in generation " + std::to_string(gen));
+        if (err & ERR_SOURCE) return fail(MCGB_E_STATE, "source sampling failed");
+        if (gen == 0 && c->opts.record_histories) {
+            CKR(copy_records(c, total));
+            CKR(copy_bank(c, r.bank[nxt], M));
+        }
+        if (grad) {
+            GradGen g;
+            g.n = total;
+            g.M = M;
+            g.own = own;
+            CKR(c->grad_mem.get(g.nfis, total));
+            CKR(c->grad_mem.get(g.off, total));
+            CKR(c->grad_mem.get(g.perm, M));
+            CK(cudaMemcpyAsync(g.nfis, r.P.nfis, 4 * total, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(g.off, r.off, 4 * total, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(g.perm, r.perm, 4 * std::max<int64_t>(M, 1), cudaMemcpyDeviceToDevice, st));
+            Bank &B = g.bank;
+            const Bank &S = r.bank[nxt];
+            CKR(c->grad_mem.get(B.x, M)); CKR(c->grad_mem.get(B.y, M)); CKR(c->grad_mem.get(B.z, M));
+            CKR(c->grad_mem.get(B.cell, M)); CKR(c->grad_mem.get(B.ix, M));
+            CKR(c->grad_mem.get(B.iy, M)); CKR(c->grad_mem.get(B.ucell, M));
+            CKR(c->grad_mem.get(B.mat, M)); CKR(c->grad_mem.get(B.root, M));
+            if (M > 0) {
+                CK(cudaMemcpyAsync(B.x, S.x, 8 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.y, S.y, 8 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.z, S.z, 8 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.cell, S.cell, 4 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.ix, S.ix, 4 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.iy, S.iy, 4 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.ucell, S.ucell, 4 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.mat, S.mat, 4 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.root, S.root, 4 * M, cudaMemcpyDeviceToDevice, st));
+            }
+            B.cap = M;
+            c->grad_gens.push_back(g);
+        }
+        if (M == 0) break;
+        // next generation: every site, in (parent, child) order
+        CK(cudaMemcpyAsync(r.src_idx, r.perm, 4 * M, cudaMemcpyDeviceToDevice, st));
+        src = r.src_idx;
+        total = M;
+        cur = nxt;
+        gb ^= 1;
+    }
+    if (gen == MAX_GEN) return fail(MCGB_E_TIMEOUT, "generation limit reached");
+    c->counters.generations = gen + 1;
+    // batch statistics
+    std::vector<double> sums(std::max(acc, 1));
+    if (acc > 0) {
+        launch_acc_reduce(r.tacc, acc, W.nrep, r.tsum, st);
+        c->launches += 1;
+        CK(cudaMemcpyAsync(sums.data(), r.tsum, sizeof(double) * acc, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    CKR(fetch_counters(c));
+    c->t_mean.clear();
+    c->t_sd.clear();
+    for (int p = 0; p < nprob; p++) {
+        const ProblemDev &P = dw.probs[p];
+        int B = P.batches;
+        std::vector<int64_t> nb(B, 0);
+        for (int64_t j = 0; j < P.n; j++) nb[(j * B) / P.n]++;
+        for (int t = 0; t < P.tally_count; t++) {
+            int gt = P.tally_first + t;
+            int ns = dw.t_nbins[gt] * dw.t_ne[gt];
+            std::vector<double> mean(ns), sd(ns);
+            for (int b = 0; b < ns; b++) {
+                double s = 0.0, s2 = 0.0;
+                for (int q = 0; q < B; q++) {
+                    double v = sums[dw.t_off[gt] + (size_t)q * ns + b];
+                    v /= (double)nb[q];
+                    s += v;
+                    s2 += v * v;
+                }
+                mean_sd(s, s2, B, mean[b], sd[b]);
+            }
+            c->t_mean.push_back(mean);
+            c->t_sd.push_back(sd);
+        }
+    }
+    if (grad) {
+        c->grad_n = N;
+        c->grad_cell = det_cell;
+        c->grad_ready = true;
+    }
+    return check_lost(c);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+extern "C" {
+
+const char *mcgb_last_error(void) { return g_err.c_str(); }
+
+int mcgb_create(mcgb_ctx **out, const mcgb_opts *opts)
+{
+    if (!out) return fail(MCGB_E_INVALID_ARG, "null output");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(MCGB_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    std::unique_ptr<mcgb_ctx> c(new mcgb_ctx());
+    if (opts) c->opts = *opts;
+    if (c->opts.device < 0 || c->opts.device >= ndev) return fail(MCGB_E_INVALID_ARG, "bad device");
+    c->device = c->opts.device;
+    CK(cudaSetDevice(c->device));
+    CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (c->opts.block != 0 && (c->opts.block < 32 || c->opts.block > 256 || c->opts.block % 32))
+        return fail(MCGB_E_INVALID_ARG, "block must be a multiple of 32 in [32, 256]");
+    *out = c.release();
+    return MCGB_OK;
+}
+
+int mcgb_destroy(mcgb_ctx *ctx)
+{
+    if (!ctx) return MCGB_OK;
+    cudaSetDevice(ctx->device);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    if (ctx->rs.pinned) cudaFreeHost(ctx->rs.pinned);
+    delete ctx;
+    return MCGB_OK;
+}
+
+int mcgb_set_stream(mcgb_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
+    ctx->stream = (cudaStream_t)stream;
+    return MCGB_OK;
+}
+
+int mcgb_set_mode(mcgb_ctx *ctx, int mode)
+{
+    if (!ctx || (mode != MCGB_MODE_EVENT && mode != MCGB_MODE_PERSISTENT))
+        return fail(MCGB_E_INVALID_ARG, "bad mode");
+    ctx->opts.mode = mode;
+    return MCGB_OK;
+}
+
+int mcgb_add_surface(mcgb_ctx *ctx, int type, const double coef[4], int bc, int *id)
+{
+    if (!ctx || !coef || type < 0 || type > 5 || bc < 0 || bc > 2)
+        return fail(MCGB_E_INVALID_ARG, "bad surface type or boundary");
+    if (bc == MCGB_BC_REFLECT && type > MCGB_SURF_PLANE)
+        return fail(MCGB_E_INVALID_ARG, "reflective boundaries must be planes");
+    if ((type == MCGB_SURF_CYLZ && !(coef[2] > 0.0)) || (type == MCGB_SURF_SPHERE && !(coef[3] > 0.0)))
+        return fail(MCGB_E_INVALID_ARG, "radius must be positive");
+    ProblemDef &d = ctx->def;
+    d.s_type.push_back(type);
+    d.s_bc.push_back(bc);
+    for (int k = 0; k < 4; k++) d.s_coef.push_back(coef[k]);
+    if (id) *id = (int)d.s_type.size() - 1;
+    return MCGB_OK;
+}
+
+int mcgb_add_cell(mcgb_ctx *ctx, int universe, int n, const int *surf, const int *sense,
+                  int fill_kind, int fill, int *id)
+{
+    if (!ctx || universe < 0 || n < 0 || (n > 0 && (!surf || !sense)) || fill < 0 ||
+        (fill_kind != MCGB_FILL_MATERIAL && fill_kind != MCGB_FILL_LATTICE))
+        return fail(MCGB_E_INVALID_ARG, "bad cell");
+    CellDef c;
+    c.univ = universe;
+    c.fillk = fill_kind;
+    c.fill = fill;
+    for (int k = 0; k < n; k++) {
+        if (surf[k] < 0 || surf[k] >= (int)ctx->def.s_type.size() || (sense[k] != 1 && sense[k] != -1))
+            return fail(MCGB_E_INVALID_ARG, "bad half-space");
+        c.surf.push_back(surf[k]);
+        c.sense.push_back(sense[k]);
+    }
+    ctx->def.cells.push_back(c);
+    if (id) *id = (int)ctx->def.cells.size() - 1;
+    return MCGB_OK;
+}
+
+int mcgb_add_lattice(mcgb_ctx *ctx, double x0, double y0, double pitch, int nx, int ny,
+                     const int *universes, int *id)
+{
+    if (!ctx || nx <= 0 || ny <= 0 || !(pitch > 0.0) || !universes)
+        return fail(MCGB_E_INVALID_ARG, "bad lattice");
+    LatDef L{x0, y0, pitch, nx, ny, std::vector<int>(universes, universes + (size_t)nx * ny)};
+    ctx->def.lats.push_back(L);
+    if (id) *id = (int)ctx->def.lats.size() - 1;
+    return MCGB_OK;
+}
+
+int mcgb_set_groups(mcgb_ctx *ctx, int G)
+{
+    if (!ctx || G <= 0 || G > MAX_G) return fail(MCGB_E_INVALID_ARG, "bad group count");
+    if (ctx->def.ce == 1 || !ctx->def.mg.empty()) return fail(MCGB_E_STATE, "groups already fixed");
+    ctx->def.G = G;
+    ctx->def.ce = 0;
+    return MCGB_OK;
+}
+
+static int check_mg(int G, const double *st, const double *ss, const double *nf)
+{
+    for (int g = 0; g < G; g++) {
+        if (!(st[g] >= 0.0) || !(nf[g] >= 0.0)) return fail(MCGB_E_INVALID_ARG, "negative cross section");
+        double acc = 0.0;
+        for (int h = 0; h < G; h++) {
+            if (!(ss[g * G + h] >= 0.0)) return fail(MCGB_E_INVALID_ARG, "negative cross section");
+            acc = acc + ss[g * G + h];
+        }
+        if (acc > st[g]) return fail(MCGB_E_INVALID_ARG, "scattering exceeds total");
+    }
+    return MCGB_OK;
+}
+
+int mcgb_add_material_mg(mcgb_ctx *ctx, const double *sigma_t, const double *sigma_s,
+                         const double *nu_sigma_f, const double *chi, int *id)
+{
+    if (!ctx || !sigma_t || !sigma_s || !nu_sigma_f || !chi) return fail(MCGB_E_INVALID_ARG, "null array");
+    int G = ctx->def.G;
+    if (ctx->def.ce != 0 || G <= 0) return fail(MCGB_E_STATE, "call mcgb_set_groups first");
+    CKR(check_mg(G, sigma_t, sigma_s, nu_sigma_f));
+    MatMGDef m{std::vector<double>(sigma_t, sigma_t + G), std::vector<double>(sigma_s, sigma_s + G * G),
+               std::vector<double>(nu_sigma_f, nu_sigma_f + G), std::vector<double>(chi, chi + G)};
+    ctx->def.mg.push_back(m);
+    if (id) *id = (int)ctx->def.mg.size() - 1;
+    return MCGB_OK;
+}
+
+int mcgb_update_material_mg(mcgb_ctx *ctx, int id, const double *sigma_t, const double *sigma_s,
+                            const double *nu_sigma_f, const double *chi)
+{
+    if (!ctx || id < 0 || id >= (int)ctx->def.mg.size()) return fail(MCGB_E_NOT_FOUND, "no such material");
+    int G = ctx->def.G;
+    CKR(check_mg(G, sigma_t, sigma_s, nu_sigma_f));
+    MatMGDef &m = ctx->def.mg[id];
+    m.sigt.assign(sigma_t, sigma_t + G);
+    m.sigs.assign(sigma_s, sigma_s + G * G);
+    m.nusf.assign(nu_sigma_f, nu_sigma_f + G);
+    if (chi) m.chi.assign(chi, chi + G);
+    return MCGB_OK;
+}
+
+int mcgb_add_nuclide_ce(mcgb_ctx *ctx, double A, int n, const double *E, const double *sig_s,
+                        const double *sig_c, const double *sig_f, double nu, int *id)
+{
+    if (!ctx || n < 2 || !(A > 0.0) || !E || !sig_s || !sig_c || !sig_f || nu < 0.0)
+        return fail(MCGB_E_INVALID_ARG, "bad nuclide");
+    if (ctx->def.ce == 0) return fail(MCGB_E_STATE, "problem is multigroup");
+    for (int k = 1; k < n; k++)
+        if (!(E[k] > E[k - 1])) return fail(MCGB_E_INVALID_ARG, "energy grid not increasing");
+    for (int k = 0; k < n; k++)
+        if (!(sig_s[k] >= 0.0 && sig_c[k] >= 0.0 && sig_f[k] >= 0.0))
+            return fail(MCGB_E_INVALID_ARG, "negative cross section");
+    ctx->def.ce = 1;
+    NucDef u{A, nu, std::vector<double>(E, E + n), std::vector<double>(sig_s, sig_s + n),
+             std::vector<double>(sig_c, sig_c + n), std::vector<double>(sig_f, sig_f + n)};
+    ctx->def.nucs.push_back(u);
+    if (id) *id = (int)ctx->def.nucs.size() - 1;
+    return MCGB_OK;
+}
+
+int mcgb_add_material_ce(mcgb_ctx *ctx, int n, const int *nuclides, const double *density, int *id)
+{
+    if (!ctx || n <= 0 || n > MAX_NUC || !nuclides || !density)
+        return fail(MCGB_E_INVALID_ARG, "bad material");
+    if (ctx->def.ce != 1) return fail(MCGB_E_STATE, "add nuclides first");
+    MatCEDef m;
+    for (int k = 0; k < n; k++) {
+        if (nuclides[k] < 0 || nuclides[k] >= (int)ctx->def.nucs.size())
+            return fail(MCGB_E_INVALID_ARG, "bad nuclide id");
+        if (!(density[k] >= 0.0)) return fail(MCGB_E_INVALID_ARG, "negative density");
+        m.nuc.push_back(nuclides[k]);
+        m.dens.push_back(density[k]);
+    }
+    ctx->def.mce.push_back(m);
+    if (id) *id = (int)ctx->def.mce.size() - 1;
+    return MCGB_OK;
+}
+
+int mcgb_set_source(mcgb_ctx *ctx, int kind, const double *params, int accept, int energy_kind,
+                    const double *energy, int n_energy, int dir_kind, const double *beam)
+{
+    if (!ctx || !params || (kind != MCGB_SRC_BOX && kind != MCGB_SRC_POINT) || accept < 0 ||
+        accept > 1 || energy_kind < 0 || energy_kind > 3 || (dir_kind != 0 && dir_kind != 1))
+        return fail(MCGB_E_INVALID_ARG, "bad source");
+    if ((energy_kind == MCGB_ENERGY_PDF || energy_kind == MCGB_ENERGY_FIXED) && (!energy || n_energy < 1))
+        return fail(MCGB_E_INVALID_ARG, "source energy data missing");
+    if (dir_kind == MCGB_DIR_BEAM && !beam) return fail(MCGB_E_INVALID_ARG, "beam direction missing");
+    SrcDef s;
+    s.kind = kind;
+    s.accept = accept;
+    s.ekind = energy_kind;
+    s.dkind = dir_kind;
+    std::memcpy(s.p, params, sizeof(double) * (kind == MCGB_SRC_BOX ? 6 : 3));
+    if (dir_kind == MCGB_DIR_BEAM) std::memcpy(s.beam, beam, sizeof s.beam);
+    if (energy_kind == MCGB_ENERGY_PDF) s.pdf.assign(energy, energy + n_energy);
+    if (energy_kind == MCGB_ENERGY_FIXED) s.E = energy[0];
+    ctx->def.src = s;
+    return MCGB_OK;
+}
+
+int mcgb_add_tally(mcgb_ctx *ctx, int filter, int n_edges, const double *edges, int *id)
+{
+    if (!ctx || filter < 0 || filter > 2 || n_edges < 0 || (n_edges > 0 && !edges))
+        return fail(MCGB_E_INVALID_ARG, "bad tally");
+    TallyDef t;
+    t.filter = filter;
+    for (int k = 0; k < n_edges; k++) {
+        if (k > 0 && !(edges[k] > edges[k - 1])) return fail(MCGB_E_INVALID_ARG, "edges not increasing");
+        t.edges.push_back(edges[k]);
+    }
+    ctx->def.tallies.push_back(t);
+    if (id) *id = (int)ctx->def.tallies.size() - 1;
+    return MCGB_OK;
+}
+
+int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions)
+{
+    if (!ctx || max_collisions < 0) return fail(MCGB_E_INVALID_ARG, "bad max_collisions");
+    ctx->def.max_coll = max_collisions;
+    return MCGB_OK;
+}
+
+int mcgb_run_eigenvalue(mcgb_ctx *ctx, int64_t n, int inactive, int active, uint64_t seed)
+{
+    if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
+    CK(cudaSetDevice(ctx->device));
+    return run_eigen(ctx, n, inactive, active, seed);
+}
+
+int mcgb_eigen_begin(mcgb_ctx *ctx, int64_t n, int inactive, int active, uint64_t seed)
+{
+    if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
+    CK(cudaSetDevice(ctx->device));
+    return eigen_begin(ctx, n, inactive, active, seed);
+}
+
+int mcgb_eigen_cycles(mcgb_ctx *ctx, int n_cycles)
+{
+    if (!ctx || n_cycles < 0) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    CK(cudaSetDevice(ctx->device));
+    return eigen_cycles(ctx, n_cycles);
+}
+
+int mcgb_eigen_finish(mcgb_ctx *ctx)
+{
+    if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
+    CK(cudaSetDevice(ctx->device));
+    return eigen_finish(ctx);
+}
+
+int mcgb_get_cycle_times(mcgb_ctx *ctx, int n_cycles, double *transport_ms, double *cycle_ms)
+{
+    if (!ctx || n_cycles < 0) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    for (int i = 0; i < n_cycles && i < (int)ctx->cyc_tms.size(); i++) {
+        if (transport_ms) transport_ms[i] = ctx->cyc_tms[i];
+        if (cycle_ms) cycle_ms[i] = ctx->cyc_ms[i];
+    }
+    return MCGB_OK;
+}
+
+int mcgb_run_fixed_source(mcgb_ctx *ctx, int64_t n, int batches, uint64_t seed)
+{
+    if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
+    if (n <= 0 || batches < 1 || batches > n) return fail(MCGB_E_INVALID_ARG, "bad run size");
+    CK(cudaSetDevice(ctx->device));
+    CKR(build_single(ctx, n, batches, seed));
+    return run_fixed_world(ctx, false, -1);
+}
+
+int mcgb_get_k(mcgb_ctx *ctx, double out[6])
+{
+    if (!ctx || !out) return fail(MCGB_E_INVALID_ARG, "null argument");
+    std::memcpy(out, ctx->k, sizeof ctx->k);
+    return MCGB_OK;
+}
+
+int mcgb_get_cycle_k(mcgb_ctx *ctx, int n_cycles, double *k_tl, double *k_col, int64_t *bank)
+{
+    if (!ctx || n_cycles < 0) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    for (int i = 0; i < n_cycles && i < (int)ctx->cyc_ktl.size(); i++) {
+        if (k_tl) k_tl[i] = ctx->cyc_ktl[i];
+        if (k_col) k_col[i] = ctx->cyc_kc[i];
+        if (bank) bank[i] = ctx->cyc_m[i];
+    }
+    return MCGB_OK;
+}
+
+int mcgb_tally_size(mcgb_ctx *ctx, int tally, int *n_bins, int *n_ebins)
+{
+    if (!ctx || tally < 0 || tally >= (int)ctx->def.tallies.size()) return fail(MCGB_E_NOT_FOUND, "no such tally");
+    const ProblemDef &d = ctx->def;
+    const TallyDef &t = d.tallies[tally];
+    int nmat = d.ce == 1 ? (int)d.mce.size() : (int)d.mg.size();
+    int nb = t.filter == MCGB_FILTER_CELL ? (int)d.cells.size()
+           : t.filter == MCGB_FILTER_LATTICE ? (d.lats.empty() ? 0 : d.lats[0].nx * d.lats[0].ny) : nmat;
+    if (n_bins) *n_bins = nb;
+    if (n_ebins) *n_ebins = d.ce == 1 ? (int)t.edges.size() - 1 : d.G;
+    return MCGB_OK;
+}
+
+int mcgb_get_tally(mcgb_ctx *ctx, int tally, double *mean, double *sd, size_t cap, size_t *needed)
+{
+    if (!ctx || tally < 0 || tally >= (int)ctx->t_mean.size()) return fail(MCGB_E_NOT_FOUND, "no tally results");
+    size_t n = ctx->t_mean[tally].size();
+    if (needed) *needed = n;
+    if (cap < n) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    if (mean) std::memcpy(mean, ctx->t_mean[tally].data(), n * sizeof(double));
+    if (sd) std::memcpy(sd, ctx->t_sd[tally].data(), n * sizeof(double));
+    return MCGB_OK;
+}
+
+int mcgb_get_counters(mcgb_ctx *ctx, mcgb_counters *out)
+{
+    if (!ctx || !out) return fail(MCGB_E_INVALID_ARG, "null argument");
+    ctx->counters.kernel_launches = ctx->launches;
+    *out = ctx->counters;
+    return MCGB_OK;
+}
+
+int mcgb_get_histories(mcgb_ctx *ctx, size_t cap, int32_t *n_coll, int32_t *n_cross,
+                       uint64_t *rng_end, int32_t *n_fis, int32_t *fate, int32_t *g_end,
+                       size_t *needed)
+{
+    if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
+    size_t n = ctx->h_coll.size();
+    if (needed) *needed = n;
+    if (cap < n) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    if (n_coll) std::memcpy(n_coll, ctx->h_coll.data(), n * 4);
+    if (n_cross) std::memcpy(n_cross, ctx->h_cross.data(), n * 4);
+    if (rng_end) std::memcpy(rng_end, ctx->h_rng.data(), n * 8);
+    if (n_fis) std::memcpy(n_fis, ctx->h_fis.data(), n * 4);
+    if (fate) std::memcpy(fate, ctx->h_fate.data(), n * 4);
+    if (g_end) std::memcpy(g_end, ctx->h_g.data(), n * 4);
+    return MCGB_OK;
+}
+
+int mcgb_get_bank(mcgb_ctx *ctx, size_t cap, double *xyz, int64_t *parent, int32_t *child,
+                  int32_t *mat, size_t *needed)
+{
+    if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
+    size_t n = ctx->b_parent.size();
+    if (needed) *needed = n;
+    if (cap < n) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    if (xyz) std::memcpy(xyz, ctx->b_xyz.data(), n * 24);
+    if (parent) std::memcpy(parent, ctx->b_parent.data(), n * 8);
+    if (child) std::memcpy(child, ctx->b_child.data(), n * 4);
+    if (mat) std::memcpy(mat, ctx->b_mat.data(), n * 4);
+    return MCGB_OK;
+}
+
+int mcgb_forward_fixed(mcgb_ctx *ctx, int64_t n, uint64_t seed, int det_cell, double *tally_out)
+{
+    if (!ctx || n <= 0) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (ctx->def.ce != 0) return fail(MCGB_E_STATE, "derivatives are multigroup only");
+    if (det_cell < 0 || det_cell >= (int)ctx->def.cells.size()) return fail(MCGB_E_INVALID_ARG, "bad detector cell");
+    CK(cudaSetDevice(ctx->device));
+    CKR(build_single(ctx, n, 1, seed));
+    CKR(run_fixed_world(ctx, true, det_cell));
+    if (tally_out) {
+        int G = ctx->def.G;
+        std::vector<double> acc(G, 0.0);
+        // the detector tally per group: sum of the stored own tallies of all generations
+        for (auto &g : ctx->grad_gens) {
+            std::vector<double> own(g.n * G);
+            CK(cudaMemcpy(own.data(), g.own, sizeof(double) * g.n * G, cudaMemcpyDeviceToHost));
+            for (int64_t j = 0; j < g.n; j++)
+                for (int q = 0; q < G; q++) acc[q] += own[j * G + q];
+        }
+        for (int q = 0; q < G; q++) tally_out[q] = acc[q] / (double)n;
+    }
+    return MCGB_OK;
+}
+
+int mcgb_backward_fixed(mcgb_ctx *ctx, const double *weights, double *d_sigt, double *d_sigs,
+                        double *d_nusf)
+{
+    if (!ctx || !weights) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (!ctx->grad_ready) return fail(MCGB_E_STATE, "run mcgb_forward_fixed first");
+    CK(cudaSetDevice(ctx->device));
+    int G = ctx->def.G, nm = (int)ctx->def.mg.size();
+    int npar = nm * G * (G + 2);
+    cudaStream_t st = ctx->stream;
+    DevAlloc tmp;
+    double *w, *grad;
+    CKR(tmp.get(w, G));
+    CKR(tmp.get(grad, npar));
+    CK(cudaMemcpyAsync(w, weights, sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(grad, 0, sizeof(double) * npar, st));
+    auto &gens = ctx->grad_gens;
+    int ng = (int)gens.size();
+    std::vector<double *> sub(ng, nullptr);
+    for (int g = 0; g < ng; g++) CKR(tmp.get(sub[g], gens[g].n));
+    for (int g = ng - 1; g >= 0; g--) {
+        launch_subtree(gens[g].own, w, G, gens[g].n, g + 1 < ng ? sub[g + 1] : nullptr, gens[g].off,
+                       gens[g].nfis, sub[g], st);
+        ctx->launches++;
+    }
+    for (int g = 0; g < ng; g++) {
+        ReplayArgs a{};
+        a.gen = g;
+        a.n = gens[g].n;
+        a.site = g > 0 ? gens[g - 1].perm : nullptr;
+        a.bank = g > 0 ? &gens[g - 1].bank : nullptr;
+        a.own = gens[g].own;
+        a.w = w;
+        a.sub_next = g + 1 < ng ? sub[g + 1] : nullptr;
+        a.off = gens[g].off;
+        a.nfis = gens[g].nfis;
+        a.det_cell = ctx->grad_cell;
+        a.G = G;
+        a.nmat = nm;
+        a.grad = grad;
+        launch_replay(ctx->world->W, a, 256, st);
+        ctx->launches++;
+    }
+    CK(cudaGetLastError());
+    std::vector<double> h(npar);
+    CK(cudaMemcpyAsync(h.data(), grad, sizeof(double) * npar, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double N = (double)ctx->grad_n;
+    for (int k = 0; k < nm * G; k++) d_sigt[k] = h[k] / N;
+    for (int k = 0; k < nm * G * G; k++) d_sigs[k] = h[nm * G + k] / N;
+    for (int k = 0; k < nm * G; k++) d_nusf[k] = h[nm * G + nm * G * G + k] / N;
+    return MCGB_OK;
+}
+
+// ---- building blocks -------------------------------------------------------
+int mcgb_rng_states(mcgb_ctx *ctx, uint64_t seed, uint64_t first_id, int64_t n_streams, int n_draws,
+                    uint64_t *out)
+{
+    if (!ctx || !out || n_streams < 0 || n_draws < 1) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    CK(cudaSetDevice(ctx->device));
+    DevAlloc tmp;
+    uint64_t *d;
+    CKR(tmp.get(d, n_streams * n_draws));
+    launch_rng_states(seed & LCG_MASK, first_id, n_streams, n_draws, d, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, d, sizeof(uint64_t) * n_streams * n_draws, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MCGB_OK;
+}
+
+static int ensure_world(mcgb_ctx *ctx)
+{
+    if (!ctx->world) {
+        ctx->world.reset(new DeviceWorld());
+        // a world with only the log tables when no problem is defined yet
+        if (ctx->def.check().empty()) return build_single(ctx, 1, 1, 1);
+        ProblemDef tiny;
+        tiny.ce = 0;
+        tiny.G = 1;
+        tiny.s_type = {SURF_PX};
+        tiny.s_bc = {BC_NONE};
+        tiny.s_coef = {0, 0, 0, 0};
+        tiny.cells.push_back(CellDef{0, FILL_MAT, 0, {}, {}});
+        tiny.mg.push_back(MatMGDef{{1.0}, {0.0}, {0.0}, {0.0}});
+        tiny.src.kind = SRC_POINT;
+        std::vector<ProblemRun> runs{{&tiny, 1, 1, 1}};
+        std::string e = build_world(runs, *ctx->world, ctx->stream);
+        if (!e.empty()) return fail(MCGB_E_STATE, e);
+        ctx->world->probs.clear();   // marks the tables as not belonging to the user's problem
+        return MCGB_OK;
+    }
+    return MCGB_OK;
+}
+
+int mcgb_log(mcgb_ctx *ctx, int64_t n, const double *xi, double *out)
+{
+    if (!ctx || n < 0 || (n > 0 && (!xi || !out))) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    CK(cudaSetDevice(ctx->device));
+    CKR(ensure_world(ctx));
+    DevAlloc tmp;
+    double *dx, *dy;
+    CKR(tmp.get(dx, n));
+    CKR(tmp.get(dy, n));
+    CK(cudaMemcpyAsync(dx, xi, 8 * n, cudaMemcpyHostToDevice, ctx->stream));
+    launch_log(ctx->world->W, n, dx, dy, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, dy, 8 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MCGB_OK;
+}
+
+int mcgb_probe(mcgb_ctx *ctx, int64_t n, const double *pos, const double *dir, int32_t *path,
+               double *dist, int32_t *kind)
+{
+    if (!ctx || n < 0 || (n > 0 && (!pos || !dir || !path || !dist || !kind)))
+        return fail(MCGB_E_INVALID_ARG, "bad argument");
+    CK(cudaSetDevice(ctx->device));
+    std::string e = ctx->def.check();
+    if (!e.empty()) return fail(MCGB_E_STATE, e);
+    CKR(build_single(ctx, 1, 1, 1));
+    DevAlloc tmp;
+    double *dp, *dd, *ddist;
+    int *dpath, *dkind;
+    CKR(tmp.get(dp, 3 * n)); CKR(tmp.get(dd, 3 * n)); CKR(tmp.get(ddist, n));
+    CKR(tmp.get(dpath, 5 * n)); CKR(tmp.get(dkind, n));
+    CK(cudaMemcpyAsync(dp, pos, 24 * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dd, dir, 24 * n, cudaMemcpyHostToDevice, ctx->stream));
+    launch_probe(ctx->world->W, ctx->world->probs[0].root_univ, n, dp, dd, dpath, ddist, dkind,
+                 ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(path, dpath, 20 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(dist, ddist, 8 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(kind, dkind, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MCGB_OK;
+}
+
+int mcgb_ce_lookup(mcgb_ctx *ctx, int mat, int64_t n, const double *E, double *out)
+{
+    if (!ctx || n < 0 || (n > 0 && (!E || !out))) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (ctx->def.ce != 1 || mat < 0 || mat >= (int)ctx->def.mce.size())
+        return fail(MCGB_E_INVALID_ARG, "bad material");
+    CK(cudaSetDevice(ctx->device));
+    std::string e = ctx->def.check();
+    if (!e.empty()) return fail(MCGB_E_STATE, e);
+    CKR(build_single(ctx, 1, 1, 1));
+    DevAlloc tmp;
+    double *dE, *dout;
+    CKR(tmp.get(dE, n));
+    CKR(tmp.get(dout, 4 * n));
+    CK(cudaMemcpyAsync(dE, E, 8 * n, cudaMemcpyHostToDevice, ctx->stream));
+    launch_ce_lookup(ctx->world->W, mat, n, dE, dout, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, dout, 32 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MCGB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batching: many independent fixed-source problems flattened into one world
+// and run generation by generation, every problem's particles in one launch.
+#include <chrono>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, mcgb_tune> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_signature(mcgb_batch *b)
+{
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, b->device);
+    std::ostringstream s;
+    s << prop.name << "|sm" << prop.multiProcessorCount << "|p" << b->runs.size();
+    int64_t n = 0, cells = 0, surfs = 0, groups = 0;
+    for (auto &r : b->runs) {
+        n += r.n;
+        cells += (int64_t)r.def->cells.size();
+        surfs += (int64_t)r.def->s_type.size();
+        groups += r.def->G;
+    }
+    s << "|n" << n << "|c" << cells << "|s" << surfs << "|g" << groups;
+    return s.str();
+}
+
+void tune_cache_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("MCGB_TUNE_CACHE");
+    if (!path) return;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string key;
+        mcgb_tune t{};
+        if (std::getline(is, key, '\t') && (is >> t.block >> t.blocks_per_sm >> t.chunk >> t.ms))
+            g_tune_cache[key] = t;
+    }
+}
+
+void tune_cache_store(const std::string &key, const mcgb_tune &t)
+{
+    g_tune_cache[key] = t;
+    const char *path = std::getenv("MCGB_TUNE_CACHE");
+    if (!path) return;
+    std::ofstream f(path, std::ios::app);
+    f << key << '\t' << t.block << ' ' << t.blocks_per_sm << ' ' << t.chunk << ' ' << t.ms << '\n';
+}
+
+}  // namespace
+
+static int batch_engine(mcgb_batch *b)
+{
+    if (!b->engine) {
+        mcgb_ctx *c = nullptr;
+        mcgb_opts o = b->opts;
+        if (o.mode == 0 && o.block == 0) o.mode = MCGB_MODE_PERSISTENT;
+        CKR(mcgb_create(&c, &o));
+        b->engine.reset(c);
+    }
+    return MCGB_OK;
+}
+
+static int batch_run_runs(mcgb_batch *b, const std::vector<ProblemRun> &runs, const mcgb_tune *tune)
+{
+    CKR(batch_engine(b));
+    mcgb_ctx *c = b->engine.get();
+    CK(cudaSetDevice(c->device));
+    if (tune) {
+        c->opts.block = tune->block;
+        c->opts.blocks_per_sm = tune->blocks_per_sm;
+    }
+    if (!c->world) c->world.reset(new DeviceWorld());
+    std::string e = build_world(runs, *c->world, c->stream);
+    if (!e.empty()) return fail(MCGB_E_STATE, e);
+    return run_fixed_world(c, false, -1);
+}
+
+extern "C" {
+
+int mcgb_batch_create(mcgb_batch **out, const mcgb_opts *opts)
+{
+    if (!out) return fail(MCGB_E_INVALID_ARG, "null output");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(MCGB_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    std::unique_ptr<mcgb_batch> b(new mcgb_batch());
+    if (opts) b->opts = *opts;
+    if (b->opts.device < 0 || b->opts.device >= ndev) return fail(MCGB_E_INVALID_ARG, "bad device");
+    b->device = b->opts.device;
+    *out = b.release();
+    return MCGB_OK;
+}
+
+int mcgb_batch_destroy(mcgb_batch *b)
+{
+    if (!b) return MCGB_OK;
+    if (b->engine) {
+        mcgb_destroy(b->engine.release());
+    }
+    delete b;
+    return MCGB_OK;
+}
+
+int mcgb_batch_add_problem(mcgb_batch *b, mcgb_ctx *problem, int64_t n, int batches, uint64_t seed,
+                           int *id)
+{
+    if (!b || !problem || n <= 0 || batches < 1 || batches > n)
+        return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if ((int)b->runs.size() >= 4096) return fail(MCGB_E_INVALID_ARG, "at most 4096 problems");
+    std::string e = problem->def.check();
+    if (!e.empty()) return fail(MCGB_E_STATE, e);
+    b->defs.emplace_back(new ProblemDef(problem->def));
+    b->runs.push_back(ProblemRun{b->defs.back().get(), n, batches, seed});
+    if (id) *id = (int)b->runs.size() - 1;
+    return MCGB_OK;
+}
+
+int mcgb_batch_autotune(mcgb_batch *b, int budget_ms, mcgb_tune *out)
+{
+    if (!b || b->runs.empty()) return fail(MCGB_E_STATE, "empty batch");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_cache_load();
+    std::string key = tune_signature(b);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+        b->tuned = it->second;
+        b->has_tune = true;
+        if (out) *out = b->tuned;
+        return MCGB_OK;
+    }
+    CKR(batch_engine(b));
+    // tuning runs: every problem at 1/scale of its size (at least 64 histories)
+    int64_t total = 0;
+    for (auto &r : b->runs) total += r.n;
+    int64_t scale = std::max<int64_t>(1, total / 400000);
+    std::vector<ProblemRun> small;
+    for (auto &r : b->runs) {
+        ProblemRun s = r;
+        s.n = std::max<int64_t>(64, r.n / scale);
+        s.batches = 1;
+        small.push_back(s);
+    }
+    mcgb_tune best{};
+    best.ms = 1e30;
+    auto t_start = std::chrono::steady_clock::now();
+    const int blocks[] = {128, 256, 64};
+    for (int blk : blocks) {
+        int occ = std::max(1, persistent_max_blocks_per_sm(blk));
+        for (int bps = occ; bps >= 1; bps = bps > 2 ? bps / 2 : bps - 1) {
+            mcgb_tune t{blk, bps, 1, 0.0};
+            // one warm-up, one timed
+            CKR(batch_run_runs(b, small, &t));
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventRecord(e0, b->engine->stream));
+            int r = batch_run_runs(b, small, &t);
+            CK(cudaEventRecord(e1, b->engine->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            CKR(r);
+            if (ms < best.ms) {
+                best = t;
+                best.ms = ms;
+            }
+            double spent = std::chrono::duration<double, std::milli>(
+                               std::chrono::steady_clock::now() - t_start).count();
+            if (budget_ms > 0 && spent > budget_ms) break;
+        }
+        double spent = std::chrono::duration<double, std::milli>(
+                           std::chrono::steady_clock::now() - t_start).count();
+        if (budget_ms > 0 && spent > budget_ms) break;
+    }
+    tune_cache_store(key, best);
+    b->tuned = best;
+    b->has_tune = true;
+    if (out) *out = best;
+    return MCGB_OK;
+}
+
+int mcgb_batch_run(mcgb_batch *b, const mcgb_tune *tune)
+{
+    if (!b || b->runs.empty()) return fail(MCGB_E_STATE, "empty batch");
+    const mcgb_tune *t = tune ? tune : (b->has_tune ? &b->tuned : nullptr);
+    CKR(batch_run_runs(b, b->runs, t));
+    mcgb_ctx *c = b->engine.get();
+    b->t_mean.clear();
+    b->t_sd.clear();
+    size_t k = 0;
+    for (auto &r : b->runs) {
+        std::vector<std::vector<double>> m, s;
+        for (size_t t2 = 0; t2 < r.def->tallies.size(); t2++, k++) {
+            m.push_back(c->t_mean[k]);
+            s.push_back(c->t_sd[k]);
+        }
+        b->t_mean.push_back(m);
+        b->t_sd.push_back(s);
+    }
+    return MCGB_OK;
+}
+
+int mcgb_batch_tally(mcgb_batch *b, int problem, int tally, double *mean, double *sd, size_t cap,
+                     size_t *needed)
+{
+    if (!b || problem < 0 || problem >= (int)b->t_mean.size() || tally < 0 ||
+        tally >= (int)b->t_mean[problem].size())
+        return fail(MCGB_E_NOT_FOUND, "no such tally result");
+    size_t n = b->t_mean[problem][tally].size();
+    if (needed) *needed = n;
+    if (cap < n) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    if (mean) std::memcpy(mean, b->t_mean[problem][tally].data(), n * 8);
+    if (sd) std::memcpy(sd, b->t_sd[problem][tally].data(), n * 8);
+    return MCGB_OK;
+}
+
+int mcgb_batch_counters(mcgb_batch *b, mcgb_counters *out)
+{
+    if (!b || !out || !b->engine) return fail(MCGB_E_STATE, "batch has not run");
+    *out = b->engine->counters;
+    return MCGB_OK;
+}
+
+}  // extern "C"

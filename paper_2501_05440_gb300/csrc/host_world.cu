@@ -1,0 +1,417 @@
+// host_world.cu -- flattening of problem definitions into device tables.
+//
+// Every array of every problem goes into one contiguous staging buffer (256-B
+// aligned sub-arrays) and one device allocation; indices are made global with
+// per-problem offsets so that a batch of problems is one World.  Derived
+// per-group constants (mean free path, fission yield and its floor/fraction,
+// scattering probability, cumulative distributions) are rounded once here.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "host_world.h"
+
+namespace mcgb {
+
+static const double LN2 = 0x1.62e42fefa39efp-1;
+
+// ln c = 2 atanh((c - 1)/(c + 1)) by its series, 40 terms (c in [1, 2]).
+double ln_series(double c)
+{
+    double s = (c - 1.0) / (c + 1.0);
+    double z = s * s;
+    double p = 1.0 / 79.0;
+    for (int k = 38; k >= 0; k--) p = p * z + 1.0 / (double)(2 * k + 1);
+    return 2.0 * s * p;
+}
+
+// Partial sums in order divided by the total; the last entry is exactly 1.
+void make_cdf(const double *w, int n, double *cdf)
+{
+    double acc = 0.0;
+    for (int k = 0; k < n; k++) {
+        acc = acc + w[k];
+        cdf[k] = acc;
+    }
+    for (int k = 0; k < n; k++) cdf[k] = cdf[k] / acc;
+    cdf[n - 1] = 1.0;
+}
+
+std::string ProblemDef::check() const
+{
+    if (src.kind < 0) return "no source defined";
+    if (cells.empty()) return "no cells defined";
+    if (ce < 0) return "no materials defined";
+    int nmat = ce ? (int)mce.size() : (int)mg.size();
+    if (nmat == 0) return "no materials defined";
+    int nu = 0;
+    for (auto &c : cells) nu = std::max(nu, c.univ + 1);
+    std::vector<int> ucount(nu, 0);
+    for (auto &c : cells) ucount[c.univ]++;
+    if (ucount[0] == 0) return "root universe 0 has no cells";
+    int ns = (int)s_type.size();
+    for (size_t i = 0; i < cells.size(); i++) {
+        auto &c = cells[i];
+        for (size_t h = 0; h < c.surf.size(); h++) {
+            if (c.surf[h] < 0 || c.surf[h] >= ns) return "cell " + std::to_string(i) + ": bad surface";
+            if (c.univ != 0 && s_bc[c.surf[h]] != BC_NONE)
+                return "cell " + std::to_string(i) + ": boundary conditions apply to root cells only";
+        }
+        if (c.fillk == FILL_MAT && (c.fill < 0 || c.fill >= nmat))
+            return "cell " + std::to_string(i) + ": bad material";
+        if (c.fillk == FILL_LAT) {
+            if (c.univ != 0) return "lattices may fill root cells only";
+            if (c.fill < 0 || c.fill >= (int)lats.size()) return "cell " + std::to_string(i) + ": bad lattice";
+        }
+    }
+    for (auto &L : lats)
+        for (int u : L.univ) {
+            if (u <= 0 || u >= nu || ucount[u] == 0) return "lattice refers to an empty universe";
+        }
+    for (auto &c : cells)
+        if (c.univ != 0 && c.fillk != FILL_MAT) return "universe cells must hold materials";
+    for (auto &t : tallies) {
+        if (t.filter == FILTER_LATTICE && lats.empty()) return "lattice tally without a lattice";
+        if (ce && t.edges.size() < 2) return "continuous-energy tally needs energy edges";
+    }
+    if (!ce && src.ekind == E_PDF && (int)src.pdf.size() != G) return "source group pdf size != G";
+    if (ce) {
+        for (auto &m : mce)
+            if ((int)m.nuc.size() > MAX_NUC) return "too many nuclides in a material";
+    }
+    return "";
+}
+
+DeviceWorld::~DeviceWorld()
+{
+    if (arena) cudaFree(arena);
+}
+
+namespace {
+
+struct Staging {
+    std::vector<char> buf;
+    template <class T> size_t put(const std::vector<T> &v)
+    {
+        size_t off = (buf.size() + 255) & ~(size_t)255;
+        buf.resize(off + std::max<size_t>(v.size() * sizeof(T), 8));
+        if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+        return off;
+    }
+};
+
+}  // namespace
+
+std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cudaStream_t st)
+{
+    std::vector<int> s_type, s_bc;
+    std::vector<double> s_coef, s_r2;
+    std::vector<int> c_univ, c_off, c_nhs, c_fillk, c_fill, hs_surf, hs_sense;
+    std::vector<double> l_x0, l_y0, l_pitch;
+    std::vector<int> l_nx, l_ny, l_uoff, l_univ;
+    std::vector<int> m_G, m_goff, m_ggoff, m_fissile;
+    std::vector<double> g_sigt, g_mfp, g_nusf, g_mu, g_mufl, g_mufr, g_ps, g_stot, g_chicdf;
+    std::vector<double> gg_sigs, gg_scdf;
+    std::vector<const NucDef *> nucs;
+    std::vector<double> n_A, n_nu;
+    std::vector<int> mc_off, mc_n, mc_nuc, mc_fissile;
+    std::vector<double> mc_dens, src_cdf;
+    std::vector<int> t_filter, t_nbins, t_ne, t_off, t_eoff, t_nedges, t_batches;
+    std::vector<double> t_edges;
+    std::vector<ProblemDev> probs;
+    int nuniv = 0;
+    int64_t acc_size = 0;
+    std::vector<int> tally_first;
+
+    for (const ProblemRun &r : runs) {
+        const ProblemDef &pd = *r.def;
+        std::string err = pd.check();
+        if (!err.empty()) return err;
+        ProblemDev P;
+        std::memset(&P, 0, sizeof P);
+        int surf0 = (int)s_type.size(), univ0 = nuniv, lat0 = (int)l_x0.size();
+        int mat0 = pd.ce ? (int)mc_off.size() : (int)m_G.size();
+        int nuc0 = (int)n_A.size();
+        P.cell0 = (int)c_univ.size();
+        P.mat0 = mat0;
+        P.root_univ = univ0;
+        P.lattice0 = pd.lats.empty() ? -1 : lat0;
+        P.ce = pd.ce;
+        P.G = pd.G;
+        for (size_t i = 0; i < pd.s_type.size(); i++) {
+            s_type.push_back(pd.s_type[i]);
+            s_bc.push_back(pd.s_bc[i]);
+            for (int k = 0; k < 4; k++) s_coef.push_back(pd.s_coef[4 * i + k]);
+            double R = pd.s_type[i] == SURF_CYLZ ? pd.s_coef[4 * i + 2]
+                     : pd.s_type[i] == SURF_SPHERE ? pd.s_coef[4 * i + 3] : 0.0;
+            s_r2.push_back(R * R);
+        }
+        int nu = 0;
+        for (auto &c : pd.cells) nu = std::max(nu, c.univ + 1);
+        for (auto &c : pd.cells) {
+            c_univ.push_back(c.univ + univ0);
+            c_off.push_back((int)hs_surf.size());
+            c_nhs.push_back((int)c.surf.size());
+            c_fillk.push_back(c.fillk);
+            c_fill.push_back(c.fillk == FILL_MAT ? c.fill + mat0 : c.fill + lat0);
+            for (size_t h = 0; h < c.surf.size(); h++) {
+                hs_surf.push_back(c.surf[h] + surf0);
+                hs_sense.push_back(c.sense[h]);
+            }
+        }
+        for (auto &L : pd.lats) {
+            l_x0.push_back(L.x0);
+            l_y0.push_back(L.y0);
+            l_pitch.push_back(L.pitch);
+            l_nx.push_back(L.nx);
+            l_ny.push_back(L.ny);
+            l_uoff.push_back((int)l_univ.size());
+            for (int u : L.univ) l_univ.push_back(u + univ0);
+        }
+        nuniv += nu;
+        if (!pd.ce) {
+            int G = pd.G;
+            for (auto &m : pd.mg) {
+                m_G.push_back(G);
+                m_goff.push_back((int)g_sigt.size());
+                m_ggoff.push_back((int)gg_sigs.size());
+                int fis = 0;
+                std::vector<double> row(G);
+                for (int g = 0; g < G; g++) {
+                    double st = m.sigt[g], nf = m.nusf[g];
+                    double acc = 0.0;
+                    for (int h = 0; h < G; h++) acc = acc + m.sigs[g * G + h];
+                    g_sigt.push_back(st);
+                    g_nusf.push_back(nf);
+                    g_stot.push_back(acc);
+                    g_mfp.push_back(st > 0.0 ? 1.0 / st : HUGE_VAL);
+                    double mu = st > 0.0 ? nf / st : 0.0;
+                    g_mu.push_back(mu);
+                    double fl = std::floor(mu);
+                    g_mufl.push_back(fl);
+                    g_mufr.push_back(mu - fl);
+                    g_ps.push_back(st > 0.0 ? acc / st : 0.0);
+                    for (int h = 0; h < G; h++) gg_sigs.push_back(m.sigs[g * G + h]);
+                    if (acc > 0.0) make_cdf(&m.sigs[g * G], G, row.data());
+                    else std::fill(row.begin(), row.end(), 1.0);
+                    for (int h = 0; h < G; h++) gg_scdf.push_back(row[h]);
+                    if (nf > 0.0) fis = 1;
+                }
+                double csum = 0.0;
+                for (int g = 0; g < G; g++) csum += m.chi[g];
+                if (csum > 0.0) make_cdf(m.chi.data(), G, row.data());
+                else std::fill(row.begin(), row.end(), 1.0);
+                for (int g = 0; g < G; g++) g_chicdf.push_back(row[g]);
+                m_fissile.push_back(fis);
+            }
+        } else {
+            for (auto &u : pd.nucs) {
+                nucs.push_back(&u);
+                n_A.push_back(u.A);
+                n_nu.push_back(u.nu);
+            }
+            for (auto &m : pd.mce) {
+                mc_off.push_back((int)mc_nuc.size());
+                mc_n.push_back((int)m.nuc.size());
+                int fis = 0;
+                for (size_t k = 0; k < m.nuc.size(); k++) {
+                    mc_nuc.push_back(m.nuc[k] + nuc0);
+                    mc_dens.push_back(m.dens[k]);
+                    const NucDef &u = pd.nucs[m.nuc[k]];
+                    if (u.nu > 0.0)
+                        for (double f : u.f)
+                            if (f > 0.0) {
+                                fis = 1;
+                                break;
+                            }
+                }
+                mc_fissile.push_back(fis);
+            }
+        }
+        P.src_kind = pd.src.kind;
+        P.src_accept = pd.src.accept;
+        P.src_ekind = pd.src.ekind;
+        P.src_dkind = pd.src.dkind;
+        std::memcpy(P.src_p, pd.src.p, sizeof P.src_p);
+        std::memcpy(P.src_beam, pd.src.beam, sizeof P.src_beam);
+        P.src_E = pd.src.E;
+        P.src_cdf_off = (int)src_cdf.size();
+        P.src_ncdf = (int)pd.src.pdf.size();
+        if (!pd.src.pdf.empty()) {
+            std::vector<double> cdf(pd.src.pdf.size());
+            make_cdf(pd.src.pdf.data(), (int)cdf.size(), cdf.data());
+            src_cdf.insert(src_cdf.end(), cdf.begin(), cdf.end());
+        }
+        P.tally_first = (int)t_filter.size();
+        P.tally_count = (int)pd.tallies.size();
+        tally_first.push_back(P.tally_first);
+        int ncell = (int)pd.cells.size();
+        int nmat = pd.ce ? (int)pd.mce.size() : (int)pd.mg.size();
+        for (auto &t : pd.tallies) {
+            int nb = t.filter == FILTER_CELL ? ncell
+                   : t.filter == FILTER_LATTICE ? pd.lats[0].nx * pd.lats[0].ny : nmat;
+            int ne = pd.ce ? (int)t.edges.size() - 1 : pd.G;
+            t_filter.push_back(t.filter);
+            t_nbins.push_back(nb);
+            t_ne.push_back(ne);
+            t_batches.push_back(r.batches);
+            t_off.push_back((int)acc_size);
+            acc_size += (int64_t)r.batches * nb * ne;
+            t_eoff.push_back((int)t_edges.size());
+            t_nedges.push_back((int)t.edges.size());
+            t_edges.insert(t_edges.end(), t.edges.begin(), t.edges.end());
+        }
+        if (acc_size > (int64_t)1 << 30) return "tally accumulators too large";
+        P.max_coll = pd.max_coll;
+        P.batches = r.batches;
+        P.seed = r.seed & 0x7FFFFFFFFFFFFFFFULL;
+        P.n = r.n;
+        probs.push_back(P);
+    }
+
+    // universes: cells in definition order
+    std::vector<int> u_off(nuniv + 1, 0), u_cells(c_univ.size());
+    for (int u : c_univ) u_off[u + 1]++;
+    for (int u = 0; u < nuniv; u++) u_off[u + 1] += u_off[u];
+    {
+        std::vector<int> fill(nuniv, 0);
+        for (size_t c = 0; c < c_univ.size(); c++) u_cells[u_off[c_univ[c]] + fill[c_univ[c]]++] = (int)c;
+    }
+    // candidates across each half-space: cells of the same universe bounded by
+    // the same surface with the opposite sense, in definition order
+    std::map<std::tuple<int, int, int>, std::vector<int>> bysurf;
+    for (size_t c = 0; c < c_univ.size(); c++)
+        for (int h = 0; h < c_nhs[c]; h++)
+            bysurf[std::make_tuple(c_univ[c], hs_surf[c_off[c] + h], hs_sense[c_off[c] + h])]
+                .push_back((int)c);
+    std::vector<int> hs_coff(hs_surf.size() + 1, 0), hs_cand;
+    for (size_t c = 0; c < c_univ.size(); c++)
+        for (int h = 0; h < c_nhs[c]; h++) {
+            int k = c_off[c] + h;
+            auto it = bysurf.find(std::make_tuple(c_univ[c], hs_surf[k], -hs_sense[k]));
+            if (it != bysurf.end()) hs_cand.insert(hs_cand.end(), it->second.begin(), it->second.end());
+            hs_coff[k + 1] = (int)hs_cand.size();
+        }
+
+    // continuous energy: union grid, per-nuclide interval maps and interval data
+    std::vector<double> Eu;
+    std::vector<int> umap, n_ivoff;
+    std::vector<double> n_iv;
+    if (!nucs.empty()) {
+        for (auto *u : nucs) Eu.insert(Eu.end(), u->E.begin(), u->E.end());
+        std::sort(Eu.begin(), Eu.end());
+        Eu.erase(std::unique(Eu.begin(), Eu.end()), Eu.end());
+        size_t nuni = Eu.size();
+        umap.resize(nucs.size() * nuni);
+        for (size_t q = 0; q < nucs.size(); q++) {
+            const NucDef &u = *nucs[q];
+            int n = (int)u.E.size();
+            n_ivoff.push_back((int)(n_iv.size() / 8));
+            for (int j = 0; j + 1 < n; j++) {
+                n_iv.push_back(u.E[j]);
+                n_iv.push_back(1.0 / (u.E[j + 1] - u.E[j]));
+                n_iv.push_back(u.s[j]);
+                n_iv.push_back(u.s[j + 1] - u.s[j]);
+                n_iv.push_back(u.c[j]);
+                n_iv.push_back(u.c[j + 1] - u.c[j]);
+                n_iv.push_back(u.f[j]);
+                n_iv.push_back(u.f[j + 1] - u.f[j]);
+            }
+            int j = 0;
+            for (size_t k = 0; k < nuni; k++) {
+                while (j + 1 < n && u.E[j + 1] <= Eu[k]) j++;
+                umap[q * nuni + k] = std::min(j, n - 2);
+            }
+        }
+    }
+    // log tables
+    std::vector<double> logtab(256), rinvtab(256), etab(64);
+    for (int j = 0; j < 256; j++) {
+        double c = 1.0 + (double)j / 256.0;
+        logtab[j] = ln_series(c);
+        rinvtab[j] = 1.0 / c;
+    }
+    for (int e = 0; e < 64; e++) etab[e] = (double)(e - 53) * LN2;
+
+    int nrep = acc_size > 0 ? (int)std::max<int64_t>(1, std::min<int64_t>(64, (1 << 20) / acc_size)) : 1;
+
+    Staging S;
+    size_t o_prob = S.put(probs);
+    size_t o_stype = S.put(s_type), o_sbc = S.put(s_bc), o_scoef = S.put(s_coef), o_sr2 = S.put(s_r2);
+    size_t o_cuniv = S.put(c_univ), o_coff = S.put(c_off), o_cnhs = S.put(c_nhs),
+           o_cfillk = S.put(c_fillk), o_cfill = S.put(c_fill);
+    size_t o_hssurf = S.put(hs_surf), o_hssense = S.put(hs_sense), o_hscoff = S.put(hs_coff),
+           o_hscand = S.put(hs_cand), o_uoff = S.put(u_off), o_ucells = S.put(u_cells);
+    size_t o_lx0 = S.put(l_x0), o_ly0 = S.put(l_y0), o_lp = S.put(l_pitch), o_lnx = S.put(l_nx),
+           o_lny = S.put(l_ny), o_luoff = S.put(l_uoff), o_luniv = S.put(l_univ);
+    size_t o_mG = S.put(m_G), o_mgoff = S.put(m_goff), o_mggoff = S.put(m_ggoff),
+           o_mfis = S.put(m_fissile);
+    size_t o_sigt = S.put(g_sigt), o_mfp = S.put(g_mfp), o_nusf = S.put(g_nusf), o_mu = S.put(g_mu),
+           o_mufl = S.put(g_mufl), o_mufr = S.put(g_mufr), o_ps = S.put(g_ps),
+           o_stot = S.put(g_stot), o_chicdf = S.put(g_chicdf), o_sigs = S.put(gg_sigs),
+           o_scdf = S.put(gg_scdf);
+    size_t o_Eu = S.put(Eu), o_umap = S.put(umap), o_nivoff = S.put(n_ivoff), o_niv = S.put(n_iv),
+           o_nA = S.put(n_A), o_nnu = S.put(n_nu);
+    size_t o_mcoff = S.put(mc_off), o_mcn = S.put(mc_n), o_mcnuc = S.put(mc_nuc),
+           o_mcfis = S.put(mc_fissile), o_mcdens = S.put(mc_dens);
+    size_t o_srccdf = S.put(src_cdf), o_logtab = S.put(logtab), o_rinv = S.put(rinvtab),
+           o_etab = S.put(etab);
+    size_t o_tf = S.put(t_filter), o_tnb = S.put(t_nbins), o_tne = S.put(t_ne), o_toff = S.put(t_off),
+           o_teoff = S.put(t_eoff), o_tned = S.put(t_nedges), o_tbat = S.put(t_batches),
+           o_tedges = S.put(t_edges);
+
+    if (dw.arena) {
+        cudaFree(dw.arena);
+        dw.arena = nullptr;
+    }
+    cudaError_t e = cudaMalloc(&dw.arena, S.buf.size());
+    if (e != cudaSuccess) return std::string("cudaMalloc(world): ") + cudaGetErrorString(e);
+    e = cudaMemcpyAsync(dw.arena, S.buf.data(), S.buf.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return std::string("upload(world): ") + cudaGetErrorString(e);
+    dw.bytes = S.buf.size();
+    char *b = (char *)dw.arena;
+    World &W = dw.W;
+    W.nprob = (int)probs.size();
+    W.prob = (const ProblemDev *)(b + o_prob);
+#define P_(field, T, off) W.field = (const T *)(b + off)
+    P_(s_type, int, o_stype); P_(s_bc, int, o_sbc); P_(s_coef, double, o_scoef); P_(s_r2, double, o_sr2);
+    P_(c_univ, int, o_cuniv); P_(c_off, int, o_coff); P_(c_nhs, int, o_cnhs);
+    P_(c_fillk, int, o_cfillk); P_(c_fill, int, o_cfill);
+    P_(hs_surf, int, o_hssurf); P_(hs_sense, int, o_hssense); P_(hs_coff, int, o_hscoff);
+    P_(hs_cand, int, o_hscand); P_(u_off, int, o_uoff); P_(u_cells, int, o_ucells);
+    P_(l_x0, double, o_lx0); P_(l_y0, double, o_ly0); P_(l_pitch, double, o_lp);
+    P_(l_nx, int, o_lnx); P_(l_ny, int, o_lny); P_(l_uoff, int, o_luoff); P_(l_univ, int, o_luniv);
+    P_(m_G, int, o_mG); P_(m_goff, int, o_mgoff); P_(m_ggoff, int, o_mggoff); P_(m_fissile, int, o_mfis);
+    P_(g_sigt, double, o_sigt); P_(g_mfp, double, o_mfp); P_(g_nusf, double, o_nusf);
+    P_(g_mu, double, o_mu); P_(g_mufl, double, o_mufl); P_(g_mufr, double, o_mufr);
+    P_(g_ps, double, o_ps); P_(g_stot, double, o_stot); P_(g_chicdf, double, o_chicdf);
+    P_(gg_sigs, double, o_sigs); P_(gg_scdf, double, o_scdf);
+    P_(Eu, double, o_Eu); P_(umap, int, o_umap); P_(n_ivoff, int, o_nivoff); P_(n_iv, double, o_niv);
+    P_(n_A, double, o_nA); P_(n_nu, double, o_nnu);
+    P_(mc_off, int, o_mcoff); P_(mc_n, int, o_mcn); P_(mc_nuc, int, o_mcnuc);
+    P_(mc_fissile, int, o_mcfis); P_(mc_dens, double, o_mcdens);
+    P_(src_cdf, double, o_srccdf); P_(logtab, double, o_logtab); P_(rinvtab, double, o_rinv);
+    P_(etab, double, o_etab);
+    P_(t_filter, int, o_tf); P_(t_nbins, int, o_tnb); P_(t_ne, int, o_tne); P_(t_off, int, o_toff);
+    P_(t_eoff, int, o_teoff); P_(t_nedges, int, o_tned); P_(t_batches, int, o_tbat);
+    P_(t_edges, double, o_tedges);
+#undef P_
+    W.nunion = (int)Eu.size();
+    W.nnuc = (int)nucs.size();
+    W.acc_size = (int)acc_size;
+    W.nrep = nrep;
+    dw.probs = probs;
+    dw.tally_first = tally_first;
+    dw.t_off = t_off;
+    dw.t_nbins = t_nbins;
+    dw.t_ne = t_ne;
+    dw.t_batches = t_batches;
+    dw.acc_size = (int)acc_size;
+    dw.nrep = nrep;
+    return "";
+}
+
+}  // namespace mcgb

@@ -1,0 +1,86 @@
+// kernels.h -- host-side launchers of the library's kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "world.h"
+
+namespace mcgb {
+
+// ---- event mode (one kernel per event type) -------------------------------
+void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const RunBufs &R, int gen,
+                   int64_t total, const int64_t *gen_base, const int *src_idx, int eigen, int block,
+                   cudaStream_t st);
+void launch_advance(const World &W, const Particles &P, const RunBufs &R, const int *list, int n,
+                    int *q_cross, int *q_coll, int block, cudaStream_t st);
+void launch_cross(const World &W, const Particles &P, const RunBufs &R, const int *q_cross,
+                  int n_bound, int *next, int block, cudaStream_t st);
+void launch_collide(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
+                    const int *q_coll, int n_bound, int *next, int block, cudaStream_t st);
+
+// ---- persistent event loop -------------------------------------------------
+struct PersistentArgs {
+    int gen;                 // cycle or generation index (stream ids gen 2^32 + local)
+    int64_t total;           // work items (slots) when gen_n is null
+    const int *gen_n;        // device total (bank size) when not null
+    const int64_t *gen_base; // [nprob + 1] first slot of each problem (device)
+    const int *src_idx;      // bank site of each slot, or null for the source definition
+    int eigen;
+    int *work;               // device work counter (zeroed before the launch)
+    int chunk;               // slots taken per pop
+};
+// births read Bsrc (the previous cycle's bank), new sites are appended to Bdst
+void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, const Bank &Bdst,
+                       const RunBufs &R, const PersistentArgs &a, int grid, int block,
+                       cudaStream_t st);
+int persistent_max_blocks_per_sm(int block);
+
+// ---- end of cycle / generation --------------------------------------------
+// Exclusive scan of n counts into out; *total = sum.  scratch holds one int per
+// 4096 inputs (scan_scratch_ints(n)).
+int64_t scan_scratch_ints(int64_t n);
+void scan_exclusive(const int *in, int *out, int64_t n, int *total, int *scratch, cudaStream_t st);
+void launch_perm(const Bank &B, const int *off, const int *M, int *perm, int grid, cudaStream_t st);
+void launch_resample(const int *perm, const int *M, int64_t N, double xi, int *src_idx,
+                     int *err, int64_t cap, cudaStream_t st);
+// sums over slots [0, total): k estimators into kout[2], counters into cnt[5]
+void launch_reduce_gen(const Particles &P, int64_t total, const int *total_dev, double *kout,
+                       unsigned long long *cnt, cudaStream_t st);
+void launch_tally_cycle(double *tacc, int acc_size, int nrep, double n, int active,
+                        double *tsum, double *tsum2, cudaStream_t st);
+void launch_acc_reduce(const double *tacc, int acc_size, int nrep, double *out, cudaStream_t st);
+void launch_gen_base(const int64_t *base, int nprob, const int *off, const int *M,
+                     int64_t *next_base, cudaStream_t st);
+void launch_copy_records(const Particles &P, int64_t n, int *ncoll, int *ncross, uint64_t *rng,
+                         int *nfis, int *fate, int *g, cudaStream_t st);
+
+// ---- building blocks for checks ---------------------------------------------
+void launch_rng_states(uint64_t seed, uint64_t first_id, int64_t n, int draws, uint64_t *out,
+                       cudaStream_t st);
+void launch_log(const World &W, int64_t n, const double *xi, double *out, cudaStream_t st);
+void launch_probe(const World &W, int root_univ, int64_t n, const double *pos, const double *dir,
+                  int *path, double *dist, int *kind, cudaStream_t st);
+void launch_ce_lookup(const World &W, int mat, int64_t n, const double *E, double *out,
+                      cudaStream_t st);
+
+// ---- derivatives (likelihood-ratio replay) --------------------------------
+struct ReplayArgs {
+    int gen;
+    int64_t n;               // slots of this generation
+    const int *site;         // bank site per slot for gen > 0 (sorted bank copy index), or null
+    const Bank *bank;        // start states of this generation (gen > 0)
+    const double *own;       // per-slot detector tally by group, this generation
+    const double *w;         // weights [G]
+    const double *sub_next;  // subtree totals of the next generation's slots (or null)
+    const int *off;          // first child slot of each slot in the next generation
+    const int *nfis;         // children per slot
+    int det_cell;
+    int G, nmat;
+    double *grad;            // [nmat*G*(G+2)] accumulators
+};
+void launch_subtree(const double *own, const double *w, int G, int64_t n, const double *sub_next,
+                    const int *off, const int *nfis, double *sub, cudaStream_t st);
+void launch_replay(const World &W, const ReplayArgs &a, int block, cudaStream_t st);
+
+}  // namespace mcgb

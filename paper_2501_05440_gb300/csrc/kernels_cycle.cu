@@ -1,0 +1,267 @@
+// kernels_cycle.cu -- end-of-cycle work: put the fission bank in (parent,
+// child) order, resample the next cycle's sources, reduce k estimators,
+// counters and tallies.
+//
+// Bank order without a general sort: every history counts the sites it banks
+// (nfis), so an exclusive scan of those counts gives each parent's first
+// position; site b goes to off[parent] + child.  The order is the unique
+// (parent, child) order whatever order the sites were appended in.
+#include "kernels.h"
+#include "transport.cuh"
+
+namespace mcgb {
+
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+int64_t scan_scratch_ints(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+// Exclusive block scan of one value per thread; returns the block total in *tot.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *tot)
+{
+    __shared__ int warp_sums[SCAN_BLOCK / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int before = wid ? warp_sums[wid - 1] : 0;
+    *tot = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_tile(const int *in, int *out, int64_t n,
+                                                          int *tile_sums)
+{
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int tot;
+    int ex = block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        if (base + k < n) out[base + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the tile sums in place; grand total to *total.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_sums(int *tile_sums, int ntiles, int *total)
+{
+    int carry = 0;
+    for (int b = 0; b < ntiles; b += SCAN_BLOCK) {
+        int i = b + threadIdx.x;
+        int v = i < ntiles ? tile_sums[i] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, &tot);
+        if (i < ntiles) tile_sums[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int *out, int64_t n, const int *tile_sums)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tile_sums[i / SCAN_TILE];
+}
+
+void scan_exclusive(const int *in, int *out, int64_t n, int *total, int *scratch, cudaStream_t st)
+{
+    int ntiles = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+    if (ntiles == 0) {
+        cudaMemsetAsync(total, 0, sizeof(int), st);
+        return;
+    }
+    k_scan_tile<<<ntiles, SCAN_BLOCK, 0, st>>>(in, out, n, scratch);
+    k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(scratch, ntiles, total);
+    if (ntiles > 1) k_scan_add<<<(int)((n + 255) / 256), 256, 0, st>>>(out, n, scratch);
+}
+
+// perm[off[parent] + child] = b for every appended site b < M.  After a bank
+// overflow (M > capacity, reported to the host) only stored sites are placed.
+__global__ void k_perm(const int *parent, const int *child, const int *off, const int *M, int *perm,
+                       int64_t cap)
+{
+    int64_t m = *M < cap ? (int64_t)*M : cap;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < m;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int64_t dst = (int64_t)off[parent[b]] + child[b];
+        if (dst < cap) perm[dst] = (int)b;
+    }
+}
+
+void launch_perm(const Bank &B, const int *off, const int *M, int *perm, int grid, cudaStream_t st)
+{
+    k_perm<<<grid, 256, 0, st>>>(B.parent, B.child, off, M, perm, B.cap);
+}
+
+// Systematic resampling of M sorted sites to N sources:
+// source j <- site floor((j + xi) M / N) (clamped to M - 1).
+__global__ void k_resample(const int *perm, const int *Mp, int64_t N, double xi, int *src_idx,
+                           int *err, int64_t cap)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    int64_t M = *Mp;
+    if (M > cap) {   // overflow: reported to the host, keep indices in bounds
+        atomicOr(err, ERR_BANK_OVERFLOW);
+        M = cap;
+    }
+    if (M <= 0) {
+        if (j == 0) atomicOr(err, ERR_SOURCE);
+        src_idx[j] = 0;
+        return;
+    }
+    double t = ((double)j + xi) * (double)M / (double)N;
+    int64_t idx = (int64_t)t;
+    if (idx >= M) idx = M - 1;
+    src_idx[j] = perm[idx];
+}
+
+void launch_resample(const int *perm, const int *M, int64_t N, double xi, int *src_idx, int *err,
+                     int64_t cap, cudaStream_t st)
+{
+    k_resample<<<(int)((N + 255) / 256), 256, 0, st>>>(perm, M, N, xi, src_idx, err, cap);
+}
+
+// Sums of per-history k estimators and event counters over the generation's slots.
+__global__ void k_reduce_gen(Particles P, int64_t total, const int *total_dev, double *kout,
+                             unsigned long long *cnt)
+{
+    int64_t n = total_dev ? (int64_t)*total_dev : total;
+    double kt = 0.0, kc = 0.0;
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        kt += P.kt[i];
+        kc += P.kc[i];
+        c[0] += P.ncoll[i];
+        c[1] += P.ncross[i];
+        int f = P.fate[i];
+        c[2] += f == FATE_LEAKED;
+        c[3] += f == FATE_LOST;
+        c[4] += f == FATE_CAPPED;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kt += __shfl_down_sync(0xffffffffu, kt, o);
+        kc += __shfl_down_sync(0xffffffffu, kc, o);
+#pragma unroll
+        for (int q = 0; q < 5; q++) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(kout, kt);
+        atomicAdd(kout + 1, kc);
+#pragma unroll
+        for (int q = 0; q < 5; q++)
+            if (c[q]) atomicAdd(cnt + q, c[q]);
+    }
+}
+
+void launch_reduce_gen(const Particles &P, int64_t total, const int *total_dev, double *kout,
+                       unsigned long long *cnt, cudaStream_t st)
+{
+    k_reduce_gen<<<304, 256, 0, st>>>(P, total, total_dev, kout, cnt);
+}
+
+// Eigenvalue cycle end: batch value v = (sum of replicas) / N; keep sum and
+// sum of squares over active cycles; clear the accumulators.
+__global__ void k_tally_cycle(double *tacc, int acc_size, int nrep, double n, int active,
+                              double *tsum, double *tsum2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= acc_size) return;
+    double v = 0.0;
+    for (int r = 0; r < nrep; r++) {
+        v += tacc[(int64_t)r * acc_size + i];
+        tacc[(int64_t)r * acc_size + i] = 0.0;
+    }
+    v = v / n;
+    if (active) {
+        tsum[i] += v;
+        tsum2[i] += v * v;
+    }
+}
+
+void launch_tally_cycle(double *tacc, int acc_size, int nrep, double n, int active,
+                        double *tsum, double *tsum2, cudaStream_t st)
+{
+    k_tally_cycle<<<(acc_size + 255) / 256, 256, 0, st>>>(tacc, acc_size, nrep, n, active, tsum,
+                                                          tsum2);
+}
+
+__global__ void k_acc_reduce(const double *tacc, int acc_size, int nrep, double *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= acc_size) return;
+    double v = 0.0;
+    for (int r = 0; r < nrep; r++) v += tacc[(int64_t)r * acc_size + i];
+    out[i] = v;
+}
+
+void launch_acc_reduce(const double *tacc, int acc_size, int nrep, double *out, cudaStream_t st)
+{
+    k_acc_reduce<<<(acc_size + 255) / 256, 256, 0, st>>>(tacc, acc_size, nrep, out);
+}
+
+// First slot of each problem in the next generation: off[base[p]] (M past the end).
+__global__ void k_gen_base(const int64_t *base, int nprob, const int *off, const int *M,
+                           int64_t *next)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > nprob) return;
+    int64_t total = base[nprob];
+    next[p] = base[p] < total ? (int64_t)off[base[p]] : (int64_t)*M;
+}
+
+void launch_gen_base(const int64_t *base, int nprob, const int *off, const int *M,
+                     int64_t *next_base, cudaStream_t st)
+{
+    k_gen_base<<<(nprob + 1 + 127) / 128, 128, 0, st>>>(base, nprob, off, M, next_base);
+}
+
+__global__ void k_copy_records(Particles P, int64_t n, int *ncoll, int *ncross, uint64_t *rng,
+                               int *nfis, int *fate, int *g)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ncoll[i] = P.ncoll[i];
+    ncross[i] = P.ncross[i];
+    rng[i] = P.s[i];
+    nfis[i] = P.nfis[i];
+    fate[i] = P.fate[i];
+    g[i] = P.g[i];
+}
+
+void launch_copy_records(const Particles &P, int64_t n, int *ncoll, int *ncross, uint64_t *rng,
+                         int *nfis, int *fate, int *g, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_copy_records<<<(int)((n + 255) / 256), 256, 0, st>>>(P, n, ncoll, ncross, rng, nfis, fate, g);
+}
+
+}  // namespace mcgb

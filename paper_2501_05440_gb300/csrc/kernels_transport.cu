@@ -1,0 +1,259 @@
+// kernels_transport.cu -- transport kernels.
+//
+// Event mode (the field-standard event-based design the paper's Sec. 2 says
+// MC/DC is moving to): one kernel per event type over compacted index queues,
+// so every warp runs one kind of event; the queues are built by warp-ballot
+// compaction with one atomic per warp.
+//
+// Persistent mode: one grid-resident kernel per cycle; each thread keeps a
+// particle in registers and runs its events, refilling from a device work
+// counter when it dies (no host round trip, no per-event launches).
+#include "kernels.h"
+#include "steps.cuh"
+
+namespace mcgb {
+
+__device__ __forceinline__ void load_ps(const Particles &P, int i, PS &p)
+{
+    p.x = P.x[i]; p.y = P.y[i]; p.z = P.z[i];
+    p.u = P.u[i]; p.v = P.v[i]; p.w = P.w[i];
+    p.E = P.E[i];
+    p.s = P.s[i];
+    p.g = P.g[i]; p.cell = P.cell[i]; p.ix = P.ix[i]; p.iy = P.iy[i]; p.ucell = P.ucell[i];
+    p.mat = P.mat[i]; p.prob = P.prob[i]; p.root = P.root[i];
+    p.nfis = P.nfis[i]; p.ncoll = P.ncoll[i]; p.ncross = P.ncross[i];
+    p.fate = P.fate[i];
+}
+
+__device__ __forceinline__ void store_ps(const Particles &P, int i, const PS &p)
+{
+    P.x[i] = p.x; P.y[i] = p.y; P.z[i] = p.z;
+    P.u[i] = p.u; P.v[i] = p.v; P.w[i] = p.w;
+    P.E[i] = p.E;
+    P.s[i] = p.s;
+    P.g[i] = p.g; P.cell[i] = p.cell; P.ix[i] = p.ix; P.iy[i] = p.iy; P.ucell[i] = p.ucell;
+    P.mat[i] = p.mat; P.prob[i] = p.prob; P.root[i] = p.root;
+    P.nfis[i] = p.nfis; P.ncoll[i] = p.ncoll; P.ncross[i] = p.ncross;
+    P.fate[i] = (signed char)p.fate;
+}
+
+__device__ __forceinline__ int find_problem(const int64_t *base, int nprob, int64_t j)
+{
+    int lo = 0, hi = nprob;   // base[lo] <= j < base[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (base[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int accum_replica(const World &W)
+{
+    return (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % (unsigned)W.nrep);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_source(World W, Particles P, Bank Bsrc, RunBufs R, int gen, int64_t total,
+                         const int64_t *gen_base, const int *src_idx, int eigen)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= total) return;
+    int prob = find_problem(gen_base, W.nprob, j);
+    const ProblemDev &Pd = W.prob[prob];
+    PS p;
+    bool ok = init_particle(W, Pd, Bsrc, p, prob, j - gen_base[prob], gen,
+                            src_idx ? src_idx[j] : -1, eigen != 0);
+    if (!ok) {
+        atomicOr(R.err, ERR_SOURCE);
+        p.fate = FATE_LOST;
+        p.cell = 0;
+        p.mat = 0;
+    }
+    store_ps(P, (int)j, p);
+    P.kt[j] = 0.0;
+    P.kc[j] = 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_advance(World W, Particles P, RunBufs R, const int *list,
+                                                 int n, int *q_cross, int *q_coll)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = -1, ev = EV_DEAD;
+    if (t < n) {
+        i = list ? list[t] : t;
+        PS p;
+        load_ps(P, i, p);
+        if (p.fate == FATE_ALIVE) {
+            const ProblemDev &Pd = W.prob[p.prob];
+            int kind, which, uk = 0;
+            double kt = P.kt[i];
+            ev = step_advance(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
+            store_ps(P, i, p);
+            P.kt[i] = kt;
+            P.bkind[i] = (signed char)kind;
+            P.bwhich[i] = which;
+            P.uk[i] = uk;
+        }
+    }
+    enqueue(ev == EV_CROSS, i, q_cross, R.q_n + 0);
+    enqueue(ev == EV_COLLIDE, i, q_coll, R.q_n + 1);
+}
+
+__global__ void __launch_bounds__(256) k_cross(World W, Particles P, RunBufs R, const int *q_cross,
+                                               int *next)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = R.q_n[0];
+    int i = -1;
+    bool alive = false;
+    if (t < n) {
+        i = q_cross[t];
+        PS p;
+        load_ps(P, i, p);
+        alive = step_cross(W, p, P.bkind[i], P.bwhich[i]) == EV_ADVANCE;
+        store_ps(P, i, p);
+    }
+    enqueue(alive, i, next, R.q_n + 2);
+}
+
+__global__ void __launch_bounds__(256) k_collide(World W, Particles P, Bank Bdst, RunBufs R,
+                                                 const int *q_coll, int *next)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = R.q_n[1];
+    int i = -1;
+    bool alive = false;
+    if (t < n) {
+        i = q_coll[t];
+        PS p;
+        load_ps(P, i, p);
+        const ProblemDev &Pd = W.prob[p.prob];
+        double kc = P.kc[i];
+        alive = step_collide(W, Pd, p, i, Bdst, R, P.uk[i], kc) == EV_ADVANCE;
+        store_ps(P, i, p);
+        P.kc[i] = kc;
+    }
+    enqueue(alive, i, next, R.q_n + 2);
+}
+
+static inline int nblocks(int64_t n, int block) { return (int)((n + block - 1) / block); }
+
+void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const RunBufs &R, int gen,
+                   int64_t total, const int64_t *gen_base, const int *src_idx, int eigen, int block,
+                   cudaStream_t st)
+{
+    if (total <= 0) return;
+    k_source<<<nblocks(total, block), block, 0, st>>>(W, P, Bsrc, R, gen, total, gen_base, src_idx,
+                                                      eigen);
+}
+
+void launch_advance(const World &W, const Particles &P, const RunBufs &R, const int *list, int n,
+                    int *q_cross, int *q_coll, int block, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_advance<<<nblocks(n, block), block, 0, st>>>(W, P, R, list, n, q_cross, q_coll);
+}
+
+void launch_cross(const World &W, const Particles &P, const RunBufs &R, const int *q_cross,
+                  int n_bound, int *next, int block, cudaStream_t st)
+{
+    if (n_bound <= 0) return;
+    k_cross<<<nblocks(n_bound, block), block, 0, st>>>(W, P, R, q_cross, next);
+}
+
+void launch_collide(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
+                    const int *q_coll, int n_bound, int *next, int block, cudaStream_t st)
+{
+    if (n_bound <= 0) return;
+    k_collide<<<nblocks(n_bound, block), block, 0, st>>>(W, P, Bdst, R, q_coll, next);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent event loop.  All lanes of a warp stay in the loop until every
+// lane has run out of work, so the warp-wide ballot/shuffle calls are always
+// made by the full warp.
+__device__ __forceinline__ void write_dead(const Particles &P, int slot, const PS &p, double kt,
+                                           double kc)
+{
+    P.nfis[slot] = p.nfis;
+    P.ncoll[slot] = p.ncoll;
+    P.ncross[slot] = p.ncross;
+    P.fate[slot] = (signed char)p.fate;
+    P.s[slot] = p.s;
+    P.g[slot] = p.g;
+    P.kt[slot] = kt;
+    P.kc[slot] = kc;
+}
+
+__global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank Bsrc, Bank Bdst,
+                                                    RunBufs R, PersistentArgs a)
+{
+    const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
+    const int lane = threadIdx.x & 31;
+    const int rep = accum_replica(W);
+    PS p;
+    p.fate = FATE_LOST;
+    int slot = -1;
+    bool alive = false, done = false;
+    double kt = 0.0, kc = 0.0;
+    const ProblemDev *Pd = W.prob;
+    for (;;) {
+        bool need = !alive && !done;
+        unsigned m = __ballot_sync(0xffffffffu, need);
+        if (m) {
+            int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(a.work, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                int64_t j = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+                if (j >= total) {
+                    done = true;
+                } else {
+                    slot = (int)j;
+                    int prob = find_problem(a.gen_base, W.nprob, j);
+                    Pd = W.prob + prob;
+                    kt = 0.0;
+                    kc = 0.0;
+                    bool ok = init_particle(W, *Pd, Bsrc, p, prob, j - a.gen_base[prob], a.gen,
+                                            a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                    if (ok) {
+                        alive = true;
+                    } else {
+                        atomicOr(R.err, ERR_SOURCE);
+                        p.fate = FATE_LOST;
+                        write_dead(P, slot, p, kt, kc);
+                    }
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+        if (alive) {
+            int kind, which, uk = 0;
+            int ev = step_advance(W, *Pd, p, slot, R, rep, kind, which, uk, kt);
+            if (ev == EV_CROSS) ev = step_cross(W, p, kind, which);
+            else if (ev == EV_COLLIDE) ev = step_collide(W, *Pd, p, slot, Bdst, R, uk, kc);
+            if (ev == EV_DEAD) {
+                alive = false;
+                write_dead(P, slot, p, kt, kc);
+            }
+        }
+    }
+}
+
+void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, const Bank &Bdst,
+                       const RunBufs &R, const PersistentArgs &a, int grid, int block,
+                       cudaStream_t st)
+{
+    k_persistent<<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
+}
+
+int persistent_max_blocks_per_sm(int block)
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent, block, 0);
+    return n;
+}
+
+}  // namespace mcgb

@@ -1,0 +1,212 @@
+// steps.cuh -- the three events of a particle (Sec. 2: a segment of transport
+// is a flight to the next event, then a surface crossing or a collision),
+// written once and used by both the one-kernel-per-event path and the
+// persistent event loop.
+#pragma once
+#include "transport.cuh"
+
+namespace mcgb {
+
+enum { EV_ADVANCE = 0, EV_CROSS = 1, EV_COLLIDE = 2, EV_DEAD = 3 };
+
+__device__ __forceinline__ int tally_batch(const ProblemDev &P, const PS &p)
+{
+    return P.batches > 1 ? (int)(((int64_t)p.root * P.batches) / P.n) : 0;
+}
+
+// Flight: distance to collision d_c = -ln(xi) / Sigma_t (one draw, always taken),
+// distance to the nearest boundary d_s, move by min(d_c, d_s) (ties cross),
+// score the track length.  Returns EV_CROSS, EV_COLLIDE or EV_DEAD (lost or cut).
+// REPLAY: same draws and moves, no tallies; the flight length is returned in d.
+template <bool REPLAY = false>
+__device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P, PS &p, int slot,
+                                            const RunBufs &R, int rep, int &kind, int &which,
+                                            int &uk, double &kt, double *d_out = nullptr)
+{
+    if (p.ncoll + p.ncross >= MAX_EVENTS) {
+        p.fate = FATE_CAPPED;
+        return EV_DEAD;
+    }
+    double sigt, mfp, nusf;
+    if (P.ce) {
+        uk = union_index(W, p.E);
+        CEXS x;
+        ce_xs(W, p.mat, uk, p.E, x);
+        sigt = x.sigt;
+        nusf = x.nusf;
+        mfp = sigt > 0.0 ? 1.0 / sigt : MCGB_INF;
+    } else {
+        int go = __ldg(W.m_goff + p.mat) + p.g;
+        sigt = __ldg(W.g_sigt + go);
+        nusf = __ldg(W.g_nusf + go);
+        mfp = __ldg(W.g_mfp + go);
+    }
+    uint64_t n = draw_n(p.s);
+    double dc = sigt > 0.0 ? -log_n(W, n) * mfp : MCGB_INF;
+    double ds = boundary(W, p, kind, which);
+    if (dc == MCGB_INF && ds == MCGB_INF) {
+        p.fate = FATE_LOST;
+        return EV_DEAD;
+    }
+    bool coll = dc < ds;
+    double d = coll ? dc : ds;
+    p.x = p.x + d * p.u;
+    p.y = p.y + d * p.v;
+    p.z = p.z + d * p.w;
+    if (REPLAY) {
+        *d_out = d;
+    } else {
+        score(W, P, p, d, tally_batch(P, p), R.tacc, rep);
+        kt = kt + d * nusf;
+        if (R.own && (p.ucell >= 0 ? p.ucell : p.cell) == R.own_cell)
+            R.own[(int64_t)slot * R.own_G + p.g] += d;
+    }
+    return coll ? EV_COLLIDE : EV_CROSS;
+}
+
+__device__ __forceinline__ int step_cross(const World &W, PS &p, int kind, int which)
+{
+    p.ncross++;
+    int r = cross(W, p, kind, which);
+    if (r == 1) {
+        p.fate = FATE_LEAKED;
+        return EV_DEAD;
+    }
+    if (r < 0) {
+        p.fate = FATE_LOST;
+        return EV_DEAD;
+    }
+    return EV_ADVANCE;
+}
+
+// Collision (analog, weight 1).  Multigroup: fission sites floor(mu) + [xi1 <=
+// frac mu], mu = nuSigma_f/Sigma_t (no division by k); scatter when xi2 <=
+// Sigma_s,tot/Sigma_t with outgoing group the first g' where xi3 <= cdf(g');
+// isotropic direction; otherwise absorbed.  Continuous energy: nuclide by
+// xi Sigma_t against the running sum, fission sites as above with nu sigma_f /
+// sigma_t of that nuclide, scatter (elastic, target at rest) when
+// xi sigma_t <= sigma_s.
+// REPLAY (multigroup only): same draws, no bank; *nf_out = sites banked.
+template <bool REPLAY = false>
+__device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P, PS &p, int slot,
+                                            const Bank &B, const RunBufs &R, int uk, double &kc,
+                                            int *nf_out = nullptr)
+{
+    p.ncoll++;
+    if (!P.ce) {
+        int go = __ldg(W.m_goff + p.mat);
+        int G = __ldg(W.m_G + p.mat);
+        int g = p.g;
+        kc = kc + __ldg(W.g_mu + go + g);
+        double xi = draw(p.s);
+        int nf = (int)__ldg(W.g_mufl + go + g) + (xi <= __ldg(W.g_mufr + go + g) ? 1 : 0);
+        if (REPLAY) {
+            *nf_out = nf;
+            p.nfis += nf;
+        } else {
+            for (int k = 0; k < nf; k++) {
+                bank_push(B, R.bank_n, R.err, p, slot);
+                p.nfis++;
+            }
+        }
+        xi = draw(p.s);
+        if (xi <= __ldg(W.g_ps + go + g)) {
+            xi = draw(p.s);
+            p.g = sample_cdf(W.gg_scdf + __ldg(W.m_ggoff + p.mat) + g * G, G, xi);
+            iso_dir(p.s, p.u, p.v, p.w);
+        } else {
+            p.fate = FATE_ABSORBED;
+            return EV_DEAD;
+        }
+    } else {
+        CEXS x;
+        ce_xs(W, p.mat, uk, p.E, x);
+        kc = kc + x.nusf / x.sigt;
+        int off = __ldg(W.mc_off + p.mat), n = __ldg(W.mc_n + p.mat);
+        double target = draw(p.s) * x.sigt;
+        double cum = 0.0;
+        int sel = n - 1;
+        bool found = false;
+#pragma unroll
+        for (int q = 0; q < MAX_NUC; q++) {
+            if (q < n && !found) {
+                cum = cum + __ldg(W.mc_dens + off + q) * x.st[q];
+                if (target <= cum) {
+                    sel = q;
+                    found = true;
+                }
+            }
+        }
+        double st = 0.0, ss = 0.0, sf = 0.0;
+#pragma unroll
+        for (int q = 0; q < MAX_NUC; q++)
+            if (q == sel) {
+                st = x.st[q];
+                ss = x.ss[q];
+                sf = x.sf[q];
+            }
+        int nuc = __ldg(W.mc_nuc + off + sel);
+        double mu = __ldg(W.n_nu + nuc) * sf / st;
+        double fl = floor(mu);
+        double xi = draw(p.s);
+        int nf = (int)fl + (xi <= mu - fl ? 1 : 0);
+        for (int k = 0; k < nf; k++) {
+            bank_push(B, R.bank_n, R.err, p, slot);
+            p.nfis++;
+        }
+        xi = draw(p.s);
+        if (xi * st <= ss) {
+            p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);
+        } else {
+            p.fate = FATE_ABSORBED;
+            return EV_DEAD;
+        }
+    }
+    if (P.max_coll && p.ncoll >= P.max_coll) {
+        p.fate = FATE_CUT;
+        return EV_DEAD;
+    }
+    return EV_ADVANCE;
+}
+
+// New particle for slot `slot` (local index `local` of its problem) of
+// generation/cycle `gen`: stream gen 2^32 + local; from the source definition
+// (site < 0) or born at bank site `site`.
+__device__ __forceinline__ bool init_particle(const World &W, const ProblemDev &P, const Bank &B,
+                                              PS &p, int prob, int64_t local, int gen, int site,
+                                              bool eigen)
+{
+    p.s = rng_stream(P.seed, ((uint64_t)gen << 32) + (uint64_t)local);
+    p.prob = prob;
+    p.nfis = 0;
+    p.ncoll = 0;
+    p.ncross = 0;
+    p.fate = FATE_ALIVE;
+    p.g = 0;
+    p.E = 0.0;
+    p.ix = -1;
+    p.iy = -1;
+    p.ucell = -1;
+    if (site < 0) {
+        p.root = (int)local;
+        return sample_source(W, P, p);
+    }
+    p.root = eigen ? (int)local : B.root[site];
+    birth_from_site(W, P, B, site, p);
+    return true;
+}
+
+// Warp-aggregated append of `val` to queue when pred holds (all lanes call).
+__device__ __forceinline__ void enqueue(bool pred, int val, int *queue, int *count)
+{
+    unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (m == 0) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) queue[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
+}  // namespace mcgb

@@ -1,0 +1,687 @@
+// transport.cuh -- device functions of event-based Monte Carlo transport.
+//
+// One particle's steps (Sec. 2 of the paper lists them as sampling a
+// direction, moving the particle, and so on; Sec. 1 names the physics):
+//   sample a distance to collision, find the nearest CSG boundary, move and
+//   score the track length, then cross the boundary or collide.
+// The paper gives no formulas.  The choices made here (random-number
+// generator, draw order, root selection, tie-breaks, estimators) are stated
+// beside each function; every floating-point expression is evaluated in the
+// order written, without contraction (the library is built with -fmad=false),
+// so that each history is bit-reproducible on any conforming IEEE machine.
+#pragma once
+#include <cstdint>
+
+#include "world.h"
+
+namespace mcgb {
+
+#define MCGB_INF __longlong_as_double(0x7FF0000000000000LL)
+
+// ---------------------------------------------------------------------------
+// Random numbers (Sec. 1: replicable on CPU and GPU).  63-bit LCG
+// s' = (g s + 1) mod 2^63, g = 2806196910506780709; stream i starts at
+// skip(seed, 152917 i) (Brown's skip-ahead); a draw advances the state and
+// returns xi = n 2^-53 with n = (s >> 10) + 1 in [1, 2^53].
+constexpr uint64_t LCG_G = 2806196910506780709ULL;
+constexpr uint64_t LCG_MASK = 0x7FFFFFFFFFFFFFFFULL;
+constexpr uint64_t LCG_STRIDE = 152917ULL;
+
+__host__ __device__ __forceinline__ uint64_t rng_next(uint64_t s)
+{
+    return (LCG_G * s + 1ULL) & LCG_MASK;
+}
+
+__host__ __device__ __forceinline__ uint64_t rng_skip(uint64_t s, uint64_t n)
+{
+    uint64_t G = 1, C = 0, h = LCG_G, f = 1;
+    n &= LCG_MASK;
+    while (n) {
+        if (n & 1) {
+            G = G * h;
+            C = C * h + f;
+        }
+        f = f * (h + 1);
+        h = h * h;
+        n >>= 1;
+    }
+    return (G * (s & LCG_MASK) + C) & LCG_MASK;
+}
+
+__host__ __device__ __forceinline__ uint64_t rng_stream(uint64_t seed, uint64_t id)
+{
+    return rng_skip(seed, id * LCG_STRIDE);
+}
+
+__device__ __forceinline__ uint64_t draw_n(uint64_t &s)
+{
+    s = rng_next(s);
+    return (s >> 10) + 1;
+}
+
+// n 2^-53 for 1 <= n <= 2^53, built from the bits (exact; no FP64 instruction).
+__device__ __forceinline__ double n_to_xi(uint64_t n)
+{
+    int lz = __clzll((long long)n);
+    uint64_t frac = ((n << lz) << 1) >> 12;
+    uint64_t bits = ((uint64_t)(1023 - 53 + 63 - lz) << 52) | frac;
+    return __longlong_as_double((long long)bits);
+}
+
+// 2 xi - 1 = (2n - 2^53) 2^-53 exactly (no FP64 instruction).
+__device__ __forceinline__ double n_to_sym(uint64_t n)
+{
+    long long k = (long long)(2 * n) - (1LL << 53);
+    if (k == 0) return 0.0;
+    uint64_t a = k < 0 ? (uint64_t)(-k) : (uint64_t)k;
+    int lz = __clzll((long long)a);
+    uint64_t frac = ((a << lz) << 1) >> 12;
+    uint64_t bits = ((uint64_t)(1023 - 53 + 63 - lz) << 52) | frac;
+    if (k < 0) bits |= 0x8000000000000000ULL;
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double draw(uint64_t &s) { return n_to_xi(draw_n(s)); }
+__device__ __forceinline__ double draw_sym(uint64_t &s) { return n_to_sym(draw_n(s)); }
+
+// ---------------------------------------------------------------------------
+// ln xi for xi = n 2^-53: table-driven (Tang, ACM TOMS 1990).  n = 2^e m,
+// m in [1,2); c = 1 + j/256 from the top 8 fraction bits; r = (m - c)(1/c);
+// ln xi = (e - 53) ln 2 + ln c + r(1 + r(-1/2 + r(1/3 + r(-1/4 + r(1/5 - r/6))))).
+// Tables (built on the host): ln c by the series 2 atanh((c-1)/(c+1)), 1/c,
+// and (e - 53) ln 2 rounded once.
+__device__ __forceinline__ double log_n(const World &W, uint64_t n)
+{
+    int lz = __clzll((long long)n);
+    int e = 63 - lz;
+    uint64_t frac = ((n << lz) << 1) >> 12;
+    double m = __longlong_as_double((long long)(0x3FF0000000000000ULL | frac));
+    int j = (int)(frac >> 44);
+    double c = __longlong_as_double((long long)(0x3FF0000000000000ULL | ((uint64_t)j << 44)));
+    double r = (m - c) * __ldg(W.rinvtab + j);
+    double q = -1.0 / 6.0;
+    q = q * r + 1.0 / 5.0;
+    q = q * r + -0.25;
+    q = q * r + 1.0 / 3.0;
+    q = q * r + -0.5;
+    q = q * r + 1.0;
+    double p = q * r;
+    return __ldg(W.etab + e) + (__ldg(W.logtab + j) + p);
+}
+
+// ---------------------------------------------------------------------------
+// Isotropic direction by Marsaglia's disk rejection (no trigonometry).
+__device__ __forceinline__ void iso_dir(uint64_t &s, double &u, double &v, double &w)
+{
+    for (int k = 0; k < 64; k++) {
+        double a = draw_sym(s);
+        double b = draw_sym(s);
+        double S = a * a + b * b;
+        if (S < 1.0) {
+            double t = 2.0 * sqrt(1.0 - S);
+            u = a * t;
+            v = b * t;
+            w = 1.0 - 2.0 * S;
+            return;
+        }
+    }
+    u = 0.0;
+    v = 0.0;
+    w = 1.0;
+}
+
+// Azimuth as (cos, sin) of the doubled angle of a point uniform in the unit disk.
+__device__ __forceinline__ void azimuth(uint64_t &s, double &cphi, double &sphi)
+{
+    for (int k = 0; k < 64; k++) {
+        double a = draw_sym(s);
+        double b = draw_sym(s);
+        double r2 = a * a + b * b;
+        if (r2 <= 1.0 && r2 > 0.0) {
+            cphi = (a * a - b * b) / r2;
+            sphi = 2.0 * a * b / r2;
+            return;
+        }
+    }
+    cphi = 1.0;
+    sphi = 0.0;
+}
+
+// Rotate (u,v,w) by polar cosine mu with a sampled azimuth (polar axis z, or x near |w| = 1).
+__device__ __forceinline__ void rotate(double mu, uint64_t &s, double &u, double &v, double &w)
+{
+    double cphi, sphi;
+    azimuth(s, cphi, sphi);
+    double st2 = 1.0 - mu * mu;
+    double st = sqrt(st2 > 0.0 ? st2 : 0.0);
+    double u0 = u, v0 = v, w0 = w;
+    double ww = 1.0 - w0 * w0;
+    if (ww > 1.0e-10) {
+        double q = sqrt(ww);
+        double f = st / q;
+        u = mu * u0 + f * (u0 * w0 * cphi - v0 * sphi);
+        v = mu * v0 + f * (v0 * w0 * cphi + u0 * sphi);
+        w = mu * w0 - st * q * cphi;
+    } else {
+        double uu = 1.0 - u0 * u0;
+        double q = sqrt(uu);
+        double f = st / q;
+        v = mu * v0 + f * (v0 * u0 * cphi - w0 * sphi);
+        w = mu * w0 + f * (w0 * u0 * cphi + v0 * sphi);
+        u = mu * u0 - st * q * cphi;
+    }
+}
+
+// Elastic scattering off a target at rest; energy floored at E_MIN.
+__device__ __forceinline__ double elastic(double E, double A, uint64_t &s, double &u, double &v,
+                                          double &w)
+{
+    double mucm = draw_sym(s);
+    double q = A * A + 2.0 * A * mucm + 1.0;
+    double Ep = E * q / ((A + 1.0) * (A + 1.0));
+    double mul = (1.0 + A * mucm) / sqrt(q);
+    if (mul > 1.0) mul = 1.0;
+    if (mul < -1.0) mul = -1.0;
+    rotate(mul, s, u, v, w);
+    return Ep < E_MIN ? E_MIN : Ep;
+}
+
+// Maxwellian fission spectrum (T = 1.33 MeV): E = -T (ln xi1 + ln xi2 a^2/(a^2+b^2)),
+// (a, b) uniform in the unit disk; resampled above 20 MeV; floored at E_MIN.
+__device__ __forceinline__ double maxwell(const World &W, uint64_t &s)
+{
+    for (int k = 0; k < 64; k++) {
+        double L1 = log_n(W, draw_n(s));
+        double L2 = log_n(W, draw_n(s));
+        double a = 1.0, r2 = 1.0;
+        for (int t = 0; t < 64; t++) {
+            double aa = draw_sym(s);
+            double bb = draw_sym(s);
+            double rr = aa * aa + bb * bb;
+            if (rr <= 1.0 && rr > 0.0) {
+                a = aa;
+                r2 = rr;
+                break;
+            }
+        }
+        double c2 = a * a / r2;
+        double E = -1.33e6 * (L1 + L2 * c2);
+        if (E <= E_MAX) return E < E_MIN ? E_MIN : E;
+    }
+    return E_MAX;
+}
+
+// First k with xi <= cdf[k] (cdf ends with exactly 1).
+__device__ __forceinline__ int sample_cdf(const double *cdf, int n, double xi)
+{
+    for (int k = 0; k < n; k++)
+        if (xi <= __ldg(cdf + k)) return k;
+    return n - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Particle held in registers
+struct PS {
+    double x, y, z, u, v, w, E;
+    uint64_t s;
+    int g, cell, ix, iy, ucell, mat, prob, root, nfis, ncoll, ncross, fate;
+};
+
+// ---------------------------------------------------------------------------
+// CSG geometry (Sec. 1: constructive solid geometry with surface tracking)
+__device__ __forceinline__ double surf_f(const World &W, int sid, double x, double y, double z)
+{
+    const double *c = W.s_coef + 4 * sid;
+    switch (__ldg(W.s_type + sid)) {
+    case SURF_PX: return x - __ldg(c);
+    case SURF_PY: return y - __ldg(c);
+    case SURF_PZ: return z - __ldg(c);
+    case SURF_PLANE: return __ldg(c) * x + __ldg(c + 1) * y + __ldg(c + 2) * z - __ldg(c + 3);
+    case SURF_CYLZ: {
+        double dx = x - __ldg(c), dy = y - __ldg(c + 1);
+        return dx * dx + dy * dy - __ldg(W.s_r2 + sid);
+    }
+    default: {
+        double dx = x - __ldg(c), dy = y - __ldg(c + 1), dz = z - __ldg(c + 2);
+        return dx * dx + dy * dy + dz * dz - __ldg(W.s_r2 + sid);
+    }
+    }
+}
+
+__device__ __forceinline__ double surf_gdot(const World &W, int sid, double x, double y, double z,
+                                            double u, double v, double w)
+{
+    const double *c = W.s_coef + 4 * sid;
+    switch (__ldg(W.s_type + sid)) {
+    case SURF_PX: return u;
+    case SURF_PY: return v;
+    case SURF_PZ: return w;
+    case SURF_PLANE: return __ldg(c) * u + __ldg(c + 1) * v + __ldg(c + 2) * w;
+    case SURF_CYLZ: return (x - __ldg(c)) * u + (y - __ldg(c + 1)) * v;
+    default: return (x - __ldg(c)) * u + (y - __ldg(c + 1)) * v + (z - __ldg(c + 2)) * w;
+    }
+}
+
+// Distance to leaving the half-space of the given sense.  The root is chosen
+// from the sense (so a surface just crossed is never re-hit), quadratic roots
+// use cancellation-free forms, and round-off negatives become 0.
+__device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, double x, double y,
+                                            double z, double u, double v, double w)
+{
+    const double *c = W.s_coef + 4 * sid;
+    int type = __ldg(W.s_type + sid);
+    double t;
+    if (type <= SURF_PLANE) {
+        double dn, f;
+        switch (type) {
+        case SURF_PX: dn = u; f = x - __ldg(c); break;
+        case SURF_PY: dn = v; f = y - __ldg(c); break;
+        case SURF_PZ: dn = w; f = z - __ldg(c); break;
+        default:
+            dn = __ldg(c) * u + __ldg(c + 1) * v + __ldg(c + 2) * w;
+            f = __ldg(c) * x + __ldg(c + 1) * y + __ldg(c + 2) * z - __ldg(c + 3);
+        }
+        if ((sense > 0 && dn < 0.0) || (sense < 0 && dn > 0.0)) {
+            t = -f / dn;
+            return t < 0.0 ? 0.0 : t;
+        }
+        return MCGB_INF;
+    }
+    double a, b, cc;
+    if (type == SURF_CYLZ) {
+        double dx = x - __ldg(c), dy = y - __ldg(c + 1);
+        a = u * u + v * v;
+        b = dx * u + dy * v;
+        cc = dx * dx + dy * dy - __ldg(W.s_r2 + sid);
+    } else {
+        double dx = x - __ldg(c), dy = y - __ldg(c + 1), dz = z - __ldg(c + 2);
+        a = u * u + v * v + w * w;
+        b = dx * u + dy * v + dz * w;
+        cc = dx * dx + dy * dy + dz * dz - __ldg(W.s_r2 + sid);
+    }
+    if (a == 0.0) return MCGB_INF;
+    double disc = b * b - a * cc;
+    if (sense < 0) {
+        if (disc < 0.0) disc = 0.0;
+        if (b <= 0.0) t = (-b + sqrt(disc)) / a;
+        else t = -cc / (b + sqrt(disc));
+        return t < 0.0 ? 0.0 : t;
+    }
+    if (b >= 0.0 || disc < 0.0) return MCGB_INF;
+    t = cc / (-b + sqrt(disc));
+    return t < 0.0 ? 0.0 : t;
+}
+
+// Does cell `ci` hold the point?  Sense from the sign of f; exactly on a surface
+// from the sign of (gradient . direction), 0 counting as +.  `forced` (a surface
+// just crossed) takes `forced_sense`.
+__device__ __forceinline__ bool cell_holds(const World &W, int ci, double x, double y, double z,
+                                           double u, double v, double w, int forced,
+                                           int forced_sense)
+{
+    int off = __ldg(W.c_off + ci), nh = __ldg(W.c_nhs + ci);
+    for (int h = 0; h < nh; h++) {
+        int sid = __ldg(W.hs_surf + off + h);
+        int sense;
+        if (sid == forced) {
+            sense = forced_sense;
+        } else {
+            double f = surf_f(W, sid, x, y, z);
+            if (f > 0.0) sense = 1;
+            else if (f < 0.0) sense = -1;
+            else sense = surf_gdot(W, sid, x, y, z, u, v, w) >= 0.0 ? 1 : -1;
+        }
+        if (sense != __ldg(W.hs_sense + off + h)) return false;
+    }
+    return true;
+}
+
+// First cell of universe U (definition order) holding the point, -1 if none.
+__device__ __forceinline__ int locate_univ(const World &W, int U, double x, double y, double z,
+                                           double u, double v, double w, int forced,
+                                           int forced_sense)
+{
+    int b = __ldg(W.u_off + U), e = __ldg(W.u_off + U + 1);
+    for (int k = b; k < e; k++) {
+        int ci = __ldg(W.u_cells + k);
+        if (cell_holds(W, ci, x, y, z, u, v, w, forced, forced_sense)) return ci;
+    }
+    return -1;
+}
+
+// After crossing half-space `hs` (global index) of a cell in universe U: scan the
+// precomputed candidates (cells of U bounded by the same surface with the other
+// sense), then the whole universe.  Cells must partition space, so the answer is
+// the same as a full scan's.
+__device__ __forceinline__ int relocate(const World &W, int U, int hs, double x, double y, double z,
+                                        double u, double v, double w)
+{
+    int forced = __ldg(W.hs_surf + hs);
+    int fs = -__ldg(W.hs_sense + hs);
+    int b = __ldg(W.hs_coff + hs), e = __ldg(W.hs_coff + hs + 1);
+    for (int k = b; k < e; k++) {
+        int ci = __ldg(W.hs_cand + k);
+        if (cell_holds(W, ci, x, y, z, u, v, w, forced, fs)) return ci;
+    }
+    return locate_univ(W, U, x, y, z, u, v, w, forced, fs);
+}
+
+__device__ __forceinline__ void local_xy(const World &W, int L, int ix, int iy, double x, double y,
+                                         double &xl, double &yl)
+{
+    double p = __ldg(W.l_pitch + L);
+    xl = x - (__ldg(W.l_x0 + L) + ((double)ix + 0.5) * p);
+    yl = y - (__ldg(W.l_y0 + L) + ((double)iy + 0.5) * p);
+}
+
+__device__ __forceinline__ void lattice_index(const World &W, int L, double x, double y, int &ix,
+                                              int &iy)
+{
+    double p = __ldg(W.l_pitch + L);
+    int i = (int)floor((x - __ldg(W.l_x0 + L)) / p);
+    int j = (int)floor((y - __ldg(W.l_y0 + L)) / p);
+    int nx = __ldg(W.l_nx + L), ny = __ldg(W.l_ny + L);
+    ix = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+    iy = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
+}
+
+// Below the root cell: lattice element universe cell and material.
+__device__ __forceinline__ bool descend(const World &W, PS &p, int hs_forced)
+{
+    if (__ldg(W.c_fillk + p.cell) == FILL_LAT) {
+        int L = __ldg(W.c_fill + p.cell);
+        double xl, yl;
+        local_xy(W, L, p.ix, p.iy, p.x, p.y, xl, yl);
+        int U = __ldg(W.l_univ + __ldg(W.l_uoff + L) + p.ix + __ldg(W.l_nx + L) * p.iy);
+        int uc;
+        if (hs_forced >= 0) uc = relocate(W, U, hs_forced, xl, yl, p.z, p.u, p.v, p.w);
+        else uc = locate_univ(W, U, xl, yl, p.z, p.u, p.v, p.w, -1, 0);
+        if (uc < 0) return false;
+        p.ucell = uc;
+        p.mat = __ldg(W.c_fill + uc);
+    } else {
+        p.ucell = -1;
+        p.ix = -1;
+        p.iy = -1;
+        p.mat = __ldg(W.c_fill + p.cell);
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool locate_full(const World &W, int root_univ, PS &p)
+{
+    int rc = locate_univ(W, root_univ, p.x, p.y, p.z, p.u, p.v, p.w, -1, 0);
+    if (rc < 0) return false;
+    p.cell = rc;
+    if (__ldg(W.c_fillk + rc) == FILL_LAT)
+        lattice_index(W, __ldg(W.c_fill + rc), p.x, p.y, p.ix, p.iy);
+    return descend(W, p, -1);
+}
+
+// Nearest boundary: root cell surfaces, then interior lattice walls (x, y), then
+// the element universe cell's surfaces; ties go to the earliest (strict <).
+__device__ __forceinline__ double boundary(const World &W, const PS &p, int &kind, int &which)
+{
+    double best = MCGB_INF;
+    kind = B_NONE;
+    which = -1;
+    int off = __ldg(W.c_off + p.cell), nh = __ldg(W.c_nhs + p.cell);
+    for (int h = 0; h < nh; h++) {
+        double t = surf_dist(W, __ldg(W.hs_surf + off + h), __ldg(W.hs_sense + off + h), p.x, p.y,
+                             p.z, p.u, p.v, p.w);
+        if (t < best) {
+            best = t;
+            kind = B_ROOT;
+            which = off + h;
+        }
+    }
+    if (__ldg(W.c_fillk + p.cell) == FILL_LAT) {
+        int L = __ldg(W.c_fill + p.cell);
+        double x0 = __ldg(W.l_x0 + L), y0 = __ldg(W.l_y0 + L), pitch = __ldg(W.l_pitch + L);
+        int nx = __ldg(W.l_nx + L), ny = __ldg(W.l_ny + L);
+        double t = MCGB_INF;
+        if (p.u > 0.0 && p.ix < nx - 1) t = (x0 + (double)(p.ix + 1) * pitch - p.x) / p.u;
+        else if (p.u < 0.0 && p.ix > 0) t = (x0 + (double)p.ix * pitch - p.x) / p.u;
+        if (t < 0.0) t = 0.0;
+        if (t < best) {
+            best = t;
+            kind = B_LATX;
+        }
+        t = MCGB_INF;
+        if (p.v > 0.0 && p.iy < ny - 1) t = (y0 + (double)(p.iy + 1) * pitch - p.y) / p.v;
+        else if (p.v < 0.0 && p.iy > 0) t = (y0 + (double)p.iy * pitch - p.y) / p.v;
+        if (t < 0.0) t = 0.0;
+        if (t < best) {
+            best = t;
+            kind = B_LATY;
+        }
+        double xl, yl;
+        local_xy(W, L, p.ix, p.iy, p.x, p.y, xl, yl);
+        int uoff = __ldg(W.c_off + p.ucell), unh = __ldg(W.c_nhs + p.ucell);
+        for (int h = 0; h < unh; h++) {
+            double tt = surf_dist(W, __ldg(W.hs_surf + uoff + h), __ldg(W.hs_sense + uoff + h), xl,
+                                  yl, p.z, p.u, p.v, p.w);
+            if (tt < best) {
+                best = tt;
+                kind = B_UNIV;
+                which = uoff + h;
+            }
+        }
+    }
+    return best;
+}
+
+// Surface crossing: vacuum -> leak (returns 1); reflective plane -> mirror the
+// direction, keep the cell; interior -> relocate with the crossed surface's
+// sense flipped; lattice wall -> step the element.  Returns -1 when no cell
+// holds the particle (lost).
+__device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
+{
+    if (kind == B_ROOT) {
+        int sid = __ldg(W.hs_surf + which);
+        int bc = __ldg(W.s_bc + sid);
+        if (bc == BC_VACUUM) return 1;
+        if (bc == BC_REFLECT) {
+            switch (__ldg(W.s_type + sid)) {
+            case SURF_PX: p.u = -p.u; break;
+            case SURF_PY: p.v = -p.v; break;
+            case SURF_PZ: p.w = -p.w; break;
+            default: {
+                const double *c = W.s_coef + 4 * sid;
+                double a = __ldg(c), b = __ldg(c + 1), cz = __ldg(c + 2);
+                double dn = a * p.u + b * p.v + cz * p.w;
+                double nn = a * a + b * b + cz * cz;
+                double k = 2.0 * dn / nn;
+                p.u = p.u - k * a;
+                p.v = p.v - k * b;
+                p.w = p.w - k * cz;
+            }
+            }
+            return 0;
+        }
+        int nc = relocate(W, __ldg(W.c_univ + p.cell), which, p.x, p.y, p.z, p.u, p.v, p.w);
+        if (nc < 0) return -1;
+        p.cell = nc;
+        if (__ldg(W.c_fillk + nc) == FILL_LAT)
+            lattice_index(W, __ldg(W.c_fill + nc), p.x, p.y, p.ix, p.iy);
+        return descend(W, p, -1) ? 0 : -1;
+    }
+    if (kind == B_LATX || kind == B_LATY) {
+        if (kind == B_LATX) p.ix += p.u > 0.0 ? 1 : -1;
+        else p.iy += p.v > 0.0 ? 1 : -1;
+        return descend(W, p, -1) ? 0 : -1;
+    }
+    return descend(W, p, which) ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Continuous-energy lookup: union-grid binary search, then each nuclide's
+// interval from the precomputed map (equal to that nuclide's own largest
+// E_j <= E); sigma = sigma_j + f (sigma_{j+1} - sigma_j), f = (E - E_j)(1/dE_j).
+struct CEXS {
+    double sigt, nusf;
+    double st[MAX_NUC], ss[MAX_NUC], sf[MAX_NUC];
+};
+
+__device__ __forceinline__ int union_index(const World &W, double E)
+{
+    int lo = 0, hi = W.nunion - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(W.Eu + mid) <= E) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void ce_xs(const World &W, int mat, int k, double E, CEXS &x)
+{
+    int off = __ldg(W.mc_off + mat), n = __ldg(W.mc_n + mat);
+    x.sigt = 0.0;
+    x.nusf = 0.0;
+#pragma unroll
+    for (int q = 0; q < MAX_NUC; q++) {
+        if (q < n) {
+            int nuc = __ldg(W.mc_nuc + off + q);
+            double dens = __ldg(W.mc_dens + off + q);
+            int j = __ldg(W.umap + (int64_t)nuc * W.nunion + k);
+            const double2 *iv = reinterpret_cast<const double2 *>(
+                W.n_iv + 8 * ((int64_t)__ldg(W.n_ivoff + nuc) + j));
+            double2 e_inv = __ldg(iv), s = __ldg(iv + 1), c = __ldg(iv + 2), f = __ldg(iv + 3);
+            double fr = (E - e_inv.x) * e_inv.y;
+            double ss = s.x + fr * s.y;
+            double sc = c.x + fr * c.y;
+            double sf = f.x + fr * f.y;
+            double st = ss + sc + sf;
+            x.st[q] = st;
+            x.ss[q] = ss;
+            x.sf[q] = sf;
+            x.sigt = x.sigt + dens * st;
+            x.nusf = x.nusf + dens * (__ldg(W.n_nu + nuc) * sf);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Track-length tallies: score d into [batch][bin][energy] of every tally of the
+// particle's problem (accumulator replica `rep` spreads atomic traffic).
+__device__ __forceinline__ void score(const World &W, const ProblemDev &P, const PS &p, double d,
+                                      int batch, double *acc, int rep)
+{
+    for (int t = P.tally_first; t < P.tally_first + P.tally_count; t++) {
+        int filter = __ldg(W.t_filter + t);
+        int bin;
+        if (filter == FILTER_CELL) {
+            bin = (p.ucell >= 0 ? p.ucell : p.cell) - P.cell0;
+        } else if (filter == FILTER_LATTICE) {
+            if (p.ucell < 0) continue;
+            bin = p.ix + __ldg(W.l_nx + P.lattice0) * p.iy;
+        } else {
+            bin = p.mat - P.mat0;
+        }
+        int e;
+        if (P.ce) {
+            const double *ed = W.t_edges + __ldg(W.t_eoff + t);
+            int ne = __ldg(W.t_nedges + t);
+            if (p.E < __ldg(ed) || p.E > __ldg(ed + ne - 1)) continue;
+            e = 0;
+            while (e + 1 < ne - 1 && __ldg(ed + e + 1) <= p.E) e++;
+        } else {
+            e = p.g;
+        }
+        int nb = __ldg(W.t_nbins + t), ne_ = __ldg(W.t_ne + t);
+        int64_t idx = (int64_t)rep * W.acc_size + __ldg(W.t_off + t) +
+                      ((int64_t)batch * nb + bin) * ne_ + e;
+        atomicAdd(acc + idx, d);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bank a fission site (parent slot, child index) -- appended in any order and
+// put in (parent, child) order at the end of the cycle.
+__device__ __forceinline__ void bank_push(const Bank &B, int *bank_n, int *err, const PS &p,
+                                          int slot)
+{
+    int pos = atomicAdd(bank_n, 1);
+    if (pos >= B.cap) {
+        atomicOr(err, ERR_BANK_OVERFLOW);
+        return;
+    }
+    B.x[pos] = p.x;
+    B.y[pos] = p.y;
+    B.z[pos] = p.z;
+    B.cell[pos] = p.cell;
+    B.ix[pos] = p.ix;
+    B.iy[pos] = p.iy;
+    B.ucell[pos] = p.ucell;
+    B.mat[pos] = p.mat;
+    B.parent[pos] = slot;
+    B.child[pos] = p.nfis;
+    B.root[pos] = p.root;
+    B.prob[pos] = p.prob;
+}
+
+// ---------------------------------------------------------------------------
+// Sources: draw order is position (3 draws per rejection attempt), energy, direction.
+__device__ __forceinline__ bool mat_fissile(const World &W, const ProblemDev &P, int mat)
+{
+    return P.ce ? __ldg(W.mc_fissile + mat) != 0 : __ldg(W.m_fissile + mat) != 0;
+}
+
+__device__ __forceinline__ void birth_energy(const World &W, const ProblemDev &P, PS &p)
+{
+    if (P.ce) p.E = maxwell(W, p.s);
+    else p.g = sample_cdf(W.g_chicdf + __ldg(W.m_goff + p.mat), __ldg(W.m_G + p.mat), draw(p.s));
+}
+
+__device__ __forceinline__ bool sample_source(const World &W, const ProblemDev &P, PS &p)
+{
+    p.u = p.v = p.w = 0.0;
+    if (P.src_kind == SRC_BOX) {
+        bool ok = false;
+        for (int t = 0; t < MAX_TRIES && !ok; t++) {
+            p.x = P.src_p[0] + draw(p.s) * (P.src_p[1] - P.src_p[0]);
+            p.y = P.src_p[2] + draw(p.s) * (P.src_p[3] - P.src_p[2]);
+            p.z = P.src_p[4] + draw(p.s) * (P.src_p[5] - P.src_p[4]);
+            if (!locate_full(W, P.root_univ, p)) continue;
+            ok = P.src_accept == 0 || mat_fissile(W, P, p.mat);
+        }
+        if (!ok) return false;
+    } else {
+        p.x = P.src_p[0];
+        p.y = P.src_p[1];
+        p.z = P.src_p[2];
+        if (!locate_full(W, P.root_univ, p)) return false;
+    }
+    switch (P.src_ekind) {
+    case E_CHI: birth_energy(W, P, p); break;
+    case E_PDF: p.g = sample_cdf(W.src_cdf + P.src_cdf_off, P.src_ncdf, draw(p.s)); break;
+    case E_FIXED: p.E = P.src_E; break;
+    default: p.E = maxwell(W, p.s);
+    }
+    if (P.src_dkind == DIR_BEAM) {
+        p.u = P.src_beam[0];
+        p.v = P.src_beam[1];
+        p.w = P.src_beam[2];
+    } else {
+        iso_dir(p.s, p.u, p.v, p.w);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void birth_from_site(const World &W, const ProblemDev &P, const Bank &B,
+                                                int b, PS &p)
+{
+    p.x = B.x[b];
+    p.y = B.y[b];
+    p.z = B.z[b];
+    p.cell = B.cell[b];
+    p.ix = B.ix[b];
+    p.iy = B.iy[b];
+    p.ucell = B.ucell[b];
+    p.mat = B.mat[b];
+    birth_energy(W, P, p);
+    iso_dir(p.s, p.u, p.v, p.w);
+}
+
+}  // namespace mcgb

@@ -1,0 +1,164 @@
+"""GPU vs oracle parity, element by element, through the C ABI.
+
+Every history draws from its own random stream and both implementations
+evaluate the same IEEE double expressions without contraction, so random
+streams, histories (collision and crossing counts, end states, fates), fission
+banks and per-cycle bank sizes must be bit-identical.  Tallies and k are sums
+over histories taken in different orders (atomics on the GPU), so they agree to
+a relative 1e-9 (rounding of ~1e6 additions of O(1) terms is ~1e-10).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle
+from tests.gpu_util import assert_same_histories, gpu_run, oracle_run, rel_close
+
+pytestmark = pytest.mark.gpu
+SUM_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def mcgb():
+    import paper_2501_05440_gb300 as m
+    m.build()
+    return m
+
+
+def test_rng_streams_bit_exact(mcgb, orc):
+    c = mcgb.Context()
+    ids = [0, 5, 152916, (3 << 32) + 7, (200 << 32) + 123456]
+    for first in ids:
+        st = c.rng_states(12345, first, 64, 200)
+        for i in [0, 1, 33, 63]:
+            s = orc.rng_stream(12345, first + i)
+            for k in range(200):
+                s = orc.rng_next(s)
+                assert int(st[i, k]) == s
+    big = c.rng_states(1, 0, 1000, 1000)
+    s = orc.rng_stream(1, 999)
+    for k in range(1000):
+        s = orc.rng_next(s)
+    assert int(big[999, 999]) == s
+
+
+def test_log_bit_exact(mcgb, orc):
+    c = mcgb.Context()
+    s = 99
+    xs = []
+    for _ in range(50000):
+        s = orc.rng_next(s)
+        xs.append(orc.rng_xi(s))
+    xs += [1.0, 0.5, 2.0**-53, 1 - 2.0**-53, 0.75]
+    xs = np.array(xs)
+    got = c.log(xs)
+    ref = np.array([orc.log(float(x)) for x in xs])
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("name", ["pin", "lattice", "slab", "box"])
+def test_geometry_probe_bit_exact(mcgb, name):
+    pb = {"pin": W.pin_cell_mg(n=10), "lattice": W.c5g7_like_lattice(n=10),
+          "slab": W.diff_slab(n=10), "box": W.batch_boxes(nproblems=2)[1]}[name]
+    c = mcgb.load_problem(mcgb.Context(), pb)
+    o = Oracle(pb)
+    xs = [s["coef"][0] for s in pb["surfaces"] if s["type"] == "px"]
+    ys = [s["coef"][0] for s in pb["surfaces"] if s["type"] == "py"]
+    zs = [s["coef"][0] for s in pb["surfaces"] if s["type"] == "pz"] or [-3.0, 3.0]
+    rng = np.random.default_rng(4)
+    n = 3000
+    pos = np.stack([rng.uniform(min(xs), max(xs), n), rng.uniform(min(ys), max(ys), n),
+                    rng.uniform(min(zs), max(zs), n)], 1)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    path, dist, kind = c.probe(pos, d)
+    for i in range(0, n, 7):
+        op, od, ok = o.probe(pos[i], d[i])
+        assert list(path[i]) == [int(v) for v in op]
+        assert dist[i] == od and kind[i] == ok
+
+
+def test_ce_lookup_bit_exact(mcgb):
+    pb = W.ce_pin_cell(n=10, npts=5000, nres=30)
+    c = mcgb.load_problem(mcgb.Context(), pb)
+    o = Oracle(pb)
+    rng = np.random.default_rng(8)
+    E = np.exp(rng.uniform(np.log(1e-5), np.log(2e7), 4000))
+    E = np.concatenate([E, pb["nuclides"][3]["E"][::97], [1e-5, 2e7]])
+    for mat in (0, 1):
+        out = c.ce_lookup(mat, E)
+        for i in range(0, len(E), 3):
+            assert np.array_equal(out[i], o.ce_lookup(mat, float(E[i])))
+
+
+def _eigen_parity(mcgb, pb, mode):
+    ncyc = pb["run"]["inactive"] + pb["run"]["active"]
+    c = gpu_run(pb, mode=mode)
+    o = oracle_run(pb)
+    gk, gc, gm = c.get_cycle_k(ncyc)
+    ok, oc, om = o.cycle_k(ncyc)
+    assert gm.tolist() == om.tolist()
+    assert rel_close(gk, ok, SUM_RTOL) and rel_close(gc, oc, SUM_RTOL)
+    assert_same_histories(c.get_histories(), o.histories())
+    gb, ob = c.get_bank(), o.bank()
+    assert np.array_equal(gb["parent"], ob["parent"]) and np.array_equal(gb["child"], ob["child"])
+    assert np.array_equal(gb["xyz"], ob["xyz"]) and np.array_equal(gb["mat"], ob["mat"])
+    for t in range(len(pb["tallies"])):
+        gmean, gsd = c.get_tally(t)
+        omean, osd = o.tally(t)
+        assert rel_close(gmean, omean, SUM_RTOL, 1e-300)
+        assert rel_close(gsd, osd, 1e-6, 1e-14)
+    gkk, okk = c.get_k(), o.k()
+    for key in ["k", "k_col", "k_analog"]:
+        assert abs(gkk[key] - okk[key]) <= SUM_RTOL * abs(okk[key])
+    cnt_g, cnt_o = c.get_counters(), o.counters()
+    for key in ["collisions", "crossings", "leaks", "lost", "capped"]:
+        assert cnt_g[key] == cnt_o[key], key
+    return c, o
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pin_cell_eigen_parity(mcgb, mode):
+    _eigen_parity(mcgb, W.pin_cell_mg(n=3000, inactive=3, active=5), mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_lattice_eigen_parity(mcgb, mode):
+    _eigen_parity(mcgb, W.c5g7_like_lattice(n=4000, inactive=2, active=3), mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ce_pin_eigen_parity(mcgb, mode):
+    _eigen_parity(mcgb, W.ce_pin_cell(n=600, inactive=1, active=2, npts=5000, nres=40), mode)
+
+
+def _fixed_parity(mcgb, pb, mode):
+    c = gpu_run(pb, mode=mode)
+    o = oracle_run(pb)
+    assert_same_histories(c.get_histories(), o.histories())
+    gb, ob = c.get_bank(), o.bank()
+    assert np.array_equal(gb["parent"], ob["parent"]) and np.array_equal(gb["xyz"], ob["xyz"])
+    for t in range(len(pb["tallies"])):
+        gmean, gsd = c.get_tally(t)
+        omean, osd = o.tally(t)
+        assert rel_close(gmean, omean, SUM_RTOL, 1e-300)
+        assert rel_close(gsd, osd, 1e-6, 1e-14)
+    cg, co = c.get_counters(), o.counters()
+    for key in ["histories", "collisions", "crossings", "leaks", "lost", "generations"]:
+        assert cg[key] == co[key], key
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_slab_fixed_source_parity(mcgb, mode):
+    _fixed_parity(mcgb, W.diff_slab(n=5000, batches=10), mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_box_fixed_source_parity(mcgb, mode):
+    for pb in W.batch_boxes(nproblems=4, nmin=500, nmax=3000)[:4]:
+        _fixed_parity(mcgb, pb, mode)
+
+
+def test_one_collision_and_absorber_parity(mcgb):
+    for pb in [W.one_collision_slab(n=5000), W.absorbing_slab_beam(n=5000)]:
+        _fixed_parity(mcgb, pb, 0)

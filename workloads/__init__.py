@@ -216,9 +216,12 @@ def c5g7_like_lattice(seed=1, n=1_000_000, inactive=50, active=100, G=7, guide_p
 # configuration 2: continuous-energy pin cell, k-eigenvalue
 # ----------------------------------------------------------------------------
 E_MIN, E_MAX = 1.0e-5, 2.0e7          # eV
+FUEL_235 = (3.5e-3, 4.5e-3)           # atom density ranges of the fuel (atoms/b-cm)
+FUEL_90 = (1.0e-3, 2.0e-3)
 
 
-def _ce_nuclide(rng, A, npts, fissile, sig_pot, a_c, a_f=0.0, nu=0.0, nres=200):
+def _ce_nuclide(rng, A, npts, fissile, sig_pot, a_c, a_f=0.0, nu=0.0, nres=200,
+                split=(2.0, 2.0, 2.0)):
     """Pointwise cross sections on a log grid with a seeded sub-interval phase.
 
     Smooth part: constant potential scattering and 1/v capture (and 1/v fission
@@ -239,7 +242,7 @@ def _ce_nuclide(rng, A, npts, fissile, sig_pot, a_c, a_f=0.0, nu=0.0, nres=200):
     E0 = np.exp(rng.uniform(math.log(1.0), math.log(1.0e5), size=nres))
     gam = rng.uniform(0.02, 0.5, size=nres) * E0 ** 0.25
     peak = np.exp(rng.uniform(math.log(10.0), math.log(1.0e4), size=nres))
-    parts = rng.dirichlet([2.0, 2.0, 2.0] if fissile else [2.0, 2.0], size=nres)
+    parts = rng.dirichlet(list(split[:3]) if fissile else list(split[:2]), size=nres)
     for i in range(nres):
         x = 2.0 * (E - E0[i]) / gam[i]
         shape = peak[i] / (1.0 + x * x)
@@ -260,13 +263,15 @@ def ce_pin_cell(seed=1, n=1_000_000, inactive=20, active=50, npts=50_000, nres=2
     """
     rng = np.random.default_rng([seed, 2])
     nucs = [
-        _ce_nuclide(rng, 1.0, npts, False, 20.0, 0.0525, nres=nres),
-        _ce_nuclide(rng, 16.0, npts, False, 3.8, 0.0003, nres=nres),
-        _ce_nuclide(rng, 90.0, npts, False, 6.0, 0.03, nres=nres),
-        _ce_nuclide(rng, 235.0, npts, True, 10.0, 15.7, a_f=93.0, nu=2.43, nres=nres),
+        _ce_nuclide(rng, 1.0, npts, False, 20.0, 0.02, nres=nres, split=(30.0, 0.005)),
+        _ce_nuclide(rng, 16.0, npts, False, 3.8, 0.0003, nres=nres, split=(30.0, 0.005)),
+        _ce_nuclide(rng, 90.0, npts, False, 6.0, 0.03, nres=nres, split=(6.0, 1.0)),
+        _ce_nuclide(rng, 235.0, npts, True, 10.0, 10.0, a_f=93.0, nu=2.43, nres=nres,
+                    split=(2.0, 0.5, 2.5)),
     ]
     fuel = {"nuclides": [3, 1, 2],
-            "density": [rng.uniform(6.0e-4, 9.0e-4), 4.6e-2, rng.uniform(1.5e-2, 2.5e-2)]}
+            "density": [rng.uniform(FUEL_235[0], FUEL_235[1]), 4.6e-2,
+                        rng.uniform(FUEL_90[0], FUEL_90[1])]}
     mod = {"nuclides": [0, 1], "density": [rng.uniform(6.0e-2, 7.0e-2), 3.3e-2]}
     surfaces, cells = _pin_geometry()
     edges = np.geomspace(E_MIN, E_MAX, nbins + 1)
