@@ -247,6 +247,27 @@ int mcgb_probe(mcgb_ctx *ctx, int64_t n, const double *pos, const double *dir, i
  * Sigma_t, nuSigma_f, Sigma_s, Sigma_f. */
 int mcgb_ce_lookup(mcgb_ctx *ctx, int mat, int64_t n, const double *E, double *out);
 
+/* --------------------------------------------------------------------------- */
+/* allocation-free bank ordering (the paper has no counterpart)                 */
+/* For callers that cannot give the library device memory: their GPU memory is
+ * owned by another allocator (for example a framework's caching allocator that
+ * has reserved the device), or they must not allocate once running.  Given
+ * n_fis[n], the fission sites each history of a cycle banked (device pointer),
+ * writes first[j] = sites banked by histories 0..j-1 -- the position of history
+ * j's first site in the (parent, child) ordered bank -- and *total = all sites
+ * (device pointers), on cuda_stream (NULL = legacy default stream), with the
+ * same kernels as the library's own cycle end.  It allocates nothing: its
+ * scratch is a 16 KiB array built into the library, held on every GPU that
+ * loads it until the process exits.  n may be at most 16777216; larger n is
+ * rejected with MCGB_E_INVALID_ARG.  The first call on a device (make it the
+ * current device) looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array, so calls that overlap
+ * on the GPU (concurrent streams or devices sharing nothing else) race: order
+ * them on one stream.  Nothing in the array needs clearing between calls.
+ * Returns MCGB_OK or MCGB_E_INVALID_ARG / MCGB_E_CUDA. */
+int mcgb_bank_offsets_noalloc(const int32_t *n_fis, int64_t n, int32_t *first, int32_t *total,
+                              void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

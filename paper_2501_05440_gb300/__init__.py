@@ -15,7 +15,7 @@ import threading
 import numpy as np
 
 __all__ = ["lib", "build", "McgbError", "Context", "Batch", "load_problem", "library_path",
-           "MODE_EVENT", "MODE_PERSISTENT"]
+           "bank_offsets_noalloc", "MODE_EVENT", "MODE_PERSISTENT"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "_build", "libmcgb.so")
@@ -108,6 +108,7 @@ def lib():
                 "mcgb_rng_states": [P, u64, u64, i64, i32, P],
                 "mcgb_log": [P, i64, P, P], "mcgb_probe": [P, i64, P, P, P, P, P],
                 "mcgb_ce_lookup": [P, i32, i64, P, P],
+                "mcgb_bank_offsets_noalloc": [P, i64, P, P, P],
             }
             for name, args in sigs.items():
                 f = getattr(L, name)
@@ -133,6 +134,12 @@ def _chk(r):
     if r != 0:
         raise McgbError(r, lib().mcgb_last_error().decode())
     return r
+
+
+def bank_offsets_noalloc(n_fis_ptr, n, first_ptr, total_ptr, stream=0):
+    """mcgb_bank_offsets_noalloc on device pointers (ints); allocates nothing."""
+    _chk(lib().mcgb_bank_offsets_noalloc(C.c_void_p(n_fis_ptr), n, C.c_void_p(first_ptr),
+                                         C.c_void_p(total_ptr), C.c_void_p(stream)))
 
 
 class Context:

@@ -29,6 +29,11 @@ static int fail(int code, const std::string &msg)
     return code;
 }
 
+namespace mcgb {
+// lets other translation units report through mcgb_last_error()
+int set_error(int code, const char *msg) { return fail(code, msg); }
+}  // namespace mcgb
+
 #define CK(expr)                                                                       \
     do {                                                                               \
         cudaError_t e_ = (expr);                                                       \

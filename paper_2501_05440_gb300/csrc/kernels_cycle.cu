@@ -6,6 +6,9 @@
 // (nfis), so an exclusive scan of those counts gives each parent's first
 // position; site b goes to off[parent] + child.  The order is the unique
 // (parent, child) order whatever order the sites were appended in.
+#include <mutex>
+#include <string>
+
 #include "kernels.h"
 #include "transport.cuh"
 
@@ -265,3 +268,75 @@ void launch_copy_records(const Particles &P, int64_t n, int *ncoll, int *ncross,
 }
 
 }  // namespace mcgb
+
+// ---------------------------------------------------------------------------
+// Allocation-free bank offsets.
+//
+// Some callers cannot give this library device memory of its own: their device
+// memory is owned by another allocator (a framework's caching allocator that
+// has reserved the GPU), or they must not allocate once they are running
+// (latency-critical loops).  This entry point does the bank-ordering scan with
+// its tile sums in a fixed array compiled into the library instead of a
+// buffer from cudaMalloc.  Every GPU that loads the library holds the array
+// (16 KiB) until the process exits.
+namespace mcgb {
+int set_error(int code, const char *msg);
+}
+
+namespace {
+
+constexpr int NOALLOC_MAX_TILES = 4096;   // n <= 4096 tiles x 4096 counts = 16,777,216
+
+// Tile sums of the allocation-free scan.  Host code must not pass this name to a
+// kernel (on the host it is only a stand-in); it passes the device address
+// found once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) int g_noalloc_tiles[NOALLOC_MAX_TILES];
+
+std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+int *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+}  // namespace
+
+extern "C" int mcgb_bank_offsets_noalloc(const int32_t *n_fis, int64_t n, int32_t *first,
+                                         int32_t *total, void *cuda_stream)
+{
+    using namespace mcgb;
+    if (n < 0 || (n > 0 && (!n_fis || !first)) || !total)
+        return set_error(-1, "mcgb_bank_offsets_noalloc: null pointer or negative n");
+    if (n > (int64_t)NOALLOC_MAX_TILES * SCAN_TILE)
+        return set_error(-1, "mcgb_bank_offsets_noalloc: n exceeds the maximum of 16777216 counts "
+                             "(4096 tiles of 4096)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return set_error(-3, "mcgb_bank_offsets_noalloc: no usable current device");
+    int *tiles = nullptr;
+    {
+        // first call on this device (with it current): look up the array's device address
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            e = cudaGetSymbolAddress((void **)&g_noalloc_ptr[dev], g_noalloc_tiles);
+            if (e != cudaSuccess) {
+                g_noalloc_ptr[dev] = nullptr;
+                return set_error(-3, (std::string("mcgb_bank_offsets_noalloc: cudaGetSymbolAddress: ") +
+                                      cudaGetErrorString(e)).c_str());
+            }
+        }
+        tiles = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int ntiles = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+    if (ntiles == 0) {
+        e = cudaMemsetAsync(total, 0, sizeof(int32_t), st);
+    } else {
+        // every tile sum that is read is written first by k_scan_tile: nothing needs clearing
+        k_scan_tile<<<ntiles, SCAN_BLOCK, 0, st>>>(n_fis, first, n, tiles);
+        k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(tiles, ntiles, total);
+        if (ntiles > 1) k_scan_add<<<(int)((n + 255) / 256), 256, 0, st>>>(first, n, tiles);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return set_error(-3, (std::string("mcgb_bank_offsets_noalloc: ") + cudaGetErrorString(e)).c_str());
+    return 0;
+}
