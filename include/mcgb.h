@@ -77,6 +77,9 @@ typedef struct {
     int record_histories;   /* keep per-history records of the last cycle / generation 0 */
     double bank_factor;     /* fission bank capacity as a multiple of N (default 3) */
     int max_iterations;     /* event-mode iteration limit per cycle (default 1e7) */
+    int pool;               /* persistent mode: particles per block held in shared memory
+                               and run event by event in sorted lists (256, 512 or 1024;
+                               0 = 512), or -1 for one particle per thread in registers */
 } mcgb_opts;
 
 /* Event and history counters of the last run. */
@@ -89,9 +92,9 @@ typedef struct {
 
 /* Launch shape chosen by the autotuner for a batch. */
 typedef struct {
-    int block;              /* threads per block */
+    int block;              /* threads per block (register-resident variant) */
     int blocks_per_sm;      /* resident blocks per SM in the persistent launch */
-    int chunk;              /* particles a warp takes per work-queue pop (1 = per lane) */
+    int pool;               /* particles per block in shared memory, -1 = register variant */
     double ms;              /* measured time of the tuning run */
 } mcgb_tune;
 

@@ -39,7 +39,7 @@ class McgbError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("device", C.c_int), ("mode", C.c_int), ("block", C.c_int),
                 ("blocks_per_sm", C.c_int), ("record_histories", C.c_int),
-                ("bank_factor", C.c_double), ("max_iterations", C.c_int)]
+                ("bank_factor", C.c_double), ("max_iterations", C.c_int), ("pool", C.c_int)]
 
 
 class Counters(C.Structure):
@@ -49,7 +49,7 @@ class Counters(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("chunk", C.c_int),
+    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("pool", C.c_int),
                 ("ms", C.c_double)]
 
 
@@ -146,11 +146,11 @@ class Context:
     """One transport problem on one GPU (mcgb_ctx)."""
 
     def __init__(self, device=0, mode=MODE_EVENT, block=0, blocks_per_sm=0,
-                 record_histories=False, bank_factor=0.0, max_iterations=0):
+                 record_histories=False, bank_factor=0.0, max_iterations=0, pool=0):
         L = lib()
         self.L = L
         self.opts = Opts(device, mode, block, blocks_per_sm, int(record_histories),
-                         bank_factor, max_iterations)
+                         bank_factor, max_iterations, pool)
         h = C.c_void_p()
         _chk(L.mcgb_create(C.byref(h), C.byref(self.opts)))
         self.h = h
@@ -389,10 +389,10 @@ def load_problem(ctx: Context, pb: dict) -> Context:
 class Batch:
     """Many independent fixed-source problems run together (mcgb_batch)."""
 
-    def __init__(self, device=0, mode=MODE_PERSISTENT, block=0, blocks_per_sm=0):
+    def __init__(self, device=0, mode=MODE_PERSISTENT, block=0, blocks_per_sm=0, pool=0):
         L = lib()
         self.L = L
-        self.opts = Opts(device, mode, block, blocks_per_sm, 0, 0.0, 0)
+        self.opts = Opts(device, mode, block, blocks_per_sm, 0, 0.0, 0, pool)
         h = C.c_void_p()
         _chk(L.mcgb_batch_create(C.byref(h), C.byref(self.opts)))
         self.h = h
@@ -415,11 +415,11 @@ class Batch:
     def autotune(self, budget_ms=2000):
         t = Tune()
         _chk(self.L.mcgb_batch_autotune(self.h, budget_ms, C.byref(t)))
-        return {"block": t.block, "blocks_per_sm": t.blocks_per_sm, "chunk": t.chunk, "ms": t.ms}
+        return {"block": t.block, "blocks_per_sm": t.blocks_per_sm, "pool": t.pool, "ms": t.ms}
 
     def run(self, tune=None):
         t = None if tune is None else Tune(tune["block"], tune["blocks_per_sm"],
-                                          tune.get("chunk", 1), 0.0)
+                                          tune.get("pool", 0), 0.0)
         _chk(self.L.mcgb_batch_run(self.h, None if t is None else C.byref(t)))
 
     def tally(self, problem, t=0):

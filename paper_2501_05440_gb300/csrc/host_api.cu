@@ -226,11 +226,21 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
         a.eigen = eigen;
         a.work = r.work;
         a.chunk = 1;
-        int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
-                                             : std::max(1, persistent_max_blocks_per_sm(block));
-        int64_t want = (total + block - 1) / block;
-        int grid = (int)std::min<int64_t>((int64_t)c->sms * bps, std::max<int64_t>(want, 1));
-        launch_persistent(W, r.P, Bsrc, Bdst, R, a, grid, block, st);
+        int pool = c->opts.pool == 0 ? 512 : c->opts.pool;
+        if (pool > 0) {
+            int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
+                                                 : std::max(1, pool_max_blocks_per_sm(pool));
+            int64_t want = (total + pool - 1) / pool;
+            int grid = (int)std::min<int64_t>((int64_t)c->sms * bps, std::max<int64_t>(want, 1));
+            if (!launch_pool(W, r.P, Bsrc, Bdst, R, a, pool, grid, st))
+                return fail(MCGB_E_INVALID_ARG, "pool must be 256, 512 or 1024");
+        } else {
+            int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
+                                                 : std::max(1, persistent_max_blocks_per_sm(block));
+            int64_t want = (total + block - 1) / block;
+            int grid = (int)std::min<int64_t>((int64_t)c->sms * bps, std::max<int64_t>(want, 1));
+            launch_persistent(W, r.P, Bsrc, Bdst, R, a, grid, block, st);
+        }
         c->launches += 1;
         CK(cudaGetLastError());
         return MCGB_OK;
@@ -698,6 +708,9 @@ int mcgb_create(mcgb_ctx **out, const mcgb_opts *opts)
     CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     if (c->opts.block != 0 && (c->opts.block < 32 || c->opts.block > 256 || c->opts.block % 32))
         return fail(MCGB_E_INVALID_ARG, "block must be a multiple of 32 in [32, 256]");
+    if (c->opts.pool != 0 && c->opts.pool != -1 && c->opts.pool != 256 && c->opts.pool != 512 &&
+        c->opts.pool != 1024)
+        return fail(MCGB_E_INVALID_ARG, "pool must be 256, 512, 1024, 0 (default) or -1");
     *out = c.release();
     return MCGB_OK;
 }
@@ -1263,7 +1276,7 @@ void tune_cache_load()
         std::istringstream is(line);
         std::string key;
         mcgb_tune t{};
-        if (std::getline(is, key, '\t') && (is >> t.block >> t.blocks_per_sm >> t.chunk >> t.ms))
+        if (std::getline(is, key, '\t') && (is >> t.block >> t.blocks_per_sm >> t.pool >> t.ms))
             g_tune_cache[key] = t;
     }
 }
@@ -1274,7 +1287,7 @@ void tune_cache_store(const std::string &key, const mcgb_tune &t)
     const char *path = std::getenv("MCGB_TUNE_CACHE");
     if (!path) return;
     std::ofstream f(path, std::ios::app);
-    f << key << '\t' << t.block << ' ' << t.blocks_per_sm << ' ' << t.chunk << ' ' << t.ms << '\n';
+    f << key << '\t' << t.block << ' ' << t.blocks_per_sm << ' ' << t.pool << ' ' << t.ms << '\n';
 }
 
 }  // namespace
@@ -1297,8 +1310,9 @@ static int batch_run_runs(mcgb_batch *b, const std::vector<ProblemRun> &runs, co
     mcgb_ctx *c = b->engine.get();
     CK(cudaSetDevice(c->device));
     if (tune) {
-        c->opts.block = tune->block;
+        c->opts.block = tune->block > 0 ? tune->block : c->opts.block;
         c->opts.blocks_per_sm = tune->blocks_per_sm;
+        c->opts.pool = tune->pool;
     }
     if (!c->world) c->world.reset(new DeviceWorld());
     std::string e = build_world(runs, *c->world, c->stream);
@@ -1376,32 +1390,35 @@ int mcgb_batch_autotune(mcgb_batch *b, int budget_ms, mcgb_tune *out)
     mcgb_tune best{};
     best.ms = 1e30;
     auto t_start = std::chrono::steady_clock::now();
-    const int blocks[] = {128, 256, 64};
-    for (int blk : blocks) {
+    // candidates: block-sorted pools (particles per block x resident blocks per SM)
+    // and the register-resident variant (threads per block x blocks per SM)
+    std::vector<mcgb_tune> cand;
+    for (int pool : {512, 1024, 256}) {
+        int occ = std::max(1, pool_max_blocks_per_sm(pool));
+        for (int bps = occ; bps >= 1; bps = bps > 2 ? bps / 2 : bps - 1) cand.push_back({0, bps, pool, 0.0});
+    }
+    for (int blk : {128, 256}) {
         int occ = std::max(1, persistent_max_blocks_per_sm(blk));
-        for (int bps = occ; bps >= 1; bps = bps > 2 ? bps / 2 : bps - 1) {
-            mcgb_tune t{blk, bps, 1, 0.0};
-            // one warm-up, one timed
-            CKR(batch_run_runs(b, small, &t));
-            cudaEvent_t e0, e1;
-            CK(cudaEventCreate(&e0));
-            CK(cudaEventCreate(&e1));
-            CK(cudaEventRecord(e0, b->engine->stream));
-            int r = batch_run_runs(b, small, &t);
-            CK(cudaEventRecord(e1, b->engine->stream));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            CKR(r);
-            if (ms < best.ms) {
-                best = t;
-                best.ms = ms;
-            }
-            double spent = std::chrono::duration<double, std::milli>(
-                               std::chrono::steady_clock::now() - t_start).count();
-            if (budget_ms > 0 && spent > budget_ms) break;
+        cand.push_back({blk, occ, -1, 0.0});
+    }
+    for (const mcgb_tune &t : cand) {
+        // one warm-up, one timed
+        CKR(batch_run_runs(b, small, &t));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, b->engine->stream));
+        int r = batch_run_runs(b, small, &t);
+        CK(cudaEventRecord(e1, b->engine->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CKR(r);
+        if (ms < best.ms) {
+            best = t;
+            best.ms = ms;
         }
         double spent = std::chrono::duration<double, std::milli>(
                            std::chrono::steady_clock::now() - t_start).count();

@@ -110,7 +110,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     std::vector<double> s_coef, s_r2;
     std::vector<int> c_univ, c_off, c_nhs, c_fillk, c_fill, hs_surf, hs_sense;
     std::vector<double> l_x0, l_y0, l_pitch;
-    std::vector<int> l_nx, l_ny, l_uoff, l_univ;
+    std::vector<int> l_nx, l_ny, l_uoff, l_univ, l_woff;
+    std::vector<double> l_wall, l_ctr;
     std::vector<int> m_G, m_goff, m_ggoff, m_fissile;
     std::vector<double> g_sigt, g_mfp, g_nusf, g_mu, g_mufl, g_mufr, g_ps, g_stot, g_chicdf;
     std::vector<double> gg_sigs, gg_scdf;
@@ -169,6 +170,15 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
             l_ny.push_back(L.ny);
             l_uoff.push_back((int)l_univ.size());
             for (int u : L.univ) l_univ.push_back(u + univ0);
+            l_woff.push_back((int)l_wall.size());
+            for (int i = 0; i <= L.nx; i++) {
+                l_wall.push_back(L.x0 + (double)i * L.pitch);
+                l_ctr.push_back(L.x0 + ((double)i + 0.5) * L.pitch);
+            }
+            for (int i = 0; i <= L.ny; i++) {
+                l_wall.push_back(L.y0 + (double)i * L.pitch);
+                l_ctr.push_back(L.y0 + ((double)i + 0.5) * L.pitch);
+            }
         }
         nuniv += nu;
         if (!pd.ce) {
@@ -345,7 +355,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     size_t o_hssurf = S.put(hs_surf), o_hssense = S.put(hs_sense), o_hscoff = S.put(hs_coff),
            o_hscand = S.put(hs_cand), o_uoff = S.put(u_off), o_ucells = S.put(u_cells);
     size_t o_lx0 = S.put(l_x0), o_ly0 = S.put(l_y0), o_lp = S.put(l_pitch), o_lnx = S.put(l_nx),
-           o_lny = S.put(l_ny), o_luoff = S.put(l_uoff), o_luniv = S.put(l_univ);
+           o_lny = S.put(l_ny), o_luoff = S.put(l_uoff), o_luniv = S.put(l_univ),
+           o_lwoff = S.put(l_woff), o_lwall = S.put(l_wall), o_lctr = S.put(l_ctr);
     size_t o_mG = S.put(m_G), o_mgoff = S.put(m_goff), o_mggoff = S.put(m_ggoff),
            o_mfis = S.put(m_fissile);
     size_t o_sigt = S.put(g_sigt), o_mfp = S.put(g_mfp), o_nusf = S.put(g_nusf), o_mu = S.put(g_mu),
@@ -384,6 +395,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(hs_cand, int, o_hscand); P_(u_off, int, o_uoff); P_(u_cells, int, o_ucells);
     P_(l_x0, double, o_lx0); P_(l_y0, double, o_ly0); P_(l_pitch, double, o_lp);
     P_(l_nx, int, o_lnx); P_(l_ny, int, o_lny); P_(l_uoff, int, o_luoff); P_(l_univ, int, o_luniv);
+    P_(l_woff, int, o_lwoff); P_(l_wall, double, o_lwall); P_(l_ctr, double, o_lctr);
     P_(m_G, int, o_mG); P_(m_goff, int, o_mgoff); P_(m_ggoff, int, o_mggoff); P_(m_fissile, int, o_mfis);
     P_(g_sigt, double, o_sigt); P_(g_mfp, double, o_mfp); P_(g_nusf, double, o_nusf);
     P_(g_mu, double, o_mu); P_(g_mufl, double, o_mufl); P_(g_mufr, double, o_mufr);

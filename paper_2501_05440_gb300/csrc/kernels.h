@@ -35,6 +35,11 @@ void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, con
                        const RunBufs &R, const PersistentArgs &a, int grid, int block,
                        cudaStream_t st);
 int persistent_max_blocks_per_sm(int block);
+// block-sorted variant: `pool` particles per block in shared memory (256, 512, 1024)
+bool launch_pool(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                 const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st);
+int pool_max_blocks_per_sm(int pool);
+int pool_threads();
 
 // ---- end of cycle / generation --------------------------------------------
 // Exclusive scan of n counts into out; *total = sum.  scratch holds one int per

@@ -79,16 +79,18 @@ __global__ void k_ce_lookup(World W, int mat, int64_t n, const double *E, double
     if (i >= n) return;
     double e = E[i];
     int k = union_index(W, e);
-    CEXS x;
-    ce_xs(W, mat, k, e, x);
+    double sigt, nusf;
+    ce_macro(W, mat, k, e, sigt, nusf);
     int off = W.mc_off[mat], nn = W.mc_n[mat];
     double ss = 0.0, sf = 0.0;
-    for (int q = 0; q < nn && q < MAX_NUC; q++) {
-        ss = ss + W.mc_dens[off + q] * x.ss[q];
-        sf = sf + W.mc_dens[off + q] * x.sf[q];
+    for (int q = 0; q < nn; q++) {
+        double a, b, c;
+        ce_micro(W, W.mc_nuc[off + q], k, e, a, b, c);
+        ss = ss + W.mc_dens[off + q] * b;
+        sf = sf + W.mc_dens[off + q] * c;
     }
-    out[4 * i] = x.sigt;
-    out[4 * i + 1] = x.nusf;
+    out[4 * i] = sigt;
+    out[4 * i + 1] = nusf;
     out[4 * i + 2] = ss;
     out[4 * i + 3] = sf;
 }

@@ -1,0 +1,277 @@
+// kernels_pool.cu -- persistent event loop with block-sorted events.
+//
+// Each block keeps a pool of P particles in shared memory (structure of
+// arrays) and repeats: refill empty slots from the device work counter; run
+// the flight (advance) of every live particle; run the surface crossings, then
+// the collisions.  Before each phase the block builds a compacted list of the
+// slots that need it, collisions ordered by material, so that consecutive
+// threads -- whole warps -- run the same event on the same kind of data.  The
+// grid stays resident for the whole cycle; no particle state goes through HBM
+// between events.  Results do not depend on which thread runs which slot:
+// every history draws from its own random stream.
+#include "kernels.h"
+#include "steps.cuh"
+
+namespace mcgb {
+
+namespace {
+
+constexpr int POOL_T = 256;          // threads per block
+constexpr int NBUCKET = 33;          // list buckets: 0 = crossings, 1..32 = material % 32
+constexpr int SLOT_EMPTY = -2;
+
+struct Pool {
+    double *x, *y, *z, *u, *v, *w, *E, *kt, *kc;
+    unsigned long long *s;
+    int *g, *cell, *ix, *iy, *ucell, *mat, *prob, *root, *nfis, *ncoll, *ncross, *gslot, *bwhich,
+        *uk, *fate, *ev;
+    int *list;
+};
+
+__host__ __device__ constexpr size_t pool_bytes(int P) { return (size_t)P * (10 * 8 + 17 * 4); }
+
+__device__ __forceinline__ Pool carve(unsigned char *base, int P)
+{
+    Pool q;
+    double *d = reinterpret_cast<double *>(base);
+    q.x = d; q.y = d + P; q.z = d + 2 * P; q.u = d + 3 * P; q.v = d + 4 * P; q.w = d + 5 * P;
+    q.E = d + 6 * P; q.kt = d + 7 * P; q.kc = d + 8 * P;
+    q.s = reinterpret_cast<unsigned long long *>(d + 9 * P);
+    int *i = reinterpret_cast<int *>(d + 10 * P);
+    q.g = i; q.cell = i + P; q.ix = i + 2 * P; q.iy = i + 3 * P; q.ucell = i + 4 * P;
+    q.mat = i + 5 * P; q.prob = i + 6 * P; q.root = i + 7 * P; q.nfis = i + 8 * P;
+    q.ncoll = i + 9 * P; q.ncross = i + 10 * P; q.gslot = i + 11 * P; q.bwhich = i + 12 * P;
+    q.uk = i + 13 * P; q.fate = i + 14 * P; q.ev = i + 15 * P; q.list = i + 16 * P;
+    return q;
+}
+
+__device__ __forceinline__ void pool_load(const Pool &q, int i, PS &p)
+{
+    p.x = q.x[i]; p.y = q.y[i]; p.z = q.z[i]; p.u = q.u[i]; p.v = q.v[i]; p.w = q.w[i];
+    p.E = q.E[i]; p.s = q.s[i];
+    p.g = q.g[i]; p.cell = q.cell[i]; p.ix = q.ix[i]; p.iy = q.iy[i]; p.ucell = q.ucell[i];
+    p.mat = q.mat[i]; p.prob = q.prob[i]; p.root = q.root[i]; p.nfis = q.nfis[i];
+    p.ncoll = q.ncoll[i]; p.ncross = q.ncross[i]; p.fate = q.fate[i];
+}
+
+__device__ __forceinline__ void pool_store(const Pool &q, int i, const PS &p)
+{
+    q.x[i] = p.x; q.y[i] = p.y; q.z[i] = p.z; q.u[i] = p.u; q.v[i] = p.v; q.w[i] = p.w;
+    q.E[i] = p.E; q.s[i] = p.s;
+    q.g[i] = p.g; q.cell[i] = p.cell; q.ix[i] = p.ix; q.iy[i] = p.iy; q.ucell[i] = p.ucell;
+    q.mat[i] = p.mat; q.prob[i] = p.prob; q.root[i] = p.root; q.nfis[i] = p.nfis;
+    q.ncoll[i] = p.ncoll; q.ncross[i] = p.ncross; q.fate[i] = p.fate;
+}
+
+// history over: its record goes to the global slot, the pool slot becomes empty
+__device__ __forceinline__ void retire(const Pool &q, const Particles &G, int i, const PS &p)
+{
+    int j = q.gslot[i];
+    G.nfis[j] = p.nfis;
+    G.ncoll[j] = p.ncoll;
+    G.ncross[j] = p.ncross;
+    G.fate[j] = (signed char)p.fate;
+    G.s[j] = p.s;
+    G.g[j] = p.g;
+    G.kt[j] = q.kt[i];
+    G.kc[j] = q.kc[i];
+    q.fate[i] = SLOT_EMPTY;
+}
+
+// Bucketed compaction of the pool: slots with key >= 0 go to q.list, grouped
+// by key in increasing order; counts per key in cnt[NBUCKET].  All threads call.
+template <int P, class KeyFn>
+__device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, KeyFn key)
+{
+    if (threadIdx.x < NBUCKET) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < P; i += POOL_T) {
+        int k = key(i);
+        if (k >= 0) atomicAdd(hist + k, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // exclusive scan of the NBUCKET counts by one warp (bucket 32 after the loop)
+        int lane = threadIdx.x;
+        int v = hist[lane];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        int last = hist[32];
+        cnt[lane] = v;
+        hist[lane] = x - v;
+        if (lane == 31) {
+            cnt[32] = last;
+            hist[32] = x;
+            cnt[NBUCKET] = x + last;     // total
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < P; i += POOL_T) {
+        int k = key(i);
+        if (k >= 0) q.list[atomicAdd(hist + k, 1)] = i;
+    }
+    __syncthreads();
+    return cnt[NBUCKET];
+}
+
+template <int P>
+__global__ void __launch_bounds__(POOL_T, 2) k_pool(World W, Particles G, Bank Bsrc, Bank Bdst,
+                                                 RunBufs R, PersistentArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int hist[NBUCKET + 1], cnt[NBUCKET + 1];
+    __shared__ int s_base, s_take, s_exhausted;
+    const Pool q = carve(smem, P);
+    const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
+    const int rep = (int)(blockIdx.x % (unsigned)W.nrep);
+    for (int i = threadIdx.x; i < P; i += POOL_T) q.fate[i] = SLOT_EMPTY;
+    if (threadIdx.x == 0) s_exhausted = 0;
+    __syncthreads();
+    for (;;) {
+        // ---- refill empty slots from the work counter
+        if (!s_exhausted) {
+            int n_empty = build_list<P>(q, hist, cnt, [&](int i) { return q.fate[i] == SLOT_EMPTY ? 0 : -1; });
+            if (threadIdx.x == 0) {
+                int take = 0, base = 0;
+                if (n_empty > 0) {
+                    base = atomicAdd(a.work, n_empty);
+                    int64_t left = total - (int64_t)base;
+                    take = left <= 0 ? 0 : (left < n_empty ? (int)left : n_empty);
+                    if (take < n_empty) s_exhausted = 1;
+                }
+                s_base = base;
+                s_take = take;
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < s_take; k += POOL_T) {
+                int i = q.list[k];
+                int64_t j = (int64_t)s_base + k;
+                int prob = 0;
+                {
+                    int lo = 0, hi = W.nprob;
+                    while (hi - lo > 1) {
+                        int mid = (lo + hi) >> 1;
+                        if (a.gen_base[mid] <= j) lo = mid;
+                        else hi = mid;
+                    }
+                    prob = lo;
+                }
+                PS p;
+                bool ok = init_particle(W, W.prob[prob], Bsrc, p, prob, j - a.gen_base[prob], a.gen,
+                                        a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                q.gslot[i] = (int)j;
+                q.kt[i] = 0.0;
+                q.kc[i] = 0.0;
+                if (!ok) {
+                    atomicOr(R.err, ERR_SOURCE);
+                    p.fate = FATE_LOST;
+                    p.cell = 0;
+                    p.mat = 0;
+                    pool_store(q, i, p);
+                    retire(q, G, i, p);
+                } else {
+                    pool_store(q, i, p);
+                }
+            }
+            __syncthreads();
+        }
+        // ---- flights of every live particle, grouped by material
+        int n_adv = build_list<P>(q, hist, cnt, [&](int i) {
+            return q.fate[i] == FATE_ALIVE ? 1 + (q.mat[i] & 31) : -1;
+        });
+        if (n_adv == 0 && s_exhausted) break;
+        for (int k = threadIdx.x; k < n_adv; k += POOL_T) {
+            int i = q.list[k];
+            PS p;
+            pool_load(q, i, p);
+            int kind, which, uk = 0;
+            double kt = q.kt[i];
+            int ev = step_advance(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which, uk, kt);
+            q.x[i] = p.x;
+            q.y[i] = p.y;
+            q.z[i] = p.z;
+            q.s[i] = p.s;
+            q.kt[i] = kt;
+            q.ev[i] = ev | (kind << 4);
+            q.bwhich[i] = which;
+            q.uk[i] = uk;
+            if (ev == EV_DEAD) {
+                q.fate[i] = p.fate;
+                retire(q, G, i, p);
+            }
+        }
+        __syncthreads();
+        // ---- crossings (bucket 0), then collisions grouped by material
+        int n_ev = build_list<P>(q, hist, cnt, [&](int i) {
+            if (q.fate[i] != FATE_ALIVE) return -1;
+            return (q.ev[i] & 15) == EV_CROSS ? 0 : 1 + (q.mat[i] & 31);
+        });
+        int n_cross = cnt[0];
+        for (int k = threadIdx.x; k < n_ev; k += POOL_T) {
+            int i = q.list[k];
+            PS p;
+            pool_load(q, i, p);
+            int ev;
+            if (k < n_cross) {
+                ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
+            } else {
+                double kc = q.kc[i];
+                ev = step_collide(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
+                q.kc[i] = kc;
+            }
+            pool_store(q, i, p);
+            if (ev == EV_DEAD) retire(q, G, i, p);
+        }
+        __syncthreads();
+    }
+}
+
+template <int P>
+void launch_pool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                   const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
+{
+    size_t sm = pool_bytes(P);
+    cudaFuncSetAttribute(k_pool<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_pool<P><<<grid, POOL_T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
+}
+
+}  // namespace
+
+int pool_threads() { return POOL_T; }
+
+int pool_max_blocks_per_sm(int P)
+{
+    int n = 0;
+    size_t sm = pool_bytes(P);
+    switch (P) {
+    case 256:
+        cudaFuncSetAttribute(k_pool<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<256>, POOL_T, sm);
+        break;
+    case 512:
+        cudaFuncSetAttribute(k_pool<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<512>, POOL_T, sm);
+        break;
+    default:
+        cudaFuncSetAttribute(k_pool<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<1024>, POOL_T, sm);
+    }
+    return n;
+}
+
+bool launch_pool(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                 const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st)
+{
+    switch (pool) {
+    case 256: launch_pool_t<256>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 512: launch_pool_t<512>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 1024: launch_pool_t<1024>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    default: return false;
+    }
+}
+
+}  // namespace mcgb

@@ -30,11 +30,8 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     double sigt, mfp, nusf;
     if (P.ce) {
         uk = union_index(W, p.E);
-        CEXS x;
-        ce_xs(W, p.mat, uk, p.E, x);
-        sigt = x.sigt;
-        nusf = x.nusf;
-        mfp = sigt > 0.0 ? 1.0 / sigt : MCGB_INF;
+        ce_macro(W, p.mat, uk, p.E, sigt, nusf);
+        mfp = is_pos(sigt) ? 1.0 / sigt : MCGB_INF;
     } else {
         int go = __ldg(W.m_goff + p.mat) + p.g;
         sigt = __ldg(W.g_sigt + go);
@@ -42,13 +39,13 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
         mfp = __ldg(W.g_mfp + go);
     }
     uint64_t n = draw_n(p.s);
-    double dc = sigt > 0.0 ? -log_n(W, n) * mfp : MCGB_INF;
+    double dc = is_pos(sigt) ? -log_n(W, n) * mfp : MCGB_INF;
     double ds = boundary(W, p, kind, which);
-    if (dc == MCGB_INF && ds == MCGB_INF) {
+    if (is_inf(dc) && is_inf(ds)) {
         p.fate = FATE_LOST;
         return EV_DEAD;
     }
-    bool coll = dc < ds;
+    bool coll = lt_mag(dc, ds);     // both are +-0, positive or +inf
     double d = coll ? dc : ds;
     p.x = p.x + d * p.u;
     p.y = p.y + d * p.v;
@@ -99,7 +96,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         int g = p.g;
         kc = kc + __ldg(W.g_mu + go + g);
         double xi = draw(p.s);
-        int nf = (int)__ldg(W.g_mufl + go + g) + (xi <= __ldg(W.g_mufr + go + g) ? 1 : 0);
+        int nf = (int)__ldg(W.g_mufl + go + g) + (lt_mag(__ldg(W.g_mufr + go + g), xi) ? 0 : 1);
         if (REPLAY) {
             *nf_out = nf;
             p.nfis += nf;
@@ -110,7 +107,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             }
         }
         xi = draw(p.s);
-        if (xi <= __ldg(W.g_ps + go + g)) {
+        if (!lt_mag(__ldg(W.g_ps + go + g), xi)) {
             xi = draw(p.s);
             p.g = sample_cdf(W.gg_scdf + __ldg(W.m_ggoff + p.mat) + g * G, G, xi);
             iso_dir(p.s, p.u, p.v, p.w);
@@ -119,43 +116,39 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             return EV_DEAD;
         }
     } else {
-        CEXS x;
-        ce_xs(W, p.mat, uk, p.E, x);
-        kc = kc + x.nusf / x.sigt;
+        double sigt, nusf;
+        ce_macro(W, p.mat, uk, p.E, sigt, nusf);
+        kc = kc + nusf / sigt;
         int off = __ldg(W.mc_off + p.mat), n = __ldg(W.mc_n + p.mat);
-        double target = draw(p.s) * x.sigt;
+        // nuclide: first whose running sum of N_i sigma_t,i reaches xi Sigma_t (the
+        // selected nuclide's values are recomputed with the lookup's arithmetic)
+        double target = draw(p.s) * sigt;
         double cum = 0.0;
         int sel = n - 1;
-        bool found = false;
-#pragma unroll
-        for (int q = 0; q < MAX_NUC; q++) {
-            if (q < n && !found) {
-                cum = cum + __ldg(W.mc_dens + off + q) * x.st[q];
-                if (target <= cum) {
-                    sel = q;
-                    found = true;
-                }
+        double st = 0.0, ss = 0.0, sf = 0.0;
+        for (int q = 0; q < n; q++) {
+            double a, b, c;
+            ce_micro(W, __ldg(W.mc_nuc + off + q), uk, p.E, a, b, c);
+            cum = cum + __ldg(W.mc_dens + off + q) * a;
+            st = a;
+            ss = b;
+            sf = c;
+            if (!lt_mag(cum, target)) {
+                sel = q;
+                break;
             }
         }
-        double st = 0.0, ss = 0.0, sf = 0.0;
-#pragma unroll
-        for (int q = 0; q < MAX_NUC; q++)
-            if (q == sel) {
-                st = x.st[q];
-                ss = x.ss[q];
-                sf = x.sf[q];
-            }
         int nuc = __ldg(W.mc_nuc + off + sel);
         double mu = __ldg(W.n_nu + nuc) * sf / st;
         double fl = floor(mu);
         double xi = draw(p.s);
-        int nf = (int)fl + (xi <= mu - fl ? 1 : 0);
+        int nf = (int)fl + (lt_mag(mu - fl, xi) ? 0 : 1);
         for (int k = 0; k < nf; k++) {
             bank_push(B, R.bank_n, R.err, p, slot);
             p.nfis++;
         }
         xi = draw(p.s);
-        if (xi * st <= ss) {
+        if (!lt_mag(ss, xi * st)) {
             p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);
         } else {
             p.fate = FATE_ABSORBED;

@@ -18,6 +18,25 @@ namespace mcgb {
 
 #define MCGB_INF __longlong_as_double(0x7FF0000000000000LL)
 
+// Comparisons done on the bit patterns (integer pipe) instead of the FP64 pipe.
+// Exact for all non-NaN values: is_neg(x) == (x < 0.0), is_pos(x) == (x > 0.0);
+// lt_mag(a, b) == (a < b) when a and b are +-0, positive or +inf.
+__device__ __forceinline__ bool is_neg(double x)
+{
+    long long b = __double_as_longlong(x);
+    return b < 0 && b != (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool is_pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool lt_mag(double a, double b)
+{
+    return (__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFLL) <
+           (__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ bool is_inf(double x)
+{
+    return __double_as_longlong(x) == 0x7FF0000000000000LL;
+}
+
 // ---------------------------------------------------------------------------
 // Random numbers (Sec. 1: replicable on CPU and GPU).  63-bit LCG
 // s' = (g s + 1) mod 2^63, g = 2806196910506780709; stream i starts at
@@ -113,38 +132,47 @@ __device__ __forceinline__ double log_n(const World &W, uint64_t n)
 // Isotropic direction by Marsaglia's disk rejection (no trigonometry).
 __device__ __forceinline__ void iso_dir(uint64_t &s, double &u, double &v, double &w)
 {
-    for (int k = 0; k < 64; k++) {
-        double a = draw_sym(s);
-        double b = draw_sym(s);
-        double S = a * a + b * b;
-        if (S < 1.0) {
-            double t = 2.0 * sqrt(1.0 - S);
-            u = a * t;
-            v = b * t;
-            w = 1.0 - 2.0 * S;
-            return;
-        }
+    // the loop repeats only the rejection test; the accepted point is used once
+    double a, b, S;
+    int k = 0;
+    do {
+        a = draw_sym(s);
+        b = draw_sym(s);
+        S = a * a + b * b;
+        k++;
+    } while (!lt_mag(S, 1.0) && k < 64);
+    if (!lt_mag(S, 1.0)) {
+        u = 0.0;
+        v = 0.0;
+        w = 1.0;
+        return;
     }
-    u = 0.0;
-    v = 0.0;
-    w = 1.0;
+    double t = 2.0 * sqrt(1.0 - S);
+    u = a * t;
+    v = b * t;
+    w = 1.0 - 2.0 * S;
 }
 
 // Azimuth as (cos, sin) of the doubled angle of a point uniform in the unit disk.
 __device__ __forceinline__ void azimuth(uint64_t &s, double &cphi, double &sphi)
 {
-    for (int k = 0; k < 64; k++) {
-        double a = draw_sym(s);
-        double b = draw_sym(s);
-        double r2 = a * a + b * b;
-        if (r2 <= 1.0 && r2 > 0.0) {
-            cphi = (a * a - b * b) / r2;
-            sphi = 2.0 * a * b / r2;
-            return;
-        }
+    double a, b, r2;
+    int k = 0;
+    bool ok;
+    do {
+        a = draw_sym(s);
+        b = draw_sym(s);
+        r2 = a * a + b * b;
+        ok = !lt_mag(1.0, r2) && is_pos(r2);
+        k++;
+    } while (!ok && k < 64);
+    if (!ok) {
+        cphi = 1.0;
+        sphi = 0.0;
+        return;
     }
-    cphi = 1.0;
-    sphi = 0.0;
+    cphi = (a * a - b * b) / r2;
+    sphi = 2.0 * a * b / r2;
 }
 
 // Rotate (u,v,w) by polar cosine mu with a sampled azimuth (polar axis z, or x near |w| = 1).
@@ -153,7 +181,7 @@ __device__ __forceinline__ void rotate(double mu, uint64_t &s, double &u, double
     double cphi, sphi;
     azimuth(s, cphi, sphi);
     double st2 = 1.0 - mu * mu;
-    double st = sqrt(st2 > 0.0 ? st2 : 0.0);
+    double st = sqrt(is_pos(st2) ? st2 : 0.0);
     double u0 = u, v0 = v, w0 = w;
     double ww = 1.0 - w0 * w0;
     if (ww > 1.0e-10) {
@@ -183,7 +211,7 @@ __device__ __forceinline__ double elastic(double E, double A, uint64_t &s, doubl
     if (mul > 1.0) mul = 1.0;
     if (mul < -1.0) mul = -1.0;
     rotate(mul, s, u, v, w);
-    return Ep < E_MIN ? E_MIN : Ep;
+    return lt_mag(Ep, E_MIN) ? E_MIN : Ep;
 }
 
 // Maxwellian fission spectrum (T = 1.33 MeV): E = -T (ln xi1 + ln xi2 a^2/(a^2+b^2)),
@@ -194,29 +222,36 @@ __device__ __forceinline__ double maxwell(const World &W, uint64_t &s)
         double L1 = log_n(W, draw_n(s));
         double L2 = log_n(W, draw_n(s));
         double a = 1.0, r2 = 1.0;
-        for (int t = 0; t < 64; t++) {
-            double aa = draw_sym(s);
-            double bb = draw_sym(s);
-            double rr = aa * aa + bb * bb;
-            if (rr <= 1.0 && rr > 0.0) {
+        {
+            double aa, bb, rr;
+            int t = 0;
+            bool ok;
+            do {
+                aa = draw_sym(s);
+                bb = draw_sym(s);
+                rr = aa * aa + bb * bb;
+                ok = !lt_mag(1.0, rr) && is_pos(rr);
+                t++;
+            } while (!ok && t < 64);
+            if (ok) {
                 a = aa;
                 r2 = rr;
-                break;
             }
         }
         double c2 = a * a / r2;
         double E = -1.33e6 * (L1 + L2 * c2);
-        if (E <= E_MAX) return E < E_MIN ? E_MIN : E;
+        if (!lt_mag(E_MAX, E)) return lt_mag(E, E_MIN) ? E_MIN : E;
     }
     return E_MAX;
 }
 
-// First k with xi <= cdf[k] (cdf ends with exactly 1).
+// First k with xi <= cdf[k] (cdf nondecreasing, ending with exactly 1): the count
+// of entries below xi, taken over the whole table (no divergent early exit).
 __device__ __forceinline__ int sample_cdf(const double *cdf, int n, double xi)
 {
-    for (int k = 0; k < n; k++)
-        if (xi <= __ldg(cdf + k)) return k;
-    return n - 1;
+    int k = 0;
+    for (int q = 0; q < n - 1; q++) k += lt_mag(__ldg(cdf + q), xi) ? 1 : 0;
+    return k;
 }
 
 // ---------------------------------------------------------------------------
@@ -281,9 +316,9 @@ __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, 
             dn = __ldg(c) * u + __ldg(c + 1) * v + __ldg(c + 2) * w;
             f = __ldg(c) * x + __ldg(c + 1) * y + __ldg(c + 2) * z - __ldg(c + 3);
         }
-        if ((sense > 0 && dn < 0.0) || (sense < 0 && dn > 0.0)) {
+        if ((sense > 0 && is_neg(dn)) || (sense < 0 && is_pos(dn))) {
             t = -f / dn;
-            return t < 0.0 ? 0.0 : t;
+            return is_neg(t) ? 0.0 : t;
         }
         return MCGB_INF;
     }
@@ -299,17 +334,29 @@ __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, 
         b = dx * u + dy * v + dz * w;
         cc = dx * dx + dy * dy + dz * dz - __ldg(W.s_r2 + sid);
     }
-    if (a == 0.0) return MCGB_INF;
+    if (!is_pos(a)) return MCGB_INF;
     double disc = b * b - a * cc;
+    // one square root and one division for every case (inside: the far root by
+    // the cancellation-free form chosen by the sign of b; outside: the near root)
+    double num, den;
     if (sense < 0) {
-        if (disc < 0.0) disc = 0.0;
-        if (b <= 0.0) t = (-b + sqrt(disc)) / a;
-        else t = -cc / (b + sqrt(disc));
-        return t < 0.0 ? 0.0 : t;
+        if (is_neg(disc)) disc = 0.0;
+        double sq = sqrt(disc);
+        if (!is_pos(b)) {
+            num = -b + sq;
+            den = a;
+        } else {
+            num = -cc;
+            den = b + sq;
+        }
+    } else {
+        if (!is_neg(b) || is_neg(disc)) return MCGB_INF;
+        double sq = sqrt(disc);
+        num = cc;
+        den = -b + sq;
     }
-    if (b >= 0.0 || disc < 0.0) return MCGB_INF;
-    t = cc / (-b + sqrt(disc));
-    return t < 0.0 ? 0.0 : t;
+    t = num / den;
+    return is_neg(t) ? 0.0 : t;
 }
 
 // Does cell `ci` hold the point?  Sense from the sign of f; exactly on a surface
@@ -327,9 +374,9 @@ __device__ __forceinline__ bool cell_holds(const World &W, int ci, double x, dou
             sense = forced_sense;
         } else {
             double f = surf_f(W, sid, x, y, z);
-            if (f > 0.0) sense = 1;
-            else if (f < 0.0) sense = -1;
-            else sense = surf_gdot(W, sid, x, y, z, u, v, w) >= 0.0 ? 1 : -1;
+            if (is_pos(f)) sense = 1;
+            else if (is_neg(f)) sense = -1;
+            else sense = is_neg(surf_gdot(W, sid, x, y, z, u, v, w)) ? -1 : 1;
         }
         if (sense != __ldg(W.hs_sense + off + h)) return false;
     }
@@ -369,9 +416,10 @@ __device__ __forceinline__ int relocate(const World &W, int U, int hs, double x,
 __device__ __forceinline__ void local_xy(const World &W, int L, int ix, int iy, double x, double y,
                                          double &xl, double &yl)
 {
-    double p = __ldg(W.l_pitch + L);
-    xl = x - (__ldg(W.l_x0 + L) + ((double)ix + 0.5) * p);
-    yl = y - (__ldg(W.l_y0 + L) + ((double)iy + 0.5) * p);
+    // x - (x0 + (ix + 0.5) pitch), the centre precomputed with that expression
+    const double *ctr = W.l_ctr + __ldg(W.l_woff + L);
+    xl = x - __ldg(ctr + ix);
+    yl = y - __ldg(ctr + __ldg(W.l_nx + L) + 1 + iy);
 }
 
 __device__ __forceinline__ void lattice_index(const World &W, int L, double x, double y, int &ix,
@@ -429,7 +477,7 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
     for (int h = 0; h < nh; h++) {
         double t = surf_dist(W, __ldg(W.hs_surf + off + h), __ldg(W.hs_sense + off + h), p.x, p.y,
                              p.z, p.u, p.v, p.w);
-        if (t < best) {
+        if (lt_mag(t, best)) {
             best = t;
             kind = B_ROOT;
             which = off + h;
@@ -437,23 +485,28 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
     }
     if (__ldg(W.c_fillk + p.cell) == FILL_LAT) {
         int L = __ldg(W.c_fill + p.cell);
-        double x0 = __ldg(W.l_x0 + L), y0 = __ldg(W.l_y0 + L), pitch = __ldg(W.l_pitch + L);
         int nx = __ldg(W.l_nx + L), ny = __ldg(W.l_ny + L);
-        double t = MCGB_INF;
-        if (p.u > 0.0 && p.ix < nx - 1) t = (x0 + (double)(p.ix + 1) * pitch - p.x) / p.u;
-        else if (p.u < 0.0 && p.ix > 0) t = (x0 + (double)p.ix * pitch - p.x) / p.u;
-        if (t < 0.0) t = 0.0;
-        if (t < best) {
-            best = t;
-            kind = B_LATX;
+        // walls x0 + i pitch, precomputed with that expression; the wall ahead is
+        // chosen first so that one division serves either direction
+        const double *xw = W.l_wall + __ldg(W.l_woff + L);
+        const double *yw = xw + nx + 1;
+        int wx = is_pos(p.u) ? (p.ix < nx - 1 ? p.ix + 1 : -1) : (is_neg(p.u) && p.ix > 0 ? p.ix : -1);
+        if (wx >= 0) {
+            double t = (__ldg(xw + wx) - p.x) / p.u;
+            if (is_neg(t)) t = 0.0;
+            if (lt_mag(t, best)) {
+                best = t;
+                kind = B_LATX;
+            }
         }
-        t = MCGB_INF;
-        if (p.v > 0.0 && p.iy < ny - 1) t = (y0 + (double)(p.iy + 1) * pitch - p.y) / p.v;
-        else if (p.v < 0.0 && p.iy > 0) t = (y0 + (double)p.iy * pitch - p.y) / p.v;
-        if (t < 0.0) t = 0.0;
-        if (t < best) {
-            best = t;
-            kind = B_LATY;
+        int wy = is_pos(p.v) ? (p.iy < ny - 1 ? p.iy + 1 : -1) : (is_neg(p.v) && p.iy > 0 ? p.iy : -1);
+        if (wy >= 0) {
+            double t = (__ldg(yw + wy) - p.y) / p.v;
+            if (is_neg(t)) t = 0.0;
+            if (lt_mag(t, best)) {
+                best = t;
+                kind = B_LATY;
+            }
         }
         double xl, yl;
         local_xy(W, L, p.ix, p.iy, p.x, p.y, xl, yl);
@@ -461,7 +514,7 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
         for (int h = 0; h < unh; h++) {
             double tt = surf_dist(W, __ldg(W.hs_surf + uoff + h), __ldg(W.hs_sense + uoff + h), xl,
                                   yl, p.z, p.u, p.v, p.w);
-            if (tt < best) {
+            if (lt_mag(tt, best)) {
                 best = tt;
                 kind = B_UNIV;
                 which = uoff + h;
@@ -507,8 +560,8 @@ __device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
         return descend(W, p, -1) ? 0 : -1;
     }
     if (kind == B_LATX || kind == B_LATY) {
-        if (kind == B_LATX) p.ix += p.u > 0.0 ? 1 : -1;
-        else p.iy += p.v > 0.0 ? 1 : -1;
+        if (kind == B_LATX) p.ix += is_pos(p.u) ? 1 : -1;
+        else p.iy += is_pos(p.v) ? 1 : -1;
         return descend(W, p, -1) ? 0 : -1;
     }
     return descend(W, p, which) ? 0 : -1;
@@ -518,47 +571,46 @@ __device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
 // Continuous-energy lookup: union-grid binary search, then each nuclide's
 // interval from the precomputed map (equal to that nuclide's own largest
 // E_j <= E); sigma = sigma_j + f (sigma_{j+1} - sigma_j), f = (E - E_j)(1/dE_j).
-struct CEXS {
-    double sigt, nusf;
-    double st[MAX_NUC], ss[MAX_NUC], sf[MAX_NUC];
-};
-
 __device__ __forceinline__ int union_index(const World &W, double E)
 {
     int lo = 0, hi = W.nunion - 1;
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
-        if (__ldg(W.Eu + mid) <= E) lo = mid;
+        if (!lt_mag(E, __ldg(W.Eu + mid))) lo = mid;
         else hi = mid;
     }
     return lo;
 }
 
-__device__ __forceinline__ void ce_xs(const World &W, int mat, int k, double E, CEXS &x)
+// One nuclide at union interval k: sigma_t (= (s + c) + f), sigma_s, sigma_f.
+__device__ __forceinline__ void ce_micro(const World &W, int nuc, int k, double E, double &st,
+                                         double &ss, double &sf)
+{
+    int j = __ldg(W.umap + (int64_t)nuc * W.nunion + k);
+    const double2 *iv =
+        reinterpret_cast<const double2 *>(W.n_iv + 8 * ((int64_t)__ldg(W.n_ivoff + nuc) + j));
+    double2 e_inv = __ldg(iv), s = __ldg(iv + 1), c = __ldg(iv + 2), f = __ldg(iv + 3);
+    double fr = (E - e_inv.x) * e_inv.y;
+    ss = s.x + fr * s.y;
+    double sc = c.x + fr * c.y;
+    sf = f.x + fr * f.y;
+    st = ss + sc + sf;
+}
+
+// Macroscopic Sigma_t and nuSigma_f: sums of N_i sigma_i in the material's nuclide order.
+__device__ __forceinline__ void ce_macro(const World &W, int mat, int k, double E, double &sigt,
+                                         double &nusf)
 {
     int off = __ldg(W.mc_off + mat), n = __ldg(W.mc_n + mat);
-    x.sigt = 0.0;
-    x.nusf = 0.0;
-#pragma unroll
-    for (int q = 0; q < MAX_NUC; q++) {
-        if (q < n) {
-            int nuc = __ldg(W.mc_nuc + off + q);
-            double dens = __ldg(W.mc_dens + off + q);
-            int j = __ldg(W.umap + (int64_t)nuc * W.nunion + k);
-            const double2 *iv = reinterpret_cast<const double2 *>(
-                W.n_iv + 8 * ((int64_t)__ldg(W.n_ivoff + nuc) + j));
-            double2 e_inv = __ldg(iv), s = __ldg(iv + 1), c = __ldg(iv + 2), f = __ldg(iv + 3);
-            double fr = (E - e_inv.x) * e_inv.y;
-            double ss = s.x + fr * s.y;
-            double sc = c.x + fr * c.y;
-            double sf = f.x + fr * f.y;
-            double st = ss + sc + sf;
-            x.st[q] = st;
-            x.ss[q] = ss;
-            x.sf[q] = sf;
-            x.sigt = x.sigt + dens * st;
-            x.nusf = x.nusf + dens * (__ldg(W.n_nu + nuc) * sf);
-        }
+    sigt = 0.0;
+    nusf = 0.0;
+    for (int q = 0; q < n; q++) {
+        int nuc = __ldg(W.mc_nuc + off + q);
+        double dens = __ldg(W.mc_dens + off + q);
+        double st, ss, sf;
+        ce_micro(W, nuc, k, E, st, ss, sf);
+        sigt = sigt + dens * st;
+        nusf = nusf + dens * (__ldg(W.n_nu + nuc) * sf);
     }
 }
 
@@ -583,9 +635,9 @@ __device__ __forceinline__ void score(const World &W, const ProblemDev &P, const
         if (P.ce) {
             const double *ed = W.t_edges + __ldg(W.t_eoff + t);
             int ne = __ldg(W.t_nedges + t);
-            if (p.E < __ldg(ed) || p.E > __ldg(ed + ne - 1)) continue;
+            if (lt_mag(p.E, __ldg(ed)) || lt_mag(__ldg(ed + ne - 1), p.E)) continue;
             e = 0;
-            while (e + 1 < ne - 1 && __ldg(ed + e + 1) <= p.E) e++;
+            while (e + 1 < ne - 1 && !lt_mag(p.E, __ldg(ed + e + 1))) e++;
         } else {
             e = p.g;
         }

@@ -66,9 +66,13 @@ struct World {
     const int *hs_surf, *hs_sense;
     const int *hs_coff, *hs_cand;   // candidate cells across each half-space (CSR)
     const int *u_off, *u_cells;     // cells of each universe (CSR, definition order)
-    // lattices
+    // lattices; wall and centre coordinates are precomputed with the same
+    // expressions the transport would evaluate: x0 + (double)i * pitch and
+    // x0 + ((double)i + 0.5) * pitch (bit-identical, fewer FP64 instructions)
     const double *l_x0, *l_y0, *l_pitch;
     const int *l_nx, *l_ny, *l_uoff, *l_univ;
+    const int *l_woff;              // first wall entry of each lattice: nx + 1 x walls, then ny + 1 y walls
+    const double *l_wall, *l_ctr;   // per lattice: x walls, y walls; x centres, y centres (same offsets)
     // multigroup materials (per-material group count and offsets)
     const int *m_G, *m_goff, *m_ggoff, *m_fissile;
     const double *g_sigt, *g_mfp, *g_nusf, *g_mu, *g_mufl, *g_mufr, *g_ps, *g_stot, *g_chicdf;

@@ -1,0 +1,182 @@
+"""GPU checks beyond the small parity cases: derivatives, batching, autograd,
+full-size runs sampled history by history, error paths and degenerate inputs."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle
+from tests.gpu_util import assert_same_histories, gpu_run, rel_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcgb():
+    import paper_2501_05440_gb300 as m
+    m.build()
+    return m
+
+
+def _close_vec(a, b, rtol):
+    a, b = np.asarray(a, float).ravel(), np.asarray(b, float).ravel()
+    scale = max(np.abs(b).max(), 1e-300)
+    return np.all(np.abs(a - b) <= rtol * np.abs(b) + 1e-12 * scale)
+
+
+@pytest.mark.parametrize("mode,pool", [(0, 0), (1, 0), (1, -1)])
+def test_replay_derivatives_match_oracle(mcgb, mode, pool):
+    pb = W.diff_slab(n=10, shield_len=8.0)
+    n, seed, det = 4000, 77, pb["detector_cell"]
+    G, nm = pb["G"], len(pb["materials"])
+    w = np.random.default_rng(1).uniform(0.5, 2.0, G)
+    c = mcgb.load_problem(mcgb.Context(mode=mode, pool=pool), pb)
+    tally = c.forward_fixed(n, seed, det)
+    g = c.backward_fixed(w, nm)
+    o = Oracle(pb).grad(n=n, seed=seed, cell=det, weights=w)
+    assert rel_close(tally, o["tally"], 1e-9, 1e-300)
+    for key in ["sigma_t", "sigma_s", "nu_sigma_f"]:
+        assert _close_vec(g[key], o[key], 1e-8), key
+    # zero-valued parameters take no score on both sides
+    for m in range(nm):
+        zero = pb["materials"][m]["sigma_s"] == 0
+        assert np.all(g["sigma_s"][m][zero] == 0.0)
+    # a second backward with other weights on the same forward pass
+    w2 = np.ones(G)
+    g2 = c.backward_fixed(w2, nm)
+    o2 = Oracle(pb).grad(n=n, seed=seed, cell=det, weights=w2)
+    assert _close_vec(g2["sigma_t"], o2["sigma_t"], 1e-8)
+
+
+def test_absorbing_slab_derivative_closed_form_on_gpu(mcgb):
+    import math
+    sig, x, L = 0.7, 3.0, 2.0
+    pb = W.absorbing_slab_beam(sigma_t=sig, thickness=x, det_len=L)
+    c = mcgb.load_problem(mcgb.Context(mode=1), pb)
+    n = 400000
+    c.forward_fixed(n, 3, 1)
+    g = c.backward_fixed([1.0], 2)
+    exact = -x * L * math.exp(-sig * x)
+    p = math.exp(-sig * x)
+    sd = x * L * math.sqrt(p * (1 - p) / n)
+    assert abs(g["sigma_t"][0, 0] - exact) < 5 * sd
+
+
+def test_autograd_function(mcgb):
+    import torch
+
+    from paper_2501_05440_gb300.autograd import detector_tally
+    pb = W.diff_slab(n=10, shield_len=8.0)
+    n, seed, det = 3000, 5, pb["detector_cell"]
+    st = torch.tensor(np.array([m["sigma_t"] for m in pb["materials"]]), requires_grad=True)
+    ss = torch.tensor(np.array([m["sigma_s"] for m in pb["materials"]]), requires_grad=True)
+    nf = torch.tensor(np.array([m["nu_sigma_f"] for m in pb["materials"]]), requires_grad=True)
+    y = detector_tally(pb, st, ss, nf, n, seed, det)
+    c = torch.linspace(0.5, 1.5, pb["G"], dtype=torch.float64)
+    (y * c).sum().backward()
+    o = Oracle(pb).grad(n=n, seed=seed, cell=det, weights=c.numpy())
+    assert rel_close(y.detach().numpy(), o["tally"], 1e-9, 1e-300)
+    assert _close_vec(st.grad.numpy(), o["sigma_t"], 1e-8)
+    assert _close_vec(ss.grad.numpy(), o["sigma_s"], 1e-8)
+    assert _close_vec(nf.grad.numpy(), o["nu_sigma_f"], 1e-8)
+
+
+@pytest.mark.parametrize("pool", [0, -1])
+def test_batch_equals_standalone_runs(mcgb, pool):
+    probs = W.batch_boxes(nproblems=6, nmin=300, nmax=4000)
+    b = mcgb.Batch(pool=pool)
+    ctxs = []
+    for p in probs:
+        c = mcgb.load_problem(mcgb.Context(), p)
+        ctxs.append(c)
+        b.add_problem(c, p["run"]["n"], p["run"]["batches"], p["run"]["seed"])
+    b.run()
+    for i, (c, p) in enumerate(zip(ctxs, probs)):
+        c.run()
+        bm, bs = b.tally(i)
+        cm, cs = c.get_tally()
+        om, osd = Oracle(p).run().tally()
+        assert rel_close(bm, cm, 1e-9, 1e-300) and rel_close(bm, om, 1e-9, 1e-300), i
+    cnt = b.counters()
+    assert cnt["histories"] >= sum(p["run"]["n"] for p in probs)
+
+
+def test_batch_autotune_and_cache(mcgb, tmp_path, monkeypatch):
+    probs = W.batch_boxes(nproblems=4, nmin=300, nmax=2000)
+    b = mcgb.Batch()
+    for p in probs:
+        c = mcgb.load_problem(mcgb.Context(), p)
+        b.add_problem(c, p["run"]["n"], p["run"]["batches"], p["run"]["seed"])
+    t = b.autotune(budget_ms=3000)
+    assert t["pool"] in (-1, 256, 512, 1024) and t["blocks_per_sm"] >= 1 and t["ms"] > 0
+    t2 = b.autotune(budget_ms=3000)      # served from the cache
+    assert t2 == t
+    b.run(t)
+
+
+@pytest.mark.parametrize("name", ["lattice", "ce"])
+def test_full_size_first_cycle_sampled(mcgb, name):
+    """Full configuration size (1e6 particles), first cycle: sampled histories
+    recomputed one by one by the oracle must be identical."""
+    pb = W.c5g7_like_lattice(n=1_000_000, inactive=0, active=1) if name == "lattice" else \
+        W.ce_pin_cell(n=1_000_000, inactive=0, active=1)
+    c = gpu_run(pb, mode=1)
+    h = c.get_histories()
+    assert len(h["n_coll"]) == 1_000_000
+    idx = np.sort(np.random.default_rng(3).choice(1_000_000, 1500 if name == "lattice" else 400,
+                                                  replace=False))
+    ho = Oracle(pb).histories_by_index(idx)
+    assert_same_histories({k: v[idx] for k, v in h.items()}, ho)
+    # properties at full size: the bank holds exactly the sites the histories counted
+    assert int(h["n_fis"].sum()) == c.get_cycle_k(1)[2][0]
+    assert np.all(h["fate"] >= 0)
+
+
+def test_error_paths(mcgb):
+    # bank overflow is reported, not written out of bounds
+    pb = W.pin_cell_mg(n=5000, inactive=1, active=1)
+    c = mcgb.load_problem(mcgb.Context(mode=1, bank_factor=0.01), pb)
+    with pytest.raises(mcgb.McgbError) as e:
+        c.run()
+    assert e.value.code == -5
+    # a gap in the geometry loses particles
+    gap = W.pin_cell_mg(n=2000, inactive=0, active=1)
+    gap["cells"] = gap["cells"][:1]          # drop the moderator cell
+    gap["source"]["box"] = [-0.3, 0.3, -0.3, 0.3, 0.0, 0.0]
+    c = mcgb.load_problem(mcgb.Context(), gap)
+    with pytest.raises(mcgb.McgbError) as e:
+        c.run()
+    assert e.value.code == -6
+    # no fissile cell for a fissile-only source
+    nf = W.pin_cell_mg(n=100, inactive=0, active=1)
+    for m in nf["materials"]:
+        m["nu_sigma_f"] = np.zeros(nf["G"])
+    c = mcgb.load_problem(mcgb.Context(), nf)
+    with pytest.raises(mcgb.McgbError) as e:
+        c.run()
+    assert e.value.code == -2
+    # invalid arguments
+    c = mcgb.Context()
+    with pytest.raises(mcgb.McgbError) as e:
+        c.add_surface(9, [0.0], 0)
+    assert e.value.code == -1
+    with pytest.raises(mcgb.McgbError) as e:
+        mcgb.Context(pool=300)
+    assert e.value.code == -1
+    c = mcgb.load_problem(mcgb.Context(), W.pin_cell_mg(n=10))
+    with pytest.raises(mcgb.McgbError) as e:
+        c.run_eigenvalue(-5, 1, 1, 1)
+    assert e.value.code == -1
+
+
+def test_degenerate_sizes(mcgb):
+    for mode in (0, 1):
+        pb = W.pin_cell_mg(n=1, inactive=0, active=2)
+        c = gpu_run(pb, mode=mode)
+        o = Oracle(pb).run()
+        assert c.get_cycle_k(2)[2].tolist() == o.cycle_k(2)[2].tolist()
+        assert_same_histories(c.get_histories(), o.histories())
+    # no tallies at all
+    pb = W.pin_cell_mg(n=500, inactive=0, active=2)
+    pb["tallies"] = []
+    c = gpu_run(pb, mode=1)
+    assert c.get_k()["k"] > 0

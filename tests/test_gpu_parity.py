@@ -91,9 +91,15 @@ def test_ce_lookup_bit_exact(mcgb):
             assert np.array_equal(out[i], o.ce_lookup(mat, float(E[i])))
 
 
-def _eigen_parity(mcgb, pb, mode):
+# execution variants: (mode, pool): one kernel per event; persistent with
+# block-sorted pools of 512 (default), 256 or 1024 particles; register-resident
+VARIANTS = [(0, 0), (1, 0), (1, 256), (1, 1024), (1, -1)]
+FEW = [(0, 0), (1, 0), (1, -1)]
+
+
+def _eigen_parity(mcgb, pb, mode, pool=0):
     ncyc = pb["run"]["inactive"] + pb["run"]["active"]
-    c = gpu_run(pb, mode=mode)
+    c = gpu_run(pb, mode=mode, pool=pool)
     o = oracle_run(pb)
     gk, gc, gm = c.get_cycle_k(ncyc)
     ok, oc, om = o.cycle_k(ncyc)
@@ -117,23 +123,23 @@ def _eigen_parity(mcgb, pb, mode):
     return c, o
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_pin_cell_eigen_parity(mcgb, mode):
-    _eigen_parity(mcgb, W.pin_cell_mg(n=3000, inactive=3, active=5), mode)
+@pytest.mark.parametrize("mode,pool", VARIANTS)
+def test_pin_cell_eigen_parity(mcgb, mode, pool):
+    _eigen_parity(mcgb, W.pin_cell_mg(n=3000, inactive=3, active=5), mode, pool)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_lattice_eigen_parity(mcgb, mode):
-    _eigen_parity(mcgb, W.c5g7_like_lattice(n=4000, inactive=2, active=3), mode)
+@pytest.mark.parametrize("mode,pool", FEW)
+def test_lattice_eigen_parity(mcgb, mode, pool):
+    _eigen_parity(mcgb, W.c5g7_like_lattice(n=4000, inactive=2, active=3), mode, pool)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_ce_pin_eigen_parity(mcgb, mode):
-    _eigen_parity(mcgb, W.ce_pin_cell(n=600, inactive=1, active=2, npts=5000, nres=40), mode)
+@pytest.mark.parametrize("mode,pool", FEW)
+def test_ce_pin_eigen_parity(mcgb, mode, pool):
+    _eigen_parity(mcgb, W.ce_pin_cell(n=600, inactive=1, active=2, npts=5000, nres=40), mode, pool)
 
 
-def _fixed_parity(mcgb, pb, mode):
-    c = gpu_run(pb, mode=mode)
+def _fixed_parity(mcgb, pb, mode, pool=0):
+    c = gpu_run(pb, mode=mode, pool=pool)
     o = oracle_run(pb)
     assert_same_histories(c.get_histories(), o.histories())
     gb, ob = c.get_bank(), o.bank()
@@ -148,15 +154,15 @@ def _fixed_parity(mcgb, pb, mode):
         assert cg[key] == co[key], key
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_slab_fixed_source_parity(mcgb, mode):
-    _fixed_parity(mcgb, W.diff_slab(n=5000, batches=10), mode)
+@pytest.mark.parametrize("mode,pool", FEW)
+def test_slab_fixed_source_parity(mcgb, mode, pool):
+    _fixed_parity(mcgb, W.diff_slab(n=5000, batches=10), mode, pool)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_box_fixed_source_parity(mcgb, mode):
+@pytest.mark.parametrize("mode,pool", FEW)
+def test_box_fixed_source_parity(mcgb, mode, pool):
     for pb in W.batch_boxes(nproblems=4, nmin=500, nmax=3000)[:4]:
-        _fixed_parity(mcgb, pb, mode)
+        _fixed_parity(mcgb, pb, mode, pool)
 
 
 def test_one_collision_and_absorber_parity(mcgb):
