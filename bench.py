@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--impl", default="mcgb", choices=["mcgb", "reference"])
     ap.add_argument("--n", type=int, default=N_PER_CYCLE, help="particles per cycle")
     ap.add_argument("--quick", action="store_true", help="headline leg only")
+    ap.add_argument("--pool", type=int, default=0,
+                    help="persistent kernel variant (particles per warp/block in shared memory)")
+    ap.add_argument("--graphs", type=int, default=0, help="0: cycles as CUDA graphs, -1: launches")
     return ap.parse_args()
 
 
@@ -153,7 +156,8 @@ class ClockSampler:
 def headline(m, W, torch, args, rank, pg):
     """Persistent form: K timed cycles after W warm-up cycles."""
     pb = W.c5g7_like_lattice(seed=1 + rank, n=args.n)
-    c = m.Context(device=int(os.environ.get("LOCAL_RANK", "0")), mode=m.MODE_PERSISTENT)
+    c = m.Context(device=int(os.environ.get("LOCAL_RANK", "0")), mode=m.MODE_PERSISTENT,
+                  pool=args.pool, graphs=args.graphs)
     c.set_stream(torch.cuda.current_stream().cuda_stream)
     m.load_problem(c, pb)
     n = args.n
@@ -308,7 +312,7 @@ def run_mcgb(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles_per_cycle": h["n"], "step": "one power-iteration cycle",
-                   "mode": "persistent", "l2": "inputs larger than L2 (particle state and fission "
+                   "mode": "persistent", "pool": args.pool, "graphs": args.graphs == 0, "l2": "inputs larger than L2 (particle state and fission "
                    "banks ~0.5 GB per GPU)", "parallelism": f"replicas x{world}"},
         "events_per_s": h["events_per_cycle"] * world / (ms_max / 1e3 / args.steps),
         "k": h["k"]["k"], "k_sd": h["k"]["k_sd"],

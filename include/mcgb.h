@@ -77,9 +77,15 @@ typedef struct {
     int record_histories;   /* keep per-history records of the last cycle / generation 0 */
     double bank_factor;     /* fission bank capacity as a multiple of N (default 3) */
     int max_iterations;     /* event-mode iteration limit per cycle (default 1e7) */
-    int pool;               /* persistent mode: particles per block held in shared memory
-                               and run event by event in sorted lists (256, 512 or 1024;
-                               0 = 512), or -1 for one particle per thread in registers */
+    int pool;               /* persistent mode: particles held in shared memory and run
+                               event type by event type from sorted lists: 256, 512 or
+                               1024 per 256-thread block; 2256 or 2512 for 256 or 512 per
+                               128-thread block; 32, 64 or 128 per warp (warp-level
+                               lists, no block barriers); 0 = default; -1 = one particle
+                               per thread in registers */
+    int graphs;             /* persistent mode: run every eigenvalue cycle after the first
+                               as one CUDA graph launch, with no host synchronisation
+                               between cycles (0 = on, -1 = off) */
 } mcgb_opts;
 
 /* Event and history counters of the last run. */

@@ -81,7 +81,8 @@ static double draw(uint64_t *s) { return (double)draw_n(s) * 0x1p-53; }
  * floating-point arithmetic", ACM TOMS 1990): n = 2^e m, m in [1,2); c_j =
  * 1 + j/256 from the top 8 fraction bits; r = (m - c_j) (1/c_j);
  * ln xi = (e - 53) ln2 + ln c_j + log1p(r) with log1p by its Taylor series to
- * r^6.  ln c_j comes from the series ln c = 2 atanh((c-1)/(c+1)).              */
+ * r^6 (Horner with fused multiply-adds).  ln c_j comes from the series
+ * ln c = 2 atanh((c-1)/(c+1)).                                                */
 static double LOG_TAB[256], RINV_TAB[256];
 static int log_ready;
 static const double LN2 = 0x1.62e42fefa39efp-1;
@@ -124,11 +125,11 @@ static double log_n(uint64_t n)
     double c = 1.0 + (double)j / 256.0;
     double r = (m - c) * RINV_TAB[j];
     double q = -1.0 / 6.0;
-    q = q * r + 1.0 / 5.0;
-    q = q * r + -0.25;
-    q = q * r + 1.0 / 3.0;
-    q = q * r + -0.5;
-    q = q * r + 1.0;
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    q = fma(q, r, 1.0);
     double p = q * r;
     return (double)(e - 53) * LN2 + (LOG_TAB[j] + p);
 }
@@ -149,7 +150,7 @@ static void iso_dir(uint64_t *s, double *u, double *v, double *w)
     for (int k = 0; k < 64; k++) {
         double a = 2.0 * draw(s) - 1.0;
         double b = 2.0 * draw(s) - 1.0;
-        double S = a * a + b * b;
+        double S = fma(a, a, b * b);
         if (S < 1.0) {
             double t = 2.0 * sqrt(1.0 - S);
             *u = a * t;
@@ -175,9 +176,9 @@ static void azimuth(uint64_t *s, double *cphi, double *sphi)
     for (int k = 0; k < 64; k++) {
         double a = 2.0 * draw(s) - 1.0;
         double b = 2.0 * draw(s) - 1.0;
-        double r2 = a * a + b * b;
+        double r2 = fma(a, a, b * b);
         if (r2 <= 1.0 && r2 > 0.0) {
-            *cphi = (a * a - b * b) / r2;
+            *cphi = fma(a, a, -(b * b)) / r2;
             *sphi = 2.0 * a * b / r2;
             return;
         }
@@ -251,7 +252,7 @@ static double maxwell(uint64_t *s)
         for (int t = 0; t < 64; t++) {
             double aa = 2.0 * draw(s) - 1.0;
             double bb = 2.0 * draw(s) - 1.0;
-            double rr = aa * aa + bb * bb;
+            double rr = fma(aa, aa, bb * bb);
             if (rr <= 1.0 && rr > 0.0) { a = aa; r2 = rr; break; }
         }
         double c2 = a * a / r2;
@@ -590,11 +591,11 @@ static double surf_f(const Surface *s, double x, double y, double z)
     case ORC_PLANE: return s->c[0] * x + s->c[1] * y + s->c[2] * z - s->c[3];
     case ORC_CYLZ: {
         double dx = x - s->c[0], dy = y - s->c[1];
-        return dx * dx + dy * dy - s->r2;
+        return fma(dx, dx, dy * dy) - s->r2;
     }
     default: {
         double dx = x - s->c[0], dy = y - s->c[1], dz = z - s->c[2];
-        return dx * dx + dy * dy + dz * dz - s->r2;
+        return fma(dx, dx, fma(dy, dy, dz * dz)) - s->r2;
     }
     }
 }
@@ -618,23 +619,27 @@ static double surf_gdot(const Surface *s, double x, double y, double z, double u
  * rules): the root is chosen from the sense, not from evaluating the position,
  * so a particle sitting on a surface it just crossed never re-hits it; roots
  * use the cancellation-free quadratic forms; a negative root from round-off is
- * taken as 0.                                                                */
+ * taken as 0.  Reading: axis planes (and lattice walls) use the direction's
+ * reciprocal, rounded once whenever the direction is set, so that
+ * t = (x0 - x) (1/u); quadratic terms are evaluated with fused multiply-adds. */
 static double surf_dist(const Surface *s, int sense, double x, double y, double z, double u,
-                        double v, double w)
+                        double v, double w, double iu, double iv, double iw)
 {
     double t;
     if (s->type <= ORC_PLANE) {
-        double dn, f;
+        double dn, f, inv;
         switch (s->type) {
-        case ORC_PX: dn = u; f = x - s->c[0]; break;
-        case ORC_PY: dn = v; f = y - s->c[0]; break;
-        case ORC_PZ: dn = w; f = z - s->c[0]; break;
+        case ORC_PX: dn = u; f = x - s->c[0]; inv = iu; break;
+        case ORC_PY: dn = v; f = y - s->c[0]; inv = iv; break;
+        case ORC_PZ: dn = w; f = z - s->c[0]; inv = iw; break;
         default:
             dn = s->c[0] * u + s->c[1] * v + s->c[2] * w;
             f = s->c[0] * x + s->c[1] * y + s->c[2] * z - s->c[3];
+            inv = 0.0;
         }
         if ((sense > 0 && dn < 0.0) || (sense < 0 && dn > 0.0)) {
-            t = -f / dn;
+            /* axis planes use the direction's reciprocal, other planes divide */
+            t = s->type == ORC_PLANE ? -f / dn : -f * inv;
             return t < 0.0 ? 0.0 : t;
         }
         return INF;
@@ -642,17 +647,17 @@ static double surf_dist(const Surface *s, int sense, double x, double y, double 
     double a, b, cc;
     if (s->type == ORC_CYLZ) {
         double dx = x - s->c[0], dy = y - s->c[1];
-        a = u * u + v * v;
-        b = dx * u + dy * v;
-        cc = dx * dx + dy * dy - s->r2;
+        a = fma(u, u, v * v);
+        b = fma(dx, u, dy * v);
+        cc = fma(dx, dx, dy * dy) - s->r2;
     } else {
         double dx = x - s->c[0], dy = y - s->c[1], dz = z - s->c[2];
-        a = u * u + v * v + w * w;
-        b = dx * u + dy * v + dz * w;
-        cc = dx * dx + dy * dy + dz * dz - s->r2;
+        a = fma(u, u, fma(v, v, w * w));
+        b = fma(dx, u, fma(dy, v, dz * w));
+        cc = fma(dx, dx, fma(dy, dy, dz * dz)) - s->r2;
     }
     if (a == 0.0) return INF;
-    double disc = b * b - a * cc;
+    double disc = fma(b, b, -(a * cc));
     if (sense < 0) {
         if (disc < 0.0) disc = 0.0;
         if (b <= 0.0) t = (-b + sqrt(disc)) / a;
@@ -716,6 +721,7 @@ static int locate_univ(const orc_ctx *c, int U, double x, double y, double z, do
 
 typedef struct {
     double x, y, z, u, v, w, E;
+    double iu, iv, iw;           /* 1/u, 1/v, 1/w, rounded when the direction is set */
     int g;
     uint64_t s;
     int cell, ix, iy, ucell, mat;
@@ -725,6 +731,13 @@ typedef struct {
 
 /* history fates */
 enum { FATE_ABSORBED = 0, FATE_LEAKED = 1, FATE_CUT = 2, FATE_LOST = 3, FATE_CAPPED = 4 };
+
+static void set_recip(Particle *p)
+{
+    p->iu = 1.0 / p->u;
+    p->iv = 1.0 / p->v;
+    p->iw = 1.0 / p->w;
+}
 
 static void local_xy(const Lattice *L, int ix, int iy, double x, double y, double *xl, double *yl)
 {
@@ -786,19 +799,19 @@ static double boundary(const orc_ctx *c, const Particle *p, int *kind, int *whic
     const Cell *rc = &c->cell[p->cell];
     for (int h = 0; h < rc->nhs; h++) {
         double t = surf_dist(&c->surf[c->hs_surf[rc->off + h]], c->hs_sense[rc->off + h], p->x,
-                             p->y, p->z, p->u, p->v, p->w);
+                             p->y, p->z, p->u, p->v, p->w, p->iu, p->iv, p->iw);
         if (t < best) { best = t; *kind = B_ROOT; *which = rc->off + h; }
     }
     if (rc->fill_kind == ORC_FILL_LATTICE) {
         const Lattice *L = &c->lat[rc->fill];
         double t = INF;
-        if (p->u > 0.0 && p->ix < L->nx - 1) t = (L->x0 + (double)(p->ix + 1) * L->pitch - p->x) / p->u;
-        else if (p->u < 0.0 && p->ix > 0) t = (L->x0 + (double)p->ix * L->pitch - p->x) / p->u;
+        if (p->u > 0.0 && p->ix < L->nx - 1) t = (L->x0 + (double)(p->ix + 1) * L->pitch - p->x) * p->iu;
+        else if (p->u < 0.0 && p->ix > 0) t = (L->x0 + (double)p->ix * L->pitch - p->x) * p->iu;
         if (t < 0.0) t = 0.0;
         if (t < best) { best = t; *kind = B_LATX; }
         t = INF;
-        if (p->v > 0.0 && p->iy < L->ny - 1) t = (L->y0 + (double)(p->iy + 1) * L->pitch - p->y) / p->v;
-        else if (p->v < 0.0 && p->iy > 0) t = (L->y0 + (double)p->iy * L->pitch - p->y) / p->v;
+        if (p->v > 0.0 && p->iy < L->ny - 1) t = (L->y0 + (double)(p->iy + 1) * L->pitch - p->y) * p->iv;
+        else if (p->v < 0.0 && p->iy > 0) t = (L->y0 + (double)p->iy * L->pitch - p->y) * p->iv;
         if (t < 0.0) t = 0.0;
         if (t < best) { best = t; *kind = B_LATY; }
         double xl, yl;
@@ -806,7 +819,7 @@ static double boundary(const orc_ctx *c, const Particle *p, int *kind, int *whic
         const Cell *uc = &c->cell[p->ucell];
         for (int h = 0; h < uc->nhs; h++) {
             double tt = surf_dist(&c->surf[c->hs_surf[uc->off + h]], c->hs_sense[uc->off + h], xl,
-                                  yl, p->z, p->u, p->v, p->w);
+                                  yl, p->z, p->u, p->v, p->w, p->iu, p->iv, p->iw);
             if (tt < best) { best = tt; *kind = B_UNIV; *which = uc->off + h; }
         }
     }
@@ -826,9 +839,9 @@ static int cross(const orc_ctx *c, Particle *p, int kind, int which)
         if (s->bc == ORC_BC_VACUUM) return 1;
         if (s->bc == ORC_BC_REFLECT) {
             switch (s->type) {
-            case ORC_PX: p->u = -p->u; break;
-            case ORC_PY: p->v = -p->v; break;
-            case ORC_PZ: p->w = -p->w; break;
+            case ORC_PX: p->u = -p->u; p->iu = -p->iu; break;
+            case ORC_PY: p->v = -p->v; p->iv = -p->iv; break;
+            case ORC_PZ: p->w = -p->w; p->iw = -p->iw; break;
             default: {
                 double dn = s->c[0] * p->u + s->c[1] * p->v + s->c[2] * p->w;
                 double nn = s->c[0] * s->c[0] + s->c[1] * s->c[1] + s->c[2] * s->c[2];
@@ -836,6 +849,7 @@ static int cross(const orc_ctx *c, Particle *p, int kind, int which)
                 p->u = p->u - k * s->c[0];
                 p->v = p->v - k * s->c[1];
                 p->w = p->w - k * s->c[2];
+                set_recip(p);
             }
             }
             return 0;
@@ -864,6 +878,7 @@ int orc_probe(orc_ctx *c, const double pos[3], const double dir[3], int out_path
     memset(&p, 0, sizeof p);
     p.x = pos[0]; p.y = pos[1]; p.z = pos[2];
     p.u = dir[0]; p.v = dir[1]; p.w = dir[2];
+    set_recip(&p);
     if (locate_full(c, &p) < 0) return fail(c, ORC_ELOST, "point outside geometry");
     out_path[0] = p.cell; out_path[1] = p.ix; out_path[2] = p.iy; out_path[3] = p.ucell;
     out_path[4] = p.mat;
@@ -1030,9 +1045,9 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
         if (dc == INF && ds == INF) { a->lost++; p->fate = FATE_LOST; break; }
         int coll = dc < ds;              /* ties: surface crossing */
         double d = coll ? dc : ds;
-        p->x = p->x + d * p->u;
-        p->y = p->y + d * p->v;
-        p->z = p->z + d * p->w;
+        p->x = fma(d, p->u, p->x);
+        p->y = fma(d, p->v, p->y);
+        p->z = fma(d, p->w, p->z);
         /* track-length estimators */
         for (int t = 0; t < c->nt; t++) {
             int bin, e;
@@ -1084,6 +1099,7 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
                 }
                 p->g = gp;
                 iso_dir(&p->s, &p->u, &p->v, &p->w);   /* isotropic (P0) scattering */
+                set_recip(p);
             } else {
                 if (gr) {
                     double sa = m->sigt[g] - m->stot[g];
@@ -1117,8 +1133,12 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
             for (int k = 0; k < nf; k++) { bank_push(a, p); p->nfis++; }
             /* scatter (elastic, target at rest) with probability sigma_s,i/sigma_t,i */
             xi = draw(&p->s);
-            if (xi * x.st[sel] <= x.ss[sel]) p->E = elastic(p->E, u->A, &p->s, &p->u, &p->v, &p->w);
-            else p->alive = 0;
+            if (xi * x.st[sel] <= x.ss[sel]) {
+                p->E = elastic(p->E, u->A, &p->s, &p->u, &p->v, &p->w);
+                set_recip(p);
+            } else {
+                p->alive = 0;
+            }
         }
         if (!p->alive) { p->fate = FATE_ABSORBED; break; }
         if (c->max_coll && p->ncoll >= c->max_coll) { p->alive = 0; p->fate = FATE_CUT; break; }
@@ -1170,6 +1190,7 @@ static int sample_source(const orc_ctx *c, Particle *p)
     }
     if (s->dkind == ORC_DIR_BEAM) { p->u = s->beam[0]; p->v = s->beam[1]; p->w = s->beam[2]; }
     else iso_dir(&p->s, &p->u, &p->v, &p->w);
+    set_recip(p);
     return 0;
 }
 
@@ -1179,6 +1200,7 @@ static void from_site(const orc_ctx *c, Particle *p, const Site *b)
     p->cell = b->cell; p->ix = b->ix; p->iy = b->iy; p->ucell = b->ucell; p->mat = b->mat;
     birth_energy(c, p);
     iso_dir(&p->s, &p->u, &p->v, &p->w);
+    set_recip(p);
 }
 
 static int site_cmp(const void *a, const void *b)

@@ -39,7 +39,8 @@ class McgbError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("device", C.c_int), ("mode", C.c_int), ("block", C.c_int),
                 ("blocks_per_sm", C.c_int), ("record_histories", C.c_int),
-                ("bank_factor", C.c_double), ("max_iterations", C.c_int), ("pool", C.c_int)]
+                ("bank_factor", C.c_double), ("max_iterations", C.c_int), ("pool", C.c_int),
+                ("graphs", C.c_int)]
 
 
 class Counters(C.Structure):
@@ -146,11 +147,11 @@ class Context:
     """One transport problem on one GPU (mcgb_ctx)."""
 
     def __init__(self, device=0, mode=MODE_EVENT, block=0, blocks_per_sm=0,
-                 record_histories=False, bank_factor=0.0, max_iterations=0, pool=0):
+                 record_histories=False, bank_factor=0.0, max_iterations=0, pool=0, graphs=0):
         L = lib()
         self.L = L
         self.opts = Opts(device, mode, block, blocks_per_sm, int(record_histories),
-                         bank_factor, max_iterations, pool)
+                         bank_factor, max_iterations, pool, graphs)
         h = C.c_void_p()
         _chk(L.mcgb_create(C.byref(h), C.byref(self.opts)))
         self.h = h
@@ -392,7 +393,7 @@ class Batch:
     def __init__(self, device=0, mode=MODE_PERSISTENT, block=0, blocks_per_sm=0, pool=0):
         L = lib()
         self.L = L
-        self.opts = Opts(device, mode, block, blocks_per_sm, 0, 0.0, 0, pool)
+        self.opts = Opts(device, mode, block, blocks_per_sm, 0, 0.0, 0, pool, 0)
         h = C.c_void_p()
         _chk(L.mcgb_batch_create(C.byref(h), C.byref(self.opts)))
         self.h = h

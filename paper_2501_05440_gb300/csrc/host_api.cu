@@ -124,6 +124,18 @@ struct mcgb_ctx {
     std::vector<double> cyc_tms, cyc_ms;   // per-cycle device time: transport, whole cycle
     std::vector<cudaEvent_t> events;
     EigenRun eig;
+    // persistent cycles replayed as CUDA graphs (two: the banks alternate)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraph_t graph_src[2] = {nullptr, nullptr};
+    cudaGraphNode_t graph_mark[2] = {nullptr, nullptr};   // event record after the transport
+    cudaEvent_t mark_ev[2] = {nullptr, nullptr};
+    int graph_launches = 0;                // kernels in one graph
+    cudaStream_t cap_stream = nullptr;
+    DevAlloc gmem;                         // cycle counter, draws, bank sizes
+    int *cyc_dev = nullptr;
+    double *xi_dev = nullptr;
+    int64_t *bankm_dev = nullptr;
+    int *pinned_cyc = nullptr;
     // derivative forward state
     std::vector<GradGen> grad_gens;
     DevAlloc grad_mem;
@@ -157,6 +169,7 @@ static int prepare_buffers(mcgb_ctx *c, int64_t cap_p, int64_t cap_b)
     CKR(m.get(P.x, cap_p)); CKR(m.get(P.y, cap_p)); CKR(m.get(P.z, cap_p));
     CKR(m.get(P.u, cap_p)); CKR(m.get(P.v, cap_p)); CKR(m.get(P.w, cap_p));
     CKR(m.get(P.E, cap_p)); CKR(m.get(P.kt, cap_p)); CKR(m.get(P.kc, cap_p));
+    CKR(m.get(P.iu, cap_p)); CKR(m.get(P.iv, cap_p)); CKR(m.get(P.iw, cap_p));
     CKR(m.get(P.s, cap_p));
     CKR(m.get(P.g, cap_p)); CKR(m.get(P.cell, cap_p)); CKR(m.get(P.ix, cap_p));
     CKR(m.get(P.iy, cap_p)); CKR(m.get(P.ucell, cap_p)); CKR(m.get(P.mat, cap_p));
@@ -209,11 +222,12 @@ static int block_size(mcgb_ctx *c) { return c->opts.block > 0 ? c->opts.block : 
 // Transport one cycle / generation of `total` slots (host-known bound).
 static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t total,
                                 const int64_t *gen_base, const int *src_idx, int eigen,
-                                const Bank &Bsrc, const Bank &Bdst)
+                                const Bank &Bsrc, const Bank &Bdst, cudaStream_t st = nullptr,
+                                const int *gen_dev = nullptr)
 {
     RunState &r = c->rs;
     const World &W = c->world->W;
-    cudaStream_t st = c->stream;
+    if (!st) st = c->stream;
     int block = block_size(c);
     if (c->opts.mode == MCGB_MODE_PERSISTENT) {
         CK(cudaMemsetAsync(r.work, 0, sizeof(int), st));
@@ -226,14 +240,16 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
         a.eigen = eigen;
         a.work = r.work;
         a.chunk = 1;
+        a.gen_dev = gen_dev;
         int pool = c->opts.pool == 0 ? 512 : c->opts.pool;
         if (pool > 0) {
             int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
                                                  : std::max(1, pool_max_blocks_per_sm(pool));
-            int64_t want = (total + pool - 1) / pool;
+            int ppb = pool_particles_per_block(pool);
+            int64_t want = (total + ppb - 1) / ppb;
             int grid = (int)std::min<int64_t>((int64_t)c->sms * bps, std::max<int64_t>(want, 1));
             if (!launch_pool(W, r.P, Bsrc, Bdst, R, a, pool, grid, st))
-                return fail(MCGB_E_INVALID_ARG, "pool must be 256, 512 or 1024");
+                return fail(MCGB_E_INVALID_ARG, "unknown pool variant");
         } else {
             int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
                                                  : std::max(1, persistent_max_blocks_per_sm(block));
@@ -416,12 +432,97 @@ static int eigen_begin(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_
     e.cyc = 0;
     e.cur = 0;
     e.seed = c->world->probs[0].seed;
+    // device copies for graph replay: the resampling draw of every cycle, bank sizes
+    for (int q = 0; q < 2; q++)
+        if (c->graph[q]) {
+            cudaGraphExecDestroy(c->graph[q]);
+            c->graph[q] = nullptr;
+        }
+    c->gmem.release();
+    CKR(c->gmem.get(c->cyc_dev, 1));
+    CKR(c->gmem.get(c->xi_dev, ncyc));
+    CKR(c->gmem.get(c->bankm_dev, ncyc));
+    {
+        std::vector<double> xi(ncyc);
+        for (int q = 0; q < ncyc; q++) {
+            uint64_t rs = rng_stream(e.seed, ((uint64_t)q << 32) + 0xFFFFFFFFULL);
+            xi[q] = draw_host(rs);
+        }
+        CK(cudaMemcpyAsync(c->xi_dev, xi.data(), sizeof(double) * ncyc, cudaMemcpyHostToDevice, st));
+        if (c->pinned_cyc) cudaFreeHost(c->pinned_cyc);
+        CK(cudaMallocHost((void **)&c->pinned_cyc, sizeof(int) * ncyc));
+        for (int q = 0; q < ncyc; q++) c->pinned_cyc[q] = q;
+        CK(cudaStreamSynchronize(st));
+    }
     if (c->events.size() < (size_t)3 * ncyc + 3) {
         size_t old = c->events.size();
         c->events.resize(3 * ncyc + 3);
         for (size_t i = old; i < c->events.size(); i++) CK(cudaEventCreate(&c->events[i]));
     }
     return MCGB_OK;
+}
+
+// Capture one cycle (source from the bank, transport, bank order, resampling,
+// statistics) as a graph per bank parity; the cycle index, its resampling
+// draw and the active flag are read on the device, and the graph's last
+// kernel records the bank size and advances the cycle index.
+static int build_cycle_graphs(mcgb_ctx *c)
+{
+    EigenRun &e = c->eig;
+    RunState &r = c->rs;
+    const World &W = c->world->W;
+    RunBufs R = run_bufs(c, nullptr, -1, 0);
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = c->cap_stream;
+    for (int parity = 0; parity < 2; parity++) {
+        int64_t l0 = c->launches;
+        if (!c->mark_ev[parity]) CK(cudaEventCreate(&c->mark_ev[parity]));
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        cudaMemsetAsync(r.bank_n, 0, sizeof(int), cs);
+        int rc = transport_generation(c, R, 0, e.N, r.gen_base[0], r.src_idx, 1, r.bank[parity],
+                                      r.bank[parity ^ 1], cs, c->cyc_dev);
+        cudaEventRecordWithFlags(c->mark_ev[parity], cs, cudaEventRecordExternal);
+        launch_reduce_gen(r.P, e.N, nullptr, r.kout, r.cnt, cs, c->cyc_dev);
+        scan_exclusive(r.P.nfis, r.off, e.N, r.M, r.scratch, cs);
+        launch_perm(r.bank[parity ^ 1], r.off, r.M, r.perm, c->sms * 4, cs);
+        launch_resample_dev(r.perm, r.M, e.N, c->xi_dev, c->cyc_dev, r.src_idx, r.err,
+                            r.bank[parity ^ 1].cap, cs);
+        launch_tally_cycle(r.tacc, W.acc_size, W.nrep, (double)e.N, 0, r.tsum, r.tsum2, cs,
+                           c->cyc_dev, e.inactive);
+        launch_cycle_end(c->cyc_dev, r.M, c->bankm_dev, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(cs, &g);
+        if (rc != MCGB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        CK(ee);
+        // the event-record node after the transport kernel, re-pointed per cycle
+        size_t nn = 0;
+        CK(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+        c->graph_mark[parity] = nullptr;
+        for (cudaGraphNode_t n : nodes) {
+            cudaGraphNodeType ty;
+            CK(cudaGraphNodeGetType(n, &ty));
+            if (ty == cudaGraphNodeTypeEventRecord) c->graph_mark[parity] = n;
+        }
+        ee = cudaGraphInstantiate(&c->graph[parity], g, 0);
+        if (c->graph_src[parity]) cudaGraphDestroy(c->graph_src[parity]);
+        c->graph_src[parity] = g;
+        CK(ee);
+        int ntiles = (int)((e.N + 4095) / 4096);
+        c->graph_launches = (int)(c->launches - l0) + 1 + (ntiles > 1 ? 3 : 2) + 3 +
+                            (W.acc_size > 0 ? 1 : 0);
+        c->launches = l0;
+    }
+    return MCGB_OK;
+}
+
+static bool use_graphs(const mcgb_ctx *c)
+{
+    return c->opts.mode == MCGB_MODE_PERSISTENT && c->opts.graphs >= 0;
 }
 
 static int eigen_cycles(mcgb_ctx *c, int k)
@@ -433,6 +534,57 @@ static int eigen_cycles(mcgb_ctx *c, int k)
     const World &W = c->world->W;
     RunBufs R = run_bufs(c, nullptr, -1, 0);
     int64_t N = e.N;
+    // cycles after the first: graph launches back to back, checked once at the end
+    if (use_graphs(c) && e.cyc >= 1 && k > 0 && e.cyc < e.ncyc) {
+        if (!c->graph[0]) CKR(build_cycle_graphs(c));
+        int first = e.cyc;
+        CK(cudaMemcpyAsync(c->cyc_dev, c->pinned_cyc + first, sizeof(int), cudaMemcpyHostToDevice, st));
+        int last = std::min(e.ncyc, first + k);
+        for (int cyc = first; cyc < last; cyc++) {
+            int par = cyc & 1;
+            if (c->graph_mark[par])
+                CK(cudaGraphExecEventRecordNodeSetEvent(c->graph[par], c->graph_mark[par],
+                                                        c->events[3 * cyc + 1]));
+            CK(cudaEventRecord(c->events[3 * cyc], st));
+            CK(cudaGraphLaunch(c->graph[par], st));
+            CK(cudaEventRecord(c->events[3 * cyc + 2], st));
+            c->launches += c->graph_launches;
+        }
+        std::vector<int64_t> bm(last - first);
+        CK(cudaMemcpyAsync(bm.data(), c->bankm_dev + first, sizeof(int64_t) * (last - first),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(r.pinned + 5, r.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int err = r.pinned[5];
+        for (int cyc = first; cyc < last; cyc++) {
+            float t1 = 0.f, t2 = 0.f;
+            if (c->graph_mark[cyc & 1]) cudaEventElapsedTime(&t1, c->events[3 * cyc], c->events[3 * cyc + 1]);
+            cudaEventElapsedTime(&t2, c->events[3 * cyc], c->events[3 * cyc + 2]);
+            c->cyc_ms[cyc] = t2;
+            c->cyc_tms[cyc] = t1;
+            c->cyc_m[cyc] = bm[cyc - first];
+        }
+        e.cyc = last;
+        if (err & ERR_BANK_OVERFLOW) {
+            e.on = false;
+            return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow");
+        }
+        if (err & ERR_SOURCE) {
+            e.on = false;
+            return fail(MCGB_E_STATE, "source sampling failed");
+        }
+        for (int cyc = first; cyc < last; cyc++)
+            if (c->cyc_m[cyc] == 0) {
+                e.on = false;
+                return fail(MCGB_E_STATE, "fission bank empty after cycle " + std::to_string(cyc));
+            }
+        e.cur = last & 1;
+        if (last == e.ncyc && c->opts.record_histories) {
+            CKR(copy_records(c, N));
+            CKR(copy_bank(c, r.bank[e.cur], c->cyc_m[last - 1]));
+        }
+        return MCGB_OK;
+    }
     for (int q = 0; q < k && e.cyc < e.ncyc; q++) {
         int cyc = e.cyc;
         int nxt = e.cur ^ 1;
@@ -708,9 +860,13 @@ int mcgb_create(mcgb_ctx **out, const mcgb_opts *opts)
     CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     if (c->opts.block != 0 && (c->opts.block < 32 || c->opts.block > 256 || c->opts.block % 32))
         return fail(MCGB_E_INVALID_ARG, "block must be a multiple of 32 in [32, 256]");
-    if (c->opts.pool != 0 && c->opts.pool != -1 && c->opts.pool != 256 && c->opts.pool != 512 &&
-        c->opts.pool != 1024)
-        return fail(MCGB_E_INVALID_ARG, "pool must be 256, 512, 1024, 0 (default) or -1");
+    {
+        int pl = c->opts.pool;
+        if (!(pl == 0 || pl == -1 || pl == 32 || pl == 64 || pl == 128 || pl == 256 || pl == 512 ||
+              pl == 1024 || pl == 2256 || pl == 2512))
+            return fail(MCGB_E_INVALID_ARG,
+                        "pool must be 32, 64, 128, 256, 512, 1024, 2256, 2512, 0 or -1");
+    }
     *out = c.release();
     return MCGB_OK;
 }
@@ -720,6 +876,13 @@ int mcgb_destroy(mcgb_ctx *ctx)
     if (!ctx) return MCGB_OK;
     cudaSetDevice(ctx->device);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    for (int q = 0; q < 2; q++) {
+        if (ctx->graph[q]) cudaGraphExecDestroy(ctx->graph[q]);
+        if (ctx->graph_src[q]) cudaGraphDestroy(ctx->graph_src[q]);
+        if (ctx->mark_ev[q]) cudaEventDestroy(ctx->mark_ev[q]);
+    }
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->pinned_cyc) cudaFreeHost(ctx->pinned_cyc);
     if (ctx->rs.pinned) cudaFreeHost(ctx->rs.pinned);
     delete ctx;
     return MCGB_OK;
@@ -1393,7 +1556,7 @@ int mcgb_batch_autotune(mcgb_batch *b, int budget_ms, mcgb_tune *out)
     // candidates: block-sorted pools (particles per block x resident blocks per SM)
     // and the register-resident variant (threads per block x blocks per SM)
     std::vector<mcgb_tune> cand;
-    for (int pool : {512, 1024, 256}) {
+    for (int pool : {512, 2256, 256, 2512, 64, 128}) {
         int occ = std::max(1, pool_max_blocks_per_sm(pool));
         for (int bps = occ; bps >= 1; bps = bps > 2 ? bps / 2 : bps - 1) cand.push_back({0, bps, pool, 0.0});
     }

@@ -29,17 +29,20 @@ struct PersistentArgs {
     int eigen;
     int *work;               // device work counter (zeroed before the launch)
     int chunk;               // slots taken per pop
+    const int *gen_dev;      // when not null: the cycle index is read here (graph replay)
 };
 // births read Bsrc (the previous cycle's bank), new sites are appended to Bdst
 void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, const Bank &Bdst,
                        const RunBufs &R, const PersistentArgs &a, int grid, int block,
                        cudaStream_t st);
 int persistent_max_blocks_per_sm(int block);
-// block-sorted variant: `pool` particles per block in shared memory (256, 512, 1024)
+// sorted-pool variants in shared memory: `pool` = 256, 512 or 1024 particles per
+// block sorted block-wide, or 32, 64 or 128 particles per warp sorted per warp
 bool launch_pool(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                  const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st);
 int pool_max_blocks_per_sm(int pool);
 int pool_threads();
+int pool_particles_per_block(int pool);
 
 // ---- end of cycle / generation --------------------------------------------
 // Exclusive scan of n counts into out; *total = sum.  scratch holds one int per
@@ -49,11 +52,18 @@ void scan_exclusive(const int *in, int *out, int64_t n, int *total, int *scratch
 void launch_perm(const Bank &B, const int *off, const int *M, int *perm, int grid, cudaStream_t st);
 void launch_resample(const int *perm, const int *M, int64_t N, double xi, int *src_idx,
                      int *err, int64_t cap, cudaStream_t st);
-// sums over slots [0, total): k estimators into kout[2], counters into cnt[5]
+// sums over slots [0, total): k estimators into kout[2] (kout[2 * *cyc_dev ..] when
+// cyc_dev is given), counters into cnt[5]
 void launch_reduce_gen(const Particles &P, int64_t total, const int *total_dev, double *kout,
-                       unsigned long long *cnt, cudaStream_t st);
+                       unsigned long long *cnt, cudaStream_t st, const int *cyc_dev = nullptr);
 void launch_tally_cycle(double *tacc, int acc_size, int nrep, double n, int active,
-                        double *tsum, double *tsum2, cudaStream_t st);
+                        double *tsum, double *tsum2, cudaStream_t st, const int *cyc_dev = nullptr,
+                        int inactive = 0);
+// resampling with the draw of the cycle read on the device: xi_tab[*cyc_dev]
+void launch_resample_dev(const int *perm, const int *M, int64_t N, const double *xi_tab,
+                         const int *cyc_dev, int *src_idx, int *err, int64_t cap, cudaStream_t st);
+// end of a replayed cycle: bank size into bank_m[*cyc], then ++*cyc
+void launch_cycle_end(int *cyc_dev, const int *M, int64_t *bank_m, cudaStream_t st);
 void launch_acc_reduce(const double *tacc, int acc_size, int nrep, double *out, cudaStream_t st);
 void launch_gen_base(const int64_t *base, int nprob, const int *off, const int *M,
                      int64_t *next_base, cudaStream_t st);

@@ -134,8 +134,7 @@ __global__ void k_resample(const int *perm, const int *Mp, int64_t N, double xi,
         atomicOr(err, ERR_BANK_OVERFLOW);
         M = cap;
     }
-    if (M <= 0) {
-        if (j == 0) atomicOr(err, ERR_SOURCE);
+    if (M <= 0) {   // empty bank: the host reports it and stops
         src_idx[j] = 0;
         return;
     }
@@ -153,9 +152,10 @@ void launch_resample(const int *perm, const int *M, int64_t N, double xi, int *s
 
 // Sums of per-history k estimators and event counters over the generation's slots.
 __global__ void k_reduce_gen(Particles P, int64_t total, const int *total_dev, double *kout,
-                             unsigned long long *cnt)
+                             unsigned long long *cnt, const int *cyc_dev)
 {
     int64_t n = total_dev ? (int64_t)*total_dev : total;
+    if (cyc_dev) kout += 2 * *cyc_dev;
     double kt = 0.0, kc = 0.0;
     unsigned long long c[5] = {0, 0, 0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -186,18 +186,19 @@ __global__ void k_reduce_gen(Particles P, int64_t total, const int *total_dev, d
 }
 
 void launch_reduce_gen(const Particles &P, int64_t total, const int *total_dev, double *kout,
-                       unsigned long long *cnt, cudaStream_t st)
+                       unsigned long long *cnt, cudaStream_t st, const int *cyc_dev)
 {
-    k_reduce_gen<<<304, 256, 0, st>>>(P, total, total_dev, kout, cnt);
+    k_reduce_gen<<<304, 256, 0, st>>>(P, total, total_dev, kout, cnt, cyc_dev);
 }
 
 // Eigenvalue cycle end: batch value v = (sum of replicas) / N; keep sum and
 // sum of squares over active cycles; clear the accumulators.
 __global__ void k_tally_cycle(double *tacc, int acc_size, int nrep, double n, int active,
-                              double *tsum, double *tsum2)
+                              double *tsum, double *tsum2, const int *cyc_dev, int inactive)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= acc_size) return;
+    if (cyc_dev) active = *cyc_dev >= inactive;
     double v = 0.0;
     for (int r = 0; r < nrep; r++) {
         v += tacc[(int64_t)r * acc_size + i];
@@ -211,10 +212,51 @@ __global__ void k_tally_cycle(double *tacc, int acc_size, int nrep, double n, in
 }
 
 void launch_tally_cycle(double *tacc, int acc_size, int nrep, double n, int active,
-                        double *tsum, double *tsum2, cudaStream_t st)
+                        double *tsum, double *tsum2, cudaStream_t st, const int *cyc_dev,
+                        int inactive)
 {
+    if (acc_size <= 0) return;
     k_tally_cycle<<<(acc_size + 255) / 256, 256, 0, st>>>(tacc, acc_size, nrep, n, active, tsum,
-                                                          tsum2);
+                                                          tsum2, cyc_dev, inactive);
+}
+
+__global__ void k_resample_dev(const int *perm, const int *Mp, int64_t N, const double *xi_tab,
+                               const int *cyc_dev, int *src_idx, int *err, int64_t cap)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double xi = xi_tab[*cyc_dev];
+    int64_t M = *Mp;
+    if (M > cap) {
+        atomicOr(err, ERR_BANK_OVERFLOW);
+        M = cap;
+    }
+    if (M <= 0) {
+        src_idx[j] = 0;
+        return;
+    }
+    double t = ((double)j + xi) * (double)M / (double)N;
+    int64_t idx = (int64_t)t;
+    if (idx >= M) idx = M - 1;
+    src_idx[j] = perm[idx];
+}
+
+void launch_resample_dev(const int *perm, const int *M, int64_t N, const double *xi_tab,
+                         const int *cyc_dev, int *src_idx, int *err, int64_t cap, cudaStream_t st)
+{
+    k_resample_dev<<<(int)((N + 255) / 256), 256, 0, st>>>(perm, M, N, xi_tab, cyc_dev, src_idx,
+                                                           err, cap);
+}
+
+__global__ void k_cycle_end(int *cyc_dev, const int *M, int64_t *bank_m)
+{
+    bank_m[*cyc_dev] = *M;
+    *cyc_dev += 1;
+}
+
+void launch_cycle_end(int *cyc_dev, const int *M, int64_t *bank_m, cudaStream_t st)
+{
+    k_cycle_end<<<1, 1, 0, st>>>(cyc_dev, M, bank_m);
 }
 
 __global__ void k_acc_reduce(const double *tacc, int acc_size, int nrep, double *out)

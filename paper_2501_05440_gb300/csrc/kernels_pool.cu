@@ -21,14 +21,14 @@ constexpr int NBUCKET = 33;          // list buckets: 0 = crossings, 1..32 = mat
 constexpr int SLOT_EMPTY = -2;
 
 struct Pool {
-    double *x, *y, *z, *u, *v, *w, *E, *kt, *kc;
+    double *x, *y, *z, *u, *v, *w, *E, *kt, *kc, *iu, *iv, *iw;
     unsigned long long *s;
     int *g, *cell, *ix, *iy, *ucell, *mat, *prob, *root, *nfis, *ncoll, *ncross, *gslot, *bwhich,
         *uk, *fate, *ev;
     int *list;
 };
 
-__host__ __device__ constexpr size_t pool_bytes(int P) { return (size_t)P * (10 * 8 + 17 * 4); }
+__host__ __device__ constexpr size_t pool_bytes(int P) { return (size_t)P * (13 * 8 + 17 * 4); }
 
 __device__ __forceinline__ Pool carve(unsigned char *base, int P)
 {
@@ -36,8 +36,9 @@ __device__ __forceinline__ Pool carve(unsigned char *base, int P)
     double *d = reinterpret_cast<double *>(base);
     q.x = d; q.y = d + P; q.z = d + 2 * P; q.u = d + 3 * P; q.v = d + 4 * P; q.w = d + 5 * P;
     q.E = d + 6 * P; q.kt = d + 7 * P; q.kc = d + 8 * P;
-    q.s = reinterpret_cast<unsigned long long *>(d + 9 * P);
-    int *i = reinterpret_cast<int *>(d + 10 * P);
+    q.iu = d + 9 * P; q.iv = d + 10 * P; q.iw = d + 11 * P;
+    q.s = reinterpret_cast<unsigned long long *>(d + 12 * P);
+    int *i = reinterpret_cast<int *>(d + 13 * P);
     q.g = i; q.cell = i + P; q.ix = i + 2 * P; q.iy = i + 3 * P; q.ucell = i + 4 * P;
     q.mat = i + 5 * P; q.prob = i + 6 * P; q.root = i + 7 * P; q.nfis = i + 8 * P;
     q.ncoll = i + 9 * P; q.ncross = i + 10 * P; q.gslot = i + 11 * P; q.bwhich = i + 12 * P;
@@ -48,6 +49,7 @@ __device__ __forceinline__ Pool carve(unsigned char *base, int P)
 __device__ __forceinline__ void pool_load(const Pool &q, int i, PS &p)
 {
     p.x = q.x[i]; p.y = q.y[i]; p.z = q.z[i]; p.u = q.u[i]; p.v = q.v[i]; p.w = q.w[i];
+    p.iu = q.iu[i]; p.iv = q.iv[i]; p.iw = q.iw[i];
     p.E = q.E[i]; p.s = q.s[i];
     p.g = q.g[i]; p.cell = q.cell[i]; p.ix = q.ix[i]; p.iy = q.iy[i]; p.ucell = q.ucell[i];
     p.mat = q.mat[i]; p.prob = q.prob[i]; p.root = q.root[i]; p.nfis = q.nfis[i];
@@ -57,6 +59,7 @@ __device__ __forceinline__ void pool_load(const Pool &q, int i, PS &p)
 __device__ __forceinline__ void pool_store(const Pool &q, int i, const PS &p)
 {
     q.x[i] = p.x; q.y[i] = p.y; q.z[i] = p.z; q.u[i] = p.u; q.v[i] = p.v; q.w[i] = p.w;
+    q.iu[i] = p.iu; q.iv[i] = p.iv; q.iw[i] = p.iw;
     q.E[i] = p.E; q.s[i] = p.s;
     q.g[i] = p.g; q.cell[i] = p.cell; q.ix[i] = p.ix; q.iy[i] = p.iy; q.ucell[i] = p.ucell;
     q.mat[i] = p.mat; q.prob[i] = p.prob; q.root[i] = p.root; q.nfis[i] = p.nfis;
@@ -80,12 +83,12 @@ __device__ __forceinline__ void retire(const Pool &q, const Particles &G, int i,
 
 // Bucketed compaction of the pool: slots with key >= 0 go to q.list, grouped
 // by key in increasing order; counts per key in cnt[NBUCKET].  All threads call.
-template <int P, class KeyFn>
+template <int P, int T, class KeyFn>
 __device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, KeyFn key)
 {
     if (threadIdx.x < NBUCKET) hist[threadIdx.x] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < P; i += POOL_T) {
+    for (int i = threadIdx.x; i < P; i += T) {
         int k = key(i);
         if (k >= 0) atomicAdd(hist + k, 1);
     }
@@ -110,7 +113,7 @@ __device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, Ke
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < P; i += POOL_T) {
+    for (int i = threadIdx.x; i < P; i += T) {
         int k = key(i);
         if (k >= 0) q.list[atomicAdd(hist + k, 1)] = i;
     }
@@ -118,23 +121,27 @@ __device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, Ke
     return cnt[NBUCKET];
 }
 
-template <int P>
-__global__ void __launch_bounds__(POOL_T, 2) k_pool(World W, Particles G, Bank Bsrc, Bank Bdst,
-                                                 RunBufs R, PersistentArgs a)
+// P particles per block of T threads; the register budget is planned for
+// 65536 / (T * 128) resident blocks (at most 128 registers per thread).
+template <int P, int T>
+__global__ void __launch_bounds__(T, 65536 / (T * 128)) k_pool(World W, Particles G, Bank Bsrc,
+                                                               Bank Bdst, RunBufs R,
+                                                               PersistentArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int hist[NBUCKET + 1], cnt[NBUCKET + 1];
     __shared__ int s_base, s_take, s_exhausted;
     const Pool q = carve(smem, P);
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
+    const int gen = a.gen_dev ? *a.gen_dev : a.gen;
     const int rep = (int)(blockIdx.x % (unsigned)W.nrep);
-    for (int i = threadIdx.x; i < P; i += POOL_T) q.fate[i] = SLOT_EMPTY;
+    for (int i = threadIdx.x; i < P; i += T) q.fate[i] = SLOT_EMPTY;
     if (threadIdx.x == 0) s_exhausted = 0;
     __syncthreads();
     for (;;) {
         // ---- refill empty slots from the work counter
         if (!s_exhausted) {
-            int n_empty = build_list<P>(q, hist, cnt, [&](int i) { return q.fate[i] == SLOT_EMPTY ? 0 : -1; });
+            int n_empty = build_list<P, T>(q, hist, cnt, [&](int i) { return q.fate[i] == SLOT_EMPTY ? 0 : -1; });
             if (threadIdx.x == 0) {
                 int take = 0, base = 0;
                 if (n_empty > 0) {
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(POOL_T, 2) k_pool(World W, Particles G, Bank B
                 s_take = take;
             }
             __syncthreads();
-            for (int k = threadIdx.x; k < s_take; k += POOL_T) {
+            for (int k = threadIdx.x; k < s_take; k += T) {
                 int i = q.list[k];
                 int64_t j = (int64_t)s_base + k;
                 int prob = 0;
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(POOL_T, 2) k_pool(World W, Particles G, Bank B
                     prob = lo;
                 }
                 PS p;
-                bool ok = init_particle(W, W.prob[prob], Bsrc, p, prob, j - a.gen_base[prob], a.gen,
+                bool ok = init_particle(W, W.prob[prob], Bsrc, p, prob, j - a.gen_base[prob], gen,
                                         a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
                 q.gslot[i] = (int)j;
                 q.kt[i] = 0.0;
@@ -180,11 +187,11 @@ __global__ void __launch_bounds__(POOL_T, 2) k_pool(World W, Particles G, Bank B
             __syncthreads();
         }
         // ---- flights of every live particle, grouped by material
-        int n_adv = build_list<P>(q, hist, cnt, [&](int i) {
+        int n_adv = build_list<P, T>(q, hist, cnt, [&](int i) {
             return q.fate[i] == FATE_ALIVE ? 1 + (q.mat[i] & 31) : -1;
         });
         if (n_adv == 0 && s_exhausted) break;
-        for (int k = threadIdx.x; k < n_adv; k += POOL_T) {
+        for (int k = threadIdx.x; k < n_adv; k += T) {
             int i = q.list[k];
             PS p;
             pool_load(q, i, p);
@@ -206,12 +213,12 @@ __global__ void __launch_bounds__(POOL_T, 2) k_pool(World W, Particles G, Bank B
         }
         __syncthreads();
         // ---- crossings (bucket 0), then collisions grouped by material
-        int n_ev = build_list<P>(q, hist, cnt, [&](int i) {
+        int n_ev = build_list<P, T>(q, hist, cnt, [&](int i) {
             if (q.fate[i] != FATE_ALIVE) return -1;
             return (q.ev[i] & 15) == EV_CROSS ? 0 : 1 + (q.mat[i] & 31);
         });
         int n_cross = cnt[0];
-        for (int k = threadIdx.x; k < n_ev; k += POOL_T) {
+        for (int k = threadIdx.x; k < n_ev; k += T) {
             int i = q.list[k];
             PS p;
             pool_load(q, i, p);
@@ -230,46 +237,213 @@ __global__ void __launch_bounds__(POOL_T, 2) k_pool(World W, Particles G, Bank B
     }
 }
 
-template <int P>
+// ---------------------------------------------------------------------------
+// Warp-level variant: each warp owns PW slots of the shared pool and sorts its
+// own events with ballots (no block barrier; warps progress independently).
+constexpr int WPOOL_T = 128;   // threads (4 warps) per block
+
+// compacts the slots of the warp's pool for which pred(i) holds into `list`
+template <int PW, class Pred>
+__device__ __forceinline__ int warp_list(int *list, Pred pred)
+{
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+#pragma unroll
+    for (int r = 0; r < PW / 32; r++) {
+        int i = r * 32 + lane;
+        bool b = pred(i);
+        unsigned m = __ballot_sync(0xffffffffu, b);
+        if (b) list[n + __popc(m & ((1u << lane) - 1u))] = i;
+        n += __popc(m);
+    }
+    __syncwarp();
+    return n;
+}
+
+// resident blocks per SM the register budget is planned for (smem allows as many)
+template <int PW> struct WpoolMinBlocks { static constexpr int value = PW <= 32 ? 6 : (PW <= 64 ? 5 : 2); };
+
+template <int PW>
+__global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(World W, Particles G, Bank Bsrc, Bank Bdst,
+                                                      RunBufs R, PersistentArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Pool q = carve(smem + (size_t)warp * pool_bytes(PW), PW);
+    const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
+    const int gen = a.gen_dev ? *a.gen_dev : a.gen;
+    const int rep = (int)((blockIdx.x * (WPOOL_T / 32) + warp) % (unsigned)W.nrep);
+    for (int i = lane; i < PW; i += 32) q.fate[i] = SLOT_EMPTY;
+    __syncwarp();
+    bool exhausted = false;
+    for (;;) {
+        if (!exhausted) {
+            int n_empty = warp_list<PW>(q.list, [&](int i) { return q.fate[i] == SLOT_EMPTY; });
+            int base = 0;
+            if (lane == 0 && n_empty > 0) base = atomicAdd(a.work, n_empty);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int take = 0;
+            if (n_empty > 0) {
+                int64_t left = total - (int64_t)base;
+                take = left <= 0 ? 0 : (left < n_empty ? (int)left : n_empty);
+                if (take < n_empty) exhausted = true;
+            }
+            for (int k = lane; k < take; k += 32) {
+                int i = q.list[k];
+                int64_t j = (int64_t)base + k;
+                int lo = 0, hi = W.nprob;
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (a.gen_base[mid] <= j) lo = mid;
+                    else hi = mid;
+                }
+                PS p;
+                bool ok = init_particle(W, W.prob[lo], Bsrc, p, lo, j - a.gen_base[lo], gen,
+                                        a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                q.gslot[i] = (int)j;
+                q.kt[i] = 0.0;
+                q.kc[i] = 0.0;
+                if (!ok) {
+                    atomicOr(R.err, ERR_SOURCE);
+                    p.fate = FATE_LOST;
+                    p.cell = 0;
+                    p.mat = 0;
+                    pool_store(q, i, p);
+                    retire(q, G, i, p);
+                } else {
+                    pool_store(q, i, p);
+                }
+            }
+            __syncwarp();
+        }
+        int n_adv = warp_list<PW>(q.list, [&](int i) { return q.fate[i] == FATE_ALIVE; });
+        if (n_adv == 0 && exhausted) break;
+        for (int k = lane; k < n_adv; k += 32) {
+            int i = q.list[k];
+            PS p;
+            pool_load(q, i, p);
+            int kind, which, uk = 0;
+            double kt = q.kt[i];
+            int ev = step_advance(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which, uk, kt);
+            q.x[i] = p.x;
+            q.y[i] = p.y;
+            q.z[i] = p.z;
+            q.s[i] = p.s;
+            q.kt[i] = kt;
+            q.ev[i] = ev | (kind << 4);
+            q.bwhich[i] = which;
+            q.uk[i] = uk;
+            if (ev == EV_DEAD) {
+                q.fate[i] = p.fate;
+                retire(q, G, i, p);
+            }
+        }
+        __syncwarp();
+        int n_x = warp_list<PW>(q.list, [&](int i) {
+            return q.fate[i] == FATE_ALIVE && (q.ev[i] & 15) == EV_CROSS;
+        });
+        for (int k = lane; k < n_x; k += 32) {
+            int i = q.list[k];
+            PS p;
+            pool_load(q, i, p);
+            int ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
+            pool_store(q, i, p);
+            if (ev == EV_DEAD) retire(q, G, i, p);
+        }
+        __syncwarp();
+        int n_c = warp_list<PW>(q.list, [&](int i) {
+            return q.fate[i] == FATE_ALIVE && (q.ev[i] & 15) == EV_COLLIDE;
+        });
+        for (int k = lane; k < n_c; k += 32) {
+            int i = q.list[k];
+            PS p;
+            pool_load(q, i, p);
+            double kc = q.kc[i];
+            int ev = step_collide(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
+            q.kc[i] = kc;
+            q.ev[i] = EV_ADVANCE;
+            pool_store(q, i, p);
+            if (ev == EV_DEAD) retire(q, G, i, p);
+        }
+        __syncwarp();
+    }
+}
+
+template <int PW>
+void launch_wpool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                    const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
+{
+    size_t sm = pool_bytes(PW) * (WPOOL_T / 32);
+    cudaFuncSetAttribute(k_wpool<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_wpool<PW><<<grid, WPOOL_T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
+}
+
+template <int PW> int wpool_occupancy()
+{
+    int n = 0;
+    size_t sm = pool_bytes(PW) * (WPOOL_T / 32);
+    cudaFuncSetAttribute(k_wpool<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wpool<PW>, WPOOL_T, sm);
+    return n;
+}
+
+template <int P, int T>
 void launch_pool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                    const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
 {
     size_t sm = pool_bytes(P);
-    cudaFuncSetAttribute(k_pool<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_pool<P><<<grid, POOL_T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
+    cudaFuncSetAttribute(k_pool<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_pool<P, T><<<grid, T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
+}
+
+template <int P, int T> int pool_occupancy()
+{
+    int n = 0;
+    size_t sm = pool_bytes(P);
+    cudaFuncSetAttribute(k_pool<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<P, T>, T, sm);
+    return n;
 }
 
 }  // namespace
 
 int pool_threads() { return POOL_T; }
 
+int pool_particles_per_block(int pool)
+{
+    return pool < 256 ? pool * (WPOOL_T / 32) : (pool > 2000 ? pool - 2000 : pool);
+}
+
+// pool codes: 32, 64, 128 = particles per warp (warp-level lists, 128-thread
+// blocks); 256, 512, 1024 = particles per 256-thread block; 2256, 2512 = 256 or
+// 512 particles per 128-thread block
 int pool_max_blocks_per_sm(int P)
 {
-    int n = 0;
-    size_t sm = pool_bytes(P);
     switch (P) {
-    case 256:
-        cudaFuncSetAttribute(k_pool<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<256>, POOL_T, sm);
-        break;
-    case 512:
-        cudaFuncSetAttribute(k_pool<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<512>, POOL_T, sm);
-        break;
-    default:
-        cudaFuncSetAttribute(k_pool<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<1024>, POOL_T, sm);
+    case 32: return wpool_occupancy<32>();
+    case 64: return wpool_occupancy<64>();
+    case 128: return wpool_occupancy<128>();
+    case 256: return pool_occupancy<256, 256>();
+    case 512: return pool_occupancy<512, 256>();
+    case 1024: return pool_occupancy<1024, 256>();
+    case 2256: return pool_occupancy<256, 128>();
+    case 2512: return pool_occupancy<512, 128>();
+    default: return 0;
     }
-    return n;
 }
 
 bool launch_pool(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                  const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st)
 {
     switch (pool) {
-    case 256: launch_pool_t<256>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 512: launch_pool_t<512>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 1024: launch_pool_t<1024>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 32: launch_wpool_t<32>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 64: launch_wpool_t<64>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 128: launch_wpool_t<128>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 256: launch_pool_t<256, 256>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 512: launch_pool_t<512, 256>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 1024: launch_pool_t<1024, 256>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 2256: launch_pool_t<256, 128>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 2512: launch_pool_t<512, 128>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
     default: return false;
     }
 }

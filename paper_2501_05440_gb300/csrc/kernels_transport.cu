@@ -17,6 +17,7 @@ __device__ __forceinline__ void load_ps(const Particles &P, int i, PS &p)
 {
     p.x = P.x[i]; p.y = P.y[i]; p.z = P.z[i];
     p.u = P.u[i]; p.v = P.v[i]; p.w = P.w[i];
+    p.iu = P.iu[i]; p.iv = P.iv[i]; p.iw = P.iw[i];
     p.E = P.E[i];
     p.s = P.s[i];
     p.g = P.g[i]; p.cell = P.cell[i]; p.ix = P.ix[i]; p.iy = P.iy[i]; p.ucell = P.ucell[i];
@@ -29,6 +30,7 @@ __device__ __forceinline__ void store_ps(const Particles &P, int i, const PS &p)
 {
     P.x[i] = p.x; P.y[i] = p.y; P.z[i] = p.z;
     P.u[i] = p.u; P.v[i] = p.v; P.w[i] = p.w;
+    P.iu[i] = p.iu; P.iv[i] = p.iv; P.iw[i] = p.iw;
     P.E[i] = p.E;
     P.s[i] = p.s;
     P.g[i] = p.g; P.cell[i] = p.cell; P.ix[i] = p.ix; P.iy[i] = p.iy; P.ucell[i] = p.ucell;
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
                                                     RunBufs R, PersistentArgs a)
 {
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
+    const int gen = a.gen_dev ? *a.gen_dev : a.gen;
     const int lane = threadIdx.x & 31;
     const int rep = accum_replica(W);
     PS p;
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
                     Pd = W.prob + prob;
                     kt = 0.0;
                     kc = 0.0;
-                    bool ok = init_particle(W, *Pd, Bsrc, p, prob, j - a.gen_base[prob], a.gen,
+                    bool ok = init_particle(W, *Pd, Bsrc, p, prob, j - a.gen_base[prob], gen,
                                             a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
                     if (ok) {
                         alive = true;

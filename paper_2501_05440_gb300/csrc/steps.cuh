@@ -47,9 +47,9 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     }
     bool coll = lt_mag(dc, ds);     // both are +-0, positive or +inf
     double d = coll ? dc : ds;
-    p.x = p.x + d * p.u;
-    p.y = p.y + d * p.v;
-    p.z = p.z + d * p.w;
+    p.x = fma(d, p.u, p.x);
+    p.y = fma(d, p.v, p.y);
+    p.z = fma(d, p.w, p.z);
     if (REPLAY) {
         *d_out = d;
     } else {
@@ -111,6 +111,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             xi = draw(p.s);
             p.g = sample_cdf(W.gg_scdf + __ldg(W.m_ggoff + p.mat) + g * G, G, xi);
             iso_dir(p.s, p.u, p.v, p.w);
+            set_recip(p);
         } else {
             p.fate = FATE_ABSORBED;
             return EV_DEAD;
@@ -150,6 +151,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         xi = draw(p.s);
         if (!lt_mag(ss, xi * st)) {
             p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);
+            set_recip(p);
         } else {
             p.fate = FATE_ABSORBED;
             return EV_DEAD;

@@ -106,7 +106,8 @@ __device__ __forceinline__ double draw_sym(uint64_t &s) { return n_to_sym(draw_n
 // ---------------------------------------------------------------------------
 // ln xi for xi = n 2^-53: table-driven (Tang, ACM TOMS 1990).  n = 2^e m,
 // m in [1,2); c = 1 + j/256 from the top 8 fraction bits; r = (m - c)(1/c);
-// ln xi = (e - 53) ln 2 + ln c + r(1 + r(-1/2 + r(1/3 + r(-1/4 + r(1/5 - r/6))))).
+// ln xi = (e - 53) ln 2 + ln c + r(1 + r(-1/2 + r(1/3 + r(-1/4 + r(1/5 - r/6))))),
+// the polynomial by Horner's rule with fused multiply-adds.
 // Tables (built on the host): ln c by the series 2 atanh((c-1)/(c+1)), 1/c,
 // and (e - 53) ln 2 rounded once.
 __device__ __forceinline__ double log_n(const World &W, uint64_t n)
@@ -119,11 +120,11 @@ __device__ __forceinline__ double log_n(const World &W, uint64_t n)
     double c = __longlong_as_double((long long)(0x3FF0000000000000ULL | ((uint64_t)j << 44)));
     double r = (m - c) * __ldg(W.rinvtab + j);
     double q = -1.0 / 6.0;
-    q = q * r + 1.0 / 5.0;
-    q = q * r + -0.25;
-    q = q * r + 1.0 / 3.0;
-    q = q * r + -0.5;
-    q = q * r + 1.0;
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    q = fma(q, r, 1.0);
     double p = q * r;
     return __ldg(W.etab + e) + (__ldg(W.logtab + j) + p);
 }
@@ -138,7 +139,7 @@ __device__ __forceinline__ void iso_dir(uint64_t &s, double &u, double &v, doubl
     do {
         a = draw_sym(s);
         b = draw_sym(s);
-        S = a * a + b * b;
+        S = fma(a, a, b * b);
         k++;
     } while (!lt_mag(S, 1.0) && k < 64);
     if (!lt_mag(S, 1.0)) {
@@ -162,7 +163,7 @@ __device__ __forceinline__ void azimuth(uint64_t &s, double &cphi, double &sphi)
     do {
         a = draw_sym(s);
         b = draw_sym(s);
-        r2 = a * a + b * b;
+        r2 = fma(a, a, b * b);
         ok = !lt_mag(1.0, r2) && is_pos(r2);
         k++;
     } while (!ok && k < 64);
@@ -171,7 +172,7 @@ __device__ __forceinline__ void azimuth(uint64_t &s, double &cphi, double &sphi)
         sphi = 0.0;
         return;
     }
-    cphi = (a * a - b * b) / r2;
+    cphi = fma(a, a, -(b * b)) / r2;
     sphi = 2.0 * a * b / r2;
 }
 
@@ -229,7 +230,7 @@ __device__ __forceinline__ double maxwell(const World &W, uint64_t &s)
             do {
                 aa = draw_sym(s);
                 bb = draw_sym(s);
-                rr = aa * aa + bb * bb;
+                rr = fma(aa, aa, bb * bb);
                 ok = !lt_mag(1.0, rr) && is_pos(rr);
                 t++;
             } while (!ok && t < 64);
@@ -258,9 +259,17 @@ __device__ __forceinline__ int sample_cdf(const double *cdf, int n, double xi)
 // Particle held in registers
 struct PS {
     double x, y, z, u, v, w, E;
+    double iu, iv, iw;   // 1/u, 1/v, 1/w, rounded whenever the direction is set
     uint64_t s;
     int g, cell, ix, iy, ucell, mat, prob, root, nfis, ncoll, ncross, fate;
 };
+
+__device__ __forceinline__ void set_recip(PS &p)
+{
+    p.iu = 1.0 / p.u;
+    p.iv = 1.0 / p.v;
+    p.iw = 1.0 / p.w;
+}
 
 // ---------------------------------------------------------------------------
 // CSG geometry (Sec. 1: constructive solid geometry with surface tracking)
@@ -274,11 +283,11 @@ __device__ __forceinline__ double surf_f(const World &W, int sid, double x, doub
     case SURF_PLANE: return __ldg(c) * x + __ldg(c + 1) * y + __ldg(c + 2) * z - __ldg(c + 3);
     case SURF_CYLZ: {
         double dx = x - __ldg(c), dy = y - __ldg(c + 1);
-        return dx * dx + dy * dy - __ldg(W.s_r2 + sid);
+        return fma(dx, dx, dy * dy) - __ldg(W.s_r2 + sid);
     }
     default: {
         double dx = x - __ldg(c), dy = y - __ldg(c + 1), dz = z - __ldg(c + 2);
-        return dx * dx + dy * dy + dz * dz - __ldg(W.s_r2 + sid);
+        return fma(dx, dx, fma(dy, dy, dz * dz)) - __ldg(W.s_r2 + sid);
     }
     }
 }
@@ -299,25 +308,30 @@ __device__ __forceinline__ double surf_gdot(const World &W, int sid, double x, d
 
 // Distance to leaving the half-space of the given sense.  The root is chosen
 // from the sense (so a surface just crossed is never re-hit), quadratic roots
-// use cancellation-free forms, and round-off negatives become 0.
+// use cancellation-free forms, and round-off negatives become 0.  Axis planes
+// (and lattice walls) use the direction's reciprocal, t = (x0 - x)(1/u);
+// quadratic terms are evaluated with fused multiply-adds.
 __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, double x, double y,
-                                            double z, double u, double v, double w)
+                                            double z, double u, double v, double w, double iu,
+                                            double iv, double iw)
 {
     const double *c = W.s_coef + 4 * sid;
     int type = __ldg(W.s_type + sid);
     double t;
     if (type <= SURF_PLANE) {
-        double dn, f;
+        double dn, f, inv;
         switch (type) {
-        case SURF_PX: dn = u; f = x - __ldg(c); break;
-        case SURF_PY: dn = v; f = y - __ldg(c); break;
-        case SURF_PZ: dn = w; f = z - __ldg(c); break;
+        case SURF_PX: dn = u; f = x - __ldg(c); inv = iu; break;
+        case SURF_PY: dn = v; f = y - __ldg(c); inv = iv; break;
+        case SURF_PZ: dn = w; f = z - __ldg(c); inv = iw; break;
         default:
             dn = __ldg(c) * u + __ldg(c + 1) * v + __ldg(c + 2) * w;
             f = __ldg(c) * x + __ldg(c + 1) * y + __ldg(c + 2) * z - __ldg(c + 3);
+            inv = 0.0;
         }
         if ((sense > 0 && is_neg(dn)) || (sense < 0 && is_pos(dn))) {
-            t = -f / dn;
+            // axis planes use the direction's reciprocal, other planes divide
+            t = type == SURF_PLANE ? -f / dn : -f * inv;
             return is_neg(t) ? 0.0 : t;
         }
         return MCGB_INF;
@@ -325,17 +339,17 @@ __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, 
     double a, b, cc;
     if (type == SURF_CYLZ) {
         double dx = x - __ldg(c), dy = y - __ldg(c + 1);
-        a = u * u + v * v;
-        b = dx * u + dy * v;
-        cc = dx * dx + dy * dy - __ldg(W.s_r2 + sid);
+        a = fma(u, u, v * v);
+        b = fma(dx, u, dy * v);
+        cc = fma(dx, dx, dy * dy) - __ldg(W.s_r2 + sid);
     } else {
         double dx = x - __ldg(c), dy = y - __ldg(c + 1), dz = z - __ldg(c + 2);
-        a = u * u + v * v + w * w;
-        b = dx * u + dy * v + dz * w;
-        cc = dx * dx + dy * dy + dz * dz - __ldg(W.s_r2 + sid);
+        a = fma(u, u, fma(v, v, w * w));
+        b = fma(dx, u, fma(dy, v, dz * w));
+        cc = fma(dx, dx, fma(dy, dy, dz * dz)) - __ldg(W.s_r2 + sid);
     }
     if (!is_pos(a)) return MCGB_INF;
-    double disc = b * b - a * cc;
+    double disc = fma(b, b, -(a * cc));
     // one square root and one division for every case (inside: the far root by
     // the cancellation-free form chosen by the sign of b; outside: the near root)
     double num, den;
@@ -476,7 +490,7 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
     int off = __ldg(W.c_off + p.cell), nh = __ldg(W.c_nhs + p.cell);
     for (int h = 0; h < nh; h++) {
         double t = surf_dist(W, __ldg(W.hs_surf + off + h), __ldg(W.hs_sense + off + h), p.x, p.y,
-                             p.z, p.u, p.v, p.w);
+                             p.z, p.u, p.v, p.w, p.iu, p.iv, p.iw);
         if (lt_mag(t, best)) {
             best = t;
             kind = B_ROOT;
@@ -487,12 +501,12 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
         int L = __ldg(W.c_fill + p.cell);
         int nx = __ldg(W.l_nx + L), ny = __ldg(W.l_ny + L);
         // walls x0 + i pitch, precomputed with that expression; the wall ahead is
-        // chosen first so that one division serves either direction
+        // chosen first, then t = (wall - x)(1/u)
         const double *xw = W.l_wall + __ldg(W.l_woff + L);
         const double *yw = xw + nx + 1;
         int wx = is_pos(p.u) ? (p.ix < nx - 1 ? p.ix + 1 : -1) : (is_neg(p.u) && p.ix > 0 ? p.ix : -1);
         if (wx >= 0) {
-            double t = (__ldg(xw + wx) - p.x) / p.u;
+            double t = (__ldg(xw + wx) - p.x) * p.iu;
             if (is_neg(t)) t = 0.0;
             if (lt_mag(t, best)) {
                 best = t;
@@ -501,7 +515,7 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
         }
         int wy = is_pos(p.v) ? (p.iy < ny - 1 ? p.iy + 1 : -1) : (is_neg(p.v) && p.iy > 0 ? p.iy : -1);
         if (wy >= 0) {
-            double t = (__ldg(yw + wy) - p.y) / p.v;
+            double t = (__ldg(yw + wy) - p.y) * p.iv;
             if (is_neg(t)) t = 0.0;
             if (lt_mag(t, best)) {
                 best = t;
@@ -513,7 +527,7 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
         int uoff = __ldg(W.c_off + p.ucell), unh = __ldg(W.c_nhs + p.ucell);
         for (int h = 0; h < unh; h++) {
             double tt = surf_dist(W, __ldg(W.hs_surf + uoff + h), __ldg(W.hs_sense + uoff + h), xl,
-                                  yl, p.z, p.u, p.v, p.w);
+                                  yl, p.z, p.u, p.v, p.w, p.iu, p.iv, p.iw);
             if (lt_mag(tt, best)) {
                 best = tt;
                 kind = B_UNIV;
@@ -536,9 +550,9 @@ __device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
         if (bc == BC_VACUUM) return 1;
         if (bc == BC_REFLECT) {
             switch (__ldg(W.s_type + sid)) {
-            case SURF_PX: p.u = -p.u; break;
-            case SURF_PY: p.v = -p.v; break;
-            case SURF_PZ: p.w = -p.w; break;
+            case SURF_PX: p.u = -p.u; p.iu = -p.iu; break;
+            case SURF_PY: p.v = -p.v; p.iv = -p.iv; break;
+            case SURF_PZ: p.w = -p.w; p.iw = -p.iw; break;
             default: {
                 const double *c = W.s_coef + 4 * sid;
                 double a = __ldg(c), b = __ldg(c + 1), cz = __ldg(c + 2);
@@ -548,6 +562,7 @@ __device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
                 p.u = p.u - k * a;
                 p.v = p.v - k * b;
                 p.w = p.w - k * cz;
+                set_recip(p);
             }
             }
             return 0;
@@ -718,6 +733,7 @@ __device__ __forceinline__ bool sample_source(const World &W, const ProblemDev &
     } else {
         iso_dir(p.s, p.u, p.v, p.w);
     }
+    set_recip(p);
     return true;
 }
 
@@ -734,6 +750,7 @@ __device__ __forceinline__ void birth_from_site(const World &W, const ProblemDev
     p.mat = B.mat[b];
     birth_energy(W, P, p);
     iso_dir(p.s, p.u, p.v, p.w);
+    set_recip(p);
 }
 
 }  // namespace mcgb

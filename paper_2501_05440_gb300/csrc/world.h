@@ -98,6 +98,7 @@ struct World {
 
 struct Particles {
     double *x, *y, *z, *u, *v, *w, *E;
+    double *iu, *iv, *iw;   // direction reciprocals
     double *kt, *kc;      // per-history k estimator sums (track length, collision)
     uint64_t *s;
     int *g, *cell, *ix, *iy, *ucell, *mat, *uk, *prob, *root, *nfis, *ncoll, *ncross, *bwhich;

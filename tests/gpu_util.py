@@ -5,9 +5,9 @@ import workloads as W
 from oracle import Oracle
 
 
-def gpu_run(pb, mode=0, record=True, pool=0, **over):
+def gpu_run(pb, mode=0, record=True, pool=0, graphs=0, **over):
     import paper_2501_05440_gb300 as m
-    c = m.Context(mode=mode, record_histories=record, pool=pool)
+    c = m.Context(mode=mode, record_histories=record, pool=pool, graphs=graphs)
     m.load_problem(c, pb)
     c.run(**over)
     return c

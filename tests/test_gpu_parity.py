@@ -91,15 +91,18 @@ def test_ce_lookup_bit_exact(mcgb):
             assert np.array_equal(out[i], o.ce_lookup(mat, float(E[i])))
 
 
-# execution variants: (mode, pool): one kernel per event; persistent with
-# block-sorted pools of 512 (default), 256 or 1024 particles; register-resident
-VARIANTS = [(0, 0), (1, 0), (1, 256), (1, 1024), (1, -1)]
-FEW = [(0, 0), (1, 0), (1, -1)]
+# execution variants (mode, pool, graphs): one kernel per event; persistent with
+# sorted pools (default, 256/1024 per 256-thread block, 256 per 128-thread
+# block, 64 per warp), cycles replayed as CUDA graphs or launched one by one;
+# one particle per thread in registers
+VARIANTS = [(0, 0, 0), (1, 0, 0), (1, 0, -1), (1, 256, 0), (1, 1024, 0), (1, 2256, 0),
+            (1, 64, 0), (1, -1, 0)]
+FEW = [(0, 0, 0), (1, 0, 0), (1, -1, -1)]
 
 
-def _eigen_parity(mcgb, pb, mode, pool=0):
+def _eigen_parity(mcgb, pb, mode, pool=0, graphs=0):
     ncyc = pb["run"]["inactive"] + pb["run"]["active"]
-    c = gpu_run(pb, mode=mode, pool=pool)
+    c = gpu_run(pb, mode=mode, pool=pool, graphs=graphs)
     o = oracle_run(pb)
     gk, gc, gm = c.get_cycle_k(ncyc)
     ok, oc, om = o.cycle_k(ncyc)
@@ -123,23 +126,39 @@ def _eigen_parity(mcgb, pb, mode, pool=0):
     return c, o
 
 
-@pytest.mark.parametrize("mode,pool", VARIANTS)
-def test_pin_cell_eigen_parity(mcgb, mode, pool):
-    _eigen_parity(mcgb, W.pin_cell_mg(n=3000, inactive=3, active=5), mode, pool)
+@pytest.mark.parametrize("mode,pool,graphs", VARIANTS)
+def test_pin_cell_eigen_parity(mcgb, mode, pool, graphs):
+    _eigen_parity(mcgb, W.pin_cell_mg(n=3000, inactive=3, active=5), mode, pool, graphs)
 
 
-@pytest.mark.parametrize("mode,pool", FEW)
-def test_lattice_eigen_parity(mcgb, mode, pool):
-    _eigen_parity(mcgb, W.c5g7_like_lattice(n=4000, inactive=2, active=3), mode, pool)
+@pytest.mark.parametrize("mode,pool,graphs", FEW)
+def test_lattice_eigen_parity(mcgb, mode, pool, graphs):
+    _eigen_parity(mcgb, W.c5g7_like_lattice(n=4000, inactive=2, active=3), mode, pool, graphs)
 
 
-@pytest.mark.parametrize("mode,pool", FEW)
-def test_ce_pin_eigen_parity(mcgb, mode, pool):
-    _eigen_parity(mcgb, W.ce_pin_cell(n=600, inactive=1, active=2, npts=5000, nres=40), mode, pool)
+@pytest.mark.parametrize("mode,pool,graphs", FEW)
+def test_ce_pin_eigen_parity(mcgb, mode, pool, graphs):
+    _eigen_parity(mcgb, W.ce_pin_cell(n=600, inactive=1, active=2, npts=5000, nres=40), mode,
+                  pool, graphs)
 
 
-def _fixed_parity(mcgb, pb, mode, pool=0):
-    c = gpu_run(pb, mode=mode, pool=pool)
+def test_stepwise_cycles_equal_one_call(mcgb):
+    """begin + cycles in several calls (graphs and launches mixed) = one run call."""
+    pb = W.pin_cell_mg(n=3000, inactive=2, active=4)
+    import paper_2501_05440_gb300 as m
+    ref = gpu_run(pb, mode=1)
+    c = m.load_problem(m.Context(mode=1, record_histories=True), pb)
+    c.eigen_begin(3000, 2, 4, pb["run"]["seed"])
+    for k in (1, 2, 3):
+        c.eigen_cycles(k)
+    c.eigen_finish()
+    assert c.get_cycle_k(6)[2].tolist() == ref.get_cycle_k(6)[2].tolist()
+    assert_same_histories(c.get_histories(), ref.get_histories())
+    assert c.get_k()["k"] == pytest.approx(ref.get_k()["k"], rel=1e-12)
+
+
+def _fixed_parity(mcgb, pb, mode, pool=0, graphs=0):
+    c = gpu_run(pb, mode=mode, pool=pool, graphs=graphs)
     o = oracle_run(pb)
     assert_same_histories(c.get_histories(), o.histories())
     gb, ob = c.get_bank(), o.bank()
@@ -154,15 +173,15 @@ def _fixed_parity(mcgb, pb, mode, pool=0):
         assert cg[key] == co[key], key
 
 
-@pytest.mark.parametrize("mode,pool", FEW)
-def test_slab_fixed_source_parity(mcgb, mode, pool):
-    _fixed_parity(mcgb, W.diff_slab(n=5000, batches=10), mode, pool)
+@pytest.mark.parametrize("mode,pool,graphs", FEW)
+def test_slab_fixed_source_parity(mcgb, mode, pool, graphs):
+    _fixed_parity(mcgb, W.diff_slab(n=5000, batches=10), mode, pool, graphs)
 
 
-@pytest.mark.parametrize("mode,pool", FEW)
-def test_box_fixed_source_parity(mcgb, mode, pool):
+@pytest.mark.parametrize("mode,pool,graphs", FEW)
+def test_box_fixed_source_parity(mcgb, mode, pool, graphs):
     for pb in W.batch_boxes(nproblems=4, nmin=500, nmax=3000)[:4]:
-        _fixed_parity(mcgb, pb, mode, pool)
+        _fixed_parity(mcgb, pb, mode, pool, graphs)
 
 
 def test_one_collision_and_absorber_parity(mcgb):
