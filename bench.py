@@ -35,15 +35,18 @@ N_PER_CYCLE = 1_000_000
 # (the nominal 1.25 TFLOP/s counts an FMA as 2); a measured FP64 instruction
 # throughput probe gave 504 G/s at the clocks it ran at.
 FP64_PEAK_GOPS = 152 * 2 * 2.07
-# FP64 instructions per event of the persistent transport kernel on this
-# workload (ncu: smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on
-# plus conversions, divided by events), see profiles/.
-FP64_INST_PER_EVENT = None
+# FP64 thread-instructions per event of the persistent transport kernel on this
+# workload: ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum of one k_pool launch
+# divided by the events of that cycle (2.095e9 / 2.25e7), profiles/k_pool_c5g7_lattice.md.
+FP64_INST_PER_EVENT = 93.1
 # Algorithmic particle-state bytes an event moves in the event-based form:
 # advance reads position/direction/energy/RNG/cell path and writes position,
 # RNG, event tag; collide or cross read and write direction, group, RNG and
 # cell path (fields counted once per kernel that touches them).
 STATE_BYTES_PER_EVENT = 120.0
+# DRAM bytes (read + write) of one k_pool launch from the same ncu capture, or None
+# when the kernel has changed since the counters were taken.
+TRAFFIC_PER_LAUNCH = None
 
 
 def parse():
@@ -280,6 +283,29 @@ def grad_leg(m, W, torch, n):
             "detector_tally": float(tal.sum())}
 
 
+def ce_leg(m, W, torch, steps=3):
+    """Continuous-energy pin cell, 1e6 particles per cycle, persistent form."""
+    pb = W.ce_pin_cell(seed=1, n=N_PER_CYCLE)
+    c = m.Context(mode=m.MODE_PERSISTENT)
+    c.set_stream(torch.cuda.current_stream().cuda_stream)
+    m.load_problem(c, pb)
+    c.eigen_begin(N_PER_CYCLE, 1, steps, 1)
+    c.eigen_cycles(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    c.eigen_cycles(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c.eigen_finish()
+    cnt = c.get_counters()
+    ev = (cnt["collisions"] + cnt["crossings"]) / (steps + 1)
+    return {"workload": "ce-pin-cell-4nuclides-keff", "value": N_PER_CYCLE * steps / (ms / 1e3),
+            "unit": "histories/s", "ms_per_step": ms / steps, "events_per_s": ev * steps / (ms / 1e3),
+            "k": c.get_k()["k"]}
+
+
 def cpu_baseline(W, n=200_000):
     import oracle
     cores = os.cpu_count() or 1
@@ -318,26 +344,33 @@ def run_mcgb(args):
         "k": h["k"]["k"], "k_sd": h["k"]["k_sd"],
         "gpu_launches": h["launches"], "clocks": h["clocks"],
     }
-    # roofline of the transport kernel (the persistent event loop: one launch per cycle)
+    # roofline of the transport kernel (the persistent event loop, one launch per cycle):
+    # bound by the FP64 pipe; the HBM fraction of the event-based state traffic beside it
     ev = h["events_per_cycle"]
-    t_kernel = h["transport_ms"] / 1e3
-    if FP64_INST_PER_EVENT:
-        ach = FP64_INST_PER_EVENT * ev / t_kernel / 1e9
-        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GOPS,
-                           "unit": "G FP64 instr/s", "frac": ach / FP64_PEAK_GOPS,
-                           "traffic": None, "kernel": "k_persistent"}
-    else:
-        peak = 6777.0
-        ach = STATE_BYTES_PER_EVENT * ev / t_kernel / 1e9
-        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                           "frac": ach / peak, "traffic": None, "kernel": "k_persistent"}
+    t_kernel = max(h["transport_ms"], 1e-9) / 1e3
+    ach = FP64_INST_PER_EVENT * ev / t_kernel / 1e9
+    out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GOPS,
+                       "unit": "G FP64 thread-instr/s", "frac": ach / FP64_PEAK_GOPS,
+                       "traffic": TRAFFIC_PER_LAUNCH, "kernel": "k_pool (persistent event loop)",
+                       "per_unit": f"{FP64_INST_PER_EVENT} FP64 instr/event x {ev:.4g} events/launch",
+                       "peak_kind": "derived: 152 SMs x 2 FP64/clk x 2.07 GHz (recipe's 1.25 TFLOP/s)"}
+    hbm = STATE_BYTES_PER_EVENT * ev / t_kernel / 1e9
+    out["hbm_roofline"] = {"achieved": hbm, "peak": 6777.0, "unit": "GB/s", "frac": hbm / 6777.0,
+                           "basis": f"{STATE_BYTES_PER_EVENT:.0f} B algorithmic state per event "
+                                    "(of measured copy bandwidth)"}
     out["transport_ms_per_cycle"] = h["transport_ms"]
     if rank == 0 and not args.quick:
         out["plain_event"] = plain_leg(m, W, torch, args, max(2, args.steps // 4))
         out["e2e"] = e2e_leg(m, W, args, max(2, args.steps // 2))
         out["batched"] = batched_leg(m, W, torch)
         out["grad"] = grad_leg(m, W, torch, 1_000_000)
+        out["ce_pin"] = ce_leg(m, W, torch)
         out["cpu_baseline"] = cpu_baseline(W)
+        from paper_2501_05440_gb300.report import core_equivalency
+        cb = out["cpu_baseline"]
+        # Eq. 1 with run times of equal work (inverse rates): CPU cores per GPU
+        out["core_equivalency"] = core_equivalency(cb["cores"], 1.0 / cb["value"], world,
+                                                   1.0 / value)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if pg is not None:

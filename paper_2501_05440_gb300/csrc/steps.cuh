@@ -101,10 +101,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             *nf_out = nf;
             p.nfis += nf;
         } else {
-            for (int k = 0; k < nf; k++) {
-                bank_push(B, R.bank_n, R.err, p, slot);
-                p.nfis++;
-            }
+            bank_append(B, R.bank_n, R.err, p, slot, nf);
         }
         xi = draw(p.s);
         if (!lt_mag(__ldg(W.g_ps + go + g), xi)) {
@@ -144,10 +141,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         double fl = floor(mu);
         double xi = draw(p.s);
         int nf = (int)fl + (lt_mag(mu - fl, xi) ? 0 : 1);
-        for (int k = 0; k < nf; k++) {
-            bank_push(B, R.bank_n, R.err, p, slot);
-            p.nfis++;
-        }
+        bank_append(B, R.bank_n, R.err, p, slot, nf);
         xi = draw(p.s);
         if (!lt_mag(ss, xi * st)) {
             p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);

@@ -10,6 +10,8 @@
 // order written, without contraction (the library is built with -fmad=false),
 // so that each history is bit-reproducible on any conforming IEEE machine.
 #pragma once
+#include <cooperative_groups.h>
+
 #include <cstdint>
 
 #include "world.h"
@@ -664,28 +666,43 @@ __device__ __forceinline__ void score(const World &W, const ProblemDev &P, const
 }
 
 // ---------------------------------------------------------------------------
-// Bank a fission site (parent slot, child index) -- appended in any order and
-// put in (parent, child) order at the end of the cycle.
-__device__ __forceinline__ void bank_push(const Bank &B, int *bank_n, int *err, const PS &p,
-                                          int slot)
+// Fission sites (parent slot, child index) are appended in any order and put in
+// (parent, child) order at the end of the cycle.  The lanes that bank together
+// reserve their sites with one atomic: counts are summed and prefix-summed from
+// three ballots of their bit planes (a count of 8 or more takes its own atomic).
+__device__ __forceinline__ void bank_append(const Bank &B, int *bank_n, int *err, PS &p, int slot,
+                                            int nf)
 {
-    int pos = atomicAdd(bank_n, 1);
-    if (pos >= B.cap) {
-        atomicOr(err, ERR_BANK_OVERFLOW);
-        return;
+    cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
+    const unsigned lt = (1u << g.thread_rank()) - 1u;
+    int small = nf < 8 ? nf : 0;
+    unsigned b0 = g.ballot(small & 1), b1 = g.ballot(small & 2), b2 = g.ballot(small & 4);
+    int total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+    int before = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+    int base = 0;
+    if (g.thread_rank() == 0 && total > 0) base = atomicAdd(bank_n, total);
+    base = g.shfl(base, 0);
+    int pos0 = nf < 8 ? base + before : atomicAdd(bank_n, nf);
+    for (int k = 0; k < nf; k++) {
+        int pos = pos0 + k;
+        if (pos >= B.cap) {
+            atomicOr(err, ERR_BANK_OVERFLOW);
+        } else {
+            B.x[pos] = p.x;
+            B.y[pos] = p.y;
+            B.z[pos] = p.z;
+            B.cell[pos] = p.cell;
+            B.ix[pos] = p.ix;
+            B.iy[pos] = p.iy;
+            B.ucell[pos] = p.ucell;
+            B.mat[pos] = p.mat;
+            B.parent[pos] = slot;
+            B.child[pos] = p.nfis;
+            B.root[pos] = p.root;
+            B.prob[pos] = p.prob;
+        }
+        p.nfis++;
     }
-    B.x[pos] = p.x;
-    B.y[pos] = p.y;
-    B.z[pos] = p.z;
-    B.cell[pos] = p.cell;
-    B.ix[pos] = p.ix;
-    B.iy[pos] = p.iy;
-    B.ucell[pos] = p.ucell;
-    B.mat[pos] = p.mat;
-    B.parent[pos] = slot;
-    B.child[pos] = p.nfis;
-    B.root[pos] = p.root;
-    B.prob[pos] = p.prob;
 }
 
 // ---------------------------------------------------------------------------
