@@ -5,7 +5,8 @@ Headline: histories/s of k-eigenvalue power iteration on the C5G7-shaped
 multigroup lattice (51x51 pins, 7 groups, 1e6 particles per cycle), one step =
 one cycle (source from the resampled bank, transport of every history, bank
 ordering, resampling, tallies), persistent event-loop form.  Beside it, in the
-same JSON line: the plain one-kernel-per-event form on the same workload, the
+same JSON line: the plain one-kernel-per-event form and the monolithic
+one-kernel-per-segment form (the paper's own GPU design) on the same workload, the
 64-problem batched run against 64 separate plain runs, derivatives per second
 through the replay-backward kernel, the FP64 roofline of the transport
 kernel, the CPU oracle timed on this host's cores, and GPU clocks sampled
@@ -94,6 +95,19 @@ def max_over_ranks(pg, x):
     return float(t.item())
 
 
+def aggregate(pg, ms, units):
+    """Whole-job rate: units of every rank over the slowest rank's time (ms)."""
+    ms_max = max_over_ranks(pg, ms)
+    total = sum_over_ranks(pg, float(units))
+    return ms_max, total, total / (ms_max / 1e3)
+
+
+def replica_problem(W, n, rank):
+    """The headline problem; replica `rank` draws from its own master seed."""
+    pb = W.c5g7_like_lattice(seed=1, n=n)
+    return W.with_run(pb, seed=int(pb["run"]["seed"]) + 1000003 * rank)
+
+
 def sum_over_ranks(pg, x):
     if pg is None:
         return x
@@ -158,7 +172,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def headline(m, W, torch, args, rank, pg):
     """Persistent form: K timed cycles after W warm-up cycles."""
-    pb = W.c5g7_like_lattice(seed=1 + rank, n=args.n)
+    pb = replica_problem(W, args.n, rank)
     c = m.Context(device=int(os.environ.get("LOCAL_RANK", "0")), mode=m.MODE_PERSISTENT,
                   pool=args.pool, graphs=args.graphs)
     c.set_stream(torch.cuda.current_stream().cuda_stream)
@@ -192,9 +206,12 @@ def headline(m, W, torch, args, rank, pg):
             "counters": cnt}
 
 
-def plain_leg(m, W, torch, args, steps):
+def plain_leg(m, W, torch, args, steps, mode=None):
+    """Host-driven launch forms: one kernel per event type (MODE_EVENT) or the
+    monolithic one-kernel-per-segment design of the paper's Sec. 2 (MODE_SEGMENT)."""
+    mode = m.MODE_EVENT if mode is None else mode
     pb = W.c5g7_like_lattice(seed=1, n=args.n)
-    c = m.Context(mode=m.MODE_EVENT)
+    c = m.Context(mode=mode)
     c.set_stream(torch.cuda.current_stream().cuda_stream)
     m.load_problem(c, pb)
     c.eigen_begin(args.n, 1, steps, 1)
@@ -208,7 +225,8 @@ def plain_leg(m, W, torch, args, steps):
     ms = e0.elapsed_time(e1)
     c.eigen_finish()
     cnt = c.get_counters()
-    return {"value": args.n * steps / (ms / 1e3), "unit": "histories/s", "mode": "event",
+    return {"value": args.n * steps / (ms / 1e3), "unit": "histories/s",
+            "mode": "segment" if mode == m.MODE_SEGMENT else "event",
             "ms_per_step": ms / steps, "steps": steps,
             "event_iterations_per_cycle": cnt["event_iterations"] / (steps + 1)}
 
@@ -329,9 +347,7 @@ def run_mcgb(args):
     torch.cuda.set_device(local)
     m.build()
     h = headline(m, W, torch, args, rank, pg)
-    ms_max = max_over_ranks(pg, h["ms"])
-    hist_total = sum_over_ranks(pg, float(h["n"] * args.steps))
-    value = hist_total / (ms_max / 1e3)
+    ms_max, hist_total, value = aggregate(pg, h["ms"], h["n"] * args.steps)
     out = {
         "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -361,6 +377,8 @@ def run_mcgb(args):
     out["transport_ms_per_cycle"] = h["transport_ms"]
     if rank == 0 and not args.quick:
         out["plain_event"] = plain_leg(m, W, torch, args, max(2, args.steps // 4))
+        out["monolithic_segment"] = plain_leg(m, W, torch, args, max(2, args.steps // 4),
+                                              m.MODE_SEGMENT)
         out["e2e"] = e2e_leg(m, W, args, max(2, args.steps // 2))
         out["batched"] = batched_leg(m, W, torch)
         out["grad"] = grad_leg(m, W, torch, 1_000_000)

@@ -66,7 +66,11 @@ enum { MCGB_DIR_ISO = 0, MCGB_DIR_BEAM = 1 };
 enum { MCGB_FILTER_CELL = 0, MCGB_FILTER_LATTICE = 1, MCGB_FILTER_MATERIAL = 2 };
 /* execution modes */
 enum { MCGB_MODE_EVENT = 0,       /* one kernel per event type, host-driven loop */
-       MCGB_MODE_PERSISTENT = 1 };/* one grid-resident event loop per cycle, CUDA graph */
+       MCGB_MODE_PERSISTENT = 1,  /* one grid-resident event loop per cycle, CUDA graph */
+       MCGB_MODE_SEGMENT = 2 };   /* the monolithic event design of Sec. 2: one kernel per
+                                     segment (flight, then the crossing or collision it
+                                     ends in) for every live particle, unsorted, with two
+                                     alternating particle lists; host-driven loop */
 
 /* Options.  Zero-initialised fields take defaults. */
 typedef struct {
@@ -76,7 +80,7 @@ typedef struct {
     int blocks_per_sm;      /* persistent mode: resident blocks per SM (default: occupancy) */
     int record_histories;   /* keep per-history records of the last cycle / generation 0 */
     double bank_factor;     /* fission bank capacity as a multiple of N (default 3) */
-    int max_iterations;     /* event-mode iteration limit per cycle (default 1e7) */
+    int max_iterations;     /* event / segment mode iteration limit per cycle (default 1e7) */
     int pool;               /* persistent mode: particles held in shared memory and run
                                event type by event type from sorted lists: 256, 512 or
                                1024 per 256-thread block; 2256 or 2512 for 256 or 512 per
@@ -92,7 +96,7 @@ typedef struct {
 typedef struct {
     int64_t histories, collisions, crossings, leaks, lost, capped, generations;
     int64_t kernel_launches;   /* kernels this library launched during the run */
-    int64_t event_iterations;  /* event mode: host loop iterations */
+    int64_t event_iterations;  /* event / segment mode: host loop iterations */
     int64_t world_bytes;       /* bytes of problem tables uploaded to the device */
 } mcgb_counters;
 

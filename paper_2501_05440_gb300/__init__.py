@@ -15,14 +15,14 @@ import threading
 import numpy as np
 
 __all__ = ["lib", "build", "McgbError", "Context", "Batch", "load_problem", "library_path",
-           "bank_offsets_noalloc", "MODE_EVENT", "MODE_PERSISTENT"]
+           "bank_offsets_noalloc", "MODE_EVENT", "MODE_PERSISTENT", "MODE_SEGMENT"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "_build", "libmcgb.so")
 _lock = threading.Lock()
 _lib = None
 
-MODE_EVENT, MODE_PERSISTENT = 0, 1
+MODE_EVENT, MODE_PERSISTENT, MODE_SEGMENT = 0, 1, 2
 SURF = {"px": 0, "py": 1, "pz": 2, "plane": 3, "cylz": 4, "sphere": 5}
 BC = {"none": 0, "vacuum": 1, "reflect": 2}
 FILL = {"material": 0, "lattice": 1}

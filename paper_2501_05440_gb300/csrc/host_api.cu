@@ -2,8 +2,9 @@
 //
 // A run keeps all particle state, banks and accumulators in device memory.
 // Power iteration per cycle: transport N histories (event mode: a host loop of
-// advance / cross / collide kernels over compacted queues; persistent mode: one
-// grid-resident kernel), then on the device: reduce k estimators, scan the
+// advance / cross / collide kernels over compacted queues; segment mode: a host
+// loop of one monolithic segment kernel; persistent mode: one grid-resident
+// kernel), then on the device: reduce k estimators, scan the
 // per-history site counts, permute the bank into (parent, child) order,
 // resample N sources, fold the cycle's tallies into the batch statistics.
 #include <algorithm>
@@ -271,10 +272,15 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
         if (it >= maxit) return fail(MCGB_E_TIMEOUT, "event iteration limit reached");
         CK(cudaMemsetAsync(r.q_n, 0, 3 * sizeof(int), st));
         int *next = r.list[cur];
-        launch_advance(W, r.P, R, list, (int)n_act, r.q_cross, r.q_coll, block, st);
-        launch_cross(W, r.P, R, r.q_cross, (int)n_act, next, block, st);
-        launch_collide(W, r.P, Bdst, R, r.q_coll, (int)n_act, next, block, st);
-        c->launches += 3;
+        if (c->opts.mode == MCGB_MODE_SEGMENT) {
+            launch_segment(W, r.P, Bdst, R, list, (int)n_act, next, block, st);
+            c->launches += 1;
+        } else {
+            launch_advance(W, r.P, R, list, (int)n_act, r.q_cross, r.q_coll, block, st);
+            launch_cross(W, r.P, R, r.q_cross, (int)n_act, next, block, st);
+            launch_collide(W, r.P, Bdst, R, r.q_coll, (int)n_act, next, block, st);
+            c->launches += 3;
+        }
         CK(cudaMemcpyAsync(r.pinned, r.q_n + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         n_act = r.pinned[0];
@@ -858,6 +864,8 @@ int mcgb_create(mcgb_ctx **out, const mcgb_opts *opts)
     c->device = c->opts.device;
     CK(cudaSetDevice(c->device));
     CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (c->opts.mode < MCGB_MODE_EVENT || c->opts.mode > MCGB_MODE_SEGMENT)
+        return fail(MCGB_E_INVALID_ARG, "mode must be MCGB_MODE_EVENT, _PERSISTENT or _SEGMENT");
     if (c->opts.block != 0 && (c->opts.block < 32 || c->opts.block > 256 || c->opts.block % 32))
         return fail(MCGB_E_INVALID_ARG, "block must be a multiple of 32 in [32, 256]");
     {
@@ -897,7 +905,7 @@ int mcgb_set_stream(mcgb_ctx *ctx, void *stream)
 
 int mcgb_set_mode(mcgb_ctx *ctx, int mode)
 {
-    if (!ctx || (mode != MCGB_MODE_EVENT && mode != MCGB_MODE_PERSISTENT))
+    if (!ctx || mode < MCGB_MODE_EVENT || mode > MCGB_MODE_SEGMENT)
         return fail(MCGB_E_INVALID_ARG, "bad mode");
     ctx->opts.mode = mode;
     return MCGB_OK;

@@ -411,6 +411,9 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(t_eoff, int, o_teoff); P_(t_nedges, int, o_tned); P_(t_batches, int, o_tbat);
     P_(t_edges, double, o_tedges);
 #undef P_
+    W.need_iw = 0;
+    for (int t : s_type)
+        if (t == SURF_PZ) W.need_iw = 1;
     W.nunion = (int)Eu.size();
     W.nnuc = (int)nucs.size();
     W.acc_size = (int)acc_size;

@@ -18,6 +18,8 @@ void launch_cross(const World &W, const Particles &P, const RunBufs &R, const in
                   int n_bound, int *next, int block, cudaStream_t st);
 void launch_collide(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
                     const int *q_coll, int n_bound, int *next, int block, cudaStream_t st);
+void launch_segment(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
+                    const int *list, int n, int *next, int block, cudaStream_t st);
 
 // ---- persistent event loop -------------------------------------------------
 struct PersistentArgs {

@@ -51,7 +51,7 @@ __global__ void k_probe(World W, int root_univ, int64_t n, const double *pos, co
     PS p;
     p.x = pos[3 * i]; p.y = pos[3 * i + 1]; p.z = pos[3 * i + 2];
     p.u = dir[3 * i]; p.v = dir[3 * i + 1]; p.w = dir[3 * i + 2];
-    set_recip(p);
+    set_recip(W, p);
     p.ix = p.iy = p.ucell = -1;
     p.cell = p.mat = -1;
     if (!locate_full(W, root_univ, p)) {

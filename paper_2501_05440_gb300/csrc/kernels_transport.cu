@@ -139,6 +139,39 @@ __global__ void __launch_bounds__(256) k_collide(World W, Particles P, Bank Bdst
     enqueue(alive, i, next, R.q_n + 2);
 }
 
+// Monolithic segment (Sec. 2: every transport operation of one segment in a
+// single kernel, no sorting or grouping of like operations): flight, then the
+// crossing or collision it ends in; survivors go to the other list.
+__global__ void __launch_bounds__(256) k_segment(World W, Particles P, Bank Bdst, RunBufs R,
+                                                 const int *list, int n, int *next)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = -1;
+    bool alive = false;
+    if (t < n) {
+        i = list ? list[t] : t;
+        PS p;
+        load_ps(P, i, p);
+        if (p.fate == FATE_ALIVE) {
+            const ProblemDev &Pd = W.prob[p.prob];
+            int kind, which, uk = 0;
+            double kt = P.kt[i];
+            int ev = step_advance(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
+            P.kt[i] = kt;
+            if (ev == EV_CROSS) {
+                ev = step_cross(W, p, kind, which);
+            } else if (ev == EV_COLLIDE) {
+                double kc = P.kc[i];
+                ev = step_collide(W, Pd, p, i, Bdst, R, uk, kc);
+                P.kc[i] = kc;
+            }
+            store_ps(P, i, p);
+            alive = ev == EV_ADVANCE;
+        }
+    }
+    enqueue(alive, i, next, R.q_n + 2);
+}
+
 static inline int nblocks(int64_t n, int block) { return (int)((n + block - 1) / block); }
 
 void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const RunBufs &R, int gen,
@@ -169,6 +202,13 @@ void launch_collide(const World &W, const Particles &P, const Bank &Bdst, const 
 {
     if (n_bound <= 0) return;
     k_collide<<<nblocks(n_bound, block), block, 0, st>>>(W, P, Bdst, R, q_coll, next);
+}
+
+void launch_segment(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
+                    const int *list, int n, int *next, int block, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_segment<<<nblocks(n, block), block, 0, st>>>(W, P, Bdst, R, list, n, next);
 }
 
 // ---------------------------------------------------------------------------

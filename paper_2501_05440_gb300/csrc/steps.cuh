@@ -54,7 +54,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
         *d_out = d;
     } else {
         score(W, P, p, d, tally_batch(P, p), R.tacc, rep);
-        kt = kt + d * nusf;
+        kt = fma(d, nusf, kt);   // a sum over histories: agreement within rounding only
         if (R.own && (p.ucell >= 0 ? p.ucell : p.cell) == R.own_cell)
             R.own[(int64_t)slot * R.own_G + p.g] += d;
     }
@@ -108,7 +108,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             xi = draw(p.s);
             p.g = sample_cdf(W.gg_scdf + __ldg(W.m_ggoff + p.mat) + g * G, G, xi);
             iso_dir(p.s, p.u, p.v, p.w);
-            set_recip(p);
+            set_recip(W, p);
         } else {
             p.fate = FATE_ABSORBED;
             return EV_DEAD;
@@ -145,7 +145,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         xi = draw(p.s);
         if (!lt_mag(ss, xi * st)) {
             p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);
-            set_recip(p);
+            set_recip(W, p);
         } else {
             p.fate = FATE_ABSORBED;
             return EV_DEAD;

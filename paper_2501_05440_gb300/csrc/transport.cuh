@@ -266,11 +266,12 @@ struct PS {
     int g, cell, ix, iy, ucell, mat, prob, root, nfis, ncoll, ncross, fate;
 };
 
-__device__ __forceinline__ void set_recip(PS &p)
+// 1/w is read only by z-planes; a world without them never computes it
+__device__ __forceinline__ void set_recip(const World &W, PS &p)
 {
     p.iu = 1.0 / p.u;
     p.iv = 1.0 / p.v;
-    p.iw = 1.0 / p.w;
+    if (W.need_iw) p.iw = 1.0 / p.w;
 }
 
 // ---------------------------------------------------------------------------
@@ -352,25 +353,18 @@ __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, 
     }
     if (!is_pos(a)) return MCGB_INF;
     double disc = fma(b, b, -(a * cc));
-    // one square root and one division for every case (inside: the far root by
-    // the cancellation-free form chosen by the sign of b; outside: the near root)
-    double num, den;
-    if (sense < 0) {
-        if (is_neg(disc)) disc = 0.0;
-        double sq = sqrt(disc);
-        if (!is_pos(b)) {
-            num = -b + sq;
-            den = a;
-        } else {
-            num = -cc;
-            den = b + sq;
-        }
-    } else {
-        if (!is_neg(b) || is_neg(disc)) return MCGB_INF;
-        double sq = sqrt(disc);
-        num = cc;
-        den = -b + sq;
-    }
+    // Inside: the far root by the cancellation-free form chosen by the sign of
+    // b, (|b| + sq) / a for b <= 0, -cc / (|b| + sq) for b > 0; outside, when
+    // approaching and hit: the near root cc / (|b| + sq).  The operands are
+    // selected first so that one square root, one addition and one division
+    // serve every lane of a warp, whichever of the cases its lanes are in.
+    const bool inside = sense < 0;
+    if (!inside && (!is_neg(b) || is_neg(disc))) return MCGB_INF;
+    if (is_neg(disc)) disc = 0.0;
+    double s1 = fabs(b) + sqrt(disc);
+    const bool far_plus = inside && !is_pos(b);
+    double num = far_plus ? s1 : (inside ? -cc : cc);
+    double den = far_plus ? a : s1;
     t = num / den;
     return is_neg(t) ? 0.0 : t;
 }
@@ -564,7 +558,7 @@ __device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
                 p.u = p.u - k * a;
                 p.v = p.v - k * b;
                 p.w = p.w - k * cz;
-                set_recip(p);
+                set_recip(W, p);
             }
             }
             return 0;
@@ -750,7 +744,7 @@ __device__ __forceinline__ bool sample_source(const World &W, const ProblemDev &
     } else {
         iso_dir(p.s, p.u, p.v, p.w);
     }
-    set_recip(p);
+    set_recip(W, p);
     return true;
 }
 
@@ -767,7 +761,7 @@ __device__ __forceinline__ void birth_from_site(const World &W, const ProblemDev
     p.mat = B.mat[b];
     birth_energy(W, P, p);
     iso_dir(p.s, p.u, p.v, p.w);
-    set_recip(p);
+    set_recip(W, p);
 }
 
 }  // namespace mcgb

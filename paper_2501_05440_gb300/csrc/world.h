@@ -56,6 +56,7 @@ struct ProblemDev {
 
 struct World {
     int nprob;
+    int need_iw;            // some z-plane exists: 1/w is read (else it is never computed)
     const ProblemDev *prob;
     // surfaces
     const int *s_type, *s_bc;

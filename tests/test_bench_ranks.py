@@ -1,0 +1,72 @@
+"""Multi-rank bench path on CPU: two gloo ranks run the same aggregation the
+GPU ranks run under torchrun (barrier, slowest-rank time, summed units), and
+replicas share the problem but not the random streams."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+RANK_SCRIPT = r"""
+import json, os, sys
+sys.path.insert(0, os.environ["ROOT"])
+import bench
+import workloads as W
+
+class A: pass
+rank, world, local, pg = bench.dist_setup(A())
+assert pg is not None and pg.get_backend() == "gloo"
+bench.barrier(pg)
+ms = [12.5, 20.0][rank]
+units = [1000, 3000][rank]
+ms_max, total, value = bench.aggregate(pg, ms, units)
+pb = bench.replica_problem(W, 100, rank)
+print(json.dumps({"rank": rank, "world": world, "ms_max": ms_max, "total": total,
+                  "value": value, "seed": pb["run"]["seed"],
+                  "sigt0": float(pb["materials"][0]["sigma_t"][0])}), flush=True)
+pg.destroy_process_group()
+"""
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_gloo_ranks_aggregate_like_torchrun(tmp_path):
+    pytest.importorskip("torch.distributed")
+    script = tmp_path / "rank.py"
+    script.write_text(RANK_SCRIPT)
+    port = _free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, ROOT=ROOT, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
+        procs.append(subprocess.Popen([sys.executable, str(script)], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=180)
+        assert p.returncode == 0, err[-2000:]
+        outs.append(__import__("json").loads(out.strip().splitlines()[-1]))
+    for o in outs:
+        assert o["world"] == 2
+        assert o["ms_max"] == 20.0                        # slowest rank
+        assert o["total"] == 4000.0                       # units of both ranks
+        assert o["value"] == pytest.approx(4000.0 / 0.020)
+    # same problem tables on both replicas, distinct master seeds
+    assert outs[0]["sigt0"] == outs[1]["sigt0"]
+    assert outs[0]["seed"] != outs[1]["seed"]
+
+
+def test_reference_arm_nonzero_rank_exits_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
