@@ -82,11 +82,12 @@ typedef struct {
     double bank_factor;     /* fission bank capacity as a multiple of N (default 3) */
     int max_iterations;     /* event / segment mode iteration limit per cycle (default 1e7) */
     int pool;               /* persistent mode: particles held in shared memory and run
-                               event type by event type from sorted lists: 256, 512 or
-                               1024 per 256-thread block; 2256 or 2512 for 256 or 512 per
+                               event type by event type from sorted lists: 256 (one per
+                               thread, three resident blocks per SM), 512 or 1024 per
+                               256-thread block; 2256 or 2512 for 256 or 512 per
                                128-thread block; 32, 64 or 128 per warp (warp-level
-                               lists, no block barriers); 0 = default; -1 = one particle
-                               per thread in registers */
+                               lists, no block barriers); 0 = default (256); -1 = one
+                               particle per thread in registers */
     int graphs;             /* persistent mode: run every eigenvalue cycle after the first
                                as one CUDA graph launch, with no host synchronisation
                                between cycles (0 = on, -1 = off) */

@@ -242,7 +242,7 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
         a.work = r.work;
         a.chunk = 1;
         a.gen_dev = gen_dev;
-        int pool = c->opts.pool == 0 ? 512 : c->opts.pool;
+        int pool = c->opts.pool == 0 ? 256 : c->opts.pool;
         if (pool > 0) {
             int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
                                                  : std::max(1, pool_max_blocks_per_sm(pool));

@@ -122,9 +122,16 @@ __device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, Ke
 }
 
 // P particles per block of T threads; the register budget is planned for
-// 65536 / (T * 128) resident blocks (at most 128 registers per thread).
+// pool_min_blocks(P, T) resident blocks (128 registers per thread at 2 blocks
+// of 256 threads; a pool of one particle per thread trades a few spilled
+// registers for a third resident block, which the shared memory allows).
+__host__ __device__ constexpr int pool_min_blocks(int P, int T)
+{
+    return (P <= T && T == 256) ? 3 : 65536 / (T * 128);
+}
+
 template <int P, int T>
-__global__ void __launch_bounds__(T, 65536 / (T * 128)) k_pool(World W, Particles G, Bank Bsrc,
+__global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Particles G, Bank Bsrc,
                                                                Bank Bdst, RunBufs R,
                                                                PersistentArgs a)
 {

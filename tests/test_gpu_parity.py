@@ -92,10 +92,10 @@ def test_ce_lookup_bit_exact(mcgb):
 
 
 # execution variants (mode, pool, graphs): one kernel per event; persistent with
-# sorted pools (default, 256/1024 per 256-thread block, 256 per 128-thread
+# sorted pools (default 256, 512/1024 per 256-thread block, 256 per 128-thread
 # block, 64 per warp), cycles replayed as CUDA graphs or launched one by one;
 # one particle per thread in registers; the monolithic segment kernel (mode 2)
-VARIANTS = [(0, 0, 0), (1, 0, 0), (1, 0, -1), (1, 256, 0), (1, 1024, 0), (1, 2256, 0),
+VARIANTS = [(0, 0, 0), (1, 0, 0), (1, 0, -1), (1, 512, 0), (1, 1024, 0), (1, 2256, 0),
             (1, 64, 0), (1, -1, 0), (2, 0, 0)]
 FEW = [(0, 0, 0), (1, 0, 0), (1, -1, -1), (2, 0, 0)]
 
