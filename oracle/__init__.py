@@ -74,6 +74,12 @@ def lib():
             L.orc_history_count.argtypes = [P]
             L.orc_bank_count.restype = i64
             L.orc_bank_count.argtypes = [P]
+            L.orc_set_time.restype = i32
+            L.orc_set_time.argtypes = [P, d, d]
+            L.orc_set_inverse_speeds.restype = i32
+            L.orc_set_inverse_speeds.argtypes = [P, i32, P]
+            L.orc_set_tally_time_bins.restype = i32
+            L.orc_set_tally_time_bins.argtypes = [P, i32, i32, P]
             for name in ["orc_add_surface", "orc_add_cell", "orc_set_groups", "orc_add_material_mg",
                          "orc_add_material_ce", "orc_set_source", "orc_add_tally",
                          "orc_set_max_collisions", "orc_get_k", "orc_get_cycle_k",
@@ -164,6 +170,18 @@ class Oracle:
             edges = _f64(t.get("edges", [0.0]))
             ne = len(edges) if "edges" in t else 0
             self._chk(L.orc_add_tally(c, FILTER[t["filter"]], ne, _p(edges)))
+        if "time" in pb:
+            tm = pb["time"]
+            self._chk(L.orc_set_time(c, float(tm.get("t0", 0.0)), float(tm["t_cut"])))
+            if pb["G"] > 0:
+                inv_v = _f64(tm["inv_v"])
+                self._keep.append(inv_v)
+                self._chk(L.orc_set_inverse_speeds(c, len(inv_v), _p(inv_v)))
+        for i, t in enumerate(pb["tallies"]):
+            if "time_edges" in t:
+                te = _f64(t["time_edges"])
+                self._keep.append(te)
+                self._chk(L.orc_set_tally_time_bins(c, i, len(te), _p(te)))
         self._chk(L.orc_set_max_collisions(c, int(pb["run"].get("max_collisions", 0))))
 
     # ---------------------------------------------------------------- runs
@@ -188,17 +206,23 @@ class Oracle:
         return ktl, kc, m
 
     def tally(self, t: int = 0):
-        nb, ne = C.c_int(), C.c_int()
-        self._chk(self.L.orc_tally_size(self.ctx, t, C.byref(nb), C.byref(ne)))
-        mean = np.zeros(nb.value * ne.value)
+        """Means and sds per (bin, group or energy bin), with a trailing time-bin
+        axis when the tally has time bins."""
+        nb, ne, nt = C.c_int(), C.c_int(), C.c_int()
+        self._chk(self.L.orc_tally_size(self.ctx, t, C.byref(nb), C.byref(ne), C.byref(nt)))
+        mean = np.zeros(nb.value * ne.value * nt.value)
         sd = np.zeros_like(mean)
         self._chk(self.L.orc_get_tally(self.ctx, t, _p(mean), _p(sd)))
-        return mean.reshape(nb.value, ne.value), sd.reshape(nb.value, ne.value)
+        shape = (nb.value, ne.value)
+        if "time_edges" in self.problem["tallies"][t]:
+            shape = shape + (nt.value,)
+        return mean.reshape(shape), sd.reshape(shape)
 
     def counters(self):
-        out = np.zeros(7, dtype=np.int64)
+        out = np.zeros(8, dtype=np.int64)
         self.L.orc_get_counters(self.ctx, _p(out))
-        keys = ["histories", "collisions", "crossings", "leaks", "lost", "capped", "generations"]
+        keys = ["histories", "collisions", "crossings", "leaks", "lost", "capped", "generations",
+                "time_cut"]
         return dict(zip(keys, out.tolist()))
 
     def histories(self):

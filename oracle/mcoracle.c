@@ -281,10 +281,14 @@ typedef struct {
     double p[6], beam[3];
     double *edata, *ecdf;
 } Source;
-typedef struct { int filter, nedges; double *edges; int nbins, ne; } Tally;
+typedef struct {
+    int filter, nedges; double *edges; int nbins, ne;
+    int ntb;                     /* time bins (0: track length, no time binning) */
+    double *tedges, *tinvw;      /* time edges and 1 / bin width */
+} Tally;
 
 typedef struct {
-    double x, y, z;
+    double x, y, z, t;
     int cell, ix, iy, ucell, mat;
     int64_t parent, root;
     int32_t child;
@@ -304,13 +308,17 @@ struct orc_ctx {
     Source src;
     int src_set;
     Tally *tally;
+    /* time dependence: source time, cutoff, 1/v per group, CE speed constant */
+    int time_on;
+    double t0, tcut, kv;
+    double *invv;
     /* results */
     double k[6];
     int ncyc;
     double *cyc_ktl, *cyc_kc;
     int64_t *cyc_m;
     double **t_sum, **t_sum2, **t_mean, **t_sd;
-    int64_t counters[7];
+    int64_t counters[8];
     int64_t nhist;
     int32_t *h_coll, *h_cross, *h_fis, *h_fate, *h_g;
     uint64_t *h_rng;
@@ -374,7 +382,10 @@ void orc_destroy(orc_ctx *c)
         free(c->nuc[i].E); free(c->nuc[i].s); free(c->nuc[i].c); free(c->nuc[i].f);
     }
     for (int i = 0; i < c->nmc; i++) { free(c->mce[i].nuc); free(c->mce[i].dens); }
-    for (int i = 0; i < c->nt; i++) free(c->tally[i].edges);
+    for (int i = 0; i < c->nt; i++) {
+        free(c->tally[i].edges); free(c->tally[i].tedges); free(c->tally[i].tinvw);
+    }
+    free(c->invv);
     free(c->src.edata); free(c->src.ecdf);
     free(c->surf); free(c->cell); free(c->hs_surf); free(c->hs_sense); free(c->lat);
     free(c->uoff); free(c->ulist); free(c->mg); free(c->nuc); free(c->mce); free(c->tally);
@@ -571,7 +582,43 @@ int orc_add_tally(orc_ctx *c, int filter, int n_edges, const double *edges)
     t->filter = filter;
     t->nedges = n_edges;
     t->edges = dup_d(edges, n_edges);
+    t->ntb = 0;
+    t->tedges = t->tinvw = NULL;
     return c->nt++;
+}
+
+int orc_set_time(orc_ctx *c, double t0, double t_cut)
+{
+    if (!(t_cut > t0) || !(t_cut < INF) || !(t0 >= 0.0))
+        return fail(c, ORC_EINVAL, "need 0 <= t0 < t_cut < inf");
+    c->time_on = 1;
+    c->t0 = t0;
+    c->tcut = t_cut;
+    return 0;
+}
+
+int orc_set_inverse_speeds(orc_ctx *c, int G, const double *inv_v)
+{
+    if (G != c->G || G <= 0) return fail(c, ORC_EINVAL, "one inverse speed per group");
+    for (int g = 0; g < G; g++)
+        if (!(inv_v[g] > 0.0) || !(inv_v[g] < INF)) return fail(c, ORC_EINVAL, "bad inverse speed");
+    free(c->invv);
+    c->invv = dup_d(inv_v, G);
+    return 0;
+}
+
+int orc_set_tally_time_bins(orc_ctx *c, int tally, int n_edges, const double *edges)
+{
+    if (tally < 0 || tally >= c->nt || n_edges < 2) return fail(c, ORC_EINVAL, "bad time bins");
+    for (int k = 0; k + 1 < n_edges; k++)
+        if (!(edges[k + 1] > edges[k])) return fail(c, ORC_EINVAL, "time edges must increase");
+    Tally *t = &c->tally[tally];
+    free(t->tedges); free(t->tinvw);
+    t->ntb = n_edges - 1;
+    t->tedges = dup_d(edges, n_edges);
+    t->tinvw = malloc(sizeof(double) * (size_t)t->ntb);
+    for (int k = 0; k < t->ntb; k++) t->tinvw[k] = 1.0 / (edges[k + 1] - edges[k]);
+    return 0;
 }
 
 int orc_set_max_collisions(orc_ctx *c, int max_collisions)
@@ -722,6 +769,7 @@ static int locate_univ(const orc_ctx *c, int U, double x, double y, double z, do
 typedef struct {
     double x, y, z, u, v, w, E;
     double iu, iv, iw;           /* 1/u, 1/v, 1/w, rounded when the direction is set */
+    double t;                    /* time (s), when the problem is time dependent */
     int g;
     uint64_t s;
     int cell, ix, iy, ucell, mat;
@@ -730,7 +778,8 @@ typedef struct {
 } Particle;
 
 /* history fates */
-enum { FATE_ABSORBED = 0, FATE_LEAKED = 1, FATE_CUT = 2, FATE_LOST = 3, FATE_CAPPED = 4 };
+enum { FATE_ABSORBED = 0, FATE_LEAKED = 1, FATE_CUT = 2, FATE_LOST = 3, FATE_CAPPED = 4,
+       FATE_TIME = 5 };
 
 static void set_recip(Particle *p)
 {
@@ -952,7 +1001,7 @@ typedef struct {
     double ktl, kc;
     Site *bank;
     int64_t nbank, capbank;
-    int64_t coll, crossn, leak, lost, capped;
+    int64_t coll, crossn, leak, lost, capped, timecut;
 } Acc;
 
 typedef struct {            /* gradient records (one per score) */
@@ -974,7 +1023,7 @@ static void bank_push(Acc *a, const Particle *p)
         a->bank = realloc(a->bank, sizeof(Site) * (size_t)a->capbank);
     }
     Site *s = &a->bank[a->nbank++];
-    s->x = p->x; s->y = p->y; s->z = p->z;
+    s->x = p->x; s->y = p->y; s->z = p->z; s->t = p->t;
     s->cell = p->cell; s->ix = p->ix; s->iy = p->iy; s->ucell = p->ucell; s->mat = p->mat;
     s->parent = p->index; s->root = p->root; s->child = p->nfis;
 }
@@ -992,6 +1041,12 @@ static void grad_rec(Grad *gr, int param, double val, double ownb, int nfb, int6
     gr->param[gr->n] = param; gr->val[gr->n] = val; gr->ownb[gr->n] = ownb;
     gr->nfb[gr->n] = nfb; gr->pid[gr->n] = pid;
     gr->n++;
+}
+
+/* values per batch of a tally: bins x energy bins x time bins */
+static size_t tally_len(const Tally *T)
+{
+    return (size_t)T->nbins * (size_t)T->ne * (size_t)(T->ntb ? T->ntb : 1);
 }
 
 static int tally_bin(const orc_ctx *c, const Tally *t, const Particle *p, int *bin, int *e)
@@ -1042,21 +1097,45 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
         double dc = sigt > 0.0 ? -log_n(n) * mfp : INF;
         int kind, which;
         double ds = boundary(c, p, &kind, &which);
-        if (dc == INF && ds == INF) { a->lost++; p->fate = FATE_LOST; break; }
+        if (!c->time_on && dc == INF && ds == INF) { a->lost++; p->fate = FATE_LOST; break; }
         int coll = dc < ds;              /* ties: surface crossing */
         double d = coll ? dc : ds;
+        /* time dependence: the flight ends where the clock reaches t_cut, at the
+         * distance (t_cut - t) / (1/v); a tie goes to the collision or crossing */
+        int tcut = 0;
+        double ta = p->t, tb = p->t;
+        if (c->time_on) {
+            double iv = c->ce ? 1.0 / (c->kv * sqrt(p->E)) : c->invv[p->g];
+            double dt = (c->tcut - p->t) / iv;
+            if (dt < 0.0) dt = 0.0;
+            if (dt < d) { tcut = 1; d = dt; }
+            if (!tcut && d == INF) { a->lost++; p->fate = FATE_LOST; break; }
+            tb = tcut ? c->tcut : fma(d, iv, p->t);
+        }
         p->x = fma(d, p->u, p->x);
         p->y = fma(d, p->v, p->y);
         p->z = fma(d, p->w, p->z);
-        /* track-length estimators */
+        /* track-length estimators; with time bins, the time spent in each bin
+         * over the bin width (population) */
         for (int t = 0; t < c->nt; t++) {
+            const Tally *T = &c->tally[t];
             int bin, e;
-            if (tally_bin(c, &c->tally[t], p, &bin, &e)) {
-                a->acc[t][(size_t)batch * c->tally[t].nbins * c->tally[t].ne +
-                          (size_t)bin * c->tally[t].ne + e] += d;
+            if (!tally_bin(c, T, p, &bin, &e)) continue;
+            if (T->ntb == 0) {
+                a->acc[t][(size_t)batch * T->nbins * T->ne + (size_t)bin * T->ne + e] += d;
+                continue;
+            }
+            double *row = a->acc[t] + ((size_t)batch * T->nbins * T->ne + (size_t)bin * T->ne + e) *
+                                          (size_t)T->ntb;
+            for (int k = 0; k < T->ntb; k++) {
+                double lo = ta > T->tedges[k] ? ta : T->tedges[k];
+                double hi = tb < T->tedges[k + 1] ? tb : T->tedges[k + 1];
+                if (lo < hi) row[k] += (hi - lo) * T->tinvw[k];
             }
         }
+        p->t = tb;
         a->ktl += d * nusf;
+        if (tcut) { a->timecut++; p->fate = FATE_TIME; break; }
         double ownb = own;
         if (gr && (p->ucell >= 0 ? p->ucell : p->cell) == gr->det_cell)
             own = own + gr->weights[p->g] * d;
@@ -1168,6 +1247,7 @@ static int sample_source(const orc_ctx *c, Particle *p)
 {
     const Source *s = &c->src;
     p->u = p->v = p->w = 0.0;
+    p->t = c->time_on ? c->t0 : 0.0;
     if (s->kind == ORC_SRC_BOX) {
         int ok = 0;
         for (int t = 0; t < MAX_TRIES && !ok; t++) {
@@ -1196,7 +1276,7 @@ static int sample_source(const orc_ctx *c, Particle *p)
 
 static void from_site(const orc_ctx *c, Particle *p, const Site *b)
 {
-    p->x = b->x; p->y = b->y; p->z = b->z;
+    p->x = b->x; p->y = b->y; p->z = b->z; p->t = b->t;
     p->cell = b->cell; p->ix = b->ix; p->iy = b->iy; p->ucell = b->ucell; p->mat = b->mat;
     birth_energy(c, p);
     iso_dir(&p->s, &p->u, &p->v, &p->w);
@@ -1225,6 +1305,8 @@ static int prepare(orc_ctx *c)
         T->ne = c->ce ? T->nedges - 1 : c->G;
         if (c->ce && T->nedges < 2) return fail(c, ORC_EINVAL, "CE tally needs energy edges");
     }
+    if (c->time_on && !c->ce && !c->invv) return fail(c, ORC_ESTATE, "no inverse speeds");
+    c->kv = sqrt(2.0 * 1.602176634e-19 / 1.67492749804e-27) * 100.0;
     free_results(c);
     memset(c->counters, 0, sizeof c->counters);
     c->t_sum = calloc(c->nt ? c->nt : 1, sizeof(double *));
@@ -1232,7 +1314,7 @@ static int prepare(orc_ctx *c)
     c->t_mean = calloc(c->nt ? c->nt : 1, sizeof(double *));
     c->t_sd = calloc(c->nt ? c->nt : 1, sizeof(double *));
     for (int t = 0; t < c->nt; t++) {
-        size_t nb = (size_t)c->tally[t].nbins * c->tally[t].ne;
+        size_t nb = tally_len(&c->tally[t]);
         c->t_sum[t] = calloc(nb ? nb : 1, sizeof(double));
         c->t_sum2[t] = calloc(nb ? nb : 1, sizeof(double));
         c->t_mean[t] = calloc(nb ? nb : 1, sizeof(double));
@@ -1247,7 +1329,7 @@ static Acc *make_accs(const orc_ctx *c, int nthr, int nbatch)
     for (int i = 0; i < nthr; i++) {
         A[i].acc = calloc(c->nt ? c->nt : 1, sizeof(double *));
         for (int t = 0; t < c->nt; t++)
-            A[i].acc[t] = calloc((size_t)nbatch * c->tally[t].nbins * c->tally[t].ne + 1,
+            A[i].acc[t] = calloc((size_t)nbatch * tally_len(&c->tally[t]) + 1,
                                  sizeof(double));
     }
     return A;
@@ -1313,7 +1395,8 @@ static void sum_counters(orc_ctx *c, Acc *A, int nthr)
     for (int i = 0; i < nthr; i++) {
         c->counters[1] += A[i].coll; c->counters[2] += A[i].crossn; c->counters[3] += A[i].leak;
         c->counters[4] += A[i].lost; c->counters[5] += A[i].capped;
-        A[i].coll = A[i].crossn = A[i].leak = A[i].lost = A[i].capped = 0;
+        c->counters[7] += A[i].timecut;
+        A[i].coll = A[i].crossn = A[i].leak = A[i].lost = A[i].capped = A[i].timecut = 0;
     }
 }
 
@@ -1337,6 +1420,7 @@ static void mean_sd(double sum, double sum2, int n, double *mean, double *sd)
  * cycles with sd = s / sqrt(n_active).                                        */
 int orc_run_eigen(orc_ctx *c, int64_t n, int inactive, int active, uint64_t seed, int threads)
 {
+    if (c->time_on) return fail(c, ORC_EINVAL, "time dependence is for fixed-source runs");
     int r = prepare(c);
     if (r) return r;
     if (n <= 0 || active < 1 || inactive < 0) return fail(c, ORC_EINVAL, "bad run size");
@@ -1385,7 +1469,7 @@ int orc_run_eigen(orc_ctx *c, int64_t n, int inactive, int active, uint64_t seed
         double ka = (double)M / (double)n;
         c->cyc_ktl[cyc] = ktl; c->cyc_kc[cyc] = kc; c->cyc_m[cyc] = M;
         for (int t = 0; t < c->nt; t++) {
-            size_t nb = (size_t)c->tally[t].nbins * c->tally[t].ne;
+            size_t nb = tally_len(&c->tally[t]);
             for (size_t b = 0; b < nb; b++) {
                 double v = 0.0;
                 for (int i = 0; i < nthr; i++) { v += A[i].acc[t][b]; A[i].acc[t][b] = 0.0; }
@@ -1412,7 +1496,7 @@ int orc_run_eigen(orc_ctx *c, int64_t n, int inactive, int active, uint64_t seed
     if (!err) {
         for (int q = 0; q < 3; q++) mean_sd(ks[q], ks2[q], active, &c->k[2 * q], &c->k[2 * q + 1]);
         for (int t = 0; t < c->nt; t++) {
-            size_t nb = (size_t)c->tally[t].nbins * c->tally[t].ne;
+            size_t nb = tally_len(&c->tally[t]);
             for (size_t b = 0; b < nb; b++)
                 mean_sd(c->t_sum[t][b], c->t_sum2[t][b], active, &c->t_mean[t][b], &c->t_sd[t][b]);
         }
@@ -1508,7 +1592,7 @@ static int run_fixed(orc_ctx *c, int64_t n, int batches, uint64_t seed, int thre
         int64_t *nb = calloc((size_t)batches, sizeof(int64_t));
         for (int64_t j = 0; j < n; j++) nb[(j * batches) / n]++;
         for (int t = 0; t < c->nt; t++) {
-            size_t ns = (size_t)c->tally[t].nbins * c->tally[t].ne;
+            size_t ns = tally_len(&c->tally[t]);
             for (size_t b = 0; b < ns; b++) {
                 double s = 0.0, s2 = 0.0;
                 for (int q = 0; q < batches; q++) {
@@ -1594,6 +1678,7 @@ int orc_grad_fixed(orc_ctx *c, int64_t n, uint64_t seed, int cell, const double 
                    double *d_sigt, double *d_sigs, double *d_nusf, double *tally)
 {
     if (c->ce) return fail(c, ORC_EINVAL, "derivatives are multigroup only");
+    if (c->time_on) return fail(c, ORC_EINVAL, "derivatives are for time-independent runs");
     Grad gr;
     memset(&gr, 0, sizeof gr);
     gr.det_cell = cell;
@@ -1661,24 +1746,25 @@ int orc_get_cycle_k(const orc_ctx *c, int n_cycles, double *k_tl, double *k_c, i
     return 0;
 }
 
-int orc_tally_size(const orc_ctx *c, int tally, int *n_bins, int *n_ebins)
+int orc_tally_size(const orc_ctx *c, int tally, int *n_bins, int *n_ebins, int *n_tbins)
 {
     if (tally < 0 || tally >= c->nt) return ORC_EINVAL;
     *n_bins = c->tally[tally].nbins;
     *n_ebins = c->tally[tally].ne;
+    *n_tbins = c->tally[tally].ntb ? c->tally[tally].ntb : 1;
     return 0;
 }
 
 int orc_get_tally(const orc_ctx *c, int tally, double *mean, double *sd)
 {
     if (tally < 0 || tally >= c->nt || !c->t_mean) return ORC_EINVAL;
-    size_t nb = (size_t)c->tally[tally].nbins * c->tally[tally].ne;
+    size_t nb = tally_len(&c->tally[tally]);
     memcpy(mean, c->t_mean[tally], sizeof(double) * nb);
     memcpy(sd, c->t_sd[tally], sizeof(double) * nb);
     return 0;
 }
 
-int orc_get_counters(const orc_ctx *c, int64_t out[7])
+int orc_get_counters(const orc_ctx *c, int64_t out[8])
 {
     memcpy(out, c->counters, sizeof c->counters);
     return 0;

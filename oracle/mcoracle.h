@@ -62,6 +62,17 @@ int orc_set_source(orc_ctx *c, int kind, const double *params, int accept, int e
 int orc_add_tally(orc_ctx *c, int filter, int n_edges, const double *edges);
 int orc_set_max_collisions(orc_ctx *c, int max_collisions);
 
+/* Time dependence (Sec. 1 "fully dynamic simulations"; Sec. 4 runs its pin cell
+ * in time-dependent fixed-source mode).  Source particles start at t0; a flight
+ * is cut where the particle's clock reaches t_cut (fate 5).  Multigroup speeds
+ * are given as 1/v per group (s/cm); continuous energy uses v = K sqrt(E),
+ * K = sqrt(2 e / m_n) * 100 cm/s per sqrt(eV).  Fixed-source runs only. */
+int orc_set_time(orc_ctx *c, double t0, double t_cut);
+int orc_set_inverse_speeds(orc_ctx *c, int G, const double *inv_v);
+/* time bins of a tally: it then scores, per bin, the time each particle spends
+ * in the bin divided by the bin width (mean population per source particle) */
+int orc_set_tally_time_bins(orc_ctx *c, int tally, int n_edges, const double *edges);
+
 /* runs */
 int orc_run_eigen(orc_ctx *c, int64_t n, int inactive, int active, uint64_t seed, int threads);
 int orc_run_fixed(orc_ctx *c, int64_t n, int batches, uint64_t seed, int threads);
@@ -69,12 +80,14 @@ int orc_run_fixed(orc_ctx *c, int64_t n, int batches, uint64_t seed, int threads
 /* results */
 int orc_get_k(const orc_ctx *c, double out[6]); /* k_TL mean, sd, k_C mean, sd, k_analog mean, sd */
 int orc_get_cycle_k(const orc_ctx *c, int n_cycles, double *k_tl, double *k_c, int64_t *bank_size);
-int orc_tally_size(const orc_ctx *c, int tally, int *n_bins, int *n_ebins);
+int orc_tally_size(const orc_ctx *c, int tally, int *n_bins, int *n_ebins, int *n_tbins);
 int orc_get_tally(const orc_ctx *c, int tally, double *mean, double *sd);
-/* counters: histories, collisions, crossings, leaks, lost, capped, generations */
-int orc_get_counters(const orc_ctx *c, int64_t out[7]);
+/* counters: histories, collisions, crossings, leaks, lost, capped, generations,
+ * time cuts */
+int orc_get_counters(const orc_ctx *c, int64_t out[8]);
 /* per-history record of the last cycle (eigen) or generation 0 (fixed):
- * fate 0 absorbed, 1 leaked, 2 cut by max_collisions, 3 lost, 4 event cap */
+ * fate 0 absorbed, 1 leaked, 2 cut by max_collisions, 3 lost, 4 event cap,
+ * 5 reached the time cutoff */
 int64_t orc_history_count(const orc_ctx *c);
 int orc_get_histories(const orc_ctx *c, int32_t *n_coll, int32_t *n_cross, uint64_t *rng_end,
                       int32_t *n_fis, int32_t *fate, int32_t *g_end);

@@ -35,6 +35,7 @@ __all__ = [
     "mg_material", "kinf_mg", "pin_cell_mg", "c5g7_like_lattice", "ce_pin_cell",
     "batch_boxes", "diff_slab", "infinite_medium_mg", "absorbing_slab_beam",
     "one_collision_slab", "infinite_medium_fixed", "scaled", "with_run", "CONFIG_NAMES",
+    "time_pulse_mg", "time_pulse_ce", "ce_time_pin",
 ]
 
 CONFIG_NAMES = {
@@ -503,3 +504,64 @@ def infinite_medium_fixed(material, pdf, seed=9, n=20_000, half=1.0, batches=20)
         "detector_cell": 0,
         "run": _fixed_run(n, seed, batches),
     }
+
+
+# ----------------------------------------------------------------------------
+# time-dependent fixed source (Sec. 1 "fully dynamic simulations"; Sec. 4 runs
+# its continuous-energy pin cell in this mode)
+# ----------------------------------------------------------------------------
+def time_pulse_mg(material, pdf, inv_v, t_cut, t_edges, seed=11, n=20_000, batches=20,
+                  half=1.0):
+    """A pulse of `n` neutrons at t = 0 in an infinite medium (reflective cube).
+
+    One material tally with time bins: the mean neutron population per source
+    neutron in each bin, per group.  With one group the population is
+    exp(v (nuSigma_f - Sigma_a) t); with several, N(t) = expm(A t) q with
+    A = (Sigma_s^T + chi nuSigma_f^T - diag Sigma_t) V, V = diag(1 / inv_v).
+    """
+    pb = infinite_medium_fixed(material, pdf, seed=seed, n=n, half=half, batches=batches)
+    pb["name"] = "mg-infinite-medium-time-pulse"
+    pb["time"] = {"t0": 0.0, "t_cut": float(t_cut), "inv_v": np.asarray(inv_v, float)}
+    pb["tallies"] = [{"filter": "material", "time_edges": np.asarray(t_edges, float)}]
+    return pb
+
+
+def time_pulse_ce(sig_c, E0, t_cut, t_edges, A=1.0, sig_s=0.0, density=0.05, seed=12,
+                  n=20_000, batches=20, half=1.0):
+    """A pulse of `n` neutrons of energy E0 (eV) in an infinite medium of one
+    nuclide with constant cross sections (barns); energy-integrated population
+    tally with time bins.  Without scattering the population is
+    exp(-N sigma_c v(E0) t), v(E) = 2.2e5 cm/s sqrt(E / 0.0253 eV)."""
+    nuc = {"A": float(A), "E": np.array([E_MIN, E_MAX]), "sig_s": np.array([sig_s, sig_s]),
+           "sig_c": np.array([sig_c, sig_c]), "sig_f": np.zeros(2), "nu": 0.0}
+    surfaces = [_surf("px", [-half], "reflect"), _surf("px", [half], "reflect"),
+                _surf("py", [-half], "reflect"), _surf("py", [half], "reflect"),
+                _surf("pz", [-half], "reflect"), _surf("pz", [half], "reflect")]
+    cells = [_cell(0, [(0, +1), (1, -1), (2, +1), (3, -1), (4, +1), (5, -1)], "material", 0)]
+    return {
+        "name": "ce-infinite-medium-time-pulse", "G": 0, "surfaces": surfaces, "cells": cells,
+        "lattices": [], "nuclides": [nuc], "materials": [{"nuclides": [0], "density": [density]}],
+        "source": {"kind": "box", "box": [-half, half, -half, half, -half, half], "accept": "any",
+                   "energy": "fixed", "E": float(E0), "direction": "iso"},
+        "tallies": [{"filter": "material", "edges": np.array([E_MIN, E_MAX]),
+                     "time_edges": np.asarray(t_edges, float)}],
+        "time": {"t0": 0.0, "t_cut": float(t_cut)},
+        "run": _fixed_run(n, seed, batches),
+    }
+
+
+def ce_time_pin(seed=1, n=10_000_000, t_cut=1.0e-5, ntbins=40, npts=50_000, nres=200,
+                batches=20):
+    """Stand-in for the paper's continuous-energy benchmark (Sec. 4): the infinite
+    pin cell of ce_pin_cell driven by a uniform 14 MeV source, time-dependent
+    fixed source; tally: neutron population per cell in `ntbins` log-spaced time
+    bins on [1e-9 s, t_cut] (energy-integrated)."""
+    pb = ce_pin_cell(seed=seed, n=n, npts=npts, nres=nres, nbins=1)
+    pb["name"] = "ce-pin-cell-4nuclides-time-14mev"
+    pb["source"] = {"kind": "box", "box": [-0.63, 0.63, -0.63, 0.63, 0.0, 0.0], "accept": "any",
+                    "energy": "fixed", "E": 14.0e6, "direction": "iso"}
+    t_edges = np.concatenate([[0.0], np.geomspace(1.0e-9, t_cut, ntbins)])
+    pb["tallies"] = [{"filter": "cell", "edges": np.array([E_MIN, E_MAX]), "time_edges": t_edges}]
+    pb["time"] = {"t0": 0.0, "t_cut": float(t_cut)}
+    pb["run"] = _fixed_run(n, seed, batches)
+    return pb
