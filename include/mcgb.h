@@ -99,6 +99,7 @@ typedef struct {
     int64_t kernel_launches;   /* kernels this library launched during the run */
     int64_t event_iterations;  /* event / segment mode: host loop iterations */
     int64_t world_bytes;       /* bytes of problem tables uploaded to the device */
+    int64_t time_cut;          /* histories that reached the time cutoff */
 } mcgb_counters;
 
 /* Launch shape chosen by the autotuner for a batch. */
@@ -173,6 +174,24 @@ int mcgb_set_source(mcgb_ctx *ctx, int kind, const double *params, int accept, i
 int mcgb_add_tally(mcgb_ctx *ctx, int filter, int n_edges, const double *edges, int *id);
 /* End each history at its max_collisions-th collision (0 = no limit). */
 int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions);
+/* Time dependence (Sec. 1 "fully dynamic simulations"; Sec. 4 runs its
+ * continuous-energy pin cell as a time-dependent fixed-source problem).  Source
+ * particles start at time t0 (s); a flight ends where the particle's clock
+ * reaches t_cut, at the distance (t_cut - t) / (1/v) when that is shorter than
+ * the distances to collision and to the nearest surface (a tie goes to the
+ * collision or crossing), and the history ends with fate 5.  Fission sites keep
+ * the time of their collision.  Speeds: 1/v per group (s/cm, multigroup, set
+ * with mcgb_set_inverse_speeds) or v = K sqrt(E / 1 eV), K = sqrt(2 e / m_n) *
+ * 100 cm/s (continuous energy).  Fixed-source runs only (an eigenvalue run or
+ * a derivative run fails); requires 0 <= t0 < t_cut < inf. */
+int mcgb_set_time(mcgb_ctx *ctx, double t0, double t_cut);
+/* inv_v[G]: 1/v of each group in s/cm, positive and finite. */
+int mcgb_set_inverse_speeds(mcgb_ctx *ctx, int G, const double *inv_v);
+/* Time bins of a tally: n_edges increasing edges (s, first >= 0).  The tally
+ * then scores, for every flight and bin, the time the flight spends in the bin
+ * times 1 / (bin width): the mean neutron population per source particle in
+ * the bin, per spatial bin and group or energy bin. */
+int mcgb_set_tally_time_bins(mcgb_ctx *ctx, int tally, int n_edges, const double *edges);
 
 /* --------------------------------------------------------------------------- */
 /* runs                                                                         */
@@ -198,14 +217,16 @@ int mcgb_run_fixed_source(mcgb_ctx *ctx, int64_t n, int batches, uint64_t seed);
 int mcgb_get_k(mcgb_ctx *ctx, double out[6]);
 /* Per-cycle k (track length), k (collision) and bank size, n_cycles entries. */
 int mcgb_get_cycle_k(mcgb_ctx *ctx, int n_cycles, double *k_tl, double *k_col, int64_t *bank);
-int mcgb_tally_size(mcgb_ctx *ctx, int tally, int *n_bins, int *n_ebins);
-/* mean and sd per source particle, [bin][ebin], cap elements each. */
+/* bins, energy bins (groups) and time bins (1 without time bins) of a tally */
+int mcgb_tally_size(mcgb_ctx *ctx, int tally, int *n_bins, int *n_ebins, int *n_tbins);
+/* mean and sd per source particle, [bin][ebin][tbin], cap elements each. */
 int mcgb_get_tally(mcgb_ctx *ctx, int tally, double *mean, double *sd, size_t cap,
                    size_t *needed);
 int mcgb_get_counters(mcgb_ctx *ctx, mcgb_counters *out);
 /* Per-history records (opts.record_histories): last cycle (eigenvalue) or
  * generation 0 (fixed source).  fate: 0 absorbed, 1 leaked, 2 cut by
- * max_collisions, 3 lost, 4 event cap.  Arrays of cap elements. */
+ * max_collisions, 3 lost, 4 event cap, 5 reached the time cutoff.  Arrays of
+ * cap elements. */
 int mcgb_get_histories(mcgb_ctx *ctx, size_t cap, int32_t *n_coll, int32_t *n_cross,
                        uint64_t *rng_end, int32_t *n_fis, int32_t *fate, int32_t *g_end,
                        size_t *needed);

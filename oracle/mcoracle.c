@@ -609,7 +609,8 @@ int orc_set_inverse_speeds(orc_ctx *c, int G, const double *inv_v)
 
 int orc_set_tally_time_bins(orc_ctx *c, int tally, int n_edges, const double *edges)
 {
-    if (tally < 0 || tally >= c->nt || n_edges < 2) return fail(c, ORC_EINVAL, "bad time bins");
+    if (tally < 0 || tally >= c->nt || n_edges < 2 || !(edges[0] >= 0.0))
+        return fail(c, ORC_EINVAL, "bad time bins");
     for (int k = 0; k + 1 < n_edges; k++)
         if (!(edges[k + 1] > edges[k])) return fail(c, ORC_EINVAL, "time edges must increase");
     Tally *t = &c->tally[tally];

@@ -46,7 +46,7 @@ class Opts(C.Structure):
 class Counters(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("histories", "collisions", "crossings", "leaks", "lost",
                                          "capped", "generations", "kernel_launches",
-                                         "event_iterations", "world_bytes")]
+                                         "event_iterations", "world_bytes", "time_cut")]
 
 
 class Tune(C.Structure):
@@ -91,12 +91,14 @@ def lib():
                 "mcgb_set_source": [P, i32, P, i32, i32, P, i32, i32, P],
                 "mcgb_add_tally": [P, i32, i32, P, P],
                 "mcgb_set_max_collisions": [P, i32],
+                "mcgb_set_time": [P, d, d], "mcgb_set_inverse_speeds": [P, i32, P],
+                "mcgb_set_tally_time_bins": [P, i32, i32, P],
                 "mcgb_run_eigenvalue": [P, i64, i32, i32, u64],
                 "mcgb_run_fixed_source": [P, i64, i32, u64],
                 "mcgb_eigen_begin": [P, i64, i32, i32, u64], "mcgb_eigen_cycles": [P, i32],
                 "mcgb_eigen_finish": [P], "mcgb_get_cycle_times": [P, i32, P, P],
                 "mcgb_get_k": [P, P], "mcgb_get_cycle_k": [P, i32, P, P, P],
-                "mcgb_tally_size": [P, i32, P, P], "mcgb_get_tally": [P, i32, P, P, sz, P],
+                "mcgb_tally_size": [P, i32, P, P, P], "mcgb_get_tally": [P, i32, P, P, sz, P],
                 "mcgb_get_counters": [P, P],
                 "mcgb_get_histories": [P, sz, P, P, P, P, P, P, P],
                 "mcgb_get_bank": [P, sz, P, P, P, P, P],
@@ -236,6 +238,17 @@ class Context:
     def set_max_collisions(self, m):
         _chk(self.L.mcgb_set_max_collisions(self.h, m))
 
+    def set_time(self, t0, t_cut):
+        _chk(self.L.mcgb_set_time(self.h, float(t0), float(t_cut)))
+
+    def set_inverse_speeds(self, inv_v):
+        a = _f64(inv_v)
+        _chk(self.L.mcgb_set_inverse_speeds(self.h, len(a), _p(a)))
+
+    def set_tally_time_bins(self, t, edges):
+        a = _f64(edges)
+        _chk(self.L.mcgb_set_tally_time_bins(self.h, t, len(a), _p(a)))
+
     def run_eigenvalue(self, n, inactive, active, seed):
         _chk(self.L.mcgb_run_eigenvalue(self.h, n, inactive, active, seed))
 
@@ -268,16 +281,20 @@ class Context:
         return a, b, m
 
     def tally_size(self, t=0):
-        nb, ne = C.c_int(), C.c_int()
-        _chk(self.L.mcgb_tally_size(self.h, t, C.byref(nb), C.byref(ne)))
-        return nb.value, ne.value
+        """(bins, energy bins or groups, time bins); 1 time bin without time bins."""
+        nb, ne, nt = C.c_int(), C.c_int(), C.c_int()
+        _chk(self.L.mcgb_tally_size(self.h, t, C.byref(nb), C.byref(ne), C.byref(nt)))
+        return nb.value, ne.value, nt.value
 
     def get_tally(self, t=0):
-        nb, ne = self.tally_size(t)
-        mean, sd = np.zeros(nb * ne), np.zeros(nb * ne)
+        """Means and sds [bin, group or energy bin] (+ a time-bin axis when the
+        tally has time bins)."""
+        nb, ne, nt = self.tally_size(t)
+        mean, sd = np.zeros(nb * ne * nt), np.zeros(nb * ne * nt)
         need = C.c_size_t()
-        _chk(self.L.mcgb_get_tally(self.h, t, _p(mean), _p(sd), nb * ne, C.byref(need)))
-        return mean.reshape(nb, ne), sd.reshape(nb, ne)
+        _chk(self.L.mcgb_get_tally(self.h, t, _p(mean), _p(sd), nb * ne * nt, C.byref(need)))
+        shape = (nb, ne, nt) if t in getattr(self, "_timed_tallies", ()) else (nb, ne)
+        return mean.reshape(shape), sd.reshape(shape)
 
     def get_counters(self):
         c = Counters()
@@ -380,8 +397,16 @@ def load_problem(ctx: Context, pb: dict) -> Context:
     energy = src["pdf"] if ek == 1 else ([src.get("E", 0.0)] if ek == 2 else [0.0])
     dk = 1 if src["direction"] == "beam" else 0
     ctx.set_source(kind, params, accept, ek, energy, dk, src.get("beam"))
-    for t in pb["tallies"]:
+    ctx._timed_tallies = set()
+    for i, t in enumerate(pb["tallies"]):
         ctx.add_tally(FILTER[t["filter"]], t.get("edges"))
+        if "time_edges" in t:
+            ctx.set_tally_time_bins(i, t["time_edges"])
+            ctx._timed_tallies.add(i)
+    if "time" in pb:
+        ctx.set_time(pb["time"].get("t0", 0.0), pb["time"]["t_cut"])
+        if pb["G"] > 0:
+            ctx.set_inverse_speeds(pb["time"]["inv_v"])
     ctx.set_max_collisions(int(pb["run"].get("max_collisions", 0)))
     ctx.problem = pb
     return ctx
@@ -425,12 +450,13 @@ class Batch:
 
     def tally(self, problem, t=0):
         ctx = self.ntallies[problem]
-        nb, ne = ctx.tally_size(t)
-        mean, sd = np.zeros(nb * ne), np.zeros(nb * ne)
+        nb, ne, nt = ctx.tally_size(t)
+        mean, sd = np.zeros(nb * ne * nt), np.zeros(nb * ne * nt)
         need = C.c_size_t()
-        _chk(self.L.mcgb_batch_tally(self.h, problem, t, _p(mean), _p(sd), nb * ne,
+        _chk(self.L.mcgb_batch_tally(self.h, problem, t, _p(mean), _p(sd), nb * ne * nt,
                                      C.byref(need)))
-        return mean.reshape(nb, ne), sd.reshape(nb, ne)
+        shape = (nb, ne, nt) if t in getattr(ctx, "_timed_tallies", ()) else (nb, ne)
+        return mean.reshape(shape), sd.reshape(shape)
 
     def counters(self):
         c = Counters()

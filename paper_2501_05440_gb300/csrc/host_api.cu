@@ -169,7 +169,7 @@ static int prepare_buffers(mcgb_ctx *c, int64_t cap_p, int64_t cap_b)
     DevAlloc &m = r.mem;
     CKR(m.get(P.x, cap_p)); CKR(m.get(P.y, cap_p)); CKR(m.get(P.z, cap_p));
     CKR(m.get(P.u, cap_p)); CKR(m.get(P.v, cap_p)); CKR(m.get(P.w, cap_p));
-    CKR(m.get(P.E, cap_p)); CKR(m.get(P.kt, cap_p)); CKR(m.get(P.kc, cap_p));
+    CKR(m.get(P.E, cap_p)); CKR(m.get(P.kt, cap_p)); CKR(m.get(P.kc, cap_p)); CKR(m.get(P.t, cap_p));
     CKR(m.get(P.iu, cap_p)); CKR(m.get(P.iv, cap_p)); CKR(m.get(P.iw, cap_p));
     CKR(m.get(P.s, cap_p));
     CKR(m.get(P.g, cap_p)); CKR(m.get(P.cell, cap_p)); CKR(m.get(P.ix, cap_p));
@@ -180,7 +180,7 @@ static int prepare_buffers(mcgb_ctx *c, int64_t cap_p, int64_t cap_b)
     P.cap = cap_p;
     for (int b = 0; b < 2; b++) {
         Bank &B = r.bank[b];
-        CKR(m.get(B.x, cap_b)); CKR(m.get(B.y, cap_b)); CKR(m.get(B.z, cap_b));
+        CKR(m.get(B.x, cap_b)); CKR(m.get(B.y, cap_b)); CKR(m.get(B.z, cap_b)); CKR(m.get(B.t, cap_b));
         CKR(m.get(B.cell, cap_b)); CKR(m.get(B.ix, cap_b)); CKR(m.get(B.iy, cap_b));
         CKR(m.get(B.ucell, cap_b)); CKR(m.get(B.mat, cap_b)); CKR(m.get(B.parent, cap_b));
         CKR(m.get(B.child, cap_b)); CKR(m.get(B.root, cap_b)); CKR(m.get(B.prob, cap_b));
@@ -312,7 +312,7 @@ static double draw_host(uint64_t &s)
 static int fetch_counters(mcgb_ctx *c)
 {
     unsigned long long h[8];
-    CK(cudaMemcpyAsync(h, c->rs.cnt, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(h, c->rs.cnt, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->counters.collisions = (int64_t)h[0];
@@ -320,6 +320,7 @@ static int fetch_counters(mcgb_ctx *c)
     c->counters.leaks = (int64_t)h[2];
     c->counters.lost = (int64_t)h[3];
     c->counters.capped = (int64_t)h[4];
+    c->counters.time_cut = (int64_t)h[5];
     c->counters.kernel_launches = c->launches;
     c->counters.world_bytes = c->world ? (int64_t)c->world->bytes : 0;
     return MCGB_OK;
@@ -403,6 +404,7 @@ static int eigen_begin(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_
 {
     if (N <= 0 || N > (int64_t)1 << 30 || active < 1 || inactive < 0 || inactive + active > 4096)
         return fail(MCGB_E_INVALID_ARG, "bad run size");
+    if (c->def.time_on) return fail(MCGB_E_INVALID_ARG, "time dependence is for fixed-source runs");
     c->eig.on = false;
     CKR(build_single(c, N, 1, seed));
     double bf = c->opts.bank_factor > 0 ? c->opts.bank_factor : 3.0;
@@ -676,7 +678,7 @@ static int eigen_finish(mcgb_ctx *c)
     c->t_sd.assign(c->def.tallies.size(), {});
     for (size_t t = 0; t < c->def.tallies.size(); t++) {
         int gt = dw.tally_first[0] + (int)t;
-        int nb = dw.t_nbins[gt] * dw.t_ne[gt];
+        int nb = dw.t_nbins[gt] * dw.t_ne[gt] * std::max(1, dw.t_ntb[gt]);
         c->t_mean[t].resize(nb);
         c->t_sd[t].resize(nb);
         for (int b = 0; b < nb; b++)
@@ -775,6 +777,7 @@ static int run_fixed_world(mcgb_ctx *c, bool grad, int det_cell)
             Bank &B = g.bank;
             const Bank &S = r.bank[nxt];
             CKR(c->grad_mem.get(B.x, M)); CKR(c->grad_mem.get(B.y, M)); CKR(c->grad_mem.get(B.z, M));
+            CKR(c->grad_mem.get(B.t, M));
             CKR(c->grad_mem.get(B.cell, M)); CKR(c->grad_mem.get(B.ix, M));
             CKR(c->grad_mem.get(B.iy, M)); CKR(c->grad_mem.get(B.ucell, M));
             CKR(c->grad_mem.get(B.mat, M)); CKR(c->grad_mem.get(B.root, M));
@@ -782,6 +785,7 @@ static int run_fixed_world(mcgb_ctx *c, bool grad, int det_cell)
                 CK(cudaMemcpyAsync(B.x, S.x, 8 * M, cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(B.y, S.y, 8 * M, cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(B.z, S.z, 8 * M, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(B.t, S.t, 8 * M, cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(B.cell, S.cell, 4 * M, cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(B.ix, S.ix, 4 * M, cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(B.iy, S.iy, 4 * M, cudaMemcpyDeviceToDevice, st));
@@ -820,7 +824,7 @@ static int run_fixed_world(mcgb_ctx *c, bool grad, int det_cell)
         for (int64_t j = 0; j < P.n; j++) nb[(j * B) / P.n]++;
         for (int t = 0; t < P.tally_count; t++) {
             int gt = P.tally_first + t;
-            int ns = dw.t_nbins[gt] * dw.t_ne[gt];
+            int ns = dw.t_nbins[gt] * dw.t_ne[gt] * std::max(1, dw.t_ntb[gt]);
             std::vector<double> mean(ns), sd(ns);
             for (int b = 0; b < ns; b++) {
                 double s = 0.0, s2 = 0.0;
@@ -1091,6 +1095,39 @@ int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions)
     return MCGB_OK;
 }
 
+int mcgb_set_time(mcgb_ctx *ctx, double t0, double t_cut)
+{
+    if (!ctx || !(t0 >= 0.0) || !(t_cut > t0) || !std::isfinite(t_cut))
+        return fail(MCGB_E_INVALID_ARG, "need 0 <= t0 < t_cut < inf");
+    ctx->def.time_on = true;
+    ctx->def.t0 = t0;
+    ctx->def.tcut = t_cut;
+    return MCGB_OK;
+}
+
+int mcgb_set_inverse_speeds(mcgb_ctx *ctx, int G, const double *inv_v)
+{
+    if (!ctx || G <= 0 || G != ctx->def.G || !inv_v)
+        return fail(MCGB_E_INVALID_ARG, "one inverse speed per group");
+    for (int g = 0; g < G; g++)
+        if (!(inv_v[g] > 0.0) || !std::isfinite(inv_v[g]))
+            return fail(MCGB_E_INVALID_ARG, "inverse speeds must be positive and finite");
+    ctx->def.invv.assign(inv_v, inv_v + G);
+    return MCGB_OK;
+}
+
+int mcgb_set_tally_time_bins(mcgb_ctx *ctx, int tally, int n_edges, const double *edges)
+{
+    if (!ctx || tally < 0 || tally >= (int)ctx->def.tallies.size() || n_edges < 2 || !edges)
+        return fail(MCGB_E_INVALID_ARG, "bad time bins");
+    if (!(edges[0] >= 0.0)) return fail(MCGB_E_INVALID_ARG, "time edges must be >= 0");
+    for (int k = 1; k < n_edges; k++)
+        if (!(edges[k] > edges[k - 1]) || !std::isfinite(edges[k]))
+            return fail(MCGB_E_INVALID_ARG, "time edges must increase");
+    ctx->def.tallies[tally].tedges.assign(edges, edges + n_edges);
+    return MCGB_OK;
+}
+
 int mcgb_run_eigenvalue(mcgb_ctx *ctx, int64_t n, int inactive, int active, uint64_t seed)
 {
     if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
@@ -1156,7 +1193,7 @@ int mcgb_get_cycle_k(mcgb_ctx *ctx, int n_cycles, double *k_tl, double *k_col, i
     return MCGB_OK;
 }
 
-int mcgb_tally_size(mcgb_ctx *ctx, int tally, int *n_bins, int *n_ebins)
+int mcgb_tally_size(mcgb_ctx *ctx, int tally, int *n_bins, int *n_ebins, int *n_tbins)
 {
     if (!ctx || tally < 0 || tally >= (int)ctx->def.tallies.size()) return fail(MCGB_E_NOT_FOUND, "no such tally");
     const ProblemDef &d = ctx->def;
@@ -1166,6 +1203,7 @@ int mcgb_tally_size(mcgb_ctx *ctx, int tally, int *n_bins, int *n_ebins)
            : t.filter == MCGB_FILTER_LATTICE ? (d.lats.empty() ? 0 : d.lats[0].nx * d.lats[0].ny) : nmat;
     if (n_bins) *n_bins = nb;
     if (n_ebins) *n_ebins = d.ce == 1 ? (int)t.edges.size() - 1 : d.G;
+    if (n_tbins) *n_tbins = t.tedges.empty() ? 1 : (int)t.tedges.size() - 1;
     return MCGB_OK;
 }
 
@@ -1223,6 +1261,7 @@ int mcgb_forward_fixed(mcgb_ctx *ctx, int64_t n, uint64_t seed, int det_cell, do
 {
     if (!ctx || n <= 0) return fail(MCGB_E_INVALID_ARG, "bad argument");
     if (ctx->def.ce != 0) return fail(MCGB_E_STATE, "derivatives are multigroup only");
+    if (ctx->def.time_on) return fail(MCGB_E_STATE, "derivatives are for time-independent runs");
     if (det_cell < 0 || det_cell >= (int)ctx->def.cells.size()) return fail(MCGB_E_INVALID_ARG, "bad detector cell");
     CK(cudaSetDevice(ctx->device));
     CKR(build_single(ctx, n, 1, seed));

@@ -75,6 +75,19 @@ std::string ProblemDef::check() const
     for (auto &t : tallies) {
         if (t.filter == FILTER_LATTICE && lats.empty()) return "lattice tally without a lattice";
         if (ce && t.edges.size() < 2) return "continuous-energy tally needs energy edges";
+        if (!t.tedges.empty()) {
+            if (t.tedges.size() < 2) return "time bins need at least two edges";
+            for (size_t k = 0; k + 1 < t.tedges.size(); k++)
+                if (!(t.tedges[k + 1] > t.tedges[k])) return "time edges must increase";
+        }
+    }
+    if (time_on) {
+        if (!(t0 >= 0.0) || !(tcut > t0) || !std::isfinite(tcut)) return "need 0 <= t0 < t_cut < inf";
+        if (!ce) {
+            if ((int)invv.size() != G) return "one inverse speed per group needed";
+            for (double x : invv)
+                if (!(x > 0.0) || !std::isfinite(x)) return "inverse speeds must be positive";
+        }
     }
     if (!ce && src.ekind == E_PDF && (int)src.pdf.size() != G) return "source group pdf size != G";
     if (ce) {
@@ -119,8 +132,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     std::vector<double> n_A, n_nu;
     std::vector<int> mc_off, mc_n, mc_nuc, mc_fissile;
     std::vector<double> mc_dens, src_cdf;
-    std::vector<int> t_filter, t_nbins, t_ne, t_off, t_eoff, t_nedges, t_batches;
-    std::vector<double> t_edges;
+    std::vector<int> t_filter, t_nbins, t_ne, t_off, t_eoff, t_nedges, t_batches, t_ntb, t_toff;
+    std::vector<double> t_edges, t_tedges, t_tinvw, g_invv;
     std::vector<ProblemDev> probs;
     int nuniv = 0;
     int64_t acc_size = 0;
@@ -268,13 +281,26 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
             t_ne.push_back(ne);
             t_batches.push_back(r.batches);
             t_off.push_back((int)acc_size);
-            acc_size += (int64_t)r.batches * nb * ne;
+            int ntb = t.tedges.empty() ? 0 : (int)t.tedges.size() - 1;
+            acc_size += (int64_t)r.batches * nb * ne * std::max(ntb, 1);
             t_eoff.push_back((int)t_edges.size());
             t_nedges.push_back((int)t.edges.size());
             t_edges.insert(t_edges.end(), t.edges.begin(), t.edges.end());
+            // time edges and 1 / width (1 / (e[k+1] - e[k]), the last entry unused)
+            t_ntb.push_back(ntb);
+            t_toff.push_back((int)t_tedges.size());
+            for (size_t k = 0; k < t.tedges.size(); k++) {
+                t_tedges.push_back(t.tedges[k]);
+                t_tinvw.push_back(k + 1 < t.tedges.size() ? 1.0 / (t.tedges[k + 1] - t.tedges[k]) : 0.0);
+            }
         }
         if (acc_size > (int64_t)1 << 30) return "tally accumulators too large";
         P.max_coll = pd.max_coll;
+        P.time_on = pd.time_on ? 1 : 0;
+        P.t0 = pd.t0;
+        P.tcut = pd.tcut;
+        P.invv_off = (int)g_invv.size();
+        if (pd.time_on && !pd.ce) g_invv.insert(g_invv.end(), pd.invv.begin(), pd.invv.end());
         P.batches = r.batches;
         P.seed = r.seed & 0x7FFFFFFFFFFFFFFFULL;
         P.n = r.n;
@@ -371,7 +397,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
            o_etab = S.put(etab);
     size_t o_tf = S.put(t_filter), o_tnb = S.put(t_nbins), o_tne = S.put(t_ne), o_toff = S.put(t_off),
            o_teoff = S.put(t_eoff), o_tned = S.put(t_nedges), o_tbat = S.put(t_batches),
-           o_tedges = S.put(t_edges);
+           o_tedges = S.put(t_edges), o_tntb = S.put(t_ntb), o_ttoff = S.put(t_toff),
+           o_ttedges = S.put(t_tedges), o_ttinvw = S.put(t_tinvw), o_ginvv = S.put(g_invv);
 
     if (dw.arena) {
         cudaFree(dw.arena);
@@ -410,7 +437,16 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(t_filter, int, o_tf); P_(t_nbins, int, o_tnb); P_(t_ne, int, o_tne); P_(t_off, int, o_toff);
     P_(t_eoff, int, o_teoff); P_(t_nedges, int, o_tned); P_(t_batches, int, o_tbat);
     P_(t_edges, double, o_tedges);
+    P_(t_ntb, int, o_tntb); P_(t_toff, int, o_ttoff); P_(t_tedges, double, o_ttedges);
+    P_(t_tinvw, double, o_ttinvw); P_(g_invv, double, o_ginvv);
 #undef P_
+    // CE speed: v = kv sqrt(E / 1 eV) cm/s, kv = sqrt(2 e / m_n) * 100
+    W.kv = std::sqrt(2.0 * 1.602176634e-19 / 1.67492749804e-27) * 100.0;
+    W.time_any = 0;
+    for (const ProblemDev &P : probs)
+        if (P.time_on) W.time_any = 1;
+    for (int n : t_ntb)
+        if (n > 0) W.time_any = 1;
     W.need_iw = 0;
     for (int t : s_type)
         if (t == SURF_PZ) W.need_iw = 1;
@@ -424,6 +460,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     dw.t_nbins = t_nbins;
     dw.t_ne = t_ne;
     dw.t_batches = t_batches;
+    dw.t_ntb = t_ntb;
     dw.acc_size = (int)acc_size;
     dw.nrep = nrep;
     return "";

@@ -41,6 +41,7 @@ struct SrcDef {
 struct TallyDef {
     int filter;
     std::vector<double> edges;
+    std::vector<double> tedges;   // time bin edges (empty: no time bins)
 };
 
 // Everything a user defines for one problem through the C ABI.
@@ -57,6 +58,9 @@ struct ProblemDef {
     SrcDef src;
     std::vector<TallyDef> tallies;
     int max_coll = 0;
+    bool time_on = false;
+    double t0 = 0.0, tcut = 0.0;
+    std::vector<double> invv;    // inverse group speeds (multigroup)
     std::string check() const;   // empty when runnable
 };
 
@@ -75,7 +79,7 @@ struct DeviceWorld {
     size_t bytes = 0;
     std::vector<ProblemDev> probs;      // host copy
     std::vector<int> tally_first;       // global tally id of each problem's first tally
-    std::vector<int> t_off, t_nbins, t_ne, t_batches;  // host copies per global tally
+    std::vector<int> t_off, t_nbins, t_ne, t_batches, t_ntb;  // host copies per global tally
     int acc_size = 0, nrep = 1;
     ~DeviceWorld();
 };

@@ -157,7 +157,7 @@ __global__ void k_reduce_gen(Particles P, int64_t total, const int *total_dev, d
     int64_t n = total_dev ? (int64_t)*total_dev : total;
     if (cyc_dev) kout += 2 * *cyc_dev;
     double kt = 0.0, kc = 0.0;
-    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         kt += P.kt[i];
@@ -168,19 +168,20 @@ __global__ void k_reduce_gen(Particles P, int64_t total, const int *total_dev, d
         c[2] += f == FATE_LEAKED;
         c[3] += f == FATE_LOST;
         c[4] += f == FATE_CAPPED;
+        c[5] += f == FATE_TIME;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         kt += __shfl_down_sync(0xffffffffu, kt, o);
         kc += __shfl_down_sync(0xffffffffu, kc, o);
 #pragma unroll
-        for (int q = 0; q < 5; q++) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
+        for (int q = 0; q < 6; q++) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(kout, kt);
         atomicAdd(kout + 1, kc);
 #pragma unroll
-        for (int q = 0; q < 5; q++)
+        for (int q = 0; q < 6; q++)
             if (c[q]) atomicAdd(cnt + q, c[q]);
     }
 }

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_replay(World W, ReplayArgs a, Bank Bsrc
             double d = 0.0;
             int g0 = p.g, m0 = p.mat;
             bool in_det = (p.ucell >= 0 ? p.ucell : p.cell) == a.det_cell;
-            int ev = step_advance<true>(W, Pd, p, (int)j, R, 0, kind, which, uk, kt, &d);
+            int ev = step_advance<true, false>(W, Pd, p, (int)j, R, 0, kind, which, uk, kt, &d);
             if (ev == EV_DEAD) break;
             double ownb = own_before;
             if (in_det) own_before = own_before + a.w[g0] * d;

@@ -21,14 +21,14 @@ constexpr int NBUCKET = 33;          // list buckets: 0 = crossings, 1..32 = mat
 constexpr int SLOT_EMPTY = -2;
 
 struct Pool {
-    double *x, *y, *z, *u, *v, *w, *E, *kt, *kc, *iu, *iv, *iw;
+    double *x, *y, *z, *u, *v, *w, *E, *kt, *kc, *iu, *iv, *iw, *t;
     unsigned long long *s;
     int *g, *cell, *ix, *iy, *ucell, *mat, *prob, *root, *nfis, *ncoll, *ncross, *gslot, *bwhich,
         *uk, *fate, *ev;
     int *list;
 };
 
-__host__ __device__ constexpr size_t pool_bytes(int P) { return (size_t)P * (13 * 8 + 17 * 4); }
+__host__ __device__ constexpr size_t pool_bytes(int P) { return (size_t)P * (14 * 8 + 17 * 4); }
 
 __device__ __forceinline__ Pool carve(unsigned char *base, int P)
 {
@@ -38,7 +38,8 @@ __device__ __forceinline__ Pool carve(unsigned char *base, int P)
     q.E = d + 6 * P; q.kt = d + 7 * P; q.kc = d + 8 * P;
     q.iu = d + 9 * P; q.iv = d + 10 * P; q.iw = d + 11 * P;
     q.s = reinterpret_cast<unsigned long long *>(d + 12 * P);
-    int *i = reinterpret_cast<int *>(d + 13 * P);
+    q.t = d + 13 * P;
+    int *i = reinterpret_cast<int *>(d + 14 * P);
     q.g = i; q.cell = i + P; q.ix = i + 2 * P; q.iy = i + 3 * P; q.ucell = i + 4 * P;
     q.mat = i + 5 * P; q.prob = i + 6 * P; q.root = i + 7 * P; q.nfis = i + 8 * P;
     q.ncoll = i + 9 * P; q.ncross = i + 10 * P; q.gslot = i + 11 * P; q.bwhich = i + 12 * P;
@@ -46,21 +47,25 @@ __device__ __forceinline__ Pool carve(unsigned char *base, int P)
     return q;
 }
 
+// TIME = false: the particle clock is neither loaded nor kept
+template <bool TIME>
 __device__ __forceinline__ void pool_load(const Pool &q, int i, PS &p)
 {
     p.x = q.x[i]; p.y = q.y[i]; p.z = q.z[i]; p.u = q.u[i]; p.v = q.v[i]; p.w = q.w[i];
     p.iu = q.iu[i]; p.iv = q.iv[i]; p.iw = q.iw[i];
-    p.E = q.E[i]; p.s = q.s[i];
+    p.E = q.E[i]; p.s = q.s[i]; p.t = TIME ? q.t[i] : 0.0;
     p.g = q.g[i]; p.cell = q.cell[i]; p.ix = q.ix[i]; p.iy = q.iy[i]; p.ucell = q.ucell[i];
     p.mat = q.mat[i]; p.prob = q.prob[i]; p.root = q.root[i]; p.nfis = q.nfis[i];
     p.ncoll = q.ncoll[i]; p.ncross = q.ncross[i]; p.fate = q.fate[i];
 }
 
+template <bool TIME>
 __device__ __forceinline__ void pool_store(const Pool &q, int i, const PS &p)
 {
     q.x[i] = p.x; q.y[i] = p.y; q.z[i] = p.z; q.u[i] = p.u; q.v[i] = p.v; q.w[i] = p.w;
     q.iu[i] = p.iu; q.iv[i] = p.iv; q.iw[i] = p.iw;
     q.E[i] = p.E; q.s[i] = p.s;
+    if (TIME) q.t[i] = p.t;
     q.g[i] = p.g; q.cell[i] = p.cell; q.ix[i] = p.ix; q.iy[i] = p.iy; q.ucell[i] = p.ucell;
     q.mat[i] = p.mat; q.prob[i] = p.prob; q.root[i] = p.root; q.nfis[i] = p.nfis;
     q.ncoll[i] = p.ncoll; q.ncross[i] = p.ncross; q.fate[i] = p.fate;
@@ -130,7 +135,7 @@ __host__ __device__ constexpr int pool_min_blocks(int P, int T)
     return (P <= T && T == 256) ? 3 : 65536 / (T * 128);
 }
 
-template <int P, int T>
+template <int P, int T, bool TIME>
 __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Particles G, Bank Bsrc,
                                                                Bank Bdst, RunBufs R,
                                                                PersistentArgs a)
@@ -185,10 +190,10 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
                     p.fate = FATE_LOST;
                     p.cell = 0;
                     p.mat = 0;
-                    pool_store(q, i, p);
+                    pool_store<TIME>(q, i, p);
                     retire(q, G, i, p);
                 } else {
-                    pool_store(q, i, p);
+                    pool_store<TIME>(q, i, p);
                 }
             }
             __syncthreads();
@@ -201,13 +206,15 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
         for (int k = threadIdx.x; k < n_adv; k += T) {
             int i = q.list[k];
             PS p;
-            pool_load(q, i, p);
+            pool_load<TIME>(q, i, p);
             int kind, which, uk = 0;
             double kt = q.kt[i];
-            int ev = step_advance(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which, uk, kt);
+            int ev = step_advance<false, TIME>(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which,
+                                                uk, kt);
             q.x[i] = p.x;
             q.y[i] = p.y;
             q.z[i] = p.z;
+            if (TIME) q.t[i] = p.t;
             q.s[i] = p.s;
             q.kt[i] = kt;
             q.ev[i] = ev | (kind << 4);
@@ -228,16 +235,16 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
         for (int k = threadIdx.x; k < n_ev; k += T) {
             int i = q.list[k];
             PS p;
-            pool_load(q, i, p);
+            pool_load<TIME>(q, i, p);
             int ev;
             if (k < n_cross) {
                 ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
             } else {
                 double kc = q.kc[i];
-                ev = step_collide(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
+                ev = step_collide<false, TIME>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
                 q.kc[i] = kc;
             }
-            pool_store(q, i, p);
+            pool_store<TIME>(q, i, p);
             if (ev == EV_DEAD) retire(q, G, i, p);
         }
         __syncthreads();
@@ -270,7 +277,7 @@ __device__ __forceinline__ int warp_list(int *list, Pred pred)
 // resident blocks per SM the register budget is planned for (smem allows as many)
 template <int PW> struct WpoolMinBlocks { static constexpr int value = PW <= 32 ? 6 : (PW <= 64 ? 5 : 2); };
 
-template <int PW>
+template <int PW, bool TIME>
 __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(World W, Particles G, Bank Bsrc, Bank Bdst,
                                                       RunBufs R, PersistentArgs a)
 {
@@ -315,10 +322,10 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
                     p.fate = FATE_LOST;
                     p.cell = 0;
                     p.mat = 0;
-                    pool_store(q, i, p);
+                    pool_store<TIME>(q, i, p);
                     retire(q, G, i, p);
                 } else {
-                    pool_store(q, i, p);
+                    pool_store<TIME>(q, i, p);
                 }
             }
             __syncwarp();
@@ -328,13 +335,15 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
         for (int k = lane; k < n_adv; k += 32) {
             int i = q.list[k];
             PS p;
-            pool_load(q, i, p);
+            pool_load<TIME>(q, i, p);
             int kind, which, uk = 0;
             double kt = q.kt[i];
-            int ev = step_advance(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which, uk, kt);
+            int ev = step_advance<false, TIME>(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which,
+                                                uk, kt);
             q.x[i] = p.x;
             q.y[i] = p.y;
             q.z[i] = p.z;
+            if (TIME) q.t[i] = p.t;
             q.s[i] = p.s;
             q.kt[i] = kt;
             q.ev[i] = ev | (kind << 4);
@@ -352,9 +361,9 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
         for (int k = lane; k < n_x; k += 32) {
             int i = q.list[k];
             PS p;
-            pool_load(q, i, p);
+            pool_load<TIME>(q, i, p);
             int ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
-            pool_store(q, i, p);
+            pool_store<TIME>(q, i, p);
             if (ev == EV_DEAD) retire(q, G, i, p);
         }
         __syncwarp();
@@ -364,51 +373,51 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
         for (int k = lane; k < n_c; k += 32) {
             int i = q.list[k];
             PS p;
-            pool_load(q, i, p);
+            pool_load<TIME>(q, i, p);
             double kc = q.kc[i];
-            int ev = step_collide(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
+            int ev = step_collide<false, TIME>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
             q.kc[i] = kc;
             q.ev[i] = EV_ADVANCE;
-            pool_store(q, i, p);
+            pool_store<TIME>(q, i, p);
             if (ev == EV_DEAD) retire(q, G, i, p);
         }
         __syncwarp();
     }
 }
 
-template <int PW>
+template <int PW, bool TIME>
 void launch_wpool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                     const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
 {
     size_t sm = pool_bytes(PW) * (WPOOL_T / 32);
-    cudaFuncSetAttribute(k_wpool<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_wpool<PW><<<grid, WPOOL_T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
+    cudaFuncSetAttribute(k_wpool<PW, TIME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_wpool<PW, TIME><<<grid, WPOOL_T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
 }
 
 template <int PW> int wpool_occupancy()
 {
     int n = 0;
     size_t sm = pool_bytes(PW) * (WPOOL_T / 32);
-    cudaFuncSetAttribute(k_wpool<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wpool<PW>, WPOOL_T, sm);
+    cudaFuncSetAttribute(k_wpool<PW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wpool<PW, false>, WPOOL_T, sm);
     return n;
 }
 
-template <int P, int T>
+template <int P, int T, bool TIME>
 void launch_pool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                    const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
 {
     size_t sm = pool_bytes(P);
-    cudaFuncSetAttribute(k_pool<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_pool<P, T><<<grid, T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
+    cudaFuncSetAttribute(k_pool<P, T, TIME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_pool<P, T, TIME><<<grid, T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
 }
 
 template <int P, int T> int pool_occupancy()
 {
     int n = 0;
     size_t sm = pool_bytes(P);
-    cudaFuncSetAttribute(k_pool<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<P, T>, T, sm);
+    cudaFuncSetAttribute(k_pool<P, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<P, T, false>, T, sm);
     return n;
 }
 
@@ -439,20 +448,29 @@ int pool_max_blocks_per_sm(int P)
     }
 }
 
+template <bool TIME>
+bool launch_pool_time(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                      const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st)
+{
+    switch (pool) {
+    case 32: launch_wpool_t<32, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 64: launch_wpool_t<64, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 128: launch_wpool_t<128, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 256: launch_pool_t<256, 256, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 512: launch_pool_t<512, 256, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 1024: launch_pool_t<1024, 256, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 2256: launch_pool_t<256, 128, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    case 2512: launch_pool_t<512, 128, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
+    default: return false;
+    }
+}
+
+// the time-aware instantiation only when the world needs it
 bool launch_pool(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                  const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st)
 {
-    switch (pool) {
-    case 32: launch_wpool_t<32>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 64: launch_wpool_t<64>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 128: launch_wpool_t<128>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 256: launch_pool_t<256, 256>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 512: launch_pool_t<512, 256>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 1024: launch_pool_t<1024, 256>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 2256: launch_pool_t<256, 128>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 2512: launch_pool_t<512, 128>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    default: return false;
-    }
+    return W.time_any ? launch_pool_time<true>(W, G, Bsrc, Bdst, R, a, pool, grid, st)
+                      : launch_pool_time<false>(W, G, Bsrc, Bdst, R, a, pool, grid, st);
 }
 
 }  // namespace mcgb

@@ -19,6 +19,7 @@ __device__ __forceinline__ void load_ps(const Particles &P, int i, PS &p)
     p.u = P.u[i]; p.v = P.v[i]; p.w = P.w[i];
     p.iu = P.iu[i]; p.iv = P.iv[i]; p.iw = P.iw[i];
     p.E = P.E[i];
+    p.t = P.t[i];
     p.s = P.s[i];
     p.g = P.g[i]; p.cell = P.cell[i]; p.ix = P.ix[i]; p.iy = P.iy[i]; p.ucell = P.ucell[i];
     p.mat = P.mat[i]; p.prob = P.prob[i]; p.root = P.root[i];
@@ -32,6 +33,7 @@ __device__ __forceinline__ void store_ps(const Particles &P, int i, const PS &p)
     P.u[i] = p.u; P.v[i] = p.v; P.w[i] = p.w;
     P.iu[i] = p.iu; P.iv[i] = p.iv; P.iw[i] = p.iw;
     P.E[i] = p.E;
+    P.t[i] = p.t;
     P.s[i] = p.s;
     P.g[i] = p.g; P.cell[i] = p.cell; P.ix[i] = p.ix; P.iy[i] = p.iy; P.ucell[i] = p.ucell;
     P.mat[i] = p.mat; P.prob[i] = p.prob; P.root[i] = p.root;
@@ -228,6 +230,7 @@ __device__ __forceinline__ void write_dead(const Particles &P, int slot, const P
     P.kc[slot] = kc;
 }
 
+template <bool TIME>
 __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank Bsrc, Bank Bdst,
                                                     RunBufs R, PersistentArgs a)
 {
@@ -274,9 +277,9 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
         if (__all_sync(0xffffffffu, done)) break;
         if (alive) {
             int kind, which, uk = 0;
-            int ev = step_advance(W, *Pd, p, slot, R, rep, kind, which, uk, kt);
+            int ev = step_advance<false, TIME>(W, *Pd, p, slot, R, rep, kind, which, uk, kt);
             if (ev == EV_CROSS) ev = step_cross(W, p, kind, which);
-            else if (ev == EV_COLLIDE) ev = step_collide(W, *Pd, p, slot, Bdst, R, uk, kc);
+            else if (ev == EV_COLLIDE) ev = step_collide<false, TIME>(W, *Pd, p, slot, Bdst, R, uk, kc);
             if (ev == EV_DEAD) {
                 alive = false;
                 write_dead(P, slot, p, kt, kc);
@@ -289,13 +292,14 @@ void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, con
                        const RunBufs &R, const PersistentArgs &a, int grid, int block,
                        cudaStream_t st)
 {
-    k_persistent<<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
+    if (W.time_any) k_persistent<true><<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
+    else k_persistent<false><<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
 }
 
 int persistent_max_blocks_per_sm(int block)
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<false>, block, 0);
     return n;
 }
 

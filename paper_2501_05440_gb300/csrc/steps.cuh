@@ -18,7 +18,8 @@ __device__ __forceinline__ int tally_batch(const ProblemDev &P, const PS &p)
 // distance to the nearest boundary d_s, move by min(d_c, d_s) (ties cross),
 // score the track length.  Returns EV_CROSS, EV_COLLIDE or EV_DEAD (lost or cut).
 // REPLAY: same draws and moves, no tallies; the flight length is returned in d.
-template <bool REPLAY = false>
+// TIME = false: the world has no time dependence (the clock is compiled out).
+template <bool REPLAY = false, bool TIME = true>
 __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const RunBufs &R, int rep, int &kind, int &which,
                                             int &uk, double &kt, double *d_out = nullptr)
@@ -41,22 +42,47 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     uint64_t n = draw_n(p.s);
     double dc = is_pos(sigt) ? -log_n(W, n) * mfp : MCGB_INF;
     double ds = boundary(W, p, kind, which);
-    if (is_inf(dc) && is_inf(ds)) {
+    const bool timed = TIME && P.time_on;
+    if (!timed && is_inf(dc) && is_inf(ds)) {
         p.fate = FATE_LOST;
         return EV_DEAD;
     }
     bool coll = lt_mag(dc, ds);     // both are +-0, positive or +inf
     double d = coll ? dc : ds;
+    // time dependence: the flight ends where the clock reaches tcut, at the
+    // distance (tcut - t) / (1/v); a tie goes to the collision or crossing
+    bool tcut = false;
+    const double ta = p.t;
+    double tb = p.t;
+    if (timed) {
+        double iv = P.ce ? 1.0 / (W.kv * sqrt(p.E)) : __ldg(W.g_invv + P.invv_off + p.g);
+        double dt = (P.tcut - p.t) / iv;
+        if (is_neg(dt)) dt = 0.0;
+        if (lt_mag(dt, d)) {
+            tcut = true;
+            d = dt;
+        }
+        if (!tcut && is_inf(d)) {
+            p.fate = FATE_LOST;
+            return EV_DEAD;
+        }
+        tb = tcut ? P.tcut : fma(d, iv, p.t);
+    }
     p.x = fma(d, p.u, p.x);
     p.y = fma(d, p.v, p.y);
     p.z = fma(d, p.w, p.z);
     if (REPLAY) {
         *d_out = d;
     } else {
-        score(W, P, p, d, tally_batch(P, p), R.tacc, rep);
+        score<TIME>(W, P, p, d, tally_batch(P, p), R.tacc, rep, ta, tb);
         kt = fma(d, nusf, kt);   // a sum over histories: agreement within rounding only
         if (R.own && (p.ucell >= 0 ? p.ucell : p.cell) == R.own_cell)
             R.own[(int64_t)slot * R.own_G + p.g] += d;
+    }
+    if (TIME) p.t = tb;
+    if (tcut) {
+        p.fate = FATE_TIME;
+        return EV_DEAD;
     }
     return coll ? EV_COLLIDE : EV_CROSS;
 }
@@ -84,7 +110,7 @@ __device__ __forceinline__ int step_cross(const World &W, PS &p, int kind, int w
 // sigma_t of that nuclide, scatter (elastic, target at rest) when
 // xi sigma_t <= sigma_s.
 // REPLAY (multigroup only): same draws, no bank; *nf_out = sites banked.
-template <bool REPLAY = false>
+template <bool REPLAY = false, bool TIME = true>
 __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const Bank &B, const RunBufs &R, int uk, double &kc,
                                             int *nf_out = nullptr)
@@ -101,7 +127,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             *nf_out = nf;
             p.nfis += nf;
         } else {
-            bank_append(B, R.bank_n, R.err, p, slot, nf);
+            bank_append<TIME>(B, R.bank_n, R.err, p, slot, nf);
         }
         xi = draw(p.s);
         if (!lt_mag(__ldg(W.g_ps + go + g), xi)) {
@@ -141,7 +167,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         double fl = floor(mu);
         double xi = draw(p.s);
         int nf = (int)fl + (lt_mag(mu - fl, xi) ? 0 : 1);
-        bank_append(B, R.bank_n, R.err, p, slot, nf);
+        bank_append<TIME>(B, R.bank_n, R.err, p, slot, nf);
         xi = draw(p.s);
         if (!lt_mag(ss, xi * st)) {
             p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);

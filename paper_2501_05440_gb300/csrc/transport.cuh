@@ -262,6 +262,7 @@ __device__ __forceinline__ int sample_cdf(const double *cdf, int n, double xi)
 struct PS {
     double x, y, z, u, v, w, E;
     double iu, iv, iw;   // 1/u, 1/v, 1/w, rounded whenever the direction is set
+    double t;            // time (s) when the problem is time dependent
     uint64_t s;
     int g, cell, ix, iy, ucell, mat, prob, root, nfis, ncoll, ncross, fate;
 };
@@ -628,8 +629,15 @@ __device__ __forceinline__ void ce_macro(const World &W, int mat, int k, double 
 // ---------------------------------------------------------------------------
 // Track-length tallies: score d into [batch][bin][energy] of every tally of the
 // particle's problem (accumulator replica `rep` spreads atomic traffic).
+// Times are finite and >= 0, so the magnitude compare orders them exactly.
+__device__ __forceinline__ bool lt_time(double a, double b) { return lt_mag(a, b); }
+
+// Track-length tallies; a tally with time bins scores instead, per bin, the
+// time the segment [ta, tb] spends in the bin times 1 / bin width (population).
+// TIME = false compiles the time bins out (worlds without time dependence).
+template <bool TIME>
 __device__ __forceinline__ void score(const World &W, const ProblemDev &P, const PS &p, double d,
-                                      int batch, double *acc, int rep)
+                                      int batch, double *acc, int rep, double ta, double tb)
 {
     for (int t = P.tally_first; t < P.tally_first + P.tally_count; t++) {
         int filter = __ldg(W.t_filter + t);
@@ -653,9 +661,23 @@ __device__ __forceinline__ void score(const World &W, const ProblemDev &P, const
             e = p.g;
         }
         int nb = __ldg(W.t_nbins + t), ne_ = __ldg(W.t_ne + t);
-        int64_t idx = (int64_t)rep * W.acc_size + __ldg(W.t_off + t) +
-                      ((int64_t)batch * nb + bin) * ne_ + e;
-        atomicAdd(acc + idx, d);
+        int ntb = TIME ? __ldg(W.t_ntb + t) : 0;
+        const int64_t base = (int64_t)rep * W.acc_size + __ldg(W.t_off + t);
+        const int64_t cell = ((int64_t)batch * nb + bin) * ne_ + e;   // [batch][bin][e]
+        if (ntb == 0) {
+            atomicAdd(acc + base + cell, d);
+            continue;
+        }
+        // [batch][bin][e][time bin]
+        const int64_t idx = base + cell * ntb;
+        const double *te = W.t_tedges + __ldg(W.t_toff + t);
+        const double *tw = W.t_tinvw + __ldg(W.t_toff + t);
+        for (int k = 0; k < ntb; k++) {
+            double e0 = __ldg(te + k), e1 = __ldg(te + k + 1);
+            double lo = lt_time(e0, ta) ? ta : e0;   // max(ta, e0)
+            double hi = lt_time(tb, e1) ? tb : e1;   // min(tb, e1)
+            if (lt_time(lo, hi)) atomicAdd(acc + idx + k, (hi - lo) * __ldg(tw + k));
+        }
     }
 }
 
@@ -664,6 +686,7 @@ __device__ __forceinline__ void score(const World &W, const ProblemDev &P, const
 // (parent, child) order at the end of the cycle.  The lanes that bank together
 // reserve their sites with one atomic: counts are summed and prefix-summed from
 // three ballots of their bit planes (a count of 8 or more takes its own atomic).
+template <bool TIME = true>
 __device__ __forceinline__ void bank_append(const Bank &B, int *bank_n, int *err, PS &p, int slot,
                                             int nf)
 {
@@ -683,6 +706,7 @@ __device__ __forceinline__ void bank_append(const Bank &B, int *bank_n, int *err
             atomicOr(err, ERR_BANK_OVERFLOW);
         } else {
             B.x[pos] = p.x;
+            B.t[pos] = TIME ? p.t : 0.0;
             B.y[pos] = p.y;
             B.z[pos] = p.z;
             B.cell[pos] = p.cell;
@@ -715,6 +739,7 @@ __device__ __forceinline__ void birth_energy(const World &W, const ProblemDev &P
 __device__ __forceinline__ bool sample_source(const World &W, const ProblemDev &P, PS &p)
 {
     p.u = p.v = p.w = 0.0;
+    p.t = P.time_on ? P.t0 : 0.0;
     if (P.src_kind == SRC_BOX) {
         bool ok = false;
         for (int t = 0; t < MAX_TRIES && !ok; t++) {
@@ -752,6 +777,7 @@ __device__ __forceinline__ void birth_from_site(const World &W, const ProblemDev
                                                 int b, PS &p)
 {
     p.x = B.x[b];
+    p.t = B.t[b];
     p.y = B.y[b];
     p.z = B.z[b];
     p.cell = B.cell[b];

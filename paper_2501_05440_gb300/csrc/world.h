@@ -32,7 +32,7 @@ enum { FILTER_CELL = 0, FILTER_LATTICE = 1, FILTER_MATERIAL = 2 };
 enum { B_NONE = 0, B_ROOT = 1, B_LATX = 2, B_LATY = 3, B_UNIV = 4 };
 // history fates
 enum { FATE_ALIVE = -1, FATE_ABSORBED = 0, FATE_LEAKED = 1, FATE_CUT = 2, FATE_LOST = 3,
-       FATE_CAPPED = 4 };
+       FATE_CAPPED = 4, FATE_TIME = 5 };
 // error flags raised by kernels
 enum { ERR_BANK_OVERFLOW = 1, ERR_SOURCE = 2, ERR_QUEUE = 4, ERR_ITER = 8 };
 
@@ -52,6 +52,11 @@ struct ProblemDev {
     int batches;
     uint64_t seed;
     int64_t n;            // source histories
+    // time dependence (fixed source): births at t0, flights cut at tcut; 1/v per
+    // group from g_invv[invv_off + g] (multigroup) or 1 / (kv sqrt(E)) (CE)
+    int time_on;
+    int invv_off;
+    double t0, tcut;
 };
 
 struct World {
@@ -91,14 +96,24 @@ struct World {
     const double *src_cdf;
     // log tables: ln(1 + j/256), 1/(1 + j/256), (e - 53) ln 2
     const double *logtab, *rinvtab, *etab;
-    // tallies (global tally ids; accumulators [rep][acc_size])
+    // tallies (global tally ids; accumulators [rep][acc_size]); a tally with
+    // t_ntb > 0 time bins has edges t_tedges[t_toff + k] and 1 / width
+    // t_tinvw[t_toff + k] and scores population instead of track length
     const int *t_filter, *t_nbins, *t_ne, *t_off, *t_eoff, *t_nedges, *t_batches;
     const double *t_edges;
+    const int *t_ntb, *t_toff;
+    const double *t_tedges, *t_tinvw;
     int acc_size, nrep;
+    // time dependence: inverse group speeds; CE speed constant v = kv sqrt(E);
+    // time_any: some problem is time dependent or some tally has time bins (the
+    // persistent kernels are then launched in their time-aware instantiation)
+    const double *g_invv;
+    double kv;
+    int time_any;
 };
 
 struct Particles {
-    double *x, *y, *z, *u, *v, *w, *E;
+    double *x, *y, *z, *u, *v, *w, *E, *t;
     double *iu, *iv, *iw;   // direction reciprocals
     double *kt, *kc;      // per-history k estimator sums (track length, collision)
     uint64_t *s;
@@ -108,7 +123,7 @@ struct Particles {
 };
 
 struct Bank {
-    double *x, *y, *z;
+    double *x, *y, *z, *t;
     int *cell, *ix, *iy, *ucell, *mat, *parent, *child, *root, *prob;
     int64_t cap;
 };
