@@ -70,6 +70,9 @@ def lib():
             L.orc_maxwell.restype = d
             L.orc_maxwell.argtypes = [P]
             L.orc_elastic.argtypes = [d, d, P, P, P]
+            L.orc_free_gas.argtypes = [d, d, d, P, P, P]
+            L.orc_set_free_gas.restype = i32
+            L.orc_set_free_gas.argtypes = [P, d, d]
             L.orc_history_count.restype = i64
             L.orc_history_count.argtypes = [P]
             L.orc_bank_count.restype = i64
@@ -170,6 +173,9 @@ class Oracle:
             edges = _f64(t.get("edges", [0.0]))
             ne = len(edges) if "edges" in t else 0
             self._chk(L.orc_add_tally(c, FILTER[t["filter"]], ne, _p(edges)))
+        if "free_gas" in pb:
+            fg = pb["free_gas"]
+            self._chk(L.orc_set_free_gas(c, float(fg["kT"]), float(fg.get("cut", 0.0))))
         if "time" in pb:
             tm = pb["time"]
             self._chk(L.orc_set_time(c, float(tm.get("t0", 0.0)), float(tm["t_cut"])))
@@ -309,6 +315,14 @@ def elastic(E, A, direction, state):
     d = _f64(direction)
     out = np.zeros(4)
     lib().orc_elastic(E, A, _p(d), C.byref(s), _p(out))
+    return out, s.value
+
+
+def free_gas(E, A, kT, direction, state):
+    s = C.c_uint64(state)
+    d = _f64(direction)
+    out = np.zeros(4)
+    lib().orc_free_gas(E, A, kT, _p(d), C.byref(s), _p(out))
     return out, s.value
 
 

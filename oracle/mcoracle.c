@@ -264,6 +264,84 @@ static double maxwell(uint64_t *s)
 
 double orc_maxwell(uint64_t *s) { return maxwell(s); }
 
+/* cos^2 of an angle uniform on [0, pi/2]: a^2 / (a^2 + b^2) of a point uniform
+ * in the unit disk (rejection, at most 64 tries; 1 if none is accepted) */
+static double disk_cos2(uint64_t *s)
+{
+    for (int t = 0; t < 64; t++) {
+        double aa = 2.0 * draw(s) - 1.0;
+        double bb = 2.0 * draw(s) - 1.0;
+        double rr = fma(aa, aa, bb * bb);
+        if (rr <= 1.0 && rr > 0.0) return aa * aa / rr;
+    }
+    return 1.0;
+}
+
+/* Elastic scattering off a free-gas target with a constant cross section (the
+ * model Sec. 4 assumes for its continuous-energy pin).  Speeds are in units of
+ * the target's thermal speed sqrt(2 kT / (A m)): the neutron's is
+ * y = sqrt(A E / kT).  The target's speed x and the cosine mu between its
+ * direction and the neutron's follow the density proportional to the relative
+ * speed r = |y Omega - x Omega_T| times the Maxwellian x^2 exp(-x^2):
+ * proposals from (x + y) x^2 exp(-x^2) -- with probability
+ * y sqrt(pi) / (y sqrt(pi) + 2) from x^2 exp(-x^2), x^2 = -(ln xi1 + ln xi2 c),
+ * c = cos^2 of a uniform angle, else from x^3 exp(-x^2), x^2 = -(ln xi1 + ln xi2)
+ * -- with mu = 2 xi - 1, accepted when xi (x + y) <= r.  The target direction is
+ * the neutron's rotated by mu.  Two-body kinematics: the centre-of-mass velocity
+ * V = (y Omega + A x Omega_T) / (A + 1) is kept, the neutron's speed in that
+ * frame A r / (A + 1) is kept and its direction there is isotropic; then
+ * E' = E |v'|^2 / y^2 (floored at 1e-5 eV) and Omega' = v' / |v'|.           */
+static double free_gas(double E, double A, double kT, uint64_t *s, double *u, double *v,
+                       double *w)
+{
+    log_init();
+    const double SQRT_PI = 1.7724538509055160273;
+    double y = sqrt(A * E / kT);
+    double py = y * SQRT_PI;
+    double x = 0.0, mu = 1.0, r = y;
+    for (int k = 0; k < MAX_TRIES; k++) {
+        double x2;
+        if (draw(s) * (py + 2.0) < py) {
+            double L1 = log_n(draw_n(s));
+            double L2 = log_n(draw_n(s));
+            double c2 = disk_cos2(s);
+            x2 = -(L1 + L2 * c2);
+        } else {
+            double L1 = log_n(draw_n(s));
+            double L2 = log_n(draw_n(s));
+            x2 = -(L1 + L2);
+        }
+        x = sqrt(x2);
+        mu = 2.0 * draw(s) - 1.0;
+        double r2 = x2 + y * y - 2.0 * x * y * mu;
+        r = sqrt(r2 > 0.0 ? r2 : 0.0);
+        if (draw(s) * (x + y) <= r) break;
+    }
+    double tu = *u, tv = *v, tw = *w;
+    rotate(mu, s, &tu, &tv, &tw);
+    double inv = 1.0 / (A + 1.0);
+    double Vx = (y * *u + A * x * tu) * inv;
+    double Vy = (y * *v + A * x * tv) * inv;
+    double Vz = (y * *w + A * x * tw) * inv;
+    double cu, cv, cw;
+    iso_dir(s, &cu, &cv, &cw);
+    double wc = A * r * inv;
+    double px = Vx + wc * cu, py2 = Vy + wc * cv, pz = Vz + wc * cw;
+    double p2 = px * px + py2 * py2 + pz * pz;
+    double ip = 1.0 / sqrt(p2);
+    *u = px * ip; *v = py2 * ip; *w = pz * ip;
+    double Ep = E * (p2 / (y * y));
+    return Ep < E_MIN ? E_MIN : Ep;
+}
+
+int orc_free_gas(double E, double A, double kT, const double dir[3], uint64_t *s, double out[4])
+{
+    double u = dir[0], v = dir[1], w = dir[2];
+    out[0] = free_gas(E, A, kT, s, &u, &v, &w);
+    out[1] = u; out[2] = v; out[3] = w;
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* problem description                                                        */
 typedef struct { int type, bc; double c[4]; double r2; } Surface;
@@ -308,6 +386,8 @@ struct orc_ctx {
     Source src;
     int src_set;
     Tally *tally;
+    /* free-gas elastic scattering below fg_emax (kT > 0 enables it) */
+    double fg_kT, fg_emax;
     /* time dependence: source time, cutoff, 1/v per group, CE speed constant */
     int time_on;
     double t0, tcut, kv;
@@ -585,6 +665,14 @@ int orc_add_tally(orc_ctx *c, int filter, int n_edges, const double *edges)
     t->ntb = 0;
     t->tedges = t->tinvw = NULL;
     return c->nt++;
+}
+
+int orc_set_free_gas(orc_ctx *c, double kT, double cut)
+{
+    if (!(kT > 0.0) || !(kT < INF) || cut < 0.0) return fail(c, ORC_EINVAL, "bad free-gas settings");
+    c->fg_kT = kT;
+    c->fg_emax = (cut > 0.0 ? cut : 400.0) * kT;
+    return 0;
 }
 
 int orc_set_time(orc_ctx *c, double t0, double t_cut)
@@ -1214,7 +1302,10 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
             /* scatter (elastic, target at rest) with probability sigma_s,i/sigma_t,i */
             xi = draw(&p->s);
             if (xi * x.st[sel] <= x.ss[sel]) {
-                p->E = elastic(p->E, u->A, &p->s, &p->u, &p->v, &p->w);
+                if (c->fg_kT > 0.0 && p->E < c->fg_emax)
+                    p->E = free_gas(p->E, u->A, c->fg_kT, &p->s, &p->u, &p->v, &p->w);
+                else
+                    p->E = elastic(p->E, u->A, &p->s, &p->u, &p->v, &p->w);
                 set_recip(p);
             } else {
                 p->alive = 0;

@@ -68,6 +68,9 @@ int orc_set_max_collisions(orc_ctx *c, int max_collisions);
  * are given as 1/v per group (s/cm); continuous energy uses v = K sqrt(E),
  * K = sqrt(2 e / m_n) * 100 cm/s per sqrt(eV).  Fixed-source runs only. */
 int orc_set_time(orc_ctx *c, double t0, double t_cut);
+/* Free-gas elastic scattering with a constant cross section (Sec. 4) for
+ * continuous-energy collisions below cut * kT (cut 0: 400); kT in eV. */
+int orc_set_free_gas(orc_ctx *c, double kT, double cut);
 int orc_set_inverse_speeds(orc_ctx *c, int G, const double *inv_v);
 /* time bins of a tally: it then scores, per bin, the time each particle spends
  * in the bin divided by the bin width (mean population per source particle) */
@@ -115,6 +118,7 @@ double orc_rng_xi(uint64_t s);
 double orc_log(double xi);
 int orc_iso_dir(uint64_t *s, double out[3]);
 int orc_elastic(double E, double A, const double dir[3], uint64_t *s, double out[4]);
+int orc_free_gas(double E, double A, double kT, const double dir[3], uint64_t *s, double out[4]);
 double orc_maxwell(uint64_t *s);
 int orc_probe(orc_ctx *c, const double pos[3], const double dir[3], int out_path[5],
               double *dist, int *kind);
