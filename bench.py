@@ -8,7 +8,8 @@ ordering, resampling, tallies), persistent event-loop form.  Beside it, in the
 same JSON line: the plain one-kernel-per-event form and the monolithic
 one-kernel-per-segment form (the paper's own GPU design) on the same workload, the
 64-problem batched run against 64 separate plain runs, derivatives per second
-through the replay-backward kernel, the FP64 roofline of the transport
+through the replay-backward kernel, the paper's time-dependent
+continuous-energy pin-cell benchmark (1e7 source histories), the FP64 roofline of the transport
 kernel, the CPU oracle timed on this host's cores, and GPU clocks sampled
 during the timed region.
 
@@ -324,6 +325,40 @@ def ce_leg(m, W, torch, steps=3):
             "k": c.get_k()["k"]}
 
 
+def ce_time_leg(m, W, torch, n=10_000_000, sample=20_000):
+    """The paper's continuous-energy benchmark shape (Sec. 4): infinite pin cell,
+    uniform 14 MeV source, time-dependent fixed source with free-gas scattering,
+    1e7 source histories; the CPU oracle on a `sample` of source histories."""
+    pb = W.ce_time_pin(n=n)
+    c = m.Context(mode=m.MODE_PERSISTENT, bank_factor=8.0)
+    c.set_stream(torch.cuda.current_stream().cuda_stream)
+    m.load_problem(c, pb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    c.run()
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    cnt = c.get_counters()
+    out = {"workload": "ce-pin-cell-4nuclides-time-14mev-free-gas", "source_histories": n,
+           "s": s, "source_histories_per_s": n / s,
+           "histories_incl_secondaries": cnt["histories"],
+           "events_per_s": (cnt["collisions"] + cnt["crossings"]) / s,
+           "generations": cnt["generations"], "time_cut": cnt["time_cut"]}
+    import oracle
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(W.with_run(pb, n=sample))
+    t0 = time.perf_counter()
+    o.run(threads=cores)
+    cpu_s = time.perf_counter() - t0
+    out["cpu_oracle"] = {"source_histories_per_s": sample / cpu_s, "cores": cores,
+                         "sample": f"{sample} source histories of the same problem"}
+    from paper_2501_05440_gb300.report import core_equivalency
+    out["core_equivalency"] = core_equivalency(cores, n / (sample / cpu_s), 1, s)
+    return out
+
+
 def cpu_baseline(W, n=200_000):
     import oracle
     cores = os.cpu_count() or 1
@@ -383,6 +418,7 @@ def run_mcgb(args):
         out["batched"] = batched_leg(m, W, torch)
         out["grad"] = grad_leg(m, W, torch, 1_000_000)
         out["ce_pin"] = ce_leg(m, W, torch)
+        out["ce_time"] = ce_time_leg(m, W, torch)
         out["cpu_baseline"] = cpu_baseline(W)
         from paper_2501_05440_gb300.report import core_equivalency
         cb = out["cpu_baseline"]

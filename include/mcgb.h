@@ -185,6 +185,13 @@ int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions);
  * 100 cm/s (continuous energy).  Fixed-source runs only (an eigenvalue run or
  * a derivative run fails); requires 0 <= t0 < t_cut < inf. */
 int mcgb_set_time(mcgb_ctx *ctx, double t0, double t_cut);
+/* Free-gas elastic scattering with a constant cross section (the model Sec. 4
+ * assumes for its continuous-energy pin cell): below cut * kT (cut 0: 400) a
+ * continuous-energy elastic collision samples the target's velocity from a
+ * Maxwellian at temperature kT (eV) weighted by the relative speed and scatters
+ * isotropically in the centre-of-mass frame; above it the target is at rest.
+ * kT > 0 and finite, cut >= 0. */
+int mcgb_set_free_gas(mcgb_ctx *ctx, double kT, double cut);
 /* inv_v[G]: 1/v of each group in s/cm, positive and finite. */
 int mcgb_set_inverse_speeds(mcgb_ctx *ctx, int G, const double *inv_v);
 /* Time bins of a tally: n_edges increasing edges (s, first >= 0).  The tally

@@ -92,6 +92,7 @@ def lib():
                 "mcgb_add_tally": [P, i32, i32, P, P],
                 "mcgb_set_max_collisions": [P, i32],
                 "mcgb_set_time": [P, d, d], "mcgb_set_inverse_speeds": [P, i32, P],
+                "mcgb_set_free_gas": [P, d, d],
                 "mcgb_set_tally_time_bins": [P, i32, i32, P],
                 "mcgb_run_eigenvalue": [P, i64, i32, i32, u64],
                 "mcgb_run_fixed_source": [P, i64, i32, u64],
@@ -237,6 +238,9 @@ class Context:
 
     def set_max_collisions(self, m):
         _chk(self.L.mcgb_set_max_collisions(self.h, m))
+
+    def set_free_gas(self, kT, cut=0.0):
+        _chk(self.L.mcgb_set_free_gas(self.h, float(kT), float(cut)))
 
     def set_time(self, t0, t_cut):
         _chk(self.L.mcgb_set_time(self.h, float(t0), float(t_cut)))
@@ -403,6 +407,8 @@ def load_problem(ctx: Context, pb: dict) -> Context:
         if "time_edges" in t:
             ctx.set_tally_time_bins(i, t["time_edges"])
             ctx._timed_tallies.add(i)
+    if "free_gas" in pb:
+        ctx.set_free_gas(pb["free_gas"]["kT"], pb["free_gas"].get("cut", 0.0))
     if "time" in pb:
         ctx.set_time(pb["time"].get("t0", 0.0), pb["time"]["t_cut"])
         if pb["G"] > 0:

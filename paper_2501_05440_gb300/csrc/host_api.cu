@@ -757,7 +757,7 @@ static int run_fixed_world(mcgb_ctx *c, bool grad, int det_cell)
         CKR(read_flags(c, M, err));
         c->counters.histories += total;
         if (err & ERR_BANK_OVERFLOW)
-            return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow in generation " + std::to_string(gen));
+            return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow in generation " + std::to_string(gen) + " (raise opts.bank_factor)");
         if (err & ERR_SOURCE) return fail(MCGB_E_STATE, "source sampling failed");
         if (gen == 0 && c->opts.record_histories) {
             CKR(copy_records(c, total));
@@ -1092,6 +1092,15 @@ int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions)
 {
     if (!ctx || max_collisions < 0) return fail(MCGB_E_INVALID_ARG, "bad max_collisions");
     ctx->def.max_coll = max_collisions;
+    return MCGB_OK;
+}
+
+int mcgb_set_free_gas(mcgb_ctx *ctx, double kT, double cut)
+{
+    if (!ctx || !(kT > 0.0) || !std::isfinite(kT) || !(cut >= 0.0) || !std::isfinite(cut))
+        return fail(MCGB_E_INVALID_ARG, "bad free-gas settings");
+    ctx->def.fg_kT = kT;
+    ctx->def.fg_cut = cut;
     return MCGB_OK;
 }
 

@@ -296,6 +296,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
         }
         if (acc_size > (int64_t)1 << 30) return "tally accumulators too large";
         P.max_coll = pd.max_coll;
+        P.fg_kT = pd.fg_kT;
+        P.fg_emax = (pd.fg_cut > 0.0 ? pd.fg_cut : 400.0) * pd.fg_kT;
         P.time_on = pd.time_on ? 1 : 0;
         P.t0 = pd.t0;
         P.tcut = pd.tcut;

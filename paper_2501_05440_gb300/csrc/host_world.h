@@ -61,6 +61,7 @@ struct ProblemDef {
     bool time_on = false;
     double t0 = 0.0, tcut = 0.0;
     std::vector<double> invv;    // inverse group speeds (multigroup)
+    double fg_kT = 0.0, fg_cut = 0.0;   // free gas: kT (eV), applied below fg_cut * kT
     std::string check() const;   // empty when runnable
 };
 

@@ -170,7 +170,10 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         bank_append<TIME>(B, R.bank_n, R.err, p, slot, nf);
         xi = draw(p.s);
         if (!lt_mag(ss, xi * st)) {
-            p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);
+            if (is_pos(P.fg_kT) && lt_mag(p.E, P.fg_emax))
+                p.E = free_gas(W, p.E, __ldg(W.n_A + nuc), P.fg_kT, p.s, p.u, p.v, p.w);
+            else
+                p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);
             set_recip(W, p);
         } else {
             p.fate = FATE_ABSORBED;

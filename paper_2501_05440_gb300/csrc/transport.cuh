@@ -248,6 +248,80 @@ __device__ __forceinline__ double maxwell(const World &W, uint64_t &s)
     return E_MAX;
 }
 
+// cos^2 of an angle uniform on [0, pi/2]: a^2 / (a^2 + b^2) of a point uniform
+// in the unit disk (rejection, at most 64 tries; 1 if none is accepted)
+__device__ __forceinline__ double disk_cos2(uint64_t &s)
+{
+    double aa, bb, rr;
+    int t = 0;
+    bool ok;
+    do {
+        aa = draw_sym(s);
+        bb = draw_sym(s);
+        rr = fma(aa, aa, bb * bb);
+        ok = !lt_mag(1.0, rr) && is_pos(rr);
+        t++;
+    } while (!ok && t < 64);
+    return ok ? aa * aa / rr : 1.0;
+}
+
+// Elastic scattering off a free-gas target with a constant cross section (the
+// model Sec. 4 assumes for its continuous-energy pin).  Speeds in units of the
+// target's thermal speed sqrt(2 kT / (A m)); the neutron's is y = sqrt(A E / kT).
+// The target speed x and cosine mu (target vs neutron direction) follow the
+// relative speed r = |y Omega - x Omega_T| times the Maxwellian x^2 exp(-x^2):
+// proposals from (x + y) x^2 exp(-x^2) -- with probability y sqrt(pi) /
+// (y sqrt(pi) + 2) from x^2 exp(-x^2) (x^2 = -(ln xi1 + ln xi2 c), c = cos^2 of
+// a uniform angle), else from x^3 exp(-x^2) (x^2 = -(ln xi1 + ln xi2)) -- with
+// mu = 2 xi - 1, accepted when xi (x + y) <= r.  The target direction is the
+// neutron's rotated by mu.  The centre-of-mass velocity V = (y Omega +
+// A x Omega_T) / (A + 1) is kept, the neutron's speed in that frame A r / (A + 1)
+// is kept and its direction there is isotropic; E' = E |v'|^2 / y^2 (floored at
+// 1e-5 eV), Omega' = v' / |v'|.
+__device__ __forceinline__ double free_gas(const World &W, double E, double A, double kT,
+                                           uint64_t &s, double &u, double &v, double &w)
+{
+    const double SQRT_PI = 1.7724538509055160273;
+    double y = sqrt(A * E / kT);
+    double py = y * SQRT_PI;
+    double x = 0.0, mu = 1.0, r = y;
+    for (int k = 0; k < MAX_TRIES; k++) {
+        double x2;
+        if (lt_mag(draw(s) * (py + 2.0), py)) {
+            double L1 = log_n(W, draw_n(s));
+            double L2 = log_n(W, draw_n(s));
+            double c2 = disk_cos2(s);
+            x2 = -(L1 + L2 * c2);
+        } else {
+            double L1 = log_n(W, draw_n(s));
+            double L2 = log_n(W, draw_n(s));
+            x2 = -(L1 + L2);
+        }
+        x = sqrt(x2);
+        mu = draw_sym(s);
+        double r2 = x2 + y * y - 2.0 * x * y * mu;
+        r = sqrt(is_pos(r2) ? r2 : 0.0);
+        if (!lt_mag(r, draw(s) * (x + y))) break;
+    }
+    double tu = u, tv = v, tw = w;
+    rotate(mu, s, tu, tv, tw);
+    double inv = 1.0 / (A + 1.0);
+    double Vx = (y * u + A * x * tu) * inv;
+    double Vy = (y * v + A * x * tv) * inv;
+    double Vz = (y * w + A * x * tw) * inv;
+    double cu, cv, cw;
+    iso_dir(s, cu, cv, cw);
+    double wc = A * r * inv;
+    double px = Vx + wc * cu, py2 = Vy + wc * cv, pz = Vz + wc * cw;
+    double p2 = px * px + py2 * py2 + pz * pz;
+    double ip = 1.0 / sqrt(p2);
+    u = px * ip;
+    v = py2 * ip;
+    w = pz * ip;
+    double Ep = E * (p2 / (y * y));
+    return lt_mag(Ep, E_MIN) ? E_MIN : Ep;
+}
+
 // First k with xi <= cdf[k] (cdf nondecreasing, ending with exactly 1): the count
 // of entries below xi, taken over the whole table (no divergent early exit).
 __device__ __forceinline__ int sample_cdf(const double *cdf, int n, double xi)

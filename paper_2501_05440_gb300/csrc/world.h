@@ -57,6 +57,8 @@ struct ProblemDev {
     int time_on;
     int invv_off;
     double t0, tcut;
+    // free-gas elastic scattering below fg_emax (fg_kT > 0 enables it)
+    double fg_kT, fg_emax;
 };
 
 struct World {

@@ -79,6 +79,19 @@ def test_ce_scattering_pulse_parity(mcgb, mode, pool, graphs):
     _parity(pb, mode, pool, graphs)
 
 
+@pytest.mark.parametrize("mode,pool,graphs", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (1, -1, 0)])
+def test_free_gas_thermal_parity(mcgb, mode, pool, graphs):
+    E = np.geomspace(W.E_MIN, W.E_MAX, 2000)
+    pb = W.time_pulse_ce(1.0, 0.0253, t_cut=5.0e-5, t_edges=np.linspace(0.0, 5.0e-5, 6),
+                         A=1.0, sig_s=20.0, density=0.05, n=4_000)
+    nuc = pb["nuclides"][0]
+    nuc["E"], nuc["sig_s"] = E, np.full_like(E, 20.0)
+    nuc["sig_c"], nuc["sig_f"] = 1.0 / np.sqrt(E), np.zeros_like(E)
+    pb["free_gas"] = {"kT": 0.0253}
+    c, o = _parity(pb, mode, pool, graphs)
+    assert c.get_counters()["collisions"] > 2 * pb["run"]["n"]
+
+
 @pytest.mark.parametrize("mode,pool,graphs", [(0, 0, 0), (1, 0, 0), (1, -1, 0)])
 def test_ce_time_pin_parity(mcgb, mode, pool, graphs):
     pb = W.ce_time_pin(n=1_500, npts=5_000, nres=40, t_cut=2e-6, ntbins=12, batches=5)
@@ -98,3 +111,21 @@ def test_time_runs_reject_eigen_and_derivatives(mcgb):
     c = mcgb.load_problem(mcgb.Context(mode=1), pb)
     with pytest.raises(mcgb.McgbError):
         c.forward_fixed(1000, 1, pb["detector_cell"])
+
+
+def test_ce_time_pin_full_size_sampled(mcgb):
+    """1e6 source histories of the time-dependent pin (the bench leg runs 1e7 of
+    the same): sampled generation-0 histories recomputed one by one by the
+    oracle are identical; every history ends absorbed or at the cutoff."""
+    from oracle import Oracle
+    pb = W.ce_time_pin(n=1_000_000)
+    c = mcgb.load_problem(mcgb.Context(mode=1, record_histories=True, bank_factor=8.0), pb)
+    c.run()
+    h = c.get_histories()
+    assert len(h["n_coll"]) == 1_000_000
+    idx = np.sort(np.random.default_rng(5).choice(1_000_000, 300, replace=False))
+    ho = Oracle(pb).histories_by_index(idx)
+    assert_same_histories({k: v[idx] for k, v in h.items()}, ho)
+    assert set(np.unique(h["fate"]).tolist()) <= {0, 5}
+    cnt = c.get_counters()
+    assert cnt["time_cut"] > 0 and cnt["leaks"] == 0 and cnt["lost"] == 0

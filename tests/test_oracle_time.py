@@ -137,6 +137,23 @@ def test_ce_one_over_v_capture_with_scattering(orc):
     assert o.counters()["collisions"] > 10 * pb["run"]["n"]
 
 
+def test_ce_one_over_v_capture_with_free_gas(orc):
+    """Free-gas scattering (upscatter included) leaves Sigma_c v constant under
+    1/v capture: the same exponential decay holds from a thermal source."""
+    a, dens = 1.0, 0.05
+    E = np.geomspace(W.E_MIN, W.E_MAX, 4000)
+    pb = W.time_pulse_ce(1.0, 0.0253, t_cut=5.0e-5, t_edges=np.linspace(0.0, 5.0e-5, 6),
+                         A=1.0, sig_s=20.0, density=dens, n=10_000)
+    nuc = pb["nuclides"][0]
+    nuc["E"], nuc["sig_s"] = E, np.full_like(E, 20.0)
+    nuc["sig_c"], nuc["sig_f"] = a / np.sqrt(E), np.zeros_like(E)
+    pb["free_gas"] = {"kT": 0.0253}
+    o, mean, sd = _run(orc, pb)
+    lam = dens * a * _v_thermal_anchor(1.0)
+    edges = np.asarray(pb["tallies"][0]["time_edges"])
+    _check(mean, sd, _bin_average(np.array([[-lam]]), np.array([1.0]), edges))
+
+
 def test_time_is_fixed_source_only(orc):
     pb = W.pin_cell_mg(n=100, inactive=1, active=1)
     pb["time"] = {"t0": 0.0, "t_cut": 1e-5, "inv_v": np.full(pb["G"], 1e-6)}

@@ -554,8 +554,9 @@ def ce_time_pin(seed=1, n=10_000_000, t_cut=1.0e-5, ntbins=40, npts=50_000, nres
                 batches=20):
     """Stand-in for the paper's continuous-energy benchmark (Sec. 4): the infinite
     pin cell of ce_pin_cell driven by a uniform 14 MeV source, time-dependent
-    fixed source; tally: neutron population per cell in `ntbins` log-spaced time
-    bins on [1e-9 s, t_cut] (energy-integrated)."""
+    fixed source, free-gas elastic scattering (kT = 0.0253 eV) below 400 kT;
+    tally: neutron population per cell in `ntbins` log-spaced time bins on
+    [1e-9 s, t_cut] (energy-integrated)."""
     pb = ce_pin_cell(seed=seed, n=n, npts=npts, nres=nres, nbins=1)
     pb["name"] = "ce-pin-cell-4nuclides-time-14mev"
     pb["source"] = {"kind": "box", "box": [-0.63, 0.63, -0.63, 0.63, 0.0, 0.0], "accept": "any",
@@ -563,5 +564,7 @@ def ce_time_pin(seed=1, n=10_000_000, t_cut=1.0e-5, ntbins=40, npts=50_000, nres
     t_edges = np.concatenate([[0.0], np.geomspace(1.0e-9, t_cut, ntbins)])
     pb["tallies"] = [{"filter": "cell", "edges": np.array([E_MIN, E_MAX]), "time_edges": t_edges}]
     pb["time"] = {"t0": 0.0, "t_cut": float(t_cut)}
+    # the paper's model: free-gas elastic scattering, here at 293.6 K
+    pb["free_gas"] = {"kT": 0.0253}
     pb["run"] = _fixed_run(n, seed, batches)
     return pb
