@@ -335,6 +335,9 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
 
     // continuous energy: union grid, per-nuclide interval maps and interval data
     std::vector<double> Eu;
+    std::vector<int> ukey_lo(2, 0);
+    long long ukey0 = 0;
+    int nukey = 1;
     std::vector<int> umap, n_ivoff;
     std::vector<double> n_iv;
     if (!nucs.empty()) {
@@ -342,6 +345,28 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
         std::sort(Eu.begin(), Eu.end());
         Eu.erase(std::unique(Eu.begin(), Eu.end()), Eu.end());
         size_t nuni = Eu.size();
+        // bucket index of the union grid: result of the plain search (largest
+        // i <= n-2 with Eu[i] <= E, else 0) at each bucket's lower edge
+        auto search = [&](double E) {
+            int lo = 0, hi = (int)nuni - 1;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (!(E < Eu[mid])) lo = mid;
+                else hi = mid;
+            }
+            return lo;
+        };
+        auto bits = [](double x) { long long b; std::memcpy(&b, &x, 8); return b; };
+        long long k0 = bits(Eu.front()) >> 44, k1 = bits(Eu.back()) >> 44;
+        ukey0 = k0;
+        nukey = (int)(k1 - k0 + 1);
+        ukey_lo.resize(nukey + 1);
+        for (int b = 0; b <= nukey; b++) {
+            long long kb = (k0 + b) << 44;
+            double edge;
+            std::memcpy(&edge, &kb, 8);
+            ukey_lo[b] = search(edge);
+        }
         umap.resize(nucs.size() * nuni);
         for (size_t q = 0; q < nucs.size(); q++) {
             const NucDef &u = *nucs[q];
@@ -391,6 +416,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
            o_mufl = S.put(g_mufl), o_mufr = S.put(g_mufr), o_ps = S.put(g_ps),
            o_stot = S.put(g_stot), o_chicdf = S.put(g_chicdf), o_sigs = S.put(gg_sigs),
            o_scdf = S.put(gg_scdf);
+    size_t o_ukey = S.put(ukey_lo);
     size_t o_Eu = S.put(Eu), o_umap = S.put(umap), o_nivoff = S.put(n_ivoff), o_niv = S.put(n_iv),
            o_nA = S.put(n_A), o_nnu = S.put(n_nu);
     size_t o_mcoff = S.put(mc_off), o_mcn = S.put(mc_n), o_mcnuc = S.put(mc_nuc),
@@ -430,6 +456,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(g_mu, double, o_mu); P_(g_mufl, double, o_mufl); P_(g_mufr, double, o_mufr);
     P_(g_ps, double, o_ps); P_(g_stot, double, o_stot); P_(g_chicdf, double, o_chicdf);
     P_(gg_sigs, double, o_sigs); P_(gg_scdf, double, o_scdf);
+    P_(ukey_lo, int, o_ukey);
     P_(Eu, double, o_Eu); P_(umap, int, o_umap); P_(n_ivoff, int, o_nivoff); P_(n_iv, double, o_niv);
     P_(n_A, double, o_nA); P_(n_nu, double, o_nnu);
     P_(mc_off, int, o_mcoff); P_(mc_n, int, o_mcn); P_(mc_nuc, int, o_mcnuc);
@@ -453,6 +480,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     for (int t : s_type)
         if (t == SURF_PZ) W.need_iw = 1;
     W.nunion = (int)Eu.size();
+    W.ukey0 = ukey0;
+    W.nukey = nukey;
     W.nnuc = (int)nucs.size();
     W.acc_size = (int)acc_size;
     W.nrep = nrep;

@@ -657,9 +657,18 @@ __device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
 // Continuous-energy lookup: union-grid binary search, then each nuclide's
 // interval from the precomputed map (equal to that nuclide's own largest
 // E_j <= E); sigma = sigma_j + f (sigma_{j+1} - sigma_j), f = (E - E_j)(1/dE_j).
+// The search starts from the bracket of E's bucket: buckets are keyed by the
+// top bits of E's bit pattern (exponent and 8 fraction bits, monotone in E for
+// E > 0), and bucket b holds the search result at its lower edge, so the
+// result at E lies between the results at its bucket's edges; the loop is the
+// plain one and returns the same index as a search over the whole grid.
 __device__ __forceinline__ int union_index(const World &W, double E)
 {
-    int lo = 0, hi = W.nunion - 1;
+    long long key = (__double_as_longlong(E) >> 44) - W.ukey0;
+    key = key < 0 ? 0 : (key > W.nukey - 1 ? W.nukey - 1 : key);
+    int lo = __ldg(W.ukey_lo + key);
+    int hi = __ldg(W.ukey_lo + key + 1) + 1;
+    if (hi > W.nunion - 1) hi = W.nunion - 1;
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
         if (!lt_mag(E, __ldg(W.Eu + mid))) lo = mid;

@@ -88,6 +88,11 @@ struct World {
     // continuous energy
     int nunion, nnuc;
     const double *Eu;        // union grid
+    // union-grid buckets: key = (bits of E >> 44) - ukey0 clamped to [0, nukey);
+    // ukey_lo[b] = search result at the lower edge of bucket b (nukey + 1 entries)
+    long long ukey0;
+    int nukey;
+    const int *ukey_lo;
     const int *umap;         // [nuc * nunion + k]: nuclide interval of union interval k
     const int *n_ivoff;      // first interval of each nuclide
     const double *n_iv;      // 8 doubles per interval: E, 1/dE, s, ds, c, dc, f, df
