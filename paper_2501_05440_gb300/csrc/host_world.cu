@@ -317,6 +317,52 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
         std::vector<int> fill(nuniv, 0);
         for (size_t c = 0; c < c_univ.size(); c++) u_cells[u_off[c_univ[c]] + fill[c_univ[c]]++] = (int)c;
     }
+    // Edge cell of each universe: the cell holding every point of a lattice
+    // element's boundary, when that can be proven: all of the universe's
+    // surfaces are z-cylinders or spheres strictly inside the element of every
+    // lattice using it (margin 1e-6 pitch), so f > 0 on the boundary, every
+    // half-space there has sense +1 and the first cell (definition order) whose
+    // half-spaces are all + is what the full search returns.  -1 otherwise.
+    std::vector<int> u_edge(nuniv, -1);
+    {
+        std::vector<double> upitch(nuniv, 0.0);   // smallest pitch of a lattice using U
+        for (size_t L = 0; L < l_pitch.size(); L++) {
+            int b = l_uoff[L], e = b + l_nx[L] * l_ny[L];
+            for (int k = b; k < e; k++) {
+                int U = l_univ[k];
+                if (upitch[U] == 0.0 || l_pitch[L] < upitch[U]) upitch[U] = l_pitch[L];
+            }
+        }
+        for (int U = 0; U < nuniv; U++) {
+            if (upitch[U] <= 0.0) continue;
+            double half = 0.5 * upitch[U] * (1.0 - 1e-6);
+            bool ok = true;
+            for (int k = u_off[U]; k < u_off[U + 1] && ok; k++) {
+                int c = u_cells[k];
+                for (int h = 0; h < c_nhs[c] && ok; h++) {
+                    int sid = hs_surf[c_off[c] + h];
+                    const double *cf = &s_coef[4 * sid];
+                    if (s_type[sid] == SURF_CYLZ)
+                        ok = std::fabs(cf[0]) + cf[2] < half && std::fabs(cf[1]) + cf[2] < half;
+                    else if (s_type[sid] == SURF_SPHERE)
+                        ok = std::fabs(cf[0]) + cf[3] < half && std::fabs(cf[1]) + cf[3] < half;
+                    else
+                        ok = false;
+                }
+            }
+            if (!ok) continue;
+            for (int k = u_off[U]; k < u_off[U + 1]; k++) {
+                int c = u_cells[k];
+                bool all_plus = true;
+                for (int h = 0; h < c_nhs[c]; h++)
+                    if (hs_sense[c_off[c] + h] != 1) all_plus = false;
+                if (all_plus) {
+                    u_edge[U] = c;
+                    break;
+                }
+            }
+        }
+    }
     // candidates across each half-space: cells of the same universe bounded by
     // the same surface with the opposite sense, in definition order
     std::map<std::tuple<int, int, int>, std::vector<int>> bysurf;
@@ -406,7 +452,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     size_t o_cuniv = S.put(c_univ), o_coff = S.put(c_off), o_cnhs = S.put(c_nhs),
            o_cfillk = S.put(c_fillk), o_cfill = S.put(c_fill);
     size_t o_hssurf = S.put(hs_surf), o_hssense = S.put(hs_sense), o_hscoff = S.put(hs_coff),
-           o_hscand = S.put(hs_cand), o_uoff = S.put(u_off), o_ucells = S.put(u_cells);
+           o_hscand = S.put(hs_cand), o_uoff = S.put(u_off), o_ucells = S.put(u_cells),
+           o_uedge = S.put(u_edge);
     size_t o_lx0 = S.put(l_x0), o_ly0 = S.put(l_y0), o_lp = S.put(l_pitch), o_lnx = S.put(l_nx),
            o_lny = S.put(l_ny), o_luoff = S.put(l_uoff), o_luniv = S.put(l_univ),
            o_lwoff = S.put(l_woff), o_lwall = S.put(l_wall), o_lctr = S.put(l_ctr);
@@ -447,7 +494,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(c_univ, int, o_cuniv); P_(c_off, int, o_coff); P_(c_nhs, int, o_cnhs);
     P_(c_fillk, int, o_cfillk); P_(c_fill, int, o_cfill);
     P_(hs_surf, int, o_hssurf); P_(hs_sense, int, o_hssense); P_(hs_coff, int, o_hscoff);
-    P_(hs_cand, int, o_hscand); P_(u_off, int, o_uoff); P_(u_cells, int, o_ucells);
+    P_(hs_cand, int, o_hscand); P_(u_off, int, o_uoff); P_(u_cells, int, o_ucells); P_(u_edge, int, o_uedge);
     P_(l_x0, double, o_lx0); P_(l_y0, double, o_ly0); P_(l_pitch, double, o_lp);
     P_(l_nx, int, o_lnx); P_(l_ny, int, o_lny); P_(l_uoff, int, o_luoff); P_(l_univ, int, o_luniv);
     P_(l_woff, int, o_lwoff); P_(l_wall, double, o_lwall); P_(l_ctr, double, o_lctr);

@@ -519,7 +519,9 @@ __device__ __forceinline__ void lattice_index(const World &W, int L, double x, d
 }
 
 // Below the root cell: lattice element universe cell and material.
-__device__ __forceinline__ bool descend(const World &W, PS &p, int hs_forced)
+// `wall`: the particle has just stepped across a lattice wall, so it lies on the
+// new element's boundary, where the universe's edge cell (if proven) holds it.
+__device__ __forceinline__ bool descend(const World &W, PS &p, int hs_forced, bool wall = false)
 {
     if (__ldg(W.c_fillk + p.cell) == FILL_LAT) {
         int L = __ldg(W.c_fill + p.cell);
@@ -527,7 +529,9 @@ __device__ __forceinline__ bool descend(const World &W, PS &p, int hs_forced)
         local_xy(W, L, p.ix, p.iy, p.x, p.y, xl, yl);
         int U = __ldg(W.l_univ + __ldg(W.l_uoff + L) + p.ix + __ldg(W.l_nx + L) * p.iy);
         int uc;
-        if (hs_forced >= 0) uc = relocate(W, U, hs_forced, xl, yl, p.z, p.u, p.v, p.w);
+        int edge = wall ? __ldg(W.u_edge + U) : -1;
+        if (edge >= 0) uc = edge;
+        else if (hs_forced >= 0) uc = relocate(W, U, hs_forced, xl, yl, p.z, p.u, p.v, p.w);
         else uc = locate_univ(W, U, xl, yl, p.z, p.u, p.v, p.w, -1, 0);
         if (uc < 0) return false;
         p.ucell = uc;
@@ -648,7 +652,7 @@ __device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
     if (kind == B_LATX || kind == B_LATY) {
         if (kind == B_LATX) p.ix += is_pos(p.u) ? 1 : -1;
         else p.iy += is_pos(p.v) ? 1 : -1;
-        return descend(W, p, -1) ? 0 : -1;
+        return descend(W, p, -1, true) ? 0 : -1;
     }
     return descend(W, p, which) ? 0 : -1;
 }
