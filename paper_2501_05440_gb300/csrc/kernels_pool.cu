@@ -7,8 +7,10 @@
 // slots that need it, collisions ordered by material, so that consecutive
 // threads -- whole warps -- run the same event on the same kind of data.  The
 // grid stays resident for the whole cycle; no particle state goes through HBM
-// between events.  Results do not depend on which thread runs which slot:
-// every history draws from its own random stream.
+// between events.  When no history is left to start and a block holds at most
+// a warp's worth of particles, each runs to its end in registers.  Results do
+// not depend on which thread runs which slot: every history draws from its own
+// random stream.
 #include "kernels.h"
 #include "steps.cuh"
 
@@ -203,6 +205,31 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
             return q.fate[i] == FATE_ALIVE ? 1 + (q.mat[i] & 31) : -1;
         });
         if (n_adv == 0 && s_exhausted) break;
+        if (s_exhausted && n_adv <= 32) {
+            // the block's last few histories (no more to start, one warp's worth):
+            // each runs to its end in a thread of warp 0, with no block barrier,
+            // list building or shared-memory round trip between its events
+            if ((int)threadIdx.x < n_adv) {
+                int i = q.list[threadIdx.x];
+                PS p;
+                pool_load<TIME>(q, i, p);
+                const ProblemDev &Pd = W.prob[p.prob];
+                const int slot = q.gslot[i];
+                double kt = q.kt[i], kc = q.kc[i];
+                for (;;) {
+                    int kind, which, uk = 0;
+                    int ev = step_advance<false, TIME>(W, Pd, p, slot, R, rep, kind, which, uk, kt);
+                    if (ev == EV_CROSS) ev = step_cross(W, p, kind, which);
+                    else if (ev == EV_COLLIDE)
+                        ev = step_collide<false, TIME>(W, Pd, p, slot, Bdst, R, uk, kc);
+                    if (ev == EV_DEAD) break;
+                }
+                q.kt[i] = kt;
+                q.kc[i] = kc;
+                retire(q, G, i, p);
+            }
+            break;
+        }
         for (int k = threadIdx.x; k < n_adv; k += T) {
             int i = q.list[k];
             PS p;
