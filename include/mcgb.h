@@ -219,6 +219,37 @@ int mcgb_get_cycle_times(mcgb_ctx *ctx, int n_cycles, double *transport_ms, doub
 int mcgb_run_fixed_source(mcgb_ctx *ctx, int64_t n, int batches, uint64_t seed);
 
 /* --------------------------------------------------------------------------- */
+/* sharded power iteration (one rank of a multi-GPU run; Sec. 1 runs MC/DC     */
+/* with MPI domain replication, here every cycle's histories are partitioned)  */
+/* A fission site as exchanged between ranks: position, time, cell path,
+ * material, child index and the global source index of its parent. */
+typedef struct {
+    double x, y, z, t;
+    int32_t cell, ix, iy, ucell, mat, child;
+    int64_t parent;
+} mcgb_site;
+/* This context transports source indices [j0, j0 + n) of every cycle of an
+ * N-history k-eigenvalue power iteration (random streams cycle 2^32 + j as in
+ * a single-device run).  The caller exchanges, after every cycle, the k sums,
+ * tally sums and ordered banks of all ranks: concatenated in rank order the
+ * banks are the global (parent, child)-ordered bank, from which every rank
+ * resamples its own sources (site of source j: floor((j + xi) M / N), xi from
+ * mcgb_cycle_xi).  Fails for time-dependent problems. */
+int mcgb_shard_begin(mcgb_ctx *ctx, int64_t N, int64_t j0, int64_t n, uint64_t seed);
+/* Transport this rank's n histories of `cycle`: cycle 0 samples the source;
+ * later cycles are born at src[0..n) (required).  ksum[2] = sums over the
+ * rank's histories of the track-length and collision k estimators (divide the
+ * all-rank sums by N); *m = sites banked by the rank. */
+int mcgb_shard_cycle(mcgb_ctx *ctx, int cycle, const mcgb_site *src, double ksum[2], int64_t *m);
+/* The last cycle's sites of this rank in (parent, child) order, cap elements. */
+int mcgb_shard_bank(mcgb_ctx *ctx, size_t cap, mcgb_site *out, size_t *needed);
+/* The last cycle's tally sums of this rank (all tallies concatenated, layout of
+ * mcgb_get_tally, before division by N), cap elements. */
+int mcgb_shard_tally(mcgb_ctx *ctx, size_t cap, double *sums, size_t *needed);
+/* The resampling draw of a cycle (first draw of stream cycle 2^32 + 2^32 - 1). */
+int mcgb_cycle_xi(mcgb_ctx *ctx, int cycle, double *xi);
+
+/* --------------------------------------------------------------------------- */
 /* results                                                                      */
 /* out[6] = k (track length) mean, sd; k (collision) mean, sd; k (analog) mean, sd. */
 int mcgb_get_k(mcgb_ctx *ctx, double out[6]);

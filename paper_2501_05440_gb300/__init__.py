@@ -49,6 +49,13 @@ class Counters(C.Structure):
                                          "event_iterations", "world_bytes", "time_cut")]
 
 
+# one fission site as exchanged between ranks (mcgb_site)
+SITE_DTYPE = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("t", "<f8"), ("cell", "<i4"),
+                       ("ix", "<i4"), ("iy", "<i4"), ("ucell", "<i4"), ("mat", "<i4"),
+                       ("child", "<i4"), ("parent", "<i8")])
+assert SITE_DTYPE.itemsize == 64
+
+
 class Tune(C.Structure):
     _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("pool", C.c_int),
                 ("ms", C.c_double)]
@@ -93,6 +100,9 @@ def lib():
                 "mcgb_set_max_collisions": [P, i32],
                 "mcgb_set_time": [P, d, d], "mcgb_set_inverse_speeds": [P, i32, P],
                 "mcgb_set_free_gas": [P, d, d],
+                "mcgb_shard_begin": [P, i64, i64, i64, u64], "mcgb_shard_cycle": [P, i32, P, P, P],
+                "mcgb_shard_bank": [P, sz, P, P], "mcgb_shard_tally": [P, sz, P, P],
+                "mcgb_cycle_xi": [P, i32, P],
                 "mcgb_set_tally_time_bins": [P, i32, i32, P],
                 "mcgb_run_eigenvalue": [P, i64, i32, i32, u64],
                 "mcgb_run_fixed_source": [P, i64, i32, u64],
@@ -238,6 +248,41 @@ class Context:
 
     def set_max_collisions(self, m):
         _chk(self.L.mcgb_set_max_collisions(self.h, m))
+
+    # sharded power iteration (see paper_2501_05440_gb300.sharded)
+    def shard_begin(self, N, j0, n, seed):
+        _chk(self.L.mcgb_shard_begin(self.h, int(N), int(j0), int(n), int(seed)))
+
+    def shard_cycle(self, cycle, sources=None):
+        """Transport this rank's histories of `cycle`; returns (k sums[2], sites banked)."""
+        ks = np.zeros(2)
+        m = C.c_int64()
+        src = None
+        if sources is not None:
+            src = np.ascontiguousarray(sources, dtype=SITE_DTYPE)
+            src = src.ctypes.data_as(C.c_void_p)
+        _chk(self.L.mcgb_shard_cycle(self.h, int(cycle), src, _p(ks), C.byref(m)))
+        return ks, m.value
+
+    def shard_bank(self):
+        need = C.c_size_t()
+        self.L.mcgb_shard_bank(self.h, 0, None, C.byref(need))
+        out = np.zeros(need.value, dtype=SITE_DTYPE)
+        _chk(self.L.mcgb_shard_bank(self.h, need.value, out.ctypes.data_as(C.c_void_p),
+                                    C.byref(need)))
+        return out
+
+    def shard_tally(self):
+        need = C.c_size_t()
+        self.L.mcgb_shard_tally(self.h, 0, None, C.byref(need))
+        out = np.zeros(need.value)
+        _chk(self.L.mcgb_shard_tally(self.h, need.value, _p(out), C.byref(need)))
+        return out
+
+    def cycle_xi(self, cycle):
+        x = C.c_double()
+        _chk(self.L.mcgb_cycle_xi(self.h, int(cycle), C.byref(x)))
+        return x.value
 
     def set_free_gas(self, kT, cut=0.0):
         _chk(self.L.mcgb_set_free_gas(self.h, float(kT), float(cut)))

@@ -143,6 +143,12 @@ struct mcgb_ctx {
     int64_t grad_n = 0;
     int grad_cell = -1;
     bool grad_ready = false;
+    // one rank's slice of a sharded power iteration
+    struct {
+        bool on = false;
+        int64_t N = 0, j0 = 0, n = 0, M = 0;
+        std::vector<double> tally;   // last cycle's tally sums, replicas reduced
+    } shard;
 };
 
 struct mcgb_batch {
@@ -1224,6 +1230,166 @@ int mcgb_get_tally(mcgb_ctx *ctx, int tally, double *mean, double *sd, size_t ca
     if (cap < n) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
     if (mean) std::memcpy(mean, ctx->t_mean[tally].data(), n * sizeof(double));
     if (sd) std::memcpy(sd, ctx->t_sd[tally].data(), n * sizeof(double));
+    return MCGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sharded power iteration: this context transports source indices
+// [j0, j0 + n) of every cycle of an N-history power iteration.  Stream ids stay
+// global (cycle 2^32 + j): the problem's first slot is given the global index
+// j0 through its generation base.  Bank order, resampling and statistics are
+// the caller's exchange step (the concatenation of the ranks' ordered banks in
+// rank order is the global (parent, child) order).
+int mcgb_shard_begin(mcgb_ctx *c, int64_t N, int64_t j0, int64_t n, uint64_t seed)
+{
+    if (!c) return fail(MCGB_E_INVALID_ARG, "null context");
+    if (N <= 0 || N > (int64_t)1 << 30 || j0 < 0 || n <= 0 || j0 + n > N)
+        return fail(MCGB_E_INVALID_ARG, "bad shard");
+    if (c->def.time_on) return fail(MCGB_E_INVALID_ARG, "time dependence is for fixed-source runs");
+    CK(cudaSetDevice(c->device));
+    c->eig.on = false;
+    c->shard.on = false;
+    CKR(build_single(c, n, 1, seed));
+    double bf = c->opts.bank_factor > 0 ? c->opts.bank_factor : 3.0;
+    int64_t cap_b = (int64_t)(bf * (double)n) + 1024;
+    CKR(prepare_buffers(c, std::max(n, cap_b), cap_b));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const World &W = c->world->W;
+    CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)W.acc_size * W.nrep, st));
+    CK(cudaMemsetAsync(r.cnt, 0, sizeof(unsigned long long) * 8, st));
+    CK(cudaMemsetAsync(r.err, 0, sizeof(int), st));
+    int64_t base[2] = {-j0, n - j0};
+    CK(cudaMemcpyAsync(r.gen_base[0], base, sizeof base, cudaMemcpyHostToDevice, st));
+    std::vector<int> iota(n);
+    for (int64_t k = 0; k < n; k++) iota[k] = (int)k;
+    CK(cudaMemcpyAsync(r.src_idx, iota.data(), 4 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    c->counters = mcgb_counters{};
+    c->counters.world_bytes = (int64_t)c->world->bytes;
+    c->launches = 0;
+    c->shard.on = true;
+    c->shard.N = N;
+    c->shard.j0 = j0;
+    c->shard.n = n;
+    c->shard.M = 0;
+    return MCGB_OK;
+}
+
+int mcgb_shard_cycle(mcgb_ctx *c, int cycle, const mcgb_site *src, double ksum[2], int64_t *m)
+{
+    if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
+    if (cycle < 0 || cycle > 4095 || (cycle > 0 && !src) || !ksum || !m)
+        return fail(MCGB_E_INVALID_ARG, "bad shard cycle");
+    CK(cudaSetDevice(c->device));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const World &W = c->world->W;
+    const int64_t n = c->shard.n;
+    Bank &Bs = r.bank[0], &Bd = r.bank[1];
+    if (src) {
+        std::vector<double> x(n), y(n), z(n), t(n);
+        std::vector<int> cell(n), ix(n), iy(n), ucell(n), mat(n);
+        for (int64_t k = 0; k < n; k++) {
+            x[k] = src[k].x; y[k] = src[k].y; z[k] = src[k].z; t[k] = src[k].t;
+            cell[k] = src[k].cell; ix[k] = src[k].ix; iy[k] = src[k].iy;
+            ucell[k] = src[k].ucell; mat[k] = src[k].mat;
+        }
+        CK(cudaMemcpyAsync(Bs.x, x.data(), 8 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Bs.y, y.data(), 8 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Bs.z, z.data(), 8 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Bs.t, t.data(), 8 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Bs.cell, cell.data(), 4 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Bs.ix, ix.data(), 4 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Bs.iy, iy.data(), 4 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Bs.ucell, ucell.data(), 4 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Bs.mat, mat.data(), 4 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));   // the host vectors go out of scope
+    }
+    CK(cudaMemsetAsync(r.bank_n, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(r.kout, 0, sizeof(double) * 2, st));
+    RunBufs R = run_bufs(c, nullptr, -1, 0);
+    CKR(transport_generation(c, R, cycle, n, r.gen_base[0], src ? r.src_idx : nullptr, 1, Bs, Bd));
+    launch_reduce_gen(r.P, n, nullptr, r.kout, r.cnt, st);
+    scan_exclusive(r.P.nfis, r.off, n, r.M, r.scratch, st);
+    launch_perm(Bd, r.off, r.M, r.perm, c->sms * 4, st);
+    c->shard.tally.assign((size_t)std::max(W.acc_size, 0), 0.0);
+    if (W.acc_size > 0) {
+        launch_acc_reduce(r.tacc, W.acc_size, W.nrep, r.tsum, st);
+        CK(cudaMemcpyAsync(c->shard.tally.data(), r.tsum, sizeof(double) * W.acc_size,
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)W.acc_size * W.nrep, st));
+    }
+    c->launches += 5;
+    CK(cudaMemcpyAsync(ksum, r.kout, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    int64_t M;
+    int err;
+    CKR(read_flags(c, M, err));
+    if (err & ERR_BANK_OVERFLOW)
+        return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow in cycle " + std::to_string(cycle) +
+                                              " (raise opts.bank_factor)");
+    if (err & ERR_SOURCE) return fail(MCGB_E_STATE, "source sampling failed");
+    c->shard.M = M;
+    *m = M;
+    c->counters.histories += n;
+    c->counters.generations += 1;
+    CKR(fetch_counters(c));
+    return MCGB_OK;
+}
+
+int mcgb_shard_bank(mcgb_ctx *c, size_t cap, mcgb_site *out, size_t *needed)
+{
+    if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
+    const int64_t M = c->shard.M;
+    if (needed) *needed = (size_t)M;
+    if (cap < (size_t)M) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    if (M == 0) return MCGB_OK;
+    if (!out) return fail(MCGB_E_INVALID_ARG, "null output");
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const Bank &B = r.bank[1];
+    std::vector<int> perm(M), par(M), ch(M), cell(M), ix(M), iy(M), ucell(M), mat(M);
+    std::vector<double> x(M), y(M), z(M), t(M);
+    CK(cudaMemcpyAsync(perm.data(), r.perm, 4 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(par.data(), B.parent, 4 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ch.data(), B.child, 4 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(cell.data(), B.cell, 4 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ix.data(), B.ix, 4 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(iy.data(), B.iy, 4 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ucell.data(), B.ucell, 4 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(mat.data(), B.mat, 4 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(x.data(), B.x, 8 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(y.data(), B.y, 8 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(z.data(), B.z, 8 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(t.data(), B.t, 8 * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int64_t k = 0; k < M; k++) {
+        int b = perm[k];
+        mcgb_site &o = out[k];
+        o.x = x[b]; o.y = y[b]; o.z = z[b]; o.t = t[b];
+        o.cell = cell[b]; o.ix = ix[b]; o.iy = iy[b]; o.ucell = ucell[b]; o.mat = mat[b];
+        o.child = ch[b];
+        o.parent = c->shard.j0 + par[b];
+    }
+    return MCGB_OK;
+}
+
+int mcgb_shard_tally(mcgb_ctx *c, size_t cap, double *sums, size_t *needed)
+{
+    if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
+    size_t n = c->shard.tally.size();
+    if (needed) *needed = n;
+    if (cap < n) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    if (n && sums) std::memcpy(sums, c->shard.tally.data(), sizeof(double) * n);
+    return MCGB_OK;
+}
+
+int mcgb_cycle_xi(mcgb_ctx *c, int cycle, double *xi)
+{
+    if (!c || !c->world || c->world->probs.empty() || cycle < 0 || cycle > 4095 || !xi)
+        return fail(MCGB_E_INVALID_ARG, "bad argument (begin a run first)");
+    uint64_t rs = rng_stream(c->world->probs[0].seed, ((uint64_t)cycle << 32) + 0xFFFFFFFFULL);
+    *xi = draw_host(rs);
     return MCGB_OK;
 }
 
