@@ -453,7 +453,9 @@ def run_reference(args):
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * 1e3 / ncyc, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "particles_per_cycle": n, "step": "one power-iteration cycle"},
+           "config": {"workload": WORKLOAD, "particles_per_cycle": N_PER_CYCLE,
+                      "step": "one power-iteration cycle",
+                      "sampled_particles_per_cycle": n},
            "cpu_baseline": {"value": value, "unit": "histories/s", "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0,
