@@ -270,29 +270,41 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
     }
     launch_source(W, r.P, Bsrc, R, gen, total, gen_base, src_idx, eigen, block, st);
     c->launches += 1;
-    int64_t n_act = total;
+    // Host-driven iterations over compacted lists.  The length of list b is kept
+    // on the device in q_n[2 + b]; kernels read it there and their grids cover
+    // the last length the host has seen (lists only shrink within a generation),
+    // so the host reads the length back only every SYNC_EVERY iterations.
+    const int SYNC_EVERY = 16;
+    int64_t bound = total;
     int cur = 0;
     const int *list = nullptr;   // identity for the first iteration
+    const int *n_dev = nullptr;
     int64_t maxit = c->opts.max_iterations > 0 ? c->opts.max_iterations : 10000000;
-    for (int64_t it = 0; n_act > 0; it++) {
+    for (int64_t it = 0;; it++) {
         if (it >= maxit) return fail(MCGB_E_TIMEOUT, "event iteration limit reached");
-        CK(cudaMemsetAsync(r.q_n, 0, 3 * sizeof(int), st));
         int *next = r.list[cur];
+        int *next_n = r.q_n + 2 + cur;
+        CK(cudaMemsetAsync(r.q_n, 0, 2 * sizeof(int), st));
+        CK(cudaMemsetAsync(next_n, 0, sizeof(int), st));
         if (c->opts.mode == MCGB_MODE_SEGMENT) {
-            launch_segment(W, r.P, Bdst, R, list, (int)n_act, next, block, st);
+            launch_segment(W, r.P, Bdst, R, list, (int)bound, n_dev, next, next_n, block, st);
             c->launches += 1;
         } else {
-            launch_advance(W, r.P, R, list, (int)n_act, r.q_cross, r.q_coll, block, st);
-            launch_cross(W, r.P, R, r.q_cross, (int)n_act, next, block, st);
-            launch_collide(W, r.P, Bdst, R, r.q_coll, (int)n_act, next, block, st);
+            launch_advance(W, r.P, R, list, (int)bound, n_dev, r.q_cross, r.q_coll, block, st);
+            launch_cross(W, r.P, R, r.q_cross, (int)bound, next, next_n, block, st);
+            launch_collide(W, r.P, Bdst, R, r.q_coll, (int)bound, next, next_n, block, st);
             c->launches += 3;
         }
-        CK(cudaMemcpyAsync(r.pinned, r.q_n + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        n_act = r.pinned[0];
-        list = next;
-        cur ^= 1;
         c->counters.event_iterations++;
+        list = next;
+        n_dev = next_n;
+        cur ^= 1;
+        if (it % SYNC_EVERY == SYNC_EVERY - 1 || it == 0) {
+            CK(cudaMemcpyAsync(r.pinned, next_n, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            bound = r.pinned[0];
+            if (bound == 0) break;
+        }
     }
     CK(cudaGetLastError());
     return MCGB_OK;

@@ -13,13 +13,15 @@ void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const R
                    int64_t total, const int64_t *gen_base, const int *src_idx, int eigen, int block,
                    cudaStream_t st);
 void launch_advance(const World &W, const Particles &P, const RunBufs &R, const int *list, int n,
-                    int *q_cross, int *q_coll, int block, cudaStream_t st);
+                    const int *n_dev, int *q_cross, int *q_coll, int block, cudaStream_t st);
 void launch_cross(const World &W, const Particles &P, const RunBufs &R, const int *q_cross,
-                  int n_bound, int *next, int block, cudaStream_t st);
+                  int n_bound, int *next, int *next_n, int block, cudaStream_t st);
 void launch_collide(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
-                    const int *q_coll, int n_bound, int *next, int block, cudaStream_t st);
+                    const int *q_coll, int n_bound, int *next, int *next_n, int block,
+                    cudaStream_t st);
 void launch_segment(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
-                    const int *list, int n, int *next, int block, cudaStream_t st);
+                    const int *list, int n, const int *n_dev, int *next, int *next_n, int block,
+                    cudaStream_t st);
 
 // ---- persistent event loop -------------------------------------------------
 struct PersistentArgs {

@@ -79,10 +79,13 @@ __global__ void k_source(World W, Particles P, Bank Bsrc, RunBufs R, int gen, in
     P.kc[j] = 0.0;
 }
 
+// n_dev (when set) holds the list's length on the device; the grid covers a
+// host-known upper bound, so the host need not wait for the count.
 __global__ void __launch_bounds__(256) k_advance(World W, Particles P, RunBufs R, const int *list,
-                                                 int n, int *q_cross, int *q_coll)
+                                                 int n, const int *n_dev, int *q_cross, int *q_coll)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n_dev) n = *n_dev;
     int i = -1, ev = EV_DEAD;
     if (t < n) {
         i = list ? list[t] : t;
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(256) k_advance(World W, Particles P, RunBufs R
 }
 
 __global__ void __launch_bounds__(256) k_cross(World W, Particles P, RunBufs R, const int *q_cross,
-                                               int *next)
+                                               int *next, int *next_n)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int n = R.q_n[0];
@@ -118,11 +121,11 @@ __global__ void __launch_bounds__(256) k_cross(World W, Particles P, RunBufs R, 
         alive = step_cross(W, p, P.bkind[i], P.bwhich[i]) == EV_ADVANCE;
         store_ps(P, i, p);
     }
-    enqueue(alive, i, next, R.q_n + 2);
+    enqueue(alive, i, next, next_n);
 }
 
 __global__ void __launch_bounds__(256) k_collide(World W, Particles P, Bank Bdst, RunBufs R,
-                                                 const int *q_coll, int *next)
+                                                 const int *q_coll, int *next, int *next_n)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int n = R.q_n[1];
@@ -138,16 +141,18 @@ __global__ void __launch_bounds__(256) k_collide(World W, Particles P, Bank Bdst
         store_ps(P, i, p);
         P.kc[i] = kc;
     }
-    enqueue(alive, i, next, R.q_n + 2);
+    enqueue(alive, i, next, next_n);
 }
 
 // Monolithic segment (Sec. 2: every transport operation of one segment in a
 // single kernel, no sorting or grouping of like operations): flight, then the
 // crossing or collision it ends in; survivors go to the other list.
 __global__ void __launch_bounds__(256) k_segment(World W, Particles P, Bank Bdst, RunBufs R,
-                                                 const int *list, int n, int *next)
+                                                 const int *list, int n, const int *n_dev,
+                                                 int *next, int *next_n)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n_dev) n = *n_dev;
     int i = -1;
     bool alive = false;
     if (t < n) {
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(256) k_segment(World W, Particles P, Bank Bdst
             alive = ev == EV_ADVANCE;
         }
     }
-    enqueue(alive, i, next, R.q_n + 2);
+    enqueue(alive, i, next, next_n);
 }
 
 static inline int nblocks(int64_t n, int block) { return (int)((n + block - 1) / block); }
@@ -186,31 +191,33 @@ void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const R
 }
 
 void launch_advance(const World &W, const Particles &P, const RunBufs &R, const int *list, int n,
-                    int *q_cross, int *q_coll, int block, cudaStream_t st)
+                    const int *n_dev, int *q_cross, int *q_coll, int block, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_advance<<<nblocks(n, block), block, 0, st>>>(W, P, R, list, n, q_cross, q_coll);
+    k_advance<<<nblocks(n, block), block, 0, st>>>(W, P, R, list, n, n_dev, q_cross, q_coll);
 }
 
 void launch_cross(const World &W, const Particles &P, const RunBufs &R, const int *q_cross,
-                  int n_bound, int *next, int block, cudaStream_t st)
+                  int n_bound, int *next, int *next_n, int block, cudaStream_t st)
 {
     if (n_bound <= 0) return;
-    k_cross<<<nblocks(n_bound, block), block, 0, st>>>(W, P, R, q_cross, next);
+    k_cross<<<nblocks(n_bound, block), block, 0, st>>>(W, P, R, q_cross, next, next_n);
 }
 
 void launch_collide(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
-                    const int *q_coll, int n_bound, int *next, int block, cudaStream_t st)
+                    const int *q_coll, int n_bound, int *next, int *next_n, int block,
+                    cudaStream_t st)
 {
     if (n_bound <= 0) return;
-    k_collide<<<nblocks(n_bound, block), block, 0, st>>>(W, P, Bdst, R, q_coll, next);
+    k_collide<<<nblocks(n_bound, block), block, 0, st>>>(W, P, Bdst, R, q_coll, next, next_n);
 }
 
 void launch_segment(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
-                    const int *list, int n, int *next, int block, cudaStream_t st)
+                    const int *list, int n, const int *n_dev, int *next, int *next_n, int block,
+                    cudaStream_t st)
 {
     if (n <= 0) return;
-    k_segment<<<nblocks(n, block), block, 0, st>>>(W, P, Bdst, R, list, n, next);
+    k_segment<<<nblocks(n, block), block, 0, st>>>(W, P, Bdst, R, list, n, n_dev, next, next_n);
 }
 
 // ---------------------------------------------------------------------------
