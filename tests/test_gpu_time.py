@@ -129,3 +129,29 @@ def test_ce_time_pin_full_size_sampled(mcgb):
     assert set(np.unique(h["fate"]).tolist()) <= {0, 5}
     cnt = c.get_counters()
     assert cnt["time_cut"] > 0 and cnt["leaks"] == 0 and cnt["lost"] == 0
+
+
+@pytest.mark.parametrize("pool", [0, -1])
+def test_batch_mixing_time_and_static_problems(mcgb, pool):
+    """A batch with a time-dependent problem runs every problem through the
+    time-aware kernels; the static problems must give their standalone (and
+    oracle) results, and the time-dependent one its own."""
+    from oracle import Oracle
+    m = _mat([0.4, 1.0], [[0.1, 0.2], [0.0, 0.6]], [0.0, 0.5], [1.0, 0.0])
+    timed = W.time_pulse_mg(m, [1.0, 0.0], [1e-7, 1e-5], t_cut=2e-4,
+                            t_edges=np.array([0.0, 1e-6, 1e-5, 1e-4, 2e-4]), n=3_000)
+    probs = W.batch_boxes(nproblems=3, nmin=500, nmax=2000)[:2] + [timed]
+    b = mcgb.Batch(pool=pool)
+    ctxs = []
+    for p in probs:
+        c = mcgb.load_problem(mcgb.Context(), p)
+        ctxs.append(c)
+        b.add_problem(c, p["run"]["n"], p["run"]["batches"], p["run"]["seed"])
+    b.run()
+    for i, (c, p) in enumerate(zip(ctxs, probs)):
+        c.run()
+        bm, _ = b.tally(i)
+        cm, _ = c.get_tally()
+        om, _ = Oracle(p).run().tally()
+        assert bm.shape == cm.shape == om.shape, i
+        assert rel_close(bm, cm, SUM_RTOL, 1e-300) and rel_close(bm, om, SUM_RTOL, 1e-300), i
