@@ -359,17 +359,38 @@ def ce_time_leg(m, W, torch, n=10_000_000, sample=20_000):
     return out
 
 
-def cpu_baseline(W, n=200_000):
+def _cpu_model():
+    """The host CPU's model name (lscpu or /proc/cpuinfo), or the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def cpu_baseline(W, n=1_000_000, cycles=5, n1=50_000):
+    """The oracle on this host's cores: `cycles` power-iteration cycles of the
+    headline workload (all cores), and one cycle of n1 particles on one core."""
     import oracle
     cores = os.cpu_count() or 1
-    pb = W.c5g7_like_lattice(seed=1, n=n, inactive=0, active=1)
+    pb = W.c5g7_like_lattice(seed=1, n=n, inactive=1, active=cycles - 1)
     o = oracle.Oracle(pb)
     t0 = time.perf_counter()
     o.run(threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "histories/s", "cores": cores, "kind": "oracle",
-            "sample": f"first power-iteration cycle of {WORKLOAD} at {n} particles (1 cycle), "
-                      f"{dt:.2f} s wall on {cores} threads"}
+    o1 = oracle.Oracle(W.c5g7_like_lattice(seed=1, n=n1, inactive=0, active=1))
+    t1 = time.perf_counter()
+    o1.run(threads=1)
+    dt1 = time.perf_counter() - t1
+    return {"value": n * cycles / dt, "unit": "histories/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cycles} power-iteration cycles of {WORKLOAD} at {n} particles, "
+                      f"{dt:.2f} s wall on {cores} threads",
+            "single_core": n1 / dt1, "single_core_sample": f"1 cycle of {n1} particles",
+            "cpu_model": _cpu_model()}
 
 
 def run_mcgb(args):
@@ -416,7 +437,7 @@ def run_mcgb(args):
                                               m.MODE_SEGMENT)
         out["e2e"] = e2e_leg(m, W, args, max(2, args.steps // 2))
         out["batched"] = batched_leg(m, W, torch)
-        out["grad"] = grad_leg(m, W, torch, 1_000_000)
+        out["grad"] = grad_leg(m, W, torch, 10_000_000)
         out["ce_pin"] = ce_leg(m, W, torch)
         out["ce_time"] = ce_time_leg(m, W, torch)
         out["cpu_baseline"] = cpu_baseline(W)
