@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--pool", type=int, default=0,
                     help="persistent kernel variant (particles per warp/block in shared memory)")
     ap.add_argument("--graphs", type=int, default=0, help="0: cycles as CUDA graphs, -1: launches")
+    ap.add_argument("--mode", default="persistent", choices=["persistent", "event", "segment"],
+                    help="launch form of the headline leg (profiling the other forms)")
     return ap.parse_args()
 
 
@@ -174,7 +176,9 @@ class ClockSampler:
 def headline(m, W, torch, args, rank, pg):
     """Persistent form: K timed cycles after W warm-up cycles."""
     pb = replica_problem(W, args.n, rank)
-    c = m.Context(device=int(os.environ.get("LOCAL_RANK", "0")), mode=m.MODE_PERSISTENT,
+    mode = {"persistent": m.MODE_PERSISTENT, "event": m.MODE_EVENT,
+            "segment": m.MODE_SEGMENT}[args.mode]
+    c = m.Context(device=int(os.environ.get("LOCAL_RANK", "0")), mode=mode,
                   pool=args.pool, graphs=args.graphs)
     c.set_stream(torch.cuda.current_stream().cuda_stream)
     m.load_problem(c, pb)
@@ -410,7 +414,7 @@ def run_mcgb(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles_per_cycle": h["n"], "step": "one power-iteration cycle",
-                   "mode": "persistent", "pool": args.pool, "graphs": args.graphs == 0, "l2": "inputs larger than L2 (particle state and fission "
+                   "mode": args.mode, "pool": args.pool, "graphs": args.graphs == 0, "l2": "inputs larger than L2 (particle state and fission "
                    "banks ~0.5 GB per GPU)", "parallelism": f"replicas x{world}"},
         "events_per_s": h["events_per_cycle"] * world / (ms_max / 1e3 / args.steps),
         "k": h["k"]["k"], "k_sd": h["k"]["k_sd"],
