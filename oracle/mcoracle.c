@@ -354,6 +354,9 @@ typedef struct {
 } MatMG;
 typedef struct { double A, nu; int n; double *E, *s, *c, *f; } Nuclide;
 typedef struct { int n; int *nuc; double *dens; int fissile; } MatCE;
+/* macroscopic total and nu-fission cross sections of a CE material at the
+ * points of its own union grid (the merged grids of its nuclides) */
+typedef struct { int n; double *E, *St, *Sf; } MacroCE;
 typedef struct {
     int kind, accept, ekind, dkind, ne;
     double p[6], beam[3];
@@ -386,6 +389,7 @@ struct orc_ctx {
     Source src;
     int src_set;
     Tally *tally;
+    MacroCE *macro;              /* per CE material, built when a run starts */
     /* free-gas elastic scattering below fg_emax (kT > 0 enables it) */
     double fg_kT, fg_emax;
     /* time dependence: source time, cutoff, 1/v per group, CE speed constant */
@@ -462,6 +466,9 @@ void orc_destroy(orc_ctx *c)
         free(c->nuc[i].E); free(c->nuc[i].s); free(c->nuc[i].c); free(c->nuc[i].f);
     }
     for (int i = 0; i < c->nmc; i++) { free(c->mce[i].nuc); free(c->mce[i].dens); }
+    if (c->macro)
+        for (int i = 0; i < c->nmc; i++) { free(c->macro[i].E); free(c->macro[i].St); free(c->macro[i].Sf); }
+    free(c->macro);
     for (int i = 0; i < c->nt; i++) {
         free(c->tally[i].edges); free(c->tally[i].tedges); free(c->tally[i].tinvw);
     }
@@ -1068,12 +1075,76 @@ static void ce_lookup(const orc_ctx *c, int mat, double E, CEXS *x)
     }
 }
 
+/* Macroscopic cross sections for a flight.  Reading: every nuclide is lin-lin
+ * on each interval of the material's union grid (its own points are union
+ * points), so the sums Sigma_t = sum_i N_i sigma_t,i and nuSigma_f are linear
+ * there too; they are tabulated at the union points (each per-nuclide value as
+ * in ce_lookup, summed in the material's order) and interpolated,
+ * Sigma(E) = S_k + ((E - E_k) (1 / (E_k+1 - E_k))) (S_k+1 - S_k), with k the
+ * largest union index <= n - 2 whose point is <= E (0 if none).  Equal to the
+ * per-nuclide sum in exact arithmetic (and exactly at the union points). */
+static int dbl_cmp(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? -1 : (x > y);
+}
+
+static void build_macro(orc_ctx *c)
+{
+    if (c->macro)
+        for (int i = 0; i < c->nmc; i++) { free(c->macro[i].E); free(c->macro[i].St); free(c->macro[i].Sf); }
+    free(c->macro);
+    c->macro = calloc(c->nmc ? c->nmc : 1, sizeof(MacroCE));
+    for (int m = 0; m < c->nmc; m++) {
+        const MatCE *mc = &c->mce[m];
+        int tot = 0;
+        for (int k = 0; k < mc->n; k++) tot += c->nuc[mc->nuc[k]].n;
+        double *E = malloc(sizeof(double) * (size_t)(tot ? tot : 1));
+        int q = 0;
+        for (int k = 0; k < mc->n; k++) {
+            const Nuclide *u = &c->nuc[mc->nuc[k]];
+            for (int j = 0; j < u->n; j++) E[q++] = u->E[j];
+        }
+        qsort(E, (size_t)tot, sizeof(double), dbl_cmp);
+        int n = 0;
+        for (int k = 0; k < tot; k++)
+            if (n == 0 || E[k] != E[n - 1]) E[n++] = E[k];
+        MacroCE *M = &c->macro[m];
+        M->n = n;
+        M->E = E;
+        M->St = malloc(sizeof(double) * (size_t)(n ? n : 1));
+        M->Sf = malloc(sizeof(double) * (size_t)(n ? n : 1));
+        for (int k = 0; k < n; k++) {
+            CEXS x;
+            ce_lookup(c, m, E[k], &x);
+            M->St[k] = x.sigt;
+            M->Sf[k] = x.nusf;
+        }
+    }
+}
+
+static void macro_xs(const orc_ctx *c, int mat, double E, double *sigt, double *nusf)
+{
+    const MacroCE *M = &c->macro[mat];
+    int lo = 0, hi = M->n - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (M->E[mid] <= E) lo = mid;
+        else hi = mid;
+    }
+    if (M->n < 2) { *sigt = M->St[0]; *nusf = M->Sf[0]; return; }
+    double f = (E - M->E[lo]) * (1.0 / (M->E[lo + 1] - M->E[lo]));
+    *sigt = M->St[lo] + f * (M->St[lo + 1] - M->St[lo]);
+    *nusf = M->Sf[lo] + f * (M->Sf[lo + 1] - M->Sf[lo]);
+}
+
 int orc_ce_lookup(orc_ctx *c, int material, double E, double out[4])
 {
     if (c->ce != 1 || material < 0 || material >= c->nmc) return fail(c, ORC_EINVAL, "bad material");
     CEXS x;
     ce_lookup(c, material, E, &x);
-    out[0] = x.sigt; out[1] = x.nusf;
+    if (!c->macro) build_macro(c);
+    macro_xs(c, material, E, &out[0], &out[1]);
     double ss = 0.0, sf = 0.0;
     for (int k = 0; k < c->mce[material].n; k++) {
         ss = ss + c->mce[material].dens[k] * x.ss[k];
@@ -1171,9 +1242,7 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
         CEXS x;
         const MatMG *m = NULL;
         if (c->ce) {
-            ce_lookup(c, p->mat, p->E, &x);
-            sigt = x.sigt;
-            nusf = x.nusf;
+            macro_xs(c, p->mat, p->E, &sigt, &nusf);
             mfp = sigt > 0.0 ? 1.0 / sigt : INF;
         } else {
             m = &c->mg[p->mat];
@@ -1284,6 +1353,7 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
             }
         } else {
             const MatCE *mc = &c->mce[p->mat];
+            ce_lookup(c, p->mat, p->E, &x);     /* per-nuclide values for the reaction */
             a->kc += nusf / sigt;
             /* nuclide by xi Sigma_t against the running sum of N_i sigma_t,i */
             double target = draw(&p->s) * sigt;
@@ -1398,6 +1468,7 @@ static int prepare(orc_ctx *c)
         if (c->ce && T->nedges < 2) return fail(c, ORC_EINVAL, "CE tally needs energy edges");
     }
     if (c->time_on && !c->ce && !c->invv) return fail(c, ORC_ESTATE, "no inverse speeds");
+    if (c->ce) build_macro(c);
     c->kv = sqrt(2.0 * 1.602176634e-19 / 1.67492749804e-27) * 100.0;
     free_results(c);
     memset(c->counters, 0, sizeof c->counters);
