@@ -329,7 +329,7 @@ def ce_leg(m, W, torch, steps=3):
             "k": c.get_k()["k"]}
 
 
-def ce_time_leg(m, W, torch, n=10_000_000, sample=20_000):
+def ce_time_leg(m, W, torch, n=10_000_000, sample=60_000):
     """The paper's continuous-energy benchmark shape (Sec. 4): infinite pin cell,
     uniform 14 MeV source, time-dependent fixed source with free-gas scattering,
     1e7 source histories; the CPU oracle on a `sample` of source histories."""

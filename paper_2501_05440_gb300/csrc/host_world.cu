@@ -404,6 +404,9 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     // continuous energy: union grid, per-nuclide interval maps and interval data
     std::vector<double> Eu;
     std::vector<int> ukey_lo(2, 0);
+    std::vector<int> cm_off, cm_n, cm_nkey, cm_koff, cm_klo;
+    std::vector<long long> cm_key0;
+    std::vector<double> cm_E, cm_rec;
     long long ukey0 = 0;
     int nukey = 1;
     std::vector<int> umap, n_ivoff;
@@ -456,6 +459,72 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
                 umap[q * nuni + k] = std::min(j, n - 2);
             }
         }
+        // Macroscopic flight cross sections per material, tabulated on the
+        // material's own union grid: at each point the per-nuclide lin-lin
+        // values (interval = largest j <= n-2 with E_j <= E), summed in the
+        // material's order; per interval (E_k, 1/dE_k, St_k, dSt_k, Sf_k, dSf_k)
+        // and a bucket index keyed like the global one.
+        for (size_t m = 0; m < mc_off.size(); m++) {
+            int o = mc_off[m], nn = mc_n[m];
+            std::vector<double> G;
+            for (int q = 0; q < nn; q++) G.insert(G.end(), nucs[mc_nuc[o + q]]->E.begin(), nucs[mc_nuc[o + q]]->E.end());
+            std::sort(G.begin(), G.end());
+            G.erase(std::unique(G.begin(), G.end()), G.end());
+            int n = (int)G.size();
+            std::vector<double> St(n), Sf(n);
+            for (int k = 0; k < n; k++) {
+                double E = G[k], sigt = 0.0, nusf = 0.0;
+                for (int q = 0; q < nn; q++) {
+                    const NucDef &u = *nucs[mc_nuc[o + q]];
+                    int lo = 0, hi = (int)u.E.size() - 1;
+                    while (hi - lo > 1) {
+                        int mid = (lo + hi) / 2;
+                        if (u.E[mid] <= E) lo = mid;
+                        else hi = mid;
+                    }
+                    double f = (E - u.E[lo]) * (1.0 / (u.E[lo + 1] - u.E[lo]));
+                    double ss = u.s[lo] + f * (u.s[lo + 1] - u.s[lo]);
+                    double sc = u.c[lo] + f * (u.c[lo + 1] - u.c[lo]);
+                    double sf = u.f[lo] + f * (u.f[lo + 1] - u.f[lo]);
+                    double st = ss + sc + sf;
+                    sigt = sigt + mc_dens[o + q] * st;
+                    nusf = nusf + mc_dens[o + q] * (u.nu * sf);
+                }
+                St[k] = sigt;
+                Sf[k] = nusf;
+            }
+            cm_off.push_back((int)cm_E.size());
+            cm_n.push_back(n);
+            for (int k = 0; k < n; k++) {
+                cm_E.push_back(G[k]);
+                bool last = k + 1 >= n;
+                cm_rec.push_back(G[k]);
+                cm_rec.push_back(last ? 0.0 : 1.0 / (G[k + 1] - G[k]));
+                cm_rec.push_back(St[k]);
+                cm_rec.push_back(last ? 0.0 : St[k + 1] - St[k]);
+                cm_rec.push_back(Sf[k]);
+                cm_rec.push_back(last ? 0.0 : Sf[k + 1] - Sf[k]);
+            }
+            auto gsearch = [&](double E) {
+                int lo = 0, hi = n - 1;
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (!(E < G[mid])) lo = mid;
+                    else hi = mid;
+                }
+                return lo;
+            };
+            long long g0 = bits(G.front()) >> 44, g1 = bits(G.back()) >> 44;
+            cm_key0.push_back(g0);
+            cm_nkey.push_back((int)(g1 - g0 + 1));
+            cm_koff.push_back((int)cm_klo.size());
+            for (long long b = 0; b <= g1 - g0 + 1; b++) {
+                long long kb = (g0 + b) << 44;
+                double edge;
+                std::memcpy(&edge, &kb, 8);
+                cm_klo.push_back(gsearch(edge));
+            }
+        }
     }
     // log tables
     std::vector<double> logtab(256), rinvtab(256), etab(64);
@@ -486,6 +555,9 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
            o_stot = S.put(g_stot), o_chicdf = S.put(g_chicdf), o_sigs = S.put(gg_sigs),
            o_scdf = S.put(gg_scdf);
     size_t o_ukey = S.put(ukey_lo);
+    size_t o_cmoff = S.put(cm_off), o_cmn = S.put(cm_n), o_cmnkey = S.put(cm_nkey),
+           o_cmkoff = S.put(cm_koff), o_cmklo = S.put(cm_klo), o_cmkey0 = S.put(cm_key0),
+           o_cmE = S.put(cm_E), o_cmrec = S.put(cm_rec);
     size_t o_Eu = S.put(Eu), o_umap = S.put(umap), o_nivoff = S.put(n_ivoff), o_niv = S.put(n_iv),
            o_nA = S.put(n_A), o_nnu = S.put(n_nu);
     size_t o_mcoff = S.put(mc_off), o_mcn = S.put(mc_n), o_mcnuc = S.put(mc_nuc),
@@ -527,6 +599,9 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(g_ps, double, o_ps); P_(g_stot, double, o_stot); P_(g_chicdf, double, o_chicdf);
     P_(gg_sigs, double, o_sigs); P_(gg_scdf, double, o_scdf);
     P_(ukey_lo, int, o_ukey);
+    P_(cm_off, int, o_cmoff); P_(cm_n, int, o_cmn); P_(cm_nkey, int, o_cmnkey);
+    P_(cm_koff, int, o_cmkoff); P_(cm_klo, int, o_cmklo); P_(cm_key0, long long, o_cmkey0);
+    P_(cm_E, double, o_cmE); P_(cm_rec, double, o_cmrec);
     P_(Eu, double, o_Eu); P_(umap, int, o_umap); P_(n_ivoff, int, o_nivoff); P_(n_iv, double, o_niv);
     P_(n_A, double, o_nA); P_(n_nu, double, o_nnu);
     P_(mc_off, int, o_mcoff); P_(mc_n, int, o_mcn); P_(mc_nuc, int, o_mcnuc);

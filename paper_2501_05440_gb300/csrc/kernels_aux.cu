@@ -81,7 +81,7 @@ __global__ void k_ce_lookup(World W, int mat, int64_t n, const double *E, double
     double e = E[i];
     int k = union_index(W, e);
     double sigt, nusf;
-    ce_macro(W, mat, k, e, sigt, nusf);
+    ce_macro(W, mat, e, sigt, nusf);
     int off = W.mc_off[mat], nn = W.mc_n[mat];
     double ss = 0.0, sf = 0.0;
     for (int q = 0; q < nn; q++) {

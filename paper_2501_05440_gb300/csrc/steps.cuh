@@ -30,8 +30,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     }
     double sigt, mfp, nusf;
     if (P.ce) {
-        uk = union_index(W, p.E);
-        ce_macro(W, p.mat, uk, p.E, sigt, nusf);
+        ce_macro(W, p.mat, p.E, sigt, nusf);
         mfp = is_pos(sigt) ? 1.0 / sigt : MCGB_INF;
     } else {
         int go = __ldg(W.m_goff + p.mat) + p.g;
@@ -141,7 +140,8 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         }
     } else {
         double sigt, nusf;
-        ce_macro(W, p.mat, uk, p.E, sigt, nusf);
+        ce_macro(W, p.mat, p.E, sigt, nusf);
+        uk = union_index(W, p.E);   // per-nuclide values for the reaction
         kc = kc + nusf / sigt;
         int off = __ldg(W.mc_off + p.mat), n = __ldg(W.mc_n + p.mat);
         // nuclide: first whose running sum of N_i sigma_t,i reaches xi Sigma_t (the

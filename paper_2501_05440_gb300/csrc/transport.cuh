@@ -703,20 +703,32 @@ __device__ __forceinline__ void ce_micro(const World &W, int nuc, int k, double 
 }
 
 // Macroscopic Sigma_t and nuSigma_f: sums of N_i sigma_i in the material's nuclide order.
-__device__ __forceinline__ void ce_macro(const World &W, int mat, int k, double E, double &sigt,
+// Macroscopic flight cross sections of a CE material: the material's table on
+// its own union grid (sums of the per-nuclide lin-lin values at its points),
+// interpolated, Sigma = S_k + ((E - E_k)(1/dE_k)) dS_k, k from the bracketed
+// search (largest k <= n-2 with E_k <= E, else 0).
+__device__ __forceinline__ void ce_macro(const World &W, int mat, double E, double &sigt,
                                          double &nusf)
 {
-    int off = __ldg(W.mc_off + mat), n = __ldg(W.mc_n + mat);
-    sigt = 0.0;
-    nusf = 0.0;
-    for (int q = 0; q < n; q++) {
-        int nuc = __ldg(W.mc_nuc + off + q);
-        double dens = __ldg(W.mc_dens + off + q);
-        double st, ss, sf;
-        ce_micro(W, nuc, k, E, st, ss, sf);
-        sigt = sigt + dens * st;
-        nusf = nusf + dens * (__ldg(W.n_nu + nuc) * sf);
+    const int off = __ldg(W.cm_off + mat), n = __ldg(W.cm_n + mat);
+    const int nkey = __ldg(W.cm_nkey + mat);
+    long long key = (__double_as_longlong(E) >> 44) - __ldg(W.cm_key0 + mat);
+    key = key < 0 ? 0 : (key > nkey - 1 ? nkey - 1 : key);
+    const int *klo = W.cm_klo + __ldg(W.cm_koff + mat);
+    int lo = __ldg(klo + key);
+    int hi = __ldg(klo + key + 1) + 1;
+    if (hi > n - 1) hi = n - 1;
+    const double *Eg = W.cm_E + off;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (!lt_mag(E, __ldg(Eg + mid))) lo = mid;
+        else hi = mid;
     }
+    const double2 *r = reinterpret_cast<const double2 *>(W.cm_rec + 6 * ((int64_t)off + lo));
+    double2 e_inv = __ldg(r), t = __ldg(r + 1), f = __ldg(r + 2);
+    double fr = (E - e_inv.x) * e_inv.y;
+    sigt = t.x + fr * t.y;
+    nusf = f.x + fr * f.y;
 }
 
 // ---------------------------------------------------------------------------

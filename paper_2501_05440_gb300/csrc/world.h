@@ -95,6 +95,12 @@ struct World {
     long long ukey0;
     int nukey;
     const int *ukey_lo;
+    // macroscopic flight cross sections per CE material on its own union grid:
+    // points cm_E[cm_off[m] + k], records of 6 doubles (E_k, 1/dE_k, St_k, dSt_k,
+    // Sf_k, dSf_k), bucket index cm_klo[cm_koff[m] + b] keyed from cm_key0[m]
+    const int *cm_off, *cm_n, *cm_nkey, *cm_koff, *cm_klo;
+    const long long *cm_key0;
+    const double *cm_E, *cm_rec;
     const int *umap;         // [nuc * nunion + k]: nuclide interval of union interval k
     const int *n_ivoff;      // first interval of each nuclide
     const double *n_iv;      // 8 doubles per interval: E, 1/dE, s, ds, c, dc, f, df
