@@ -1,0 +1,63 @@
+"""Argument and state checks of the time, free-gas and shard calls: bad
+arguments fail with MCGB_E_INVALID_ARG (-1) or MCGB_E_STATE (-2), nothing runs."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcgb():
+    import paper_2501_05440_gb300 as m
+    m.build()
+    return m
+
+
+def _code(fn, *a):
+    import paper_2501_05440_gb300 as m
+    with pytest.raises(m.McgbError) as e:
+        fn(*a)
+    return e.value.code
+
+
+def test_time_and_free_gas_arguments(mcgb):
+    c = mcgb.load_problem(mcgb.Context(), W.pin_cell_mg(n=100, inactive=1, active=1))
+    assert _code(c.set_time, 1e-5, 1e-6) == -1          # t_cut <= t0
+    assert _code(c.set_time, -1.0, 1e-6) == -1          # t0 < 0
+    assert _code(c.set_time, 0.0, float("inf")) == -1
+    assert _code(c.set_inverse_speeds, [1e-6, 1e-6]) == -1   # wrong group count
+    assert _code(c.set_inverse_speeds, [0.0] * 7) == -1
+    assert _code(c.set_tally_time_bins, 0, [0.0]) == -1      # one edge
+    assert _code(c.set_tally_time_bins, 0, [0.0, 1e-6, 1e-6]) == -1
+    assert _code(c.set_tally_time_bins, 0, [-1e-6, 1e-6]) == -1
+    assert _code(c.set_tally_time_bins, 5, [0.0, 1e-6]) == -1     # no such tally
+    assert _code(c.set_free_gas, 0.0) == -1
+    assert _code(c.set_free_gas, 0.0253, -1.0) == -1
+
+
+def test_time_without_speeds_fails_at_run(mcgb):
+    pb = W.diff_slab(n=500, batches=2)
+    c = mcgb.load_problem(mcgb.Context(), pb)
+    c.set_time(0.0, 1e-5)                                # multigroup, no 1/v given
+    assert _code(c.run) in (-1, -2)
+
+
+def test_shard_states_and_arguments(mcgb):
+    pb = W.pin_cell_mg(n=1000, inactive=1, active=1)
+    c = mcgb.load_problem(mcgb.Context(mode=1), pb)
+    assert _code(c.shard_cycle, 0) == -2                 # no shard begun
+    assert _code(c.shard_begin, 1000, 900, 200, 1) == -1  # slice past N
+    assert _code(c.shard_begin, 0, 0, 1, 1) == -1
+    c.shard_begin(1000, 0, 500, 1)
+    assert _code(c.shard_cycle, 1, None) == -1           # later cycles need sources
+    ks, m = c.shard_cycle(0)
+    assert m > 0 and ks[0] > 0
+    bank = c.shard_bank()
+    assert len(bank) == m and np.all(bank["parent"] < 500)
+    assert np.all(np.diff(bank["parent"] * 64 + bank["child"]) > 0)   # (parent, child) order
+    t = W.time_pulse_mg(W.mg_material(np.random.default_rng(1), 2, fissile=False), [1.0, 0.0],
+                        [1e-6, 1e-5], t_cut=1e-5, t_edges=[0.0, 1e-5], n=100)
+    ct = mcgb.load_problem(mcgb.Context(mode=1), t)
+    assert _code(ct.shard_begin, 100, 0, 100, 1) == -1   # time-dependent: fixed source only
