@@ -199,3 +199,21 @@ def test_degenerate_sizes(mcgb):
     pb["tallies"] = []
     c = gpu_run(pb, mode=1)
     assert c.get_k()["k"] > 0
+
+
+def test_full_size_graph_cycles_equal_launches(mcgb):
+    """The bench's launch configuration at full size: cycles replayed as CUDA
+    graphs give the bank sizes, last-cycle histories and bank of cycles
+    launched one by one (which the smaller parity tests pin to the oracle)."""
+    pb = W.c5g7_like_lattice(n=1_000_000, inactive=1, active=2)
+    runs = []
+    for graphs in (0, -1):
+        c = mcgb.load_problem(mcgb.Context(mode=1, record_histories=True, graphs=graphs), pb)
+        c.run()
+        runs.append(c)
+    g, l = runs
+    assert g.get_cycle_k(3)[2].tolist() == l.get_cycle_k(3)[2].tolist()
+    assert_same_histories(g.get_histories(), l.get_histories())
+    bg, bl = g.get_bank(), l.get_bank()
+    assert np.array_equal(bg["parent"], bl["parent"]) and np.array_equal(bg["xyz"], bl["xyz"])
+    assert abs(g.get_k()["k"] - l.get_k()["k"]) <= 1e-12 * abs(l.get_k()["k"])
