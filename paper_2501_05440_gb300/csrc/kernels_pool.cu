@@ -90,19 +90,33 @@ __device__ __forceinline__ void retire(const Pool &q, const Particles &G, int i,
 
 // Bucketed compaction of the pool: slots with key >= 0 go to q.list, grouped
 // by key in increasing order; counts per key in cnt[NBUCKET].  All threads call.
+// The lanes of a warp with equal keys find each other (match), and one of them
+// reserves their places in the bucket with a single shared-memory atomic; each
+// lane keeps its rank for the placing pass after the scan of the bucket counts.
 template <int P, int T, class KeyFn>
 __device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, KeyFn key)
 {
+    static_assert(P % T == 0, "every lane of a warp takes the same number of slots");
+    constexpr int R = P / T;
+    const int lane = threadIdx.x & 31;
+    const unsigned lower = (1u << lane) - 1u;
     if (threadIdx.x < NBUCKET) hist[threadIdx.x] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < P; i += T) {
-        int k = key(i);
-        if (k >= 0) atomicAdd(hist + k, 1);
+    int kr[R], rank[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        int k = key(threadIdx.x + r * T);
+        unsigned m = __match_any_sync(0xffffffffu, k);
+        int first = __ffs(m) - 1;
+        int base = 0;
+        if (k >= 0 && lane == first) base = atomicAdd(hist + k, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, first);
+        kr[r] = k;
+        rank[r] = base + __popc(m & lower);
     }
     __syncthreads();
     if (threadIdx.x < 32) {
         // exclusive scan of the NBUCKET counts by one warp (bucket 32 after the loop)
-        int lane = threadIdx.x;
         int v = hist[lane];
         int x = v;
 #pragma unroll
@@ -120,10 +134,9 @@ __device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, Ke
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < P; i += T) {
-        int k = key(i);
-        if (k >= 0) q.list[atomicAdd(hist + k, 1)] = i;
-    }
+#pragma unroll
+    for (int r = 0; r < R; r++)
+        if (kr[r] >= 0) q.list[hist[kr[r]] + rank[r]] = threadIdx.x + r * T;
     __syncthreads();
     return cnt[NBUCKET];
 }
