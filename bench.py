@@ -48,7 +48,7 @@ FP64_INST_PER_EVENT = 71.4
 STATE_BYTES_PER_EVENT = 120.0
 # DRAM bytes (read + write) of one k_pool launch from the same ncu capture, or None
 # when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 80477952 + 91316224
+TRAFFIC_PER_LAUNCH = 80932096 + 90760448
 
 
 def parse():
