@@ -31,7 +31,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     double sigt, mfp, nusf;
     if (P.ce) {
         ce_macro(W, p.mat, p.E, sigt, nusf);
-        mfp = is_pos(sigt) ? 1.0 / sigt : MCGB_INF;
+        mfp = is_pos(sigt) ? __drcp_rn(sigt) : MCGB_INF;   // correctly rounded 1 / sigt
     } else {
         int go = __ldg(W.m_goff + p.mat) + p.g;
         sigt = __ldg(W.g_sigt + go);
@@ -54,7 +54,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     const double ta = p.t;
     double tb = p.t;
     if (timed) {
-        double iv = P.ce ? 1.0 / (W.kv * sqrt(p.E)) : __ldg(W.g_invv + P.invv_off + p.g);
+        double iv = P.ce ? __drcp_rn(W.kv * sqrt(p.E)) : __ldg(W.g_invv + P.invv_off + p.g);
         double dt = (P.tcut - p.t) / iv;
         if (is_neg(dt)) dt = 0.0;
         if (lt_mag(dt, d)) {

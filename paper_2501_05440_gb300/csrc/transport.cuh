@@ -341,12 +341,13 @@ struct PS {
     int g, cell, ix, iy, ucell, mat, prob, root, nfis, ncoll, ncross, fate;
 };
 
-// 1/w is read only by z-planes; a world without them never computes it
+// 1/w is read only by z-planes; a world without them never computes it.
+// __drcp_rn is the correctly rounded reciprocal, the same value as 1.0 / x.
 __device__ __forceinline__ void set_recip(const World &W, PS &p)
 {
-    p.iu = 1.0 / p.u;
-    p.iv = 1.0 / p.v;
-    if (W.need_iw) p.iw = 1.0 / p.w;
+    p.iu = __drcp_rn(p.u);
+    p.iv = __drcp_rn(p.v);
+    if (W.need_iw) p.iw = __drcp_rn(p.w);
 }
 
 // ---------------------------------------------------------------------------
