@@ -46,6 +46,19 @@ FP64_INST_PER_EVENT = 71.4
 # RNG, event tag; collide or cross read and write direction, group, RNG and
 # cell path (fields counted once per kernel that touches them).
 STATE_BYTES_PER_EVENT = 120.0
+def _hbm_peak():
+    """The measured copy bandwidth of the GB300s (GB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6777.0
+
+
+HBM_PEAK_GBS = _hbm_peak()
+# DRAM bytes (read + write) of the first k_advance launch of a cycle (1e6
+# particles) from an ncu capture, or None when the kernel has changed since.
+ADVANCE_TRAFFIC_PER_LAUNCH = None
 # DRAM bytes (read + write) of one k_pool launch from the same ncu capture, or None
 # when the kernel has changed since the counters were taken.
 TRAFFIC_PER_LAUNCH = 80932096 + 90760448
@@ -230,10 +243,26 @@ def plain_leg(m, W, torch, args, steps, mode=None):
     ms = e0.elapsed_time(e1)
     c.eigen_finish()
     cnt = c.get_counters()
-    return {"value": args.n * steps / (ms / 1e3), "unit": "histories/s",
-            "mode": "segment" if mode == m.MODE_SEGMENT else "event",
-            "ms_per_step": ms / steps, "steps": steps,
-            "event_iterations_per_cycle": cnt["event_iterations"] / (steps + 1)}
+    out = {"value": args.n * steps / (ms / 1e3), "unit": "histories/s",
+           "mode": "segment" if mode == m.MODE_SEGMENT else "event",
+           "ms_per_step": ms / steps, "steps": steps,
+           "event_iterations_per_cycle": cnt["event_iterations"] / (steps + 1)}
+    if mode == m.MODE_EVENT:
+        # HBM roofline of the flight kernel: each cycle's first k_advance launch
+        # (the whole cycle's particles, identity list), timed with CUDA events
+        # on the launching stream inside the library
+        et = c.get_event_timing()
+        if et["launches"] > 0 and et["advance_ms"] > 0:
+            gbs = et["bytes_per_particle"] * et["particles"] / (et["advance_ms"] / 1e3) / 1e9
+            out["roofline"] = {"bound": "hbm", "kernel": "k_advance (first flight of a cycle)",
+                               "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                               "frac": gbs / HBM_PEAK_GBS,
+                               "per_unit": f"{et['bytes_per_particle']:.0f} B/particle x "
+                                           f"{et['particles'] / et['launches']:.4g} particles/launch",
+                               "ms_per_launch": et["advance_ms"] / et["launches"],
+                               "traffic": ADVANCE_TRAFFIC_PER_LAUNCH,
+                               "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    return out
 
 
 def e2e_leg(m, W, args, steps):
@@ -431,7 +460,7 @@ def run_mcgb(args):
                        "per_unit": f"{FP64_INST_PER_EVENT} FP64 instr/event x {ev:.4g} events/launch",
                        "peak_kind": "derived: 152 SMs x 2 FP64/clk x 2.07 GHz (recipe's 1.25 TFLOP/s)"}
     hbm = STATE_BYTES_PER_EVENT * ev / t_kernel / 1e9
-    out["hbm_roofline"] = {"achieved": hbm, "peak": 6777.0, "unit": "GB/s", "frac": hbm / 6777.0,
+    out["hbm_roofline"] = {"achieved": hbm, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": hbm / HBM_PEAK_GBS,
                            "basis": f"{STATE_BYTES_PER_EVENT:.0f} B algorithmic state per event "
                                     "(of measured copy bandwidth)"}
     out["transport_ms_per_cycle"] = h["transport_ms"]

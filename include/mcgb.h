@@ -261,6 +261,15 @@ int mcgb_tally_size(mcgb_ctx *ctx, int tally, int *n_bins, int *n_ebins, int *n_
 int mcgb_get_tally(mcgb_ctx *ctx, int tally, double *mean, double *sd, size_t cap,
                    size_t *needed);
 int mcgb_get_counters(mcgb_ctx *ctx, mcgb_counters *out);
+/* One-kernel-per-event mode (Sec. 2's event-based form): device time summed
+ * over the first flight launch of every generation run so far (one k_advance
+ * over the whole generation, identity list), the particles those launches
+ * processed, their number, and the algorithmic state bytes one particle moves
+ * in such a launch (fields loaded and stored, queue entry).  Zeros until an
+ * event-mode generation has run.  Any output pointer may be NULL. */
+int mcgb_get_event_timing(mcgb_ctx *ctx, double *advance_ms, int64_t *particles, int64_t *launches,
+                          double *bytes_per_particle);
+
 /* Per-history records (opts.record_histories): last cycle (eigenvalue) or
  * generation 0 (fixed source).  fate: 0 absorbed, 1 leaked, 2 cut by
  * max_collisions, 3 lost, 4 event cap, 5 reached the time cutoff.  Arrays of

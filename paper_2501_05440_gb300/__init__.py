@@ -108,6 +108,7 @@ def lib():
                 "mcgb_run_fixed_source": [P, i64, i32, u64],
                 "mcgb_eigen_begin": [P, i64, i32, i32, u64], "mcgb_eigen_cycles": [P, i32],
                 "mcgb_eigen_finish": [P], "mcgb_get_cycle_times": [P, i32, P, P],
+                "mcgb_get_event_timing": [P, P, P, P, P],
                 "mcgb_get_k": [P, P], "mcgb_get_cycle_k": [P, i32, P, P, P],
                 "mcgb_tally_size": [P, i32, P, P, P], "mcgb_get_tally": [P, i32, P, P, sz, P],
                 "mcgb_get_counters": [P, P],
@@ -314,6 +315,15 @@ class Context:
         a, b = np.zeros(n), np.zeros(n)
         _chk(self.L.mcgb_get_cycle_times(self.h, n, _p(a), _p(b)))
         return a, b
+
+    def get_event_timing(self):
+        """Event mode: summed device time of each generation's first flight
+        launch (the whole generation in one k_advance), the particles and
+        launches it covers, and the algorithmic state bytes per particle."""
+        ms, n, k, b = C.c_double(), C.c_int64(), C.c_int64(), C.c_double()
+        _chk(self.L.mcgb_get_event_timing(self.h, C.byref(ms), C.byref(n), C.byref(k), C.byref(b)))
+        return {"advance_ms": ms.value, "particles": n.value, "launches": k.value,
+                "bytes_per_particle": b.value}
 
     def run_fixed_source(self, n, batches, seed):
         _chk(self.L.mcgb_run_fixed_source(self.h, n, batches, seed))

@@ -131,6 +131,11 @@ struct mcgb_ctx {
     cudaGraphNode_t graph_mark[2] = {nullptr, nullptr};   // event record after the transport
     cudaEvent_t mark_ev[2] = {nullptr, nullptr};
     int graph_launches = 0;                // kernels in one graph
+    // event mode: device time of each generation's first flight launch (the
+    // whole generation in one k_advance launch over the identity list)
+    cudaEvent_t adv_ev[2] = {nullptr, nullptr};
+    double adv_ms = 0.0;
+    int64_t adv_n = 0, adv_launches = 0;
     cudaStream_t cap_stream = nullptr;
     DevAlloc gmem;                         // cycle counter, draws, bank sizes
     int *cyc_dev = nullptr;
@@ -275,6 +280,10 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
     // the last length the host has seen (lists only shrink within a generation),
     // so the host reads the length back only every SYNC_EVERY iterations.
     const int SYNC_EVERY = 16;
+    if (c->opts.mode == MCGB_MODE_EVENT && !c->adv_ev[0]) {
+        CK(cudaEventCreate(&c->adv_ev[0]));
+        CK(cudaEventCreate(&c->adv_ev[1]));
+    }
     int64_t bound = total;
     int cur = 0;
     const int *list = nullptr;   // identity for the first iteration
@@ -290,7 +299,10 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
             launch_segment(W, r.P, Bdst, R, list, (int)bound, n_dev, next, next_n, block, st);
             c->launches += 1;
         } else {
+            const bool timed = it == 0 && c->adv_ev[0];
+            if (timed) CK(cudaEventRecord(c->adv_ev[0], st));
             launch_advance(W, r.P, R, list, (int)bound, n_dev, r.q_cross, r.q_coll, block, st);
+            if (timed) CK(cudaEventRecord(c->adv_ev[1], st));
             launch_cross(W, r.P, R, r.q_cross, (int)bound, next, next_n, block, st);
             launch_collide(W, r.P, Bdst, R, r.q_coll, (int)bound, next, next_n, block, st);
             c->launches += 3;
@@ -302,6 +314,13 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
         if (it % SYNC_EVERY == SYNC_EVERY - 1 || it == 0) {
             CK(cudaMemcpyAsync(r.pinned, next_n, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
+            if (it == 0 && c->opts.mode == MCGB_MODE_EVENT && c->adv_ev[0]) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, c->adv_ev[0], c->adv_ev[1]));
+                c->adv_ms += ms;
+                c->adv_n += total;
+                c->adv_launches += 1;
+            }
             bound = r.pinned[0];
             if (bound == 0) break;
         }
@@ -906,6 +925,8 @@ int mcgb_destroy(mcgb_ctx *ctx)
     if (!ctx) return MCGB_OK;
     cudaSetDevice(ctx->device);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    for (int q = 0; q < 2; q++)
+        if (ctx->adv_ev[q]) cudaEventDestroy(ctx->adv_ev[q]);
     for (int q = 0; q < 2; q++) {
         if (ctx->graph[q]) cudaGraphExecDestroy(ctx->graph[q]);
         if (ctx->graph_src[q]) cudaGraphDestroy(ctx->graph_src[q]);
@@ -1825,6 +1846,18 @@ int mcgb_batch_autotune(mcgb_batch *b, int budget_ms, mcgb_tune *out)
     b->tuned = best;
     b->has_tune = true;
     if (out) *out = best;
+    return MCGB_OK;
+}
+
+int mcgb_get_event_timing(mcgb_ctx *ctx, double *advance_ms, int64_t *particles,
+                          int64_t *launches, double *bytes_per_particle)
+{
+    if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
+    if (!ctx->world) return fail(MCGB_E_STATE, "no problem has run");
+    if (advance_ms) *advance_ms = ctx->adv_ms;
+    if (particles) *particles = ctx->adv_n;
+    if (launches) *launches = ctx->adv_launches;
+    if (bytes_per_particle) *bytes_per_particle = event_advance_bytes(ctx->world->W);
     return MCGB_OK;
 }
 

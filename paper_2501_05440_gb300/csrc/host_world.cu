@@ -621,6 +621,9 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
         if (P.time_on) W.time_any = 1;
     for (int n : t_ntb)
         if (n > 0) W.time_any = 1;
+    W.ce_any = 0;
+    for (const ProblemDev &P : probs)
+        if (P.ce) W.ce_any = 1;
     W.need_iw = 0;
     for (int t : s_type)
         if (t == SURF_PZ) W.need_iw = 1;

@@ -12,6 +12,9 @@ namespace mcgb {
 void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const RunBufs &R, int gen,
                    int64_t total, const int64_t *gen_base, const int *src_idx, int eigen, int block,
                    cudaStream_t st);
+// Algorithmic state bytes one particle moves in a k_advance launch over the
+// identity list: the fields loaded and stored, the flight's event queue entry.
+double event_advance_bytes(const World &W);
 void launch_advance(const World &W, const Particles &P, const RunBufs &R, const int *list, int n,
                     const int *n_dev, int *q_cross, int *q_coll, int block, cudaStream_t st);
 void launch_cross(const World &W, const Particles &P, const RunBufs &R, const int *q_cross,

@@ -41,6 +41,25 @@ __device__ __forceinline__ void store_ps(const Particles &P, int i, const PS &p)
     P.fate[i] = (signed char)p.fate;
 }
 
+// One kernel per event: each kernel moves only the state fields its step reads
+// and the ones it can change (event_advance_bytes counts those of k_advance).
+// Fields a world does not use are neither read nor written: 1/w without
+// z-planes, E without continuous-energy problems, t without time dependence.
+__device__ __forceinline__ void load_geom(const World &W, const Particles &P, int i, PS &p)
+{
+    p.x = P.x[i]; p.y = P.y[i]; p.z = P.z[i];
+    p.u = P.u[i]; p.v = P.v[i]; p.w = P.w[i];
+    p.iu = P.iu[i]; p.iv = P.iv[i]; p.iw = W.need_iw ? P.iw[i] : 0.0;
+    p.cell = P.cell[i]; p.ix = P.ix[i]; p.iy = P.iy[i]; p.ucell = P.ucell[i]; p.mat = P.mat[i];
+}
+
+__device__ __forceinline__ void store_dir(const World &W, const Particles &P, int i, const PS &p)
+{
+    P.u[i] = p.u; P.v[i] = p.v; P.w[i] = p.w;
+    P.iu[i] = p.iu; P.iv[i] = p.iv;
+    if (W.need_iw) P.iw[i] = p.iw;
+}
+
 __device__ __forceinline__ int find_problem(const int64_t *base, int nprob, int64_t j)
 {
     int lo = 0, hi = nprob;   // base[lo] <= j < base[hi]
@@ -81,7 +100,7 @@ __global__ void k_source(World W, Particles P, Bank Bsrc, RunBufs R, int gen, in
 
 // n_dev (when set) holds the list's length on the device; the grid covers a
 // host-known upper bound, so the host need not wait for the count.
-__global__ void __launch_bounds__(256) k_advance(World W, Particles P, RunBufs R, const int *list,
+__global__ void __launch_bounds__(256, 4) k_advance(World W, Particles P, RunBufs R, const int *list,
                                                  int n, const int *n_dev, int *q_cross, int *q_coll)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -90,13 +109,22 @@ __global__ void __launch_bounds__(256) k_advance(World W, Particles P, RunBufs R
     if (t < n) {
         i = list ? list[t] : t;
         PS p;
-        load_ps(P, i, p);
+        p.fate = P.fate[i];
         if (p.fate == FATE_ALIVE) {
+            load_geom(W, P, i, p);
+            p.E = W.ce_any ? P.E[i] : 0.0;
+            p.t = W.time_any ? P.t[i] : 0.0;
+            p.s = P.s[i];
+            p.g = P.g[i]; p.prob = P.prob[i]; p.root = P.root[i];
+            p.ncoll = P.ncoll[i]; p.ncross = P.ncross[i];
             const ProblemDev &Pd = W.prob[p.prob];
             int kind, which, uk = 0;
             double kt = P.kt[i];
             ev = step_advance(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
-            store_ps(P, i, p);
+            P.x[i] = p.x; P.y[i] = p.y; P.z[i] = p.z;
+            if (W.time_any) P.t[i] = p.t;
+            P.s[i] = p.s;
+            if (p.fate != FATE_ALIVE) P.fate[i] = (signed char)p.fate;
             P.kt[i] = kt;
             P.bkind[i] = (signed char)kind;
             P.bwhich[i] = which;
@@ -117,14 +145,24 @@ __global__ void __launch_bounds__(256) k_cross(World W, Particles P, RunBufs R, 
     if (t < n) {
         i = q_cross[t];
         PS p;
-        load_ps(P, i, p);
+        load_geom(W, P, i, p);
+        p.ncross = P.ncross[i];
+        p.fate = FATE_ALIVE;
+        const double u = p.u, v = p.v, w = p.w;
         alive = step_cross(W, p, P.bkind[i], P.bwhich[i]) == EV_ADVANCE;
-        store_ps(P, i, p);
+        P.ncross[i] = p.ncross;
+        P.cell[i] = p.cell; P.ix[i] = p.ix; P.iy[i] = p.iy; P.ucell[i] = p.ucell; P.mat[i] = p.mat;
+        if (!alive) P.fate[i] = (signed char)p.fate;
+        // a reflection changed the direction
+        if (__double_as_longlong(u) != __double_as_longlong(p.u) ||
+            __double_as_longlong(v) != __double_as_longlong(p.v) ||
+            __double_as_longlong(w) != __double_as_longlong(p.w))
+            store_dir(W, P, i, p);
     }
     enqueue(alive, i, next, next_n);
 }
 
-__global__ void __launch_bounds__(256) k_collide(World W, Particles P, Bank Bdst, RunBufs R,
+__global__ void __launch_bounds__(256, 4) k_collide(World W, Particles P, Bank Bdst, RunBufs R,
                                                  const int *q_coll, int *next, int *next_n)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,11 +172,25 @@ __global__ void __launch_bounds__(256) k_collide(World W, Particles P, Bank Bdst
     if (t < n) {
         i = q_coll[t];
         PS p;
-        load_ps(P, i, p);
+        p.x = P.x[i]; p.y = P.y[i]; p.z = P.z[i];
+        p.u = P.u[i]; p.v = P.v[i]; p.w = P.w[i];
+        p.t = W.time_any ? P.t[i] : 0.0;
+        p.E = W.ce_any ? P.E[i] : 0.0;
+        p.s = P.s[i];
+        p.g = P.g[i]; p.cell = P.cell[i]; p.ix = P.ix[i]; p.iy = P.iy[i]; p.ucell = P.ucell[i];
+        p.mat = P.mat[i]; p.prob = P.prob[i]; p.root = P.root[i];
+        p.nfis = P.nfis[i]; p.ncoll = P.ncoll[i];
+        p.fate = FATE_ALIVE;
         const ProblemDev &Pd = W.prob[p.prob];
         double kc = P.kc[i];
         alive = step_collide(W, Pd, p, i, Bdst, R, P.uk[i], kc) == EV_ADVANCE;
-        store_ps(P, i, p);
+        P.ncoll[i] = p.ncoll;
+        P.nfis[i] = p.nfis;
+        P.g[i] = p.g;
+        if (W.ce_any) P.E[i] = p.E;
+        P.s[i] = p.s;
+        if (alive) store_dir(W, P, i, p);
+        else P.fate[i] = (signed char)p.fate;
         P.kc[i] = kc;
     }
     enqueue(alive, i, next, next_n);
@@ -180,6 +232,19 @@ __global__ void __launch_bounds__(256) k_segment(World W, Particles P, Bank Bdst
 }
 
 static inline int nblocks(int64_t n, int block) { return (int)((n + block - 1) / block); }
+
+double event_advance_bytes(const World &W)
+{
+    const double d = 8.0, i4 = 4.0;
+    // loads: fate; x y z u v w 1/u 1/v [1/w] [E] [t] s; g cell ix iy ucell mat
+    // prob root ncoll ncross; kt
+    double rd = 1.0 + d * (8 + (W.need_iw ? 1 : 0) + (W.ce_any ? 1 : 0) + (W.time_any ? 1 : 0) + 1) +
+                i4 * 10 + d;
+    // stores: x y z [t] s kt; kind (1 B), crossed surface, union index; the
+    // queue entry of the event that follows
+    double wr = d * (3 + (W.time_any ? 1 : 0) + 1 + 1) + 1.0 + i4 * 2 + i4;
+    return rd + wr;
+}
 
 void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const RunBufs &R, int gen,
                    int64_t total, const int64_t *gen_base, const int *src_idx, int eigen, int block,

@@ -125,6 +125,7 @@ struct World {
     const double *g_invv;
     double kv;
     int time_any;
+    int ce_any;             // some problem has continuous-energy physics (particles carry E)
 };
 
 struct Particles {

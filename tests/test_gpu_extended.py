@@ -217,3 +217,19 @@ def test_full_size_graph_cycles_equal_launches(mcgb):
     bg, bl = g.get_bank(), l.get_bank()
     assert np.array_equal(bg["parent"], bl["parent"]) and np.array_equal(bg["xyz"], bl["xyz"])
     assert abs(g.get_k()["k"] - l.get_k()["k"]) <= 1e-12 * abs(l.get_k()["k"])
+
+
+def test_event_mode_flight_timing(mcgb):
+    """Event mode reports the device time of each cycle's first flight launch
+    and the state bytes one particle moves in it (lattice, multigroup, no
+    z-planes, no time: 121 B loaded, 53 B stored); other modes report none."""
+    pb = W.c5g7_like_lattice(n=20_000, inactive=1, active=2)
+    c = mcgb.load_problem(mcgb.Context(mode=0), pb)
+    c.run()
+    t = c.get_event_timing()
+    assert t["launches"] == 3 and t["particles"] == 3 * 20_000
+    assert t["advance_ms"] > 0.0
+    assert t["bytes_per_particle"] == 174.0
+    c = mcgb.load_problem(mcgb.Context(mode=1), pb)
+    c.run()
+    assert c.get_event_timing()["launches"] == 0
