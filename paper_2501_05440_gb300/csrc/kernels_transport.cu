@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256, 4) k_collide(World W, Particles P, Bank B
 // Monolithic segment (Sec. 2: every transport operation of one segment in a
 // single kernel, no sorting or grouping of like operations): flight, then the
 // crossing or collision it ends in; survivors go to the other list.
-__global__ void __launch_bounds__(256) k_segment(World W, Particles P, Bank Bdst, RunBufs R,
+__global__ void __launch_bounds__(256, 3) k_segment(World W, Particles P, Bank Bdst, RunBufs R,
                                                  const int *list, int n, const int *n_dev,
                                                  int *next, int *next_n)
 {
@@ -210,8 +210,17 @@ __global__ void __launch_bounds__(256) k_segment(World W, Particles P, Bank Bdst
     if (t < n) {
         i = list ? list[t] : t;
         PS p;
-        load_ps(P, i, p);
+        p.fate = P.fate[i];
         if (p.fate == FATE_ALIVE) {
+            // the fields the segment's steps read (as in k_advance, plus the
+            // fission-site count a collision continues)
+            load_geom(W, P, i, p);
+            p.E = W.ce_any ? P.E[i] : 0.0;
+            p.t = W.time_any ? P.t[i] : 0.0;
+            p.s = P.s[i];
+            p.g = P.g[i]; p.prob = P.prob[i]; p.root = P.root[i];
+            p.ncoll = P.ncoll[i]; p.ncross = P.ncross[i]; p.nfis = P.nfis[i];
+            const double u = p.u, v = p.v, w = p.w;
             const ProblemDev &Pd = W.prob[p.prob];
             int kind, which, uk = 0;
             double kt = P.kt[i];
@@ -219,12 +228,28 @@ __global__ void __launch_bounds__(256) k_segment(World W, Particles P, Bank Bdst
             P.kt[i] = kt;
             if (ev == EV_CROSS) {
                 ev = step_cross(W, p, kind, which);
+                P.ncross[i] = p.ncross;
+                P.cell[i] = p.cell; P.ix[i] = p.ix; P.iy[i] = p.iy; P.ucell[i] = p.ucell;
+                P.mat[i] = p.mat;
             } else if (ev == EV_COLLIDE) {
                 double kc = P.kc[i];
                 ev = step_collide(W, Pd, p, i, Bdst, R, uk, kc);
                 P.kc[i] = kc;
+                P.ncoll[i] = p.ncoll;
+                P.nfis[i] = p.nfis;
+                P.g[i] = p.g;
+                if (W.ce_any) P.E[i] = p.E;
             }
-            store_ps(P, i, p);
+            // what every segment changes: position, clock, random state; the
+            // direction after a scattering or reflection; the fate at the end
+            P.x[i] = p.x; P.y[i] = p.y; P.z[i] = p.z;
+            if (W.time_any) P.t[i] = p.t;
+            P.s[i] = p.s;
+            if (__double_as_longlong(u) != __double_as_longlong(p.u) ||
+                __double_as_longlong(v) != __double_as_longlong(p.v) ||
+                __double_as_longlong(w) != __double_as_longlong(p.w))
+                store_dir(W, P, i, p);
+            if (p.fate != FATE_ALIVE) P.fate[i] = (signed char)p.fate;
             alive = ev == EV_ADVANCE;
         }
     }
