@@ -774,12 +774,22 @@ __device__ __forceinline__ void score(const World &W, const ProblemDev &P, const
             atomicAdd(acc + base + cell, d);
             continue;
         }
-        // [batch][bin][e][time bin]
+        // [batch][bin][e][time bin].  Only bins with e_k < tb and ta < e_{k+1}
+        // can score (the edges increase): the first is found by bisection,
+        // the loop stops at the first edge >= tb.
         const int64_t idx = base + cell * ntb;
         const double *te = W.t_tedges + __ldg(W.t_toff + t);
         const double *tw = W.t_tinvw + __ldg(W.t_toff + t);
-        for (int k = 0; k < ntb; k++) {
-            double e0 = __ldg(te + k), e1 = __ldg(te + k + 1);
+        int k0 = 0, k1 = ntb;   // first k with ta < e_{k+1}
+        while (k0 < k1) {
+            int mid = (k0 + k1) >> 1;
+            if (lt_time(ta, __ldg(te + mid + 1))) k1 = mid;
+            else k0 = mid + 1;
+        }
+        for (int k = k0; k < ntb; k++) {
+            double e0 = __ldg(te + k);
+            if (!lt_time(e0, tb)) break;
+            double e1 = __ldg(te + k + 1);
             double lo = lt_time(e0, ta) ? ta : e0;   // max(ta, e0)
             double hi = lt_time(tb, e1) ? tb : e1;   // min(tb, e1)
             if (lt_time(lo, hi)) atomicAdd(acc + idx + k, (hi - lo) * __ldg(tw + k));
