@@ -58,10 +58,10 @@ def _hbm_peak():
 HBM_PEAK_GBS = _hbm_peak()
 # DRAM bytes (read + write) of the first k_advance launch of a cycle (1e6
 # particles) from an ncu capture, or None when the kernel has changed since.
-ADVANCE_TRAFFIC_PER_LAUNCH = None
+ADVANCE_TRAFFIC_PER_LAUNCH = 124688128 + 23504640
 # DRAM bytes (read + write) of one k_pool launch from the same ncu capture, or None
 # when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 80932096 + 90760448
+TRAFFIC_PER_LAUNCH = 80293632 + 90151680
 
 
 def parse():
