@@ -367,23 +367,30 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     // least half a pitch outside the lattice's interior walls: from an element
     // that is not on the lattice's outer ring, the next lattice wall towards
     // any of those planes is strictly nearer, so their distances never win.
+    // Each such plane gets the side of the lattice it lies on (1: low x,
+    // 2: high x, 3: low y, 4: high y), and by the same argument only an element
+    // in the outer column or row on that side can reach it first.
     std::vector<int> c_skiproot(c_univ.size(), 0);
+    std::vector<int> hs_side(hs_surf.size(), 0);
     for (size_t c = 0; c < c_univ.size(); c++) {
         if (c_fillk[c] != FILL_LAT) continue;
         int L = c_fill[c];
         double x0 = l_x0[L], y0 = l_y0[L], p = l_pitch[L];
         bool ok = c_nhs[c] > 0;
+        std::vector<int> side(c_nhs[c], 0);
         for (int h = 0; h < c_nhs[c] && ok; h++) {
             int sid = hs_surf[c_off[c] + h];
             double v = s_coef[4 * sid];
-            if (s_type[sid] == SURF_PX)
-                ok = v <= x0 + 0.5 * p || v >= x0 + ((double)l_nx[L] - 0.5) * p;
-            else if (s_type[sid] == SURF_PY)
-                ok = v <= y0 + 0.5 * p || v >= y0 + ((double)l_ny[L] - 0.5) * p;
-            else
-                ok = false;
+            if (s_type[sid] == SURF_PX) {
+                side[h] = v <= x0 + 0.5 * p ? 1 : (v >= x0 + ((double)l_nx[L] - 0.5) * p ? 2 : 0);
+            } else if (s_type[sid] == SURF_PY) {
+                side[h] = v <= y0 + 0.5 * p ? 3 : (v >= y0 + ((double)l_ny[L] - 0.5) * p ? 4 : 0);
+            }
+            ok = side[h] != 0;
         }
         c_skiproot[c] = ok ? 1 : 0;
+        if (ok)
+            for (int h = 0; h < c_nhs[c]; h++) hs_side[c_off[c] + h] = side[h];
     }
     // candidates across each half-space: cells of the same universe bounded by
     // the same surface with the opposite sense, in definition order
@@ -544,7 +551,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
            o_cfillk = S.put(c_fillk), o_cfill = S.put(c_fill);
     size_t o_hssurf = S.put(hs_surf), o_hssense = S.put(hs_sense), o_hscoff = S.put(hs_coff),
            o_hscand = S.put(hs_cand), o_uoff = S.put(u_off), o_ucells = S.put(u_cells),
-           o_uedge = S.put(u_edge), o_cskip = S.put(c_skiproot);
+           o_uedge = S.put(u_edge), o_cskip = S.put(c_skiproot), o_hsside = S.put(hs_side);
     size_t o_lx0 = S.put(l_x0), o_ly0 = S.put(l_y0), o_lp = S.put(l_pitch), o_lnx = S.put(l_nx),
            o_lny = S.put(l_ny), o_luoff = S.put(l_uoff), o_luniv = S.put(l_univ),
            o_lwoff = S.put(l_woff), o_lwall = S.put(l_wall), o_lctr = S.put(l_ctr);
@@ -590,6 +597,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(hs_surf, int, o_hssurf); P_(hs_sense, int, o_hssense); P_(hs_coff, int, o_hscoff);
     P_(hs_cand, int, o_hscand); P_(u_off, int, o_uoff); P_(u_cells, int, o_ucells); P_(u_edge, int, o_uedge);
     P_(c_skiproot, int, o_cskip);
+    P_(hs_side, int, o_hsside);
     P_(l_x0, double, o_lx0); P_(l_y0, double, o_ly0); P_(l_pitch, double, o_lp);
     P_(l_nx, int, o_lnx); P_(l_ny, int, o_lny); P_(l_uoff, int, o_luoff); P_(l_univ, int, o_luniv);
     P_(l_woff, int, o_lwoff); P_(l_wall, double, o_lwall); P_(l_ctr, double, o_lctr);

@@ -564,13 +564,19 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
     kind = B_NONE;
     which = -1;
     int off = __ldg(W.c_off + p.cell), nh = __ldg(W.c_nhs + p.cell);
-    // interior lattice elements: a lattice wall is strictly nearer than every
-    // root plane ahead (proven per cell when the world is built)
-    if (__ldg(W.c_skiproot + p.cell)) {
+    // a root plane on a lattice side is reached first only from the outer
+    // column or row on that side: from elsewhere a lattice wall ahead is
+    // strictly nearer (proven per cell when the world is built)
+    unsigned sides = 0xFu;
+    const bool skip = __ldg(W.c_skiproot + p.cell) != 0;
+    if (skip) {
         int L = __ldg(W.c_fill + p.cell);
-        if (p.ix > 0 && p.iy > 0 && p.ix < __ldg(W.l_nx + L) - 1 && p.iy < __ldg(W.l_ny + L) - 1) nh = 0;
+        sides = (p.ix == 0 ? 1u : 0u) | (p.ix == __ldg(W.l_nx + L) - 1 ? 2u : 0u) |
+                (p.iy == 0 ? 4u : 0u) | (p.iy == __ldg(W.l_ny + L) - 1 ? 8u : 0u);
+        if (!sides) nh = 0;
     }
     for (int h = 0; h < nh; h++) {
+        if (skip && !((sides >> (__ldg(W.hs_side + off + h) - 1)) & 1u)) continue;
         double t = surf_dist(W, __ldg(W.hs_surf + off + h), __ldg(W.hs_sense + off + h), p.x, p.y,
                              p.z, p.u, p.v, p.w, p.iu, p.iv, p.iw);
         if (lt_mag(t, best)) {
