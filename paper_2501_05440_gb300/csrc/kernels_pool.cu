@@ -19,7 +19,8 @@ namespace mcgb {
 namespace {
 
 constexpr int POOL_T = 256;          // threads per block
-constexpr int NBUCKET = 33;          // list buckets: 0 = crossings, 1..32 = material % 32
+constexpr int NBUCKET = 33;          // list buckets (flights: 1 + material % 32; events: 0 lattice
+                                     // steps, 1 surface crossings, 2 + material % 31 collisions)
 constexpr int SLOT_EMPTY = -2;
 
 struct Pool {
@@ -266,12 +267,16 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
             }
         }
         __syncthreads();
-        // ---- crossings (bucket 0), then collisions grouped by material
+        // ---- crossings (lattice steps in bucket 0, surface crossings in 1), then
+        // collisions grouped by material
         int n_ev = build_list<P, T>(q, hist, cnt, [&](int i) {
             if (q.fate[i] != FATE_ALIVE) return -1;
-            return (q.ev[i] & 15) == EV_CROSS ? 0 : 1 + (q.mat[i] & 31);
+            const int e = q.ev[i];
+            if ((e & 15) != EV_CROSS) return 2 + (q.mat[i] % 31);
+            const int kind = e >> 4;   // lattice steps apart from surface crossings
+            return (kind == B_LATX || kind == B_LATY) ? 0 : 1;
         });
-        int n_cross = cnt[0];
+        int n_cross = cnt[0] + cnt[1];
         for (int k = threadIdx.x; k < n_ev; k += T) {
             int i = q.list[k];
             PS p;

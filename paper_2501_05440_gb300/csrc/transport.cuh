@@ -526,14 +526,18 @@ __device__ __forceinline__ bool descend(const World &W, PS &p, int hs_forced, bo
 {
     if (__ldg(W.c_fillk + p.cell) == FILL_LAT) {
         int L = __ldg(W.c_fill + p.cell);
-        double xl, yl;
-        local_xy(W, L, p.ix, p.iy, p.x, p.y, xl, yl);
         int U = __ldg(W.l_univ + __ldg(W.l_uoff + L) + p.ix + __ldg(W.l_nx + L) * p.iy);
         int uc;
         int edge = wall ? __ldg(W.u_edge + U) : -1;
-        if (edge >= 0) uc = edge;
-        else if (hs_forced >= 0) uc = relocate(W, U, hs_forced, xl, yl, p.z, p.u, p.v, p.w);
-        else uc = locate_univ(W, U, xl, yl, p.z, p.u, p.v, p.w, -1, 0);
+        if (edge >= 0) {
+            uc = edge;
+        } else {
+            // element-local coordinates only where a cell test needs them
+            double xl, yl;
+            local_xy(W, L, p.ix, p.iy, p.x, p.y, xl, yl);
+            uc = hs_forced >= 0 ? relocate(W, U, hs_forced, xl, yl, p.z, p.u, p.v, p.w)
+                                : locate_univ(W, U, xl, yl, p.z, p.u, p.v, p.w, -1, 0);
+        }
         if (uc < 0) return false;
         p.ucell = uc;
         p.mat = __ldg(W.c_fill + uc);
