@@ -39,8 +39,8 @@ N_PER_CYCLE = 1_000_000
 FP64_PEAK_GOPS = 152 * 2 * 2.07
 # FP64 thread-instructions per event of the persistent transport kernel on this
 # workload: ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum of one k_pool launch
-# divided by the events of that cycle (1.603e9 / 2.246e7), profiles/k_pool_c5g7_lattice.md.
-FP64_INST_PER_EVENT = 71.4
+# divided by the events of that cycle (1.589e9 / 2.246e7), profiles/k_pool_c5g7_lattice.md.
+FP64_INST_PER_EVENT = 70.7
 # Algorithmic particle-state bytes an event moves in the event-based form:
 # advance reads position/direction/energy/RNG/cell path and writes position,
 # RNG, event tag; collide or cross read and write direction, group, RNG and
@@ -58,10 +58,10 @@ def _hbm_peak():
 HBM_PEAK_GBS = _hbm_peak()
 # DRAM bytes (read + write) of the first k_advance launch of a cycle (1e6
 # particles) from an ncu capture, or None when the kernel has changed since.
-ADVANCE_TRAFFIC_PER_LAUNCH = 124688128 + 23504640
+ADVANCE_TRAFFIC_PER_LAUNCH = 124711168 + 24160000
 # DRAM bytes (read + write) of one k_pool launch from the same ncu capture, or None
 # when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 80293632 + 90151680
+TRAFFIC_PER_LAUNCH = 80781568 + 90735104
 
 
 def parse():
