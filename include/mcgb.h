@@ -303,9 +303,11 @@ int mcgb_batch_destroy(mcgb_batch *b);
  * destroyed afterwards): n source histories in `batches` batches, seed. */
 int mcgb_batch_add_problem(mcgb_batch *b, mcgb_ctx *problem, int64_t n, int batches,
                            uint64_t seed, int *id);
-/* Time candidate launch shapes on a fraction of the work and return the best;
- * results are cached per (problem signature, device) in memory and, when the
- * environment variable MCGB_TUNE_CACHE names a file, on disk. */
+/* Time candidate launch shapes on a fraction of the work, time the three
+ * fastest again on the whole batch, and return the best (the budget bounds
+ * the first stage); results are cached per (problem signature, device) in
+ * memory and, when the environment variable MCGB_TUNE_CACHE names a file, on
+ * disk. */
 int mcgb_batch_autotune(mcgb_batch *b, int budget_ms, mcgb_tune *out);
 /* Run every problem: tune NULL = the cached or default shape. */
 int mcgb_batch_run(mcgb_batch *b, const mcgb_tune *tune);

@@ -1819,28 +1819,46 @@ int mcgb_batch_autotune(mcgb_batch *b, int budget_ms, mcgb_tune *out)
         int occ = std::max(1, persistent_max_blocks_per_sm(blk));
         cand.push_back({blk, occ, -1, 0.0});
     }
-    for (const mcgb_tune &t : cand) {
-        // one warm-up, one timed
-        CKR(batch_run_runs(b, small, &t));
+    // device time of one batch run with tuning t
+    auto timed = [&](const std::vector<ProblemRun> &runs, const mcgb_tune &t, float &ms) -> int {
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, b->engine->stream));
-        int r = batch_run_runs(b, small, &t);
+        int r = batch_run_runs(b, runs, &t);
         CK(cudaEventRecord(e1, b->engine->stream));
         CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        CKR(r);
+        return r;
+    };
+    // stage 1: every candidate on the scaled-down batch (one warm-up, one timed)
+    std::vector<mcgb_tune> tried;
+    for (const mcgb_tune &t : cand) {
+        CKR(batch_run_runs(b, small, &t));
+        float ms = 0.f;
+        CKR(timed(small, t, ms));
+        mcgb_tune tt = t;
+        tt.ms = ms;
+        tried.push_back(tt);
+        double spent = std::chrono::duration<double, std::milli>(
+                           std::chrono::steady_clock::now() - t_start).count();
+        if (budget_ms > 0 && spent > budget_ms) break;
+    }
+    // stage 2: the three fastest again at full size (small runs rank the
+    // launch shapes only roughly), best of those
+    std::sort(tried.begin(), tried.end(),
+              [](const mcgb_tune &a, const mcgb_tune &c2) { return a.ms < c2.ms; });
+    if (tried.size() > 3) tried.resize(3);
+    for (const mcgb_tune &t : tried) {
+        float ms = 0.f;
+        if (scale > 1) CKR(timed(b->runs, t, ms));
+        else ms = (float)t.ms;
         if (ms < best.ms) {
             best = t;
             best.ms = ms;
         }
-        double spent = std::chrono::duration<double, std::milli>(
-                           std::chrono::steady_clock::now() - t_start).count();
-        if (budget_ms > 0 && spent > budget_ms) break;
     }
     tune_cache_store(key, best);
     b->tuned = best;
