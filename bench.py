@@ -62,6 +62,13 @@ ADVANCE_TRAFFIC_PER_LAUNCH = 124711168 + 24160000
 # DRAM bytes (read + write) of one k_pool launch from the same ncu capture, or None
 # when the kernel has changed since the counters were taken.
 TRAFFIC_PER_LAUNCH = 80781568 + 90735104
+# Other counters of the same two captures (profiles/k_pool_c5g7_lattice.md,
+# profiles/event_mode_c5g7_lattice.md): L2 sector hit rate, active lanes per
+# issued instruction / 32, FP64 pipe busy fraction of the elapsed time.
+NCU_K_POOL = {"l2_hit_rate": 0.8612, "warp_exec_efficiency": 20.13 / 32, "fp64_pipe_busy": 0.5309,
+              "source": "profiles/k_pool_c5g7_lattice.md"}
+NCU_K_ADVANCE = {"l2_hit_rate": 0.4985, "fp64_pipe_busy": 0.7760, "dram_throughput": 0.1030,
+                 "source": "profiles/event_mode_c5g7_lattice.md"}
 
 
 def parse():
@@ -260,7 +267,7 @@ def plain_leg(m, W, torch, args, steps, mode=None):
                                "per_unit": f"{et['bytes_per_particle']:.0f} B/particle x "
                                            f"{et['particles'] / et['launches']:.4g} particles/launch",
                                "ms_per_launch": et["advance_ms"] / et["launches"],
-                               "traffic": ADVANCE_TRAFFIC_PER_LAUNCH,
+                               "traffic": ADVANCE_TRAFFIC_PER_LAUNCH, "ncu": NCU_K_ADVANCE,
                                "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     return out
 
@@ -456,7 +463,8 @@ def run_mcgb(args):
     ach = FP64_INST_PER_EVENT * ev / t_kernel / 1e9
     out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GOPS,
                        "unit": "G FP64 thread-instr/s", "frac": ach / FP64_PEAK_GOPS,
-                       "traffic": TRAFFIC_PER_LAUNCH, "kernel": "k_pool (persistent event loop)",
+                       "traffic": TRAFFIC_PER_LAUNCH, "ncu": NCU_K_POOL,
+                       "kernel": "k_pool (persistent event loop)",
                        "per_unit": f"{FP64_INST_PER_EVENT} FP64 instr/event x {ev:.4g} events/launch",
                        "peak_kind": "derived: 152 SMs x 2 FP64/clk x 2.07 GHz (recipe's 1.25 TFLOP/s)"}
     hbm = STATE_BYTES_PER_EVENT * ev / t_kernel / 1e9
