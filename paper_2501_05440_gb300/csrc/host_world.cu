@@ -121,6 +121,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
 {
     std::vector<int> s_type, s_bc;
     std::vector<double> s_coef, s_r2;
+    std::vector<int> s_zc;
     std::vector<int> c_univ, c_off, c_nhs, c_fillk, c_fill, hs_surf, hs_sense;
     std::vector<double> l_x0, l_y0, l_pitch;
     std::vector<int> l_nx, l_ny, l_uoff, l_univ, l_woff;
@@ -161,6 +162,12 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
             double R = pd.s_type[i] == SURF_CYLZ ? pd.s_coef[4 * i + 2]
                      : pd.s_type[i] == SURF_SPHERE ? pd.s_coef[4 * i + 3] : 0.0;
             s_r2.push_back(R * R);
+            // z-cylinder on the axis (centre coordinates +0.0): x - 0.0 == x for
+            // every x, so the distance code skips those subtractions
+            uint64_t c0, c1;
+            std::memcpy(&c0, &pd.s_coef[4 * i], 8);
+            std::memcpy(&c1, &pd.s_coef[4 * i + 1], 8);
+            s_zc.push_back(pd.s_type[i] == SURF_CYLZ && c0 == 0 && c1 == 0 ? 1 : 0);
         }
         int nu = 0;
         for (auto &c : pd.cells) nu = std::max(nu, c.univ + 1);
@@ -546,7 +553,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
 
     Staging S;
     size_t o_prob = S.put(probs);
-    size_t o_stype = S.put(s_type), o_sbc = S.put(s_bc), o_scoef = S.put(s_coef), o_sr2 = S.put(s_r2);
+    size_t o_stype = S.put(s_type), o_sbc = S.put(s_bc), o_scoef = S.put(s_coef), o_sr2 = S.put(s_r2),
+           o_szc = S.put(s_zc);
     size_t o_cuniv = S.put(c_univ), o_coff = S.put(c_off), o_cnhs = S.put(c_nhs),
            o_cfillk = S.put(c_fillk), o_cfill = S.put(c_fill);
     size_t o_hssurf = S.put(hs_surf), o_hssense = S.put(hs_sense), o_hscoff = S.put(hs_coff),
@@ -592,6 +600,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     W.prob = (const ProblemDev *)(b + o_prob);
 #define P_(field, T, off) W.field = (const T *)(b + off)
     P_(s_type, int, o_stype); P_(s_bc, int, o_sbc); P_(s_coef, double, o_scoef); P_(s_r2, double, o_sr2);
+    P_(s_zc, int, o_szc);
     P_(c_univ, int, o_cuniv); P_(c_off, int, o_coff); P_(c_nhs, int, o_cnhs);
     P_(c_fillk, int, o_cfillk); P_(c_fill, int, o_cfill);
     P_(hs_surf, int, o_hssurf); P_(hs_sense, int, o_hssense); P_(hs_coff, int, o_hscoff);

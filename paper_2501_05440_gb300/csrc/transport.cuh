@@ -117,10 +117,16 @@ __device__ __forceinline__ double log_n(const World &W, uint64_t n)
     int lz = __clzll((long long)n);
     int e = 63 - lz;
     uint64_t frac = ((n << lz) << 1) >> 12;
-    double m = __longlong_as_double((long long)(0x3FF0000000000000ULL | frac));
     int j = (int)(frac >> 44);
-    double c = __longlong_as_double((long long)(0x3FF0000000000000ULL | ((uint64_t)j << 44)));
-    double r = (m - c) * __ldg(W.rinvtab + j);
+    // m - c is exact (c <= m < 2c): the low 44 fraction bits times 2^-52,
+    // built from the bits like n_to_xi instead of subtracted on the FP64 pipe
+    uint64_t lo = frac & ((1ULL << 44) - 1);
+    double mc = 0.0;
+    if (lo) {
+        int z = __clzll((long long)lo);
+        mc = __longlong_as_double((long long)(((uint64_t)(1034 - z) << 52) | (((lo << z) << 1) >> 12)));
+    }
+    double r = mc * __ldg(W.rinvtab + j);
     double q = -1.0 / 6.0;
     q = fma(q, r, 1.0 / 5.0);
     q = fma(q, r, -0.25);
@@ -417,7 +423,11 @@ __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, 
     }
     double a, b, cc;
     if (type == SURF_CYLZ) {
-        double dx = x - __ldg(c), dy = y - __ldg(c + 1);
+        double dx = x, dy = y;   // a cylinder on the axis: x - 0.0 is x
+        if (!__ldg(W.s_zc + sid)) {
+            dx = x - __ldg(c);
+            dy = y - __ldg(c + 1);
+        }
         a = fma(u, u, v * v);
         b = fma(dx, u, dy * v);
         cc = fma(dx, dx, dy * dy) - __ldg(W.s_r2 + sid);

@@ -69,6 +69,7 @@ struct World {
     const int *s_type, *s_bc;
     const double *s_coef;   // 4 per surface
     const double *s_r2;     // R*R for quadrics
+    const int *s_zc;        // z-cylinder centred at (+0, +0)
     // cells and half-spaces
     const int *c_univ, *c_off, *c_nhs, *c_fillk, *c_fill;
     const int *hs_surf, *hs_sense;
