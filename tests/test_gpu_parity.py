@@ -187,3 +187,13 @@ def test_box_fixed_source_parity(mcgb, mode, pool, graphs):
 def test_one_collision_and_absorber_parity(mcgb):
     for pb in [W.one_collision_slab(n=5000), W.absorbing_slab_beam(n=5000)]:
         _fixed_parity(mcgb, pb, 0)
+
+
+@pytest.mark.parametrize("mode,pool,graphs", FEW)
+def test_ce_infinite_medium_eigen_parity(mcgb, mode, pool, graphs):
+    E = np.array([W.E_MIN, 1.0, W.E_MAX])
+    nuc = lambda A, sc, cc, sf, nu: {"A": A, "E": E, "sig_s": np.full(3, sc), "sig_c": np.full(3, cc),
+                                     "sig_f": np.full(3, sf), "nu": nu}
+    pb = W.ce_infinite_eigen([nuc(235.0, 4.0, 1.0, 2.0, 2.43), nuc(1.0, 3.0, 0.5, 0.0, 0.0)],
+                             [0.02, 0.04], n=3000, inactive=2, active=3)
+    _eigen_parity(mcgb, pb, mode, pool, graphs)

@@ -24,17 +24,7 @@ def _nuc(A, s, c, f, nu):
 
 
 def _infinite_ce(nucs, dens, n=20_000, inactive=2, active=30, seed=5):
-    half = 1.0
-    pb = W.time_pulse_ce(1.0, 1.0e6, t_cut=1.0, t_edges=[0.0, 1.0], half=half)
-    pb.pop("time")
-    pb["name"] = "ce-infinite-medium-eigen"
-    pb["nuclides"] = nucs
-    pb["materials"] = [{"nuclides": list(range(len(nucs))), "density": list(dens)}]
-    pb["source"] = {"kind": "box", "box": [-half, half, -half, half, -half, half],
-                    "accept": "fissile", "energy": "maxwell", "direction": "iso"}
-    pb["tallies"] = [{"filter": "material", "edges": np.array([W.E_MIN, W.E_MAX])}]
-    pb["run"] = {"mode": "eigen", "n": n, "inactive": inactive, "active": active, "seed": seed}
-    return pb
+    return W.ce_infinite_eigen(nucs, dens, n=n, inactive=inactive, active=active, seed=seed)
 
 
 @pytest.mark.parametrize("A_mod", [1.0, 16.0])

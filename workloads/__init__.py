@@ -550,6 +550,25 @@ def time_pulse_ce(sig_c, E0, t_cut, t_edges, A=1.0, sig_s=0.0, density=0.05, see
     }
 
 
+def ce_infinite_eigen(nuclides, density, n=20_000, inactive=2, active=30, seed=5, half=1.0):
+    """k-eigenvalue in an infinite medium (reflective cube) of one continuous-
+    energy material: `nuclides` (dicts as in ce_pin_cell) at atom densities
+    `density`; fission-spectrum source; one material tally."""
+    surfaces = [_surf("px", [-half], "reflect"), _surf("px", [half], "reflect"),
+                _surf("py", [-half], "reflect"), _surf("py", [half], "reflect"),
+                _surf("pz", [-half], "reflect"), _surf("pz", [half], "reflect")]
+    cells = [_cell(0, [(0, +1), (1, -1), (2, +1), (3, -1), (4, +1), (5, -1)], "material", 0)]
+    return {
+        "name": "ce-infinite-medium-eigen", "G": 0, "surfaces": surfaces, "cells": cells,
+        "lattices": [], "nuclides": list(nuclides),
+        "materials": [{"nuclides": list(range(len(nuclides))), "density": list(density)}],
+        "source": {"kind": "box", "box": [-half, half, -half, half, -half, half],
+                   "accept": "fissile", "energy": "maxwell", "direction": "iso"},
+        "tallies": [{"filter": "material", "edges": np.array([E_MIN, E_MAX])}],
+        "run": _eigen_run(n, inactive, active, seed),
+    }
+
+
 def ce_time_pin(seed=1, n=10_000_000, t_cut=1.0e-5, ntbins=40, npts=50_000, nres=200,
                 batches=20):
     """Stand-in for the paper's continuous-energy benchmark (Sec. 4): the infinite
