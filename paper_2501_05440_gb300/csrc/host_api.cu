@@ -50,25 +50,46 @@ int set_error(int code, const char *msg) { return fail(code, msg); }
     } while (0)
 
 // ---------------------------------------------------------------------------
-// device buffers of a run
+// device buffers of a run: carved from a few large slabs (one cudaMalloc per
+// slab instead of one per array; every array starts on a 256-byte boundary)
 struct DevAlloc {
+    size_t slab = (size_t)1 << 20;   // size of a new slab (at least the request)
     std::vector<void *> ptrs;
+    char *cur = nullptr;
+    size_t left = 0;
     ~DevAlloc() { release(); }
     void release()
     {
         for (void *p : ptrs) cudaFree(p);
         ptrs.clear();
+        cur = nullptr;
+        left = 0;
     }
     template <class T> int get(T *&p, int64_t n)
     {
-        void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
-        if (e != cudaSuccess) {
-            p = nullptr;
-            return fail(MCGB_E_OOM, std::string("device allocation: ") + cudaGetErrorString(e));
+        const size_t bytes = ((size_t)std::max<int64_t>(n, 1) * sizeof(T) + 255) & ~(size_t)255;
+        if (bytes > left) {
+            void *q = nullptr;
+            size_t sz = std::max(bytes, slab);
+            cudaError_t e = cudaMalloc(&q, sz);
+            if (e != cudaSuccess && sz > bytes) {
+                // no room for a whole slab: this and later arrays get their own
+                cudaGetLastError();
+                slab = 0;
+                sz = bytes;
+                e = cudaMalloc(&q, sz);
+            }
+            if (e != cudaSuccess) {
+                p = nullptr;
+                return fail(MCGB_E_OOM, std::string("device allocation: ") + cudaGetErrorString(e));
+            }
+            ptrs.push_back(q);
+            cur = (char *)q;
+            left = sz;
         }
-        ptrs.push_back(q);
-        p = (T *)q;
+        p = (T *)cur;
+        cur += bytes;
+        left -= bytes;
         return MCGB_OK;
     }
 };
@@ -178,6 +199,9 @@ static int prepare_buffers(mcgb_ctx *c, int64_t cap_p, int64_t cap_b)
     cap_b = std::max(cap_b, r.cap_b);
     Particles &P = r.P;
     DevAlloc &m = r.mem;
+    // one slab holds every array below (29 per particle, 13 per bank site in
+    // each of two banks, lists, queues, scan scratch, tallies)
+    m.slab = 8 * (size_t)(40 * cap_p + 28 * cap_b) + 8 * (size_t)std::max(acc, 1) * 3 + ((size_t)16 << 20);
     CKR(m.get(P.x, cap_p)); CKR(m.get(P.y, cap_p)); CKR(m.get(P.z, cap_p));
     CKR(m.get(P.u, cap_p)); CKR(m.get(P.v, cap_p)); CKR(m.get(P.w, cap_p));
     CKR(m.get(P.E, cap_p)); CKR(m.get(P.kt, cap_p)); CKR(m.get(P.kc, cap_p)); CKR(m.get(P.t, cap_p));
