@@ -673,6 +673,8 @@ static int eigen_cycles(mcgb_ctx *c, int k)
         c->launches += 7;
         CK(cudaEventRecord(ev2, st));
         CK(cudaGetLastError());
+        // the later cycles' graphs are captured while the first cycle runs
+        if (cyc == 0 && use_graphs(c) && !c->graph[0] && e.ncyc > 1) CKR(build_cycle_graphs(c));
         int64_t M;
         int err;
         CKR(read_flags(c, M, err));
