@@ -331,6 +331,11 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     // half-space there has sense +1 and the first cell (definition order) whose
     // half-spaces are all + is what the full search returns.  -1 otherwise.
     std::vector<int> u_edge(nuniv, -1);
+    // c_inner: a universe cell inside (sense -1) a cylinder or sphere that lies
+    // strictly inside every lattice element holding the universe (same margin):
+    // a particle there leaves that surface before it can reach a lattice wall or
+    // a root plane beyond it, so those distances never win and are not computed.
+    std::vector<int> c_inner(c_univ.size(), 0);
     {
         std::vector<double> upitch(nuniv, 0.0);   // smallest pitch of a lattice using U
         for (size_t L = 0; L < l_pitch.size(); L++) {
@@ -355,6 +360,17 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
                         ok = std::fabs(cf[0]) + cf[3] < half && std::fabs(cf[1]) + cf[3] < half;
                     else
                         ok = false;
+                }
+            }
+            for (int k = u_off[U]; k < u_off[U + 1]; k++) {
+                int c = u_cells[k];
+                for (int h = 0; h < c_nhs[c]; h++) {
+                    int sid = hs_surf[c_off[c] + h];
+                    const double *cf = &s_coef[4 * sid];
+                    double R = s_type[sid] == SURF_CYLZ ? cf[2] : s_type[sid] == SURF_SPHERE ? cf[3] : -1.0;
+                    if (R >= 0.0 && hs_sense[c_off[c] + h] == -1 && std::fabs(cf[0]) + R < half &&
+                        std::fabs(cf[1]) + R < half)
+                        c_inner[c] = 1;
                 }
             }
             if (!ok) continue;
@@ -559,7 +575,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
            o_cfillk = S.put(c_fillk), o_cfill = S.put(c_fill);
     size_t o_hssurf = S.put(hs_surf), o_hssense = S.put(hs_sense), o_hscoff = S.put(hs_coff),
            o_hscand = S.put(hs_cand), o_uoff = S.put(u_off), o_ucells = S.put(u_cells),
-           o_uedge = S.put(u_edge), o_cskip = S.put(c_skiproot), o_hsside = S.put(hs_side);
+           o_uedge = S.put(u_edge), o_cskip = S.put(c_skiproot), o_hsside = S.put(hs_side),
+           o_cinner = S.put(c_inner);
     size_t o_lx0 = S.put(l_x0), o_ly0 = S.put(l_y0), o_lp = S.put(l_pitch), o_lnx = S.put(l_nx),
            o_lny = S.put(l_ny), o_luoff = S.put(l_uoff), o_luniv = S.put(l_univ),
            o_lwoff = S.put(l_woff), o_lwall = S.put(l_wall), o_lctr = S.put(l_ctr);
@@ -607,6 +624,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(hs_cand, int, o_hscand); P_(u_off, int, o_uoff); P_(u_cells, int, o_ucells); P_(u_edge, int, o_uedge);
     P_(c_skiproot, int, o_cskip);
     P_(hs_side, int, o_hsside);
+    P_(c_inner, int, o_cinner);
     P_(l_x0, double, o_lx0); P_(l_y0, double, o_ly0); P_(l_pitch, double, o_lp);
     P_(l_nx, int, o_lnx); P_(l_ny, int, o_lny); P_(l_uoff, int, o_luoff); P_(l_univ, int, o_luniv);
     P_(l_woff, int, o_lwoff); P_(l_wall, double, o_lwall); P_(l_ctr, double, o_lctr);

@@ -583,7 +583,10 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
     // strictly nearer (proven per cell when the world is built)
     unsigned sides = 0xFu;
     const bool skip = __ldg(W.c_skiproot + p.cell) != 0;
-    if (skip) {
+    // inside a surface strictly inside the element: only that cell's surfaces
+    const bool inner = p.ucell >= 0 && __ldg(W.c_inner + p.ucell) != 0;
+    if (inner) nh = 0;
+    if (skip && !inner) {
         int L = __ldg(W.c_fill + p.cell);
         sides = (p.ix == 0 ? 1u : 0u) | (p.ix == __ldg(W.l_nx + L) - 1 ? 2u : 0u) |
                 (p.iy == 0 ? 4u : 0u) | (p.iy == __ldg(W.l_ny + L) - 1 ? 8u : 0u);
@@ -606,7 +609,7 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
         // chosen first, then t = (wall - x)(1/u)
         const double *xw = W.l_wall + __ldg(W.l_woff + L);
         const double *yw = xw + nx + 1;
-        int wx = is_pos(p.u) ? (p.ix < nx - 1 ? p.ix + 1 : -1) : (is_neg(p.u) && p.ix > 0 ? p.ix : -1);
+        int wx = inner ? -1 : (is_pos(p.u) ? (p.ix < nx - 1 ? p.ix + 1 : -1) : (is_neg(p.u) && p.ix > 0 ? p.ix : -1));
         if (wx >= 0) {
             double t = (__ldg(xw + wx) - p.x) * p.iu;
             if (is_neg(t)) t = 0.0;
@@ -615,7 +618,7 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
                 kind = B_LATX;
             }
         }
-        int wy = is_pos(p.v) ? (p.iy < ny - 1 ? p.iy + 1 : -1) : (is_neg(p.v) && p.iy > 0 ? p.iy : -1);
+        int wy = inner ? -1 : (is_pos(p.v) ? (p.iy < ny - 1 ? p.iy + 1 : -1) : (is_neg(p.v) && p.iy > 0 ? p.iy : -1));
         if (wy >= 0) {
             double t = (__ldg(yw + wy) - p.y) * p.iv;
             if (is_neg(t)) t = 0.0;

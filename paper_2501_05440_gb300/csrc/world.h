@@ -78,6 +78,7 @@ struct World {
     const int *u_edge;              // cell holding a lattice element's whole boundary, or -1
     const int *c_skiproot;          // lattice root cell whose planes interior elements never reach first
     const int *hs_side;             // per half-space of such a cell: lattice side of its plane (1..4)
+    const int *c_inner;             // universe cell inside a surface strictly inside its element
     // lattices; wall and centre coordinates are precomputed with the same
     // expressions the transport would evaluate: x0 + (double)i * pitch and
     // x0 + ((double)i + 0.5) * pitch (bit-identical, fewer FP64 instructions)
