@@ -39,8 +39,8 @@ N_PER_CYCLE = 1_000_000
 FP64_PEAK_GOPS = 152 * 2 * 2.07
 # FP64 thread-instructions per event of the persistent transport kernel on this
 # workload: ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum of one k_pool launch
-# divided by the events of that cycle (1.524e9 / 2.246e7), profiles/k_pool_c5g7_lattice.md.
-FP64_INST_PER_EVENT = 67.9
+# divided by the events of that cycle (1.455e9 / 2.246e7), profiles/k_pool_c5g7_lattice.md.
+FP64_INST_PER_EVENT = 64.8
 # Algorithmic particle-state bytes an event moves in the event-based form:
 # advance reads position/direction/energy/RNG/cell path and writes position,
 # RNG, event tag; collide or cross read and write direction, group, RNG and
@@ -58,16 +58,16 @@ def _hbm_peak():
 HBM_PEAK_GBS = _hbm_peak()
 # DRAM bytes (read + write) of the first k_advance launch of a cycle (1e6
 # particles) from an ncu capture, or None when the kernel has changed since.
-ADVANCE_TRAFFIC_PER_LAUNCH = 124699648 + 24173824
+ADVANCE_TRAFFIC_PER_LAUNCH = 124725504 + 25844480
 # DRAM bytes (read + write) of one k_pool launch from the same ncu capture, or None
 # when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 79966720 + 89870592
+TRAFFIC_PER_LAUNCH = 79513600 + 90772992
 # Other counters of the same two captures (profiles/k_pool_c5g7_lattice.md,
 # profiles/event_mode_c5g7_lattice.md): L2 sector hit rate, active lanes per
 # issued instruction / 32, FP64 pipe busy fraction of the elapsed time.
-NCU_K_POOL = {"l2_hit_rate": 0.8473, "warp_exec_efficiency": 20.03 / 32, "fp64_pipe_busy": 0.5008,
+NCU_K_POOL = {"l2_hit_rate": 0.8478, "warp_exec_efficiency": 20.34 / 32, "fp64_pipe_busy": 0.4798,
               "source": "profiles/k_pool_c5g7_lattice.md"}
-NCU_K_ADVANCE = {"l2_hit_rate": 0.4974, "fp64_pipe_busy": 0.7566, "dram_throughput": 0.1117,
+NCU_K_ADVANCE = {"l2_hit_rate": 0.4982, "fp64_pipe_busy": 0.7524, "dram_throughput": 0.1546,
                  "source": "profiles/event_mode_c5g7_lattice.md"}
 
 
