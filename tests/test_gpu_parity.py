@@ -197,3 +197,15 @@ def test_ce_infinite_medium_eigen_parity(mcgb, mode, pool, graphs):
     pb = W.ce_infinite_eigen([nuc(235.0, 4.0, 1.0, 2.0, 2.43), nuc(1.0, 3.0, 0.5, 0.0, 0.0)],
                              [0.02, 0.04], n=3000, inactive=2, active=3)
     _eigen_parity(mcgb, pb, mode, pool, graphs)
+
+
+@pytest.mark.parametrize("radius", [0.6299, 0.63])
+@pytest.mark.parametrize("mode,pool,graphs", [(0, 0, 0), (1, 0, 0)])
+def test_lattice_tight_pins_parity(mcgb, radius, mode, pool, graphs):
+    """Pins nearly filling their element (r = 0.6299 of a 0.63 half pitch: the
+    fuel cell is proven inside, so its flights skip the lattice walls and root
+    planes) and touching it (r = 0.63: nothing skipped) -- histories equal the
+    oracle's, which always evaluates every surface."""
+    pb = W.c5g7_like_lattice(n=4000, inactive=2, active=3)
+    pb["surfaces"][4]["coef"][2] = radius
+    _eigen_parity(mcgb, pb, mode, pool, graphs)
