@@ -3,6 +3,11 @@
 TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import this package.  The CUDA library never
 uses it.  This module only marshals arguments; all arithmetic is in the C file.
+
+``Oracle(problem)`` evaluates every step by its plain definition (libm log,
+true division, no fused multiply-add, nuclide sums at the particle's energy).
+``Oracle(problem, strict=True)`` adopts the CUDA library's rounding
+conventions instead, for bit-for-bit comparisons of histories.
 """
 from __future__ import annotations
 
@@ -67,10 +72,17 @@ def lib():
             L.orc_rng_xi.argtypes = [u64]
             L.orc_log.restype = d
             L.orc_log.argtypes = [d]
+            L.orc_log_table.restype = d
+            L.orc_log_table.argtypes = [i32]
+            L.orc_site_index.restype = i64
+            L.orc_site_index.argtypes = [i64, u64, i64, i64]
             L.orc_maxwell.restype = d
-            L.orc_maxwell.argtypes = [P]
-            L.orc_elastic.argtypes = [d, d, P, P, P]
-            L.orc_free_gas.argtypes = [d, d, d, P, P, P]
+            L.orc_maxwell.argtypes = [P, i32]
+            L.orc_elastic.argtypes = [d, d, P, P, P, i32]
+            L.orc_free_gas.argtypes = [d, d, d, P, P, P, i32]
+            L.orc_iso_dir.argtypes = [P, P, i32]
+            L.orc_set_arith.restype = i32
+            L.orc_set_arith.argtypes = [P, i32]
             L.orc_set_free_gas.restype = i32
             L.orc_set_free_gas.argtypes = [P, d, d]
             L.orc_history_count.restype = i64
@@ -113,11 +125,13 @@ class OracleError(RuntimeError):
 class Oracle:
     """One problem loaded into the CPU oracle."""
 
-    def __init__(self, problem: dict):
+    def __init__(self, problem: dict, strict: bool = False):
         self.L = lib()
         self.problem = problem
+        self.strict = bool(strict)
         self.ctx = C.c_void_p(self.L.orc_create())
         self._keep = []
+        self._chk(self.L.orc_set_arith(self.ctx, 1 if strict else 0))
         self._load(problem)
 
     def __del__(self):
@@ -300,33 +314,44 @@ def rng_xi(s):
 
 
 def log(xi):
+    """ln xi by the strict mode's table-driven method"""
     return lib().orc_log(xi)
 
 
-def iso_dir(state):
+def log_table(j):
+    """entry j of the strict logarithm's table of ln(1 + j/256)"""
+    return lib().orc_log_table(j)
+
+
+def site_index(j, n, M, N):
+    """bank site taken by source j of N after M sites, resampling draw n 2^-53"""
+    return lib().orc_site_index(j, n, M, N)
+
+
+def iso_dir(state, strict=False):
     s = C.c_uint64(state)
     out = np.zeros(3)
-    lib().orc_iso_dir(C.byref(s), _p(out))
+    lib().orc_iso_dir(C.byref(s), _p(out), 1 if strict else 0)
     return out, s.value
 
 
-def elastic(E, A, direction, state):
+def elastic(E, A, direction, state, strict=False):
     s = C.c_uint64(state)
     d = _f64(direction)
     out = np.zeros(4)
-    lib().orc_elastic(E, A, _p(d), C.byref(s), _p(out))
+    lib().orc_elastic(E, A, _p(d), C.byref(s), _p(out), 1 if strict else 0)
     return out, s.value
 
 
-def free_gas(E, A, kT, direction, state):
+def free_gas(E, A, kT, direction, state, strict=False):
     s = C.c_uint64(state)
     d = _f64(direction)
     out = np.zeros(4)
-    lib().orc_free_gas(E, A, kT, _p(d), C.byref(s), _p(out))
+    lib().orc_free_gas(E, A, kT, _p(d), C.byref(s), _p(out), 1 if strict else 0)
     return out, s.value
 
 
-def maxwell(state):
+def maxwell(state, strict=False):
     s = C.c_uint64(state)
-    e = lib().orc_maxwell(C.byref(s))
+    e = lib().orc_maxwell(C.byref(s), 1 if strict else 0)
     return e, s.value

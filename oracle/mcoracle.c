@@ -12,8 +12,15 @@
  * cycle or generation.  Wherever the paper is silent the choice is stated in a
  * comment beginning "Reading:".
  *
- * Arithmetic is plain IEEE double with no contraction (compile with
- * -ffp-contract=off); each formula is evaluated in the order written.
+ * Arithmetic.  The default (plain) mode writes each quantity as its definition
+ * reads: ln xi from libm, d = (distance along the normal) / (direction cosine),
+ * sums and products in the order written with no fused multiply-add (compile
+ * with -ffp-contract=off), continuous-energy cross sections summed over
+ * nuclides at the particle's energy, discrete outcomes sampled against
+ * unnormalised running sums.  The strict mode exists only to compare against
+ * the CUDA library bit for bit; it adopts that library's rounding conventions,
+ * each marked "Strict:" below.  The two modes draw the same random numbers in
+ * the same order and differ only in rounding.
  */
 #include "mcoracle.h"
 
@@ -33,38 +40,41 @@
 
 /* ------------------------------------------------------------------------- */
 /* Random numbers.  The paper (Sec. 1) states only that streams are replicable
- * on CPU and GPU.  Reading: the 63-bit multiplicative-congruential family
- * generator s' = (g s + c) mod 2^63, g = 2806196910506780709, c = 1, with
- * Brown's O(log n) skip-ahead ("Random number generation with arbitrary
- * strides", 1994); stream i starts at skip(seed, i * 152917).  A draw advances
- * the state and returns xi = ((s >> 10) + 1) 2^-53, in (0, 1].                */
-#define LCG_G 2806196910506780709ULL
-#define LCG_C 1ULL
-#define LCG_MASK 0x7FFFFFFFFFFFFFFFULL
-#define LCG_STRIDE 152917ULL
+ * on CPU and GPU.  Reading: the 63-bit congruential generator of the MCNP /
+ * OpenMC family, s' = (g s + c) mod 2^63 with g = 2806196910506780709, c = 1;
+ * stream i starts 152917 i steps after the seed; a draw advances the state and
+ * returns xi = ((s >> 10) + 1) 2^-53, in (0, 1].                              */
+#define LCG_MULT 2806196910506780709ULL
+#define LCG_ADD 1ULL
+#define LCG_BITS 0x7FFFFFFFFFFFFFFFULL
+#define STREAM_STRIDE 152917ULL
 
-uint64_t orc_rng_next(uint64_t s) { return (LCG_G * s + LCG_C) & LCG_MASK; }
+uint64_t orc_rng_next(uint64_t s) { return (LCG_MULT * s + LCG_ADD) & LCG_BITS; }
 
 double orc_rng_xi(uint64_t s) { return (double)((s >> 10) + 1) * 0x1p-53; }
 
+/* n steps at once (Brown, "Random number generation with arbitrary strides",
+ * 1994).  k steps are the affine map s -> A_k s + B_k (mod 2^63).  Reading the
+ * bits of n from the most significant down: k -> 2k composes the map with
+ * itself, A_2k = A_k^2, B_2k = (A_k + 1) B_k; k -> k + 1 appends one step,
+ * A_k+1 = g A_k, B_k+1 = g B_k + c.  Unsigned arithmetic wraps mod 2^64, and
+ * only the low 63 bits are kept at the end.                                   */
 uint64_t orc_rng_skip(uint64_t s, uint64_t n)
 {
-    /* compose the affine map s -> g s + c with itself n times by binary powers */
-    uint64_t G = 1, C = 0, h = LCG_G, f = LCG_C;
-    n &= LCG_MASK;
-    while (n) {
-        if (n & 1) {
-            G = G * h;
-            C = C * h + f;
+    uint64_t A = 1, B = 0;
+    n &= LCG_BITS;
+    for (int bit = 62; bit >= 0; bit--) {
+        B = (A + 1) * B;
+        A = A * A;
+        if ((n >> bit) & 1) {
+            A = LCG_MULT * A;
+            B = LCG_MULT * B + LCG_ADD;
         }
-        f = f * (h + 1);
-        h = h * h;
-        n >>= 1;
     }
-    return (G * (s & LCG_MASK) + C) & LCG_MASK;
+    return (A * (s & LCG_BITS) + B) & LCG_BITS;
 }
 
-uint64_t orc_rng_stream(uint64_t seed, uint64_t id) { return orc_rng_skip(seed, id * LCG_STRIDE); }
+uint64_t orc_rng_stream(uint64_t seed, uint64_t id) { return orc_rng_skip(seed, id * STREAM_STRIDE); }
 
 static uint64_t draw_n(uint64_t *s)
 {
@@ -75,82 +85,83 @@ static uint64_t draw_n(uint64_t *s)
 static double draw(uint64_t *s) { return (double)draw_n(s) * 0x1p-53; }
 
 /* ------------------------------------------------------------------------- */
-/* Natural logarithm of xi = n 2^-53 (n in [1, 2^53]) for the flight distance.
- * Reading: both implementations evaluate ln with the same table-driven method
- * (Tang, "Table-driven implementation of the logarithm function in IEEE
- * floating-point arithmetic", ACM TOMS 1990): n = 2^e m, m in [1,2); c_j =
- * 1 + j/256 from the top 8 fraction bits; r = (m - c_j) (1/c_j);
- * ln xi = (e - 53) ln2 + ln c_j + log1p(r) with log1p by its Taylor series to
- * r^6 (Horner with fused multiply-adds).  ln c_j comes from the series
- * ln c = 2 atanh((c-1)/(c+1)).                                                */
-static double LOG_TAB[256], RINV_TAB[256];
-static int log_ready;
-static const double LN2 = 0x1.62e42fefa39efp-1;
+/* ln xi for the flight distance and the spectra.  Plain: libm's log.
+ * Strict: the table-driven method of Tang ("Table-driven implementation of the
+ * logarithm function in IEEE floating-point arithmetic", ACM TOMS 1990), as the
+ * CUDA library evaluates it: xi = 2^(e-53) m with m in [1, 2); c = 1 + j/256
+ * from the top 8 bits of m's fraction; r = (m - c) (1/c);
+ * ln xi = (e - 53) ln 2 + ln c + log1p(r), log1p by its Taylor polynomial to
+ * r^6 evaluated by Horner's rule with fused multiply-adds.  The table holds
+ * ln c correctly rounded (computed here in extended precision and rounded
+ * once) and 1/c rounded once.                                                 */
+static double TANG_LN[256], TANG_RECIP[256];
+static int tang_ready;
+static const double LN2_D = 0x1.62e42fefa39efp-1;
 
-static double ln_series(double c)
+static void tang_init(void)
 {
-    double s = (c - 1.0) / (c + 1.0);
-    double z = s * s;
-    double p = 1.0 / 79.0;
-    for (int k = 38; k >= 0; k--) p = p * z + 1.0 / (double)(2 * k + 1);
-    return 2.0 * s * p;
-}
-
-static void log_init(void)
-{
-    if (log_ready) return;
+    if (tang_ready) return;
     for (int j = 0; j < 256; j++) {
-        double c = 1.0 + (double)j / 256.0;
-        LOG_TAB[j] = ln_series(c);
-        RINV_TAB[j] = 1.0 / c;
+        long double c = 1.0L + (long double)j / 256.0L;
+        TANG_LN[j] = (double)logl(c);
+        TANG_RECIP[j] = 1.0 / (double)c;
     }
-    log_ready = 1;
+    tang_ready = 1;
 }
 
-static int top_bit(uint64_t n)
+double orc_log_table(int j)
+{
+    tang_init();
+    return j >= 0 && j < 256 ? TANG_LN[j] : NAN;
+}
+
+/* n in [1, 2^53]: xi = n 2^-53 */
+static double tang_log(uint64_t n)
 {
     int e = 0;
-    while (n >> 1) {
-        n >>= 1;
-        e++;
-    }
-    return e;
-}
-
-static double log_n(uint64_t n)
-{
-    int e = top_bit(n);
-    double m = ldexp((double)n, -e);
-    int j = (int)(((n << (63 - e)) >> 55) & 0xFF);
+    while ((n >> e) > 1) e++;                         /* 2^e <= n < 2^(e+1) */
+    double m = ldexp((double)n, -e);                  /* exact */
+    int j = (int)((m - 1.0) * 256.0);                 /* exact: top 8 fraction bits */
     double c = 1.0 + (double)j / 256.0;
-    double r = (m - c) * RINV_TAB[j];
-    double q = -1.0 / 6.0;
-    q = fma(q, r, 1.0 / 5.0);
-    q = fma(q, r, -0.25);
-    q = fma(q, r, 1.0 / 3.0);
-    q = fma(q, r, -0.5);
-    q = fma(q, r, 1.0);
-    double p = q * r;
-    return (double)(e - 53) * LN2 + (LOG_TAB[j] + p);
+    double r = (m - c) * TANG_RECIP[j];
+    double h = -1.0 / 6.0;
+    h = fma(h, r, 1.0 / 5.0);
+    h = fma(h, r, -0.25);
+    h = fma(h, r, 1.0 / 3.0);
+    h = fma(h, r, -0.5);
+    h = fma(h, r, 1.0);
+    return (double)(e - 53) * LN2_D + (TANG_LN[j] + h * r);
 }
 
 double orc_log(double xi)
 {
-    log_init();
+    tang_init();
     if (!(xi > 0.0) || xi > 1.0) return NAN;
-    return log_n((uint64_t)(xi * 0x1p53));
+    return tang_log((uint64_t)(xi * 0x1p53));
+}
+
+/* ln of xi = n 2^-53 in the given mode */
+static double ln_xi(uint64_t n, int strict)
+{
+    return strict ? tang_log(n) : log((double)n * 0x1p-53);
+}
+
+/* a^2 + b^2.  Strict: the first product is fused into the addition. */
+static double sumsq2(double a, double b, int strict)
+{
+    return strict ? fma(a, a, b * b) : a * a + b * b;
 }
 
 /* ------------------------------------------------------------------------- */
 /* Isotropic direction (Marsaglia, "Choosing a point from the surface of a
  * sphere", 1972): (a, b) uniform in the unit disk by rejection, S = a^2 + b^2,
  * Omega = (2a sqrt(1-S), 2b sqrt(1-S), 1 - 2S).  No trigonometric function.   */
-static void iso_dir(uint64_t *s, double *u, double *v, double *w)
+static void iso_dir(uint64_t *s, double *u, double *v, double *w, int strict)
 {
     for (int k = 0; k < 64; k++) {
         double a = 2.0 * draw(s) - 1.0;
         double b = 2.0 * draw(s) - 1.0;
-        double S = fma(a, a, b * b);
+        double S = sumsq2(a, b, strict);
         if (S < 1.0) {
             double t = 2.0 * sqrt(1.0 - S);
             *u = a * t;
@@ -162,36 +173,45 @@ static void iso_dir(uint64_t *s, double *u, double *v, double *w)
     *u = 0.0; *v = 0.0; *w = 1.0;
 }
 
-int orc_iso_dir(uint64_t *s, double out[3])
+int orc_iso_dir(uint64_t *s, double out[3], int mode)
 {
-    iso_dir(s, &out[0], &out[1], &out[2]);
+    iso_dir(s, &out[0], &out[1], &out[2], mode == ORC_STRICT);
     return 0;
 }
 
-/* Uniform azimuth as (cos phi, sin phi) without trigonometry: (a, b) uniform in
- * the unit disk by rejection; the doubled angle of (a, b) is uniform, giving
- * cos = (a^2 - b^2)/r2, sin = 2ab/r2.                                         */
-static void azimuth(uint64_t *s, double *cphi, double *sphi)
+/* A point uniform in the unit disk minus its centre, by rejection (at most 64
+ * tries): returns 1 with (a, b) and r2 = a^2 + b^2 in (0, 1], else 0.        */
+static int disk_point(uint64_t *s, double *a, double *b, double *r2, int strict)
 {
     for (int k = 0; k < 64; k++) {
-        double a = 2.0 * draw(s) - 1.0;
-        double b = 2.0 * draw(s) - 1.0;
-        double r2 = fma(a, a, b * b);
-        if (r2 <= 1.0 && r2 > 0.0) {
-            *cphi = fma(a, a, -(b * b)) / r2;
-            *sphi = 2.0 * a * b / r2;
-            return;
+        double x = 2.0 * draw(s) - 1.0;
+        double y = 2.0 * draw(s) - 1.0;
+        double q = sumsq2(x, y, strict);
+        if (q <= 1.0 && q > 0.0) {
+            *a = x; *b = y; *r2 = q;
+            return 1;
         }
     }
-    *cphi = 1.0; *sphi = 0.0;
+    return 0;
+}
+
+/* Uniform azimuth as (cos phi, sin phi) without trigonometry: the doubled
+ * angle of a disk point (a, b) is uniform, cos = (a^2 - b^2)/r2,
+ * sin = 2ab/r2.                                                               */
+static void azimuth(uint64_t *s, double *cphi, double *sphi, int strict)
+{
+    double a, b, r2;
+    if (!disk_point(s, &a, &b, &r2, strict)) { *cphi = 1.0; *sphi = 0.0; return; }
+    *cphi = (strict ? fma(a, a, -(b * b)) : a * a - b * b) / r2;
+    *sphi = 2.0 * a * b / r2;
 }
 
 /* Rotate direction (u,v,w) by polar cosine mu about itself, azimuth sampled
  * (textbook rotation, polar axis z, or x when |w| is near 1).                 */
-static void rotate(double mu, uint64_t *s, double *u, double *v, double *w)
+static void rotate(double mu, uint64_t *s, double *u, double *v, double *w, int strict)
 {
     double cphi, sphi;
-    azimuth(s, &cphi, &sphi);
+    azimuth(s, &cphi, &sphi, strict);
     double st2 = 1.0 - mu * mu;
     double st = sqrt(st2 > 0.0 ? st2 : 0.0);
     double u0 = *u, v0 = *v, w0 = *w;
@@ -218,7 +238,7 @@ static void rotate(double mu, uint64_t *s, double *u, double *v, double *w)
  * Reading: E' is floored at 1e-5 eV (the paper's data start there).           */
 #define E_MIN 1.0e-5
 #define E_MAX 2.0e7
-static double elastic(double E, double A, uint64_t *s, double *u, double *v, double *w)
+static double elastic(double E, double A, uint64_t *s, double *u, double *v, double *w, int strict)
 {
     double mucm = 2.0 * draw(s) - 1.0;
     double q = A * A + 2.0 * A * mucm + 1.0;
@@ -226,55 +246,47 @@ static double elastic(double E, double A, uint64_t *s, double *u, double *v, dou
     double mul = (1.0 + A * mucm) / sqrt(q);
     if (mul > 1.0) mul = 1.0;
     if (mul < -1.0) mul = -1.0;
-    rotate(mul, s, u, v, w);
+    rotate(mul, s, u, v, w, strict);
     return Ep < E_MIN ? E_MIN : Ep;
 }
 
-int orc_elastic(double E, double A, const double dir[3], uint64_t *s, double out[4])
+int orc_elastic(double E, double A, const double dir[3], uint64_t *s, double out[4], int mode)
 {
     double u = dir[0], v = dir[1], w = dir[2];
-    out[0] = elastic(E, A, s, &u, &v, &w);
+    out[0] = elastic(E, A, s, &u, &v, &w, mode == ORC_STRICT);
     out[1] = u; out[2] = v; out[3] = w;
     return 0;
 }
 
+/* cos^2 of an angle uniform on [0, pi/2]: a^2 / (a^2 + b^2) of a disk point
+ * (1 if no point is accepted in 64 tries)                                     */
+static double disk_cos2(uint64_t *s, int strict)
+{
+    double a, b, r2;
+    if (!disk_point(s, &a, &b, &r2, strict)) return 1.0;
+    return a * a / r2;
+}
+
 /* Fission spectrum.  Reading: Maxwellian with T = 1.33 MeV sampled by the
  * Everett-Cashwell rule E = -T (ln xi1 + ln xi2 cos^2 theta) with theta uniform;
- * cos^2 theta is taken as a^2 / (a^2 + b^2) of a point uniform in the unit disk
- * (no trigonometry); energies above 20 MeV are resampled.                     */
-static double maxwell(uint64_t *s)
+ * cos^2 theta is a^2 / (a^2 + b^2) of a point uniform in the unit disk (no
+ * trigonometry); energies above 20 MeV are resampled.                         */
+static double maxwell(uint64_t *s, int strict)
 {
-    log_init();
     for (int k = 0; k < 64; k++) {
-        double L1 = log_n(draw_n(s));
-        double L2 = log_n(draw_n(s));
-        double a = 1.0, r2 = 1.0;
-        for (int t = 0; t < 64; t++) {
-            double aa = 2.0 * draw(s) - 1.0;
-            double bb = 2.0 * draw(s) - 1.0;
-            double rr = fma(aa, aa, bb * bb);
-            if (rr <= 1.0 && rr > 0.0) { a = aa; r2 = rr; break; }
-        }
-        double c2 = a * a / r2;
+        double L1 = ln_xi(draw_n(s), strict);
+        double L2 = ln_xi(draw_n(s), strict);
+        double c2 = disk_cos2(s, strict);
         double E = -1.33e6 * (L1 + L2 * c2);
         if (E <= E_MAX) return E < E_MIN ? E_MIN : E;
     }
     return E_MAX;
 }
 
-double orc_maxwell(uint64_t *s) { return maxwell(s); }
-
-/* cos^2 of an angle uniform on [0, pi/2]: a^2 / (a^2 + b^2) of a point uniform
- * in the unit disk (rejection, at most 64 tries; 1 if none is accepted) */
-static double disk_cos2(uint64_t *s)
+double orc_maxwell(uint64_t *s, int mode)
 {
-    for (int t = 0; t < 64; t++) {
-        double aa = 2.0 * draw(s) - 1.0;
-        double bb = 2.0 * draw(s) - 1.0;
-        double rr = fma(aa, aa, bb * bb);
-        if (rr <= 1.0 && rr > 0.0) return aa * aa / rr;
-    }
-    return 1.0;
+    tang_init();
+    return maxwell(s, mode == ORC_STRICT);
 }
 
 /* Elastic scattering off a free-gas target with a constant cross section (the
@@ -292,9 +304,8 @@ static double disk_cos2(uint64_t *s)
  * frame A r / (A + 1) is kept and its direction there is isotropic; then
  * E' = E |v'|^2 / y^2 (floored at 1e-5 eV) and Omega' = v' / |v'|.           */
 static double free_gas(double E, double A, double kT, uint64_t *s, double *u, double *v,
-                       double *w)
+                       double *w, int strict)
 {
-    log_init();
     const double SQRT_PI = 1.7724538509055160273;
     double y = sqrt(A * E / kT);
     double py = y * SQRT_PI;
@@ -302,13 +313,13 @@ static double free_gas(double E, double A, double kT, uint64_t *s, double *u, do
     for (int k = 0; k < MAX_TRIES; k++) {
         double x2;
         if (draw(s) * (py + 2.0) < py) {
-            double L1 = log_n(draw_n(s));
-            double L2 = log_n(draw_n(s));
-            double c2 = disk_cos2(s);
+            double L1 = ln_xi(draw_n(s), strict);
+            double L2 = ln_xi(draw_n(s), strict);
+            double c2 = disk_cos2(s, strict);
             x2 = -(L1 + L2 * c2);
         } else {
-            double L1 = log_n(draw_n(s));
-            double L2 = log_n(draw_n(s));
+            double L1 = ln_xi(draw_n(s), strict);
+            double L2 = ln_xi(draw_n(s), strict);
             x2 = -(L1 + L2);
         }
         x = sqrt(x2);
@@ -318,13 +329,13 @@ static double free_gas(double E, double A, double kT, uint64_t *s, double *u, do
         if (draw(s) * (x + y) <= r) break;
     }
     double tu = *u, tv = *v, tw = *w;
-    rotate(mu, s, &tu, &tv, &tw);
+    rotate(mu, s, &tu, &tv, &tw, strict);
     double inv = 1.0 / (A + 1.0);
     double Vx = (y * *u + A * x * tu) * inv;
     double Vy = (y * *v + A * x * tv) * inv;
     double Vz = (y * *w + A * x * tw) * inv;
     double cu, cv, cw;
-    iso_dir(s, &cu, &cv, &cw);
+    iso_dir(s, &cu, &cv, &cw, strict);
     double wc = A * r * inv;
     double px = Vx + wc * cu, py2 = Vy + wc * cv, pz = Vz + wc * cw;
     double p2 = px * px + py2 * py2 + pz * pz;
@@ -334,12 +345,29 @@ static double free_gas(double E, double A, double kT, uint64_t *s, double *u, do
     return Ep < E_MIN ? E_MIN : Ep;
 }
 
-int orc_free_gas(double E, double A, double kT, const double dir[3], uint64_t *s, double out[4])
+int orc_free_gas(double E, double A, double kT, const double dir[3], uint64_t *s, double out[4],
+                 int mode)
 {
+    tang_init();
     double u = dir[0], v = dir[1], w = dir[2];
-    out[0] = free_gas(E, A, kT, s, &u, &v, &w);
+    out[0] = free_gas(E, A, kT, s, &u, &v, &w, mode == ORC_STRICT);
     out[1] = u; out[2] = v; out[3] = w;
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Resampling site (power iteration, Sec. 4).  Reading: systematic sampling --
+ * source j of N takes bank site floor((j + xi) M / N), xi = n 2^-53 the
+ * cycle's draw, clamped to M - 1 (reached only at xi = 1, j = N - 1).  The
+ * floor of the rational is taken exactly in integers: (j + n 2^-53) M / N =
+ * (j M 2^53 + n M) / (N 2^53).                                                */
+int64_t orc_site_index(int64_t j, uint64_t n, int64_t M, int64_t N)
+{
+    unsigned __int128 num = ((unsigned __int128)(uint64_t)j << 53) + n;
+    num *= (uint64_t)M;
+    unsigned __int128 den = (unsigned __int128)(uint64_t)N << 53;
+    int64_t k = (int64_t)(num / den);
+    return k >= M ? M - 1 : k;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -349,7 +377,8 @@ typedef struct { int universe, nhs, off, fill_kind, fill; } Cell;
 typedef struct { double x0, y0, pitch; int nx, ny; int *univ; } Lattice;
 typedef struct {
     double *sigt, *sigs, *nusf, *chi;          /* input */
-    double *mfp, *mu, *mufl, *mufr, *ps, *stot, *scdf, *chicdf;   /* derived */
+    double *stot, *chitot;                     /* row sums of sigma_s; sum of chi */
+    double *mfp, *ps, *scdf, *chicdf;          /* strict mode's rounded-once constants */
     int fissile;
 } MatMG;
 typedef struct { double A, nu; int n; double *E, *s, *c, *f; } Nuclide;
@@ -360,7 +389,7 @@ typedef struct { int n; double *E, *St, *Sf; } MacroCE;
 typedef struct {
     int kind, accept, ekind, dkind, ne;
     double p[6], beam[3];
-    double *edata, *ecdf;
+    double *edata, *ecdf, etot;
 } Source;
 typedef struct {
     int filter, nedges; double *edges; int nbins, ne;
@@ -377,6 +406,7 @@ typedef struct {
 
 struct orc_ctx {
     char err[256];
+    int strict;                  /* ORC_STRICT: the CUDA library's rounding conventions */
     int ns, nc, nhs, nl, G, nm, nn, nmc, nt, ce, max_coll;
     Surface *surf;
     Cell *cell;
@@ -430,7 +460,7 @@ static double *dup_d(const double *a, int n)
 
 orc_ctx *orc_create(void)
 {
-    log_init();
+    tang_init();
     orc_ctx *c = calloc(1, sizeof(orc_ctx));
     c->G = 0;
     c->ce = -1;
@@ -459,8 +489,8 @@ void orc_destroy(orc_ctx *c)
     for (int i = 0; i < c->nl; i++) free(c->lat[i].univ);
     for (int i = 0; i < c->nm; i++) {
         MatMG *m = &c->mg[i];
-        free(m->sigt); free(m->sigs); free(m->nusf); free(m->chi); free(m->mfp); free(m->mu);
-        free(m->mufl); free(m->mufr); free(m->ps); free(m->stot); free(m->scdf); free(m->chicdf);
+        free(m->sigt); free(m->sigs); free(m->nusf); free(m->chi); free(m->stot); free(m->chitot);
+        free(m->mfp); free(m->ps); free(m->scdf); free(m->chicdf);
     }
     for (int i = 0; i < c->nn; i++) {
         free(c->nuc[i].E); free(c->nuc[i].s); free(c->nuc[i].c); free(c->nuc[i].f);
@@ -480,6 +510,13 @@ void orc_destroy(orc_ctx *c)
 }
 
 const char *orc_error(const orc_ctx *c) { return c ? c->err : "null context"; }
+
+int orc_set_arith(orc_ctx *c, int mode)
+{
+    if (mode != ORC_PLAIN && mode != ORC_STRICT) return fail(c, ORC_EINVAL, "bad arithmetic mode");
+    c->strict = mode == ORC_STRICT;
+    return 0;
+}
 
 int orc_add_surface(orc_ctx *c, int type, const double coef[4], int bc)
 {
@@ -541,24 +578,41 @@ int orc_set_groups(orc_ctx *c, int G)
     return 0;
 }
 
-/* cumulative distribution of non-negative weights: partial sums in order divided
- * by the total; the last entry is exactly 1.  Sampling takes the first k with
- * xi <= cdf[k].                                                              */
-static void make_cdf(const double *w, int n, double *cdf)
+/* Discrete sampling from non-negative weights w[0..n-1] with total W: the
+ * outcome is the first k whose running sum w[0] + ... + w[k] reaches xi W.
+ * Plain: exactly that comparison.  Strict: the CUDA library's table of the
+ * running sums each divided by W (the last set to exactly 1), searched for the
+ * first entry >= xi.                                                         */
+static double weight_total(const double *w, int n)
 {
-    double acc = 0.0;
-    for (int k = 0; k < n; k++) {
-        acc = acc + w[k];
-        cdf[k] = acc;
-    }
-    for (int k = 0; k < n; k++) cdf[k] = cdf[k] / acc;
-    cdf[n - 1] = 1.0;
+    double W = 0.0;
+    for (int k = 0; k < n; k++) W = W + w[k];
+    return W;
 }
 
-static int sample_cdf(const double *cdf, int n, double xi)
+static void strict_cdf(const double *w, int n, double *tab)
 {
-    for (int k = 0; k < n; k++)
-        if (xi <= cdf[k]) return k;
+    double W = weight_total(w, n);
+    double run = 0.0;
+    for (int k = 0; k < n; k++) {
+        run = run + w[k];
+        tab[k] = k == n - 1 ? 1.0 : run / W;
+    }
+}
+
+static int sample_discrete(const double *w, double W, const double *tab, int n, double xi,
+                           int strict)
+{
+    if (strict) {
+        for (int k = 0; k < n - 1; k++)
+            if (xi <= tab[k]) return k;
+        return n - 1;
+    }
+    double target = xi * W, run = 0.0;
+    for (int k = 0; k < n - 1; k++) {
+        run = run + w[k];
+        if (target <= run) return k;
+    }
     return n - 1;
 }
 
@@ -573,39 +627,29 @@ int orc_add_material_mg(orc_ctx *c, const double *sigma_t, const double *sigma_s
     m->sigs = dup_d(sigma_s, G * G);
     m->nusf = dup_d(nu_sigma_f, G);
     m->chi = dup_d(chi, G);
-    m->mfp = malloc(sizeof(double) * G);
-    m->mu = malloc(sizeof(double) * G);
-    m->mufl = malloc(sizeof(double) * G);
-    m->mufr = malloc(sizeof(double) * G);
-    m->ps = malloc(sizeof(double) * G);
     m->stot = malloc(sizeof(double) * G);
+    m->chitot = malloc(sizeof(double));
+    m->mfp = malloc(sizeof(double) * G);
+    m->ps = malloc(sizeof(double) * G);
     m->scdf = malloc(sizeof(double) * G * G);
     m->chicdf = malloc(sizeof(double) * G);
     m->fissile = 0;
     for (int g = 0; g < G; g++) {
         if (sigma_t[g] < 0.0 || nu_sigma_f[g] < 0.0) return fail(c, ORC_EINVAL, "negative XS");
-        double acc = 0.0;
-        for (int h = 0; h < G; h++) {
+        for (int h = 0; h < G; h++)
             if (sigma_s[g * G + h] < 0.0) return fail(c, ORC_EINVAL, "negative XS");
-            acc = acc + sigma_s[g * G + h];
-        }
-        if (acc > sigma_t[g]) return fail(c, ORC_EINVAL, "scattering exceeds total");
-        m->stot[g] = acc;
-        /* Reading: per-group constants are rounded once: mean free path 1/Sigma_t,
-         * fission yield mu = nuSigma_f/Sigma_t and scattering probability
-         * Sigma_s,tot/Sigma_t (all 0 in a void, Sigma_t = 0).                   */
+        m->stot[g] = weight_total(&sigma_s[g * G], G);
+        if (m->stot[g] > sigma_t[g]) return fail(c, ORC_EINVAL, "scattering exceeds total");
+        /* Strict: the mean free path 1/Sigma_t and the scattering probability
+         * Sigma_s,tot/Sigma_t are rounded once per group (0 and inf in a void). */
         m->mfp[g] = sigma_t[g] > 0.0 ? 1.0 / sigma_t[g] : INF;
-        m->mu[g] = sigma_t[g] > 0.0 ? nu_sigma_f[g] / sigma_t[g] : 0.0;
-        m->mufl[g] = floor(m->mu[g]);
-        m->mufr[g] = m->mu[g] - m->mufl[g];
-        m->ps[g] = sigma_t[g] > 0.0 ? acc / sigma_t[g] : 0.0;
-        if (acc > 0.0) make_cdf(&sigma_s[g * G], G, &m->scdf[g * G]);
+        m->ps[g] = sigma_t[g] > 0.0 ? m->stot[g] / sigma_t[g] : 0.0;
+        if (m->stot[g] > 0.0) strict_cdf(&sigma_s[g * G], G, &m->scdf[g * G]);
         else for (int h = 0; h < G; h++) m->scdf[g * G + h] = 1.0;
         if (nu_sigma_f[g] > 0.0) m->fissile = 1;
     }
-    double csum = 0.0;
-    for (int g = 0; g < G; g++) csum += chi[g];
-    if (csum > 0.0) make_cdf(chi, G, m->chicdf);
+    m->chitot[0] = weight_total(chi, G);
+    if (m->chitot[0] > 0.0) strict_cdf(chi, G, m->chicdf);
     else for (int g = 0; g < G; g++) m->chicdf[g] = 1.0;
     return c->nm++;
 }
@@ -657,7 +701,10 @@ int orc_set_source(orc_ctx *c, int kind, const double *params, int accept, int e
     s->ne = n_energy;
     s->edata = dup_d(energy, n_energy);
     s->ecdf = malloc(sizeof(double) * (n_energy ? n_energy : 1));
-    if (energy_kind == ORC_E_PDF) make_cdf(energy, n_energy, s->ecdf);
+    if (energy_kind == ORC_E_PDF) {
+        s->etot = weight_total(energy, n_energy);
+        strict_cdf(energy, n_energy, s->ecdf);
+    }
     c->src_set = 1;
     return 0;
 }
@@ -725,7 +772,11 @@ int orc_set_max_collisions(orc_ctx *c, int max_collisions)
 
 /* ------------------------------------------------------------------------- */
 /* geometry                                                                   */
-static double surf_f(const Surface *s, double x, double y, double z)
+/* Surface functions f(r): f < 0 on the negative side.  Planes n.r - d, a
+ * z-cylinder (x-x0)^2 + (y-y0)^2 - R^2, a sphere likewise in three
+ * coordinates.  Strict: the sums of squares are evaluated with fused
+ * multiply-adds.                                                              */
+static double surf_f(const Surface *s, double x, double y, double z, int strict)
 {
     switch (s->type) {
     case ORC_PX: return x - s->c[0];
@@ -734,11 +785,12 @@ static double surf_f(const Surface *s, double x, double y, double z)
     case ORC_PLANE: return s->c[0] * x + s->c[1] * y + s->c[2] * z - s->c[3];
     case ORC_CYLZ: {
         double dx = x - s->c[0], dy = y - s->c[1];
-        return fma(dx, dx, dy * dy) - s->r2;
+        return sumsq2(dx, dy, strict) - s->r2;
     }
     default: {
         double dx = x - s->c[0], dy = y - s->c[1], dz = z - s->c[2];
-        return fma(dx, dx, fma(dy, dy, dz * dz)) - s->r2;
+        double q = strict ? fma(dx, dx, fma(dy, dy, dz * dz)) : dx * dx + dy * dy + dz * dz;
+        return q - s->r2;
     }
     }
 }
@@ -760,13 +812,18 @@ static double surf_gdot(const Surface *s, double x, double y, double z, double u
 /* Distance along the direction to where the particle leaves the half-space of
  * the given sense.  Reading (the paper names surface tracking, Sec. 1, without
  * rules): the root is chosen from the sense, not from evaluating the position,
- * so a particle sitting on a surface it just crossed never re-hits it; roots
- * use the cancellation-free quadratic forms; a negative root from round-off is
- * taken as 0.  Reading: axis planes (and lattice walls) use the direction's
- * reciprocal, rounded once whenever the direction is set, so that
- * t = (x0 - x) (1/u); quadratic terms are evaluated with fused multiply-adds. */
+ * so a particle sitting on a surface it just crossed never re-hits it; a
+ * negative root from round-off is taken as 0.
+ * Plane: t = -f(r) / (n.Omega) when the particle moves towards the other side.
+ * Quadric: f(r + t Omega) = a t^2 + 2 b t + cc with a = |Omega_perp|^2,
+ * b = (r - r0).Omega_perp, cc = f(r), disc = b^2 - a cc; roots by the
+ * cancellation-free forms: inside (sense -1) the far root, (-b + sqrt(disc))/a
+ * for b <= 0 and -cc/(b + sqrt(disc)) for b > 0; outside, when approaching
+ * (b < 0) and hit (disc >= 0), the near root cc/(-b + sqrt(disc)).
+ * Strict: axis planes multiply by the direction's reciprocal carried with the
+ * particle, t = -f (1/u); quadric terms use fused multiply-adds.             */
 static double surf_dist(const Surface *s, int sense, double x, double y, double z, double u,
-                        double v, double w, double iu, double iv, double iw)
+                        double v, double w, double iu, double iv, double iw, int strict)
 {
     double t;
     if (s->type <= ORC_PLANE) {
@@ -781,8 +838,7 @@ static double surf_dist(const Surface *s, int sense, double x, double y, double 
             inv = 0.0;
         }
         if ((sense > 0 && dn < 0.0) || (sense < 0 && dn > 0.0)) {
-            /* axis planes use the direction's reciprocal, other planes divide */
-            t = s->type == ORC_PLANE ? -f / dn : -f * inv;
+            t = (strict && s->type != ORC_PLANE) ? -f * inv : -f / dn;
             return t < 0.0 ? 0.0 : t;
         }
         return INF;
@@ -790,17 +846,29 @@ static double surf_dist(const Surface *s, int sense, double x, double y, double 
     double a, b, cc;
     if (s->type == ORC_CYLZ) {
         double dx = x - s->c[0], dy = y - s->c[1];
-        a = fma(u, u, v * v);
-        b = fma(dx, u, dy * v);
-        cc = fma(dx, dx, dy * dy) - s->r2;
+        if (strict) {
+            a = fma(u, u, v * v);
+            b = fma(dx, u, dy * v);
+            cc = fma(dx, dx, dy * dy) - s->r2;
+        } else {
+            a = u * u + v * v;
+            b = dx * u + dy * v;
+            cc = dx * dx + dy * dy - s->r2;
+        }
     } else {
         double dx = x - s->c[0], dy = y - s->c[1], dz = z - s->c[2];
-        a = fma(u, u, fma(v, v, w * w));
-        b = fma(dx, u, fma(dy, v, dz * w));
-        cc = fma(dx, dx, fma(dy, dy, dz * dz)) - s->r2;
+        if (strict) {
+            a = fma(u, u, fma(v, v, w * w));
+            b = fma(dx, u, fma(dy, v, dz * w));
+            cc = fma(dx, dx, fma(dy, dy, dz * dz)) - s->r2;
+        } else {
+            a = u * u + v * v + w * w;
+            b = dx * u + dy * v + dz * w;
+            cc = dx * dx + dy * dy + dz * dz - s->r2;
+        }
     }
     if (a == 0.0) return INF;
-    double disc = fma(b, b, -(a * cc));
+    double disc = strict ? fma(b, b, -(a * cc)) : b * b - a * cc;
     if (sense < 0) {
         if (disc < 0.0) disc = 0.0;
         if (b <= 0.0) t = (-b + sqrt(disc)) / a;
@@ -850,7 +918,7 @@ static int locate_univ(const orc_ctx *c, int U, double x, double y, double z, do
                 sense = forced_sense;
             } else {
                 const Surface *s = &c->surf[sid];
-                double f = surf_f(s, x, y, z);
+                double f = surf_f(s, x, y, z, c->strict);
                 if (f > 0.0) sense = 1;
                 else if (f < 0.0) sense = -1;
                 else sense = surf_gdot(s, x, y, z, u, v, w) >= 0.0 ? 1 : -1;
@@ -877,6 +945,8 @@ typedef struct {
 enum { FATE_ABSORBED = 0, FATE_LEAKED = 1, FATE_CUT = 2, FATE_LOST = 3, FATE_CAPPED = 4,
        FATE_TIME = 5 };
 
+/* Strict: the particle carries 1/u, 1/v, 1/w, rounded whenever its direction
+ * is set (axis-plane and lattice-wall distances multiply by them). */
 static void set_recip(Particle *p)
 {
     p->iu = 1.0 / p->u;
@@ -944,19 +1014,26 @@ static double boundary(const orc_ctx *c, const Particle *p, int *kind, int *whic
     const Cell *rc = &c->cell[p->cell];
     for (int h = 0; h < rc->nhs; h++) {
         double t = surf_dist(&c->surf[c->hs_surf[rc->off + h]], c->hs_sense[rc->off + h], p->x,
-                             p->y, p->z, p->u, p->v, p->w, p->iu, p->iv, p->iw);
+                             p->y, p->z, p->u, p->v, p->w, p->iu, p->iv, p->iw, c->strict);
         if (t < best) { best = t; *kind = B_ROOT; *which = rc->off + h; }
     }
     if (rc->fill_kind == ORC_FILL_LATTICE) {
         const Lattice *L = &c->lat[rc->fill];
+        /* the wall ahead, x0 + i pitch; t = (wall - x) / u (strict: times 1/u) */
         double t = INF;
-        if (p->u > 0.0 && p->ix < L->nx - 1) t = (L->x0 + (double)(p->ix + 1) * L->pitch - p->x) * p->iu;
-        else if (p->u < 0.0 && p->ix > 0) t = (L->x0 + (double)p->ix * L->pitch - p->x) * p->iu;
+        int wx = p->u > 0.0 && p->ix < L->nx - 1 ? p->ix + 1 : (p->u < 0.0 && p->ix > 0 ? p->ix : -1);
+        if (wx >= 0) {
+            double gap = L->x0 + (double)wx * L->pitch - p->x;
+            t = c->strict ? gap * p->iu : gap / p->u;
+        }
         if (t < 0.0) t = 0.0;
         if (t < best) { best = t; *kind = B_LATX; }
         t = INF;
-        if (p->v > 0.0 && p->iy < L->ny - 1) t = (L->y0 + (double)(p->iy + 1) * L->pitch - p->y) * p->iv;
-        else if (p->v < 0.0 && p->iy > 0) t = (L->y0 + (double)p->iy * L->pitch - p->y) * p->iv;
+        int wy = p->v > 0.0 && p->iy < L->ny - 1 ? p->iy + 1 : (p->v < 0.0 && p->iy > 0 ? p->iy : -1);
+        if (wy >= 0) {
+            double gap = L->y0 + (double)wy * L->pitch - p->y;
+            t = c->strict ? gap * p->iv : gap / p->v;
+        }
         if (t < 0.0) t = 0.0;
         if (t < best) { best = t; *kind = B_LATY; }
         double xl, yl;
@@ -964,7 +1041,7 @@ static double boundary(const orc_ctx *c, const Particle *p, int *kind, int *whic
         const Cell *uc = &c->cell[p->ucell];
         for (int h = 0; h < uc->nhs; h++) {
             double tt = surf_dist(&c->surf[c->hs_surf[uc->off + h]], c->hs_sense[uc->off + h], xl,
-                                  yl, p->z, p->u, p->v, p->w, p->iu, p->iv, p->iw);
+                                  yl, p->z, p->u, p->v, p->w, p->iu, p->iv, p->iw, c->strict);
             if (tt < best) { best = tt; *kind = B_UNIV; *which = uc->off + h; }
         }
     }
@@ -1035,11 +1112,11 @@ int orc_probe(orc_ctx *c, const double pos[3], const double dir[3], int out_path
 /* ------------------------------------------------------------------------- */
 /* continuous-energy lookup.  Reading: for each nuclide, the interval is the
  * largest grid index j with E_j <= E (binary search, clamped to the last
- * interval); cross sections are linear in E on it, with the interval's
- * reciprocal width rounded once: f = (E - E_j) (1/(E_{j+1} - E_j)),
- * sigma = sigma_j + f (sigma_{j+1} - sigma_j).  Macroscopic values are
- * N_i sigma_i summed in the material's nuclide order; sigma_t,i =
- * (sigma_s + sigma_c) + sigma_f.                                             */
+ * interval); cross sections are linear in E on it (lin-lin interpolation):
+ * f = (E - E_j) / (E_{j+1} - E_j), sigma = sigma_j + f (sigma_{j+1} - sigma_j).
+ * Macroscopic values are N_i sigma_i summed in the material's nuclide order;
+ * sigma_t,i = (sigma_s + sigma_c) + sigma_f.  Strict: the interval's
+ * reciprocal width is rounded once, f = (E - E_j) (1/(E_{j+1} - E_j)).       */
 typedef struct {
     double sigt, nusf;
     double st[16], ss[16], sf[16];
@@ -1064,7 +1141,8 @@ static void ce_lookup(const orc_ctx *c, int mat, double E, CEXS *x)
     for (int k = 0; k < m->n; k++) {
         const Nuclide *u = &c->nuc[m->nuc[k]];
         int j = nuc_interval(u, E);
-        double f = (E - u->E[j]) * (1.0 / (u->E[j + 1] - u->E[j]));
+        double f = c->strict ? (E - u->E[j]) * (1.0 / (u->E[j + 1] - u->E[j]))
+                             : (E - u->E[j]) / (u->E[j + 1] - u->E[j]);
         double ss = u->s[j] + f * (u->s[j + 1] - u->s[j]);
         double sc = u->c[j] + f * (u->c[j + 1] - u->c[j]);
         double sf = u->f[j] + f * (u->f[j + 1] - u->f[j]);
@@ -1075,14 +1153,16 @@ static void ce_lookup(const orc_ctx *c, int mat, double E, CEXS *x)
     }
 }
 
-/* Macroscopic cross sections for a flight.  Reading: every nuclide is lin-lin
- * on each interval of the material's union grid (its own points are union
- * points), so the sums Sigma_t = sum_i N_i sigma_t,i and nuSigma_f are linear
- * there too; they are tabulated at the union points (each per-nuclide value as
- * in ce_lookup, summed in the material's order) and interpolated,
+/* Strict: macroscopic cross sections for a flight come from a per-material
+ * table, as in the CUDA library.  Every nuclide is lin-lin on each interval of
+ * the material's union grid (its own points are union points), so the sums
+ * Sigma_t = sum_i N_i sigma_t,i and nuSigma_f are linear there too; they are
+ * tabulated at the union points (each per-nuclide value as in ce_lookup,
+ * summed in the material's order) and interpolated,
  * Sigma(E) = S_k + ((E - E_k) (1 / (E_k+1 - E_k))) (S_k+1 - S_k), with k the
  * largest union index <= n - 2 whose point is <= E (0 if none).  Equal to the
- * per-nuclide sum in exact arithmetic (and exactly at the union points). */
+ * per-nuclide sum in exact arithmetic (and exactly at the union points); the
+ * plain mode sums the nuclides at the particle's energy instead.            */
 static int dbl_cmp(const void *a, const void *b)
 {
     double x = *(const double *)a, y = *(const double *)b;
@@ -1138,13 +1218,26 @@ static void macro_xs(const orc_ctx *c, int mat, double E, double *sigt, double *
     *nusf = M->Sf[lo] + f * (M->Sf[lo + 1] - M->Sf[lo]);
 }
 
+/* flight cross sections Sigma_t, nuSigma_f of a CE material in the context's mode */
+static void flight_xs(const orc_ctx *c, int mat, double E, double *sigt, double *nusf)
+{
+    if (c->strict) {
+        macro_xs(c, mat, E, sigt, nusf);
+        return;
+    }
+    CEXS x;
+    ce_lookup(c, mat, E, &x);
+    *sigt = x.sigt;
+    *nusf = x.nusf;
+}
+
 int orc_ce_lookup(orc_ctx *c, int material, double E, double out[4])
 {
     if (c->ce != 1 || material < 0 || material >= c->nmc) return fail(c, ORC_EINVAL, "bad material");
     CEXS x;
     ce_lookup(c, material, E, &x);
-    if (!c->macro) build_macro(c);
-    macro_xs(c, material, E, &out[0], &out[1]);
+    if (c->strict && !c->macro) build_macro(c);
+    flight_xs(c, material, E, &out[0], &out[1]);
     double ss = 0.0, sf = 0.0;
     for (int k = 0; k < c->mce[material].n; k++) {
         ss = ss + c->mce[material].dens[k] * x.ss[k];
@@ -1238,21 +1331,26 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
     for (;;) {
         if (p->ncoll + p->ncross >= MAX_EVENTS) { a->capped++; p->fate = FATE_CAPPED; break; }
         /* cross sections at the particle's material and energy */
-        double sigt, mfp, nusf;
+        const int strict = c->strict;
+        double sigt, nusf;
         CEXS x;
         const MatMG *m = NULL;
         if (c->ce) {
-            macro_xs(c, p->mat, p->E, &sigt, &nusf);
-            mfp = sigt > 0.0 ? 1.0 / sigt : INF;
+            flight_xs(c, p->mat, p->E, &sigt, &nusf);
         } else {
             m = &c->mg[p->mat];
             sigt = m->sigt[p->g];
             nusf = m->nusf[p->g];
-            mfp = m->mfp[p->g];
         }
-        /* distance to collision: d_c = -ln(xi) / Sigma_t (a draw is always taken) */
+        /* distance to collision: d_c = -ln(xi) / Sigma_t (a draw is always
+         * taken).  Strict: -ln(xi) times 1/Sigma_t rounded once (per group in
+         * multigroup data, per lookup in continuous energy). */
         uint64_t n = draw_n(&p->s);
-        double dc = sigt > 0.0 ? -log_n(n) * mfp : INF;
+        double dc = INF;
+        if (sigt > 0.0) {
+            if (!strict) dc = -ln_xi(n, 0) / sigt;
+            else dc = -ln_xi(n, 1) * (c->ce ? 1.0 / sigt : m->mfp[p->g]);
+        }
         int kind, which;
         double ds = boundary(c, p, &kind, &which);
         if (!c->time_on && dc == INF && ds == INF) { a->lost++; p->fate = FATE_LOST; break; }
@@ -1263,16 +1361,36 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
         int tcut = 0;
         double ta = p->t, tb = p->t;
         if (c->time_on) {
-            double iv = c->ce ? 1.0 / (c->kv * sqrt(p->E)) : c->invv[p->g];
-            double dt = (c->tcut - p->t) / iv;
-            if (dt < 0.0) dt = 0.0;
-            if (dt < d) { tcut = 1; d = dt; }
-            if (!tcut && d == INF) { a->lost++; p->fate = FATE_LOST; break; }
-            tb = tcut ? c->tcut : fma(d, iv, p->t);
+            /* multigroup: 1/v given per group; continuous energy: v = K sqrt(E).
+             * Plain: flight time d / v, distance to the cutoff (t_cut - t) v.
+             * Strict: 1/v rounded once per flight, (t_cut - t) / (1/v), and the
+             * clock advanced by one fused multiply-add t + d (1/v). */
+            if (c->ce && !strict) {
+                double vel = c->kv * sqrt(p->E);
+                double dt = (c->tcut - p->t) * vel;
+                if (dt < 0.0) dt = 0.0;
+                if (dt < d) { tcut = 1; d = dt; }
+                if (!tcut && d == INF) { a->lost++; p->fate = FATE_LOST; break; }
+                tb = tcut ? c->tcut : p->t + d / vel;
+            } else {
+                double iv = c->ce ? 1.0 / (c->kv * sqrt(p->E)) : c->invv[p->g];
+                double dt = (c->tcut - p->t) / iv;
+                if (dt < 0.0) dt = 0.0;
+                if (dt < d) { tcut = 1; d = dt; }
+                if (!tcut && d == INF) { a->lost++; p->fate = FATE_LOST; break; }
+                tb = tcut ? c->tcut : (strict ? fma(d, iv, p->t) : p->t + d * iv);
+            }
         }
-        p->x = fma(d, p->u, p->x);
-        p->y = fma(d, p->v, p->y);
-        p->z = fma(d, p->w, p->z);
+        /* move: r + d Omega (strict: one fused multiply-add per coordinate) */
+        if (strict) {
+            p->x = fma(d, p->u, p->x);
+            p->y = fma(d, p->v, p->y);
+            p->z = fma(d, p->w, p->z);
+        } else {
+            p->x = p->x + d * p->u;
+            p->y = p->y + d * p->v;
+            p->z = p->z + d * p->w;
+        }
         /* track-length estimators; with time bins, the time spent in each bin
          * over the bin width (population) */
         for (int t = 0; t < c->nt; t++) {
@@ -1285,10 +1403,14 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
             }
             double *row = a->acc[t] + ((size_t)batch * T->nbins * T->ne + (size_t)bin * T->ne + e) *
                                           (size_t)T->ntb;
+            /* overlap of [ta, tb] with the bin over the bin width (strict: times
+             * the width's reciprocal rounded once) */
             for (int k = 0; k < T->ntb; k++) {
                 double lo = ta > T->tedges[k] ? ta : T->tedges[k];
                 double hi = tb < T->tedges[k + 1] ? tb : T->tedges[k + 1];
-                if (lo < hi) row[k] += (hi - lo) * T->tinvw[k];
+                if (lo < hi)
+                    row[k] += strict ? (hi - lo) * T->tinvw[k]
+                                     : (hi - lo) / (T->tedges[k + 1] - T->tedges[k]);
             }
         }
         p->t = tb;
@@ -1310,39 +1432,44 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
         int nfb = p->nfis;
         if (!c->ce) {
             int g = p->g;
-            a->kc += m->mu[g];
-            if (gr) grad_rec(gr, p->mat * G + g, mfp - d, ownb, nfb, pid);
+            const double rsig = 1.0 / sigt;           /* 1/Sigma_t (Sigma_t > 0 here) */
+            const double mu = m->nusf[g] / sigt;      /* expected fission sites */
+            const double mufl = floor(mu), mufr = mu - mufl;
+            a->kc += mu;
+            if (gr) grad_rec(gr, p->mat * G + g, rsig - d, ownb, nfb, pid);
             /* fission sites: floor(mu) + [xi <= frac(mu)], mu = nuSigma_f/Sigma_t.
              * Reading: no division by k; the population is controlled by resampling. */
             double xi = draw(&p->s);
-            int nf = (int)m->mufl[g] + (xi <= m->mufr[g] ? 1 : 0);
-            if (gr && m->nusf[g] != 0.0 && m->mufr[g] != 0.0) {
-                double fac = nf > (int)m->mufl[g] ? 1.0 / m->mufr[g] : -1.0 / (1.0 - m->mufr[g]);
+            int nf = (int)mufl + (xi <= mufr ? 1 : 0);
+            if (gr && m->nusf[g] != 0.0 && mufr != 0.0) {
+                double fac = nf > (int)mufl ? 1.0 / mufr : -1.0 / (1.0 - mufr);
                 int nm = c->nm;
-                grad_rec(gr, nm * G + nm * G * G + p->mat * G + g, mfp * fac, ownb, nfb, pid);
-                grad_rec(gr, p->mat * G + g, -(m->mu[g] * mfp) * fac, ownb, nfb, pid);
+                grad_rec(gr, nm * G + nm * G * G + p->mat * G + g, rsig * fac, ownb, nfb, pid);
+                grad_rec(gr, p->mat * G + g, -(mu * rsig) * fac, ownb, nfb, pid);
             }
             for (int k = 0; k < nf; k++) { bank_push(a, p); p->nfis++; }
-            /* analog reaction: scatter with probability Sigma_s,tot / Sigma_t */
+            /* analog reaction: scatter with probability Sigma_s,tot / Sigma_t, i.e.
+             * when xi Sigma_t <= Sigma_s,tot (strict: xi <= the ratio rounded once) */
             xi = draw(&p->s);
-            if (xi <= m->ps[g]) {
+            int scatter = strict ? xi <= m->ps[g] : xi * sigt <= m->stot[g];
+            if (scatter) {
                 xi = draw(&p->s);
-                int gp = sample_cdf(&m->scdf[g * G], G, xi);
+                int gp = sample_discrete(&m->sigs[g * G], m->stot[g], &m->scdf[g * G], G, xi, strict);
                 if (gr) {
                     int nm = c->nm;
                     grad_rec(gr, nm * G + (p->mat * G + g) * G + gp, 1.0 / m->sigs[g * G + gp], ownb,
                              nfb, pid);
-                    grad_rec(gr, p->mat * G + g, -mfp, ownb, nfb, pid);
+                    grad_rec(gr, p->mat * G + g, -rsig, ownb, nfb, pid);
                 }
                 p->g = gp;
-                iso_dir(&p->s, &p->u, &p->v, &p->w);   /* isotropic (P0) scattering */
+                iso_dir(&p->s, &p->u, &p->v, &p->w, strict);   /* isotropic (P0) scattering */
                 set_recip(p);
             } else {
                 if (gr) {
                     double sa = m->sigt[g] - m->stot[g];
                     if (sa > 0.0) {
                         int nm = c->nm;
-                        grad_rec(gr, p->mat * G + g, 1.0 / sa - mfp, ownb, nfb, pid);
+                        grad_rec(gr, p->mat * G + g, 1.0 / sa - rsig, ownb, nfb, pid);
                         for (int h = 0; h < G; h++)
                             if (m->sigs[g * G + h] != 0.0)
                                 grad_rec(gr, nm * G + (p->mat * G + g) * G + h, -1.0 / sa, ownb, nfb,
@@ -1373,9 +1500,9 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
             xi = draw(&p->s);
             if (xi * x.st[sel] <= x.ss[sel]) {
                 if (c->fg_kT > 0.0 && p->E < c->fg_emax)
-                    p->E = free_gas(p->E, u->A, c->fg_kT, &p->s, &p->u, &p->v, &p->w);
+                    p->E = free_gas(p->E, u->A, c->fg_kT, &p->s, &p->u, &p->v, &p->w, strict);
                 else
-                    p->E = elastic(p->E, u->A, &p->s, &p->u, &p->v, &p->w);
+                    p->E = elastic(p->E, u->A, &p->s, &p->u, &p->v, &p->w, strict);
                 set_recip(p);
             } else {
                 p->alive = 0;
@@ -1393,8 +1520,12 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
 /* sources                                                                    */
 static int birth_energy(const orc_ctx *c, Particle *p)
 {
-    if (c->ce) p->E = maxwell(&p->s);
-    else p->g = sample_cdf(c->mg[p->mat].chicdf, c->G, draw(&p->s));
+    if (c->ce) {
+        p->E = maxwell(&p->s, c->strict);
+    } else {
+        const MatMG *m = &c->mg[p->mat];
+        p->g = sample_discrete(m->chi, m->chitot[0], m->chicdf, c->G, draw(&p->s), c->strict);
+    }
     return 0;
 }
 
@@ -1426,12 +1557,14 @@ static int sample_source(const orc_ctx *c, Particle *p)
     }
     switch (s->ekind) {
     case ORC_E_CHI: birth_energy(c, p); break;
-    case ORC_E_PDF: p->g = sample_cdf(s->ecdf, s->ne, draw(&p->s)); break;
+    case ORC_E_PDF:
+        p->g = sample_discrete(s->edata, s->etot, s->ecdf, s->ne, draw(&p->s), c->strict);
+        break;
     case ORC_E_FIXED: p->E = s->edata[0]; break;
-    default: p->E = maxwell(&p->s);
+    default: p->E = maxwell(&p->s, c->strict);
     }
     if (s->dkind == ORC_DIR_BEAM) { p->u = s->beam[0]; p->v = s->beam[1]; p->w = s->beam[2]; }
-    else iso_dir(&p->s, &p->u, &p->v, &p->w);
+    else iso_dir(&p->s, &p->u, &p->v, &p->w, c->strict);
     set_recip(p);
     return 0;
 }
@@ -1441,7 +1574,7 @@ static void from_site(const orc_ctx *c, Particle *p, const Site *b)
     p->x = b->x; p->y = b->y; p->z = b->z; p->t = b->t;
     p->cell = b->cell; p->ix = b->ix; p->iy = b->iy; p->ucell = b->ucell; p->mat = b->mat;
     birth_energy(c, p);
-    iso_dir(&p->s, &p->u, &p->v, &p->w);
+    iso_dir(&p->s, &p->u, &p->v, &p->w, c->strict);
     set_recip(p);
 }
 
@@ -1468,7 +1601,7 @@ static int prepare(orc_ctx *c)
         if (c->ce && T->nedges < 2) return fail(c, ORC_EINVAL, "CE tally needs energy edges");
     }
     if (c->time_on && !c->ce && !c->invv) return fail(c, ORC_ESTATE, "no inverse speeds");
-    if (c->ce) build_macro(c);
+    if (c->ce && c->strict) build_macro(c);
     c->kv = sqrt(2.0 * 1.602176634e-19 / 1.67492749804e-27) * 100.0;
     free_results(c);
     memset(c->counters, 0, sizeof c->counters);
@@ -1577,8 +1710,8 @@ static void mean_sd(double sum, double sum2, int n, double *mean, double *sd)
 /* Power iteration (Sec. 4 runs 50 inactive + 100 active cycles).  Reading:
  * cycle c's particle j uses stream c 2^32 + j; after a cycle the bank (sorted
  * by parent and child) of M sites is resampled systematically to N:
- * site j <- bank[floor((j + xi) M / N)], xi the first draw of stream
- * c 2^32 + 2^32 - 1.  Per cycle k_analog = M/N, k_TL = sum d nuSigma_f / N,
+ * site j <- bank[floor((j + xi) M / N)] (orc_site_index), xi the first draw of
+ * stream c 2^32 + 2^32 - 1.  Per cycle k_analog = M/N, k_TL = sum d nuSigma_f / N,
  * k_C = sum nuSigma_f/Sigma_t / N; k and tallies are means over active
  * cycles with sd = s / sqrt(n_active).                                        */
 int orc_run_eigen(orc_ctx *c, int64_t n, int inactive, int active, uint64_t seed, int threads)
@@ -1649,12 +1782,8 @@ int orc_run_eigen(orc_ctx *c, int64_t n, int inactive, int active, uint64_t seed
         if (cyc == ncyc - 1) record_histories(c, P, n);
         if (M == 0) { err = fail(c, ORC_ESTATE, "fission bank empty after cycle %d", cyc); break; }
         uint64_t rs = orc_rng_stream(seed, ((uint64_t)cyc << 32) + 0xFFFFFFFFULL);
-        double xi = draw(&rs);
-        for (int64_t j = 0; j < n; j++) {
-            double t = ((double)j + xi) * (double)M / (double)n;
-            int64_t idx = (int64_t)t;
-            site[j] = idx >= M ? M - 1 : idx;
-        }
+        uint64_t xn = draw_n(&rs);
+        for (int64_t j = 0; j < n; j++) site[j] = orc_site_index(j, xn, M, n);
     }
     if (!err) {
         for (int q = 0; q < 3; q++) mean_sd(ks[q], ks2[q], active, &c->k[2 * q], &c->k[2 * q + 1]);

@@ -14,6 +14,16 @@
  * so each step follows the textbook algorithm; every choice the paper leaves
  * open is stated where the code makes it.
  *
+ * Two arithmetic modes.  PLAIN (the default) evaluates every step as its
+ * definition is written: ln from libm, distances by true division, no fused
+ * multiply-adds, continuous-energy cross sections as the sum over nuclides of
+ * N_i sigma_i(E), sampling against unnormalised partial sums.  STRICT follows
+ * the rounding conventions the CUDA library chose for speed (a table-driven
+ * logarithm, carried direction reciprocals, explicit fused multiply-adds,
+ * per-material macroscopic tables), so that histories can be compared bit for
+ * bit; every such convention is marked "Strict:" where it is made.  Both modes
+ * take the same random draws in the same order.
+ *
  * All functions return 0 on success or a negative code; orc_error() gives a
  * message.  Arrays passed in are copied.  Output arrays are caller-owned.
  */
@@ -38,9 +48,13 @@ enum { ORC_E_CHI = 0, ORC_E_PDF = 1, ORC_E_FIXED = 2, ORC_E_MAXWELL = 3 };
 enum { ORC_DIR_ISO = 0, ORC_DIR_BEAM = 1 };
 enum { ORC_FILTER_CELL = 0, ORC_FILTER_LATTICE = 1, ORC_FILTER_MATERIAL = 2 };
 
+enum { ORC_PLAIN = 0, ORC_STRICT = 1 };
+
 orc_ctx *orc_create(void);
 void orc_destroy(orc_ctx *c);
 const char *orc_error(const orc_ctx *c);
+/* arithmetic mode of the context's runs (ORC_PLAIN, the default, or ORC_STRICT) */
+int orc_set_arith(orc_ctx *c, int mode);
 
 /* geometry */
 int orc_add_surface(orc_ctx *c, int type, const double coef[4], int bc);
@@ -110,16 +124,23 @@ int orc_get_bank(const orc_ctx *c, double *xyz, int64_t *parent, int32_t *child,
 int orc_grad_fixed(orc_ctx *c, int64_t n, uint64_t seed, int cell, const double *weights,
                    double *d_sigt, double *d_sigs, double *d_nusf, double *tally);
 
-/* building blocks exposed for the pin tests */
+/* building blocks exposed for the pin tests; `mode` is ORC_PLAIN or ORC_STRICT */
 uint64_t orc_rng_skip(uint64_t s, uint64_t n);
 uint64_t orc_rng_stream(uint64_t seed, uint64_t id);
 uint64_t orc_rng_next(uint64_t s);
 double orc_rng_xi(uint64_t s);
+/* ln xi by the strict mode's table-driven method (xi in (0, 1]) */
 double orc_log(double xi);
-int orc_iso_dir(uint64_t *s, double out[3]);
-int orc_elastic(double E, double A, const double dir[3], uint64_t *s, double out[4]);
-int orc_free_gas(double E, double A, double kT, const double dir[3], uint64_t *s, double out[4]);
-double orc_maxwell(uint64_t *s);
+/* entry j (0..255) of that method's table of ln(1 + j/256) */
+double orc_log_table(int j);
+/* index of the bank site that source j of N takes after a cycle banked M sites,
+ * for the resampling draw xi = n 2^-53 (n in [1, 2^53]) */
+int64_t orc_site_index(int64_t j, uint64_t n, int64_t M, int64_t N);
+int orc_iso_dir(uint64_t *s, double out[3], int mode);
+int orc_elastic(double E, double A, const double dir[3], uint64_t *s, double out[4], int mode);
+int orc_free_gas(double E, double A, double kT, const double dir[3], uint64_t *s, double out[4],
+                 int mode);
+double orc_maxwell(uint64_t *s, int mode);
 int orc_probe(orc_ctx *c, const double pos[3], const double dir[3], int out_path[5],
               double *dist, int *kind);
 int orc_ce_lookup(orc_ctx *c, int material, double E, double out[4]);

@@ -461,6 +461,15 @@ static int check_lost(mcgb_ctx *c)
 
 // ---------------------------------------------------------------------------
 // k-eigenvalue power iteration, stepwise: begin, any number of cycles, finish.
+static void drop_cycle_graphs(mcgb_ctx *c)
+{
+    for (int q = 0; q < 2; q++)
+        if (c->graph[q]) {
+            cudaGraphExecDestroy(c->graph[q]);
+            c->graph[q] = nullptr;
+        }
+}
+
 static int eigen_begin(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_t seed)
 {
     if (N <= 0 || N > (int64_t)1 << 30 || active < 1 || inactive < 0 || inactive + active > 4096)
@@ -502,11 +511,7 @@ static int eigen_begin(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_
     e.cur = 0;
     e.seed = c->world->probs[0].seed;
     // device copies for graph replay: the resampling draw of every cycle, bank sizes
-    for (int q = 0; q < 2; q++)
-        if (c->graph[q]) {
-            cudaGraphExecDestroy(c->graph[q]);
-            c->graph[q] = nullptr;
-        }
+    drop_cycle_graphs(c);
     c->gmem.release();
     CKR(c->gmem.get(c->cyc_dev, 1));
     CKR(c->gmem.get(c->xi_dev, ncyc));
@@ -535,7 +540,18 @@ static int eigen_begin(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_
 // statistics) as a graph per bank parity; the cycle index, its resampling
 // draw and the active flag are read on the device, and the graph's last
 // kernel records the bank size and advances the cycle index.
+static int capture_cycle_graphs(mcgb_ctx *c);
+
+// Both cycle graphs, or neither: a failed capture or instantiation leaves no
+// graph behind, so the next call captures again from the start.
 static int build_cycle_graphs(mcgb_ctx *c)
+{
+    int rc = capture_cycle_graphs(c);
+    if (rc != MCGB_OK) drop_cycle_graphs(c);
+    return rc;
+}
+
+static int capture_cycle_graphs(mcgb_ctx *c)
 {
     EigenRun &e = c->eig;
     RunState &r = c->rs;
@@ -605,7 +621,7 @@ static int eigen_cycles(mcgb_ctx *c, int k)
     int64_t N = e.N;
     // cycles after the first: graph launches back to back, checked once at the end
     if (use_graphs(c) && e.cyc >= 1 && k > 0 && e.cyc < e.ncyc) {
-        if (!c->graph[0]) CKR(build_cycle_graphs(c));
+        if (!c->graph[0] || !c->graph[1]) CKR(build_cycle_graphs(c));
         int first = e.cyc;
         CK(cudaMemcpyAsync(c->cyc_dev, c->pinned_cyc + first, sizeof(int), cudaMemcpyHostToDevice, st));
         int last = std::min(e.ncyc, first + k);
@@ -673,8 +689,10 @@ static int eigen_cycles(mcgb_ctx *c, int k)
         c->launches += 7;
         CK(cudaEventRecord(ev2, st));
         CK(cudaGetLastError());
-        // the later cycles' graphs are captured while the first cycle runs
-        if (cyc == 0 && use_graphs(c) && !c->graph[0] && e.ncyc > 1) CKR(build_cycle_graphs(c));
+        // the later cycles' graphs are captured while the first cycle runs; a
+        // failed capture is reported once this cycle's results are recorded
+        int graph_rc = MCGB_OK;
+        if (cyc == 0 && use_graphs(c) && !c->graph[0] && e.ncyc > 1) graph_rc = build_cycle_graphs(c);
         int64_t M;
         int err;
         CKR(read_flags(c, M, err));
@@ -702,6 +720,7 @@ static int eigen_cycles(mcgb_ctx *c, int k)
             return fail(MCGB_E_STATE, "fission bank empty after cycle " + std::to_string(cyc));
         }
         e.cur = nxt;
+        if (graph_rc != MCGB_OK) return graph_rc;
     }
     return MCGB_OK;
 }

@@ -17,14 +17,55 @@ namespace mcgb {
 
 static const double LN2 = 0x1.62e42fefa39efp-1;
 
-// ln c = 2 atanh((c - 1)/(c + 1)) by its series, 40 terms (c in [1, 2]).
-double ln_series(double c)
+// Double-double numbers hi + lo (|lo| <= half an ulp of hi) for the table of
+// the logarithm: Knuth's two-sum, the exact product by a fused multiply-add,
+// and division by long division in double-double.
+struct DD {
+    double hi, lo;
+};
+
+static DD dd_fast(double a, double b)   // |a| >= |b|: a + b exactly as hi + lo
 {
-    double s = (c - 1.0) / (c + 1.0);
-    double z = s * s;
-    double p = 1.0 / 79.0;
-    for (int k = 38; k >= 0; k--) p = p * z + 1.0 / (double)(2 * k + 1);
-    return 2.0 * s * p;
+    double s = a + b;
+    return {s, b - (s - a)};
+}
+
+static DD dd_add(DD a, DD b)
+{
+    double s = a.hi + b.hi;
+    double v = s - a.hi;
+    double e = (a.hi - (s - v)) + (b.hi - v);
+    return dd_fast(s, e + (a.lo + b.lo));
+}
+
+static DD dd_mul(DD a, DD b)
+{
+    double p = a.hi * b.hi;
+    double e = std::fma(a.hi, b.hi, -p);
+    return dd_fast(p, e + (a.hi * b.lo + a.lo * b.hi));
+}
+
+static DD dd_div(DD a, DD b)
+{
+    double q1 = a.hi / b.hi;
+    DD r = dd_add(a, dd_mul(b, DD{-q1, 0.0}));
+    double q2 = r.hi / b.hi;
+    r = dd_add(r, dd_mul(b, DD{-q2, 0.0}));
+    double q3 = r.hi / b.hi;
+    return dd_add(dd_fast(q1, q2), DD{q3, 0.0});
+}
+
+// ln(1 + j/256) correctly rounded: 2 atanh(s), s = j / (512 + j), summed as
+// s (1 + s^2/3 + s^4/5 + ...) in double-double (s <= 1/3: 40 terms leave
+// less than 1e-38), then rounded once.
+double ln_table_entry(int j)
+{
+    DD s = dd_div(DD{(double)j, 0.0}, DD{512.0 + (double)j, 0.0});
+    DD z = dd_mul(s, s);
+    DD p{0.0, 0.0};
+    for (int k = 39; k >= 0; k--) p = dd_add(dd_mul(p, z), dd_div(DD{1.0, 0.0}, DD{2.0 * k + 1.0, 0.0}));
+    DD r = dd_mul(dd_mul(DD{2.0, 0.0}, s), p);
+    return r.hi + r.lo;
 }
 
 // Partial sums in order divided by the total; the last entry is exactly 1.
@@ -333,8 +374,9 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     std::vector<int> u_edge(nuniv, -1);
     // c_inner: a universe cell inside (sense -1) a cylinder or sphere that lies
     // strictly inside every lattice element holding the universe (same margin):
-    // a particle there leaves that surface before it can reach a lattice wall or
-    // a root plane beyond it, so those distances never win and are not computed.
+    // a particle there leaves that surface before it can reach a lattice wall,
+    // so those distances never win and are not computed (root surfaces are
+    // skipped only where c_rootfar below proves it too).
     std::vector<int> c_inner(c_univ.size(), 0);
     {
         std::vector<double> upitch(nuniv, 0.0);   // smallest pitch of a lattice using U
@@ -414,6 +456,30 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
         c_skiproot[c] = ok ? 1 : 0;
         if (ok)
             for (int h = 0; h < c_nhs[c]; h++) hs_side[c_off[c] + h] = side[h];
+    }
+    // Root cells filled by a lattice whose half-spaces are all x / y planes
+    // lying on or outside the lattice's outer edges (within 1e-7 pitch): a
+    // particle in an inner cell (inside a cylinder or sphere at least 5e-7
+    // pitch inside its element) leaves that convex surface before it can reach
+    // such a plane, so from inner cells of these root cells no root surface
+    // is evaluated.  Any other root boundary (a z-plane, a plane cutting the
+    // lattice's elements) is evaluated from inner cells as from any other.
+    std::vector<int> c_rootfar(c_univ.size(), 0);
+    for (size_t c = 0; c < c_univ.size(); c++) {
+        if (c_fillk[c] != FILL_LAT) continue;
+        int L = c_fill[c];
+        double p = l_pitch[L], m = 1e-7 * p;
+        double xl = l_x0[L], xh = l_x0[L] + (double)l_nx[L] * p;
+        double yl = l_y0[L], yh = l_y0[L] + (double)l_ny[L] * p;
+        bool ok = true;
+        for (int h = 0; h < c_nhs[c] && ok; h++) {
+            int sid = hs_surf[c_off[c] + h];
+            double v = s_coef[4 * sid];
+            if (s_type[sid] == SURF_PX) ok = v <= xl + m || v >= xh - m;
+            else if (s_type[sid] == SURF_PY) ok = v <= yl + m || v >= yh - m;
+            else ok = false;
+        }
+        c_rootfar[c] = ok ? 1 : 0;
     }
     // candidates across each half-space: cells of the same universe bounded by
     // the same surface with the opposite sense, in definition order
@@ -560,7 +626,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     std::vector<double> logtab(256), rinvtab(256), etab(64);
     for (int j = 0; j < 256; j++) {
         double c = 1.0 + (double)j / 256.0;
-        logtab[j] = ln_series(c);
+        logtab[j] = ln_table_entry(j);
         rinvtab[j] = 1.0 / c;
     }
     for (int e = 0; e < 64; e++) etab[e] = (double)(e - 53) * LN2;
@@ -576,7 +642,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     size_t o_hssurf = S.put(hs_surf), o_hssense = S.put(hs_sense), o_hscoff = S.put(hs_coff),
            o_hscand = S.put(hs_cand), o_uoff = S.put(u_off), o_ucells = S.put(u_cells),
            o_uedge = S.put(u_edge), o_cskip = S.put(c_skiproot), o_hsside = S.put(hs_side),
-           o_cinner = S.put(c_inner);
+           o_cinner = S.put(c_inner), o_crootfar = S.put(c_rootfar);
     size_t o_lx0 = S.put(l_x0), o_ly0 = S.put(l_y0), o_lp = S.put(l_pitch), o_lnx = S.put(l_nx),
            o_lny = S.put(l_ny), o_luoff = S.put(l_uoff), o_luniv = S.put(l_univ),
            o_lwoff = S.put(l_woff), o_lwall = S.put(l_wall), o_lctr = S.put(l_ctr);
@@ -625,6 +691,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(c_skiproot, int, o_cskip);
     P_(hs_side, int, o_hsside);
     P_(c_inner, int, o_cinner);
+    P_(c_rootfar, int, o_crootfar);
     P_(l_x0, double, o_lx0); P_(l_y0, double, o_ly0); P_(l_pitch, double, o_lp);
     P_(l_nx, int, o_lnx); P_(l_ny, int, o_lny); P_(l_uoff, int, o_luoff); P_(l_univ, int, o_luniv);
     P_(l_woff, int, o_lwoff); P_(l_wall, double, o_lwall); P_(l_ctr, double, o_lctr);

@@ -89,7 +89,7 @@ struct DeviceWorld {
 std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cudaStream_t st);
 
 // Host-side tables identical to the device ones (shared with the checks).
-double ln_series(double c);
+double ln_table_entry(int j);
 void make_cdf(const double *w, int n, double *cdf);
 
 }  // namespace mcgb

@@ -583,10 +583,13 @@ __device__ __forceinline__ double boundary(const World &W, const PS &p, int &kin
     // strictly nearer (proven per cell when the world is built)
     unsigned sides = 0xFu;
     const bool skip = __ldg(W.c_skiproot + p.cell) != 0;
-    // inside a surface strictly inside the element: only that cell's surfaces
+    // inside a surface strictly inside the element: no lattice wall is reached
+    // first, and no root surface either when all of them lie on or beyond the
+    // lattice's edges
     const bool inner = p.ucell >= 0 && __ldg(W.c_inner + p.ucell) != 0;
-    if (inner) nh = 0;
-    if (skip && !inner) {
+    if (inner && __ldg(W.c_rootfar + p.cell) != 0) {
+        nh = 0;
+    } else if (skip) {
         int L = __ldg(W.c_fill + p.cell);
         sides = (p.ix == 0 ? 1u : 0u) | (p.ix == __ldg(W.l_nx + L) - 1 ? 2u : 0u) |
                 (p.iy == 0 ? 4u : 0u) | (p.iy == __ldg(W.l_ny + L) - 1 ? 8u : 0u);

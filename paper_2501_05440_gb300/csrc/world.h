@@ -79,6 +79,7 @@ struct World {
     const int *c_skiproot;          // lattice root cell whose planes interior elements never reach first
     const int *hs_side;             // per half-space of such a cell: lattice side of its plane (1..4)
     const int *c_inner;             // universe cell inside a surface strictly inside its element
+    const int *c_rootfar;           // lattice root cell whose surfaces are planes on or beyond the lattice's edges
     // lattices; wall and centre coordinates are precomputed with the same
     // expressions the transport would evaluate: x0 + (double)i * pitch and
     // x0 + ((double)i + 0.5) * pitch (bit-identical, fewer FP64 instructions)

@@ -15,14 +15,16 @@ import oracle  # noqa: E402
 import workloads as W  # noqa: E402
 
 
-def pin_cell_small():
+def pin_cell_small(strict=False):
     pb = W.pin_cell_mg(n=1000, inactive=2, active=3)
-    o = oracle.Oracle(pb).run(threads=1)
+    o = oracle.Oracle(pb, strict=strict).run(threads=1)
     ktl, kc, m = o.cycle_k(5)
     h = o.histories()
     b = o.bank()
+    mode = "strict" if strict else "plain"
     return {
-        "what": "oracle, multigroup pin cell (seed 1), 1000 particles/cycle, 2+3 cycles, 1 thread",
+        "what": f"oracle ({mode} arithmetic), multigroup pin cell (seed 1), 1000 particles/cycle, "
+                "2+3 cycles, 1 thread",
         "bank_size": m.tolist(), "k_tl": ktl.tolist(), "k_col": kc.tolist(),
         "rng_end_first16": [int(v) for v in h["rng_end"][:16]],
         "n_coll_first16": h["n_coll"][:16].tolist(), "n_cross_first16": h["n_cross"][:16].tolist(),
@@ -45,5 +47,7 @@ def rng_words():
 if __name__ == "__main__":
     with open(os.path.join(HERE, "oracle_pin_cell_small.json"), "w") as f:
         json.dump(pin_cell_small(), f, indent=1)
+    with open(os.path.join(HERE, "oracle_pin_cell_small_strict.json"), "w") as f:
+        json.dump(pin_cell_small(strict=True), f, indent=1)
     with open(os.path.join(HERE, "oracle_rng_words.json"), "w") as f:
         json.dump(rng_words(), f, indent=1)

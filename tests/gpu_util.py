@@ -13,8 +13,10 @@ def gpu_run(pb, mode=0, record=True, pool=0, graphs=0, **over):
     return c
 
 
-def oracle_run(pb, threads=0, **over):
-    return Oracle(pb).run(threads=threads, **over)
+def oracle_run(pb, threads=0, strict=True, **over):
+    """The oracle on the same problem; strict (the CUDA library's rounding
+    conventions) for bit-for-bit comparisons, plain for tolerance ones."""
+    return Oracle(pb, strict=strict).run(threads=threads, **over)
 
 
 def assert_same_histories(hg, ho):

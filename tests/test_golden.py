@@ -4,6 +4,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 import workloads as W
 
@@ -27,9 +28,10 @@ def test_table1_core_equivalency():
     assert abs(core_equivalency(112, 5080.0, 4, mi300["c5g7_runtime_s"]) - 362) > 30
 
 
-def test_oracle_regression_record(orc):
-    ref = _load("oracle_pin_cell_small.json")
-    o = orc.Oracle(W.pin_cell_mg(n=1000, inactive=2, active=3)).run(threads=1)
+@pytest.mark.parametrize("strict", [False, True])
+def test_oracle_regression_record(orc, strict):
+    ref = _load("oracle_pin_cell_small_strict.json" if strict else "oracle_pin_cell_small.json")
+    o = orc.Oracle(W.pin_cell_mg(n=1000, inactive=2, active=3), strict=strict).run(threads=1)
     ktl, kc, m = o.cycle_k(5)
     assert m.tolist() == ref["bank_size"]
     assert ktl.tolist() == ref["k_tl"] and kc.tolist() == ref["k_col"]
@@ -38,7 +40,7 @@ def test_oracle_regression_record(orc):
     assert h["n_coll"][:16].tolist() == ref["n_coll_first16"]
     assert np.array_equal(o.bank()["xyz"][:4], np.array(ref["bank_xyz_first4"]))
     # thread count changes only summation order, never histories or banks
-    o4 = orc.Oracle(W.pin_cell_mg(n=1000, inactive=2, active=3)).run(threads=4)
+    o4 = orc.Oracle(W.pin_cell_mg(n=1000, inactive=2, active=3), strict=strict).run(threads=4)
     assert o4.cycle_k(5)[2].tolist() == ref["bank_size"]
 
 

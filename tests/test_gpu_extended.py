@@ -32,7 +32,7 @@ def test_replay_derivatives_match_oracle(mcgb, mode, pool):
     c = mcgb.load_problem(mcgb.Context(mode=mode, pool=pool), pb)
     tally = c.forward_fixed(n, seed, det)
     g = c.backward_fixed(w, nm)
-    o = Oracle(pb).grad(n=n, seed=seed, cell=det, weights=w)
+    o = Oracle(pb, strict=True).grad(n=n, seed=seed, cell=det, weights=w)
     assert rel_close(tally, o["tally"], 1e-9, 1e-300)
     for key in ["sigma_t", "sigma_s", "nu_sigma_f"]:
         assert _close_vec(g[key], o[key], 1e-8), key
@@ -43,7 +43,7 @@ def test_replay_derivatives_match_oracle(mcgb, mode, pool):
     # a second backward with other weights on the same forward pass
     w2 = np.ones(G)
     g2 = c.backward_fixed(w2, nm)
-    o2 = Oracle(pb).grad(n=n, seed=seed, cell=det, weights=w2)
+    o2 = Oracle(pb, strict=True).grad(n=n, seed=seed, cell=det, weights=w2)
     assert _close_vec(g2["sigma_t"], o2["sigma_t"], 1e-8)
 
 
@@ -73,7 +73,7 @@ def test_autograd_function(mcgb):
     y = detector_tally(pb, st, ss, nf, n, seed, det)
     c = torch.linspace(0.5, 1.5, pb["G"], dtype=torch.float64)
     (y * c).sum().backward()
-    o = Oracle(pb).grad(n=n, seed=seed, cell=det, weights=c.numpy())
+    o = Oracle(pb, strict=True).grad(n=n, seed=seed, cell=det, weights=c.numpy())
     assert rel_close(y.detach().numpy(), o["tally"], 1e-9, 1e-300)
     assert _close_vec(st.grad.numpy(), o["sigma_t"], 1e-8)
     assert _close_vec(ss.grad.numpy(), o["sigma_s"], 1e-8)
@@ -94,7 +94,7 @@ def test_batch_equals_standalone_runs(mcgb, pool):
         c.run()
         bm, bs = b.tally(i)
         cm, cs = c.get_tally()
-        om, osd = Oracle(p).run().tally()
+        om, osd = Oracle(p, strict=True).run().tally()
         assert rel_close(bm, cm, 1e-9, 1e-300) and rel_close(bm, om, 1e-9, 1e-300), i
     cnt = b.counters()
     assert cnt["histories"] >= sum(p["run"]["n"] for p in probs)
@@ -124,7 +124,7 @@ def test_full_size_first_cycle_sampled(mcgb, name):
     assert len(h["n_coll"]) == 1_000_000
     idx = np.sort(np.random.default_rng(3).choice(1_000_000, 1500 if name == "lattice" else 400,
                                                   replace=False))
-    ho = Oracle(pb).histories_by_index(idx)
+    ho = Oracle(pb, strict=True).histories_by_index(idx)
     assert_same_histories({k: v[idx] for k, v in h.items()}, ho)
     # properties at full size: the bank holds exactly the sites the histories counted
     assert int(h["n_fis"].sum()) == c.get_cycle_k(1)[2][0]
@@ -182,7 +182,7 @@ def test_degenerate_sizes(mcgb):
             except mcgb.McgbError as e:
                 g_err = e.code
             try:
-                o = Oracle(pb).run()
+                o = Oracle(pb, strict=True).run()
             except OracleError:
                 o_err = -2
             assert g_err == o_err, (n, seed, mode, g_err, o_err)
@@ -192,7 +192,7 @@ def test_degenerate_sizes(mcgb):
     # one source history, fixed source
     pb = W.diff_slab(n=1, batches=1)
     c = gpu_run(pb, mode=1)
-    o = Oracle(pb).run()
+    o = Oracle(pb, strict=True).run()
     assert_same_histories(c.get_histories(), o.histories())
     # no tallies at all
     pb = W.pin_cell_mg(n=500, inactive=0, active=2)

@@ -61,7 +61,7 @@ def test_geometry_probe_bit_exact(mcgb, name):
     pb = {"pin": W.pin_cell_mg(n=10), "lattice": W.c5g7_like_lattice(n=10),
           "slab": W.diff_slab(n=10), "box": W.batch_boxes(nproblems=2)[1]}[name]
     c = mcgb.load_problem(mcgb.Context(), pb)
-    o = Oracle(pb)
+    o = Oracle(pb, strict=True)
     xs = [s["coef"][0] for s in pb["surfaces"] if s["type"] == "px"]
     ys = [s["coef"][0] for s in pb["surfaces"] if s["type"] == "py"]
     zs = [s["coef"][0] for s in pb["surfaces"] if s["type"] == "pz"] or [-3.0, 3.0]
@@ -81,7 +81,7 @@ def test_geometry_probe_bit_exact(mcgb, name):
 def test_ce_lookup_bit_exact(mcgb):
     pb = W.ce_pin_cell(n=10, npts=5000, nres=30)
     c = mcgb.load_problem(mcgb.Context(), pb)
-    o = Oracle(pb)
+    o = Oracle(pb, strict=True)
     rng = np.random.default_rng(8)
     E = np.exp(rng.uniform(np.log(1e-5), np.log(2e7), 4000))
     E = np.concatenate([E, pb["nuclides"][3]["E"][::97], [1e-5, 2e7]])
@@ -208,4 +208,25 @@ def test_lattice_tight_pins_parity(mcgb, radius, mode, pool, graphs):
     oracle's, which always evaluates every surface."""
     pb = W.c5g7_like_lattice(n=4000, inactive=2, active=3)
     pb["surfaces"][4]["coef"][2] = radius
+    _eigen_parity(mcgb, pb, mode, pool, graphs)
+
+
+# Root boundaries that reach inside the lattice's elements: z-planes bounding a
+# lattice of finite height, and a reflective x-plane through the first column's
+# pin centres.  A particle in a fuel pin can reach them before it leaves the
+# pin.  Radius 0.54: the fuel cell is inside its element, so its flights skip
+# the lattice walls (and root surfaces only where none of them cuts an
+# element); radius 0.63 touches the element and nothing is skipped.
+SMALL_LATTICES = {
+    "z-planes": dict(z_planes=(-3.0, 3.0, "reflect", "vacuum")),
+    "x-plane-through-pins": dict(x_plane=(0.63, "reflect")),
+    "both": dict(x_plane=(0.63, "reflect"), z_planes=(-2.0, 2.0, "vacuum", "reflect")),
+}
+
+
+@pytest.mark.parametrize("radius", [0.54, 0.63])
+@pytest.mark.parametrize("name", sorted(SMALL_LATTICES))
+@pytest.mark.parametrize("mode,pool,graphs", [(0, 0, 0), (1, 0, 0), (2, 0, 0)])
+def test_lattice_root_boundaries_inside_elements(mcgb, name, radius, mode, pool, graphs):
+    pb = W.small_lattice(n=4000, inactive=2, active=3, r=radius, **SMALL_LATTICES[name])
     _eigen_parity(mcgb, pb, mode, pool, graphs)

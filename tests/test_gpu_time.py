@@ -124,7 +124,7 @@ def test_ce_time_pin_full_size_sampled(mcgb):
     h = c.get_histories()
     assert len(h["n_coll"]) == 1_000_000
     idx = np.sort(np.random.default_rng(5).choice(1_000_000, 300, replace=False))
-    ho = Oracle(pb).histories_by_index(idx)
+    ho = Oracle(pb, strict=True).histories_by_index(idx)
     assert_same_histories({k: v[idx] for k, v in h.items()}, ho)
     assert set(np.unique(h["fate"]).tolist()) <= {0, 5}
     cnt = c.get_counters()
@@ -152,6 +152,6 @@ def test_batch_mixing_time_and_static_problems(mcgb, pool):
         c.run()
         bm, _ = b.tally(i)
         cm, _ = c.get_tally()
-        om, _ = Oracle(p).run().tally()
+        om, _ = Oracle(p, strict=True).run().tally()
         assert bm.shape == cm.shape == om.shape, i
         assert rel_close(bm, cm, SUM_RTOL, 1e-300) and rel_close(bm, om, SUM_RTOL, 1e-300), i

@@ -22,9 +22,11 @@ def _reference(pb, mat, E):
     return st, nf
 
 
-def test_macro_table_equals_nuclide_sum(orc):
+@pytest.mark.parametrize("strict", [False, True])
+def test_macro_table_equals_nuclide_sum(orc, strict):
+    """strict: the per-material macroscopic table; plain: the nuclide sum at E"""
     pb = W.ce_pin_cell(n=100, npts=3000, nres=30)
-    o = orc.Oracle(pb)
+    o = orc.Oracle(pb, strict=strict)
     rng = np.random.default_rng(4)
     E = np.exp(rng.uniform(np.log(W.E_MIN), np.log(W.E_MAX), 3000))
     E = np.concatenate([E, pb["nuclides"][3]["E"][::7], pb["nuclides"][0]["E"][::11]])

@@ -35,7 +35,8 @@ __all__ = [
     "mg_material", "kinf_mg", "pin_cell_mg", "c5g7_like_lattice", "ce_pin_cell",
     "batch_boxes", "diff_slab", "infinite_medium_mg", "absorbing_slab_beam",
     "one_collision_slab", "infinite_medium_fixed", "scaled", "with_run", "CONFIG_NAMES",
-    "time_pulse_mg", "time_pulse_ce", "ce_time_pin",
+    "time_pulse_mg", "time_pulse_ce", "ce_time_pin", "void_lattice_beam", "ce_void_beam",
+    "small_lattice",
 ]
 
 CONFIG_NAMES = {
@@ -587,3 +588,94 @@ def ce_time_pin(seed=1, n=10_000_000, t_cut=1.0e-5, ntbins=40, npts=50_000, nres
     pb["free_gas"] = {"kT": 0.0253}
     pb["run"] = _fixed_run(n, seed, batches)
     return pb
+
+
+# ----------------------------------------------------------------------------
+# pins of tally layouts and lattice boundaries
+# ----------------------------------------------------------------------------
+def void_lattice_beam(nx=3, ny=2, pitch=1.25, row=1, n=200, seed=21):
+    """A void nx x ny lattice of pitch `pitch` from the origin, vacuum outside,
+    with a beam along +x entering at x = 0 through the middle of row `row`.
+    Every history crosses the row's elements one after the other, each over a
+    track of exactly one pitch, and leaks; the lattice-filter tally must hold
+    `pitch` in bins ix + nx * row and 0 elsewhere."""
+    G = 1
+    void = {"sigma_t": np.zeros(G), "sigma_s": np.zeros((G, G)), "nu_sigma_f": np.zeros(G),
+            "chi": np.zeros(G)}
+    X, Y = nx * pitch, ny * pitch
+    surfaces = [_surf("px", [0.0], "vacuum"), _surf("px", [X], "vacuum"),
+                _surf("py", [0.0], "vacuum"), _surf("py", [Y], "vacuum")]
+    cells = [_cell(0, [(0, +1), (1, -1), (2, +1), (3, -1)], "lattice", 0),
+             _cell(1, [], "material", 0)]
+    lattice = {"x0": 0.0, "y0": 0.0, "pitch": float(pitch), "nx": int(nx), "ny": int(ny),
+               "universes": np.ones(nx * ny, dtype=np.int32)}
+    return {
+        "name": "void-lattice-beam", "G": G, "surfaces": surfaces, "cells": cells,
+        "lattices": [lattice], "materials": [void],
+        "source": {"kind": "point", "point": [0.0, (row + 0.5) * pitch, 0.0], "energy": "pdf",
+                   "pdf": np.ones(G), "direction": "beam", "beam": [1.0, 0.0, 0.0]},
+        "tallies": [{"filter": "lattice"}],
+        "run": _fixed_run(n, seed, 4),
+    }
+
+
+def ce_void_beam(E, edges, length=2.0, n=200, seed=22):
+    """Continuous energy: a beam of fixed energy E along +x through a slab of
+    a material whose nuclide has zero cross sections, vacuum at both faces.
+    Each history streams `length` at energy E and leaks; the cell tally with
+    energy edges `edges` must hold `length` in the bin E falls in (the largest
+    b with edges[b] <= E, the top edge closing the last bin) and nothing when E
+    is outside [edges[0], edges[-1]]."""
+    grid = np.array([E_MIN, 1.0, E_MAX])
+    nuc = {"A": 1.0, "E": grid, "sig_s": np.zeros(3), "sig_c": np.zeros(3), "sig_f": np.zeros(3),
+           "nu": 0.0}
+    surfaces = [_surf("px", [0.0], "vacuum"), _surf("px", [length], "vacuum")]
+    cells = [_cell(0, [(0, +1), (1, -1)], "material", 0)]
+    return {
+        "name": "ce-void-beam", "G": 0, "surfaces": surfaces, "cells": cells, "lattices": [],
+        "nuclides": [nuc], "materials": [{"nuclides": [0], "density": [1.0]}],
+        "source": {"kind": "point", "point": [0.0, 0.0, 0.0], "energy": "fixed", "E": float(E),
+                   "direction": "beam", "beam": [1.0, 0.0, 0.0]},
+        "tallies": [{"filter": "cell", "edges": np.asarray(edges, float)}],
+        "run": _fixed_run(n, seed, 4),
+    }
+
+
+def small_lattice(seed=31, n=4000, inactive=2, active=3, nx=4, ny=4, pitch=1.26, r=0.54,
+                  z_planes=None, x_plane=None, G=7):
+    """A small k-eigenvalue lattice of pin cells (fuel cylinder of radius r in
+    moderator, every element alike) with root boundaries that reach inside the
+    lattice's elements.  z_planes = (zlo, zhi, bc_lo, bc_hi): the root cell is
+    also bounded by z-planes (the lattice is finite in height).  x_plane =
+    (x, bc): the root cell's low-x boundary is a plane at x (through the first
+    column's pin centres for x = pitch / 2) instead of the lattice's edge.
+    Otherwise the outer boundary is reflective at low x and y and vacuum at
+    high x and y."""
+    rng = np.random.default_rng([seed, 5])
+    fuel = mg_material(rng, G, fissile=True, kinf=1.3)
+    mod = mg_material(rng, G, fissile=False)
+    X, Y = nx * pitch, ny * pitch
+    xlo, xbc = (0.0, "reflect") if x_plane is None else (float(x_plane[0]), x_plane[1])
+    surfaces = [_surf("px", [xlo], xbc), _surf("px", [X], "vacuum"),
+                _surf("py", [0.0], "reflect"), _surf("py", [Y], "vacuum"),
+                _surf("cylz", [0.0, 0.0, r])]
+    root = [(0, +1), (1, -1), (2, +1), (3, -1)]
+    zlo = zhi = None
+    if z_planes is not None:
+        zlo, zhi, blo, bhi = z_planes
+        surfaces += [_surf("pz", [zlo], blo), _surf("pz", [zhi], bhi)]
+        root += [(5, +1), (6, -1)]
+    cells = [_cell(0, root, "lattice", 0),
+             _cell(1, [(4, -1)], "material", 0),
+             _cell(1, [(4, +1)], "material", 1)]
+    lattice = {"x0": 0.0, "y0": 0.0, "pitch": float(pitch), "nx": int(nx), "ny": int(ny),
+               "universes": np.ones(nx * ny, dtype=np.int32)}
+    box = [xlo, X, 0.0, Y, zlo if zlo is not None else 0.0, zhi if zhi is not None else 0.0]
+    return {
+        "name": "small-lattice", "G": G, "surfaces": surfaces, "cells": cells,
+        "lattices": [lattice], "materials": [fuel, mod],
+        "source": {"kind": "box", "box": box, "accept": "fissile", "energy": "chi",
+                   "direction": "iso"},
+        "tallies": [{"filter": "lattice"}, {"filter": "cell"}],
+        "run": _eigen_run(n, inactive, active, seed),
+    }
