@@ -33,19 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = "histories/s on 1 GB300, batched vs plain event launch; % HBM roofline; grad/s"
 WORKLOAD = "mg-c5g7-like-lattice-51x51-7g-keff"
 N_PER_CYCLE = 1_000_000
-# FP64-pipe peak of one GB300: 152 SMs x 2 FP64 results per clock per SM x 2.07 GHz
-# (the nominal 1.25 TFLOP/s counts an FMA as 2); a measured FP64 instruction
-# throughput probe gave 504 G/s at the clocks it ran at.
-FP64_PEAK_GOPS = 152 * 2 * 2.07
-# FP64 thread-instructions per event of the persistent transport kernel on this
-# workload: ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum of one k_pool launch
-# divided by the events of that cycle (1.455e9 / 2.246e7), profiles/k_pool_c5g7_lattice.md.
-FP64_INST_PER_EVENT = 64.8
 # Algorithmic particle-state bytes an event moves in the event-based form:
 # advance reads position/direction/energy/RNG/cell path and writes position,
 # RNG, event tag; collide or cross read and write direction, group, RNG and
 # cell path (fields counted once per kernel that touches them).
 STATE_BYTES_PER_EVENT = 120.0
+
+
 def _hbm_peak():
     """The measured copy bandwidth of the GB300s (GB/s)."""
     try:
@@ -56,19 +50,28 @@ def _hbm_peak():
 
 
 HBM_PEAK_GBS = _hbm_peak()
-# DRAM bytes (read + write) of the first k_advance launch of a cycle (1e6
-# particles) from an ncu capture, or None when the kernel has changed since.
-ADVANCE_TRAFFIC_PER_LAUNCH = 124725504 + 25844480
-# DRAM bytes (read + write) of one k_pool launch from the same ncu capture, or None
-# when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 79513600 + 90772992
-# Other counters of the same two captures (profiles/k_pool_c5g7_lattice.md,
-# profiles/event_mode_c5g7_lattice.md): L2 sector hit rate, active lanes per
-# issued instruction / 32, FP64 pipe busy fraction of the elapsed time.
-NCU_K_POOL = {"l2_hit_rate": 0.8478, "warp_exec_efficiency": 20.34 / 32, "fp64_pipe_busy": 0.4798,
-              "source": "profiles/k_pool_c5g7_lattice.md"}
-NCU_K_ADVANCE = {"l2_hit_rate": 0.4982, "fp64_pipe_busy": 0.7524, "dram_throughput": 0.1546,
-                 "source": "profiles/event_mode_c5g7_lattice.md"}
+# Counters from ncu captures of the transport kernels on the headline workload
+# (one k_pool launch = one 1e6-history cycle; the first k_advance launch of an
+# event-mode cycle).  They hold for the kernel sources they were taken on,
+# NCU_SOURCES = paper_2501_05440_gb300.kernel_source_hash() of that build, and
+# are reported as null once the sources differ.
+#   fp64_inst_per_event: sm__thread_inst_executed_pipe_fp64_pred_on.sum / events
+#   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum
+#   l2_hit_rate: lts__t_sector_hit_rate; warp_exec_efficiency: active lanes per
+#   issued instruction / 32; fp64_pipe_busy: FP64 pipe cycles / elapsed cycles
+NCU_SOURCES = None
+NCU_K_POOL = {"fp64_inst_per_event": None, "dram_bytes_per_launch": None, "l2_hit_rate": None,
+              "warp_exec_efficiency": None, "fp64_pipe_busy": None}
+NCU_K_ADVANCE = {"dram_bytes_per_launch": None, "l2_hit_rate": None, "fp64_pipe_busy": None,
+                 "dram_throughput": None}
+
+
+def ncu_counters(m):
+    """The recorded counters when they were taken on these kernel sources, else
+    None (stale)."""
+    if NCU_SOURCES is None or NCU_SOURCES != m.kernel_source_hash():
+        return None, None
+    return dict(NCU_K_POOL), dict(NCU_K_ADVANCE)
 
 
 def parse():
@@ -225,7 +228,12 @@ def headline(m, W, torch, args, rank, pg):
     tms, cms = c.get_cycle_times(ncyc)
     k = c.get_k()
     events = (cnt["collisions"] + cnt["crossings"]) / ncyc    # per cycle (the cycles are alike)
+    probe_clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    probe_clocks.start()
+    fp64_ops, fp64_ms = c.fp64_throughput(iters=100_000)
+    clk["fp64_probe"] = probe_clocks.stop()
     return {"ms": ms, "n": n, "launches": launches, "clocks": clk, "k": k,
+            "fp64_ops_per_s": fp64_ops, "fp64_probe_ms": fp64_ms,
             "transport_ms": sum(tms[args.warmup:]) / args.steps,
             "cycle_ms": sum(cms[args.warmup:]) / args.steps, "events_per_cycle": events,
             "counters": cnt}
@@ -250,15 +258,24 @@ def plain_leg(m, W, torch, args, steps, mode=None):
     ms = e0.elapsed_time(e1)
     c.eigen_finish()
     cnt = c.get_counters()
+    events = (cnt["collisions"] + cnt["crossings"]) / (steps + 1)   # per cycle
     out = {"value": args.n * steps / (ms / 1e3), "unit": "histories/s",
            "mode": "segment" if mode == m.MODE_SEGMENT else "event",
-           "ms_per_step": ms / steps, "steps": steps,
+           "ms_per_step": ms / steps, "steps": steps, "events_per_cycle": events,
            "event_iterations_per_cycle": cnt["event_iterations"] / (steps + 1)}
+    # HBM roofline of the whole cycle: the algorithmic state bytes of every
+    # event of the cycle over the cycle's time (all its launches)
+    gbs_cycle = STATE_BYTES_PER_EVENT * events / (ms / steps / 1e3) / 1e9
+    out["hbm_roofline_cycle"] = {"achieved": gbs_cycle, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                 "frac": gbs_cycle / HBM_PEAK_GBS,
+                                 "basis": f"{STATE_BYTES_PER_EVENT:.0f} B/event x {events:.4g} "
+                                          "events per cycle / cycle time (of measured copy bandwidth)"}
     if mode == m.MODE_EVENT:
         # HBM roofline of the flight kernel: each cycle's first k_advance launch
         # (the whole cycle's particles, identity list), timed with CUDA events
         # on the launching stream inside the library
         et = c.get_event_timing()
+        _, adv = ncu_counters(m)
         if et["launches"] > 0 and et["advance_ms"] > 0:
             gbs = et["bytes_per_particle"] * et["particles"] / (et["advance_ms"] / 1e3) / 1e9
             out["roofline"] = {"bound": "hbm", "kernel": "k_advance (first flight of a cycle)",
@@ -267,7 +284,8 @@ def plain_leg(m, W, torch, args, steps, mode=None):
                                "per_unit": f"{et['bytes_per_particle']:.0f} B/particle x "
                                            f"{et['particles'] / et['launches']:.4g} particles/launch",
                                "ms_per_launch": et["advance_ms"] / et["launches"],
-                               "traffic": ADVANCE_TRAFFIC_PER_LAUNCH, "ncu": NCU_K_ADVANCE,
+                               "traffic": adv["dram_bytes_per_launch"] if adv else None,
+                               "ncu": adv,
                                "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     return out
 
@@ -323,23 +341,37 @@ def batched_leg(m, W, torch):
 
 
 def grad_leg(m, W, torch, n):
+    """Derivatives through the public torch API: DetectorTally on CUDA tensors
+    (device-pointer calls, no host copies of any array), forward then backward
+    of sum(tally), 1e7 histories of the slab."""
+    import numpy as np
+
+    from paper_2501_05440_gb300.autograd import detector_tally
     pb = W.diff_slab(n=n)
-    c = m.Context(mode=m.MODE_PERSISTENT)
-    m.load_problem(c, pb)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    eng = m.load_problem(m.Context(device=dev.index, mode=m.MODE_PERSISTENT), pb)
     det = pb["detector_cell"]
-    c.forward_fixed(min(n, 10000), 1, det)
-    c.backward_fixed([1.0] * pb["G"], len(pb["materials"]))
+
+    def xs():
+        return [torch.tensor(np.array([mat[k] for mat in pb["materials"]]), device=dev,
+                             requires_grad=True) for k in ("sigma_t", "sigma_s", "nu_sigma_f")]
+
+    st, ss, nf = xs()     # warm-up at a smaller size
+    detector_tally(pb, st, ss, nf, min(n, 10000), 1, det, engine=eng).sum().backward()
+    st, ss, nf = xs()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tal = c.forward_fixed(n, 1, det)
+    y = detector_tally(pb, st, ss, nf, n, 1, det, engine=eng)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    c.backward_fixed([1.0] * pb["G"], len(pb["materials"]))
+    y.sum().backward()
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     return {"histories": n, "forward_s": t1 - t0, "backward_s": t2 - t1,
             "grad_histories_per_s": n / (t2 - t1), "forward_histories_per_s": n / (t1 - t0),
-            "detector_tally": float(tal.sum())}
+            "detector_tally": float(y.detach().sum().item()),
+            "api": "paper_2501_05440_gb300.autograd.DetectorTally on CUDA tensors",
+            "grad_norm_sigma_t": float(st.grad.norm().item())}
 
 
 def ce_leg(m, W, torch, steps=3):
@@ -456,17 +488,25 @@ def run_mcgb(args):
         "k": h["k"]["k"], "k_sd": h["k"]["k_sd"],
         "gpu_launches": h["launches"], "clocks": h["clocks"],
     }
-    # roofline of the transport kernel (the persistent event loop, one launch per cycle):
-    # bound by the FP64 pipe; the HBM fraction of the event-based state traffic beside it
+    # roofline of the transport kernel (the persistent event loop, one launch per
+    # cycle, timed with CUDA events on its stream inside the library): bound by
+    # the FP64 pipe, against the FP64 throughput measured in this run; the HBM
+    # fraction of the event-based state traffic beside it
     ev = h["events_per_cycle"]
     t_kernel = max(h["transport_ms"], 1e-9) / 1e3
-    ach = FP64_INST_PER_EVENT * ev / t_kernel / 1e9
-    out["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GOPS,
-                       "unit": "G FP64 thread-instr/s", "frac": ach / FP64_PEAK_GOPS,
-                       "traffic": TRAFFIC_PER_LAUNCH, "ncu": NCU_K_POOL,
+    pool, _ = ncu_counters(m)
+    ipe = pool["fp64_inst_per_event"] if pool else None
+    peak = h["fp64_ops_per_s"] / 1e9
+    ach = ipe * ev / t_kernel / 1e9 if ipe else None
+    out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak,
+                       "unit": "G FP64 thread-instr/s", "frac": ach / peak if ach else None,
+                       "traffic": pool["dram_bytes_per_launch"] if pool else None, "ncu": pool,
                        "kernel": "k_pool (persistent event loop)",
-                       "per_unit": f"{FP64_INST_PER_EVENT} FP64 instr/event x {ev:.4g} events/launch",
-                       "peak_kind": "derived: 152 SMs x 2 FP64/clk x 2.07 GHz (recipe's 1.25 TFLOP/s)"}
+                       "per_unit": f"{ipe} FP64 instr/event (ncu) x {ev:.4g} events/launch",
+                       "kernel_ms": h["transport_ms"],
+                       "peak_kind": "measured in this run: mcgb_fp64_throughput (independent FMA "
+                                    f"chains, {h['fp64_probe_ms']:.1f} ms launch)",
+                       "kernel_sources": m.kernel_source_hash(), "ncu_sources": NCU_SOURCES}
     hbm = STATE_BYTES_PER_EVENT * ev / t_kernel / 1e9
     out["hbm_roofline"] = {"achieved": hbm, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": hbm / HBM_PEAK_GBS,
                            "basis": f"{STATE_BYTES_PER_EVENT:.0f} B algorithmic state per event "
@@ -525,8 +565,37 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def launch_ranks(args):
+    """--gpus N > 1 outside torchrun: start N ranks on this node (one process per
+    GPU, rendezvous on 127.0.0.1) and return their exit status.  Refuses when
+    the node has fewer GPUs than asked for."""
+    import socket
+    try:
+        import torch
+        have = torch.cuda.device_count()
+    except Exception:
+        have = 0
+    if args.impl == "mcgb" and have < args.gpus:
+        print(f"bench.py: --gpus {args.gpus} asked for, {have} CUDA device(s) visible; "
+              "refusing to run fewer ranks", file=sys.stderr)
+        return 2
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={args.gpus}", "--master-addr", "127.0.0.1",
+           f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 if __name__ == "__main__":
     a = parse()
+    world = os.environ.get("WORLD_SIZE")
+    if world is None and a.gpus > 1:
+        sys.exit(launch_ranks(a))
+    if world is not None and int(world) != a.gpus:
+        print(f"bench.py: --gpus {a.gpus} but WORLD_SIZE={world}; refusing", file=sys.stderr)
+        sys.exit(2)
     if a.impl == "reference":
         run_reference(a)
     else:

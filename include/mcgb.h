@@ -80,7 +80,11 @@ typedef struct {
     int blocks_per_sm;      /* persistent mode: resident blocks per SM (default: occupancy) */
     int record_histories;   /* keep per-history records of the last cycle / generation 0 */
     double bank_factor;     /* fission bank capacity as a multiple of N (default 3) */
-    int max_iterations;     /* event / segment mode iteration limit per cycle (default 1e7) */
+    int max_iterations;     /* event / segment mode: host loop iterations per cycle or
+                               generation (default 1e7); persistent mode: passes of each
+                               block's (or warp's) event loop per launch (default none).
+                               Reaching it fails the run with MCGB_E_TIMEOUT, the
+                               unfinished histories abandoned; the context stays usable */
     int pool;               /* persistent mode: particles held in shared memory and run
                                event type by event type from sorted lists: 256 (one per
                                thread, three resident blocks per SM), 512 or 1024 per
@@ -295,6 +299,31 @@ int mcgb_forward_fixed(mcgb_ctx *ctx, int64_t n, uint64_t seed, int det_cell, do
 int mcgb_backward_fixed(mcgb_ctx *ctx, const double *weights, double *d_sigt, double *d_sigs,
                         double *d_nusf);
 
+/* Device-pointer variants of the three calls above, for callers whose arrays
+ * live on the context's device (the torch binding): every array argument is a
+ * device pointer on the context's device, caller-owned, read or written in
+ * order on the context's stream; no array goes through host memory.
+ *
+ * mcgb_update_material_mg_dev: new Sigma_t [n_mat][G], Sigma_s [n_mat][G][G]
+ *   ([from][to]) and nuSigma_f [n_mat][G] of materials first .. first+n_mat-1
+ *   (chi unchanged), written into the device tables (the world is built from
+ *   the definition first if it is not current).  The host-side definition
+ *   keeps its old values: a later definition change or a host-array run
+ *   rebuilds the tables from it.  Values are checked on the device; a
+ *   negative value or Sigma_s,tot > Sigma_t leaves that row unchanged and
+ *   makes the next mcgb_forward_fixed_dev fail with MCGB_E_INVALID_ARG.
+ * mcgb_forward_fixed_dev: as mcgb_forward_fixed on the current device tables;
+ *   tally[G] (device) may be NULL.  The run's control flow still reads bank
+ *   sizes and status flags on the host.
+ * mcgb_backward_fixed_dev: as mcgb_backward_fixed with weights[G],
+ *   d_sigt[M*G], d_sigs[M*G*G], d_nusf[M*G] on the device; returns when the
+ *   results are written. */
+int mcgb_update_material_mg_dev(mcgb_ctx *ctx, int first, int n_mat, const double *sigma_t,
+                                const double *sigma_s, const double *nu_sigma_f);
+int mcgb_forward_fixed_dev(mcgb_ctx *ctx, int64_t n, uint64_t seed, int det_cell, double *tally);
+int mcgb_backward_fixed_dev(mcgb_ctx *ctx, const double *weights, double *d_sigt, double *d_sigs,
+                            double *d_nusf);
+
 /* --------------------------------------------------------------------------- */
 /* batching: many independent fixed-source problems in one persistent launch    */
 int mcgb_batch_create(mcgb_batch **out, const mcgb_opts *opts);
@@ -323,6 +352,13 @@ int mcgb_rng_states(mcgb_ctx *ctx, uint64_t seed, uint64_t first_id, int64_t n_s
                     int n_draws, uint64_t *out);
 /* out[i] = ln(xi[i]) for xi[i] = k 2^-53, k in [1, 2^53] (the transport's log). */
 int mcgb_log(mcgb_ctx *ctx, int64_t n, const double *xi, double *out);
+/* FP64 throughput of this device, measured: a grid of 8 blocks of 256 threads
+ * per SM runs independent fused multiply-add chains, `iters` steps of 8 chains
+ * per thread, timed with CUDA events on the context's stream after one
+ * untimed launch.  *ops_per_s = FP64 thread-instructions per second (an FMA
+ * counts once), *ms = the timed launch.  The roofline of the FP64-bound
+ * transport kernels is taken against this (the paper gives no peak). */
+int mcgb_fp64_throughput(mcgb_ctx *ctx, int64_t iters, double *ops_per_s, double *ms);
 /* Geometry probe: locate each point (direction dir) and the distance to the
  * nearest boundary.  path[5*i..] = root cell, ix, iy, universe cell, material. */
 int mcgb_probe(mcgb_ctx *ctx, int64_t n, const double *pos, const double *dir, int32_t *path,
@@ -345,9 +381,10 @@ int mcgb_ce_lookup(mcgb_ctx *ctx, int mat, int64_t n, const double *E, double *o
  * loads it until the process exits.  n may be at most 16777216; larger n is
  * rejected with MCGB_E_INVALID_ARG.  The first call on a device (make it the
  * current device) looks up the array's device address; make that first call
- * before any stream capture.  All calls share the array, so calls that overlap
- * on the GPU (concurrent streams or devices sharing nothing else) race: order
- * them on one stream.  Nothing in the array needs clearing between calls.
+ * before any stream capture.  Each device holds its own copy of the array, and
+ * all calls on one device share it: calls that overlap on the same GPU (on
+ * concurrent streams) race, so order them on one stream; calls on different
+ * devices do not interfere.  Nothing in the array needs clearing between calls.
  * Returns MCGB_OK or MCGB_E_INVALID_ARG / MCGB_E_CUDA. */
 int mcgb_bank_offsets_noalloc(const int32_t *n_fis, int64_t n, int32_t *first, int32_t *total,
                               void *cuda_stream);

@@ -15,7 +15,8 @@ import threading
 import numpy as np
 
 __all__ = ["lib", "build", "McgbError", "Context", "Batch", "load_problem", "library_path",
-           "bank_offsets_noalloc", "MODE_EVENT", "MODE_PERSISTENT", "MODE_SEGMENT"]
+           "bank_offsets_noalloc", "kernel_source_hash", "MODE_EVENT", "MODE_PERSISTENT",
+           "MODE_SEGMENT"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "_build", "libmcgb.so")
@@ -59,6 +60,22 @@ assert SITE_DTYPE.itemsize == 64
 class Tune(C.Structure):
     _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("pool", C.c_int),
                 ("ms", C.c_double)]
+
+
+# the files that define the device code of the transport kernels
+_KERNEL_SOURCES = ["kernels.h", "world.h", "transport.cuh", "steps.cuh", "kernels_pool.cu",
+                   "kernels_transport.cu"]
+
+
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the transport kernels' device
+    sources: profiler counters taken on a build are valid while it matches."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in _KERNEL_SOURCES:
+        with open(os.path.join(_HERE, "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
 
 
 def library_path():
@@ -116,12 +133,16 @@ def lib():
                 "mcgb_get_bank": [P, sz, P, P, P, P, P],
                 "mcgb_forward_fixed": [P, i64, u64, i32, P],
                 "mcgb_backward_fixed": [P, P, P, P, P],
+                "mcgb_update_material_mg_dev": [P, i32, i32, P, P, P],
+                "mcgb_forward_fixed_dev": [P, i64, u64, i32, P],
+                "mcgb_backward_fixed_dev": [P, P, P, P, P],
                 "mcgb_batch_create": [P, P], "mcgb_batch_destroy": [P],
                 "mcgb_batch_add_problem": [P, P, i64, i32, u64, P],
                 "mcgb_batch_autotune": [P, i32, P], "mcgb_batch_run": [P, P],
                 "mcgb_batch_tally": [P, i32, i32, P, P, sz, P], "mcgb_batch_counters": [P, P],
                 "mcgb_rng_states": [P, u64, u64, i64, i32, P],
                 "mcgb_log": [P, i64, P, P], "mcgb_probe": [P, i64, P, P, P, P, P],
+                "mcgb_fp64_throughput": [P, i64, P, P],
                 "mcgb_ce_lookup": [P, i32, i64, P, P],
                 "mcgb_bank_offsets_noalloc": [P, i64, P, P, P],
             }
@@ -393,6 +414,20 @@ class Context:
         return {"sigma_t": a.reshape(nmat, G), "sigma_s": b.reshape(nmat, G, G),
                 "nu_sigma_f": c.reshape(nmat, G)}
 
+    # device-pointer variants: arguments are device addresses (ints) on this
+    # context's device, e.g. torch.Tensor.data_ptr() of contiguous float64 tensors
+    def update_material_mg_dev(self, first, n_mat, sigma_t, sigma_s, nu_sigma_f):
+        _chk(self.L.mcgb_update_material_mg_dev(self.h, int(first), int(n_mat), C.c_void_p(sigma_t),
+                                                C.c_void_p(sigma_s), C.c_void_p(nu_sigma_f)))
+
+    def forward_fixed_dev(self, n, seed, det_cell, tally):
+        _chk(self.L.mcgb_forward_fixed_dev(self.h, int(n), int(seed), int(det_cell),
+                                           C.c_void_p(tally)))
+
+    def backward_fixed_dev(self, weights, d_sigma_t, d_sigma_s, d_nu_sigma_f):
+        _chk(self.L.mcgb_backward_fixed_dev(self.h, C.c_void_p(weights), C.c_void_p(d_sigma_t),
+                                            C.c_void_p(d_sigma_s), C.c_void_p(d_nu_sigma_f)))
+
     def rng_states(self, seed, first_id, n_streams, n_draws):
         out = np.zeros(n_streams * n_draws, dtype=np.uint64)
         _chk(self.L.mcgb_rng_states(self.h, seed, first_id, n_streams, n_draws, _p(out)))
@@ -403,6 +438,13 @@ class Context:
         out = np.zeros_like(x)
         _chk(self.L.mcgb_log(self.h, len(x), _p(x), _p(out)))
         return out
+
+    def fp64_throughput(self, iters=20000):
+        """Measured FP64 thread-instructions per second of this device, and
+        the timed launch in ms."""
+        ops, ms = C.c_double(), C.c_double()
+        _chk(self.L.mcgb_fp64_throughput(self.h, int(iters), C.byref(ops), C.byref(ms)))
+        return ops.value, ms.value
 
     def probe(self, pos, direction):
         p, d = _f64(pos).reshape(-1, 3), _f64(direction).reshape(-1, 3)

@@ -132,6 +132,12 @@ struct mcgb_ctx {
     std::unique_ptr<DeviceWorld> world;
     RunState rs;
     int64_t launches = 0;
+    // the device world was built from the definition as it stood at def_version
+    int64_t def_version = 0, world_version = -1;
+    // device-side material updates: validity flag, checked before the next run
+    DevAlloc upd_mem;
+    int *upd_bad = nullptr;
+    bool upd_pending = false;
     // results
     double k[6] = {0, 0, 0, 0, 0, 0};
     std::vector<double> cyc_ktl, cyc_kc;
@@ -277,6 +283,7 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
         a.work = r.work;
         a.chunk = 1;
         a.gen_dev = gen_dev;
+        a.max_passes = c->opts.max_iterations > 0 ? c->opts.max_iterations : 0;
         int pool = c->opts.pool == 0 ? 256 : c->opts.pool;
         if (pool > 0) {
             int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
@@ -314,7 +321,12 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
     const int *n_dev = nullptr;
     int64_t maxit = c->opts.max_iterations > 0 ? c->opts.max_iterations : 10000000;
     for (int64_t it = 0;; it++) {
-        if (it >= maxit) return fail(MCGB_E_TIMEOUT, "event iteration limit reached");
+        if (it >= maxit) {
+            // the queued launches finish on their own (each is bounded); the
+            // stream is drained so that the caller may reuse the context
+            CK(cudaStreamSynchronize(st));
+            return fail(MCGB_E_TIMEOUT, "event iteration limit reached");
+        }
         int *next = r.list[cur];
         int *next_n = r.q_n + 2 + cur;
         CK(cudaMemsetAsync(r.q_n, 0, 2 * sizeof(int), st));
@@ -446,9 +458,12 @@ static int read_flags(mcgb_ctx *c, int64_t &M, int &err)
 static int build_single(mcgb_ctx *c, int64_t n, int batches, uint64_t seed)
 {
     if (!c->world) c->world.reset(new DeviceWorld());
+    c->world_version = -1;
+    c->upd_pending = false;   // a rebuilt world holds the host definition's tables
     std::vector<ProblemRun> runs{{&c->def, n, batches, seed}};
     std::string e = build_world(runs, *c->world, c->stream);
     if (!e.empty()) return fail(MCGB_E_STATE, e);
+    c->world_version = c->def_version;
     return MCGB_OK;
 }
 
@@ -658,6 +673,10 @@ static int eigen_cycles(mcgb_ctx *c, int k)
             e.on = false;
             return fail(MCGB_E_STATE, "source sampling failed");
         }
+        if (err & ERR_ITER) {
+            e.on = false;
+            return fail(MCGB_E_TIMEOUT, "persistent event loop pass limit reached");
+        }
         for (int cyc = first; cyc < last; cyc++)
             if (c->cyc_m[cyc] == 0) {
                 e.on = false;
@@ -710,6 +729,11 @@ static int eigen_cycles(mcgb_ctx *c, int k)
         if (err & ERR_SOURCE) {
             e.on = false;
             return fail(MCGB_E_STATE, "source sampling failed");
+        }
+        if (err & ERR_ITER) {
+            e.on = false;
+            return fail(MCGB_E_TIMEOUT, "persistent event loop pass limit reached in cycle " +
+                                            std::to_string(cyc));
         }
         if (cyc == e.ncyc - 1 && c->opts.record_histories) {
             CKR(copy_records(c, N));
@@ -841,6 +865,9 @@ static int run_fixed_world(mcgb_ctx *c, bool grad, int det_cell)
         if (err & ERR_BANK_OVERFLOW)
             return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow in generation " + std::to_string(gen) + " (raise opts.bank_factor)");
         if (err & ERR_SOURCE) return fail(MCGB_E_STATE, "source sampling failed");
+        if (err & ERR_ITER)
+            return fail(MCGB_E_TIMEOUT, "persistent event loop pass limit reached in generation " +
+                                            std::to_string(gen));
         if (gen == 0 && c->opts.record_histories) {
             CKR(copy_records(c, total));
             CKR(copy_bank(c, r.bank[nxt], M));
@@ -1001,6 +1028,7 @@ int mcgb_set_mode(mcgb_ctx *ctx, int mode)
 
 int mcgb_add_surface(mcgb_ctx *ctx, int type, const double coef[4], int bc, int *id)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || !coef || type < 0 || type > 5 || bc < 0 || bc > 2)
         return fail(MCGB_E_INVALID_ARG, "bad surface type or boundary");
     if (bc == MCGB_BC_REFLECT && type > MCGB_SURF_PLANE)
@@ -1018,6 +1046,7 @@ int mcgb_add_surface(mcgb_ctx *ctx, int type, const double coef[4], int bc, int 
 int mcgb_add_cell(mcgb_ctx *ctx, int universe, int n, const int *surf, const int *sense,
                   int fill_kind, int fill, int *id)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || universe < 0 || n < 0 || (n > 0 && (!surf || !sense)) || fill < 0 ||
         (fill_kind != MCGB_FILL_MATERIAL && fill_kind != MCGB_FILL_LATTICE))
         return fail(MCGB_E_INVALID_ARG, "bad cell");
@@ -1039,6 +1068,7 @@ int mcgb_add_cell(mcgb_ctx *ctx, int universe, int n, const int *surf, const int
 int mcgb_add_lattice(mcgb_ctx *ctx, double x0, double y0, double pitch, int nx, int ny,
                      const int *universes, int *id)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || nx <= 0 || ny <= 0 || !(pitch > 0.0) || !universes)
         return fail(MCGB_E_INVALID_ARG, "bad lattice");
     LatDef L{x0, y0, pitch, nx, ny, std::vector<int>(universes, universes + (size_t)nx * ny)};
@@ -1049,6 +1079,7 @@ int mcgb_add_lattice(mcgb_ctx *ctx, double x0, double y0, double pitch, int nx, 
 
 int mcgb_set_groups(mcgb_ctx *ctx, int G)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || G <= 0 || G > MAX_G) return fail(MCGB_E_INVALID_ARG, "bad group count");
     if (ctx->def.ce == 1 || !ctx->def.mg.empty()) return fail(MCGB_E_STATE, "groups already fixed");
     ctx->def.G = G;
@@ -1073,6 +1104,7 @@ static int check_mg(int G, const double *st, const double *ss, const double *nf)
 int mcgb_add_material_mg(mcgb_ctx *ctx, const double *sigma_t, const double *sigma_s,
                          const double *nu_sigma_f, const double *chi, int *id)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || !sigma_t || !sigma_s || !nu_sigma_f || !chi) return fail(MCGB_E_INVALID_ARG, "null array");
     int G = ctx->def.G;
     if (ctx->def.ce != 0 || G <= 0) return fail(MCGB_E_STATE, "call mcgb_set_groups first");
@@ -1087,6 +1119,7 @@ int mcgb_add_material_mg(mcgb_ctx *ctx, const double *sigma_t, const double *sig
 int mcgb_update_material_mg(mcgb_ctx *ctx, int id, const double *sigma_t, const double *sigma_s,
                             const double *nu_sigma_f, const double *chi)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || id < 0 || id >= (int)ctx->def.mg.size()) return fail(MCGB_E_NOT_FOUND, "no such material");
     int G = ctx->def.G;
     CKR(check_mg(G, sigma_t, sigma_s, nu_sigma_f));
@@ -1101,6 +1134,7 @@ int mcgb_update_material_mg(mcgb_ctx *ctx, int id, const double *sigma_t, const 
 int mcgb_add_nuclide_ce(mcgb_ctx *ctx, double A, int n, const double *E, const double *sig_s,
                         const double *sig_c, const double *sig_f, double nu, int *id)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || n < 2 || !(A > 0.0) || !E || !sig_s || !sig_c || !sig_f || nu < 0.0)
         return fail(MCGB_E_INVALID_ARG, "bad nuclide");
     if (ctx->def.ce == 0) return fail(MCGB_E_STATE, "problem is multigroup");
@@ -1119,6 +1153,7 @@ int mcgb_add_nuclide_ce(mcgb_ctx *ctx, double A, int n, const double *E, const d
 
 int mcgb_add_material_ce(mcgb_ctx *ctx, int n, const int *nuclides, const double *density, int *id)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || n <= 0 || n > MAX_NUC || !nuclides || !density)
         return fail(MCGB_E_INVALID_ARG, "bad material");
     if (ctx->def.ce != 1) return fail(MCGB_E_STATE, "add nuclides first");
@@ -1138,6 +1173,7 @@ int mcgb_add_material_ce(mcgb_ctx *ctx, int n, const int *nuclides, const double
 int mcgb_set_source(mcgb_ctx *ctx, int kind, const double *params, int accept, int energy_kind,
                     const double *energy, int n_energy, int dir_kind, const double *beam)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || !params || (kind != MCGB_SRC_BOX && kind != MCGB_SRC_POINT) || accept < 0 ||
         accept > 1 || energy_kind < 0 || energy_kind > 3 || (dir_kind != 0 && dir_kind != 1))
         return fail(MCGB_E_INVALID_ARG, "bad source");
@@ -1159,6 +1195,7 @@ int mcgb_set_source(mcgb_ctx *ctx, int kind, const double *params, int accept, i
 
 int mcgb_add_tally(mcgb_ctx *ctx, int filter, int n_edges, const double *edges, int *id)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || filter < 0 || filter > 2 || n_edges < 0 || (n_edges > 0 && !edges))
         return fail(MCGB_E_INVALID_ARG, "bad tally");
     TallyDef t;
@@ -1174,6 +1211,7 @@ int mcgb_add_tally(mcgb_ctx *ctx, int filter, int n_edges, const double *edges, 
 
 int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || max_collisions < 0) return fail(MCGB_E_INVALID_ARG, "bad max_collisions");
     ctx->def.max_coll = max_collisions;
     return MCGB_OK;
@@ -1181,6 +1219,7 @@ int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions)
 
 int mcgb_set_free_gas(mcgb_ctx *ctx, double kT, double cut)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || !(kT > 0.0) || !std::isfinite(kT) || !(cut >= 0.0) || !std::isfinite(cut))
         return fail(MCGB_E_INVALID_ARG, "bad free-gas settings");
     ctx->def.fg_kT = kT;
@@ -1190,6 +1229,7 @@ int mcgb_set_free_gas(mcgb_ctx *ctx, double kT, double cut)
 
 int mcgb_set_time(mcgb_ctx *ctx, double t0, double t_cut)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || !(t0 >= 0.0) || !(t_cut > t0) || !std::isfinite(t_cut))
         return fail(MCGB_E_INVALID_ARG, "need 0 <= t0 < t_cut < inf");
     ctx->def.time_on = true;
@@ -1200,6 +1240,7 @@ int mcgb_set_time(mcgb_ctx *ctx, double t0, double t_cut)
 
 int mcgb_set_inverse_speeds(mcgb_ctx *ctx, int G, const double *inv_v)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || G <= 0 || G != ctx->def.G || !inv_v)
         return fail(MCGB_E_INVALID_ARG, "one inverse speed per group");
     for (int g = 0; g < G; g++)
@@ -1211,6 +1252,7 @@ int mcgb_set_inverse_speeds(mcgb_ctx *ctx, int G, const double *inv_v)
 
 int mcgb_set_tally_time_bins(mcgb_ctx *ctx, int tally, int n_edges, const double *edges)
 {
+    if (ctx) ctx->def_version++;
     if (!ctx || tally < 0 || tally >= (int)ctx->def.tallies.size() || n_edges < 2 || !edges)
         return fail(MCGB_E_INVALID_ARG, "bad time bins");
     if (!(edges[0] >= 0.0)) return fail(MCGB_E_INVALID_ARG, "time edges must be >= 0");
@@ -1407,6 +1449,7 @@ int mcgb_shard_cycle(mcgb_ctx *c, int cycle, const mcgb_site *src, double ksum[2
         return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow in cycle " + std::to_string(cycle) +
                                               " (raise opts.bank_factor)");
     if (err & ERR_SOURCE) return fail(MCGB_E_STATE, "source sampling failed");
+    if (err & ERR_ITER) return fail(MCGB_E_TIMEOUT, "persistent event loop pass limit reached");
     c->shard.M = M;
     *m = M;
     c->counters.histories += n;
@@ -1534,20 +1577,13 @@ int mcgb_forward_fixed(mcgb_ctx *ctx, int64_t n, uint64_t seed, int det_cell, do
     return MCGB_OK;
 }
 
-int mcgb_backward_fixed(mcgb_ctx *ctx, const double *weights, double *d_sigt, double *d_sigs,
-                        double *d_nusf)
+// The replay backward on the context's stream: weights w [G] and the summed
+// scores grad [nm G (G + 2)] are device buffers (grad zeroed here).
+static int backward_core(mcgb_ctx *ctx, const double *w, double *grad, DevAlloc &tmp)
 {
-    if (!ctx || !weights) return fail(MCGB_E_INVALID_ARG, "bad argument");
-    if (!ctx->grad_ready) return fail(MCGB_E_STATE, "run mcgb_forward_fixed first");
-    CK(cudaSetDevice(ctx->device));
     int G = ctx->def.G, nm = (int)ctx->def.mg.size();
     int npar = nm * G * (G + 2);
     cudaStream_t st = ctx->stream;
-    DevAlloc tmp;
-    double *w, *grad;
-    CKR(tmp.get(w, G));
-    CKR(tmp.get(grad, npar));
-    CK(cudaMemcpyAsync(w, weights, sizeof(double) * G, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(grad, 0, sizeof(double) * npar, st));
     auto &gens = ctx->grad_gens;
     int ng = (int)gens.size();
@@ -1577,6 +1613,24 @@ int mcgb_backward_fixed(mcgb_ctx *ctx, const double *weights, double *d_sigt, do
         ctx->launches++;
     }
     CK(cudaGetLastError());
+    return MCGB_OK;
+}
+
+int mcgb_backward_fixed(mcgb_ctx *ctx, const double *weights, double *d_sigt, double *d_sigs,
+                        double *d_nusf)
+{
+    if (!ctx || !weights) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (!ctx->grad_ready) return fail(MCGB_E_STATE, "run mcgb_forward_fixed first");
+    CK(cudaSetDevice(ctx->device));
+    int G = ctx->def.G, nm = (int)ctx->def.mg.size();
+    int npar = nm * G * (G + 2);
+    cudaStream_t st = ctx->stream;
+    DevAlloc tmp;
+    double *w, *grad;
+    CKR(tmp.get(w, G));
+    CKR(tmp.get(grad, npar));
+    CK(cudaMemcpyAsync(w, weights, sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    CKR(backward_core(ctx, w, grad, tmp));
     std::vector<double> h(npar);
     CK(cudaMemcpyAsync(h.data(), grad, sizeof(double) * npar, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1584,6 +1638,108 @@ int mcgb_backward_fixed(mcgb_ctx *ctx, const double *weights, double *d_sigt, do
     for (int k = 0; k < nm * G; k++) d_sigt[k] = h[k] / N;
     for (int k = 0; k < nm * G * G; k++) d_sigs[k] = h[nm * G + k] / N;
     for (int k = 0; k < nm * G; k++) d_nusf[k] = h[nm * G + nm * G * G + k] / N;
+    return MCGB_OK;
+}
+
+// ---- device-pointer variants of the derivative path -----------------------
+int mcgb_update_material_mg_dev(mcgb_ctx *ctx, int first, int n_mat, const double *sigma_t,
+                                const double *sigma_s, const double *nu_sigma_f)
+{
+    if (!ctx || !sigma_t || !sigma_s || !nu_sigma_f) return fail(MCGB_E_INVALID_ARG, "null array");
+    if (ctx->def.ce != 0 || ctx->def.G <= 0) return fail(MCGB_E_STATE, "problem is not multigroup");
+    if (first < 0 || n_mat < 1 || first + n_mat > (int)ctx->def.mg.size())
+        return fail(MCGB_E_NOT_FOUND, "no such material");
+    CK(cudaSetDevice(ctx->device));
+    // the tables live in the device world: build it from the definition first
+    if (!ctx->world || ctx->world_version != ctx->def_version || ctx->world->probs.size() != 1)
+        CKR(build_single(ctx, 1, 1, 1));
+    if (!ctx->upd_bad) {
+        CKR(ctx->upd_mem.get(ctx->upd_bad, 1));
+        CK(cudaMemsetAsync(ctx->upd_bad, 0, sizeof(int), ctx->stream));
+    }
+    launch_update_mg(ctx->world->W, ctx->world->probs[0].mat0 + first, n_mat, ctx->def.G, sigma_t,
+                     sigma_s, nu_sigma_f, ctx->upd_bad, ctx->stream);
+    ctx->launches += 2;
+    CK(cudaGetLastError());
+    ctx->upd_pending = true;
+    return MCGB_OK;
+}
+
+// The world of the next single-problem run of n histories from `seed`: the
+// current one, with its run parameters replaced, when it was built from the
+// current definition for one problem with one tally batch (it may hold device
+// updates); otherwise rebuilt from the definition.
+static int world_for_run(mcgb_ctx *ctx, int64_t n, uint64_t seed)
+{
+    DeviceWorld *dw = ctx->world.get();
+    bool reuse = dw && ctx->world_version == ctx->def_version && dw->probs.size() == 1 &&
+                 dw->probs[0].batches == 1;
+    if (!reuse) return build_single(ctx, n, 1, seed);
+    ProblemDev &P = dw->probs[0];
+    P.n = n;
+    P.seed = seed & 0x7FFFFFFFFFFFFFFFULL;
+    CK(cudaMemcpyAsync(const_cast<ProblemDev *>(dw->W.prob), &P, sizeof(ProblemDev),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));   // P is pageable host memory
+    return MCGB_OK;
+}
+
+int mcgb_forward_fixed_dev(mcgb_ctx *ctx, int64_t n, uint64_t seed, int det_cell, double *tally)
+{
+    if (!ctx || n <= 0) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (ctx->def.ce != 0) return fail(MCGB_E_STATE, "derivatives are multigroup only");
+    if (ctx->def.time_on) return fail(MCGB_E_STATE, "derivatives are for time-independent runs");
+    if (det_cell < 0 || det_cell >= (int)ctx->def.cells.size())
+        return fail(MCGB_E_INVALID_ARG, "bad detector cell");
+    CK(cudaSetDevice(ctx->device));
+    CKR(world_for_run(ctx, n, seed));
+    if (ctx->upd_pending) {
+        int bad = 0;
+        CK(cudaMemcpyAsync(&bad, ctx->upd_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->upd_pending = false;
+        if (bad) {
+            CK(cudaMemsetAsync(ctx->upd_bad, 0, sizeof(int), ctx->stream));
+            return fail(MCGB_E_INVALID_ARG,
+                        "mcgb_update_material_mg_dev: negative cross section or scattering above total");
+        }
+    }
+    CKR(run_fixed_world(ctx, true, det_cell));
+    if (tally) {
+        int G = ctx->def.G;
+        for (size_t g = 0; g < ctx->grad_gens.size(); g++) {
+            launch_own_sum(ctx->grad_gens[g].own, ctx->grad_gens[g].n, G, g > 0 ? 1 : 0, tally,
+                           ctx->stream);
+            ctx->launches++;
+        }
+        if (ctx->grad_gens.empty()) CK(cudaMemsetAsync(tally, 0, sizeof(double) * G, ctx->stream));
+        launch_scale(tally, G, (double)n, tally, ctx->stream);
+        ctx->launches++;
+        CK(cudaGetLastError());
+    }
+    return MCGB_OK;
+}
+
+int mcgb_backward_fixed_dev(mcgb_ctx *ctx, const double *weights, double *d_sigt, double *d_sigs,
+                            double *d_nusf)
+{
+    if (!ctx || !weights || !d_sigt || !d_sigs || !d_nusf) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (!ctx->grad_ready) return fail(MCGB_E_STATE, "run a forward pass first");
+    CK(cudaSetDevice(ctx->device));
+    int G = ctx->def.G, nm = (int)ctx->def.mg.size();
+    int npar = nm * G * (G + 2);
+    DevAlloc tmp;
+    double *grad;
+    CKR(tmp.get(grad, npar));
+    CKR(backward_core(ctx, weights, grad, tmp));
+    double N = (double)ctx->grad_n;
+    launch_scale(grad, (int64_t)nm * G, N, d_sigt, ctx->stream);
+    launch_scale(grad + nm * G, (int64_t)nm * G * G, N, d_sigs, ctx->stream);
+    launch_scale(grad + nm * G + nm * G * G, (int64_t)nm * G, N, d_nusf, ctx->stream);
+    ctx->launches += 3;
+    CK(cudaGetLastError());
+    // the scratch is released when this call returns: finish with it first
+    CK(cudaStreamSynchronize(ctx->stream));
     return MCGB_OK;
 }
 
@@ -1642,6 +1798,33 @@ int mcgb_log(mcgb_ctx *ctx, int64_t n, const double *xi, double *out)
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, dy, 8 * n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    return MCGB_OK;
+}
+
+int mcgb_fp64_throughput(mcgb_ctx *ctx, int64_t iters, double *ops_per_s, double *ms)
+{
+    if (!ctx || iters <= 0 || !ops_per_s || !ms) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    CK(cudaSetDevice(ctx->device));
+    int grid = ctx->sms * 8;
+    DevAlloc tmp;
+    double *sink;
+    CKR(tmp.get(sink, grid));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    launch_fp64_rate(grid, (long long)iters, sink, ctx->stream);
+    cudaEventRecord(e0, ctx->stream);
+    launch_fp64_rate(grid, (long long)iters, sink, ctx->stream);
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t err = cudaStreamSynchronize(ctx->stream);
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(err);
+    ctx->launches += 2;
+    *ms = t;
+    *ops_per_s = (double)grid * 256.0 * (double)iters * fp64_rate_chains() / (t / 1e3);
     return MCGB_OK;
 }
 

@@ -37,6 +37,8 @@ struct PersistentArgs {
     int *work;               // device work counter (zeroed before the launch)
     int chunk;               // slots taken per pop
     const int *gen_dev;      // when not null: the cycle index is read here (graph replay)
+    long long max_passes;    // > 0: a block (warp) stops after this many passes of its event
+                             // loop and raises ERR_ITER (histories left unfinished)
 };
 // births read Bsrc (the previous cycle's bank), new sites are appended to Bdst
 void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, const Bank &Bdst,
@@ -81,6 +83,10 @@ void launch_copy_records(const Particles &P, int64_t n, int *ncoll, int *ncross,
 void launch_rng_states(uint64_t seed, uint64_t first_id, int64_t n, int draws, uint64_t *out,
                        cudaStream_t st);
 void launch_log(const World &W, int64_t n, const double *xi, double *out, cudaStream_t st);
+// FP64 throughput probe: grid blocks of 256 threads, fp64_rate_chains() FMAs per
+// thread per iteration
+void launch_fp64_rate(int grid, long long iters, double *sink, cudaStream_t st);
+int fp64_rate_chains();
 void launch_probe(const World &W, int root_univ, int64_t n, const double *pos, const double *dir,
                   int *path, double *dist, int *kind, cudaStream_t st);
 void launch_ce_lookup(const World &W, int mat, int64_t n, const double *E, double *out,
@@ -104,5 +110,12 @@ struct ReplayArgs {
 void launch_subtree(const double *own, const double *w, int G, int64_t n, const double *sub_next,
                     const int *off, const int *nfis, double *sub, cudaStream_t st);
 void launch_replay(const World &W, const ReplayArgs &a, int block, cudaStream_t st);
+// device-pointer derivative path: new multigroup tables written in place
+// (*bad set on invalid input), detector tally sums, scaling
+void launch_update_mg(const World &W, int first, int nmat, int G, const double *sigt,
+                      const double *sigs, const double *nusf, int *bad, cudaStream_t st);
+void launch_own_sum(const double *own, int64_t n, int G, int accumulate, double *out,
+                    cudaStream_t st);
+void launch_scale(const double *src, int64_t n, double N, double *dst, cudaStream_t st);
 
 }  // namespace mcgb

@@ -23,6 +23,36 @@ void launch_rng_states(uint64_t seed, uint64_t first_id, int64_t n, int draws, u
     k_rng_states<<<(int)((n + 255) / 256), 256, 0, st>>>(seed, first_id, n, draws, out);
 }
 
+// FP64 throughput probe: each thread runs FP64_CHAINS independent fused
+// multiply-add chains of `iters` steps, so with enough resident warps the FP64
+// pipe, not its latency, sets the rate.  x -> a x + b with 0 < a < 1 stays
+// finite and positive; the sum is stored only if negative (never), so the
+// compiler cannot drop the chains.
+constexpr int FP64_CHAINS = 8;
+
+__global__ void __launch_bounds__(256) k_fp64_rate(long long iters, double a, double b,
+                                                   double *sink)
+{
+    double x[FP64_CHAINS];
+#pragma unroll
+    for (int k = 0; k < FP64_CHAINS; k++) x[k] = 1e-3 * (double)threadIdx.x + (double)k;
+    for (long long i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < FP64_CHAINS; k++) x[k] = fma(x[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < FP64_CHAINS; k++) s += x[k];
+    if (s < 0.0) sink[blockIdx.x] = s;
+}
+
+int fp64_rate_chains() { return FP64_CHAINS; }
+
+void launch_fp64_rate(int grid, long long iters, double *sink, cudaStream_t st)
+{
+    k_fp64_rate<<<grid, 256, 0, st>>>(iters, 0.999999, 1e-6, sink);
+}
+
 __global__ void k_log(World W, int64_t n, const double *xi, double *out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -135,3 +135,116 @@ void launch_replay(const World &W, const ReplayArgs &a, int block, cudaStream_t 
 }
 
 }  // namespace mcgb
+
+// ---------------------------------------------------------------------------
+// Device-side counterparts of the host steps around the derivative path, so
+// that callers holding their data on the device (torch tensors) need no host
+// copies.
+
+namespace mcgb {
+
+// New multigroup tables of materials [first, first + nmat) from device arrays
+// sigma_t [nmat][G], sigma_s [nmat][G][G] ([from][to]), nu_sigma_f [nmat][G]:
+// one thread per (material, group) row writes the row and its derived
+// constants with the same expressions the world builder evaluates on the host
+// (1/Sigma_t, mu = nuSigma_f/Sigma_t, floor and fraction, Sigma_s,tot/Sigma_t,
+// the scattering cdf).  A negative value or Sigma_s,tot > Sigma_t sets *bad
+// and leaves that row untouched.
+__global__ void k_update_mg(World W, int first, int nmat, int G, const double *sigt,
+                            const double *sigs, const double *nusf, int *bad)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nmat * G) return;
+    int mi = r / G, g = r - mi * G;
+    int m = first + mi;
+    const double st = sigt[r], nf = nusf[r];
+    const double *row = sigs + (int64_t)r * G;
+    bool ok = st >= 0.0 && nf >= 0.0;
+    double acc = 0.0;
+    for (int h = 0; h < G; h++) {
+        ok = ok && row[h] >= 0.0;
+        acc = acc + row[h];
+    }
+    ok = ok && !(acc > st);
+    if (!ok) {
+        atomicOr(bad, 1);
+        return;
+    }
+    const int go = W.m_goff[m] + g, gg = W.m_ggoff[m] + g * G;
+    double *g_sigt = const_cast<double *>(W.g_sigt), *g_nusf = const_cast<double *>(W.g_nusf);
+    double *g_stot = const_cast<double *>(W.g_stot), *g_mfp = const_cast<double *>(W.g_mfp);
+    double *g_mu = const_cast<double *>(W.g_mu), *g_mufl = const_cast<double *>(W.g_mufl);
+    double *g_mufr = const_cast<double *>(W.g_mufr), *g_ps = const_cast<double *>(W.g_ps);
+    double *gg_sigs = const_cast<double *>(W.gg_sigs), *gg_scdf = const_cast<double *>(W.gg_scdf);
+    g_sigt[go] = st;
+    g_nusf[go] = nf;
+    g_stot[go] = acc;
+    g_mfp[go] = st > 0.0 ? 1.0 / st : MCGB_INF;
+    double mu = st > 0.0 ? nf / st : 0.0;
+    double fl = floor(mu);
+    g_mu[go] = mu;
+    g_mufl[go] = fl;
+    g_mufr[go] = mu - fl;
+    g_ps[go] = st > 0.0 ? acc / st : 0.0;
+    double run = 0.0;
+    for (int h = 0; h < G; h++) {
+        gg_sigs[gg + h] = row[h];
+        run = run + row[h];
+        gg_scdf[gg + h] = acc > 0.0 ? (h == G - 1 ? 1.0 : run / acc) : 1.0;
+    }
+}
+
+// material fissile flags after an update: any nuSigma_f > 0
+__global__ void k_update_fissile(World W, int first, int nmat, int G)
+{
+    int mi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mi >= nmat) return;
+    int m = first + mi;
+    int fis = 0;
+    for (int g = 0; g < G; g++) fis |= W.g_nusf[W.m_goff[m] + g] > 0.0;
+    const_cast<int *>(W.m_fissile)[m] = fis;
+}
+
+void launch_update_mg(const World &W, int first, int nmat, int G, const double *sigt,
+                      const double *sigs, const double *nusf, int *bad, cudaStream_t st)
+{
+    int rows = nmat * G;
+    k_update_mg<<<(rows + 127) / 128, 128, 0, st>>>(W, first, nmat, G, sigt, sigs, nusf, bad);
+    k_update_fissile<<<(nmat + 127) / 128, 128, 0, st>>>(W, first, nmat, G);
+}
+
+// out[q] (+)= sum_j own[j G + q]: one block per group, a fixed reduction order
+__global__ void k_own_sum(const double *own, int64_t n, int G, int accumulate, double *out)
+{
+    __shared__ double part[256];
+    int q = blockIdx.x;
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s += own[j * G + q];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = accumulate ? out[q] + part[0] : part[0];
+}
+
+void launch_own_sum(const double *own, int64_t n, int G, int accumulate, double *out,
+                    cudaStream_t st)
+{
+    k_own_sum<<<G, 256, 0, st>>>(own, n, G, accumulate, out);
+}
+
+// dst[k] = src[k] / N for k < n
+__global__ void k_scale(const double *src, int64_t n, double N, double *dst)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[k] = src[k] / N;
+}
+
+void launch_scale(const double *src, int64_t n, double N, double *dst, cudaStream_t st)
+{
+    if (n > 0) k_scale<<<(int)((n + 255) / 256), 256, 0, st>>>(src, n, N, dst);
+}
+
+}  // namespace mcgb

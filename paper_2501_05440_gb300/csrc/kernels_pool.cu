@@ -166,7 +166,12 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
     for (int i = threadIdx.x; i < P; i += T) q.fate[i] = SLOT_EMPTY;
     if (threadIdx.x == 0) s_exhausted = 0;
     __syncthreads();
+    long long passes = 0;
     for (;;) {
+        if (a.max_passes > 0 && ++passes > a.max_passes) {   // block-uniform
+            if (threadIdx.x == 0) atomicOr(R.err, ERR_ITER);
+            break;
+        }
         // ---- refill empty slots from the work counter
         if (!s_exhausted) {
             int n_empty = build_list<P, T>(q, hist, cnt, [&](int i) { return q.fate[i] == SLOT_EMPTY ? 0 : -1; });
@@ -335,7 +340,12 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
     for (int i = lane; i < PW; i += 32) q.fate[i] = SLOT_EMPTY;
     __syncwarp();
     bool exhausted = false;
+    long long passes = 0;
     for (;;) {
+        if (a.max_passes > 0 && ++passes > a.max_passes) {   // warp-uniform
+            if (lane == 0) atomicOr(R.err, ERR_ITER);
+            break;
+        }
         if (!exhausted) {
             int n_empty = warp_list<PW>(q.list, [&](int i) { return q.fate[i] == SLOT_EMPTY; });
             int base = 0;

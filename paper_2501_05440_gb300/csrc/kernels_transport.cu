@@ -341,7 +341,12 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
     bool alive = false, done = false;
     double kt = 0.0, kc = 0.0;
     const ProblemDev *Pd = W.prob;
+    long long passes = 0;
     for (;;) {
+        if (a.max_passes > 0 && ++passes > a.max_passes) {   // warp-uniform
+            if (lane == 0) atomicOr(R.err, ERR_ITER);
+            break;
+        }
         bool need = !alive && !done;
         unsigned m = __ballot_sync(0xffffffffu, need);
         if (m) {

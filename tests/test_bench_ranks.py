@@ -66,8 +66,8 @@ def test_two_gloo_ranks_aggregate_like_torchrun(tmp_path):
 def test_reference_arm_nonzero_rank_exits_quietly():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True,
-                       text=True, timeout=120)
+                        "--gpus", "2", "--steps", "1", "--warmup", "3"], env=env,
+                       capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
 
@@ -95,3 +95,30 @@ def test_reference_arm_line_on_cpu():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_gpus_flag_starts_ranks_or_refuses():
+    """--gpus N is honoured: outside torchrun bench.py starts N ranks itself,
+    and refuses (exit 2) when it cannot, instead of running one."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    env.pop("WORLD_SIZE", None)
+    # the CUDA arm with no GPU visible: refused, nothing run
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2"],
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 2 and "refusing" in r.stderr
+    # a rank count that contradicts the launcher's
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2"],
+                       env=dict(env, WORLD_SIZE="1", RANK="0"), capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 2 and "refusing" in r.stderr
+    # the reference arm (CPU oracle) under two ranks started by bench.py itself:
+    # rank 0 prints the one JSON line, rank 1 exits without work
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "0"],
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    import json
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference" and out["n_gpus"] == 2

@@ -1,9 +1,11 @@
 """Argument and state checks of the time, free-gas and shard calls: bad
-arguments fail with MCGB_E_INVALID_ARG (-1) or MCGB_E_STATE (-2), nothing runs."""
+arguments fail with MCGB_E_INVALID_ARG (-1) or MCGB_E_STATE (-2), nothing runs.
+Iteration limits fail with MCGB_E_TIMEOUT (-7)."""
 import numpy as np
 import pytest
 
 import workloads as W
+from tests.gpu_util import assert_same_histories
 
 pytestmark = pytest.mark.gpu
 
@@ -61,3 +63,34 @@ def test_shard_states_and_arguments(mcgb):
                         [1e-6, 1e-5], t_cut=1e-5, t_edges=[0.0, 1e-5], n=100)
     ct = mcgb.load_problem(mcgb.Context(mode=1), t)
     assert _code(ct.shard_begin, 100, 0, 100, 1) == -1   # time-dependent: fixed source only
+
+
+# Iteration limits: reaching one is an error status the host reads (no trap, no
+# hang); the unfinished histories are abandoned and the device stays usable.
+@pytest.mark.parametrize("mode", [0, 2])
+def test_event_iteration_limit_times_out(mcgb, mode):
+    pb = W.pin_cell_mg(n=2000, inactive=0, active=1)
+    c = mcgb.load_problem(mcgb.Context(mode=mode, max_iterations=1), pb)
+    with pytest.raises(mcgb.McgbError) as e:
+        c.run()
+    assert e.value.code == -7
+    ok = mcgb.load_problem(mcgb.Context(mode=mode), pb)
+    ok.run()
+    assert ok.get_k()["k"] > 0
+
+
+@pytest.mark.parametrize("pool", [0, 512, 64, -1])
+@pytest.mark.parametrize("fixed", [False, True])
+def test_persistent_pass_limit_times_out(mcgb, pool, fixed):
+    pb = W.diff_slab(n=3000, batches=5) if fixed else W.pin_cell_mg(n=3000, inactive=1, active=1)
+    c = mcgb.load_problem(mcgb.Context(mode=1, pool=pool, max_iterations=2), pb)
+    with pytest.raises(mcgb.McgbError) as e:
+        c.run()
+    assert e.value.code == -7
+    # a limit the run never reaches changes nothing
+    a = mcgb.load_problem(mcgb.Context(mode=1, pool=pool, record_histories=True,
+                                       max_iterations=1_000_000), pb)
+    a.run()
+    b = mcgb.load_problem(mcgb.Context(mode=1, pool=pool, record_histories=True), pb)
+    b.run()
+    assert_same_histories(a.get_histories(), b.get_histories())

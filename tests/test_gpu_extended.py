@@ -1,5 +1,7 @@
 """GPU checks beyond the small parity cases: derivatives, batching, autograd,
 full-size runs sampled history by history, error paths and degenerate inputs."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -78,6 +80,62 @@ def test_autograd_function(mcgb):
     assert _close_vec(st.grad.numpy(), o["sigma_t"], 1e-8)
     assert _close_vec(ss.grad.numpy(), o["sigma_s"], 1e-8)
     assert _close_vec(nf.grad.numpy(), o["nu_sigma_f"], 1e-8)
+
+
+def test_autograd_function_cuda_tensors(mcgb):
+    """CUDA tensors take the device-pointer calls (no host copies of any array)
+    and give the host-array path's results; a second forward with changed
+    cross sections uses the updated device tables."""
+    import torch
+
+    from paper_2501_05440_gb300.autograd import detector_tally
+    pb = W.diff_slab(n=10, shield_len=8.0)
+    n, seed, det = 3000, 5, pb["detector_cell"]
+    dev = torch.device("cuda", 0)
+    st0 = np.array([m["sigma_t"] for m in pb["materials"]])
+    ss0 = np.array([m["sigma_s"] for m in pb["materials"]])
+    nf0 = np.array([m["nu_sigma_f"] for m in pb["materials"]])
+    c = torch.linspace(0.5, 1.5, pb["G"], dtype=torch.float64)
+    eng = None
+    for scale in (1.0, 1.1):
+        st = torch.tensor(st0 * scale, device=dev, requires_grad=True)
+        ss = torch.tensor(ss0, device=dev, requires_grad=True)
+        nf = torch.tensor(nf0, device=dev, requires_grad=True)
+        if eng is None:
+            eng = mcgb.load_problem(mcgb.Context(mode=1), pb)
+        y = detector_tally(pb, st, ss, nf, n, seed, det, engine=eng)
+        assert y.is_cuda
+        (y * c.to(dev)).sum().backward()
+        assert st.grad.is_cuda and ss.grad.is_cuda and nf.grad.is_cuda
+        p2 = copy.deepcopy(pb)
+        for m in range(len(pb["materials"])):
+            p2["materials"][m]["sigma_t"] = st0[m] * scale
+        o = Oracle(p2, strict=True).grad(n=n, seed=seed, cell=det, weights=c.numpy())
+        assert rel_close(y.detach().cpu().numpy(), o["tally"], 1e-9, 1e-300), scale
+        assert _close_vec(st.grad.cpu().numpy(), o["sigma_t"], 1e-8), scale
+        assert _close_vec(ss.grad.cpu().numpy(), o["sigma_s"], 1e-8), scale
+        assert _close_vec(nf.grad.cpu().numpy(), o["nu_sigma_f"], 1e-8), scale
+
+
+def test_device_material_update_rejects_invalid(mcgb):
+    import torch
+    pb = W.diff_slab(n=10, shield_len=8.0)
+    G, nm = pb["G"], len(pb["materials"])
+    eng = mcgb.load_problem(mcgb.Context(mode=1), pb)
+    st = torch.tensor(np.array([m["sigma_t"] for m in pb["materials"]]), device="cuda")
+    ss = torch.tensor(np.array([m["sigma_s"] for m in pb["materials"]]), device="cuda")
+    nf = torch.tensor(np.array([m["nu_sigma_f"] for m in pb["materials"]]), device="cuda")
+    st[1, 2] = 0.5 * ss[1, 2].sum()          # scattering above total
+    eng.update_material_mg_dev(0, nm, st.data_ptr(), ss.data_ptr(), nf.data_ptr())
+    out = torch.empty(G, dtype=torch.float64, device="cuda")
+    with pytest.raises(mcgb.McgbError) as e:
+        eng.forward_fixed_dev(1000, 1, pb["detector_cell"], out.data_ptr())
+    assert e.value.code == -1
+    # the flag is cleared: valid tables run
+    st[1, 2] = 2.0 * ss[1, 2].sum() + 0.1
+    eng.update_material_mg_dev(0, nm, st.data_ptr(), ss.data_ptr(), nf.data_ptr())
+    eng.forward_fixed_dev(1000, 1, pb["detector_cell"], out.data_ptr())
+    assert torch.all(out >= 0)
 
 
 @pytest.mark.parametrize("pool", [0, -1])
