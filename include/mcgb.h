@@ -232,26 +232,39 @@ typedef struct {
     int32_t cell, ix, iy, ucell, mat, child;
     int64_t parent;
 } mcgb_site;
-/* This context transports source indices [j0, j0 + n) of every cycle of an
- * N-history k-eigenvalue power iteration (random streams cycle 2^32 + j as in
- * a single-device run).  The caller exchanges, after every cycle, the k sums,
- * tally sums and ordered banks of all ranks: concatenated in rank order the
- * banks are the global (parent, child)-ordered bank, from which every rank
- * resamples its own sources (site of source j: floor((j + xi) M / N), xi from
- * mcgb_cycle_xi).  Fails for time-dependent problems. */
-int mcgb_shard_begin(mcgb_ctx *ctx, int64_t N, int64_t j0, int64_t n, uint64_t seed);
-/* Transport this rank's n histories of `cycle`: cycle 0 samples the source;
- * later cycles are born at src[0..n) (required).  ksum[2] = sums over the
- * rank's histories of the track-length and collision k estimators (divide the
- * all-rank sums by N); *m = sites banked by the rank. */
-int mcgb_shard_cycle(mcgb_ctx *ctx, int cycle, const mcgb_site *src, double ksum[2], int64_t *m);
-/* The last cycle's sites of this rank in (parent, child) order, cap elements. */
-int mcgb_shard_bank(mcgb_ctx *ctx, size_t cap, mcgb_site *out, size_t *needed);
-/* The last cycle's tally sums of this rank (all tallies concatenated, layout of
- * mcgb_get_tally, before division by N), cap elements. */
-int mcgb_shard_tally(mcgb_ctx *ctx, size_t cap, double *sums, size_t *needed);
-/* The resampling draw of a cycle (first draw of stream cycle 2^32 + 2^32 - 1). */
-int mcgb_cycle_xi(mcgb_ctx *ctx, int cycle, double *xi);
+/* One rank's share of an N-history k-eigenvalue power iteration of
+ * inactive + active cycles: this context transports source indices
+ * [j0, j0 + n) of every cycle (random streams cycle 2^32 + j as in a
+ * single-device run).  Every cycle is three calls, in order:
+ *   mcgb_shard_cycle   transport the slice; *m = sites the rank banked;
+ *   mcgb_shard_export  write the rank's sites in (parent, child) order and its
+ *                      sums [k_tl, k_c, tally sums (layout of mcgb_get_tally,
+ *                      before division by N)] to caller device buffers;
+ *   (the caller sums the sums over ranks and concatenates the ranks' sites in
+ *    rank order -- the global (parent, child)-ordered bank -- moving bytes
+ *    only)
+ *   mcgb_shard_import  fold the all-rank sums into the run's statistics and
+ *                      resample this rank's sources of the next cycle from the
+ *                      global bank: source j takes site floor((j + xi) M / N),
+ *                      at most M - 1, xi the cycle's draw -- exactly what one
+ *                      device does, so the ranks together reproduce the
+ *                      single-device run.
+ * mcgb_shard_finish after the last cycle makes k, per-cycle k and bank sizes
+ * and the tallies available through mcgb_get_k / mcgb_get_cycle_k /
+ * mcgb_get_tally, as after mcgb_run_eigenvalue.  Every pointer of export and
+ * import is a device pointer on the context's device, used in order on its
+ * stream.  Calls out of order fail with MCGB_E_STATE; an empty global bank
+ * fails import with MCGB_E_STATE.  Time-dependent problems are rejected. */
+int mcgb_shard_begin(mcgb_ctx *ctx, int64_t N, int64_t j0, int64_t n, int inactive, int active,
+                     uint64_t seed);
+int mcgb_shard_cycle(mcgb_ctx *ctx, int cycle, int64_t *m);
+/* bank_cap >= *m sites, sums_cap >= *n_sums; bank and sums NULL: only *n_sums */
+int mcgb_shard_export(mcgb_ctx *ctx, mcgb_site *bank, size_t bank_cap, double *sums,
+                      size_t sums_cap, size_t *n_sums);
+/* sums: the all-rank sums; bank[0..M): the global ordered bank */
+int mcgb_shard_import(mcgb_ctx *ctx, int cycle, const double *sums, const mcgb_site *bank,
+                      int64_t M);
+int mcgb_shard_finish(mcgb_ctx *ctx);
 
 /* --------------------------------------------------------------------------- */
 /* results                                                                      */

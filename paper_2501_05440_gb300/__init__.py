@@ -117,9 +117,9 @@ def lib():
                 "mcgb_set_max_collisions": [P, i32],
                 "mcgb_set_time": [P, d, d], "mcgb_set_inverse_speeds": [P, i32, P],
                 "mcgb_set_free_gas": [P, d, d],
-                "mcgb_shard_begin": [P, i64, i64, i64, u64], "mcgb_shard_cycle": [P, i32, P, P, P],
-                "mcgb_shard_bank": [P, sz, P, P], "mcgb_shard_tally": [P, sz, P, P],
-                "mcgb_cycle_xi": [P, i32, P],
+                "mcgb_shard_begin": [P, i64, i64, i64, i32, i32, u64],
+                "mcgb_shard_cycle": [P, i32, P], "mcgb_shard_export": [P, P, sz, P, sz, P],
+                "mcgb_shard_import": [P, i32, P, P, i64], "mcgb_shard_finish": [P],
                 "mcgb_set_tally_time_bins": [P, i32, i32, P],
                 "mcgb_run_eigenvalue": [P, i64, i32, i32, u64],
                 "mcgb_run_fixed_source": [P, i64, i32, u64],
@@ -272,39 +272,33 @@ class Context:
         _chk(self.L.mcgb_set_max_collisions(self.h, m))
 
     # sharded power iteration (see paper_2501_05440_gb300.sharded)
-    def shard_begin(self, N, j0, n, seed):
-        _chk(self.L.mcgb_shard_begin(self.h, int(N), int(j0), int(n), int(seed)))
+    def shard_begin(self, N, j0, n, inactive, active, seed):
+        _chk(self.L.mcgb_shard_begin(self.h, int(N), int(j0), int(n), int(inactive), int(active),
+                                     int(seed)))
 
-    def shard_cycle(self, cycle, sources=None):
-        """Transport this rank's histories of `cycle`; returns (k sums[2], sites banked)."""
-        ks = np.zeros(2)
+    def shard_cycle(self, cycle):
+        """Transport this rank's histories of `cycle`; returns the sites it banked."""
         m = C.c_int64()
-        src = None
-        if sources is not None:
-            src = np.ascontiguousarray(sources, dtype=SITE_DTYPE)
-            src = src.ctypes.data_as(C.c_void_p)
-        _chk(self.L.mcgb_shard_cycle(self.h, int(cycle), src, _p(ks), C.byref(m)))
-        return ks, m.value
+        _chk(self.L.mcgb_shard_cycle(self.h, int(cycle), C.byref(m)))
+        return m.value
 
-    def shard_bank(self):
-        need = C.c_size_t()
-        self.L.mcgb_shard_bank(self.h, 0, None, C.byref(need))
-        out = np.zeros(need.value, dtype=SITE_DTYPE)
-        _chk(self.L.mcgb_shard_bank(self.h, need.value, out.ctypes.data_as(C.c_void_p),
-                                    C.byref(need)))
-        return out
+    def shard_sums_size(self):
+        n = C.c_size_t()
+        _chk(self.L.mcgb_shard_export(self.h, None, 0, None, 0, C.byref(n)))
+        return n.value
 
-    def shard_tally(self):
-        need = C.c_size_t()
-        self.L.mcgb_shard_tally(self.h, 0, None, C.byref(need))
-        out = np.zeros(need.value)
-        _chk(self.L.mcgb_shard_tally(self.h, need.value, _p(out), C.byref(need)))
-        return out
+    def shard_export(self, bank, bank_cap, sums, sums_cap):
+        """bank, sums: device addresses (ints) of 64-byte site records and doubles"""
+        n = C.c_size_t()
+        _chk(self.L.mcgb_shard_export(self.h, C.c_void_p(bank), int(bank_cap), C.c_void_p(sums),
+                                      int(sums_cap), C.byref(n)))
 
-    def cycle_xi(self, cycle):
-        x = C.c_double()
-        _chk(self.L.mcgb_cycle_xi(self.h, int(cycle), C.byref(x)))
-        return x.value
+    def shard_import(self, cycle, sums, bank, M):
+        _chk(self.L.mcgb_shard_import(self.h, int(cycle), C.c_void_p(sums), C.c_void_p(bank),
+                                      int(M)))
+
+    def shard_finish(self):
+        _chk(self.L.mcgb_shard_finish(self.h))
 
     def set_free_gas(self, kT, cut=0.0):
         _chk(self.L.mcgb_set_free_gas(self.h, float(kT), float(cut)))

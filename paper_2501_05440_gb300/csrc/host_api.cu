@@ -179,7 +179,10 @@ struct mcgb_ctx {
     struct {
         bool on = false;
         int64_t N = 0, j0 = 0, n = 0, M = 0;
-        std::vector<double> tally;   // last cycle's tally sums, replicas reduced
+        int inactive = 0, ncyc = 0, cyc = 0;
+        int state = 0;               // 0: transport next, 1: export next, 2: import next
+        DevAlloc mem;
+        double *sums = nullptr;      // the rank's [k_tl, k_c, tally...] sums of the last cycle
     } shard;
 };
 
@@ -1360,11 +1363,14 @@ int mcgb_get_tally(mcgb_ctx *ctx, int tally, double *mean, double *sd, size_t ca
 // j0 through its generation base.  Bank order, resampling and statistics are
 // the caller's exchange step (the concatenation of the ranks' ordered banks in
 // rank order is the global (parent, child) order).
-int mcgb_shard_begin(mcgb_ctx *c, int64_t N, int64_t j0, int64_t n, uint64_t seed)
+int mcgb_shard_begin(mcgb_ctx *c, int64_t N, int64_t j0, int64_t n, int inactive, int active,
+                     uint64_t seed)
 {
     if (!c) return fail(MCGB_E_INVALID_ARG, "null context");
     if (N <= 0 || N > (int64_t)1 << 30 || j0 < 0 || n <= 0 || j0 + n > N)
         return fail(MCGB_E_INVALID_ARG, "bad shard");
+    if (inactive < 0 || active < 1 || inactive + active > 4096)
+        return fail(MCGB_E_INVALID_ARG, "bad cycle counts");
     if (c->def.time_on) return fail(MCGB_E_INVALID_ARG, "time dependence is for fixed-source runs");
     CK(cudaSetDevice(c->device));
     c->eig.on = false;
@@ -1376,7 +1382,11 @@ int mcgb_shard_begin(mcgb_ctx *c, int64_t N, int64_t j0, int64_t n, uint64_t see
     RunState &r = c->rs;
     cudaStream_t st = c->stream;
     const World &W = c->world->W;
-    CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)W.acc_size * W.nrep, st));
+    int acc = W.acc_size;
+    CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)acc * W.nrep, st));
+    CK(cudaMemsetAsync(r.tsum, 0, sizeof(double) * (size_t)std::max(acc, 1), st));
+    CK(cudaMemsetAsync(r.tsum2, 0, sizeof(double) * (size_t)std::max(acc, 1), st));
+    CK(cudaMemsetAsync(r.kout, 0, sizeof(double) * 2 * 4096, st));
     CK(cudaMemsetAsync(r.cnt, 0, sizeof(unsigned long long) * 8, st));
     CK(cudaMemsetAsync(r.err, 0, sizeof(int), st));
     int64_t base[2] = {-j0, n - j0};
@@ -1384,6 +1394,8 @@ int mcgb_shard_begin(mcgb_ctx *c, int64_t N, int64_t j0, int64_t n, uint64_t see
     std::vector<int> iota(n);
     for (int64_t k = 0; k < n; k++) iota[k] = (int)k;
     CK(cudaMemcpyAsync(r.src_idx, iota.data(), 4 * n, cudaMemcpyHostToDevice, st));
+    c->shard.mem.release();
+    CKR(c->shard.mem.get(c->shard.sums, 2 + acc));
     CK(cudaStreamSynchronize(st));
     c->counters = mcgb_counters{};
     c->counters.world_bytes = (int64_t)c->world->bytes;
@@ -1393,55 +1405,42 @@ int mcgb_shard_begin(mcgb_ctx *c, int64_t N, int64_t j0, int64_t n, uint64_t see
     c->shard.j0 = j0;
     c->shard.n = n;
     c->shard.M = 0;
+    c->shard.inactive = inactive;
+    c->shard.ncyc = inactive + active;
+    c->shard.cyc = 0;
+    c->shard.state = 0;
+    c->cyc_m.assign(inactive + active, 0);
+    c->cyc_ktl.assign(inactive + active, 0.0);
+    c->cyc_kc.assign(inactive + active, 0.0);
     return MCGB_OK;
 }
 
-int mcgb_shard_cycle(mcgb_ctx *c, int cycle, const mcgb_site *src, double ksum[2], int64_t *m)
+int mcgb_shard_cycle(mcgb_ctx *c, int cycle, int64_t *m)
 {
     if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
-    if (cycle < 0 || cycle > 4095 || (cycle > 0 && !src) || !ksum || !m)
-        return fail(MCGB_E_INVALID_ARG, "bad shard cycle");
+    if (!m) return fail(MCGB_E_INVALID_ARG, "null output");
+    if (cycle != c->shard.cyc || c->shard.state != 0 || cycle >= c->shard.ncyc)
+        return fail(MCGB_E_STATE, "cycles run in order: transport, export, import");
     CK(cudaSetDevice(c->device));
     RunState &r = c->rs;
     cudaStream_t st = c->stream;
     const World &W = c->world->W;
     const int64_t n = c->shard.n;
     Bank &Bs = r.bank[0], &Bd = r.bank[1];
-    if (src) {
-        std::vector<double> x(n), y(n), z(n), t(n);
-        std::vector<int> cell(n), ix(n), iy(n), ucell(n), mat(n);
-        for (int64_t k = 0; k < n; k++) {
-            x[k] = src[k].x; y[k] = src[k].y; z[k] = src[k].z; t[k] = src[k].t;
-            cell[k] = src[k].cell; ix[k] = src[k].ix; iy[k] = src[k].iy;
-            ucell[k] = src[k].ucell; mat[k] = src[k].mat;
-        }
-        CK(cudaMemcpyAsync(Bs.x, x.data(), 8 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Bs.y, y.data(), 8 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Bs.z, z.data(), 8 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Bs.t, t.data(), 8 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Bs.cell, cell.data(), 4 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Bs.ix, ix.data(), 4 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Bs.iy, iy.data(), 4 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Bs.ucell, ucell.data(), 4 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Bs.mat, mat.data(), 4 * n, cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));   // the host vectors go out of scope
-    }
+    double *sums = c->shard.sums;
     CK(cudaMemsetAsync(r.bank_n, 0, sizeof(int), st));
-    CK(cudaMemsetAsync(r.kout, 0, sizeof(double) * 2, st));
+    CK(cudaMemsetAsync(sums, 0, sizeof(double) * 2, st));
     RunBufs R = run_bufs(c, nullptr, -1, 0);
-    CKR(transport_generation(c, R, cycle, n, r.gen_base[0], src ? r.src_idx : nullptr, 1, Bs, Bd));
-    launch_reduce_gen(r.P, n, nullptr, r.kout, r.cnt, st);
+    CKR(transport_generation(c, R, cycle, n, r.gen_base[0], cycle > 0 ? r.src_idx : nullptr, 1, Bs,
+                             Bd));
+    launch_reduce_gen(r.P, n, nullptr, sums, r.cnt, st);
     scan_exclusive(r.P.nfis, r.off, n, r.M, r.scratch, st);
     launch_perm(Bd, r.off, r.M, r.perm, c->sms * 4, st);
-    c->shard.tally.assign((size_t)std::max(W.acc_size, 0), 0.0);
     if (W.acc_size > 0) {
-        launch_acc_reduce(r.tacc, W.acc_size, W.nrep, r.tsum, st);
-        CK(cudaMemcpyAsync(c->shard.tally.data(), r.tsum, sizeof(double) * W.acc_size,
-                           cudaMemcpyDeviceToHost, st));
+        launch_acc_reduce(r.tacc, W.acc_size, W.nrep, sums + 2, st);
         CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)W.acc_size * W.nrep, st));
     }
     c->launches += 5;
-    CK(cudaMemcpyAsync(ksum, r.kout, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
     int64_t M;
     int err;
     CKR(read_flags(c, M, err));
@@ -1451,6 +1450,7 @@ int mcgb_shard_cycle(mcgb_ctx *c, int cycle, const mcgb_site *src, double ksum[2
     if (err & ERR_SOURCE) return fail(MCGB_E_STATE, "source sampling failed");
     if (err & ERR_ITER) return fail(MCGB_E_TIMEOUT, "persistent event loop pass limit reached");
     c->shard.M = M;
+    c->shard.state = 1;
     *m = M;
     c->counters.histories += n;
     c->counters.generations += 1;
@@ -1458,59 +1458,101 @@ int mcgb_shard_cycle(mcgb_ctx *c, int cycle, const mcgb_site *src, double ksum[2
     return MCGB_OK;
 }
 
-int mcgb_shard_bank(mcgb_ctx *c, size_t cap, mcgb_site *out, size_t *needed)
+int mcgb_shard_export(mcgb_ctx *c, mcgb_site *bank, size_t bank_cap, double *sums, size_t sums_cap,
+                      size_t *n_sums)
 {
     if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
+    const size_t ns = 2 + (size_t)std::max(c->world->W.acc_size, 0);
+    if (n_sums) *n_sums = ns;
+    if (!sums && !bank) return MCGB_OK;   // size query
+    if (c->shard.state != 1) return fail(MCGB_E_STATE, "run mcgb_shard_cycle first");
     const int64_t M = c->shard.M;
-    if (needed) *needed = (size_t)M;
-    if (cap < (size_t)M) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
-    if (M == 0) return MCGB_OK;
-    if (!out) return fail(MCGB_E_INVALID_ARG, "null output");
+    if (bank_cap < (size_t)M || sums_cap < ns) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    if ((M > 0 && !bank) || !sums) return fail(MCGB_E_INVALID_ARG, "null output");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = c->stream;
+    launch_pack_sites(c->rs.bank[1], c->rs.perm, M, c->shard.j0, reinterpret_cast<ShardSite *>(bank),
+                      st);
+    CK(cudaMemcpyAsync(sums, c->shard.sums, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
+    c->launches += 1;
+    CK(cudaGetLastError());
+    c->shard.state = 2;
+    return MCGB_OK;
+}
+
+int mcgb_shard_import(mcgb_ctx *c, int cycle, const double *sums, const mcgb_site *bank, int64_t M)
+{
+    if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
+    if (cycle != c->shard.cyc || c->shard.state != 2)
+        return fail(MCGB_E_STATE, "cycles run in order: transport, export, import");
+    if (!sums || M < 0 || (M > 0 && !bank)) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (M == 0) {
+        c->shard.on = false;
+        return fail(MCGB_E_STATE, "fission bank empty after cycle " + std::to_string(cycle));
+    }
+    CK(cudaSetDevice(c->device));
     RunState &r = c->rs;
     cudaStream_t st = c->stream;
-    const Bank &B = r.bank[1];
-    std::vector<int> perm(M), par(M), ch(M), cell(M), ix(M), iy(M), ucell(M), mat(M);
-    std::vector<double> x(M), y(M), z(M), t(M);
-    CK(cudaMemcpyAsync(perm.data(), r.perm, 4 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(par.data(), B.parent, 4 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ch.data(), B.child, 4 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(cell.data(), B.cell, 4 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ix.data(), B.ix, 4 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(iy.data(), B.iy, 4 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ucell.data(), B.ucell, 4 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(mat.data(), B.mat, 4 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(x.data(), B.x, 8 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(y.data(), B.y, 8 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(z.data(), B.z, 8 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(t.data(), B.t, 8 * M, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    for (int64_t k = 0; k < M; k++) {
-        int b = perm[k];
-        mcgb_site &o = out[k];
-        o.x = x[b]; o.y = y[b]; o.z = z[b]; o.t = t[b];
-        o.cell = cell[b]; o.ix = ix[b]; o.iy = iy[b]; o.ucell = ucell[b]; o.mat = mat[b];
-        o.child = ch[b];
-        o.parent = c->shard.j0 + par[b];
+    const int acc = c->world->W.acc_size;
+    const double N = (double)c->shard.N;
+    launch_shard_stats(sums, acc, N, cycle, cycle >= c->shard.inactive, r.kout, r.tsum, r.tsum2, st);
+    c->launches += 1;
+    c->cyc_m[cycle] = M;
+    if (cycle + 1 < c->shard.ncyc) {
+        if (c->shard.n > r.bank[0].cap) return fail(MCGB_E_BANK_OVERFLOW, "source slice above the bank");
+        uint64_t rs = rng_stream(c->world->probs[0].seed, ((uint64_t)cycle << 32) + 0xFFFFFFFFULL);
+        double xi = draw_host(rs);
+        launch_unpack_sources(reinterpret_cast<const ShardSite *>(bank), M, c->shard.N, c->shard.j0,
+                              c->shard.n, xi, r.bank[0], st);
+        c->launches += 1;
     }
+    CK(cudaGetLastError());
+    c->shard.cyc = cycle + 1;
+    c->shard.state = 0;
     return MCGB_OK;
 }
 
-int mcgb_shard_tally(mcgb_ctx *c, size_t cap, double *sums, size_t *needed)
+int mcgb_shard_finish(mcgb_ctx *c)
 {
     if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
-    size_t n = c->shard.tally.size();
-    if (needed) *needed = n;
-    if (cap < n) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
-    if (n && sums) std::memcpy(sums, c->shard.tally.data(), sizeof(double) * n);
-    return MCGB_OK;
-}
-
-int mcgb_cycle_xi(mcgb_ctx *c, int cycle, double *xi)
-{
-    if (!c || !c->world || c->world->probs.empty() || cycle < 0 || cycle > 4095 || !xi)
-        return fail(MCGB_E_INVALID_ARG, "bad argument (begin a run first)");
-    uint64_t rs = rng_stream(c->world->probs[0].seed, ((uint64_t)cycle << 32) + 0xFFFFFFFFULL);
-    *xi = draw_host(rs);
+    if (c->shard.cyc < c->shard.ncyc) return fail(MCGB_E_STATE, "cycles remain to be run");
+    CK(cudaSetDevice(c->device));
+    c->shard.on = false;
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const int ncyc = c->shard.ncyc, inactive = c->shard.inactive, active = ncyc - inactive;
+    const int acc = c->world->W.acc_size;
+    const double N = (double)c->shard.N;
+    std::vector<double> kout(2 * ncyc), ts(std::max(acc, 1)), ts2(std::max(acc, 1));
+    CK(cudaMemcpyAsync(kout.data(), r.kout, sizeof(double) * 2 * ncyc, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ts.data(), r.tsum, sizeof(double) * acc, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ts2.data(), r.tsum2, sizeof(double) * acc, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double ks[3] = {0, 0, 0}, ks2[3] = {0, 0, 0};
+    for (int cyc = 0; cyc < ncyc; cyc++) {
+        c->cyc_ktl[cyc] = kout[2 * cyc] / N;
+        c->cyc_kc[cyc] = kout[2 * cyc + 1] / N;
+        if (cyc >= inactive) {
+            double kv[3] = {c->cyc_ktl[cyc], c->cyc_kc[cyc], (double)c->cyc_m[cyc] / N};
+            for (int q = 0; q < 3; q++) {
+                ks[q] += kv[q];
+                ks2[q] += kv[q] * kv[q];
+            }
+        }
+    }
+    for (int q = 0; q < 3; q++) mean_sd(ks[q], ks2[q], active, c->k[2 * q], c->k[2 * q + 1]);
+    DeviceWorld &dw = *c->world;
+    c->t_mean.assign(c->def.tallies.size(), {});
+    c->t_sd.assign(c->def.tallies.size(), {});
+    for (size_t t = 0; t < c->def.tallies.size(); t++) {
+        int gt = dw.tally_first[0] + (int)t;
+        int nb = dw.t_nbins[gt] * dw.t_ne[gt] * std::max(1, dw.t_ntb[gt]);
+        c->t_mean[t].resize(nb);
+        c->t_sd[t].resize(nb);
+        for (int b = 0; b < nb; b++)
+            mean_sd(ts[dw.t_off[gt] + b], ts2[dw.t_off[gt] + b], active, c->t_mean[t][b],
+                    c->t_sd[t][b]);
+    }
     return MCGB_OK;
 }
 

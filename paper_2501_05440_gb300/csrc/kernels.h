@@ -74,6 +74,14 @@ void launch_resample_dev(const int *perm, const int *M, int64_t N, const double 
 // end of a replayed cycle: bank size into bank_m[*cyc], then ++*cyc
 void launch_cycle_end(int *cyc_dev, const int *M, int64_t *bank_m, cudaStream_t st);
 void launch_acc_reduce(const double *tacc, int acc_size, int nrep, double *out, cudaStream_t st);
+// sharded power iteration: pack the rank's ordered sites, resample its next
+// sources from the global bank, fold the all-rank sums into the statistics
+void launch_pack_sites(const Bank &B, const int *perm, int64_t M, int64_t j0, ShardSite *out,
+                       cudaStream_t st);
+void launch_unpack_sources(const ShardSite *bank, int64_t M, int64_t N, int64_t j0, int64_t n,
+                           double xi, const Bank &Bs, cudaStream_t st);
+void launch_shard_stats(const double *sums, int acc_size, double N, int cyc, int active,
+                        double *kout, double *tsum, double *tsum2, cudaStream_t st);
 void launch_gen_base(const int64_t *base, int nprob, const int *off, const int *M,
                      int64_t *next_base, cudaStream_t st);
 void launch_copy_records(const Particles &P, int64_t n, int *ncoll, int *ncross, uint64_t *rng,

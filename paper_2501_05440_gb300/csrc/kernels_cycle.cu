@@ -392,3 +392,86 @@ extern "C" int mcgb_bank_offsets_noalloc(const int32_t *n_fis, int64_t n, int32_
         return set_error(-3, (std::string("mcgb_bank_offsets_noalloc: ") + cudaGetErrorString(e)).c_str());
     return 0;
 }
+
+// ---------------------------------------------------------------------------
+// Sharded power iteration: one rank's share of the per-cycle exchange.
+
+namespace mcgb {
+
+// The rank's sites in (parent, child) order as records: out[k] = site perm[k]
+// of B, its parent made global (j0 + local index).
+__global__ void k_pack_sites(Bank B, const int *perm, int64_t M, int64_t j0, ShardSite *out)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    int b = perm[k];
+    ShardSite s;
+    s.x = B.x[b];
+    s.y = B.y[b];
+    s.z = B.z[b];
+    s.t = B.t[b];
+    s.cell = B.cell[b];
+    s.ix = B.ix[b];
+    s.iy = B.iy[b];
+    s.ucell = B.ucell[b];
+    s.mat = B.mat[b];
+    s.child = B.child[b];
+    s.parent = j0 + B.parent[b];
+    out[k] = s;
+}
+
+void launch_pack_sites(const Bank &B, const int *perm, int64_t M, int64_t j0, ShardSite *out,
+                       cudaStream_t st)
+{
+    if (M > 0) k_pack_sites<<<(int)((M + 255) / 256), 256, 0, st>>>(B, perm, M, j0, out);
+}
+
+// Sources j0 .. j0+n-1 of the next cycle from the global ordered bank of M
+// sites: systematic resampling with the cycle's draw (site_index, exactly as
+// a single device resamples), written as the birth bank Bs in local order.
+__global__ void k_unpack_sources(const ShardSite *bank, int64_t M, int64_t N, int64_t j0, int64_t n,
+                                 double xi, Bank Bs)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const ShardSite &s = bank[site_index(j0 + k, xi, M, N)];
+    Bs.x[k] = s.x;
+    Bs.y[k] = s.y;
+    Bs.z[k] = s.z;
+    Bs.t[k] = s.t;
+    Bs.cell[k] = s.cell;
+    Bs.ix[k] = s.ix;
+    Bs.iy[k] = s.iy;
+    Bs.ucell[k] = s.ucell;
+    Bs.mat[k] = s.mat;
+}
+
+void launch_unpack_sources(const ShardSite *bank, int64_t M, int64_t N, int64_t j0, int64_t n,
+                           double xi, const Bank &Bs, cudaStream_t st)
+{
+    if (n > 0 && M > 0)
+        k_unpack_sources<<<(int)((n + 255) / 256), 256, 0, st>>>(bank, M, N, j0, n, xi, Bs);
+}
+
+// Statistics of one cycle from the all-rank sums [k_tl, k_c, tally...]: the k
+// sums go to kout[2 cyc ..]; in an active cycle each tally batch value
+// v = sum / N is added to tsum and v^2 to tsum2 (as k_tally_cycle does).
+__global__ void k_shard_stats(const double *sums, int acc_size, double N, int cyc, int active,
+                              double *kout, double *tsum, double *tsum2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 2) kout[2 * cyc + i] = sums[i];
+    if (i >= acc_size || !active) return;
+    double v = sums[2 + i] / N;
+    tsum[i] += v;
+    tsum2[i] += v * v;
+}
+
+void launch_shard_stats(const double *sums, int acc_size, double N, int cyc, int active,
+                        double *kout, double *tsum, double *tsum2, cudaStream_t st)
+{
+    int n = acc_size > 2 ? acc_size : 2;
+    k_shard_stats<<<(n + 255) / 256, 256, 0, st>>>(sums, acc_size, N, cyc, active, kout, tsum, tsum2);
+}
+
+}  // namespace mcgb

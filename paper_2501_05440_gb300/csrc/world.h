@@ -148,6 +148,15 @@ struct Bank {
     int64_t cap;
 };
 
+// One fission-bank site as exchanged between the ranks of a sharded run (the
+// layout of the C ABI's mcgb_site: 64 bytes).
+struct ShardSite {
+    double x, y, z, t;
+    int32_t cell, ix, iy, ucell, mat, child;
+    int64_t parent;
+};
+static_assert(sizeof(ShardSite) == 64, "site records are 64 bytes");
+
 // Per-run device counters and accumulators.
 struct RunBufs {
     double *kacc;          // [KSLOTS][2]: track-length and collision k sums

@@ -47,22 +47,35 @@ def test_time_without_speeds_fails_at_run(mcgb):
 
 
 def test_shard_states_and_arguments(mcgb):
+    import torch
+
+    from paper_2501_05440_gb300 import SITE_DTYPE
     pb = W.pin_cell_mg(n=1000, inactive=1, active=1)
     c = mcgb.load_problem(mcgb.Context(mode=1), pb)
-    assert _code(c.shard_cycle, 0) == -2                 # no shard begun
-    assert _code(c.shard_begin, 1000, 900, 200, 1) == -1  # slice past N
-    assert _code(c.shard_begin, 0, 0, 1, 1) == -1
-    c.shard_begin(1000, 0, 500, 1)
-    assert _code(c.shard_cycle, 1, None) == -1           # later cycles need sources
-    ks, m = c.shard_cycle(0)
-    assert m > 0 and ks[0] > 0
-    bank = c.shard_bank()
-    assert len(bank) == m and np.all(bank["parent"] < 500)
-    assert np.all(np.diff(bank["parent"] * 64 + bank["child"]) > 0)   # (parent, child) order
+    assert _code(c.shard_cycle, 0) == -2                       # no shard begun
+    assert _code(c.shard_begin, 1000, 900, 200, 1, 1, 1) == -1  # slice past N
+    assert _code(c.shard_begin, 0, 0, 1, 1, 1, 1) == -1
+    assert _code(c.shard_begin, 1000, 0, 500, 1, 0, 1) == -1    # no active cycle
+    c.set_stream(torch.cuda.current_stream().cuda_stream)
+    c.shard_begin(1000, 0, 500, 1, 1, 1)
+    ns = c.shard_sums_size()
+    sums = torch.empty(ns, dtype=torch.float64, device="cuda")
+    assert _code(c.shard_import, 0, sums.data_ptr(), 0, 0) == -2   # export first
+    m = c.shard_cycle(0)
+    assert m > 0
+    bank = torch.empty((m, 64), dtype=torch.uint8, device="cuda")
+    assert _code(c.shard_export, bank.data_ptr(), m - 1, sums.data_ptr(), ns) == -1  # too small
+    c.shard_export(bank.data_ptr(), m, sums.data_ptr(), ns)
+    b = np.frombuffer(bank.cpu().numpy().tobytes(), dtype=SITE_DTYPE)
+    assert np.all(b["parent"] < 500)
+    assert np.all(np.diff(b["parent"] * 64 + b["child"]) > 0)   # (parent, child) order
+    s = sums.cpu().numpy()
+    assert s[0] > 0 and s[1] > 0
+    assert _code(c.shard_import, 0, sums.data_ptr(), bank.data_ptr(), 0) == -2   # empty bank
     t = W.time_pulse_mg(W.mg_material(np.random.default_rng(1), 2, fissile=False), [1.0, 0.0],
                         [1e-6, 1e-5], t_cut=1e-5, t_edges=[0.0, 1e-5], n=100)
     ct = mcgb.load_problem(mcgb.Context(mode=1), t)
-    assert _code(ct.shard_begin, 100, 0, 100, 1) == -1   # time-dependent: fixed source only
+    assert _code(ct.shard_begin, 100, 0, 100, 1, 1, 1) == -1   # time-dependent: fixed source only
 
 
 # Iteration limits: reaching one is an error status the host reads (no trap, no

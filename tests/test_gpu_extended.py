@@ -291,3 +291,34 @@ def test_event_mode_flight_timing(mcgb):
     c = mcgb.load_problem(mcgb.Context(mode=1), pb)
     c.run()
     assert c.get_event_timing()["launches"] == 0
+
+
+def test_bench_batch_at_full_size(mcgb):
+    """The benchmark's 64-problem batch (1e3-1e6 histories each, 8.7e6 in all)
+    in its autotuned persistent launch equals 64 standalone runs problem by
+    problem, and sampled generation-0 histories of the 16 largest problems
+    equal the oracle's, one by one."""
+    probs = W.batch_boxes()
+    b = mcgb.Batch()
+    ctxs = []
+    for p in probs:
+        c = mcgb.load_problem(mcgb.Context(mode=1, record_histories=True), p)
+        ctxs.append(c)
+        b.add_problem(c, p["run"]["n"], p["run"]["batches"], p["run"]["seed"])
+    t = b.autotune(budget_ms=3000)
+    b.run(t)
+    big = set(np.argsort([p["run"]["n"] for p in probs])[-16:].tolist())
+    rng = np.random.default_rng(17)
+    for i, (c, p) in enumerate(zip(ctxs, probs)):
+        c.run()
+        bm, bs = b.tally(i)
+        cm, cs = c.get_tally()
+        assert rel_close(bm, cm, 1e-9, 1e-300), i
+        assert rel_close(bs, cs, 1e-6, 1e-14), i
+        if i in big:
+            n = p["run"]["n"]
+            idx = np.sort(rng.choice(n, 150, replace=False))
+            h = c.get_histories()
+            ho = Oracle(p, strict=True).histories_by_index(idx)
+            assert_same_histories({k: np.asarray(v)[idx] for k, v in h.items()}, ho)
+    assert b.counters()["histories"] >= sum(p["run"]["n"] for p in probs)

@@ -37,20 +37,41 @@ def test_one_rank_equals_single_run(mcgb, mode):
     from paper_2501_05440_gb300.sharded import run_sharded_eigen
     pb = _problem()
     r = pb["run"]
+    ncyc = r["inactive"] + r["active"]
     ref = _single(mcgb, pb)
     c = mcgb.load_problem(mcgb.Context(mode=mode), pb)
     res = run_sharded_eigen(c, r["n"], r["inactive"], r["active"], r["seed"])
-    k_tl, k_c, m = ref.get_cycle_k(r["inactive"] + r["active"])
-    assert res["bank_m"].tolist() == m.tolist()
-    assert np.allclose(res["k_tl"], k_tl, rtol=1e-12) and np.allclose(res["k_col"], k_c, rtol=1e-12)
+    k_tl, k_c, m = ref.get_cycle_k(ncyc)
+    s_tl, s_c, s_m = c.get_cycle_k(ncyc)
+    assert s_m.tolist() == m.tolist()
+    assert np.allclose(s_tl, k_tl, rtol=1e-12) and np.allclose(s_c, k_c, rtol=1e-12)
     b = ref.get_bank()
     g = res["bank"]
     assert np.array_equal(g["parent"], b["parent"]) and np.array_equal(g["child"], b["child"])
     xyz = np.stack([g["x"], g["y"], g["z"]], axis=1).ravel()
     assert np.array_equal(xyz, np.asarray(b["xyz"]).ravel())
-    mean, _ = ref.get_tally(0)
-    assert np.allclose(res["tally_mean"], mean.ravel(), rtol=1e-9, atol=1e-300)
-    assert abs(res["k"] - ref.get_k()["k"]) <= 1e-12 * abs(ref.get_k()["k"])
+    for t in range(len(pb["tallies"])):
+        mean, sd = ref.get_tally(t)
+        smean, ssd = c.get_tally(t)
+        assert np.allclose(smean, mean, rtol=1e-9, atol=1e-300)
+        assert np.allclose(ssd, sd, rtol=1e-6, atol=1e-14)
+    for key in ("k", "k_col", "k_analog"):
+        assert abs(c.get_k()[key] - ref.get_k()[key]) <= 1e-12 * abs(ref.get_k()[key])
+
+
+def test_shard_calls_out_of_order(mcgb):
+    pb = _problem()
+    c = mcgb.load_problem(mcgb.Context(mode=1), pb)
+    with pytest.raises(mcgb.McgbError) as e:
+        c.shard_cycle(0)
+    assert e.value.code == -2                      # no shard begun
+    c.shard_begin(6000, 0, 6000, 1, 1, 3)
+    with pytest.raises(mcgb.McgbError) as e:
+        c.shard_cycle(1)
+    assert e.value.code == -2                      # cycles in order
+    with pytest.raises(mcgb.McgbError) as e:
+        c.shard_finish()
+    assert e.value.code == -2                      # cycles remain
 
 
 RANK = r"""
@@ -66,9 +87,10 @@ pb = W.c5g7_like_lattice(n=6000, inactive=2, active=3)
 r = pb["run"]
 c = m.load_problem(m.Context(mode=1), pb)
 res = run_sharded_eigen(c, r["n"], r["inactive"], r["active"], r["seed"], group=dist)
-if dist.get_rank() == 0:
-    np.savez(os.environ["OUT"], bank_m=res["bank_m"], k_tl=res["k_tl"], bank=res["bank"].tobytes(),
-             tally=res["tally_mean"])
+mean, sd = c.get_tally(0)
+np.savez(os.environ["OUT"] + f".{dist.get_rank()}.npz", bank_m=c.get_cycle_k(5)[2],
+         k_tl=c.get_cycle_k(5)[0], bank=np.frombuffer(res["bank"].tobytes(), dtype=np.uint8),
+         tally=mean.ravel(), k=c.get_k()["k"])
 dist.destroy_process_group()
 """
 
@@ -80,13 +102,15 @@ def _free_port():
 
 
 def test_two_ranks_equal_single_run(mcgb, tmp_path):
+    """two processes on this device (their kernels never wait on each other),
+    exchanging over gloo"""
     from paper_2501_05440_gb300 import SITE_DTYPE
     pb = _problem()
     r = pb["run"]
     ref = _single(mcgb, pb)
     script = tmp_path / "rank.py"
     script.write_text(RANK)
-    out = str(tmp_path / "res.npz")
+    out = str(tmp_path / "res")
     port = _free_port()
     procs = []
     for k in range(2):
@@ -97,13 +121,15 @@ def test_two_ranks_equal_single_run(mcgb, tmp_path):
     for p in procs:
         _, err = p.communicate(timeout=600)
         assert p.returncode == 0, err[-3000:]
-    res = np.load(out)
     _, _, m = ref.get_cycle_k(r["inactive"] + r["active"])
-    assert res["bank_m"].tolist() == m.tolist()
-    g = np.frombuffer(res["bank"].tobytes(), dtype=SITE_DTYPE)
     b = ref.get_bank()
-    assert np.array_equal(g["parent"], b["parent"]) and np.array_equal(g["child"], b["child"])
-    xyz = np.stack([g["x"], g["y"], g["z"]], axis=1).ravel()
-    assert np.array_equal(xyz, np.asarray(b["xyz"]).ravel())
     mean, _ = ref.get_tally(0)
-    assert np.allclose(res["tally"], mean.ravel(), rtol=1e-9, atol=1e-300)
+    for k in range(2):   # every rank holds the whole run's results
+        res = np.load(f"{out}.{k}.npz")
+        assert res["bank_m"].tolist() == m.tolist()
+        g = np.frombuffer(res["bank"].tobytes(), dtype=SITE_DTYPE)
+        assert np.array_equal(g["parent"], b["parent"]) and np.array_equal(g["child"], b["child"])
+        xyz = np.stack([g["x"], g["y"], g["z"]], axis=1).ravel()
+        assert np.array_equal(xyz, np.asarray(b["xyz"]).ravel())
+        assert np.allclose(res["tally"], mean.ravel(), rtol=1e-9, atol=1e-300)
+        assert abs(float(res["k"]) - ref.get_k()["k"]) <= 1e-12 * abs(ref.get_k()["k"])
