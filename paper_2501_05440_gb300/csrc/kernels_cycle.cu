@@ -189,7 +189,24 @@ __global__ void k_reduce_gen(Particles P, int64_t total, const int *total_dev, d
 #pragma unroll
         for (int q = 0; q < 6; q++) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
     }
+    // the block's warps combine in shared memory: one set of atomics per block
+    __shared__ double wk[2][8];
+    __shared__ unsigned long long wc[6][8];
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+        wk[0][warp] = kt;
+        wk[1][warp] = kc;
+#pragma unroll
+        for (int q = 0; q < 6; q++) wc[q][warp] = c[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; w++) {
+            kt += wk[0][w];
+            kc += wk[1][w];
+#pragma unroll
+            for (int q = 0; q < 6; q++) c[q] += wc[q][w];
+        }
         atomicAdd(kout, kt);
         atomicAdd(kout + 1, kc);
 #pragma unroll
@@ -201,7 +218,31 @@ __global__ void k_reduce_gen(Particles P, int64_t total, const int *total_dev, d
 void launch_reduce_gen(const Particles &P, int64_t total, const int *total_dev, double *kout,
                        unsigned long long *cnt, cudaStream_t st, const int *cyc_dev)
 {
-    k_reduce_gen<<<304, 256, 0, st>>>(P, total, total_dev, kout, cnt, cyc_dev);
+    k_reduce_gen<<<608, 256, 0, st>>>(P, total, total_dev, kout, cnt, cyc_dev);
+}
+
+// Sum of the replicas of accumulator i, in replica order, clearing them when
+// `clear`.  The loads of a batch of replicas are issued together (they do not
+// wait for the previous batch's stores), so the sum is bound by memory
+// throughput rather than one memory latency per replica.
+constexpr int REP_BATCH = 16;
+
+__device__ __forceinline__ double sum_replicas(double *tacc, int acc_size, int nrep, int i, bool clear)
+{
+    double v = 0.0;
+    for (int r0 = 0; r0 < nrep; r0 += REP_BATCH) {
+        double a[REP_BATCH];
+#pragma unroll
+        for (int q = 0; q < REP_BATCH; q++)
+            a[q] = r0 + q < nrep ? __ldcg(tacc + (int64_t)(r0 + q) * acc_size + i) : 0.0;
+#pragma unroll
+        for (int q = 0; q < REP_BATCH; q++)
+            if (r0 + q < nrep) {
+                v += a[q];
+                if (clear) tacc[(int64_t)(r0 + q) * acc_size + i] = 0.0;
+            }
+    }
+    return v;
 }
 
 // Eigenvalue cycle end: batch value v = (sum of replicas) / N; keep sum and
@@ -212,11 +253,7 @@ __global__ void k_tally_cycle(double *tacc, int acc_size, int nrep, double n, in
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= acc_size) return;
     if (cyc_dev) active = *cyc_dev >= inactive;
-    double v = 0.0;
-    for (int r = 0; r < nrep; r++) {
-        v += tacc[(int64_t)r * acc_size + i];
-        tacc[(int64_t)r * acc_size + i] = 0.0;
-    }
+    double v = sum_replicas(tacc, acc_size, nrep, i, true);
     v = v / n;
     if (active) {
         tsum[i] += v;
@@ -229,8 +266,8 @@ void launch_tally_cycle(double *tacc, int acc_size, int nrep, double n, int acti
                         int inactive)
 {
     if (acc_size <= 0) return;
-    k_tally_cycle<<<(acc_size + 255) / 256, 256, 0, st>>>(tacc, acc_size, nrep, n, active, tsum,
-                                                          tsum2, cyc_dev, inactive);
+    k_tally_cycle<<<(acc_size + 63) / 64, 64, 0, st>>>(tacc, acc_size, nrep, n, active, tsum,
+                                                       tsum2, cyc_dev, inactive);
 }
 
 __global__ void k_resample_dev(const int *perm, const int *Mp, int64_t N, const double *xi_tab,
@@ -273,14 +310,12 @@ __global__ void k_acc_reduce(const double *tacc, int acc_size, int nrep, double 
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= acc_size) return;
-    double v = 0.0;
-    for (int r = 0; r < nrep; r++) v += tacc[(int64_t)r * acc_size + i];
-    out[i] = v;
+    out[i] = sum_replicas(const_cast<double *>(tacc), acc_size, nrep, i, false);
 }
 
 void launch_acc_reduce(const double *tacc, int acc_size, int nrep, double *out, cudaStream_t st)
 {
-    k_acc_reduce<<<(acc_size + 255) / 256, 256, 0, st>>>(tacc, acc_size, nrep, out);
+    k_acc_reduce<<<(acc_size + 63) / 64, 64, 0, st>>>(tacc, acc_size, nrep, out);
 }
 
 // First slot of each problem in the next generation: off[base[p]] (M past the end).

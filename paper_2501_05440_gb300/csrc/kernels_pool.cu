@@ -90,19 +90,28 @@ __device__ __forceinline__ void retire(const Pool &q, const Particles &G, int i,
 }
 
 // Bucketed compaction of the pool: slots with key >= 0 go to q.list, grouped
-// by key in increasing order; counts per key in cnt[NBUCKET].  All threads call.
-// The lanes of a warp with equal keys find each other (match), and one of them
-// reserves their places in the bucket with a single shared-memory atomic; each
-// lane keeps its rank for the placing pass after the scan of the bucket counts.
-template <int P, int T, class KeyFn>
-__device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, KeyFn key)
+// by key in increasing order; counts per key in cnt[NBUCKET], the total in
+// cnt[NBUCKET] and returned.  All threads call.  The lanes of a warp with equal
+// keys find each other (match), and one of them reserves their places in the
+// bucket with a single shared-memory atomic; after one barrier every warp
+// scans the bucket counts itself and places its own slots, so a second barrier
+// ends the call.  Two count arrays are used in turn (hb selects), each zeroed
+// during the other's call.  REFILL: thread 0 also takes the block's share of
+// the device work counter (s_base, s_take; s_exhausted when it runs out).
+template <int P, int T, bool REFILL = false, class KeyFn>
+__device__ __forceinline__ int build_list(const Pool &q, int *hist2, int &hb, int *cnt, KeyFn key,
+                                          int *work = nullptr, int64_t total_work = 0,
+                                          int *s_base = nullptr, int *s_take = nullptr,
+                                          int *s_exhausted = nullptr)
 {
     static_assert(P % T == 0, "every lane of a warp takes the same number of slots");
+    static_assert(NBUCKET == 33, "32 buckets scanned by the lanes of a warp, one more after them");
     constexpr int R = P / T;
     const int lane = threadIdx.x & 31;
     const unsigned lower = (1u << lane) - 1u;
-    if (threadIdx.x < NBUCKET) hist[threadIdx.x] = 0;
-    __syncthreads();
+    int *hist = hist2 + hb * (NBUCKET + 1);
+    int *other = hist2 + (hb ^ 1) * (NBUCKET + 1);
+    hb ^= 1;
     int kr[R], rank[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -116,30 +125,46 @@ __device__ __forceinline__ int build_list(const Pool &q, int *hist, int *cnt, Ke
         rank[r] = base + __popc(m & lower);
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        // exclusive scan of the NBUCKET counts by one warp (bucket 32 after the loop)
-        int v = hist[lane];
-        int x = v;
+    // exclusive scan of the 33 bucket counts, in every warp
+    int v = hist[lane];
+    int x = v;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        int last = hist[32];
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int last = hist[32];
+    const int base32 = __shfl_sync(0xffffffffu, x, 31);
+    const int total = base32 + last;
+    const int excl = x - v;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        int off = __shfl_sync(0xffffffffu, excl, kr[r] & 31);
+        if (kr[r] == 32) off = base32;
+        if (kr[r] >= 0) q.list[off + rank[r]] = threadIdx.x + r * T;
+    }
+    if (threadIdx.x < 32) {
         cnt[lane] = v;
-        hist[lane] = x - v;
-        if (lane == 31) {
+        other[lane] = 0;
+        if (lane == 0) {
             cnt[32] = last;
-            hist[32] = x;
-            cnt[NBUCKET] = x + last;     // total
+            cnt[NBUCKET] = total;
+            other[32] = 0;
+            if (REFILL) {
+                int take = 0, b = 0;
+                if (total > 0) {
+                    b = atomicAdd(work, total);
+                    int64_t left = total_work - (int64_t)b;
+                    take = left <= 0 ? 0 : (left < total ? (int)left : total);
+                    if (take < total) *s_exhausted = 1;
+                }
+                *s_base = b;
+                *s_take = take;
+            }
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < R; r++)
-        if (kr[r] >= 0) q.list[hist[kr[r]] + rank[r]] = threadIdx.x + r * T;
-    __syncthreads();
-    return cnt[NBUCKET];
+    return total;
 }
 
 // P particles per block of T threads; the register budget is planned for
@@ -157,9 +182,11 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
                                                                PersistentArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int hist[NBUCKET + 1], cnt[NBUCKET + 1];
+    __shared__ int hist[2 * (NBUCKET + 1)], cnt[NBUCKET + 1];
     __shared__ int s_base, s_take, s_exhausted;
     const Pool q = carve(smem, P);
+    int hb = 0;
+    for (int k = threadIdx.x; k < 2 * (NBUCKET + 1); k += T) hist[k] = 0;
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
     const int gen = a.gen_dev ? *a.gen_dev : a.gen;
     const int rep = (int)(blockIdx.x % (unsigned)W.nrep);
@@ -174,19 +201,9 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
         }
         // ---- refill empty slots from the work counter
         if (!s_exhausted) {
-            int n_empty = build_list<P, T>(q, hist, cnt, [&](int i) { return q.fate[i] == SLOT_EMPTY ? 0 : -1; });
-            if (threadIdx.x == 0) {
-                int take = 0, base = 0;
-                if (n_empty > 0) {
-                    base = atomicAdd(a.work, n_empty);
-                    int64_t left = total - (int64_t)base;
-                    take = left <= 0 ? 0 : (left < n_empty ? (int)left : n_empty);
-                    if (take < n_empty) s_exhausted = 1;
-                }
-                s_base = base;
-                s_take = take;
-            }
-            __syncthreads();
+            build_list<P, T, true>(q, hist, hb, cnt,
+                                   [&](int i) { return q.fate[i] == SLOT_EMPTY ? 0 : -1; }, a.work,
+                                   total, &s_base, &s_take, &s_exhausted);
             for (int k = threadIdx.x; k < s_take; k += T) {
                 int i = q.list[k];
                 int64_t j = (int64_t)s_base + k;
@@ -220,7 +237,7 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
             __syncthreads();
         }
         // ---- flights of every live particle, grouped by material
-        int n_adv = build_list<P, T>(q, hist, cnt, [&](int i) {
+        int n_adv = build_list<P, T>(q, hist, hb, cnt, [&](int i) {
             return q.fate[i] == FATE_ALIVE ? 1 + (q.mat[i] & 31) : -1;
         });
         if (n_adv == 0 && s_exhausted) break;
@@ -274,7 +291,7 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Part
         __syncthreads();
         // ---- crossings (lattice steps in bucket 0, surface crossings in 1), then
         // collisions grouped by material
-        int n_ev = build_list<P, T>(q, hist, cnt, [&](int i) {
+        int n_ev = build_list<P, T>(q, hist, hb, cnt, [&](int i) {
             if (q.fate[i] != FATE_ALIVE) return -1;
             const int e = q.ev[i];
             if ((e & 15) != EV_CROSS) return 2 + (q.mat[i] % 31);
