@@ -290,7 +290,7 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
         int pool = c->opts.pool == 0 ? 256 : c->opts.pool;
         if (pool > 0) {
             int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
-                                                 : std::max(1, pool_max_blocks_per_sm(pool));
+                                                 : std::max(1, pool_max_blocks_per_sm(pool, W.ce_any != 0));
             int ppb = pool_particles_per_block(pool);
             int64_t want = (total + ppb - 1) / ppb;
             int grid = (int)std::min<int64_t>((int64_t)c->sms * bps, std::max<int64_t>(want, 1));
@@ -1940,7 +1940,8 @@ std::string tune_signature(mcgb_batch *b)
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, b->device);
     std::ostringstream s;
-    s << prop.name << "|sm" << prop.multiProcessorCount << "|p" << b->runs.size();
+    // kernel generation: a tuning taken on other kernel builds does not apply
+    s << "kv2|" << prop.name << "|sm" << prop.multiProcessorCount << "|p" << b->runs.size();
     int64_t n = 0, cells = 0, surfs = 0, groups = 0;
     for (auto &r : b->runs) {
         n += r.n;
@@ -2081,8 +2082,10 @@ int mcgb_batch_autotune(mcgb_batch *b, int budget_ms, mcgb_tune *out)
     // candidates: block-sorted pools (particles per block x resident blocks per SM)
     // and the register-resident variant (threads per block x blocks per SM)
     std::vector<mcgb_tune> cand;
+    bool ce = false;
+    for (auto &r : b->runs) ce = ce || r.def->ce == 1;
     for (int pool : {512, 2256, 256, 2512, 64, 128}) {
-        int occ = std::max(1, pool_max_blocks_per_sm(pool));
+        int occ = std::max(1, pool_max_blocks_per_sm(pool, ce));
         for (int bps = occ; bps >= 1; bps = bps > 2 ? bps / 2 : bps - 1) cand.push_back({0, bps, pool, 0.0});
     }
     for (int blk : {128, 256}) {

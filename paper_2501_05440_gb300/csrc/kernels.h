@@ -49,7 +49,9 @@ int persistent_max_blocks_per_sm(int block);
 // block sorted block-wide, or 32, 64 or 128 particles per warp sorted per warp
 bool launch_pool(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                  const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st);
-int pool_max_blocks_per_sm(int pool);
+// resident blocks per SM of a pool variant (ce: the instantiation with
+// continuous-energy physics, which runs with fewer blocks)
+int pool_max_blocks_per_sm(int pool, bool ce);
 int pool_threads();
 int pool_particles_per_block(int pool);
 

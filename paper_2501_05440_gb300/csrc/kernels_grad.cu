@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) k_replay(World W, ReplayArgs a, Bank Bsrc
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n;
          j += (int64_t)gridDim.x * blockDim.x) {
         PS p;
-        if (!init_particle(W, Pd, Bsrc, p, 0, j, a.gen, a.site ? a.site[j] : -1, false)) continue;
+        if (!init_particle<false>(W, Pd, Bsrc, p, 0, j, a.gen, a.site ? a.site[j] : -1, false)) continue;
         double own_total = 0.0;
         for (int g = 0; g < G; g++) own_total += a.w[g] * a.own[j * G + g];
         double c_total = 0.0;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_replay(World W, ReplayArgs a, Bank Bsrc
             double d = 0.0;
             int g0 = p.g, m0 = p.mat;
             bool in_det = (p.ucell >= 0 ? p.ucell : p.cell) == a.det_cell;
-            int ev = step_advance<true, false>(W, Pd, p, (int)j, R, 0, kind, which, uk, kt, &d);
+            int ev = step_advance<true, false, false>(W, Pd, p, (int)j, R, 0, kind, which, uk, kt, &d);
             if (ev == EV_DEAD) break;
             double ownb = own_before;
             if (in_det) own_before = own_before + a.w[g0] * d;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_replay(World W, ReplayArgs a, Bank Bsrc
             double mfp = __ldg(W.g_mfp + go);
             atomicAdd(sg + it, (mfp - d) * D);
             int nfb = p.nfis, nf = 0;
-            ev = step_collide<true>(W, Pd, p, (int)j, none, R, 0, kc, &nf);
+            ev = step_collide<true, true, false>(W, Pd, p, (int)j, none, R, 0, kc, &nf);
             double nusf = __ldg(W.g_nusf + go), mufr = __ldg(W.g_mufr + go);
             if (nusf != 0.0 && mufr != 0.0) {
                 double fac = nf > (int)__ldg(W.g_mufl + go) ? 1.0 / mufr : -1.0 / (1.0 - mufr);

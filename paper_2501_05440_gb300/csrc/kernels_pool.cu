@@ -1,548 +1,43 @@
-// kernels_pool.cu -- persistent event loop with block-sorted events.
-//
-// Each block keeps a pool of P particles in shared memory (structure of
-// arrays) and repeats: refill empty slots from the device work counter; run
-// the flight (advance) of every live particle; run the surface crossings, then
-// the collisions.  Before each phase the block builds a compacted list of the
-// slots that need it, collisions ordered by material, so that consecutive
-// threads -- whole warps -- run the same event on the same kind of data.  The
-// grid stays resident for the whole cycle; no particle state goes through HBM
-// between events.  When no history is left to start and a block holds at most
-// a warp's worth of particles, each runs to its end in registers.  Results do
-// not depend on which thread runs which slot: every history draws from its own
-// random stream.
+// kernels_pool.cu -- dispatch to the persistent pool kernels (pool.cuh): the
+// instantiation without continuous-energy physics when the world has none, and
+// the one without the particle clock when nothing is time dependent.
 #include "kernels.h"
-#include "steps.cuh"
 
 namespace mcgb {
 
-namespace {
+bool launch_pool_mg(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                    const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st);
+bool launch_pool_mg_time(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                         const RunBufs &R, const PersistentArgs &a, int pool, int grid,
+                         cudaStream_t st);
+bool launch_pool_ce(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                    const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st);
+bool launch_pool_ce_time(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
+                         const RunBufs &R, const PersistentArgs &a, int pool, int grid,
+                         cudaStream_t st);
+int pool_occupancy_mg(int pool);
+int pool_occupancy_ce(int pool);
 
-constexpr int POOL_T = 256;          // threads per block
-constexpr int NBUCKET = 33;          // list buckets (flights: 1 + material % 32; events: 0 lattice
-                                     // steps, 1 surface crossings, 2 + material % 31 collisions)
-constexpr int SLOT_EMPTY = -2;
-
-struct Pool {
-    double *x, *y, *z, *u, *v, *w, *E, *kt, *kc, *iu, *iv, *iw, *t;
-    unsigned long long *s;
-    int *g, *cell, *ix, *iy, *ucell, *mat, *prob, *root, *nfis, *ncoll, *ncross, *gslot, *bwhich,
-        *uk, *fate, *ev;
-    int *list;
-};
-
-__host__ __device__ constexpr size_t pool_bytes(int P) { return (size_t)P * (14 * 8 + 17 * 4); }
-
-__device__ __forceinline__ Pool carve(unsigned char *base, int P)
-{
-    Pool q;
-    double *d = reinterpret_cast<double *>(base);
-    q.x = d; q.y = d + P; q.z = d + 2 * P; q.u = d + 3 * P; q.v = d + 4 * P; q.w = d + 5 * P;
-    q.E = d + 6 * P; q.kt = d + 7 * P; q.kc = d + 8 * P;
-    q.iu = d + 9 * P; q.iv = d + 10 * P; q.iw = d + 11 * P;
-    q.s = reinterpret_cast<unsigned long long *>(d + 12 * P);
-    q.t = d + 13 * P;
-    int *i = reinterpret_cast<int *>(d + 14 * P);
-    q.g = i; q.cell = i + P; q.ix = i + 2 * P; q.iy = i + 3 * P; q.ucell = i + 4 * P;
-    q.mat = i + 5 * P; q.prob = i + 6 * P; q.root = i + 7 * P; q.nfis = i + 8 * P;
-    q.ncoll = i + 9 * P; q.ncross = i + 10 * P; q.gslot = i + 11 * P; q.bwhich = i + 12 * P;
-    q.uk = i + 13 * P; q.fate = i + 14 * P; q.ev = i + 15 * P; q.list = i + 16 * P;
-    return q;
-}
-
-// TIME = false: the particle clock is neither loaded nor kept
-template <bool TIME>
-__device__ __forceinline__ void pool_load(const Pool &q, int i, PS &p)
-{
-    p.x = q.x[i]; p.y = q.y[i]; p.z = q.z[i]; p.u = q.u[i]; p.v = q.v[i]; p.w = q.w[i];
-    p.iu = q.iu[i]; p.iv = q.iv[i]; p.iw = q.iw[i];
-    p.E = q.E[i]; p.s = q.s[i]; p.t = TIME ? q.t[i] : 0.0;
-    p.g = q.g[i]; p.cell = q.cell[i]; p.ix = q.ix[i]; p.iy = q.iy[i]; p.ucell = q.ucell[i];
-    p.mat = q.mat[i]; p.prob = q.prob[i]; p.root = q.root[i]; p.nfis = q.nfis[i];
-    p.ncoll = q.ncoll[i]; p.ncross = q.ncross[i]; p.fate = q.fate[i];
-}
-
-template <bool TIME>
-__device__ __forceinline__ void pool_store(const Pool &q, int i, const PS &p)
-{
-    q.x[i] = p.x; q.y[i] = p.y; q.z[i] = p.z; q.u[i] = p.u; q.v[i] = p.v; q.w[i] = p.w;
-    q.iu[i] = p.iu; q.iv[i] = p.iv; q.iw[i] = p.iw;
-    q.E[i] = p.E; q.s[i] = p.s;
-    if (TIME) q.t[i] = p.t;
-    q.g[i] = p.g; q.cell[i] = p.cell; q.ix[i] = p.ix; q.iy[i] = p.iy; q.ucell[i] = p.ucell;
-    q.mat[i] = p.mat; q.prob[i] = p.prob; q.root[i] = p.root; q.nfis[i] = p.nfis;
-    q.ncoll[i] = p.ncoll; q.ncross[i] = p.ncross; q.fate[i] = p.fate;
-}
-
-// history over: its record goes to the global slot, the pool slot becomes empty
-__device__ __forceinline__ void retire(const Pool &q, const Particles &G, int i, const PS &p)
-{
-    int j = q.gslot[i];
-    G.nfis[j] = p.nfis;
-    G.ncoll[j] = p.ncoll;
-    G.ncross[j] = p.ncross;
-    G.fate[j] = (signed char)p.fate;
-    G.s[j] = p.s;
-    G.g[j] = p.g;
-    G.kt[j] = q.kt[i];
-    G.kc[j] = q.kc[i];
-    q.fate[i] = SLOT_EMPTY;
-}
-
-// Bucketed compaction of the pool: slots with key >= 0 go to q.list, grouped
-// by key in increasing order; counts per key in cnt[NBUCKET], the total in
-// cnt[NBUCKET] and returned.  All threads call.  The lanes of a warp with equal
-// keys find each other (match), and one of them reserves their places in the
-// bucket with a single shared-memory atomic; after one barrier every warp
-// scans the bucket counts itself and places its own slots, so a second barrier
-// ends the call.  Two count arrays are used in turn (hb selects), each zeroed
-// during the other's call.  REFILL: thread 0 also takes the block's share of
-// the device work counter (s_base, s_take; s_exhausted when it runs out).
-template <int P, int T, bool REFILL = false, class KeyFn>
-__device__ __forceinline__ int build_list(const Pool &q, int *hist2, int &hb, int *cnt, KeyFn key,
-                                          int *work = nullptr, int64_t total_work = 0,
-                                          int *s_base = nullptr, int *s_take = nullptr,
-                                          int *s_exhausted = nullptr)
-{
-    static_assert(P % T == 0, "every lane of a warp takes the same number of slots");
-    static_assert(NBUCKET == 33, "32 buckets scanned by the lanes of a warp, one more after them");
-    constexpr int R = P / T;
-    const int lane = threadIdx.x & 31;
-    const unsigned lower = (1u << lane) - 1u;
-    int *hist = hist2 + hb * (NBUCKET + 1);
-    int *other = hist2 + (hb ^ 1) * (NBUCKET + 1);
-    hb ^= 1;
-    int kr[R], rank[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        int k = key(threadIdx.x + r * T);
-        unsigned m = __match_any_sync(0xffffffffu, k);
-        int first = __ffs(m) - 1;
-        int base = 0;
-        if (k >= 0 && lane == first) base = atomicAdd(hist + k, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, first);
-        kr[r] = k;
-        rank[r] = base + __popc(m & lower);
-    }
-    __syncthreads();
-    // exclusive scan of the 33 bucket counts, in every warp
-    int v = hist[lane];
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    const int last = hist[32];
-    const int base32 = __shfl_sync(0xffffffffu, x, 31);
-    const int total = base32 + last;
-    const int excl = x - v;
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        int off = __shfl_sync(0xffffffffu, excl, kr[r] & 31);
-        if (kr[r] == 32) off = base32;
-        if (kr[r] >= 0) q.list[off + rank[r]] = threadIdx.x + r * T;
-    }
-    if (threadIdx.x < 32) {
-        cnt[lane] = v;
-        other[lane] = 0;
-        if (lane == 0) {
-            cnt[32] = last;
-            cnt[NBUCKET] = total;
-            other[32] = 0;
-            if (REFILL) {
-                int take = 0, b = 0;
-                if (total > 0) {
-                    b = atomicAdd(work, total);
-                    int64_t left = total_work - (int64_t)b;
-                    take = left <= 0 ? 0 : (left < total ? (int)left : total);
-                    if (take < total) *s_exhausted = 1;
-                }
-                *s_base = b;
-                *s_take = take;
-            }
-        }
-    }
-    __syncthreads();
-    return total;
-}
-
-// P particles per block of T threads; the register budget is planned for
-// pool_min_blocks(P, T) resident blocks (128 registers per thread at 2 blocks
-// of 256 threads; a pool of one particle per thread trades a few spilled
-// registers for a third resident block, which the shared memory allows).
-__host__ __device__ constexpr int pool_min_blocks(int P, int T)
-{
-    return (P <= T && T == 256) ? 3 : 65536 / (T * 128);
-}
-
-template <int P, int T, bool TIME>
-__global__ void __launch_bounds__(T, pool_min_blocks(P, T)) k_pool(World W, Particles G, Bank Bsrc,
-                                                               Bank Bdst, RunBufs R,
-                                                               PersistentArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int hist[2 * (NBUCKET + 1)], cnt[NBUCKET + 1];
-    __shared__ int s_base, s_take, s_exhausted;
-    const Pool q = carve(smem, P);
-    int hb = 0;
-    for (int k = threadIdx.x; k < 2 * (NBUCKET + 1); k += T) hist[k] = 0;
-    const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
-    const int gen = a.gen_dev ? *a.gen_dev : a.gen;
-    const int rep = (int)(blockIdx.x % (unsigned)W.nrep);
-    for (int i = threadIdx.x; i < P; i += T) q.fate[i] = SLOT_EMPTY;
-    if (threadIdx.x == 0) s_exhausted = 0;
-    __syncthreads();
-    long long passes = 0;
-    for (;;) {
-        if (a.max_passes > 0 && ++passes > a.max_passes) {   // block-uniform
-            if (threadIdx.x == 0) atomicOr(R.err, ERR_ITER);
-            break;
-        }
-        // ---- refill empty slots from the work counter
-        if (!s_exhausted) {
-            build_list<P, T, true>(q, hist, hb, cnt,
-                                   [&](int i) { return q.fate[i] == SLOT_EMPTY ? 0 : -1; }, a.work,
-                                   total, &s_base, &s_take, &s_exhausted);
-            for (int k = threadIdx.x; k < s_take; k += T) {
-                int i = q.list[k];
-                int64_t j = (int64_t)s_base + k;
-                int prob = 0;
-                {
-                    int lo = 0, hi = W.nprob;
-                    while (hi - lo > 1) {
-                        int mid = (lo + hi) >> 1;
-                        if (a.gen_base[mid] <= j) lo = mid;
-                        else hi = mid;
-                    }
-                    prob = lo;
-                }
-                PS p;
-                bool ok = init_particle(W, W.prob[prob], Bsrc, p, prob, j - a.gen_base[prob], gen,
-                                        a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
-                q.gslot[i] = (int)j;
-                q.kt[i] = 0.0;
-                q.kc[i] = 0.0;
-                if (!ok) {
-                    atomicOr(R.err, ERR_SOURCE);
-                    p.fate = FATE_LOST;
-                    p.cell = 0;
-                    p.mat = 0;
-                    pool_store<TIME>(q, i, p);
-                    retire(q, G, i, p);
-                } else {
-                    pool_store<TIME>(q, i, p);
-                }
-            }
-            __syncthreads();
-        }
-        // ---- flights of every live particle, grouped by material
-        int n_adv = build_list<P, T>(q, hist, hb, cnt, [&](int i) {
-            return q.fate[i] == FATE_ALIVE ? 1 + (q.mat[i] & 31) : -1;
-        });
-        if (n_adv == 0 && s_exhausted) break;
-        if (s_exhausted && n_adv <= 32) {
-            // the block's last few histories (no more to start, one warp's worth):
-            // each runs to its end in a thread of warp 0, with no block barrier,
-            // list building or shared-memory round trip between its events
-            if ((int)threadIdx.x < n_adv) {
-                int i = q.list[threadIdx.x];
-                PS p;
-                pool_load<TIME>(q, i, p);
-                const ProblemDev &Pd = W.prob[p.prob];
-                const int slot = q.gslot[i];
-                double kt = q.kt[i], kc = q.kc[i];
-                for (;;) {
-                    int kind, which, uk = 0;
-                    int ev = step_advance<false, TIME>(W, Pd, p, slot, R, rep, kind, which, uk, kt);
-                    if (ev == EV_CROSS) ev = step_cross(W, p, kind, which);
-                    else if (ev == EV_COLLIDE)
-                        ev = step_collide<false, TIME>(W, Pd, p, slot, Bdst, R, uk, kc);
-                    if (ev == EV_DEAD) break;
-                }
-                q.kt[i] = kt;
-                q.kc[i] = kc;
-                retire(q, G, i, p);
-            }
-            break;
-        }
-        for (int k = threadIdx.x; k < n_adv; k += T) {
-            int i = q.list[k];
-            PS p;
-            pool_load<TIME>(q, i, p);
-            int kind, which, uk = 0;
-            double kt = q.kt[i];
-            int ev = step_advance<false, TIME>(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which,
-                                                uk, kt);
-            q.x[i] = p.x;
-            q.y[i] = p.y;
-            q.z[i] = p.z;
-            if (TIME) q.t[i] = p.t;
-            q.s[i] = p.s;
-            q.kt[i] = kt;
-            q.ev[i] = ev | (kind << 4);
-            q.bwhich[i] = which;
-            q.uk[i] = uk;
-            if (ev == EV_DEAD) {
-                q.fate[i] = p.fate;
-                retire(q, G, i, p);
-            }
-        }
-        __syncthreads();
-        // ---- crossings (lattice steps in bucket 0, surface crossings in 1), then
-        // collisions grouped by material
-        int n_ev = build_list<P, T>(q, hist, hb, cnt, [&](int i) {
-            if (q.fate[i] != FATE_ALIVE) return -1;
-            const int e = q.ev[i];
-            if ((e & 15) != EV_CROSS) return 2 + (q.mat[i] % 31);
-            const int kind = e >> 4;   // lattice steps apart from surface crossings
-            return (kind == B_LATX || kind == B_LATY) ? 0 : 1;
-        });
-        int n_cross = cnt[0] + cnt[1];
-        for (int k = threadIdx.x; k < n_ev; k += T) {
-            int i = q.list[k];
-            PS p;
-            pool_load<TIME>(q, i, p);
-            int ev;
-            if (k < n_cross) {
-                ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
-            } else {
-                double kc = q.kc[i];
-                ev = step_collide<false, TIME>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
-                q.kc[i] = kc;
-            }
-            pool_store<TIME>(q, i, p);
-            if (ev == EV_DEAD) retire(q, G, i, p);
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Warp-level variant: each warp owns PW slots of the shared pool and sorts its
-// own events with ballots (no block barrier; warps progress independently).
-constexpr int WPOOL_T = 128;   // threads (4 warps) per block
-
-// compacts the slots of the warp's pool for which pred(i) holds into `list`
-template <int PW, class Pred>
-__device__ __forceinline__ int warp_list(int *list, Pred pred)
-{
-    const int lane = threadIdx.x & 31;
-    int n = 0;
-#pragma unroll
-    for (int r = 0; r < PW / 32; r++) {
-        int i = r * 32 + lane;
-        bool b = pred(i);
-        unsigned m = __ballot_sync(0xffffffffu, b);
-        if (b) list[n + __popc(m & ((1u << lane) - 1u))] = i;
-        n += __popc(m);
-    }
-    __syncwarp();
-    return n;
-}
-
-// resident blocks per SM the register budget is planned for (smem allows as many)
-template <int PW> struct WpoolMinBlocks { static constexpr int value = PW <= 32 ? 6 : (PW <= 64 ? 5 : 2); };
-
-template <int PW, bool TIME>
-__global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(World W, Particles G, Bank Bsrc, Bank Bdst,
-                                                      RunBufs R, PersistentArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Pool q = carve(smem + (size_t)warp * pool_bytes(PW), PW);
-    const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
-    const int gen = a.gen_dev ? *a.gen_dev : a.gen;
-    const int rep = (int)((blockIdx.x * (WPOOL_T / 32) + warp) % (unsigned)W.nrep);
-    for (int i = lane; i < PW; i += 32) q.fate[i] = SLOT_EMPTY;
-    __syncwarp();
-    bool exhausted = false;
-    long long passes = 0;
-    for (;;) {
-        if (a.max_passes > 0 && ++passes > a.max_passes) {   // warp-uniform
-            if (lane == 0) atomicOr(R.err, ERR_ITER);
-            break;
-        }
-        if (!exhausted) {
-            int n_empty = warp_list<PW>(q.list, [&](int i) { return q.fate[i] == SLOT_EMPTY; });
-            int base = 0;
-            if (lane == 0 && n_empty > 0) base = atomicAdd(a.work, n_empty);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            int take = 0;
-            if (n_empty > 0) {
-                int64_t left = total - (int64_t)base;
-                take = left <= 0 ? 0 : (left < n_empty ? (int)left : n_empty);
-                if (take < n_empty) exhausted = true;
-            }
-            for (int k = lane; k < take; k += 32) {
-                int i = q.list[k];
-                int64_t j = (int64_t)base + k;
-                int lo = 0, hi = W.nprob;
-                while (hi - lo > 1) {
-                    int mid = (lo + hi) >> 1;
-                    if (a.gen_base[mid] <= j) lo = mid;
-                    else hi = mid;
-                }
-                PS p;
-                bool ok = init_particle(W, W.prob[lo], Bsrc, p, lo, j - a.gen_base[lo], gen,
-                                        a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
-                q.gslot[i] = (int)j;
-                q.kt[i] = 0.0;
-                q.kc[i] = 0.0;
-                if (!ok) {
-                    atomicOr(R.err, ERR_SOURCE);
-                    p.fate = FATE_LOST;
-                    p.cell = 0;
-                    p.mat = 0;
-                    pool_store<TIME>(q, i, p);
-                    retire(q, G, i, p);
-                } else {
-                    pool_store<TIME>(q, i, p);
-                }
-            }
-            __syncwarp();
-        }
-        int n_adv = warp_list<PW>(q.list, [&](int i) { return q.fate[i] == FATE_ALIVE; });
-        if (n_adv == 0 && exhausted) break;
-        for (int k = lane; k < n_adv; k += 32) {
-            int i = q.list[k];
-            PS p;
-            pool_load<TIME>(q, i, p);
-            int kind, which, uk = 0;
-            double kt = q.kt[i];
-            int ev = step_advance<false, TIME>(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which,
-                                                uk, kt);
-            q.x[i] = p.x;
-            q.y[i] = p.y;
-            q.z[i] = p.z;
-            if (TIME) q.t[i] = p.t;
-            q.s[i] = p.s;
-            q.kt[i] = kt;
-            q.ev[i] = ev | (kind << 4);
-            q.bwhich[i] = which;
-            q.uk[i] = uk;
-            if (ev == EV_DEAD) {
-                q.fate[i] = p.fate;
-                retire(q, G, i, p);
-            }
-        }
-        __syncwarp();
-        int n_x = warp_list<PW>(q.list, [&](int i) {
-            return q.fate[i] == FATE_ALIVE && (q.ev[i] & 15) == EV_CROSS;
-        });
-        for (int k = lane; k < n_x; k += 32) {
-            int i = q.list[k];
-            PS p;
-            pool_load<TIME>(q, i, p);
-            int ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
-            pool_store<TIME>(q, i, p);
-            if (ev == EV_DEAD) retire(q, G, i, p);
-        }
-        __syncwarp();
-        int n_c = warp_list<PW>(q.list, [&](int i) {
-            return q.fate[i] == FATE_ALIVE && (q.ev[i] & 15) == EV_COLLIDE;
-        });
-        for (int k = lane; k < n_c; k += 32) {
-            int i = q.list[k];
-            PS p;
-            pool_load<TIME>(q, i, p);
-            double kc = q.kc[i];
-            int ev = step_collide<false, TIME>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
-            q.kc[i] = kc;
-            q.ev[i] = EV_ADVANCE;
-            pool_store<TIME>(q, i, p);
-            if (ev == EV_DEAD) retire(q, G, i, p);
-        }
-        __syncwarp();
-    }
-}
-
-template <int PW, bool TIME>
-void launch_wpool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
-                    const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
-{
-    size_t sm = pool_bytes(PW) * (WPOOL_T / 32);
-    cudaFuncSetAttribute(k_wpool<PW, TIME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_wpool<PW, TIME><<<grid, WPOOL_T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
-}
-
-template <int PW> int wpool_occupancy()
-{
-    int n = 0;
-    size_t sm = pool_bytes(PW) * (WPOOL_T / 32);
-    cudaFuncSetAttribute(k_wpool<PW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wpool<PW, false>, WPOOL_T, sm);
-    return n;
-}
-
-template <int P, int T, bool TIME>
-void launch_pool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
-                   const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
-{
-    size_t sm = pool_bytes(P);
-    cudaFuncSetAttribute(k_pool<P, T, TIME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_pool<P, T, TIME><<<grid, T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
-}
-
-template <int P, int T> int pool_occupancy()
-{
-    int n = 0;
-    size_t sm = pool_bytes(P);
-    cudaFuncSetAttribute(k_pool<P, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<P, T, false>, T, sm);
-    return n;
-}
-
-}  // namespace
-
-int pool_threads() { return POOL_T; }
+int pool_threads() { return 256; }
 
 int pool_particles_per_block(int pool)
 {
-    return pool < 256 ? pool * (WPOOL_T / 32) : (pool > 2000 ? pool - 2000 : pool);
+    return pool < 256 ? pool * 4 : (pool > 2000 ? pool - 2000 : pool);
 }
 
-// pool codes: 32, 64, 128 = particles per warp (warp-level lists, 128-thread
-// blocks); 256, 512, 1024 = particles per 256-thread block; 2256, 2512 = 256 or
-// 512 particles per 128-thread block
-int pool_max_blocks_per_sm(int P)
+int pool_max_blocks_per_sm(int pool, bool ce)
 {
-    switch (P) {
-    case 32: return wpool_occupancy<32>();
-    case 64: return wpool_occupancy<64>();
-    case 128: return wpool_occupancy<128>();
-    case 256: return pool_occupancy<256, 256>();
-    case 512: return pool_occupancy<512, 256>();
-    case 1024: return pool_occupancy<1024, 256>();
-    case 2256: return pool_occupancy<256, 128>();
-    case 2512: return pool_occupancy<512, 128>();
-    default: return 0;
-    }
+    return ce ? pool_occupancy_ce(pool) : pool_occupancy_mg(pool);
 }
 
-template <bool TIME>
-bool launch_pool_time(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
-                      const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st)
-{
-    switch (pool) {
-    case 32: launch_wpool_t<32, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 64: launch_wpool_t<64, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 128: launch_wpool_t<128, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 256: launch_pool_t<256, 256, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 512: launch_pool_t<512, 256, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 1024: launch_pool_t<1024, 256, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 2256: launch_pool_t<256, 128, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    case 2512: launch_pool_t<512, 128, TIME>(W, G, Bsrc, Bdst, R, a, grid, st); return true;
-    default: return false;
-    }
-}
-
-// the time-aware instantiation only when the world needs it
 bool launch_pool(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                  const RunBufs &R, const PersistentArgs &a, int pool, int grid, cudaStream_t st)
 {
-    return W.time_any ? launch_pool_time<true>(W, G, Bsrc, Bdst, R, a, pool, grid, st)
-                      : launch_pool_time<false>(W, G, Bsrc, Bdst, R, a, pool, grid, st);
+    if (W.ce_any)
+        return W.time_any ? launch_pool_ce_time(W, G, Bsrc, Bdst, R, a, pool, grid, st)
+                          : launch_pool_ce(W, G, Bsrc, Bdst, R, a, pool, grid, st);
+    return W.time_any ? launch_pool_mg_time(W, G, Bsrc, Bdst, R, a, pool, grid, st)
+                      : launch_pool_mg(W, G, Bsrc, Bdst, R, a, pool, grid, st);
 }
 
 }  // namespace mcgb

@@ -77,6 +77,9 @@ __device__ __forceinline__ int accum_replica(const World &W)
 }
 
 // ---------------------------------------------------------------------------
+// CE = false: instantiations for worlds without continuous-energy problems
+// (that physics compiled out; chosen by launch_* from W.ce_any).
+template <bool CE>
 __global__ void k_source(World W, Particles P, Bank Bsrc, RunBufs R, int gen, int64_t total,
                          const int64_t *gen_base, const int *src_idx, int eigen)
 {
@@ -85,8 +88,8 @@ __global__ void k_source(World W, Particles P, Bank Bsrc, RunBufs R, int gen, in
     int prob = find_problem(gen_base, W.nprob, j);
     const ProblemDev &Pd = W.prob[prob];
     PS p;
-    bool ok = init_particle(W, Pd, Bsrc, p, prob, j - gen_base[prob], gen,
-                            src_idx ? src_idx[j] : -1, eigen != 0);
+    bool ok = init_particle<CE>(W, Pd, Bsrc, p, prob, j - gen_base[prob], gen,
+                                src_idx ? src_idx[j] : -1, eigen != 0);
     if (!ok) {
         atomicOr(R.err, ERR_SOURCE);
         p.fate = FATE_LOST;
@@ -100,6 +103,7 @@ __global__ void k_source(World W, Particles P, Bank Bsrc, RunBufs R, int gen, in
 
 // n_dev (when set) holds the list's length on the device; the grid covers a
 // host-known upper bound, so the host need not wait for the count.
+template <bool CE>
 __global__ void __launch_bounds__(256, 4) k_advance(World W, Particles P, RunBufs R, const int *list,
                                                  int n, const int *n_dev, int *q_cross, int *q_coll)
 {
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(256, 4) k_advance(World W, Particles P, RunBuf
             const ProblemDev &Pd = W.prob[p.prob];
             int kind, which, uk = 0;
             double kt = P.kt[i];
-            ev = step_advance(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
+            ev = step_advance<false, true, CE>(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
             P.x[i] = p.x; P.y[i] = p.y; P.z[i] = p.z;
             if (W.time_any) P.t[i] = p.t;
             P.s[i] = p.s;
@@ -162,6 +166,7 @@ __global__ void __launch_bounds__(256) k_cross(World W, Particles P, RunBufs R, 
     enqueue(alive, i, next, next_n);
 }
 
+template <bool CE>
 __global__ void __launch_bounds__(256, 4) k_collide(World W, Particles P, Bank Bdst, RunBufs R,
                                                  const int *q_coll, int *next, int *next_n)
 {
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(256, 4) k_collide(World W, Particles P, Bank B
         p.fate = FATE_ALIVE;
         const ProblemDev &Pd = W.prob[p.prob];
         double kc = P.kc[i];
-        alive = step_collide(W, Pd, p, i, Bdst, R, P.uk[i], kc) == EV_ADVANCE;
+        alive = step_collide<false, true, CE>(W, Pd, p, i, Bdst, R, P.uk[i], kc) == EV_ADVANCE;
         P.ncoll[i] = p.ncoll;
         P.nfis[i] = p.nfis;
         P.g[i] = p.g;
@@ -199,6 +204,7 @@ __global__ void __launch_bounds__(256, 4) k_collide(World W, Particles P, Bank B
 // Monolithic segment (Sec. 2: every transport operation of one segment in a
 // single kernel, no sorting or grouping of like operations): flight, then the
 // crossing or collision it ends in; survivors go to the other list.
+template <bool CE>
 __global__ void __launch_bounds__(256, 3) k_segment(World W, Particles P, Bank Bdst, RunBufs R,
                                                  const int *list, int n, const int *n_dev,
                                                  int *next, int *next_n)
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(256, 3) k_segment(World W, Particles P, Bank B
             const ProblemDev &Pd = W.prob[p.prob];
             int kind, which, uk = 0;
             double kt = P.kt[i];
-            int ev = step_advance(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
+            int ev = step_advance<false, true, CE>(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
             P.kt[i] = kt;
             if (ev == EV_CROSS) {
                 ev = step_cross(W, p, kind, which);
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(256, 3) k_segment(World W, Particles P, Bank B
                 P.mat[i] = p.mat;
             } else if (ev == EV_COLLIDE) {
                 double kc = P.kc[i];
-                ev = step_collide(W, Pd, p, i, Bdst, R, uk, kc);
+                ev = step_collide<false, true, CE>(W, Pd, p, i, Bdst, R, uk, kc);
                 P.kc[i] = kc;
                 P.ncoll[i] = p.ncoll;
                 P.nfis[i] = p.nfis;
@@ -276,15 +282,22 @@ void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const R
                    cudaStream_t st)
 {
     if (total <= 0) return;
-    k_source<<<nblocks(total, block), block, 0, st>>>(W, P, Bsrc, R, gen, total, gen_base, src_idx,
-                                                      eigen);
+    if (W.ce_any)
+        k_source<true><<<nblocks(total, block), block, 0, st>>>(W, P, Bsrc, R, gen, total, gen_base,
+                                                                src_idx, eigen);
+    else
+        k_source<false><<<nblocks(total, block), block, 0, st>>>(W, P, Bsrc, R, gen, total, gen_base,
+                                                                 src_idx, eigen);
 }
 
 void launch_advance(const World &W, const Particles &P, const RunBufs &R, const int *list, int n,
                     const int *n_dev, int *q_cross, int *q_coll, int block, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_advance<<<nblocks(n, block), block, 0, st>>>(W, P, R, list, n, n_dev, q_cross, q_coll);
+    if (W.ce_any)
+        k_advance<true><<<nblocks(n, block), block, 0, st>>>(W, P, R, list, n, n_dev, q_cross, q_coll);
+    else
+        k_advance<false><<<nblocks(n, block), block, 0, st>>>(W, P, R, list, n, n_dev, q_cross, q_coll);
 }
 
 void launch_cross(const World &W, const Particles &P, const RunBufs &R, const int *q_cross,
@@ -299,7 +312,10 @@ void launch_collide(const World &W, const Particles &P, const Bank &Bdst, const 
                     cudaStream_t st)
 {
     if (n_bound <= 0) return;
-    k_collide<<<nblocks(n_bound, block), block, 0, st>>>(W, P, Bdst, R, q_coll, next, next_n);
+    if (W.ce_any)
+        k_collide<true><<<nblocks(n_bound, block), block, 0, st>>>(W, P, Bdst, R, q_coll, next, next_n);
+    else
+        k_collide<false><<<nblocks(n_bound, block), block, 0, st>>>(W, P, Bdst, R, q_coll, next, next_n);
 }
 
 void launch_segment(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
@@ -307,7 +323,11 @@ void launch_segment(const World &W, const Particles &P, const Bank &Bdst, const 
                     cudaStream_t st)
 {
     if (n <= 0) return;
-    k_segment<<<nblocks(n, block), block, 0, st>>>(W, P, Bdst, R, list, n, n_dev, next, next_n);
+    if (W.ce_any)
+        k_segment<true><<<nblocks(n, block), block, 0, st>>>(W, P, Bdst, R, list, n, n_dev, next, next_n);
+    else
+        k_segment<false><<<nblocks(n, block), block, 0, st>>>(W, P, Bdst, R, list, n, n_dev, next,
+                                                              next_n);
 }
 
 // ---------------------------------------------------------------------------
@@ -327,7 +347,7 @@ __device__ __forceinline__ void write_dead(const Particles &P, int slot, const P
     P.kc[slot] = kc;
 }
 
-template <bool TIME>
+template <bool TIME, bool CE>
 __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank Bsrc, Bank Bdst,
                                                     RunBufs R, PersistentArgs a)
 {
@@ -364,7 +384,7 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
                     Pd = W.prob + prob;
                     kt = 0.0;
                     kc = 0.0;
-                    bool ok = init_particle(W, *Pd, Bsrc, p, prob, j - a.gen_base[prob], gen,
+                    bool ok = init_particle<CE>(W, *Pd, Bsrc, p, prob, j - a.gen_base[prob], gen,
                                             a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
                     if (ok) {
                         alive = true;
@@ -379,9 +399,9 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
         if (__all_sync(0xffffffffu, done)) break;
         if (alive) {
             int kind, which, uk = 0;
-            int ev = step_advance<false, TIME>(W, *Pd, p, slot, R, rep, kind, which, uk, kt);
+            int ev = step_advance<false, TIME, CE>(W, *Pd, p, slot, R, rep, kind, which, uk, kt);
             if (ev == EV_CROSS) ev = step_cross(W, p, kind, which);
-            else if (ev == EV_COLLIDE) ev = step_collide<false, TIME>(W, *Pd, p, slot, Bdst, R, uk, kc);
+            else if (ev == EV_COLLIDE) ev = step_collide<false, TIME, CE>(W, *Pd, p, slot, Bdst, R, uk, kc);
             if (ev == EV_DEAD) {
                 alive = false;
                 write_dead(P, slot, p, kt, kc);
@@ -394,14 +414,19 @@ void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, con
                        const RunBufs &R, const PersistentArgs &a, int grid, int block,
                        cudaStream_t st)
 {
-    if (W.time_any) k_persistent<true><<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
-    else k_persistent<false><<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
+    if (W.ce_any) {
+        if (W.time_any) k_persistent<true, true><<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
+        else k_persistent<false, true><<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
+    } else {
+        if (W.time_any) k_persistent<true, false><<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
+        else k_persistent<false, false><<<grid, block, 0, st>>>(W, P, Bsrc, Bdst, R, a);
+    }
 }
 
 int persistent_max_blocks_per_sm(int block)
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<false>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<false, true>, block, 0);
     return n;
 }
 

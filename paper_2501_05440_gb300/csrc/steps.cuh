@@ -19,7 +19,9 @@ __device__ __forceinline__ int tally_batch(const ProblemDev &P, const PS &p)
 // score the track length.  Returns EV_CROSS, EV_COLLIDE or EV_DEAD (lost or cut).
 // REPLAY: same draws and moves, no tallies; the flight length is returned in d.
 // TIME = false: the world has no time dependence (the clock is compiled out).
-template <bool REPLAY = false, bool TIME = true>
+// CE = false: the world has no continuous-energy problem (that physics is
+// compiled out: a smaller kernel with fewer registers and spills).
+template <bool REPLAY = false, bool TIME = true, bool CE = true>
 __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const RunBufs &R, int rep, int &kind, int &which,
                                             int &uk, double &kt, double *d_out = nullptr)
@@ -29,7 +31,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
         return EV_DEAD;
     }
     double sigt, mfp, nusf;
-    if (P.ce) {
+    if (CE && P.ce) {
         ce_macro(W, p.mat, p.E, sigt, nusf);
         mfp = is_pos(sigt) ? __drcp_rn(sigt) : MCGB_INF;   // correctly rounded 1 / sigt
     } else {
@@ -54,7 +56,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     const double ta = p.t;
     double tb = p.t;
     if (timed) {
-        double iv = P.ce ? __drcp_rn(W.kv * sqrt(p.E)) : __ldg(W.g_invv + P.invv_off + p.g);
+        double iv = (CE && P.ce) ? __drcp_rn(W.kv * sqrt(p.E)) : __ldg(W.g_invv + P.invv_off + p.g);
         double dt = (P.tcut - p.t) / iv;
         if (is_neg(dt)) dt = 0.0;
         if (lt_mag(dt, d)) {
@@ -73,7 +75,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     if (REPLAY) {
         *d_out = d;
     } else {
-        score<TIME>(W, P, p, d, tally_batch(P, p), R.tacc, rep, ta, tb);
+        score<TIME, CE>(W, P, p, d, tally_batch(P, p), R.tacc, rep, ta, tb);
         kt = fma(d, nusf, kt);   // a sum over histories: agreement within rounding only
         if (R.own && (p.ucell >= 0 ? p.ucell : p.cell) == R.own_cell)
             R.own[(int64_t)slot * R.own_G + p.g] += d;
@@ -109,13 +111,13 @@ __device__ __forceinline__ int step_cross(const World &W, PS &p, int kind, int w
 // sigma_t of that nuclide, scatter (elastic, target at rest) when
 // xi sigma_t <= sigma_s.
 // REPLAY (multigroup only): same draws, no bank; *nf_out = sites banked.
-template <bool REPLAY = false, bool TIME = true>
+template <bool REPLAY = false, bool TIME = true, bool CE = true>
 __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const Bank &B, const RunBufs &R, int uk, double &kc,
                                             int *nf_out = nullptr)
 {
     p.ncoll++;
-    if (!P.ce) {
+    if (!CE || !P.ce) {
         int go = __ldg(W.m_goff + p.mat);
         int G = __ldg(W.m_G + p.mat);
         int g = p.g;
@@ -190,6 +192,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
 // New particle for slot `slot` (local index `local` of its problem) of
 // generation/cycle `gen`: stream gen 2^32 + local; from the source definition
 // (site < 0) or born at bank site `site`.
+template <bool CE = true>
 __device__ __forceinline__ bool init_particle(const World &W, const ProblemDev &P, const Bank &B,
                                               PS &p, int prob, int64_t local, int gen, int site,
                                               bool eigen)
@@ -207,10 +210,10 @@ __device__ __forceinline__ bool init_particle(const World &W, const ProblemDev &
     p.ucell = -1;
     if (site < 0) {
         p.root = (int)local;
-        return sample_source(W, P, p);
+        return sample_source<CE>(W, P, p);
     }
     p.root = eigen ? (int)local : B.root[site];
-    birth_from_site(W, P, B, site, p);
+    birth_from_site<CE>(W, P, B, site, p);
     return true;
 }
 

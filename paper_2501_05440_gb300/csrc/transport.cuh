@@ -767,7 +767,7 @@ __device__ __forceinline__ bool lt_time(double a, double b) { return lt_mag(a, b
 // Track-length tallies; a tally with time bins scores instead, per bin, the
 // time the segment [ta, tb] spends in the bin times 1 / bin width (population).
 // TIME = false compiles the time bins out (worlds without time dependence).
-template <bool TIME>
+template <bool TIME, bool CE = true>
 __device__ __forceinline__ void score(const World &W, const ProblemDev &P, const PS &p, double d,
                                       int batch, double *acc, int rep, double ta, double tb)
 {
@@ -783,7 +783,7 @@ __device__ __forceinline__ void score(const World &W, const ProblemDev &P, const
             bin = p.mat - P.mat0;
         }
         int e;
-        if (P.ce) {
+        if (CE && P.ce) {
             const double *ed = W.t_edges + __ldg(W.t_eoff + t);
             int ne = __ldg(W.t_nedges + t);
             if (lt_mag(p.E, __ldg(ed)) || lt_mag(__ldg(ed + ne - 1), p.E)) continue;
@@ -872,12 +872,14 @@ __device__ __forceinline__ bool mat_fissile(const World &W, const ProblemDev &P,
     return P.ce ? __ldg(W.mc_fissile + mat) != 0 : __ldg(W.m_fissile + mat) != 0;
 }
 
+template <bool CE = true>
 __device__ __forceinline__ void birth_energy(const World &W, const ProblemDev &P, PS &p)
 {
-    if (P.ce) p.E = maxwell(W, p.s);
+    if (CE && P.ce) p.E = maxwell(W, p.s);
     else p.g = sample_cdf(W.g_chicdf + __ldg(W.m_goff + p.mat), __ldg(W.m_G + p.mat), draw(p.s));
 }
 
+template <bool CE = true>
 __device__ __forceinline__ bool sample_source(const World &W, const ProblemDev &P, PS &p)
 {
     p.u = p.v = p.w = 0.0;
@@ -899,10 +901,10 @@ __device__ __forceinline__ bool sample_source(const World &W, const ProblemDev &
         if (!locate_full(W, P.root_univ, p)) return false;
     }
     switch (P.src_ekind) {
-    case E_CHI: birth_energy(W, P, p); break;
+    case E_CHI: birth_energy<CE>(W, P, p); break;
     case E_PDF: p.g = sample_cdf(W.src_cdf + P.src_cdf_off, P.src_ncdf, draw(p.s)); break;
     case E_FIXED: p.E = P.src_E; break;
-    default: p.E = maxwell(W, p.s);
+    default: if (CE) p.E = maxwell(W, p.s);
     }
     if (P.src_dkind == DIR_BEAM) {
         p.u = P.src_beam[0];
@@ -915,6 +917,7 @@ __device__ __forceinline__ bool sample_source(const World &W, const ProblemDev &
     return true;
 }
 
+template <bool CE = true>
 __device__ __forceinline__ void birth_from_site(const World &W, const ProblemDev &P, const Bank &B,
                                                 int b, PS &p)
 {
@@ -927,7 +930,7 @@ __device__ __forceinline__ void birth_from_site(const World &W, const ProblemDev
     p.iy = B.iy[b];
     p.ucell = B.ucell[b];
     p.mat = B.mat[b];
-    birth_energy(W, P, p);
+    birth_energy<CE>(W, P, p);
     iso_dir(p.s, p.u, p.v, p.w);
     set_recip(W, p);
 }
