@@ -63,8 +63,9 @@ class Tune(C.Structure):
 
 
 # the files that define the device code of the transport kernels
-_KERNEL_SOURCES = ["kernels.h", "world.h", "transport.cuh", "steps.cuh", "kernels_pool.cu",
-                   "kernels_transport.cu"]
+_KERNEL_SOURCES = ["kernels.h", "world.h", "transport.cuh", "steps.cuh", "pool.cuh",
+                   "kernels_pool.cu", "kernels_pool_mg.cu", "kernels_pool_mg_time.cu",
+                   "kernels_pool_ce.cu", "kernels_pool_ce_time.cu", "kernels_transport.cu"]
 
 
 def kernel_source_hash():
