@@ -267,6 +267,66 @@ int mcgb_shard_import(mcgb_ctx *ctx, int cycle, const double *sums, const mcgb_s
 int mcgb_shard_finish(mcgb_ctx *ctx);
 
 /* --------------------------------------------------------------------------- */
+/* spatial domain decomposition (one rank of a multi-GPU run; Sec. 1: MC/DC's  */
+/* domain "replicated or decomposed" over MPI)                                 */
+/* A particle in flight between the domains of two ranks. */
+typedef struct {
+    double x, y, z, u, v, w, E;
+    double drem;            /* remaining distance to the collision sampled before the
+                               domain boundary cut the flight (< 0: none) */
+    uint64_t s;             /* random-number state */
+    int64_t hist;           /* the history's source index in its cycle */
+    int32_t g, cell, ix, iy, ucell, mat, prob, root, nfis, ncoll, ncross, dest;
+} mcgb_flight;
+/* This context owns the slab cuts[rank] <= coordinate `axis` (0 x, 1 y, 2 z)
+ * < cuts[rank + 1] of an N-history k-eigenvalue power iteration of inactive +
+ * active cycles (cuts: n_domains + 1 increasing values, +-inf allowed at the
+ * ends).  A history is transported by the rank whose slab holds it: a flight
+ * that reaches the slab's boundary stops there and the particle -- with the
+ * rest of its sampled collision distance, so no random number is drawn again
+ * -- is handed to the neighbouring rank.  Random streams are per history, so
+ * every history is the single-device one up to the rounding of the cut
+ * flights (one domain: identical).  Every cycle, in order:
+ *   mcgb_domain_sources  the cycle's sources in this slab (cycle 0: sampled
+ *                        from the source definition; later: resampled from
+ *                        the global ordered bank of the previous cycle,
+ *                        bank[0..M), device records);
+ *   repeat:  mcgb_domain_sweep (transport every particle in the slab until it
+ *            dies or leaves; *n_out = particles leaving), mcgb_domain_outbox
+ *            (copy them to a device buffer), and mcgb_domain_inbox with the
+ *            outboxes of all ranks (each rank keeps the particles addressed
+ *            to it) -- until no rank has a particle leaving;
+ *   mcgb_domain_export   the rank's share of the cycle end, to device buffers:
+ *                        nfis[N] = sites banked by each history that ended in
+ *                        this slab (0 for the others), sites[0..m) = the sites
+ *                        banked in this slab (any order), sums = [k_tl, k_c,
+ *                        tally sums]; *m, *n_sums their sizes (sites and sums
+ *                        NULL: only the sizes);
+ *   mcgb_domain_import   the all-rank sums, nfis summed over ranks, and every
+ *                        rank's sites (concatenated, any order): the statistics
+ *                        of the cycle and the global (parent, child)-ordered bank.
+ * mcgb_domain_finish then fills mcgb_get_k / mcgb_get_cycle_k / mcgb_get_tally
+ * as mcgb_run_eigenvalue does.  mcgb_domain_records writes, for checks, the
+ * per-history records of the last cycle's histories that ended in this slab
+ * (device arrays of N; zero for the others, so that their sum over ranks is
+ * the complete record).  All arrays of these calls are device pointers on the
+ * context's device, used in order on its stream.  Out-of-order calls fail with
+ * MCGB_E_STATE; time-dependent problems are rejected. */
+int mcgb_domain_begin(mcgb_ctx *ctx, int64_t N, int inactive, int active, uint64_t seed, int axis,
+                      const double *cuts, int n_domains, int rank);
+int mcgb_domain_sources(mcgb_ctx *ctx, int cycle, const mcgb_site *bank, int64_t M);
+int mcgb_domain_sweep(mcgb_ctx *ctx, int64_t *n_out);
+int mcgb_domain_outbox(mcgb_ctx *ctx, mcgb_flight *out, size_t cap);
+int mcgb_domain_inbox(mcgb_ctx *ctx, const mcgb_flight *in, int64_t n);
+int mcgb_domain_export(mcgb_ctx *ctx, int32_t *nfis, mcgb_site *sites, size_t sites_cap,
+                       double *sums, size_t sums_cap, size_t *m, size_t *n_sums);
+int mcgb_domain_import(mcgb_ctx *ctx, int cycle, const double *sums, const int32_t *nfis,
+                       const mcgb_site *sites, int64_t M);
+int mcgb_domain_finish(mcgb_ctx *ctx);
+int mcgb_domain_records(mcgb_ctx *ctx, int32_t *n_coll, int32_t *n_cross, int32_t *n_fis,
+                        int32_t *fate, int32_t *g_end, uint64_t *rng_end);
+
+/* --------------------------------------------------------------------------- */
 /* results                                                                      */
 /* out[6] = k (track length) mean, sd; k (collision) mean, sd; k (analog) mean, sd. */
 int mcgb_get_k(mcgb_ctx *ctx, double out[6]);

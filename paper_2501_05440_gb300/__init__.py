@@ -121,6 +121,12 @@ def lib():
                 "mcgb_shard_begin": [P, i64, i64, i64, i32, i32, u64],
                 "mcgb_shard_cycle": [P, i32, P], "mcgb_shard_export": [P, P, sz, P, sz, P],
                 "mcgb_shard_import": [P, i32, P, P, i64], "mcgb_shard_finish": [P],
+                "mcgb_domain_begin": [P, i64, i32, i32, u64, i32, P, i32, i32],
+                "mcgb_domain_sources": [P, i32, P, i64], "mcgb_domain_sweep": [P, P],
+                "mcgb_domain_outbox": [P, P, sz], "mcgb_domain_inbox": [P, P, i64],
+                "mcgb_domain_export": [P, P, P, sz, P, sz, P, P],
+                "mcgb_domain_import": [P, i32, P, P, P, i64], "mcgb_domain_finish": [P],
+                "mcgb_domain_records": [P, P, P, P, P, P, P],
                 "mcgb_set_tally_time_bins": [P, i32, i32, P],
                 "mcgb_run_eigenvalue": [P, i64, i32, i32, u64],
                 "mcgb_run_fixed_source": [P, i64, i32, u64],
@@ -300,6 +306,49 @@ class Context:
 
     def shard_finish(self):
         _chk(self.L.mcgb_shard_finish(self.h))
+
+    # spatial domain decomposition: array arguments are device addresses (ints)
+    def domain_begin(self, N, inactive, active, seed, axis, cuts, rank):
+        c = _f64(cuts)
+        _chk(self.L.mcgb_domain_begin(self.h, int(N), int(inactive), int(active), int(seed),
+                                      int(axis), _p(c), len(c) - 1, int(rank)))
+
+    def domain_sources(self, cycle, bank=None, M=0):
+        _chk(self.L.mcgb_domain_sources(self.h, int(cycle), C.c_void_p(bank), int(M)))
+
+    def domain_sweep(self):
+        """Transport the slab's particles; returns how many leave it."""
+        n = C.c_int64()
+        _chk(self.L.mcgb_domain_sweep(self.h, C.byref(n)))
+        return n.value
+
+    def domain_outbox(self, out, cap):
+        _chk(self.L.mcgb_domain_outbox(self.h, C.c_void_p(out), int(cap)))
+
+    def domain_inbox(self, recs, n):
+        _chk(self.L.mcgb_domain_inbox(self.h, C.c_void_p(recs), int(n)))
+
+    def domain_export_sizes(self):
+        m, ns = C.c_size_t(), C.c_size_t()
+        _chk(self.L.mcgb_domain_export(self.h, None, None, 0, None, 0, C.byref(m), C.byref(ns)))
+        return m.value, ns.value
+
+    def domain_export(self, nfis, sites, sites_cap, sums, sums_cap):
+        m, ns = C.c_size_t(), C.c_size_t()
+        _chk(self.L.mcgb_domain_export(self.h, C.c_void_p(nfis), C.c_void_p(sites), int(sites_cap),
+                                       C.c_void_p(sums), int(sums_cap), C.byref(m), C.byref(ns)))
+        return m.value, ns.value
+
+    def domain_import(self, cycle, sums, nfis, sites, M):
+        _chk(self.L.mcgb_domain_import(self.h, int(cycle), C.c_void_p(sums), C.c_void_p(nfis),
+                                       C.c_void_p(sites), int(M)))
+
+    def domain_finish(self):
+        _chk(self.L.mcgb_domain_finish(self.h))
+
+    def domain_records(self, n_coll, n_cross, n_fis, fate, g_end, rng_end):
+        _chk(self.L.mcgb_domain_records(self.h, *[C.c_void_p(a) for a in
+                                                  (n_coll, n_cross, n_fis, fate, g_end, rng_end)]))
 
     def set_free_gas(self, kT, cut=0.0):
         _chk(self.L.mcgb_set_free_gas(self.h, float(kT), float(cut)))

@@ -184,6 +184,19 @@ struct mcgb_ctx {
         DevAlloc mem;
         double *sums = nullptr;      // the rank's [k_tl, k_c, tally...] sums of the last cycle
     } shard;
+    // one rank's slab of a spatially decomposed power iteration
+    struct {
+        bool on = false;
+        int64_t N = 0, cap = 0, M = 0, n_out = 0;
+        int inactive = 0, ncyc = 0, cyc = 0, rank = 0, nd = 1;
+        int state = 0;               // 0: sources next, 1: sweeping, 2: import next
+        DomainCut cut{};
+        DevAlloc mem;
+        double *cuts = nullptr;
+        int *list = nullptr, *n_list = nullptr, *outbox = nullptr, *n_out_dev = nullptr;
+        int *work = nullptr;
+        ShardSite *glob = nullptr;   // the last cycle's global (parent, child)-ordered bank
+    } dom;
 };
 
 struct mcgb_batch {
@@ -214,6 +227,7 @@ static int prepare_buffers(mcgb_ctx *c, int64_t cap_p, int64_t cap_b)
     CKR(m.get(P.x, cap_p)); CKR(m.get(P.y, cap_p)); CKR(m.get(P.z, cap_p));
     CKR(m.get(P.u, cap_p)); CKR(m.get(P.v, cap_p)); CKR(m.get(P.w, cap_p));
     CKR(m.get(P.E, cap_p)); CKR(m.get(P.kt, cap_p)); CKR(m.get(P.kc, cap_p)); CKR(m.get(P.t, cap_p));
+    CKR(m.get(P.drem, cap_p));
     CKR(m.get(P.iu, cap_p)); CKR(m.get(P.iv, cap_p)); CKR(m.get(P.iw, cap_p));
     CKR(m.get(P.s, cap_p));
     CKR(m.get(P.g, cap_p)); CKR(m.get(P.cell, cap_p)); CKR(m.get(P.ix, cap_p));
@@ -1512,17 +1526,16 @@ int mcgb_shard_import(mcgb_ctx *c, int cycle, const double *sums, const mcgb_sit
     return MCGB_OK;
 }
 
-int mcgb_shard_finish(mcgb_ctx *c)
+// Statistics of a power iteration run in pieces (sharded or domain
+// decomposed): per-cycle k from the summed estimators in r.kout, the bank
+// sizes in c->cyc_m, k means and sds over the active cycles, tally batch
+// means and sds from r.tsum / r.tsum2 -- as eigen_finish computes them.
+static int finish_power_iteration(mcgb_ctx *c, int ncyc, int inactive, double N)
 {
-    if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
-    if (c->shard.cyc < c->shard.ncyc) return fail(MCGB_E_STATE, "cycles remain to be run");
-    CK(cudaSetDevice(c->device));
-    c->shard.on = false;
     RunState &r = c->rs;
     cudaStream_t st = c->stream;
-    const int ncyc = c->shard.ncyc, inactive = c->shard.inactive, active = ncyc - inactive;
+    const int active = ncyc - inactive;
     const int acc = c->world->W.acc_size;
-    const double N = (double)c->shard.N;
     std::vector<double> kout(2 * ncyc), ts(std::max(acc, 1)), ts2(std::max(acc, 1));
     CK(cudaMemcpyAsync(kout.data(), r.kout, sizeof(double) * 2 * ncyc, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ts.data(), r.tsum, sizeof(double) * acc, cudaMemcpyDeviceToHost, st));
@@ -1553,6 +1566,268 @@ int mcgb_shard_finish(mcgb_ctx *c)
             mean_sd(ts[dw.t_off[gt] + b], ts2[dw.t_off[gt] + b], active, c->t_mean[t][b],
                     c->t_sd[t][b]);
     }
+    return MCGB_OK;
+}
+
+int mcgb_shard_finish(mcgb_ctx *c)
+{
+    if (!c || !c->shard.on) return fail(MCGB_E_STATE, "no shard begun");
+    if (c->shard.cyc < c->shard.ncyc) return fail(MCGB_E_STATE, "cycles remain to be run");
+    CK(cudaSetDevice(c->device));
+    c->shard.on = false;
+    return finish_power_iteration(c, c->shard.ncyc, c->shard.inactive, (double)c->shard.N);
+}
+
+// ---- spatial domain decomposition ------------------------------------------
+int mcgb_domain_begin(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_t seed, int axis,
+                      const double *cuts, int n_domains, int rank)
+{
+    if (!c || !cuts) return fail(MCGB_E_INVALID_ARG, "null argument");
+    if (N <= 0 || N > (int64_t)1 << 30 || inactive < 0 || active < 1 || inactive + active > 4096)
+        return fail(MCGB_E_INVALID_ARG, "bad run size");
+    if (axis < 0 || axis > 2 || n_domains < 1 || n_domains > 1024 || rank < 0 || rank >= n_domains)
+        return fail(MCGB_E_INVALID_ARG, "bad domain layout");
+    if (!(cuts[0] == -HUGE_VAL) || !(cuts[n_domains] == HUGE_VAL))
+        return fail(MCGB_E_INVALID_ARG, "the outer cuts must be -inf and +inf");
+    for (int r = 0; r < n_domains; r++)
+        if (!(cuts[r] < cuts[r + 1])) return fail(MCGB_E_INVALID_ARG, "cuts must increase");
+    if (c->def.time_on) return fail(MCGB_E_INVALID_ARG, "time dependence is for fixed-source runs");
+    CK(cudaSetDevice(c->device));
+    c->eig.on = false;
+    c->shard.on = false;
+    c->dom.on = false;
+    CKR(build_single(c, N, 1, seed));
+    double bf = c->opts.bank_factor > 0 ? c->opts.bank_factor : 3.0;
+    int64_t cap_b = (int64_t)(bf * (double)N) + 1024;
+    CKR(prepare_buffers(c, std::max(N, cap_b), cap_b));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const World &W = c->world->W;
+    CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)W.acc_size * W.nrep, st));
+    CK(cudaMemsetAsync(r.tsum, 0, sizeof(double) * (size_t)std::max(W.acc_size, 1), st));
+    CK(cudaMemsetAsync(r.tsum2, 0, sizeof(double) * (size_t)std::max(W.acc_size, 1), st));
+    CK(cudaMemsetAsync(r.kout, 0, sizeof(double) * 2 * 4096, st));
+    CK(cudaMemsetAsync(r.cnt, 0, sizeof(unsigned long long) * 8, st));
+    CK(cudaMemsetAsync(r.err, 0, sizeof(int), st));
+    auto &d = c->dom;
+    d.mem.release();
+    CKR(d.mem.get(d.cuts, n_domains + 1));
+    CKR(d.mem.get(d.list, N));
+    CKR(d.mem.get(d.outbox, N));
+    CKR(d.mem.get(d.n_list, 4));
+    CKR(d.mem.get(d.n_out_dev, 4));
+    CKR(d.mem.get(d.work, 4));
+    CKR(d.mem.get(d.glob, cap_b));
+    CK(cudaMemcpyAsync(d.cuts, cuts, sizeof(double) * (n_domains + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    c->counters = mcgb_counters{};
+    c->counters.world_bytes = (int64_t)c->world->bytes;
+    c->launches = 0;
+    d.on = true;
+    d.N = N;
+    d.cap = cap_b;
+    d.M = 0;
+    d.inactive = inactive;
+    d.ncyc = inactive + active;
+    d.cyc = 0;
+    d.rank = rank;
+    d.nd = n_domains;
+    d.state = 0;
+    d.cut = DomainCut{axis, cuts[rank], cuts[rank + 1]};
+    c->cyc_m.assign(d.ncyc, 0);
+    c->cyc_ktl.assign(d.ncyc, 0.0);
+    c->cyc_kc.assign(d.ncyc, 0.0);
+    return MCGB_OK;
+}
+
+static int domain_check(mcgb_ctx *c, int state, const char *what)
+{
+    if (!c || !c->dom.on) return fail(MCGB_E_STATE, "no domain run begun");
+    if (c->dom.state != state) return fail(MCGB_E_STATE, std::string("out of order: ") + what);
+    return MCGB_OK;
+}
+
+int mcgb_domain_sources(mcgb_ctx *c, int cycle, const mcgb_site *bank, int64_t M)
+{
+    CKR(domain_check(c, 0, "sources begin a cycle"));
+    auto &d = c->dom;
+    if (cycle != d.cyc || cycle >= d.ncyc) return fail(MCGB_E_STATE, "cycles run in order");
+    const ShardSite *b = reinterpret_cast<const ShardSite *>(bank);
+    if (cycle > 0 && !b) {
+        b = d.glob;   // the bank this context assembled at the last import
+        M = d.M;
+    }
+    if (cycle > 0 && M <= 0) return fail(MCGB_E_INVALID_ARG, "no bank to resample");
+    CK(cudaSetDevice(c->device));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    double xi = 0.0;
+    if (cycle > 0) {
+        uint64_t rs = rng_stream(c->world->probs[0].seed, ((uint64_t)(cycle - 1) << 32) + 0xFFFFFFFFULL);
+        xi = draw_host(rs);
+    }
+    CK(cudaMemsetAsync(d.n_list, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(r.bank_n, 0, sizeof(int), st));
+    launch_dom_sources(c->world->W, r.P, cycle, d.N, cycle > 0 ? b : nullptr, M, xi, d.cut, d.cuts,
+                       d.nd, d.rank, d.list, d.n_list, r.err, st);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    d.state = 1;
+    return MCGB_OK;
+}
+
+int mcgb_domain_sweep(mcgb_ctx *c, int64_t *n_out)
+{
+    CKR(domain_check(c, 1, "sweeps follow the sources"));
+    if (!n_out) return fail(MCGB_E_INVALID_ARG, "null output");
+    auto &d = c->dom;
+    CK(cudaSetDevice(c->device));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    CK(cudaMemcpyAsync(r.pinned + 8, d.n_list, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int n = r.pinned[8];
+    CK(cudaMemsetAsync(d.n_out_dev, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(d.work, 0, sizeof(int), st));
+    RunBufs R = run_bufs(c, nullptr, -1, 0);
+    launch_dom_sweep(c->world->W, r.P, r.bank[1], R, d.list, n, d.work, d.cut, d.outbox, d.n_out_dev,
+                     c->sms * 8, st);
+    c->launches += n > 0 ? 1 : 0;
+    CK(cudaMemsetAsync(d.n_list, 0, sizeof(int), st));
+    CK(cudaMemcpyAsync(r.pinned + 9, d.n_out_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(r.pinned + 10, r.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(r.pinned + 11, r.bank_n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int err = r.pinned[10];
+    if (r.pinned[11] > r.bank[1].cap) err |= ERR_BANK_OVERFLOW;
+    if (err & ERR_BANK_OVERFLOW)
+        return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow (raise opts.bank_factor)");
+    if (err & ERR_SOURCE) return fail(MCGB_E_STATE, "source sampling failed");
+    d.n_out = r.pinned[9];
+    *n_out = d.n_out;
+    return MCGB_OK;
+}
+
+int mcgb_domain_outbox(mcgb_ctx *c, mcgb_flight *out, size_t cap)
+{
+    CKR(domain_check(c, 1, "the outbox follows a sweep"));
+    auto &d = c->dom;
+    if (cap < (size_t)d.n_out || (d.n_out > 0 && !out))
+        return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    CK(cudaSetDevice(c->device));
+    launch_dom_pack(c->rs.P, d.outbox, (int)d.n_out, d.cut, d.rank, reinterpret_cast<FlightRec *>(out),
+                    c->stream);
+    c->launches += d.n_out > 0 ? 1 : 0;
+    CK(cudaGetLastError());
+    return MCGB_OK;
+}
+
+int mcgb_domain_inbox(mcgb_ctx *c, const mcgb_flight *in, int64_t n)
+{
+    CKR(domain_check(c, 1, "the inbox follows a sweep"));
+    if (n < 0 || (n > 0 && !in)) return fail(MCGB_E_INVALID_ARG, "bad inbox");
+    CK(cudaSetDevice(c->device));
+    auto &d = c->dom;
+    launch_dom_unpack(c->world->W, c->rs.P, reinterpret_cast<const FlightRec *>(in), n, d.rank,
+                      d.list, d.n_list, c->stream);
+    c->launches += n > 0 ? 1 : 0;
+    CK(cudaGetLastError());
+    return MCGB_OK;
+}
+
+int mcgb_domain_export(mcgb_ctx *c, int32_t *nfis, mcgb_site *sites, size_t sites_cap, double *sums,
+                       size_t sums_cap, size_t *m, size_t *n_sums)
+{
+    CKR(domain_check(c, 1, "the export ends a cycle's sweeps"));
+    auto &d = c->dom;
+    CK(cudaSetDevice(c->device));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const World &W = c->world->W;
+    const size_t ns = 2 + (size_t)std::max(W.acc_size, 0);
+    CK(cudaMemcpyAsync(r.pinned + 11, r.bank_n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int64_t mloc = r.pinned[11];
+    if (m) *m = (size_t)mloc;
+    if (n_sums) *n_sums = ns;
+    if (!nfis && !sites && !sums) return MCGB_OK;   // size query
+    if (!nfis || !sums || (mloc > 0 && !sites)) return fail(MCGB_E_INVALID_ARG, "null output");
+    if (sites_cap < (size_t)mloc || sums_cap < ns) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    CK(cudaMemsetAsync(sums, 0, sizeof(double) * 2, st));
+    launch_dom_reduce(r.P, d.N, sums, r.cnt, nfis, st);
+    if (W.acc_size > 0) {
+        launch_acc_reduce(r.tacc, W.acc_size, W.nrep, sums + 2, st);
+        CK(cudaMemsetAsync(r.tacc, 0, sizeof(double) * (size_t)W.acc_size * W.nrep, st));
+    }
+    launch_dom_sites(r.bank[1], mloc, reinterpret_cast<ShardSite *>(sites), st);
+    c->launches += 3;
+    CK(cudaGetLastError());
+    d.state = 2;
+    return MCGB_OK;
+}
+
+int mcgb_domain_import(mcgb_ctx *c, int cycle, const double *sums, const int32_t *nfis,
+                       const mcgb_site *sites, int64_t M)
+{
+    CKR(domain_check(c, 2, "the import follows the export"));
+    auto &d = c->dom;
+    if (cycle != d.cyc) return fail(MCGB_E_STATE, "cycles run in order");
+    if (!sums || !nfis || M < 0 || (M > 0 && !sites)) return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (M == 0) {
+        d.on = false;
+        return fail(MCGB_E_STATE, "fission bank empty after cycle " + std::to_string(cycle));
+    }
+    if (M > d.cap) {
+        d.on = false;
+        return fail(MCGB_E_BANK_OVERFLOW, "fission bank overflow (raise opts.bank_factor)");
+    }
+    CK(cudaSetDevice(c->device));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const World &W = c->world->W;
+    launch_shard_stats(sums, W.acc_size, (double)d.N, cycle, cycle >= d.inactive, r.kout, r.tsum,
+                       r.tsum2, st);
+    scan_exclusive(nfis, r.off, d.N, r.M, r.scratch, st);
+    CK(cudaMemsetAsync(r.err, 0, sizeof(int), st));
+    launch_dom_place(reinterpret_cast<const ShardSite *>(sites), M, r.off, d.glob, d.cap, r.err, st);
+    c->launches += 5;
+    CK(cudaMemcpyAsync(r.pinned + 4, r.M, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(r.pinned + 5, r.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((int64_t)r.pinned[4] != M || (r.pinned[5] & ERR_BANK_OVERFLOW)) {
+        d.on = false;
+        return fail(MCGB_E_STATE, "the sites do not match the histories' site counts");
+    }
+    c->cyc_m[cycle] = M;
+    d.M = M;
+    d.cyc = cycle + 1;
+    d.state = 0;
+    c->counters.generations += 1;
+    return MCGB_OK;
+}
+
+int mcgb_domain_finish(mcgb_ctx *c)
+{
+    if (!c || !c->dom.on) return fail(MCGB_E_STATE, "no domain run begun");
+    if (c->dom.cyc < c->dom.ncyc || c->dom.state != 0) return fail(MCGB_E_STATE, "cycles remain to be run");
+    CK(cudaSetDevice(c->device));
+    c->dom.on = false;
+    CKR(fetch_counters(c));
+    c->counters.histories = c->dom.N * c->dom.ncyc;
+    return finish_power_iteration(c, c->dom.ncyc, c->dom.inactive, (double)c->dom.N);
+}
+
+int mcgb_domain_records(mcgb_ctx *c, int32_t *n_coll, int32_t *n_cross, int32_t *n_fis, int32_t *fate,
+                        int32_t *g_end, uint64_t *rng_end)
+{
+    if (!c || !c->world || c->dom.N <= 0) return fail(MCGB_E_STATE, "no domain run");
+    if (!n_coll || !n_cross || !n_fis || !fate || !g_end || !rng_end)
+        return fail(MCGB_E_INVALID_ARG, "null output");
+    CK(cudaSetDevice(c->device));
+    launch_dom_records(c->rs.P, c->dom.N, n_coll, n_cross, n_fis, fate, g_end,
+                       reinterpret_cast<unsigned long long *>(rng_end), c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
     return MCGB_OK;
 }
 

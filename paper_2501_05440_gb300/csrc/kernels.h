@@ -84,6 +84,25 @@ void launch_unpack_sources(const ShardSite *bank, int64_t M, int64_t N, int64_t 
                            double xi, const Bank &Bs, cudaStream_t st);
 void launch_shard_stats(const double *sums, int acc_size, double N, int cyc, int active,
                         double *kout, double *tsum, double *tsum2, cudaStream_t st);
+// spatial domain decomposition (kernels_domain.cu)
+void launch_dom_sources(const World &W, const Particles &P, int gen, int64_t N,
+                        const ShardSite *bank, int64_t M, double xi, const DomainCut &dom,
+                        const double *cuts, int nd, int rank, int *list, int *n_list, int *err,
+                        cudaStream_t st);
+void launch_dom_sweep(const World &W, const Particles &P, const Bank &Bdst, const RunBufs &R,
+                      const int *list, int n, int *work, const DomainCut &dom, int *outbox,
+                      int *n_out, int grid, cudaStream_t st);
+void launch_dom_pack(const Particles &P, const int *outbox, int n, const DomainCut &dom, int rank,
+                     FlightRec *out, cudaStream_t st);
+void launch_dom_unpack(const World &W, const Particles &P, const FlightRec *in, int64_t n, int rank,
+                       int *list, int *n_list, cudaStream_t st);
+void launch_dom_reduce(const Particles &P, int64_t N, double *ksum, unsigned long long *cnt,
+                       int *nfis_out, cudaStream_t st);
+void launch_dom_sites(const Bank &B, int64_t m, ShardSite *out, cudaStream_t st);
+void launch_dom_place(const ShardSite *in, int64_t m, const int *off, ShardSite *glob, int64_t cap,
+                      int *err, cudaStream_t st);
+void launch_dom_records(const Particles &P, int64_t N, int *nc, int *nx, int *nf, int *fate, int *g,
+                        unsigned long long *rng, cudaStream_t st);
 void launch_gen_base(const int64_t *base, int nprob, const int *off, const int *M,
                      int64_t *next_base, cudaStream_t st);
 void launch_copy_records(const Particles &P, int64_t n, int *ncoll, int *ncross, uint64_t *rng,

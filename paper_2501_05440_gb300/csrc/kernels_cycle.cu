@@ -124,21 +124,6 @@ void launch_perm(const Bank &B, const int *off, const int *M, int *perm, int gri
 
 // Systematic resampling of M sorted sites to N sources:
 // source j <- site floor((j + xi) M / N) (clamped to M - 1).
-// Systematic resampling: source j of N takes bank site floor((j + xi) M / N),
-// at most M - 1.  xi = n 2^-53 exactly (n in [1, 2^53]), so the floor of the
-// rational is exact in integers: (j + n 2^-53) M / N = (j M + n M 2^-53) / N,
-// and floor((K + f) / N) = floor(K / N) for an integer K and 0 <= f < 1, with
-// K = j M + floor(n M / 2^53).  (j M < 2^63 for j < N <= 2^31, M <= 2^32.)
-__device__ __forceinline__ int64_t site_index(int64_t j, double xi, int64_t M, int64_t N)
-{
-    uint64_t n = (uint64_t)(xi * 0x1p53);
-    uint64_t m = (uint64_t)M;
-    uint64_t lo = n * m, hi = __umul64hi(n, m);
-    uint64_t K = (uint64_t)j * m + ((hi << 11) | (lo >> 53));
-    int64_t idx = (int64_t)(K / (uint64_t)N);
-    return idx >= M ? M - 1 : idx;
-}
-
 __global__ void k_resample(const int *perm, const int *Mp, int64_t N, double xi, int *src_idx,
                            int *err, int64_t cap)
 {
@@ -153,7 +138,7 @@ __global__ void k_resample(const int *perm, const int *Mp, int64_t N, double xi,
         src_idx[j] = 0;
         return;
     }
-    src_idx[j] = perm[site_index(j, xi, M, N)];
+    src_idx[j] = perm[site_index_of(j, xi, M, N)];
 }
 
 void launch_resample(const int *perm, const int *M, int64_t N, double xi, int *src_idx, int *err,
@@ -285,7 +270,7 @@ __global__ void k_resample_dev(const int *perm, const int *Mp, int64_t N, const 
         src_idx[j] = 0;
         return;
     }
-    src_idx[j] = perm[site_index(j, xi, M, N)];
+    src_idx[j] = perm[site_index_of(j, xi, M, N)];
 }
 
 void launch_resample_dev(const int *perm, const int *M, int64_t N, const double *xi_tab,
@@ -462,14 +447,14 @@ void launch_pack_sites(const Bank &B, const int *perm, int64_t M, int64_t j0, Sh
 }
 
 // Sources j0 .. j0+n-1 of the next cycle from the global ordered bank of M
-// sites: systematic resampling with the cycle's draw (site_index, exactly as
+// sites: systematic resampling with the cycle's draw (site_index_of, exactly as
 // a single device resamples), written as the birth bank Bs in local order.
 __global__ void k_unpack_sources(const ShardSite *bank, int64_t M, int64_t N, int64_t j0, int64_t n,
                                  double xi, Bank Bs)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const ShardSite &s = bank[site_index(j0 + k, xi, M, N)];
+    const ShardSite &s = bank[site_index_of(j0 + k, xi, M, N)];
     Bs.x[k] = s.x;
     Bs.y[k] = s.y;
     Bs.z[k] = s.z;

@@ -7,7 +7,8 @@
 
 namespace mcgb {
 
-enum { EV_ADVANCE = 0, EV_CROSS = 1, EV_COLLIDE = 2, EV_DEAD = 3 };
+enum { EV_ADVANCE = 0, EV_CROSS = 1, EV_COLLIDE = 2, EV_DEAD = 3, EV_EXPORT = 4 };
+
 
 __device__ __forceinline__ int tally_batch(const ProblemDev &P, const PS &p)
 {
@@ -21,10 +22,14 @@ __device__ __forceinline__ int tally_batch(const ProblemDev &P, const PS &p)
 // TIME = false: the world has no time dependence (the clock is compiled out).
 // CE = false: the world has no continuous-energy problem (that physics is
 // compiled out: a smaller kernel with fewer registers and spills).
-template <bool REPLAY = false, bool TIME = true, bool CE = true>
+// DOM: the flight also stops where it leaves the slab *dom (EV_EXPORT), and
+// *drem carries the rest of the sampled collision distance to the next flight
+// (which then takes no draw; *drem < 0: sample as usual).
+template <bool REPLAY = false, bool TIME = true, bool CE = true, bool DOM = false>
 __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const RunBufs &R, int rep, int &kind, int &which,
-                                            int &uk, double &kt, double *d_out = nullptr)
+                                            int &uk, double &kt, double *d_out = nullptr,
+                                            const DomainCut *dom = nullptr, double *drem = nullptr)
 {
     if (p.ncoll + p.ncross >= MAX_EVENTS) {
         p.fate = FATE_CAPPED;
@@ -40,8 +45,14 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
         nusf = __ldg(W.g_nusf + go);
         mfp = __ldg(W.g_mfp + go);
     }
-    uint64_t n = draw_n(p.s);
-    double dc = is_pos(sigt) ? -log_n(W, n) * mfp : MCGB_INF;
+    double dc;
+    if (DOM && !is_neg(*drem)) {
+        dc = *drem;     // the rest of a flight cut at the slab's boundary
+    } else {
+        uint64_t n = draw_n(p.s);
+        dc = is_pos(sigt) ? -log_n(W, n) * mfp : MCGB_INF;
+    }
+    if (DOM) *drem = -1.0;
     double ds = boundary(W, p, kind, which);
     const bool timed = TIME && P.time_on;
     if (!timed && is_inf(dc) && is_inf(ds)) {
@@ -50,6 +61,22 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     }
     bool coll = lt_mag(dc, ds);     // both are +-0, positive or +inf
     double d = coll ? dc : ds;
+    bool leaves = false;
+    if (DOM) {
+        // distance to the slab's boundary ahead along its axis; strictly
+        // nearer than the collision and the surface: the particle stops there
+        const double c = dom->axis == 0 ? p.x : (dom->axis == 1 ? p.y : p.z);
+        const double dir = dom->axis == 0 ? p.u : (dom->axis == 1 ? p.v : p.w);
+        double tdom = MCGB_INF;
+        if (is_pos(dir) && !is_inf(dom->hi)) tdom = (dom->hi - c) / dir;
+        else if (is_neg(dir) && !is_inf(-dom->lo)) tdom = (dom->lo - c) / dir;
+        if (is_neg(tdom)) tdom = 0.0;
+        if (lt_mag(tdom, d)) {
+            leaves = true;
+            *drem = dc - tdom;    // +inf stays +inf
+            d = tdom;
+        }
+    }
     // time dependence: the flight ends where the clock reaches tcut, at the
     // distance (tcut - t) / (1/v); a tie goes to the collision or crossing
     bool tcut = false;
@@ -85,6 +112,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
         p.fate = FATE_TIME;
         return EV_DEAD;
     }
+    if (DOM && leaves) return EV_EXPORT;
     return coll ? EV_COLLIDE : EV_CROSS;
 }
 

@@ -865,6 +865,21 @@ __device__ __forceinline__ void bank_append(const Bank &B, int *bank_n, int *err
     }
 }
 
+// Systematic resampling: source j of N takes bank site floor((j + xi) M / N),
+// at most M - 1.  xi = n 2^-53 exactly (n in [1, 2^53]), so the floor of the
+// rational is exact in integers: (j + n 2^-53) M / N = (j M + n M 2^-53) / N,
+// and floor((K + f) / N) = floor(K / N) for an integer K and 0 <= f < 1, with
+// K = j M + floor(n M / 2^53).  (j M < 2^63 for j < N <= 2^31, M <= 2^32.)
+__device__ __forceinline__ int64_t site_index_of(int64_t j, double xi, int64_t M, int64_t N)
+{
+    uint64_t n = (uint64_t)(xi * 0x1p53);
+    uint64_t m = (uint64_t)M;
+    uint64_t lo = n * m, hi = __umul64hi(n, m);
+    uint64_t K = (uint64_t)j * m + ((hi << 11) | (lo >> 53));
+    int64_t idx = (int64_t)(K / (uint64_t)N);
+    return idx >= M ? M - 1 : idx;
+}
+
 // ---------------------------------------------------------------------------
 // Sources: draw order is position (3 draws per rejection attempt), energy, direction.
 __device__ __forceinline__ bool mat_fissile(const World &W, const ProblemDev &P, int mat)

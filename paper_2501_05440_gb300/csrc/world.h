@@ -32,7 +32,9 @@ enum { FILTER_CELL = 0, FILTER_LATTICE = 1, FILTER_MATERIAL = 2 };
 enum { B_NONE = 0, B_ROOT = 1, B_LATX = 2, B_LATY = 3, B_UNIV = 4 };
 // history fates
 enum { FATE_ALIVE = -1, FATE_ABSORBED = 0, FATE_LEAKED = 1, FATE_CUT = 2, FATE_LOST = 3,
-       FATE_CAPPED = 4, FATE_TIME = 5 };
+       FATE_CAPPED = 4, FATE_TIME = 5,
+       // domain decomposition: left this rank's slab / never in it this cycle
+       FATE_MOVED = 6, FATE_ELSEWHERE = 7 };
 // error flags raised by kernels
 enum { ERR_BANK_OVERFLOW = 1, ERR_SOURCE = 2, ERR_QUEUE = 4, ERR_ITER = 8 };
 
@@ -136,6 +138,7 @@ struct Particles {
     double *x, *y, *z, *u, *v, *w, *E, *t;
     double *iu, *iv, *iw;   // direction reciprocals
     double *kt, *kc;      // per-history k estimator sums (track length, collision)
+    double *drem;         // domain decomposition: rest of a cut flight's collision distance
     uint64_t *s;
     int *g, *cell, *ix, *iy, *ucell, *mat, *uk, *prob, *root, *nfis, *ncoll, *ncross, *bwhich;
     signed char *bkind, *fate;
@@ -148,6 +151,13 @@ struct Bank {
     int64_t cap;
 };
 
+// The slab a rank owns in a spatially decomposed run: lo <= coordinate `axis`
+// (0 x, 1 y, 2 z) < hi; the outermost slabs reach to -inf and +inf.
+struct DomainCut {
+    int axis;
+    double lo, hi;
+};
+
 // One fission-bank site as exchanged between the ranks of a sharded run (the
 // layout of the C ABI's mcgb_site: 64 bytes).
 struct ShardSite {
@@ -156,6 +166,16 @@ struct ShardSite {
     int64_t parent;
 };
 static_assert(sizeof(ShardSite) == 64, "site records are 64 bytes");
+
+// A particle handed between the ranks of a spatially decomposed run (the
+// layout of the C ABI's mcgb_flight: 128 bytes).
+struct FlightRec {
+    double x, y, z, u, v, w, E, drem;
+    uint64_t s;
+    int64_t hist;
+    int32_t g, cell, ix, iy, ucell, mat, prob, root, nfis, ncoll, ncross, dest;
+};
+static_assert(sizeof(FlightRec) == 128, "flight records are 128 bytes");
 
 // Per-run device counters and accumulators.
 struct RunBufs {
