@@ -215,6 +215,24 @@ int mcgb_run_eigenvalue(mcgb_ctx *ctx, int64_t n, int inactive, int active, uint
 int mcgb_eigen_begin(mcgb_ctx *ctx, int64_t n, int inactive, int active, uint64_t seed);
 int mcgb_eigen_cycles(mcgb_ctx *ctx, int n_cycles);
 int mcgb_eigen_finish(mcgb_ctx *ctx);
+/* Checkpoint and restart of a power iteration (no counterpart in the paper).
+ * Between cycles of a run begun with mcgb_eigen_begin -- at least one cycle
+ * run and at least one left -- mcgb_eigen_checkpoint writes into the host
+ * buffer buf[0..cap) all that the remaining cycles and the final statistics
+ * depend on: the run's sizes and seed, a fingerprint of the uploaded problem,
+ * the cycle index, the per-cycle k sums, bank sizes and times so far, the
+ * tally sums and sums of squares, the event counters, and the next cycle's
+ * n sources as 64-byte mcgb_site records; a checksum ends it.  *needed = its
+ * size (buf NULL: size query only; cap too small: MCGB_E_INVALID_ARG).  The
+ * run goes on unchanged.
+ * mcgb_eigen_restore begins the run again from such a record, on a context
+ * holding the same problem (any mode or launch options; another fingerprint,
+ * a bad checksum or a truncated record: MCGB_E_INVALID_ARG): the remaining
+ * mcgb_eigen_cycles and mcgb_eigen_finish then give the results of the
+ * uninterrupted run bit for bit, since every history's random stream depends
+ * only on the seed, the cycle and its source index. */
+int mcgb_eigen_checkpoint(mcgb_ctx *ctx, void *buf, size_t cap, size_t *needed);
+int mcgb_eigen_restore(mcgb_ctx *ctx, const void *buf, size_t size);
 /* Device time of each cycle (CUDA events on the context's stream): the
  * transport phase and the whole cycle, in ms. */
 int mcgb_get_cycle_times(mcgb_ctx *ctx, int n_cycles, double *transport_ms, double *cycle_ms);

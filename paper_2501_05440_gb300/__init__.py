@@ -132,6 +132,7 @@ def lib():
                 "mcgb_run_fixed_source": [P, i64, i32, u64],
                 "mcgb_eigen_begin": [P, i64, i32, i32, u64], "mcgb_eigen_cycles": [P, i32],
                 "mcgb_eigen_finish": [P], "mcgb_get_cycle_times": [P, i32, P, P],
+                "mcgb_eigen_checkpoint": [P, P, sz, P], "mcgb_eigen_restore": [P, P, sz],
                 "mcgb_get_event_timing": [P, P, P, P, P],
                 "mcgb_get_k": [P, P], "mcgb_get_cycle_k": [P, i32, P, P, P],
                 "mcgb_tally_size": [P, i32, P, P, P], "mcgb_get_tally": [P, i32, P, P, sz, P],
@@ -375,6 +376,19 @@ class Context:
 
     def eigen_finish(self):
         _chk(self.L.mcgb_eigen_finish(self.h))
+
+    def eigen_checkpoint(self):
+        """The state of the power iteration between two cycles, as bytes."""
+        need = C.c_size_t()
+        _chk(self.L.mcgb_eigen_checkpoint(self.h, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value)
+        _chk(self.L.mcgb_eigen_checkpoint(self.h, buf, need.value, C.byref(need)))
+        return buf.raw
+
+    def eigen_restore(self, blob):
+        """Begin the power iteration again from eigen_checkpoint()'s bytes."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        _chk(self.L.mcgb_eigen_restore(self.h, buf, len(blob)))
 
     def get_cycle_times(self, n):
         a, b = np.zeros(n), np.zeros(n)

@@ -106,6 +106,7 @@ struct EigenRun {            // a power iteration in progress
     int64_t N = 0;
     int inactive = 0, active = 0, ncyc = 0, cyc = 0, cur = 0;
     uint64_t seed = 0;
+    uint64_t seed_arg = 0;   // as given to mcgb_eigen_begin (checkpoints)
 };
 
 struct RunState {
@@ -542,6 +543,7 @@ static int eigen_begin(mcgb_ctx *c, int64_t N, int inactive, int active, uint64_
     e.cyc = 0;
     e.cur = 0;
     e.seed = c->world->probs[0].seed;
+    e.seed_arg = seed;
     // device copies for graph replay: the resampling draw of every cycle, bank sizes
     drop_cycle_graphs(c);
     c->gmem.release();
@@ -1306,6 +1308,157 @@ int mcgb_eigen_finish(mcgb_ctx *ctx)
     if (!ctx) return fail(MCGB_E_INVALID_ARG, "null context");
     CK(cudaSetDevice(ctx->device));
     return eigen_finish(ctx);
+}
+
+// ---- checkpoint and restart of a power iteration ---------------------------
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    uint64_t fingerprint, seed;
+    int64_t N, launches;
+    int32_t inactive, active, cyc, acc;
+    mcgb_counters counters;
+    unsigned long long cnt[8];
+};
+const char CKPT_MAGIC[8] = {'M', 'C', 'G', 'B', 'E', 'I', 'G', '1'};
+
+// header | k sums [2 cyc] | bank sizes [cyc] | cycle and transport times [cyc] each |
+// tally sums, sums of squares [acc] each | next cycle's sources [N] | checksum
+size_t ckpt_size(int64_t cyc, int64_t acc, int64_t N)
+{
+    return sizeof(CkptHeader) + (size_t)cyc * (2 * sizeof(double) + sizeof(int64_t) + 2 * sizeof(double)) +
+           (size_t)acc * 2 * sizeof(double) + (size_t)N * sizeof(ShardSite) + sizeof(uint64_t);
+}
+
+uint64_t ckpt_checksum(const unsigned char *p, size_t n)   // FNV-1a over 8-byte words, then the tail
+{
+    uint64_t h = 14695981039346656037ULL;
+    const size_t nw = n / 8;
+    for (size_t k = 0; k < nw; k++) {
+        uint64_t w;
+        std::memcpy(&w, p + 8 * k, 8);
+        h = (h ^ w) * 1099511628211ULL;
+    }
+    for (size_t k = 8 * nw; k < n; k++) h = (h ^ (uint64_t)p[k]) * 1099511628211ULL;
+    return h;
+}
+
+}  // namespace
+
+int mcgb_eigen_checkpoint(mcgb_ctx *c, void *buf, size_t cap, size_t *needed)
+{
+    if (!c || !needed) return fail(MCGB_E_INVALID_ARG, "null argument");
+    EigenRun &e = c->eig;
+    if (!e.on) return fail(MCGB_E_STATE, "no eigenvalue run in progress");
+    if (e.cyc < 1 || e.cyc >= e.ncyc) return fail(MCGB_E_STATE, "a checkpoint is taken between two cycles");
+    const int acc = std::max(c->world->W.acc_size, 0);
+    const int cyc = e.cyc;
+    const size_t size = ckpt_size(cyc, acc, e.N);
+    *needed = size;
+    if (!buf) return MCGB_OK;
+    if (cap < size) return fail(MCGB_E_INVALID_ARG, "output capacity too small");
+    CK(cudaSetDevice(c->device));
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, CKPT_MAGIC, 8);
+    h.fingerprint = c->world->fingerprint;
+    h.seed = e.seed_arg;
+    h.N = e.N;
+    h.launches = c->launches;
+    h.inactive = e.inactive;
+    h.active = e.active;
+    h.cyc = cyc;
+    h.acc = acc;
+    h.counters = c->counters;
+    unsigned char *p = static_cast<unsigned char *>(buf);
+    unsigned char *q = p + sizeof h;
+    CK(cudaMemcpyAsync(h.cnt, r.cnt, sizeof h.cnt, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(q, r.kout, sizeof(double) * 2 * cyc, cudaMemcpyDeviceToHost, st));
+    q += sizeof(double) * 2 * cyc;
+    std::memcpy(q, c->cyc_m.data(), sizeof(int64_t) * cyc);
+    q += sizeof(int64_t) * cyc;
+    std::memcpy(q, c->cyc_ms.data(), sizeof(double) * cyc);
+    q += sizeof(double) * cyc;
+    std::memcpy(q, c->cyc_tms.data(), sizeof(double) * cyc);
+    q += sizeof(double) * cyc;
+    CK(cudaMemcpyAsync(q, r.tsum, sizeof(double) * acc, cudaMemcpyDeviceToHost, st));
+    q += sizeof(double) * acc;
+    CK(cudaMemcpyAsync(q, r.tsum2, sizeof(double) * acc, cudaMemcpyDeviceToHost, st));
+    q += sizeof(double) * acc;
+    // the next cycle's sources, in source order: bank sites through the resampled indices
+    DevAlloc tmp;
+    ShardSite *src = nullptr;
+    CKR(tmp.get(src, e.N));
+    launch_pack_sites(r.bank[e.cur], r.src_idx, e.N, 0, src, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(q, src, sizeof(ShardSite) * e.N, cudaMemcpyDeviceToHost, st));
+    q += sizeof(ShardSite) * e.N;
+    CK(cudaStreamSynchronize(st));
+    std::memcpy(p, &h, sizeof h);
+    const uint64_t sum = ckpt_checksum(p, size - sizeof(uint64_t));
+    std::memcpy(q, &sum, sizeof sum);
+    return MCGB_OK;
+}
+
+int mcgb_eigen_restore(mcgb_ctx *c, const void *buf, size_t size)
+{
+    if (!c || !buf) return fail(MCGB_E_INVALID_ARG, "null argument");
+    if (size < sizeof(CkptHeader) + sizeof(uint64_t)) return fail(MCGB_E_INVALID_ARG, "truncated checkpoint");
+    const unsigned char *p = static_cast<const unsigned char *>(buf);
+    CkptHeader h;
+    std::memcpy(&h, p, sizeof h);
+    if (std::memcmp(h.magic, CKPT_MAGIC, 8) != 0) return fail(MCGB_E_INVALID_ARG, "not a checkpoint");
+    if (h.N <= 0 || h.N > (int64_t)1 << 30 || h.inactive < 0 || h.active < 1 ||
+        h.inactive + h.active > 4096 || h.cyc < 1 || h.cyc >= h.inactive + h.active || h.acc < 0 ||
+        h.acc > (1 << 30))
+        return fail(MCGB_E_INVALID_ARG, "bad checkpoint header");
+    const size_t want = ckpt_size(h.cyc, h.acc, h.N);
+    if (size != want) return fail(MCGB_E_INVALID_ARG, "truncated checkpoint");
+    uint64_t sum;
+    std::memcpy(&sum, p + want - sizeof sum, sizeof sum);
+    if (ckpt_checksum(p, want - sizeof sum) != sum) return fail(MCGB_E_INVALID_ARG, "checkpoint checksum mismatch");
+    CK(cudaSetDevice(c->device));
+    CKR(eigen_begin(c, h.N, h.inactive, h.active, h.seed));
+    EigenRun &e = c->eig;
+    if (c->world->fingerprint != h.fingerprint || c->world->W.acc_size != h.acc) {
+        e.on = false;
+        return fail(MCGB_E_INVALID_ARG, "the checkpoint is of another problem");
+    }
+    RunState &r = c->rs;
+    cudaStream_t st = c->stream;
+    const int cyc = h.cyc, acc = h.acc;
+    const unsigned char *q = p + sizeof h;
+    CK(cudaMemcpyAsync(r.cnt, h.cnt, sizeof h.cnt, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(r.kout, q, sizeof(double) * 2 * cyc, cudaMemcpyHostToDevice, st));
+    q += sizeof(double) * 2 * cyc;
+    std::memcpy(c->cyc_m.data(), q, sizeof(int64_t) * cyc);
+    q += sizeof(int64_t) * cyc;
+    std::memcpy(c->cyc_ms.data(), q, sizeof(double) * cyc);
+    q += sizeof(double) * cyc;
+    std::memcpy(c->cyc_tms.data(), q, sizeof(double) * cyc);
+    q += sizeof(double) * cyc;
+    CK(cudaMemcpyAsync(r.tsum, q, sizeof(double) * acc, cudaMemcpyHostToDevice, st));
+    q += sizeof(double) * acc;
+    CK(cudaMemcpyAsync(r.tsum2, q, sizeof(double) * acc, cudaMemcpyHostToDevice, st));
+    q += sizeof(double) * acc;
+    DevAlloc tmp;
+    ShardSite *src = nullptr;
+    CKR(tmp.get(src, h.N));
+    CK(cudaMemcpyAsync(src, q, sizeof(ShardSite) * h.N, cudaMemcpyHostToDevice, st));
+    e.cur = cyc & 1;
+    launch_sites_to_bank(src, h.N, r.bank[e.cur], st);
+    CK(cudaGetLastError());
+    std::vector<int> iota(h.N);
+    for (int64_t k = 0; k < h.N; k++) iota[k] = (int)k;
+    CK(cudaMemcpyAsync(r.src_idx, iota.data(), sizeof(int) * h.N, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    e.cyc = cyc;
+    c->counters = h.counters;
+    c->launches = h.launches + 1;
+    return MCGB_OK;
 }
 
 int mcgb_get_cycle_times(mcgb_ctx *ctx, int n_cycles, double *transport_ms, double *cycle_ms)

@@ -677,6 +677,17 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return std::string("upload(world): ") + cudaGetErrorString(e);
     dw.bytes = S.buf.size();
+    // FNV-1a (64-bit) over 8-byte words, then the tail bytes
+    uint64_t fp = 14695981039346656037ULL;
+    const size_t nw = S.buf.size() / 8;
+    for (size_t k = 0; k < nw; k++) {
+        uint64_t w;
+        std::memcpy(&w, S.buf.data() + 8 * k, 8);
+        fp = (fp ^ w) * 1099511628211ULL;
+    }
+    for (size_t k = 8 * nw; k < S.buf.size(); k++)
+        fp = (fp ^ (uint64_t)(unsigned char)S.buf[k]) * 1099511628211ULL;
+    dw.fingerprint = fp;
     char *b = (char *)dw.arena;
     World &W = dw.W;
     W.nprob = (int)probs.size();

@@ -82,6 +82,7 @@ struct DeviceWorld {
     std::vector<int> tally_first;       // global tally id of each problem's first tally
     std::vector<int> t_off, t_nbins, t_ne, t_batches, t_ntb;  // host copies per global tally
     int acc_size = 0, nrep = 1;
+    uint64_t fingerprint = 0;           // FNV-1a of the uploaded bytes (checkpoints)
     ~DeviceWorld();
 };
 

@@ -82,6 +82,7 @@ void launch_pack_sites(const Bank &B, const int *perm, int64_t M, int64_t j0, Sh
                        cudaStream_t st);
 void launch_unpack_sources(const ShardSite *bank, int64_t M, int64_t N, int64_t j0, int64_t n,
                            double xi, const Bank &Bs, cudaStream_t st);
+void launch_sites_to_bank(const ShardSite *in, int64_t n, const Bank &Bs, cudaStream_t st);
 void launch_shard_stats(const double *sums, int acc_size, double N, int cyc, int active,
                         double *kout, double *tsum, double *tsum2, cudaStream_t st);
 // spatial domain decomposition (kernels_domain.cu)

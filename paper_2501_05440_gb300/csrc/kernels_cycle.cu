@@ -473,6 +473,33 @@ void launch_unpack_sources(const ShardSite *bank, int64_t M, int64_t N, int64_t 
         k_unpack_sources<<<(int)((n + 255) / 256), 256, 0, st>>>(bank, M, N, j0, n, xi, Bs);
 }
 
+// Birth sites k = 0 .. n-1 from records in source order (a restored checkpoint:
+// source j of the cycle is born at site j).
+__global__ void k_sites_to_bank(const ShardSite *in, int64_t n, Bank Bs)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const ShardSite &s = in[k];
+    Bs.x[k] = s.x;
+    Bs.y[k] = s.y;
+    Bs.z[k] = s.z;
+    Bs.t[k] = s.t;
+    Bs.cell[k] = s.cell;
+    Bs.ix[k] = s.ix;
+    Bs.iy[k] = s.iy;
+    Bs.ucell[k] = s.ucell;
+    Bs.mat[k] = s.mat;
+    Bs.parent[k] = (int)k;
+    Bs.child[k] = 0;
+    Bs.root[k] = (int)k;
+    Bs.prob[k] = 0;
+}
+
+void launch_sites_to_bank(const ShardSite *in, int64_t n, const Bank &Bs, cudaStream_t st)
+{
+    if (n > 0) k_sites_to_bank<<<(int)((n + 255) / 256), 256, 0, st>>>(in, n, Bs);
+}
+
 // Statistics of one cycle from the all-rank sums [k_tl, k_c, tally...]: the k
 // sums go to kout[2 cyc ..]; in an active cycle each tally batch value
 // v = sum / N is added to tsum and v^2 to tsum2 (as k_tally_cycle does).
