@@ -178,7 +178,7 @@ int mcgb_set_source(mcgb_ctx *ctx, int kind, const double *params, int accept, i
 int mcgb_add_tally(mcgb_ctx *ctx, int filter, int n_edges, const double *edges, int *id);
 /* End each history at its max_collisions-th collision (0 = no limit). */
 int mcgb_set_max_collisions(mcgb_ctx *ctx, int max_collisions);
-/* Time dependence (Sec. 1 "fully dynamic simulations"; Sec. 4 runs its
+/* Time dependence (Sec. 1: time-dependent transport; Sec. 4 runs its
  * continuous-energy pin cell as a time-dependent fixed-source problem).  Source
  * particles start at time t0 (s); a flight ends where the particle's clock
  * reaches t_cut, at the distance (t_cut - t) / (1/v) when that is shorter than

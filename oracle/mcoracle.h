@@ -76,7 +76,7 @@ int orc_set_source(orc_ctx *c, int kind, const double *params, int accept, int e
 int orc_add_tally(orc_ctx *c, int filter, int n_edges, const double *edges);
 int orc_set_max_collisions(orc_ctx *c, int max_collisions);
 
-/* Time dependence (Sec. 1 "fully dynamic simulations"; Sec. 4 runs its pin cell
+/* Time dependence (Sec. 1: time-dependent transport; Sec. 4 runs its pin cell
  * in time-dependent fixed-source mode).  Source particles start at t0; a flight
  * is cut where the particle's clock reaches t_cut (fate 5).  Multigroup speeds
  * are given as 1/v per group (s/cm); continuous energy uses v = K sqrt(E),

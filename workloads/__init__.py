@@ -508,7 +508,7 @@ def infinite_medium_fixed(material, pdf, seed=9, n=20_000, half=1.0, batches=20)
 
 
 # ----------------------------------------------------------------------------
-# time-dependent fixed source (Sec. 1 "fully dynamic simulations"; Sec. 4 runs
+# time-dependent fixed source (Sec. 1: time-dependent transport; Sec. 4 runs
 # its continuous-energy pin cell in this mode)
 # ----------------------------------------------------------------------------
 def time_pulse_mg(material, pdf, inv_v, t_cut, t_edges, seed=11, n=20_000, batches=20,
