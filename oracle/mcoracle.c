@@ -202,16 +202,43 @@ static void azimuth(uint64_t *s, double *cphi, double *sphi, int strict)
 {
     double a, b, r2;
     if (!disk_point(s, &a, &b, &r2, strict)) { *cphi = 1.0; *sphi = 0.0; return; }
-    *cphi = (strict ? fma(a, a, -(b * b)) : a * a - b * b) / r2;
+    if (strict) {           /* one reciprocal, rounded once, for both */
+        double inv = 1.0 / r2;
+        *cphi = fma(a, a, -(b * b)) * inv;
+        *sphi = 2.0 * a * b * inv;
+        return;
+    }
+    *cphi = (a * a - b * b) / r2;
     *sphi = 2.0 * a * b / r2;
 }
 
 /* Rotate direction (u,v,w) by polar cosine mu about itself, azimuth sampled
- * (textbook rotation, polar axis z, or x when |w| is near 1).                 */
+ * (textbook rotation, polar axis z, or x when |w| is near 1).  Strict: each
+ * product that is added to another term is fused into that addition.        */
 static void rotate(double mu, uint64_t *s, double *u, double *v, double *w, int strict)
 {
     double cphi, sphi;
     azimuth(s, &cphi, &sphi, strict);
+    if (strict) {
+        double st2 = fma(-mu, mu, 1.0);
+        double st = sqrt(st2 > 0.0 ? st2 : 0.0);
+        double u0 = *u, v0 = *v, w0 = *w;
+        double ww = fma(-w0, w0, 1.0);
+        if (ww > 1.0e-10) {
+            double q = sqrt(ww);
+            double f = st / q;
+            *u = fma(mu, u0, f * fma(u0 * w0, cphi, -(v0 * sphi)));
+            *v = fma(mu, v0, f * fma(v0 * w0, cphi, u0 * sphi));
+            *w = fma(mu, w0, -(st * q * cphi));
+        } else {
+            double q = sqrt(fma(-u0, u0, 1.0));
+            double f = st / q;
+            *v = fma(mu, v0, f * fma(v0 * u0, cphi, -(w0 * sphi)));
+            *w = fma(mu, w0, f * fma(w0 * u0, cphi, v0 * sphi));
+            *u = fma(mu, u0, -(st * q * cphi));
+        }
+        return;
+    }
     double st2 = 1.0 - mu * mu;
     double st = sqrt(st2 > 0.0 ? st2 : 0.0);
     double u0 = *u, v0 = *v, w0 = *w;
@@ -234,16 +261,25 @@ static void rotate(double mu, uint64_t *s, double *u, double *v, double *w, int 
 
 /* Elastic scattering off a target at rest (textbook two-body kinematics):
  * mu_cm = 2 xi - 1, q = A^2 + 2 A mu_cm + 1, E' = E q / (A+1)^2,
- * mu_lab = (1 + A mu_cm) / sqrt(q).
+ * mu_lab = (1 + A mu_cm) / sqrt(q).  Strict: q = (2A) mu_cm + (A^2 + 1) with
+ * A^2 + 1 rounded once and the product fused, E' = (E q) (1/(A+1)^2) with the
+ * reciprocal rounded once, mu_lab's numerator fused.
  * Reading: E' is floored at 1e-5 eV (the paper's data start there).           */
 #define E_MIN 1.0e-5
 #define E_MAX 2.0e7
 static double elastic(double E, double A, uint64_t *s, double *u, double *v, double *w, int strict)
 {
     double mucm = 2.0 * draw(s) - 1.0;
-    double q = A * A + 2.0 * A * mucm + 1.0;
-    double Ep = E * q / ((A + 1.0) * (A + 1.0));
-    double mul = (1.0 + A * mucm) / sqrt(q);
+    double q, Ep, mul;
+    if (strict) {
+        q = fma(2.0 * A, mucm, fma(A, A, 1.0));
+        Ep = E * q * (1.0 / ((A + 1.0) * (A + 1.0)));
+        mul = fma(A, mucm, 1.0) / sqrt(q);
+    } else {
+        q = A * A + 2.0 * A * mucm + 1.0;
+        Ep = E * q / ((A + 1.0) * (A + 1.0));
+        mul = (1.0 + A * mucm) / sqrt(q);
+    }
     if (mul > 1.0) mul = 1.0;
     if (mul < -1.0) mul = -1.0;
     rotate(mul, s, u, v, w, strict);
@@ -1116,7 +1152,10 @@ int orc_probe(orc_ctx *c, const double pos[3], const double dir[3], int out_path
  * f = (E - E_j) / (E_{j+1} - E_j), sigma = sigma_j + f (sigma_{j+1} - sigma_j).
  * Macroscopic values are N_i sigma_i summed in the material's nuclide order;
  * sigma_t,i = (sigma_s + sigma_c) + sigma_f.  Strict: the interval's
- * reciprocal width is rounded once, f = (E - E_j) (1/(E_{j+1} - E_j)).       */
+ * reciprocal width is rounded once, f = (E - E_j) (1/(E_{j+1} - E_j)), and
+ * for a reaction (fused) the product is fused into the addition,
+ * sigma = fma(f, sigma_{j+1} - sigma_j, sigma_j); the tables of the strict
+ * macroscopic lookup take the unfused form.                                 */
 typedef struct {
     double sigt, nusf;
     double st[16], ss[16], sf[16];
@@ -1133,7 +1172,7 @@ static int nuc_interval(const Nuclide *u, double E)
     return lo;
 }
 
-static void ce_lookup(const orc_ctx *c, int mat, double E, CEXS *x)
+static void ce_lookup(const orc_ctx *c, int mat, double E, CEXS *x, int fused)
 {
     const MatCE *m = &c->mce[mat];
     x->sigt = 0.0;
@@ -1143,9 +1182,16 @@ static void ce_lookup(const orc_ctx *c, int mat, double E, CEXS *x)
         int j = nuc_interval(u, E);
         double f = c->strict ? (E - u->E[j]) * (1.0 / (u->E[j + 1] - u->E[j]))
                              : (E - u->E[j]) / (u->E[j + 1] - u->E[j]);
-        double ss = u->s[j] + f * (u->s[j + 1] - u->s[j]);
-        double sc = u->c[j] + f * (u->c[j + 1] - u->c[j]);
-        double sf = u->f[j] + f * (u->f[j + 1] - u->f[j]);
+        double ss, sc, sf;
+        if (fused) {
+            ss = fma(f, u->s[j + 1] - u->s[j], u->s[j]);
+            sc = fma(f, u->c[j + 1] - u->c[j], u->c[j]);
+            sf = fma(f, u->f[j + 1] - u->f[j], u->f[j]);
+        } else {
+            ss = u->s[j] + f * (u->s[j + 1] - u->s[j]);
+            sc = u->c[j] + f * (u->c[j + 1] - u->c[j]);
+            sf = u->f[j] + f * (u->f[j + 1] - u->f[j]);
+        }
         double st = ss + sc + sf;
         x->st[k] = st; x->ss[k] = ss; x->sf[k] = sf;
         x->sigt = x->sigt + m->dens[k] * st;
@@ -1159,7 +1205,7 @@ static void ce_lookup(const orc_ctx *c, int mat, double E, CEXS *x)
  * Sigma_t = sum_i N_i sigma_t,i and nuSigma_f are linear there too; they are
  * tabulated at the union points (each per-nuclide value as in ce_lookup,
  * summed in the material's order) and interpolated,
- * Sigma(E) = S_k + ((E - E_k) (1 / (E_k+1 - E_k))) (S_k+1 - S_k), with k the
+ * Sigma(E) = fma((E - E_k) (1 / (E_k+1 - E_k)), S_k+1 - S_k, S_k), with k the
  * largest union index <= n - 2 whose point is <= E (0 if none).  Equal to the
  * per-nuclide sum in exact arithmetic (and exactly at the union points); the
  * plain mode sums the nuclides at the particle's energy instead.            */
@@ -1196,7 +1242,7 @@ static void build_macro(orc_ctx *c)
         M->Sf = malloc(sizeof(double) * (size_t)(n ? n : 1));
         for (int k = 0; k < n; k++) {
             CEXS x;
-            ce_lookup(c, m, E[k], &x);
+            ce_lookup(c, m, E[k], &x, 0);
             M->St[k] = x.sigt;
             M->Sf[k] = x.nusf;
         }
@@ -1214,8 +1260,8 @@ static void macro_xs(const orc_ctx *c, int mat, double E, double *sigt, double *
     }
     if (M->n < 2) { *sigt = M->St[0]; *nusf = M->Sf[0]; return; }
     double f = (E - M->E[lo]) * (1.0 / (M->E[lo + 1] - M->E[lo]));
-    *sigt = M->St[lo] + f * (M->St[lo + 1] - M->St[lo]);
-    *nusf = M->Sf[lo] + f * (M->Sf[lo + 1] - M->Sf[lo]);
+    *sigt = fma(f, M->St[lo + 1] - M->St[lo], M->St[lo]);
+    *nusf = fma(f, M->Sf[lo + 1] - M->Sf[lo], M->Sf[lo]);
 }
 
 /* flight cross sections Sigma_t, nuSigma_f of a CE material in the context's mode */
@@ -1226,7 +1272,7 @@ static void flight_xs(const orc_ctx *c, int mat, double E, double *sigt, double 
         return;
     }
     CEXS x;
-    ce_lookup(c, mat, E, &x);
+    ce_lookup(c, mat, E, &x, 0);
     *sigt = x.sigt;
     *nusf = x.nusf;
 }
@@ -1235,7 +1281,7 @@ int orc_ce_lookup(orc_ctx *c, int material, double E, double out[4])
 {
     if (c->ce != 1 || material < 0 || material >= c->nmc) return fail(c, ORC_EINVAL, "bad material");
     CEXS x;
-    ce_lookup(c, material, E, &x);
+    ce_lookup(c, material, E, &x, c->strict);
     if (c->strict && !c->macro) build_macro(c);
     flight_xs(c, material, E, &out[0], &out[1]);
     double ss = 0.0, sf = 0.0;
@@ -1480,14 +1526,14 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
             }
         } else {
             const MatCE *mc = &c->mce[p->mat];
-            ce_lookup(c, p->mat, p->E, &x);     /* per-nuclide values for the reaction */
+            ce_lookup(c, p->mat, p->E, &x, strict);   /* per-nuclide values for the reaction */
             a->kc += nusf / sigt;
             /* nuclide by xi Sigma_t against the running sum of N_i sigma_t,i */
             double target = draw(&p->s) * sigt;
             double cum = 0.0;
             int sel = mc->n - 1;
             for (int k = 0; k < mc->n; k++) {
-                cum = cum + mc->dens[k] * x.st[k];
+                cum = strict ? fma(mc->dens[k], x.st[k], cum) : cum + mc->dens[k] * x.st[k];
                 if (target <= cum) { sel = k; break; }
             }
             const Nuclide *u = &c->nuc[mc->nuc[sel]];

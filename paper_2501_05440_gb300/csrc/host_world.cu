@@ -171,7 +171,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     std::vector<double> g_sigt, g_mfp, g_nusf, g_mu, g_mufl, g_mufr, g_ps, g_stot, g_chicdf;
     std::vector<double> gg_sigs, gg_scdf;
     std::vector<const NucDef *> nucs;
-    std::vector<double> n_A, n_nu;
+    std::vector<double> n_A, n_nu, n_kin;
     std::vector<int> mc_off, mc_n, mc_nuc, mc_fissile;
     std::vector<double> mc_dens, src_cdf;
     std::vector<int> t_filter, t_nbins, t_ne, t_off, t_eoff, t_nedges, t_batches, t_ntb, t_toff;
@@ -282,6 +282,9 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
                 nucs.push_back(&u);
                 n_A.push_back(u.A);
                 n_nu.push_back(u.nu);
+                // elastic kinematics: A, 2A, A^2 + 1 (one rounding), 1 / (A + 1)^2
+                const double A1 = u.A + 1.0, A1sq = A1 * A1;
+                n_kin.insert(n_kin.end(), {u.A, 2.0 * u.A, std::fma(u.A, u.A, 1.0), 1.0 / A1sq});
             }
             for (auto &m : pd.mce) {
                 mc_off.push_back((int)mc_nuc.size());
@@ -657,7 +660,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
            o_cmkoff = S.put(cm_koff), o_cmklo = S.put(cm_klo), o_cmkey0 = S.put(cm_key0),
            o_cmE = S.put(cm_E), o_cmrec = S.put(cm_rec);
     size_t o_Eu = S.put(Eu), o_umap = S.put(umap), o_nivoff = S.put(n_ivoff), o_niv = S.put(n_iv),
-           o_nA = S.put(n_A), o_nnu = S.put(n_nu);
+           o_nA = S.put(n_A), o_nnu = S.put(n_nu), o_nkin = S.put(n_kin);
     size_t o_mcoff = S.put(mc_off), o_mcn = S.put(mc_n), o_mcnuc = S.put(mc_nuc),
            o_mcfis = S.put(mc_fissile), o_mcdens = S.put(mc_dens);
     size_t o_srccdf = S.put(src_cdf), o_logtab = S.put(logtab), o_rinv = S.put(rinvtab),
@@ -716,7 +719,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(cm_koff, int, o_cmkoff); P_(cm_klo, int, o_cmklo); P_(cm_key0, long long, o_cmkey0);
     P_(cm_E, double, o_cmE); P_(cm_rec, double, o_cmrec);
     P_(Eu, double, o_Eu); P_(umap, int, o_umap); P_(n_ivoff, int, o_nivoff); P_(n_iv, double, o_niv);
-    P_(n_A, double, o_nA); P_(n_nu, double, o_nnu);
+    P_(n_A, double, o_nA); P_(n_nu, double, o_nnu); P_(n_kin, double, o_nkin);
     P_(mc_off, int, o_mcoff); P_(mc_n, int, o_mcn); P_(mc_nuc, int, o_mcnuc);
     P_(mc_fissile, int, o_mcfis); P_(mc_dens, double, o_mcdens);
     P_(src_cdf, double, o_srccdf); P_(logtab, double, o_logtab); P_(rinvtab, double, o_rinv);

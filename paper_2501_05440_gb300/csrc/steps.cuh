@@ -174,8 +174,8 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         uk = union_index(W, p.E);   // per-nuclide values for the reaction
         kc = kc + nusf / sigt;
         int off = __ldg(W.mc_off + p.mat), n = __ldg(W.mc_n + p.mat);
-        // nuclide: first whose running sum of N_i sigma_t,i reaches xi Sigma_t (the
-        // selected nuclide's values are recomputed with the lookup's arithmetic)
+        // nuclide: first whose running sum of N_i sigma_t,i (each term fused into
+        // the sum) reaches xi Sigma_t
         double target = draw(p.s) * sigt;
         double cum = 0.0;
         int sel = n - 1;
@@ -183,7 +183,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         for (int q = 0; q < n; q++) {
             double a, b, c;
             ce_micro(W, __ldg(W.mc_nuc + off + q), uk, p.E, a, b, c);
-            cum = cum + __ldg(W.mc_dens + off + q) * a;
+            cum = fma(__ldg(W.mc_dens + off + q), a, cum);
             st = a;
             ss = b;
             sf = c;
@@ -203,7 +203,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             if (is_pos(P.fg_kT) && lt_mag(p.E, P.fg_emax))
                 p.E = free_gas(W, p.E, __ldg(W.n_A + nuc), P.fg_kT, p.s, p.u, p.v, p.w);
             else
-                p.E = elastic(p.E, __ldg(W.n_A + nuc), p.s, p.u, p.v, p.w);
+                p.E = elastic(p.E, W.n_kin + 4 * nuc, p.s, p.u, p.v, p.w);
             set_recip(W, p);
         } else {
             p.fate = FATE_ABSORBED;

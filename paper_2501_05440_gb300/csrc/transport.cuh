@@ -180,8 +180,9 @@ __device__ __forceinline__ void azimuth(uint64_t &s, double &cphi, double &sphi)
         sphi = 0.0;
         return;
     }
-    cphi = fma(a, a, -(b * b)) / r2;
-    sphi = 2.0 * a * b / r2;
+    const double inv = __drcp_rn(r2);   // correctly rounded 1 / r2
+    cphi = fma(a, a, -(b * b)) * inv;
+    sphi = 2.0 * a * b * inv;
 }
 
 // Rotate (u,v,w) by polar cosine mu with a sampled azimuth (polar axis z, or x near |w| = 1).
@@ -189,34 +190,38 @@ __device__ __forceinline__ void rotate(double mu, uint64_t &s, double &u, double
 {
     double cphi, sphi;
     azimuth(s, cphi, sphi);
-    double st2 = 1.0 - mu * mu;
+    double st2 = fma(-mu, mu, 1.0);
     double st = sqrt(is_pos(st2) ? st2 : 0.0);
     double u0 = u, v0 = v, w0 = w;
-    double ww = 1.0 - w0 * w0;
+    double ww = fma(-w0, w0, 1.0);
     if (ww > 1.0e-10) {
         double q = sqrt(ww);
         double f = st / q;
-        u = mu * u0 + f * (u0 * w0 * cphi - v0 * sphi);
-        v = mu * v0 + f * (v0 * w0 * cphi + u0 * sphi);
-        w = mu * w0 - st * q * cphi;
+        u = fma(mu, u0, f * fma(u0 * w0, cphi, -(v0 * sphi)));
+        v = fma(mu, v0, f * fma(v0 * w0, cphi, u0 * sphi));
+        w = fma(mu, w0, -(st * q * cphi));
     } else {
-        double uu = 1.0 - u0 * u0;
+        double uu = fma(-u0, u0, 1.0);
         double q = sqrt(uu);
         double f = st / q;
-        v = mu * v0 + f * (v0 * u0 * cphi - w0 * sphi);
-        w = mu * w0 + f * (w0 * u0 * cphi + v0 * sphi);
-        u = mu * u0 - st * q * cphi;
+        v = fma(mu, v0, f * fma(v0 * u0, cphi, -(w0 * sphi)));
+        w = fma(mu, w0, f * fma(w0 * u0, cphi, v0 * sphi));
+        u = fma(mu, u0, -(st * q * cphi));
     }
 }
 
-// Elastic scattering off a target at rest; energy floored at E_MIN.
-__device__ __forceinline__ double elastic(double E, double A, uint64_t &s, double &u, double &v,
-                                          double &w)
+// Elastic scattering off a target at rest; energy floored at E_MIN.  kin holds
+// the nuclide's constants {A, 2A, A^2 + 1 (one rounding), 1 / (A + 1)^2}:
+// q = 2A mu_cm + (A^2 + 1), E' = (E q) / (A + 1)^2, mu_lab = (A mu_cm + 1) / sqrt(q).
+__device__ __forceinline__ double elastic(double E, const double *kin, uint64_t &s, double &u,
+                                          double &v, double &w)
 {
+    const double2 k01 = __ldg(reinterpret_cast<const double2 *>(kin));
+    const double2 k23 = __ldg(reinterpret_cast<const double2 *>(kin) + 1);
     double mucm = draw_sym(s);
-    double q = A * A + 2.0 * A * mucm + 1.0;
-    double Ep = E * q / ((A + 1.0) * (A + 1.0));
-    double mul = (1.0 + A * mucm) / sqrt(q);
+    double q = fma(k01.y, mucm, k23.x);
+    double Ep = E * q * k23.y;
+    double mul = fma(k01.x, mucm, 1.0) / sqrt(q);
     if (mul > 1.0) mul = 1.0;
     if (mul < -1.0) mul = -1.0;
     rotate(mul, s, u, v, w);
@@ -723,9 +728,9 @@ __device__ __forceinline__ void ce_micro(const World &W, int nuc, int k, double 
         reinterpret_cast<const double2 *>(W.n_iv + 8 * ((int64_t)__ldg(W.n_ivoff + nuc) + j));
     double2 e_inv = __ldg(iv), s = __ldg(iv + 1), c = __ldg(iv + 2), f = __ldg(iv + 3);
     double fr = (E - e_inv.x) * e_inv.y;
-    ss = s.x + fr * s.y;
-    double sc = c.x + fr * c.y;
-    sf = f.x + fr * f.y;
+    ss = fma(fr, s.y, s.x);
+    double sc = fma(fr, c.y, c.x);
+    sf = fma(fr, f.y, f.x);
     st = ss + sc + sf;
 }
 
@@ -754,8 +759,8 @@ __device__ __forceinline__ void ce_macro(const World &W, int mat, double E, doub
     const double2 *r = reinterpret_cast<const double2 *>(W.cm_rec + 6 * ((int64_t)off + lo));
     double2 e_inv = __ldg(r), t = __ldg(r + 1), f = __ldg(r + 2);
     double fr = (E - e_inv.x) * e_inv.y;
-    sigt = t.x + fr * t.y;
-    nusf = f.x + fr * f.y;
+    sigt = fma(fr, t.y, t.x);
+    nusf = fma(fr, f.y, f.x);
 }
 
 // ---------------------------------------------------------------------------
