@@ -91,7 +91,8 @@ static double draw(uint64_t *s) { return (double)draw_n(s) * 0x1p-53; }
  * CUDA library evaluates it: xi = 2^(e-53) m with m in [1, 2); c = 1 + j/256
  * from the top 8 bits of m's fraction; r = (m - c) (1/c);
  * ln xi = (e - 53) ln 2 + ln c + log1p(r), log1p by its Taylor polynomial to
- * r^6 evaluated by Horner's rule with fused multiply-adds.  The table holds
+ * r^6 evaluated by Horner's rule with fused multiply-adds, its last product
+ * fused into the addition of ln c.  The table holds
  * ln c correctly rounded (computed here in extended precision and rounded
  * once) and 1/c rounded once.                                                 */
 static double TANG_LN[256], TANG_RECIP[256];
@@ -130,7 +131,7 @@ static double tang_log(uint64_t n)
     h = fma(h, r, 1.0 / 3.0);
     h = fma(h, r, -0.5);
     h = fma(h, r, 1.0);
-    return (double)(e - 53) * LN2_D + (TANG_LN[j] + h * r);
+    return (double)(e - 53) * LN2_D + fma(h, r, TANG_LN[j]);
 }
 
 double orc_log(double xi)
@@ -885,7 +886,7 @@ static double surf_dist(const Surface *s, int sense, double x, double y, double 
         if (strict) {
             a = fma(u, u, v * v);
             b = fma(dx, u, dy * v);
-            cc = fma(dx, dx, dy * dy) - s->r2;
+            cc = fma(dx, dx, fma(dy, dy, -s->r2));
         } else {
             a = u * u + v * v;
             b = dx * u + dy * v;
@@ -896,7 +897,7 @@ static double surf_dist(const Surface *s, int sense, double x, double y, double 
         if (strict) {
             a = fma(u, u, fma(v, v, w * w));
             b = fma(dx, u, fma(dy, v, dz * w));
-            cc = fma(dx, dx, fma(dy, dy, dz * dz)) - s->r2;
+            cc = fma(dx, dx, fma(dy, dy, fma(dz, dz, -s->r2)));
         } else {
             a = u * u + v * v + w * w;
             b = dx * u + dy * v + dz * w;

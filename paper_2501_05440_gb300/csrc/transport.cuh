@@ -102,14 +102,29 @@ __device__ __forceinline__ double n_to_sym(uint64_t n)
     return __longlong_as_double((long long)bits);
 }
 
+// 2 (2 xi - 1) = (2n - 2^53) 2^-52 exactly (no FP64 instruction).
+__device__ __forceinline__ double n_to_sym2(uint64_t n)
+{
+    long long k = (long long)(2 * n) - (1LL << 53);
+    if (k == 0) return 0.0;
+    uint64_t a = k < 0 ? (uint64_t)(-k) : (uint64_t)k;
+    int lz = __clzll((long long)a);
+    uint64_t frac = ((a << lz) << 1) >> 12;
+    uint64_t bits = ((uint64_t)(1023 - 52 + 63 - lz) << 52) | frac;
+    if (k < 0) bits |= 0x8000000000000000ULL;
+    return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ double draw(uint64_t &s) { return n_to_xi(draw_n(s)); }
 __device__ __forceinline__ double draw_sym(uint64_t &s) { return n_to_sym(draw_n(s)); }
+__device__ __forceinline__ double draw_sym2(uint64_t &s) { return n_to_sym2(draw_n(s)); }
 
 // ---------------------------------------------------------------------------
 // ln xi for xi = n 2^-53: table-driven (Tang, ACM TOMS 1990).  n = 2^e m,
 // m in [1,2); c = 1 + j/256 from the top 8 fraction bits; r = (m - c)(1/c);
 // ln xi = (e - 53) ln 2 + ln c + r(1 + r(-1/2 + r(1/3 + r(-1/4 + r(1/5 - r/6))))),
-// the polynomial by Horner's rule with fused multiply-adds.
+// the polynomial by Horner's rule with fused multiply-adds, its last product
+// fused into the addition of ln c.
 // Tables (built on the host): ln c by the series 2 atanh((c-1)/(c+1)), 1/c,
 // and (e - 53) ln 2 rounded once.
 __device__ __forceinline__ double log_n(const World &W, uint64_t n)
@@ -133,33 +148,36 @@ __device__ __forceinline__ double log_n(const World &W, uint64_t n)
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
     q = fma(q, r, 1.0);
-    double p = q * r;
-    return __ldg(W.etab + e) + (__ldg(W.logtab + j) + p);
+    return __ldg(W.etab + e) + fma(q, r, __ldg(W.logtab + j));
 }
 
 // ---------------------------------------------------------------------------
-// Isotropic direction by Marsaglia's disk rejection (no trigonometry).
+// Isotropic direction by Marsaglia's disk rejection (no trigonometry): (a, b)
+// uniform in the unit disk, S = a^2 + b^2 < 1, Omega = (2a sqrt(1 - S),
+// 2b sqrt(1 - S), 1 - 2S).  Computed from 2a, 2b and 4S, which are exact
+// scalings: the doublings fold into the draws and the fused constants, and
+// every value is the one of the formula as written (S = fma(a, a, b b)).
 __device__ __forceinline__ void iso_dir(uint64_t &s, double &u, double &v, double &w)
 {
     // the loop repeats only the rejection test; the accepted point is used once
-    double a, b, S;
+    double a2, b2, S4;
     int k = 0;
     do {
-        a = draw_sym(s);
-        b = draw_sym(s);
-        S = fma(a, a, b * b);
+        a2 = draw_sym2(s);
+        b2 = draw_sym2(s);
+        S4 = fma(a2, a2, b2 * b2);
         k++;
-    } while (!lt_mag(S, 1.0) && k < 64);
-    if (!lt_mag(S, 1.0)) {
+    } while (!lt_mag(S4, 4.0) && k < 64);
+    if (!lt_mag(S4, 4.0)) {
         u = 0.0;
         v = 0.0;
         w = 1.0;
         return;
     }
-    double t = 2.0 * sqrt(1.0 - S);
-    u = a * t;
-    v = b * t;
-    w = 1.0 - 2.0 * S;
+    double t = sqrt(fma(-0.25, S4, 1.0));
+    u = a2 * t;
+    v = b2 * t;
+    w = fma(-0.5, S4, 1.0);
 }
 
 // Azimuth as (cos, sin) of the doubled angle of a point uniform in the unit disk.
@@ -435,12 +453,12 @@ __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, 
         }
         a = fma(u, u, v * v);
         b = fma(dx, u, dy * v);
-        cc = fma(dx, dx, dy * dy) - __ldg(W.s_r2 + sid);
+        cc = fma(dx, dx, fma(dy, dy, -__ldg(W.s_r2 + sid)));
     } else {
         double dx = x - __ldg(c), dy = y - __ldg(c + 1), dz = z - __ldg(c + 2);
         a = fma(u, u, fma(v, v, w * w));
         b = fma(dx, u, fma(dy, v, dz * w));
-        cc = fma(dx, dx, fma(dy, dy, dz * dz)) - __ldg(W.s_r2 + sid);
+        cc = fma(dx, dx, fma(dy, dy, fma(dz, dz, -__ldg(W.s_r2 + sid))));
     }
     if (!is_pos(a)) return MCGB_INF;
     double disc = fma(b, b, -(a * cc));
