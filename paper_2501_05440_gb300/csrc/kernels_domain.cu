@@ -148,10 +148,12 @@ __global__ void __launch_bounds__(256) k_dom_sweep(World W, Particles P, Bank Bd
         int ev;
         for (;;) {
             int kind, which, uk = 0;
+            double xt = 0.0, xn = 0.0;
             ev = step_advance<false, false, CE, true>(W, Pd, p, j, R, rep, kind, which, uk, kt,
-                                                      nullptr, &dom, &drem);
+                                                      nullptr, &dom, &drem, &xt, &xn);
             if (ev == EV_CROSS) ev = step_cross(W, p, kind, which);
-            else if (ev == EV_COLLIDE) ev = step_collide<false, false, CE>(W, Pd, p, j, Bdst, R, uk, kc);
+            else if (ev == EV_COLLIDE)
+                ev = step_collide<false, false, CE>(W, Pd, p, j, Bdst, R, uk, kc, nullptr, true, xt, xn);
             if (ev == EV_DEAD || ev == EV_EXPORT) break;
         }
         if (ev == EV_EXPORT) {

@@ -230,7 +230,9 @@ __global__ void __launch_bounds__(256, 3) k_segment(World W, Particles P, Bank B
             const ProblemDev &Pd = W.prob[p.prob];
             int kind, which, uk = 0;
             double kt = P.kt[i];
-            int ev = step_advance<false, true, CE>(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
+            double xt = 0.0, xn = 0.0;
+            int ev = step_advance<false, true, CE>(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt,
+                                                   nullptr, nullptr, nullptr, &xt, &xn);
             P.kt[i] = kt;
             if (ev == EV_CROSS) {
                 ev = step_cross(W, p, kind, which);
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256, 3) k_segment(World W, Particles P, Bank B
                 P.mat[i] = p.mat;
             } else if (ev == EV_COLLIDE) {
                 double kc = P.kc[i];
-                ev = step_collide<false, true, CE>(W, Pd, p, i, Bdst, R, uk, kc);
+                ev = step_collide<false, true, CE>(W, Pd, p, i, Bdst, R, uk, kc, nullptr, true, xt, xn);
                 P.kc[i] = kc;
                 P.ncoll[i] = p.ncoll;
                 P.nfis[i] = p.nfis;
@@ -399,9 +401,12 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
         if (__all_sync(0xffffffffu, done)) break;
         if (alive) {
             int kind, which, uk = 0;
-            int ev = step_advance<false, TIME, CE>(W, *Pd, p, slot, R, rep, kind, which, uk, kt);
+            double xt = 0.0, xn = 0.0;
+            int ev = step_advance<false, TIME, CE>(W, *Pd, p, slot, R, rep, kind, which, uk, kt, nullptr,
+                                                   nullptr, nullptr, &xt, &xn);
             if (ev == EV_CROSS) ev = step_cross(W, p, kind, which);
-            else if (ev == EV_COLLIDE) ev = step_collide<false, TIME, CE>(W, *Pd, p, slot, Bdst, R, uk, kc);
+            else if (ev == EV_COLLIDE)
+                ev = step_collide<false, TIME, CE>(W, *Pd, p, slot, Bdst, R, uk, kc, nullptr, true, xt, xn);
             if (ev == EV_DEAD) {
                 alive = false;
                 write_dead(P, slot, p, kt, kc);

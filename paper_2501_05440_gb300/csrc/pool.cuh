@@ -29,14 +29,20 @@ constexpr int SLOT_EMPTY = -2;
 
 struct Pool {
     double *x, *y, *z, *u, *v, *w, *E, *kt, *kc, *iu, *iv, *iw, *t;
+    double *sg, *nf;   // continuous energy: the last flight's Sigma_t, nuSigma_f
     unsigned long long *s;
     int *g, *cell, *ix, *iy, *ucell, *mat, *prob, *root, *nfis, *ncoll, *ncross, *gslot, *bwhich,
         *uk, *fate, *ev;
     int *list;
 };
 
-__host__ __device__ constexpr size_t pool_bytes(int P) { return (size_t)P * (14 * 8 + 17 * 4); }
+// bytes of a pool of P particles (two more doubles per particle with CE)
+__host__ __device__ constexpr size_t pool_bytes(int P, bool CE)
+{
+    return (size_t)P * ((CE ? 16 : 14) * 8 + 17 * 4);
+}
 
+template <bool CE>
 __device__ __forceinline__ Pool carve(unsigned char *base, int P)
 {
     Pool q;
@@ -46,7 +52,9 @@ __device__ __forceinline__ Pool carve(unsigned char *base, int P)
     q.iu = d + 9 * P; q.iv = d + 10 * P; q.iw = d + 11 * P;
     q.s = reinterpret_cast<unsigned long long *>(d + 12 * P);
     q.t = d + 13 * P;
-    int *i = reinterpret_cast<int *>(d + 14 * P);
+    q.sg = CE ? d + 14 * P : nullptr;
+    q.nf = CE ? d + 15 * P : nullptr;
+    int *i = reinterpret_cast<int *>(d + (CE ? 16 : 14) * P);
     q.g = i; q.cell = i + P; q.ix = i + 2 * P; q.iy = i + 3 * P; q.ucell = i + 4 * P;
     q.mat = i + 5 * P; q.prob = i + 6 * P; q.root = i + 7 * P; q.nfis = i + 8 * P;
     q.ncoll = i + 9 * P; q.ncross = i + 10 * P; q.gslot = i + 11 * P; q.bwhich = i + 12 * P;
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int hist[2 * (NBUCKET + 1)], cnt[NBUCKET + 1];
     __shared__ int s_base, s_take, s_exhausted;
-    const Pool q = carve(smem, P);
+    const Pool q = carve<CE>(smem, P);
     int hb = 0;
     for (int k = threadIdx.x; k < 2 * (NBUCKET + 1); k += T) hist[k] = 0;
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
@@ -259,10 +267,13 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
                 double kt = q.kt[i], kc = q.kc[i];
                 for (;;) {
                     int kind, which, uk = 0;
-                    int ev = step_advance<false, TIME, CE>(W, Pd, p, slot, R, rep, kind, which, uk, kt);
+                    double xt = 0.0, xn = 0.0;
+                    int ev = step_advance<false, TIME, CE>(W, Pd, p, slot, R, rep, kind, which, uk, kt,
+                                                           nullptr, nullptr, nullptr, &xt, &xn);
                     if (ev == EV_CROSS) ev = step_cross(W, p, kind, which);
                     else if (ev == EV_COLLIDE)
-                        ev = step_collide<false, TIME, CE>(W, Pd, p, slot, Bdst, R, uk, kc);
+                        ev = step_collide<false, TIME, CE>(W, Pd, p, slot, Bdst, R, uk, kc, nullptr,
+                                                           true, xt, xn);
                     if (ev == EV_DEAD) break;
                 }
                 q.kt[i] = kt;
@@ -277,8 +288,13 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
             pool_load<TIME>(q, i, p);
             int kind, which, uk = 0;
             double kt = q.kt[i];
+            double xt = 0.0, xn = 0.0;
             int ev = step_advance<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which,
-                                                uk, kt);
+                                                uk, kt, nullptr, nullptr, nullptr, &xt, &xn);
+            if (CE) {
+                q.sg[i] = xt;
+                q.nf[i] = xn;
+            }
             q.x[i] = p.x;
             q.y[i] = p.y;
             q.z[i] = p.z;
@@ -313,7 +329,8 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
                 ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
             } else {
                 double kc = q.kc[i];
-                ev = step_collide<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
+                ev = step_collide<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc,
+                                                   nullptr, CE, CE ? q.sg[i] : 0.0, CE ? q.nf[i] : 0.0);
                 q.kc[i] = kc;
             }
             pool_store<TIME>(q, i, p);
@@ -355,7 +372,7 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Pool q = carve(smem + (size_t)warp * pool_bytes(PW), PW);
+    const Pool q = carve<CE>(smem + (size_t)warp * pool_bytes(PW, CE), PW);
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
     const int gen = a.gen_dev ? *a.gen_dev : a.gen;
     const int rep = (int)((blockIdx.x * (WPOOL_T / 32) + warp) % (unsigned)W.nrep);
@@ -415,8 +432,13 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
             pool_load<TIME>(q, i, p);
             int kind, which, uk = 0;
             double kt = q.kt[i];
+            double xt = 0.0, xn = 0.0;
             int ev = step_advance<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], R, rep, kind, which,
-                                                uk, kt);
+                                                uk, kt, nullptr, nullptr, nullptr, &xt, &xn);
+            if (CE) {
+                q.sg[i] = xt;
+                q.nf[i] = xn;
+            }
             q.x[i] = p.x;
             q.y[i] = p.y;
             q.z[i] = p.z;
@@ -452,7 +474,8 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
             PS p;
             pool_load<TIME>(q, i, p);
             double kc = q.kc[i];
-            int ev = step_collide<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc);
+            int ev = step_collide<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc,
+                                                   nullptr, CE, CE ? q.sg[i] : 0.0, CE ? q.nf[i] : 0.0);
             q.kc[i] = kc;
             q.ev[i] = EV_ADVANCE;
             pool_store<TIME>(q, i, p);
@@ -466,7 +489,7 @@ template <int PW, bool TIME, bool CE>
 void launch_wpool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                     const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
 {
-    size_t sm = pool_bytes(PW) * (WPOOL_T / 32);
+    size_t sm = pool_bytes(PW, CE) * (WPOOL_T / 32);
     cudaFuncSetAttribute(k_wpool<PW, TIME, CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_wpool<PW, TIME, CE><<<grid, WPOOL_T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
 }
@@ -474,7 +497,7 @@ void launch_wpool_t(const World &W, const Particles &G, const Bank &Bsrc, const 
 template <int PW, bool CE> int wpool_occupancy()
 {
     int n = 0;
-    size_t sm = pool_bytes(PW) * (WPOOL_T / 32);
+    size_t sm = pool_bytes(PW, CE) * (WPOOL_T / 32);
     cudaFuncSetAttribute(k_wpool<PW, false, CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wpool<PW, false, CE>, WPOOL_T, sm);
     return n;
@@ -484,7 +507,7 @@ template <int P, int T, bool TIME, bool CE>
 void launch_pool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                    const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
 {
-    size_t sm = pool_bytes(P);
+    size_t sm = pool_bytes(P, CE);
     cudaFuncSetAttribute(k_pool<P, T, TIME, CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_pool<P, T, TIME, CE><<<grid, T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
 }
@@ -492,7 +515,7 @@ void launch_pool_t(const World &W, const Particles &G, const Bank &Bsrc, const B
 template <int P, int T, bool CE> int pool_occupancy()
 {
     int n = 0;
-    size_t sm = pool_bytes(P);
+    size_t sm = pool_bytes(P, CE);
     cudaFuncSetAttribute(k_pool<P, T, false, CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<P, T, false, CE>, T, sm);
     return n;

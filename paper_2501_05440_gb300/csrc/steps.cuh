@@ -25,11 +25,14 @@ __device__ __forceinline__ int tally_batch(const ProblemDev &P, const PS &p)
 // DOM: the flight also stops where it leaves the slab *dom (EV_EXPORT), and
 // *drem carries the rest of the sampled collision distance to the next flight
 // (which then takes no draw; *drem < 0: sample as usual).
+// xs_t, xs_nf (continuous energy): receive the flight's Sigma_t and nuSigma_f,
+// which a collision at the flight's end can take instead of looking them up again.
 template <bool REPLAY = false, bool TIME = true, bool CE = true, bool DOM = false>
 __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const RunBufs &R, int rep, int &kind, int &which,
                                             int &uk, double &kt, double *d_out = nullptr,
-                                            const DomainCut *dom = nullptr, double *drem = nullptr)
+                                            const DomainCut *dom = nullptr, double *drem = nullptr,
+                                            double *xs_t = nullptr, double *xs_nf = nullptr)
 {
     if (p.ncoll + p.ncross >= MAX_EVENTS) {
         p.fate = FATE_CAPPED;
@@ -39,6 +42,10 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     if (CE && P.ce) {
         ce_macro(W, p.mat, p.E, sigt, nusf);
         mfp = is_pos(sigt) ? __drcp_rn(sigt) : MCGB_INF;   // correctly rounded 1 / sigt
+        if (xs_t) {
+            *xs_t = sigt;
+            *xs_nf = nusf;
+        }
     } else {
         int go = __ldg(W.m_goff + p.mat) + p.g;
         sigt = __ldg(W.g_sigt + go);
@@ -139,10 +146,13 @@ __device__ __forceinline__ int step_cross(const World &W, PS &p, int kind, int w
 // sigma_t of that nuclide, scatter (elastic, target at rest) when
 // xi sigma_t <= sigma_s.
 // REPLAY (multigroup only): same draws, no bank; *nf_out = sites banked.
+// xs_given (continuous energy): xs_t, xs_nf are the Sigma_t, nuSigma_f of the
+// flight that ended here (same material and energy), not looked up again.
 template <bool REPLAY = false, bool TIME = true, bool CE = true>
 __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const Bank &B, const RunBufs &R, int uk, double &kc,
-                                            int *nf_out = nullptr)
+                                            int *nf_out = nullptr, bool xs_given = false,
+                                            double xs_t = 0.0, double xs_nf = 0.0)
 {
     p.ncoll++;
     if (!CE || !P.ce) {
@@ -170,7 +180,12 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         }
     } else {
         double sigt, nusf;
-        ce_macro(W, p.mat, p.E, sigt, nusf);
+        if (xs_given) {
+            sigt = xs_t;
+            nusf = xs_nf;
+        } else {
+            ce_macro(W, p.mat, p.E, sigt, nusf);
+        }
         uk = union_index(W, p.E);   // per-nuclide values for the reaction
         kc = kc + nusf / sigt;
         int off = __ldg(W.mc_off + p.mat), n = __ldg(W.mc_n + p.mat);
