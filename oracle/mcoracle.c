@@ -1528,7 +1528,8 @@ static void transport(const orc_ctx *c, Particle *p, Acc *a, int batch, Grad *gr
         } else {
             const MatCE *mc = &c->mce[p->mat];
             ce_lookup(c, p->mat, p->E, &x, strict);   /* per-nuclide values for the reaction */
-            a->kc += nusf / sigt;
+            /* strict: nuSigma_f times the flight's reciprocal 1/Sigma_t, rounded once */
+            a->kc += strict ? nusf * (1.0 / sigt) : nusf / sigt;
             /* nuclide by xi Sigma_t against the running sum of N_i sigma_t,i */
             double target = draw(&p->s) * sigt;
             double cum = 0.0;

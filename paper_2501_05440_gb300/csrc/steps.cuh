@@ -25,8 +25,9 @@ __device__ __forceinline__ int tally_batch(const ProblemDev &P, const PS &p)
 // DOM: the flight also stops where it leaves the slab *dom (EV_EXPORT), and
 // *drem carries the rest of the sampled collision distance to the next flight
 // (which then takes no draw; *drem < 0: sample as usual).
-// xs_t, xs_nf (continuous energy): receive the flight's Sigma_t and nuSigma_f,
-// which a collision at the flight's end can take instead of looking them up again.
+// xs_t, xs_nf (continuous energy): receive the flight's Sigma_t and its
+// collision estimate of k, nuSigma_f (1/Sigma_t), which a collision at the
+// flight's end takes instead of looking them up again.
 template <bool REPLAY = false, bool TIME = true, bool CE = true, bool DOM = false>
 __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const RunBufs &R, int rep, int &kind, int &which,
@@ -44,7 +45,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
         mfp = is_pos(sigt) ? __drcp_rn(sigt) : MCGB_INF;   // correctly rounded 1 / sigt
         if (xs_t) {
             *xs_t = sigt;
-            *xs_nf = nusf;
+            *xs_nf = nusf * mfp;
         }
     } else {
         int go = __ldg(W.m_goff + p.mat) + p.g;
@@ -146,8 +147,8 @@ __device__ __forceinline__ int step_cross(const World &W, PS &p, int kind, int w
 // sigma_t of that nuclide, scatter (elastic, target at rest) when
 // xi sigma_t <= sigma_s.
 // REPLAY (multigroup only): same draws, no bank; *nf_out = sites banked.
-// xs_given (continuous energy): xs_t, xs_nf are the Sigma_t, nuSigma_f of the
-// flight that ended here (same material and energy), not looked up again.
+// xs_given (continuous energy): xs_t, xs_nf are Sigma_t and nuSigma_f (1/Sigma_t)
+// of the flight that ended here (same material and energy), not looked up again.
 template <bool REPLAY = false, bool TIME = true, bool CE = true>
 __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P, PS &p, int slot,
                                             const Bank &B, const RunBufs &R, int uk, double &kc,
@@ -179,15 +180,17 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             return EV_DEAD;
         }
     } else {
-        double sigt, nusf;
+        double sigt, kterm;   // k_c scores nuSigma_f / Sigma_t as nuSigma_f (1/Sigma_t)
         if (xs_given) {
             sigt = xs_t;
-            nusf = xs_nf;
+            kterm = xs_nf;
         } else {
+            double nusf;
             ce_macro(W, p.mat, p.E, sigt, nusf);
+            kterm = nusf * __drcp_rn(sigt);
         }
         uk = union_index(W, p.E);   // per-nuclide values for the reaction
-        kc = kc + nusf / sigt;
+        kc = kc + kterm;
         int off = __ldg(W.mc_off + p.mat), n = __ldg(W.mc_n + p.mat);
         // nuclide: first whose running sum of N_i sigma_t,i (each term fused into
         // the sum) reaches xi Sigma_t
