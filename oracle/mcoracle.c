@@ -344,7 +344,10 @@ static double free_gas(double E, double A, double kT, uint64_t *s, double *u, do
                        double *w, int strict)
 {
     const double SQRT_PI = 1.7724538509055160273;
-    double y = sqrt(A * E / kT);
+    /* strict: y^2 = (A E)(1/kT), products fused into the additions that
+     * follow them, E' = |v'|^2 (kT (1/A)) (= E |v'|^2 / y^2) */
+    double y2 = strict ? A * E * (1.0 / kT) : A * E / kT;
+    double y = sqrt(y2);
     double py = y * SQRT_PI;
     double x = 0.0, mu = 1.0, r = y;
     for (int k = 0; k < MAX_TRIES; k++) {
@@ -353,7 +356,7 @@ static double free_gas(double E, double A, double kT, uint64_t *s, double *u, do
             double L1 = ln_xi(draw_n(s), strict);
             double L2 = ln_xi(draw_n(s), strict);
             double c2 = disk_cos2(s, strict);
-            x2 = -(L1 + L2 * c2);
+            x2 = strict ? -fma(L2, c2, L1) : -(L1 + L2 * c2);
         } else {
             double L1 = ln_xi(draw_n(s), strict);
             double L2 = ln_xi(draw_n(s), strict);
@@ -361,24 +364,36 @@ static double free_gas(double E, double A, double kT, uint64_t *s, double *u, do
         }
         x = sqrt(x2);
         mu = 2.0 * draw(s) - 1.0;
-        double r2 = x2 + y * y - 2.0 * x * y * mu;
+        double r2 = strict ? fma(-(2.0 * x * y), mu, x2 + y2) : x2 + y * y - 2.0 * x * y * mu;
         r = sqrt(r2 > 0.0 ? r2 : 0.0);
         if (draw(s) * (x + y) <= r) break;
     }
     double tu = *u, tv = *v, tw = *w;
     rotate(mu, s, &tu, &tv, &tw, strict);
     double inv = 1.0 / (A + 1.0);
-    double Vx = (y * *u + A * x * tu) * inv;
-    double Vy = (y * *v + A * x * tv) * inv;
-    double Vz = (y * *w + A * x * tw) * inv;
+    double Vx, Vy, Vz, px, py2, pz, p2;
     double cu, cv, cw;
-    iso_dir(s, &cu, &cv, &cw, strict);
-    double wc = A * r * inv;
-    double px = Vx + wc * cu, py2 = Vy + wc * cv, pz = Vz + wc * cw;
-    double p2 = px * px + py2 * py2 + pz * pz;
+    if (strict) {
+        double Ax = A * x;
+        Vx = fma(y, *u, Ax * tu) * inv;
+        Vy = fma(y, *v, Ax * tv) * inv;
+        Vz = fma(y, *w, Ax * tw) * inv;
+        iso_dir(s, &cu, &cv, &cw, strict);
+        double wc = A * r * inv;
+        px = fma(wc, cu, Vx); py2 = fma(wc, cv, Vy); pz = fma(wc, cw, Vz);
+        p2 = fma(px, px, fma(py2, py2, pz * pz));
+    } else {
+        Vx = (y * *u + A * x * tu) * inv;
+        Vy = (y * *v + A * x * tv) * inv;
+        Vz = (y * *w + A * x * tw) * inv;
+        iso_dir(s, &cu, &cv, &cw, strict);
+        double wc = A * r * inv;
+        px = Vx + wc * cu; py2 = Vy + wc * cv; pz = Vz + wc * cw;
+        p2 = px * px + py2 * py2 + pz * pz;
+    }
     double ip = 1.0 / sqrt(p2);
     *u = px * ip; *v = py2 * ip; *w = pz * ip;
-    double Ep = E * (p2 / (y * y));
+    double Ep = strict ? p2 * (kT * (1.0 / A)) : E * (p2 / (y * y));
     return Ep < E_MIN ? E_MIN : Ep;
 }
 

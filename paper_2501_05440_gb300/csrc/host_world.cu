@@ -282,9 +282,10 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
                 nucs.push_back(&u);
                 n_A.push_back(u.A);
                 n_nu.push_back(u.nu);
-                // elastic kinematics: A, 2A, A^2 + 1 (one rounding), 1 / (A + 1)^2
+                // kinematics: A, 2A, A^2 + 1 (one rounding), 1/(A + 1)^2, 1/(A + 1), 1/A
                 const double A1 = u.A + 1.0, A1sq = A1 * A1;
-                n_kin.insert(n_kin.end(), {u.A, 2.0 * u.A, std::fma(u.A, u.A, 1.0), 1.0 / A1sq});
+                n_kin.insert(n_kin.end(), {u.A, 2.0 * u.A, std::fma(u.A, u.A, 1.0), 1.0 / A1sq,
+                                           1.0 / A1, 1.0 / u.A});
             }
             for (auto &m : pd.mce) {
                 mc_off.push_back((int)mc_nuc.size());
@@ -349,6 +350,7 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
         P.max_coll = pd.max_coll;
         P.fg_kT = pd.fg_kT;
         P.fg_emax = (pd.fg_cut > 0.0 ? pd.fg_cut : 400.0) * pd.fg_kT;
+        P.fg_ikT = pd.fg_kT > 0.0 ? 1.0 / pd.fg_kT : 0.0;
         P.time_on = pd.time_on ? 1 : 0;
         P.t0 = pd.t0;
         P.tcut = pd.tcut;

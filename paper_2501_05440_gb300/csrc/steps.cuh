@@ -219,9 +219,9 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         xi = draw(p.s);
         if (!lt_mag(ss, xi * st)) {
             if (is_pos(P.fg_kT) && lt_mag(p.E, P.fg_emax))
-                p.E = free_gas(W, p.E, __ldg(W.n_A + nuc), P.fg_kT, p.s, p.u, p.v, p.w);
+                p.E = free_gas(W, p.E, W.n_kin + 6 * nuc, P.fg_kT, P.fg_ikT, p.s, p.u, p.v, p.w);
             else
-                p.E = elastic(p.E, W.n_kin + 4 * nuc, p.s, p.u, p.v, p.w);
+                p.E = elastic(p.E, W.n_kin + 6 * nuc, p.s, p.u, p.v, p.w);
             set_recip(W, p);
         } else {
             p.fate = FATE_ABSORBED;

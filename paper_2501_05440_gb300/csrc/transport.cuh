@@ -229,7 +229,7 @@ __device__ __forceinline__ void rotate(double mu, uint64_t &s, double &u, double
 }
 
 // Elastic scattering off a target at rest; energy floored at E_MIN.  kin holds
-// the nuclide's constants {A, 2A, A^2 + 1 (one rounding), 1 / (A + 1)^2}:
+// the nuclide's constants {A, 2A, A^2 + 1 (one rounding), 1 / (A + 1)^2, ...}:
 // q = 2A mu_cm + (A^2 + 1), E' = (E q) / (A + 1)^2, mu_lab = (A mu_cm + 1) / sqrt(q).
 __device__ __forceinline__ double elastic(double E, const double *kin, uint64_t &s, double &u,
                                           double &v, double &w)
@@ -306,12 +306,18 @@ __device__ __forceinline__ double disk_cos2(uint64_t &s)
 // neutron's rotated by mu.  The centre-of-mass velocity V = (y Omega +
 // A x Omega_T) / (A + 1) is kept, the neutron's speed in that frame A r / (A + 1)
 // is kept and its direction there is isotropic; E' = E |v'|^2 / y^2 (floored at
-// 1e-5 eV), Omega' = v' / |v'|.
-__device__ __forceinline__ double free_gas(const World &W, double E, double A, double kT,
-                                           uint64_t &s, double &u, double &v, double &w)
+// 1e-5 eV), Omega' = v' / |v'|.  Rounding: y^2 = (A E)(1/kT); each product
+// that is added to another term is fused into that addition; 1/(A + 1) and
+// 1/A come from the nuclide's constants kin = {A, 2A, A^2 + 1, 1/(A+1)^2,
+// 1/(A+1), 1/A}; E' = |v'|^2 (kT (1/A)), which is E |v'|^2 / y^2.
+__device__ __forceinline__ double free_gas(const World &W, double E, const double *kin, double kT,
+                                           double ikT, uint64_t &s, double &u, double &v, double &w)
 {
     const double SQRT_PI = 1.7724538509055160273;
-    double y = sqrt(A * E / kT);
+    const double A = __ldg(kin);
+    const double2 k45 = __ldg(reinterpret_cast<const double2 *>(kin) + 2);   // 1/(A+1), 1/A
+    const double y2 = A * E * ikT;
+    const double y = sqrt(y2);
     double py = y * SQRT_PI;
     double x = 0.0, mu = 1.0, r = y;
     for (int k = 0; k < MAX_TRIES; k++) {
@@ -320,7 +326,7 @@ __device__ __forceinline__ double free_gas(const World &W, double E, double A, d
             double L1 = log_n(W, draw_n(s));
             double L2 = log_n(W, draw_n(s));
             double c2 = disk_cos2(s);
-            x2 = -(L1 + L2 * c2);
+            x2 = -fma(L2, c2, L1);
         } else {
             double L1 = log_n(W, draw_n(s));
             double L2 = log_n(W, draw_n(s));
@@ -328,26 +334,27 @@ __device__ __forceinline__ double free_gas(const World &W, double E, double A, d
         }
         x = sqrt(x2);
         mu = draw_sym(s);
-        double r2 = x2 + y * y - 2.0 * x * y * mu;
+        double r2 = fma(-(2.0 * x * y), mu, x2 + y2);
         r = sqrt(is_pos(r2) ? r2 : 0.0);
         if (!lt_mag(r, draw(s) * (x + y))) break;
     }
     double tu = u, tv = v, tw = w;
     rotate(mu, s, tu, tv, tw);
-    double inv = 1.0 / (A + 1.0);
-    double Vx = (y * u + A * x * tu) * inv;
-    double Vy = (y * v + A * x * tv) * inv;
-    double Vz = (y * w + A * x * tw) * inv;
+    const double inv = k45.x;
+    const double Ax = A * x;
+    double Vx = fma(y, u, Ax * tu) * inv;
+    double Vy = fma(y, v, Ax * tv) * inv;
+    double Vz = fma(y, w, Ax * tw) * inv;
     double cu, cv, cw;
     iso_dir(s, cu, cv, cw);
     double wc = A * r * inv;
-    double px = Vx + wc * cu, py2 = Vy + wc * cv, pz = Vz + wc * cw;
-    double p2 = px * px + py2 * py2 + pz * pz;
-    double ip = 1.0 / sqrt(p2);
+    double px = fma(wc, cu, Vx), py2 = fma(wc, cv, Vy), pz = fma(wc, cw, Vz);
+    double p2 = fma(px, px, fma(py2, py2, pz * pz));
+    double ip = __drcp_rn(sqrt(p2));   // correctly rounded, the same as 1.0 / sqrt(p2)
     u = px * ip;
     v = py2 * ip;
     w = pz * ip;
-    double Ep = E * (p2 / (y * y));
+    double Ep = p2 * (kT * k45.y);
     return lt_mag(Ep, E_MIN) ? E_MIN : Ep;
 }
 

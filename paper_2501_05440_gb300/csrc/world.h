@@ -60,7 +60,7 @@ struct ProblemDev {
     int invv_off;
     double t0, tcut;
     // free-gas elastic scattering below fg_emax (fg_kT > 0 enables it)
-    double fg_kT, fg_emax;
+    double fg_kT, fg_emax, fg_ikT;   // fg_ikT = 1 / fg_kT, rounded once
 };
 
 struct World {
@@ -111,7 +111,7 @@ struct World {
     const int *n_ivoff;      // first interval of each nuclide
     const double *n_iv;      // 8 doubles per interval: E, 1/dE, s, ds, c, dc, f, df
     const double *n_A, *n_nu;
-    const double *n_kin;      // per nuclide {A, 2A, A^2 + 1, 1 / (A + 1)^2} (elastic kinematics)
+    const double *n_kin;      // per nuclide {A, 2A, A^2 + 1, 1/(A + 1)^2, 1/(A + 1), 1/A} (kinematics)
     const int *mc_off, *mc_n, *mc_nuc, *mc_fissile;
     const double *mc_dens;
     // source group distributions
