@@ -59,12 +59,12 @@ HBM_PEAK_GBS = _hbm_peak()
 #   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum
 #   l2_hit_rate: lts__t_sector_hit_rate; warp_exec_efficiency: active lanes per
 #   issued instruction / 32; fp64_pipe_busy: FP64 pipe cycles / elapsed cycles
-NCU_SOURCES = "5323c8db7307df8c"
-NCU_K_POOL = {"fp64_inst_per_event": 1432863808 / 2.233e7, "dram_bytes_per_launch": 91850752 + 147299840,
-              "l2_hit_rate": 0.9074, "warp_exec_efficiency": 20.42 / 32, "fp64_pipe_busy": 0.5146}
-NCU_K_ADVANCE = {"dram_bytes_per_launch": 124732416 + 25252352, "l2_hit_rate": 0.4967,
-                 "fp64_pipe_busy": 0.7658, "dram_throughput": 0.1608,
-                 "fp64_inst_per_particle": 54000000 / 1e6}
+NCU_SOURCES = "eb9039b82e38efc8"
+NCU_K_POOL = {"fp64_inst_per_event": 1374739648 / 2.233e7, "dram_bytes_per_launch": 90796032 + 151323136,
+              "l2_hit_rate": 0.9076, "warp_exec_efficiency": 20.39 / 32, "fp64_pipe_busy": 0.4951}
+NCU_K_ADVANCE = {"dram_bytes_per_launch": 124694784 + 24608000, "l2_hit_rate": 0.4976,
+                 "fp64_pipe_busy": 0.7513, "dram_throughput": 0.1625,
+                 "fp64_inst_per_particle": 52000000 / 1e6}
 
 
 def ncu_counters(m):
