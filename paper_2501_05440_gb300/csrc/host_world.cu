@@ -644,6 +644,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
            o_szc = S.put(s_zc);
     size_t o_cuniv = S.put(c_univ), o_coff = S.put(c_off), o_cnhs = S.put(c_nhs),
            o_cfillk = S.put(c_fillk), o_cfill = S.put(c_fill);
+    // a half-space index travels in 24 bits of a pooled particle's event word
+    if (hs_surf.size() >= ((size_t)1 << 23)) return "too many half-spaces (at most 8388607)";
     size_t o_hssurf = S.put(hs_surf), o_hssense = S.put(hs_sense), o_hscoff = S.put(hs_coff),
            o_hscand = S.put(hs_cand), o_uoff = S.put(u_off), o_ucells = S.put(u_cells),
            o_uedge = S.put(u_edge), o_cskip = S.put(c_skiproot), o_hsside = S.put(hs_side),

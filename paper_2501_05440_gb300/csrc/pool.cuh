@@ -28,58 +28,77 @@ constexpr int NBUCKET = 33;          // list buckets (flights: 1 + material % 32
 constexpr int SLOT_EMPTY = -2;
 
 struct Pool {
-    double *x, *y, *z, *u, *v, *w, *E, *kt, *kc, *iu, *iv, *iw, *t;
-    double *sg, *nf;   // continuous energy: the last flight's Sigma_t, nuSigma_f
+    double *x, *y, *z, *u, *v, *w, *kt, *kc, *iu, *iv, *iw;
+    double *E, *sg, *nf;   // continuous energy only: energy, the last flight's Sigma_t, nuSigma_f
+    double *t;             // time-dependent only: the clock
     unsigned long long *s;
-    int *g, *cell, *ix, *iy, *ucell, *mat, *prob, *root, *nfis, *ncoll, *ncross, *gslot, *bwhich,
-        *uk, *fate, *ev;
+    int *g, *cell, *ix, *iy, *ucell, *mat, *prob, *root, *nfis, *ncoll, *ncross, *gslot, *fate;
+    int *evw;              // the flight's outcome: event | kind << 4 | (surface + 1) << 8
+    int *uk;               // continuous energy only: union-grid index
     int *list;
 };
 
-// bytes of a pool of P particles (two more doubles per particle with CE)
-__host__ __device__ constexpr size_t pool_bytes(int P, bool CE)
+// Fields per particle: 12 doubles and 15 ints always, 3 doubles and an int
+// more with continuous energy, a double more with time.  A multigroup pool of
+// 256 particles (156 B each) leaves four blocks per SM room for a larger L1.
+__host__ __device__ constexpr size_t pool_bytes(int P, bool TIME, bool CE)
 {
-    return (size_t)P * ((CE ? 16 : 14) * 8 + 17 * 4);
+    return (size_t)P * ((12 + (CE ? 3 : 0) + (TIME ? 1 : 0)) * 8 + (15 + (CE ? 1 : 0)) * 4);
 }
 
-template <bool CE>
+__device__ __forceinline__ int pack_ev(int ev, int kind, int which)
+{
+    return ev | (kind << 4) | ((which + 1) << 8);
+}
+__device__ __forceinline__ int ev_kind(int e) { return (e >> 4) & 15; }
+__device__ __forceinline__ int ev_which(int e) { return (int)((unsigned)e >> 8) - 1; }
+
+template <bool TIME, bool CE>
 __device__ __forceinline__ Pool carve(unsigned char *base, int P)
 {
     Pool q;
     double *d = reinterpret_cast<double *>(base);
-    q.x = d; q.y = d + P; q.z = d + 2 * P; q.u = d + 3 * P; q.v = d + 4 * P; q.w = d + 5 * P;
-    q.E = d + 6 * P; q.kt = d + 7 * P; q.kc = d + 8 * P;
-    q.iu = d + 9 * P; q.iv = d + 10 * P; q.iw = d + 11 * P;
-    q.s = reinterpret_cast<unsigned long long *>(d + 12 * P);
-    q.t = d + 13 * P;
-    q.sg = CE ? d + 14 * P : nullptr;
-    q.nf = CE ? d + 15 * P : nullptr;
-    int *i = reinterpret_cast<int *>(d + (CE ? 16 : 14) * P);
-    q.g = i; q.cell = i + P; q.ix = i + 2 * P; q.iy = i + 3 * P; q.ucell = i + 4 * P;
-    q.mat = i + 5 * P; q.prob = i + 6 * P; q.root = i + 7 * P; q.nfis = i + 8 * P;
-    q.ncoll = i + 9 * P; q.ncross = i + 10 * P; q.gslot = i + 11 * P; q.bwhich = i + 12 * P;
-    q.uk = i + 13 * P; q.fate = i + 14 * P; q.ev = i + 15 * P; q.list = i + 16 * P;
+    int k = 0;
+    auto nd = [&]() { return d + (size_t)(k++) * P; };
+    q.x = nd(); q.y = nd(); q.z = nd(); q.u = nd(); q.v = nd(); q.w = nd();
+    q.kt = nd(); q.kc = nd(); q.iu = nd(); q.iv = nd(); q.iw = nd();
+    q.s = reinterpret_cast<unsigned long long *>(nd());
+    q.E = CE ? nd() : nullptr;
+    q.sg = CE ? nd() : nullptr;
+    q.nf = CE ? nd() : nullptr;
+    q.t = TIME ? nd() : nullptr;
+    int *i = reinterpret_cast<int *>(d + (size_t)k * P);
+    int m = 0;
+    auto ni = [&]() { return i + (size_t)(m++) * P; };
+    q.g = ni(); q.cell = ni(); q.ix = ni(); q.iy = ni(); q.ucell = ni(); q.mat = ni();
+    q.prob = ni(); q.root = ni(); q.nfis = ni(); q.ncoll = ni(); q.ncross = ni();
+    q.gslot = ni(); q.fate = ni(); q.evw = ni();
+    q.uk = CE ? ni() : nullptr;
+    q.list = ni();
     return q;
 }
 
-// TIME = false: the particle clock is neither loaded nor kept
-template <bool TIME>
+// TIME = false: the particle clock is neither loaded nor kept; CE = false: nor the energy
+template <bool TIME, bool CE>
 __device__ __forceinline__ void pool_load(const Pool &q, int i, PS &p)
 {
     p.x = q.x[i]; p.y = q.y[i]; p.z = q.z[i]; p.u = q.u[i]; p.v = q.v[i]; p.w = q.w[i];
     p.iu = q.iu[i]; p.iv = q.iv[i]; p.iw = q.iw[i];
-    p.E = q.E[i]; p.s = q.s[i]; p.t = TIME ? q.t[i] : 0.0;
+    p.E = CE ? q.E[i] : 0.0;
+    p.s = q.s[i];
+    p.t = TIME ? q.t[i] : 0.0;
     p.g = q.g[i]; p.cell = q.cell[i]; p.ix = q.ix[i]; p.iy = q.iy[i]; p.ucell = q.ucell[i];
     p.mat = q.mat[i]; p.prob = q.prob[i]; p.root = q.root[i]; p.nfis = q.nfis[i];
     p.ncoll = q.ncoll[i]; p.ncross = q.ncross[i]; p.fate = q.fate[i];
 }
 
-template <bool TIME>
+template <bool TIME, bool CE>
 __device__ __forceinline__ void pool_store(const Pool &q, int i, const PS &p)
 {
     q.x[i] = p.x; q.y[i] = p.y; q.z[i] = p.z; q.u[i] = p.u; q.v[i] = p.v; q.w[i] = p.w;
     q.iu[i] = p.iu; q.iv[i] = p.iv; q.iw[i] = p.iw;
-    q.E[i] = p.E; q.s[i] = p.s;
+    if (CE) q.E[i] = p.E;
+    q.s[i] = p.s;
     if (TIME) q.t[i] = p.t;
     q.g[i] = p.g; q.cell[i] = p.cell; q.ix[i] = p.ix; q.iy[i] = p.iy; q.ucell[i] = p.ucell;
     q.mat[i] = p.mat; q.prob[i] = p.prob; q.root[i] = p.root; q.nfis[i] = p.nfis;
@@ -197,7 +216,7 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int hist[2 * (NBUCKET + 1)], cnt[NBUCKET + 1];
     __shared__ int s_base, s_take, s_exhausted;
-    const Pool q = carve<CE>(smem, P);
+    const Pool q = carve<TIME, CE>(smem, P);
     int hb = 0;
     for (int k = threadIdx.x; k < 2 * (NBUCKET + 1); k += T) hist[k] = 0;
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
@@ -241,10 +260,10 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
                     p.fate = FATE_LOST;
                     p.cell = 0;
                     p.mat = 0;
-                    pool_store<TIME>(q, i, p);
+                    pool_store<TIME, CE>(q, i, p);
                     retire(q, G, i, p);
                 } else {
-                    pool_store<TIME>(q, i, p);
+                    pool_store<TIME, CE>(q, i, p);
                 }
             }
             __syncthreads();
@@ -261,7 +280,7 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
             if ((int)threadIdx.x < n_adv) {
                 int i = q.list[threadIdx.x];
                 PS p;
-                pool_load<TIME>(q, i, p);
+                pool_load<TIME, CE>(q, i, p);
                 const ProblemDev &Pd = W.prob[p.prob];
                 const int slot = q.gslot[i];
                 double kt = q.kt[i], kc = q.kc[i];
@@ -285,7 +304,7 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
         for (int k = threadIdx.x; k < n_adv; k += T) {
             int i = q.list[k];
             PS p;
-            pool_load<TIME>(q, i, p);
+            pool_load<TIME, CE>(q, i, p);
             int kind, which, uk = 0;
             double kt = q.kt[i];
             double xt = 0.0, xn = 0.0;
@@ -301,9 +320,8 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
             if (TIME) q.t[i] = p.t;
             q.s[i] = p.s;
             q.kt[i] = kt;
-            q.ev[i] = ev | (kind << 4);
-            q.bwhich[i] = which;
-            q.uk[i] = uk;
+            q.evw[i] = pack_ev(ev, kind, which);
+            if (CE) q.uk[i] = uk;
             if (ev == EV_DEAD) {
                 q.fate[i] = p.fate;
                 retire(q, G, i, p);
@@ -314,26 +332,26 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, 
         // collisions grouped by material
         int n_ev = build_list<P, T>(q, hist, hb, cnt, [&](int i) {
             if (q.fate[i] != FATE_ALIVE) return -1;
-            const int e = q.ev[i];
+            const int e = q.evw[i];
             if ((e & 15) != EV_CROSS) return 2 + (q.mat[i] % 31);
-            const int kind = e >> 4;   // lattice steps apart from surface crossings
+            const int kind = ev_kind(e);   // lattice steps apart from surface crossings
             return (kind == B_LATX || kind == B_LATY) ? 0 : 1;
         });
         int n_cross = cnt[0] + cnt[1];
         for (int k = threadIdx.x; k < n_ev; k += T) {
             int i = q.list[k];
             PS p;
-            pool_load<TIME>(q, i, p);
+            pool_load<TIME, CE>(q, i, p);
             int ev;
             if (k < n_cross) {
-                ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
+                ev = step_cross(W, p, ev_kind(q.evw[i]), ev_which(q.evw[i]));
             } else {
                 double kc = q.kc[i];
-                ev = step_collide<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc,
+                ev = step_collide<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, CE ? q.uk[i] : 0, kc,
                                                    nullptr, CE, CE ? q.sg[i] : 0.0, CE ? q.nf[i] : 0.0);
                 q.kc[i] = kc;
             }
-            pool_store<TIME>(q, i, p);
+            pool_store<TIME, CE>(q, i, p);
             if (ev == EV_DEAD) retire(q, G, i, p);
         }
         __syncthreads();
@@ -372,7 +390,7 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Pool q = carve<CE>(smem + (size_t)warp * pool_bytes(PW, CE), PW);
+    const Pool q = carve<TIME, CE>(smem + (size_t)warp * pool_bytes(PW, TIME, CE), PW);
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
     const int gen = a.gen_dev ? *a.gen_dev : a.gen;
     const int rep = (int)((blockIdx.x * (WPOOL_T / 32) + warp) % (unsigned)W.nrep);
@@ -416,10 +434,10 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
                     p.fate = FATE_LOST;
                     p.cell = 0;
                     p.mat = 0;
-                    pool_store<TIME>(q, i, p);
+                    pool_store<TIME, CE>(q, i, p);
                     retire(q, G, i, p);
                 } else {
-                    pool_store<TIME>(q, i, p);
+                    pool_store<TIME, CE>(q, i, p);
                 }
             }
             __syncwarp();
@@ -429,7 +447,7 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
         for (int k = lane; k < n_adv; k += 32) {
             int i = q.list[k];
             PS p;
-            pool_load<TIME>(q, i, p);
+            pool_load<TIME, CE>(q, i, p);
             int kind, which, uk = 0;
             double kt = q.kt[i];
             double xt = 0.0, xn = 0.0;
@@ -445,9 +463,8 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
             if (TIME) q.t[i] = p.t;
             q.s[i] = p.s;
             q.kt[i] = kt;
-            q.ev[i] = ev | (kind << 4);
-            q.bwhich[i] = which;
-            q.uk[i] = uk;
+            q.evw[i] = pack_ev(ev, kind, which);
+            if (CE) q.uk[i] = uk;
             if (ev == EV_DEAD) {
                 q.fate[i] = p.fate;
                 retire(q, G, i, p);
@@ -455,30 +472,30 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
         }
         __syncwarp();
         int n_x = warp_list<PW>(q.list, [&](int i) {
-            return q.fate[i] == FATE_ALIVE && (q.ev[i] & 15) == EV_CROSS;
+            return q.fate[i] == FATE_ALIVE && (q.evw[i] & 15) == EV_CROSS;
         });
         for (int k = lane; k < n_x; k += 32) {
             int i = q.list[k];
             PS p;
-            pool_load<TIME>(q, i, p);
-            int ev = step_cross(W, p, q.ev[i] >> 4, q.bwhich[i]);
-            pool_store<TIME>(q, i, p);
+            pool_load<TIME, CE>(q, i, p);
+            int ev = step_cross(W, p, ev_kind(q.evw[i]), ev_which(q.evw[i]));
+            pool_store<TIME, CE>(q, i, p);
             if (ev == EV_DEAD) retire(q, G, i, p);
         }
         __syncwarp();
         int n_c = warp_list<PW>(q.list, [&](int i) {
-            return q.fate[i] == FATE_ALIVE && (q.ev[i] & 15) == EV_COLLIDE;
+            return q.fate[i] == FATE_ALIVE && (q.evw[i] & 15) == EV_COLLIDE;
         });
         for (int k = lane; k < n_c; k += 32) {
             int i = q.list[k];
             PS p;
-            pool_load<TIME>(q, i, p);
+            pool_load<TIME, CE>(q, i, p);
             double kc = q.kc[i];
-            int ev = step_collide<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, q.uk[i], kc,
+            int ev = step_collide<false, TIME, CE>(W, W.prob[p.prob], p, q.gslot[i], Bdst, R, CE ? q.uk[i] : 0, kc,
                                                    nullptr, CE, CE ? q.sg[i] : 0.0, CE ? q.nf[i] : 0.0);
             q.kc[i] = kc;
-            q.ev[i] = EV_ADVANCE;
-            pool_store<TIME>(q, i, p);
+            q.evw[i] = EV_ADVANCE;
+            pool_store<TIME, CE>(q, i, p);
             if (ev == EV_DEAD) retire(q, G, i, p);
         }
         __syncwarp();
@@ -489,7 +506,7 @@ template <int PW, bool TIME, bool CE>
 void launch_wpool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                     const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
 {
-    size_t sm = pool_bytes(PW, CE) * (WPOOL_T / 32);
+    size_t sm = pool_bytes(PW, TIME, CE) * (WPOOL_T / 32);
     cudaFuncSetAttribute(k_wpool<PW, TIME, CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_wpool<PW, TIME, CE><<<grid, WPOOL_T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
 }
@@ -497,7 +514,7 @@ void launch_wpool_t(const World &W, const Particles &G, const Bank &Bsrc, const 
 template <int PW, bool CE> int wpool_occupancy()
 {
     int n = 0;
-    size_t sm = pool_bytes(PW, CE) * (WPOOL_T / 32);
+    size_t sm = pool_bytes(PW, false, CE) * (WPOOL_T / 32);
     cudaFuncSetAttribute(k_wpool<PW, false, CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wpool<PW, false, CE>, WPOOL_T, sm);
     return n;
@@ -507,7 +524,7 @@ template <int P, int T, bool TIME, bool CE>
 void launch_pool_t(const World &W, const Particles &G, const Bank &Bsrc, const Bank &Bdst,
                    const RunBufs &R, const PersistentArgs &a, int grid, cudaStream_t st)
 {
-    size_t sm = pool_bytes(P, CE);
+    size_t sm = pool_bytes(P, TIME, CE);
     cudaFuncSetAttribute(k_pool<P, T, TIME, CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_pool<P, T, TIME, CE><<<grid, T, sm, st>>>(W, G, Bsrc, Bdst, R, a);
 }
@@ -515,7 +532,7 @@ void launch_pool_t(const World &W, const Particles &G, const Bank &Bsrc, const B
 template <int P, int T, bool CE> int pool_occupancy()
 {
     int n = 0;
-    size_t sm = pool_bytes(P, CE);
+    size_t sm = pool_bytes(P, false, CE);
     cudaFuncSetAttribute(k_pool<P, T, false, CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool<P, T, false, CE>, T, sm);
     return n;
