@@ -199,17 +199,18 @@ __device__ __forceinline__ int build_list(const Pool &q, int *hist2, int &hb, in
 }
 
 // P particles per block of T threads; the register budget is planned for
-// pool_min_blocks(P, T, CE) resident blocks (128 registers per thread at 2
-// blocks of 256 threads; a pool of one particle per thread trades spilled
-// registers for a third resident block, or a fourth when the continuous-energy
-// physics is compiled out -- measured faster -- which the shared memory allows).
-__host__ __device__ constexpr int pool_min_blocks(int P, int T, bool CE)
+// pool_min_blocks(P, T, TIME, CE) resident blocks (128 registers per thread at
+// 2 blocks of 256 threads; a pool of one particle per thread trades spilled
+// registers for a fourth resident block -- measured faster -- which the shared
+// memory allows, or a third for the time-dependent continuous-energy physics,
+// where the fourth was slower).
+__host__ __device__ constexpr int pool_min_blocks(int P, int T, bool TIME, bool CE)
 {
-    return (P <= T && T == 256) ? (CE ? 3 : 4) : 65536 / (T * 128);
+    return (P <= T && T == 256) ? ((CE && TIME) ? 3 : 4) : 65536 / (T * 128);
 }
 
 template <int P, int T, bool TIME, bool CE>
-__global__ void __launch_bounds__(T, pool_min_blocks(P, T, CE)) k_pool(World W, Particles G, Bank Bsrc,
+__global__ void __launch_bounds__(T, pool_min_blocks(P, T, TIME, CE)) k_pool(World W, Particles G, Bank Bsrc,
                                                                Bank Bdst, RunBufs R,
                                                                PersistentArgs a)
 {
