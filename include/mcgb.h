@@ -87,7 +87,7 @@ typedef struct {
                                unfinished histories abandoned; the context stays usable */
     int pool;               /* persistent mode: particles held in shared memory and run
                                event type by event type from sorted lists: 256 (one per
-                               thread, three resident blocks per SM), 512 or 1024 per
+                               thread, four resident blocks per SM), 512 or 1024 per
                                256-thread block; 2256 or 2512 for 256 or 512 per
                                128-thread block; 32, 64 or 128 per warp (warp-level
                                lists, no block barriers); 0 = default (256); -1 = one
