@@ -59,11 +59,11 @@ HBM_PEAK_GBS = _hbm_peak()
 #   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum
 #   l2_hit_rate: lts__t_sector_hit_rate; warp_exec_efficiency: active lanes per
 #   issued instruction / 32; fp64_pipe_busy: FP64 pipe cycles / elapsed cycles
-NCU_SOURCES = "eb9039b82e38efc8"
-NCU_K_POOL = {"fp64_inst_per_event": 1374739648 / 2.233e7, "dram_bytes_per_launch": 90796032 + 151323136,
-              "l2_hit_rate": 0.9076, "warp_exec_efficiency": 20.39 / 32, "fp64_pipe_busy": 0.4951}
-NCU_K_ADVANCE = {"dram_bytes_per_launch": 124694784 + 24608000, "l2_hit_rate": 0.4976,
-                 "fp64_pipe_busy": 0.7513, "dram_throughput": 0.1625,
+NCU_SOURCES = "8f9f0575323c7248"
+NCU_K_POOL = {"fp64_inst_per_event": 1374739840 / 2.233e7, "dram_bytes_per_launch": 90889728 + 141473536,
+              "l2_hit_rate": 0.8949, "warp_exec_efficiency": 20.37 / 32, "fp64_pipe_busy": 0.5163}
+NCU_K_ADVANCE = {"dram_bytes_per_launch": 124678400 + 24086016, "l2_hit_rate": 0.4979,
+                 "fp64_pipe_busy": 0.7617, "dram_throughput": 0.1646,
                  "fp64_inst_per_particle": 52000000 / 1e6}
 
 
