@@ -443,6 +443,12 @@ int mcgb_rng_states(mcgb_ctx *ctx, uint64_t seed, uint64_t first_id, int64_t n_s
                     int n_draws, uint64_t *out);
 /* out[i] = ln(xi[i]) for xi[i] = k 2^-53, k in [1, 2^53] (the transport's log). */
 int mcgb_log(mcgb_ctx *ctx, int64_t n, const double *xi, double *out);
+/* The transport's float64 square root, quotient and reciprocal, which it
+ * computes on the integer and float32 pipes (the paper prescribes none): for
+ * each i, out[3*i] = sqrt(a[i]), out[3*i+1] = a[i] / b[i], out[3*i+2] =
+ * 1 / b[i], each the IEEE round-to-nearest value (a negative a[i] gives NaN).
+ * a, b: n host doubles each; out: 3 n host doubles. */
+int mcgb_fpint_ops(mcgb_ctx *ctx, int64_t n, const double *a, const double *b, double *out);
 /* FP64 throughput of this device, measured: a grid of 8 blocks of 256 threads
  * per SM runs independent fused multiply-add chains, `iters` steps of 8 chains
  * per thread, timed with CUDA events on the context's stream after one

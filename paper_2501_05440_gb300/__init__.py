@@ -63,7 +63,7 @@ class Tune(C.Structure):
 
 
 # the files that define the device code of the transport kernels
-_KERNEL_SOURCES = ["kernels.h", "world.h", "transport.cuh", "steps.cuh", "pool.cuh",
+_KERNEL_SOURCES = ["kernels.h", "world.h", "fpint.cuh", "transport.cuh", "steps.cuh", "pool.cuh",
                    "kernels_pool.cu", "kernels_pool_mg.cu", "kernels_pool_mg_time.cu",
                    "kernels_pool_ce.cu", "kernels_pool_ce_time.cu", "kernels_transport.cu"]
 
@@ -151,6 +151,7 @@ def lib():
                 "mcgb_rng_states": [P, u64, u64, i64, i32, P],
                 "mcgb_log": [P, i64, P, P], "mcgb_probe": [P, i64, P, P, P, P, P],
                 "mcgb_fp64_throughput": [P, i64, P, P],
+                "mcgb_fpint_ops": [P, i64, P, P, P],
                 "mcgb_ce_lookup": [P, i32, i64, P, P],
                 "mcgb_bank_offsets_noalloc": [P, i64, P, P, P],
             }
@@ -495,6 +496,16 @@ class Context:
         x = _f64(xi)
         out = np.zeros_like(x)
         _chk(self.L.mcgb_log(self.h, len(x), _p(x), _p(out)))
+        return out
+
+    def fpint_ops(self, a, b):
+        """The transport's float64 sqrt(a), a / b and 1 / b (integer-pipe,
+        correctly rounded), as an (n, 3) array."""
+        x, y = _f64(a).ravel(), _f64(b).ravel()
+        if x.shape != y.shape:
+            raise ValueError("a and b differ in length")
+        out = np.zeros((len(x), 3))
+        _chk(self.L.mcgb_fpint_ops(self.h, len(x), _p(x), _p(y), _p(out)))
         return out
 
     def fp64_throughput(self, iters=20000):

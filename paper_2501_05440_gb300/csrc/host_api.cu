@@ -2271,6 +2271,27 @@ int mcgb_log(mcgb_ctx *ctx, int64_t n, const double *xi, double *out)
     return MCGB_OK;
 }
 
+int mcgb_fpint_ops(mcgb_ctx *ctx, int64_t n, const double *a, const double *b, double *out)
+{
+    if (!ctx || n < 0 || n > ((int64_t)1 << 31) || (n > 0 && (!a || !b || !out)))
+        return fail(MCGB_E_INVALID_ARG, "bad argument");
+    if (n == 0) return MCGB_OK;
+    CK(cudaSetDevice(ctx->device));
+    DevAlloc tmp;
+    double *da, *db, *dout;
+    CKR(tmp.get(da, n));
+    CKR(tmp.get(db, n));
+    CKR(tmp.get(dout, 3 * n));
+    CK(cudaMemcpyAsync(da, a, 8 * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(db, b, 8 * n, cudaMemcpyHostToDevice, ctx->stream));
+    launch_fpint_ops(n, da, db, dout, ctx->stream);
+    CK(cudaGetLastError());
+    ctx->launches += 1;
+    CK(cudaMemcpyAsync(out, dout, 24 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MCGB_OK;
+}
+
 int mcgb_fp64_throughput(mcgb_ctx *ctx, int64_t iters, double *ops_per_s, double *ms)
 {
     if (!ctx || iters <= 0 || !ops_per_s || !ms) return fail(MCGB_E_INVALID_ARG, "bad argument");

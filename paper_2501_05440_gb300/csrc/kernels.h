@@ -113,6 +113,7 @@ void launch_copy_records(const Particles &P, int64_t n, int *ncoll, int *ncross,
 void launch_rng_states(uint64_t seed, uint64_t first_id, int64_t n, int draws, uint64_t *out,
                        cudaStream_t st);
 void launch_log(const World &W, int64_t n, const double *xi, double *out, cudaStream_t st);
+void launch_fpint_ops(int64_t n, const double *a, const double *b, double *out, cudaStream_t st);
 // FP64 throughput probe: grid blocks of 256 threads, fp64_rate_chains() FMAs per
 // thread per iteration
 void launch_fp64_rate(int grid, long long iters, double *sink, cudaStream_t st);

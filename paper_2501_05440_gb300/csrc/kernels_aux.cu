@@ -73,6 +73,22 @@ void launch_log(const World &W, int64_t n, const double *xi, double *out, cudaSt
     k_log<<<(int)((n + 255) / 256), 256, 0, st>>>(W, n, xi, out);
 }
 
+__global__ void k_fpint_ops(int64_t n, const double *a, const double *b, double *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = a[i], y = b[i];
+    out[3 * i] = sqrt_rn(x);
+    out[3 * i + 1] = div_rn(x, y);
+    out[3 * i + 2] = rcp_rn(y);
+}
+
+void launch_fpint_ops(int64_t n, const double *a, const double *b, double *out, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_fpint_ops<<<(int)((n + 255) / 256), 256, 0, st>>>(n, a, b, out);
+}
+
 __global__ void k_probe(World W, int root_univ, int64_t n, const double *pos, const double *dir,
                         int *path, double *dist, int *kind)
 {

@@ -42,7 +42,7 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     double sigt, mfp, nusf;
     if (CE && P.ce) {
         ce_macro(W, p.mat, p.E, sigt, nusf);
-        mfp = is_pos(sigt) ? __drcp_rn(sigt) : MCGB_INF;   // correctly rounded 1 / sigt
+        mfp = is_pos(sigt) ? rcp_rn(sigt) : MCGB_INF;   // correctly rounded 1 / sigt
         if (xs_t) {
             *xs_t = sigt;
             *xs_nf = nusf * mfp;
@@ -76,8 +76,8 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
         const double c = dom->axis == 0 ? p.x : (dom->axis == 1 ? p.y : p.z);
         const double dir = dom->axis == 0 ? p.u : (dom->axis == 1 ? p.v : p.w);
         double tdom = MCGB_INF;
-        if (is_pos(dir) && !is_inf(dom->hi)) tdom = (dom->hi - c) / dir;
-        else if (is_neg(dir) && !is_inf(-dom->lo)) tdom = (dom->lo - c) / dir;
+        if (is_pos(dir) && !is_inf(dom->hi)) tdom = div_rn(dom->hi - c, dir);
+        else if (is_neg(dir) && !is_inf(-dom->lo)) tdom = div_rn(dom->lo - c, dir);
         if (is_neg(tdom)) tdom = 0.0;
         if (lt_mag(tdom, d)) {
             leaves = true;
@@ -91,8 +91,8 @@ __device__ __forceinline__ int step_advance(const World &W, const ProblemDev &P,
     const double ta = p.t;
     double tb = p.t;
     if (timed) {
-        double iv = (CE && P.ce) ? __drcp_rn(W.kv * sqrt(p.E)) : __ldg(W.g_invv + P.invv_off + p.g);
-        double dt = (P.tcut - p.t) / iv;
+        double iv = (CE && P.ce) ? rcp_rn(W.kv * sqrt_rn(p.E)) : __ldg(W.g_invv + P.invv_off + p.g);
+        double dt = div_rn(P.tcut - p.t, iv);
         if (is_neg(dt)) dt = 0.0;
         if (lt_mag(dt, d)) {
             tcut = true;
@@ -187,7 +187,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         } else {
             double nusf;
             ce_macro(W, p.mat, p.E, sigt, nusf);
-            kterm = nusf * __drcp_rn(sigt);
+            kterm = nusf * rcp_rn(sigt);
         }
         uk = union_index(W, p.E);   // per-nuclide values for the reaction
         kc = kc + kterm;
@@ -211,7 +211,7 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
             }
         }
         int nuc = __ldg(W.mc_nuc + off + sel);
-        double mu = __ldg(W.n_nu + nuc) * sf / st;
+        double mu = div_rn(__ldg(W.n_nu + nuc) * sf, st);
         double fl = floor(mu);
         double xi = draw(p.s);
         int nf = (int)fl + (lt_mag(mu - fl, xi) ? 0 : 1);

@@ -14,6 +14,7 @@
 
 #include <cstdint>
 
+#include "fpint.cuh"
 #include "world.h"
 
 namespace mcgb {
@@ -174,7 +175,7 @@ __device__ __forceinline__ void iso_dir(uint64_t &s, double &u, double &v, doubl
         w = 1.0;
         return;
     }
-    double t = sqrt(fma(-0.25, S4, 1.0));
+    double t = sqrt_rn(fma(-0.25, S4, 1.0));
     u = a2 * t;
     v = b2 * t;
     w = fma(-0.5, S4, 1.0);
@@ -198,7 +199,7 @@ __device__ __forceinline__ void azimuth(uint64_t &s, double &cphi, double &sphi)
         sphi = 0.0;
         return;
     }
-    const double inv = __drcp_rn(r2);   // correctly rounded 1 / r2
+    const double inv = rcp_rn(r2);   // correctly rounded 1 / r2
     cphi = fma(a, a, -(b * b)) * inv;
     sphi = 2.0 * a * b * inv;
 }
@@ -209,19 +210,19 @@ __device__ __forceinline__ void rotate(double mu, uint64_t &s, double &u, double
     double cphi, sphi;
     azimuth(s, cphi, sphi);
     double st2 = fma(-mu, mu, 1.0);
-    double st = sqrt(is_pos(st2) ? st2 : 0.0);
+    double st = sqrt_rn(is_pos(st2) ? st2 : 0.0);
     double u0 = u, v0 = v, w0 = w;
     double ww = fma(-w0, w0, 1.0);
     if (ww > 1.0e-10) {
-        double q = sqrt(ww);
-        double f = st / q;
+        double q = sqrt_rn(ww);
+        double f = div_rn(st, q);
         u = fma(mu, u0, f * fma(u0 * w0, cphi, -(v0 * sphi)));
         v = fma(mu, v0, f * fma(v0 * w0, cphi, u0 * sphi));
         w = fma(mu, w0, -(st * q * cphi));
     } else {
         double uu = fma(-u0, u0, 1.0);
-        double q = sqrt(uu);
-        double f = st / q;
+        double q = sqrt_rn(uu);
+        double f = div_rn(st, q);
         v = fma(mu, v0, f * fma(v0 * u0, cphi, -(w0 * sphi)));
         w = fma(mu, w0, f * fma(w0 * u0, cphi, v0 * sphi));
         u = fma(mu, u0, -(st * q * cphi));
@@ -239,7 +240,7 @@ __device__ __forceinline__ double elastic(double E, const double *kin, uint64_t 
     double mucm = draw_sym(s);
     double q = fma(k01.y, mucm, k23.x);
     double Ep = E * q * k23.y;
-    double mul = fma(k01.x, mucm, 1.0) / sqrt(q);
+    double mul = div_rn(fma(k01.x, mucm, 1.0), sqrt_rn(q));
     if (mul > 1.0) mul = 1.0;
     if (mul < -1.0) mul = -1.0;
     rotate(mul, s, u, v, w);
@@ -270,7 +271,7 @@ __device__ __forceinline__ double maxwell(const World &W, uint64_t &s)
                 r2 = rr;
             }
         }
-        double c2 = a * a / r2;
+        double c2 = div_rn(a * a, r2);
         double E = -1.33e6 * (L1 + L2 * c2);
         if (!lt_mag(E_MAX, E)) return lt_mag(E, E_MIN) ? E_MIN : E;
     }
@@ -291,7 +292,7 @@ __device__ __forceinline__ double disk_cos2(uint64_t &s)
         ok = !lt_mag(1.0, rr) && is_pos(rr);
         t++;
     } while (!ok && t < 64);
-    return ok ? aa * aa / rr : 1.0;
+    return ok ? div_rn(aa * aa, rr) : 1.0;
 }
 
 // Elastic scattering off a free-gas target with a constant cross section (the
@@ -317,7 +318,7 @@ __device__ __forceinline__ double free_gas(const World &W, double E, const doubl
     const double A = __ldg(kin);
     const double2 k45 = __ldg(reinterpret_cast<const double2 *>(kin) + 2);   // 1/(A+1), 1/A
     const double y2 = A * E * ikT;
-    const double y = sqrt(y2);
+    const double y = sqrt_rn(y2);
     double py = y * SQRT_PI;
     double x = 0.0, mu = 1.0, r = y;
     for (int k = 0; k < MAX_TRIES; k++) {
@@ -332,10 +333,10 @@ __device__ __forceinline__ double free_gas(const World &W, double E, const doubl
             double L2 = log_n(W, draw_n(s));
             x2 = -(L1 + L2);
         }
-        x = sqrt(x2);
+        x = sqrt_rn(x2);
         mu = draw_sym(s);
         double r2 = fma(-(2.0 * x * y), mu, x2 + y2);
-        r = sqrt(is_pos(r2) ? r2 : 0.0);
+        r = sqrt_rn(is_pos(r2) ? r2 : 0.0);
         if (!lt_mag(r, draw(s) * (x + y))) break;
     }
     double tu = u, tv = v, tw = w;
@@ -350,7 +351,7 @@ __device__ __forceinline__ double free_gas(const World &W, double E, const doubl
     double wc = A * r * inv;
     double px = fma(wc, cu, Vx), py2 = fma(wc, cv, Vy), pz = fma(wc, cw, Vz);
     double p2 = fma(px, px, fma(py2, py2, pz * pz));
-    double ip = __drcp_rn(sqrt(p2));   // correctly rounded, the same as 1.0 / sqrt(p2)
+    double ip = rcp_rn(sqrt_rn(p2));   // correctly rounded, the same as 1.0 / sqrt(p2)
     u = px * ip;
     v = py2 * ip;
     w = pz * ip;
@@ -378,12 +379,12 @@ struct PS {
 };
 
 // 1/w is read only by z-planes; a world without them never computes it.
-// __drcp_rn is the correctly rounded reciprocal, the same value as 1.0 / x.
+// rcp_rn is the correctly rounded reciprocal, the same value as 1.0 / x.
 __device__ __forceinline__ void set_recip(const World &W, PS &p)
 {
-    p.iu = __drcp_rn(p.u);
-    p.iv = __drcp_rn(p.v);
-    if (W.need_iw) p.iw = __drcp_rn(p.w);
+    p.iu = rcp_rn(p.u);
+    p.iv = rcp_rn(p.v);
+    if (W.need_iw) p.iw = rcp_rn(p.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,7 +447,7 @@ __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, 
         }
         if ((sense > 0 && is_neg(dn)) || (sense < 0 && is_pos(dn))) {
             // axis planes use the direction's reciprocal, other planes divide
-            t = type == SURF_PLANE ? -f / dn : -f * inv;
+            t = type == SURF_PLANE ? div_rn(-f, dn) : -f * inv;
             return is_neg(t) ? 0.0 : t;
         }
         return MCGB_INF;
@@ -477,11 +478,11 @@ __device__ __forceinline__ double surf_dist(const World &W, int sid, int sense, 
     const bool inside = sense < 0;
     if (!inside && (!is_neg(b) || is_neg(disc))) return MCGB_INF;
     if (is_neg(disc)) disc = 0.0;
-    double s1 = fabs(b) + sqrt(disc);
+    double s1 = fabs(b) + sqrt_rn(disc);
     const bool far_plus = inside && !is_pos(b);
     double num = far_plus ? s1 : (inside ? -cc : cc);
     double den = far_plus ? a : s1;
-    t = num / den;
+    t = div_rn(num, den);
     return is_neg(t) ? 0.0 : t;
 }
 
@@ -552,8 +553,8 @@ __device__ __forceinline__ void lattice_index(const World &W, int L, double x, d
                                               int &iy)
 {
     double p = __ldg(W.l_pitch + L);
-    int i = (int)floor((x - __ldg(W.l_x0 + L)) / p);
-    int j = (int)floor((y - __ldg(W.l_y0 + L)) / p);
+    int i = (int)floor(div_rn(x - __ldg(W.l_x0 + L), p));
+    int j = (int)floor(div_rn(y - __ldg(W.l_y0 + L), p));
     int nx = __ldg(W.l_nx + L), ny = __ldg(W.l_ny + L);
     ix = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
     iy = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
@@ -696,7 +697,7 @@ __device__ __forceinline__ int cross(const World &W, PS &p, int kind, int which)
                 double a = __ldg(c), b = __ldg(c + 1), cz = __ldg(c + 2);
                 double dn = a * p.u + b * p.v + cz * p.w;
                 double nn = a * a + b * b + cz * cz;
-                double k = 2.0 * dn / nn;
+                double k = div_rn(2.0 * dn, nn);
                 p.u = p.u - k * a;
                 p.v = p.v - k * b;
                 p.w = p.w - k * cz;
