@@ -9,9 +9,12 @@
 namespace mcgb {
 
 // ---- event mode (one kernel per event type) -------------------------------
+// Births of every slot of a generation into P (gen_dev: the cycle index is read
+// there when not null, for graph replay).  The event forms start from these;
+// the persistent kernels take their births from them too (PersistentArgs::preborn).
 void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const RunBufs &R, int gen,
                    int64_t total, const int64_t *gen_base, const int *src_idx, int eigen, int block,
-                   cudaStream_t st);
+                   cudaStream_t st, const int *gen_dev = nullptr);
 // Algorithmic state bytes one particle moves in a k_advance launch over the
 // identity list: the fields loaded and stored, the flight's event queue entry.
 double event_advance_bytes(const World &W);
@@ -39,6 +42,8 @@ struct PersistentArgs {
     const int *gen_dev;      // when not null: the cycle index is read here (graph replay)
     long long max_passes;    // > 0: a block (warp) stops after this many passes of its event
                              // loop and raises ERR_ITER (histories left unfinished)
+    int preborn;             // 1: slot j's birth was made by launch_source into the
+                             // particle arrays, and a refill copies it from there
 };
 // births read Bsrc (the previous cycle's bank), new sites are appended to Bdst
 void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, const Bank &Bdst,

@@ -81,10 +81,11 @@ __device__ __forceinline__ int accum_replica(const World &W)
 // (that physics compiled out; chosen by launch_* from W.ce_any).
 template <bool CE>
 __global__ void k_source(World W, Particles P, Bank Bsrc, RunBufs R, int gen, int64_t total,
-                         const int64_t *gen_base, const int *src_idx, int eigen)
+                         const int64_t *gen_base, const int *src_idx, int eigen, const int *gen_dev)
 {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= total) return;
+    if (gen_dev) gen = *gen_dev;
     int prob = find_problem(gen_base, W.nprob, j);
     const ProblemDev &Pd = W.prob[prob];
     PS p;
@@ -281,15 +282,15 @@ double event_advance_bytes(const World &W)
 
 void launch_source(const World &W, const Particles &P, const Bank &Bsrc, const RunBufs &R, int gen,
                    int64_t total, const int64_t *gen_base, const int *src_idx, int eigen, int block,
-                   cudaStream_t st)
+                   cudaStream_t st, const int *gen_dev)
 {
     if (total <= 0) return;
     if (W.ce_any)
         k_source<true><<<nblocks(total, block), block, 0, st>>>(W, P, Bsrc, R, gen, total, gen_base,
-                                                                src_idx, eigen);
+                                                                src_idx, eigen, gen_dev);
     else
         k_source<false><<<nblocks(total, block), block, 0, st>>>(W, P, Bsrc, R, gen, total, gen_base,
-                                                                 src_idx, eigen);
+                                                                 src_idx, eigen, gen_dev);
 }
 
 void launch_advance(const World &W, const Particles &P, const RunBufs &R, const int *list, int n,
@@ -386,8 +387,9 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
                     Pd = W.prob + prob;
                     kt = 0.0;
                     kc = 0.0;
-                    bool ok = init_particle<CE>(W, *Pd, Bsrc, p, prob, j - a.gen_base[prob], gen,
-                                            a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                    bool ok = a.preborn ? load_born<TIME, CE>(W, P, j, p)
+                                        : init_particle<CE>(W, *Pd, Bsrc, p, prob, j - a.gen_base[prob], gen,
+                                                            a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
                     if (ok) {
                         alive = true;
                     } else {

@@ -251,8 +251,9 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, TIME, CE)) k_pool(Wor
                     prob = lo;
                 }
                 PS p;
-                bool ok = init_particle<CE>(W, W.prob[prob], Bsrc, p, prob, j - a.gen_base[prob], gen,
-                                        a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                bool ok = a.preborn ? load_born<TIME, CE>(W, G, j, p)
+                                    : init_particle<CE>(W, W.prob[prob], Bsrc, p, prob, j - a.gen_base[prob],
+                                                        gen, a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
                 q.gslot[i] = (int)j;
                 q.kt[i] = 0.0;
                 q.kc[i] = 0.0;
@@ -425,8 +426,9 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
                     else hi = mid;
                 }
                 PS p;
-                bool ok = init_particle<CE>(W, W.prob[lo], Bsrc, p, lo, j - a.gen_base[lo], gen,
-                                        a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                bool ok = a.preborn ? load_born<TIME, CE>(W, G, j, p)
+                                    : init_particle<CE>(W, W.prob[lo], Bsrc, p, lo, j - a.gen_base[lo], gen,
+                                                        a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
                 q.gslot[i] = (int)j;
                 q.kt[i] = 0.0;
                 q.kc[i] = 0.0;

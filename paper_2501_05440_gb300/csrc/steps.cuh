@@ -263,6 +263,27 @@ __device__ __forceinline__ bool init_particle(const World &W, const ProblemDev &
     return true;
 }
 
+// The birth of slot j that launch_source stored in the particle arrays (fields
+// a world does not use are not read); false when the source could not place
+// the particle (k_source raised the error and stored it as lost).
+template <bool TIME = true, bool CE = true>
+__device__ __forceinline__ bool load_born(const World &W, const Particles &G, int64_t j, PS &p)
+{
+    p.x = G.x[j]; p.y = G.y[j]; p.z = G.z[j];
+    p.u = G.u[j]; p.v = G.v[j]; p.w = G.w[j];
+    p.iu = G.iu[j]; p.iv = G.iv[j]; p.iw = W.need_iw ? G.iw[j] : 0.0;
+    p.E = CE ? G.E[j] : 0.0;
+    p.t = TIME ? G.t[j] : 0.0;
+    p.s = G.s[j];
+    p.g = G.g[j]; p.cell = G.cell[j]; p.ix = G.ix[j]; p.iy = G.iy[j]; p.ucell = G.ucell[j];
+    p.mat = G.mat[j]; p.prob = G.prob[j]; p.root = G.root[j];
+    p.nfis = 0;
+    p.ncoll = 0;
+    p.ncross = 0;
+    p.fate = G.fate[j];
+    return p.fate == FATE_ALIVE;
+}
+
 // Warp-aggregated append of `val` to queue when pred holds (all lanes call).
 __device__ __forceinline__ void enqueue(bool pred, int val, int *queue, int *count)
 {
