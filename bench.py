@@ -55,16 +55,20 @@ HBM_PEAK_GBS = _hbm_peak()
 # event-mode cycle).  They hold for the kernel sources they were taken on,
 # NCU_SOURCES = paper_2501_05440_gb300.kernel_source_hash() of that build, and
 # are reported as null once the sources differ.
-#   fp64_inst_per_event: sm__thread_inst_executed_pipe_fp64_pred_on.sum / events
+#   fp64_inst_per_event: sm__thread_inst_executed_pipe_fp64_pred_on.sum of the
+#   cycle's births kernel and transport kernel / events
 #   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum
 #   l2_hit_rate: lts__t_sector_hit_rate; warp_exec_efficiency: active lanes per
 #   issued instruction / 32; fp64_pipe_busy: FP64 pipe cycles / elapsed cycles
-NCU_SOURCES = "8f9f0575323c7248"
-NCU_K_POOL = {"fp64_inst_per_event": 1374739840 / 2.233e7, "dram_bytes_per_launch": 90889728 + 141473536,
-              "l2_hit_rate": 0.8949, "warp_exec_efficiency": 20.37 / 32, "fp64_pipe_busy": 0.5163}
-NCU_K_ADVANCE = {"dram_bytes_per_launch": 124678400 + 24086016, "l2_hit_rate": 0.4979,
-                 "fp64_pipe_busy": 0.7617, "dram_throughput": 0.1646,
-                 "fp64_inst_per_particle": 52000000 / 1e6}
+NCU_SOURCES = "84c25240931993bc"
+# k_source + k_pool of one cycle (2.233e7 events); DRAM bytes and rates of k_pool
+NCU_K_POOL = {"fp64_inst_per_event": (974839712 + 13809248) / 2.233e7,
+              "dram_bytes_per_launch": 130292224 + 73434624, "l2_hit_rate": 0.6472,
+              "warp_exec_efficiency": 20.29 / 32, "fp64_pipe_busy": 0.4371,
+              "births_kernel_dram_bytes": 59869440 + 100994816}
+NCU_K_ADVANCE = {"dram_bytes_per_launch": 124708608 + 23806720, "l2_hit_rate": 0.4811,
+                 "fp64_pipe_busy": 0.6543, "dram_throughput": 0.1979,
+                 "fp64_inst_per_particle": 36000000 / 1e6}
 
 
 def ncu_counters(m):
@@ -489,10 +493,11 @@ def run_mcgb(args):
         "k": h["k"]["k"], "k_sd": h["k"]["k_sd"],
         "gpu_launches": h["launches"], "clocks": h["clocks"],
     }
-    # roofline of the transport kernel (the persistent event loop, one launch per
-    # cycle, timed with CUDA events on its stream inside the library): bound by
-    # the FP64 pipe, against the FP64 throughput measured in this run; the HBM
-    # fraction of the event-based state traffic beside it
+    # roofline of the transport kernels (the generation's births, then the
+    # persistent event loop: one launch of each per cycle, timed together with
+    # CUDA events on their stream inside the library): bound by the FP64 pipe,
+    # against the FP64 throughput measured in this run; the HBM fraction of the
+    # event-based state traffic beside it
     ev = h["events_per_cycle"]
     t_kernel = max(h["transport_ms"], 1e-9) / 1e3
     pool, _ = ncu_counters(m)
@@ -502,7 +507,7 @@ def run_mcgb(args):
     out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak,
                        "unit": "G FP64 thread-instr/s", "frac": ach / peak if ach else None,
                        "traffic": pool["dram_bytes_per_launch"] if pool else None, "ncu": pool,
-                       "kernel": "k_pool (persistent event loop)",
+                       "kernel": "k_source + k_pool (the generation's births, then the persistent event loop)",
                        "per_unit": f"{ipe} FP64 instr/event (ncu) x {ev:.4g} events/launch",
                        "kernel_ms": h["transport_ms"],
                        "peak_kind": "measured in this run: mcgb_fp64_throughput (independent FMA "

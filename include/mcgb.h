@@ -90,7 +90,9 @@ typedef struct {
                                thread, four resident blocks per SM), 512 or 1024 per
                                256-thread block; 2256 or 2512 for 256 or 512 per
                                128-thread block; 32, 64 or 128 per warp (warp-level
-                               lists, no block barriers); 0 = default (256); -1 = one
+                               lists, no block barriers); 0 = default (2256 for
+                               multigroup worlds, 256 for continuous energy, 512 for
+                               continuous energy with time dependence); -1 = one
                                particle per thread in registers */
     int graphs;             /* persistent mode: run every eigenvalue cycle after the first
                                as one CUDA graph launch, with no host synchronisation

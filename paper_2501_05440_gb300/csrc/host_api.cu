@@ -279,6 +279,16 @@ static RunBufs run_bufs(mcgb_ctx *c, double *own, int own_cell, int own_G)
 
 static int block_size(mcgb_ctx *c) { return c->opts.block > 0 ? c->opts.block : 256; }
 
+// The default persistent pool by the physics the world holds (measured on the
+// lattice, the continuous-energy pin and the time benchmark): 256 particles per
+// 128-thread block for multigroup worlds, 256 per 256-thread block for
+// continuous energy, 512 per 256-thread block with time dependence as well.
+static int default_pool(const World &W)
+{
+    if (!W.ce_any) return 2256;
+    return W.time_any ? 512 : 256;
+}
+
 // Transport one cycle / generation of `total` slots (host-known bound).
 static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t total,
                                 const int64_t *gen_base, const int *src_idx, int eigen,
@@ -308,7 +318,7 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
         a.preborn = 1;
         launch_source(W, r.P, Bsrc, R, gen, total, gen_base, src_idx, eigen, block, st, gen_dev);
         c->launches += 1;
-        int pool = c->opts.pool == 0 ? 256 : c->opts.pool;
+        int pool = c->opts.pool == 0 ? default_pool(W) : c->opts.pool;
         if (pool > 0) {
             int bps = c->opts.blocks_per_sm > 0 ? c->opts.blocks_per_sm
                                                  : std::max(1, pool_max_blocks_per_sm(pool, W.ce_any != 0));
