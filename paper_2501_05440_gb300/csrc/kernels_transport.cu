@@ -114,17 +114,19 @@ __global__ void __launch_bounds__(256, 4) k_advance(World W, Particles P, RunBuf
     if (t < n) {
         i = list ? list[t] : t;
         PS p;
+        // every field is requested before the fate is tested, so that one round
+        // trip to memory serves them all (slot i is always in bounds)
         p.fate = P.fate[i];
+        load_geom(W, P, i, p);
+        p.E = W.ce_any ? P.E[i] : 0.0;
+        p.t = W.time_any ? P.t[i] : 0.0;
+        p.s = P.s[i];
+        p.g = P.g[i]; p.prob = P.prob[i]; p.root = P.root[i];
+        p.ncoll = P.ncoll[i]; p.ncross = P.ncross[i];
+        double kt = P.kt[i];
         if (p.fate == FATE_ALIVE) {
-            load_geom(W, P, i, p);
-            p.E = W.ce_any ? P.E[i] : 0.0;
-            p.t = W.time_any ? P.t[i] : 0.0;
-            p.s = P.s[i];
-            p.g = P.g[i]; p.prob = P.prob[i]; p.root = P.root[i];
-            p.ncoll = P.ncoll[i]; p.ncross = P.ncross[i];
             const ProblemDev &Pd = W.prob[p.prob];
             int kind, which, uk = 0;
-            double kt = P.kt[i];
             ev = step_advance<false, true, CE>(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt);
             P.x[i] = p.x; P.y[i] = p.y; P.z[i] = p.z;
             if (W.time_any) P.t[i] = p.t;
@@ -136,8 +138,7 @@ __global__ void __launch_bounds__(256, 4) k_advance(World W, Particles P, RunBuf
             P.uk[i] = uk;
         }
     }
-    enqueue(ev == EV_CROSS, i, q_cross, R.q_n + 0);
-    enqueue(ev == EV_COLLIDE, i, q_coll, R.q_n + 1);
+    enqueue2(ev == EV_CROSS, ev == EV_COLLIDE, i, q_cross, R.q_n + 0, q_coll, R.q_n + 1);
 }
 
 __global__ void __launch_bounds__(256) k_cross(World W, Particles P, RunBufs R, const int *q_cross,
@@ -217,20 +218,21 @@ __global__ void __launch_bounds__(256, 3) k_segment(World W, Particles P, Bank B
     if (t < n) {
         i = list ? list[t] : t;
         PS p;
+        // the fields the segment's steps read (as in k_advance, plus the
+        // fission-site count a collision continues), all requested before the
+        // fate is tested
         p.fate = P.fate[i];
+        load_geom(W, P, i, p);
+        p.E = W.ce_any ? P.E[i] : 0.0;
+        p.t = W.time_any ? P.t[i] : 0.0;
+        p.s = P.s[i];
+        p.g = P.g[i]; p.prob = P.prob[i]; p.root = P.root[i];
+        p.ncoll = P.ncoll[i]; p.ncross = P.ncross[i]; p.nfis = P.nfis[i];
+        double kt = P.kt[i];
         if (p.fate == FATE_ALIVE) {
-            // the fields the segment's steps read (as in k_advance, plus the
-            // fission-site count a collision continues)
-            load_geom(W, P, i, p);
-            p.E = W.ce_any ? P.E[i] : 0.0;
-            p.t = W.time_any ? P.t[i] : 0.0;
-            p.s = P.s[i];
-            p.g = P.g[i]; p.prob = P.prob[i]; p.root = P.root[i];
-            p.ncoll = P.ncoll[i]; p.ncross = P.ncross[i]; p.nfis = P.nfis[i];
             const double u = p.u, v = p.v, w = p.w;
             const ProblemDev &Pd = W.prob[p.prob];
             int kind, which, uk = 0;
-            double kt = P.kt[i];
             double xt = 0.0, xn = 0.0;
             int ev = step_advance<false, true, CE>(W, Pd, p, i, R, accum_replica(W), kind, which, uk, kt,
                                                    nullptr, nullptr, nullptr, &xt, &xn);

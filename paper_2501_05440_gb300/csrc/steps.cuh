@@ -284,17 +284,44 @@ __device__ __forceinline__ bool load_born(const World &W, const Particles &G, in
     return p.fate == FATE_ALIVE;
 }
 
-// Warp-aggregated append of `val` to queue when pred holds (all lanes call).
+// Block-aggregated append of `val` to queue a when pa holds and to queue b when
+// pb holds: each warp counts its lanes with a ballot, the warps reserve their
+// places in the block's share with shared-memory atomics, and one thread takes
+// the block's share of each queue with a single global atomic (one per block
+// instead of one per warp: the queue counters are the only addresses every
+// block of the launch updates).  Every thread of the block must call it, with
+// a block size a multiple of 32; qb may be null (one queue).
+__device__ __forceinline__ void enqueue2(bool pa, bool pb, int val, int *qa, int *na, int *qb, int *nb)
+{
+    __shared__ int s_n[2], s_base[2];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_n[0] = 0;
+        s_n[1] = 0;
+    }
+    __syncthreads();
+    const unsigned ma = __ballot_sync(0xffffffffu, pa), mb = __ballot_sync(0xffffffffu, pb);
+    int wa = 0, wb = 0;
+    if (lane == 0) {
+        if (ma) wa = atomicAdd(&s_n[0], __popc(ma));
+        if (mb) wb = atomicAdd(&s_n[1], __popc(mb));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_base[0] = s_n[0] ? atomicAdd(na, s_n[0]) : 0;
+        s_base[1] = s_n[1] ? atomicAdd(nb, s_n[1]) : 0;
+    }
+    __syncthreads();
+    wa = __shfl_sync(0xffffffffu, wa, 0);
+    wb = __shfl_sync(0xffffffffu, wb, 0);
+    const unsigned lt = (1u << lane) - 1u;
+    if (pa) qa[s_base[0] + wa + __popc(ma & lt)] = val;
+    if (pb) qb[s_base[1] + wb + __popc(mb & lt)] = val;
+}
+
 __device__ __forceinline__ void enqueue(bool pred, int val, int *queue, int *count)
 {
-    unsigned m = __ballot_sync(0xffffffffu, pred);
-    if (m == 0) return;
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (pred) queue[base + __popc(m & ((1u << lane) - 1u))] = val;
+    enqueue2(pred, false, val, queue, count, nullptr, nullptr);
 }
 
 }  // namespace mcgb
