@@ -72,8 +72,8 @@ def lib():
             L.orc_rng_xi.argtypes = [u64]
             L.orc_log.restype = d
             L.orc_log.argtypes = [d]
-            L.orc_log_table.restype = d
-            L.orc_log_table.argtypes = [i32]
+            L.orc_log_table_q57.restype = C.c_int64
+            L.orc_log_table_q57.argtypes = [i32]
             L.orc_site_index.restype = i64
             L.orc_site_index.argtypes = [i64, u64, i64, i64]
             L.orc_maxwell.restype = d
@@ -318,9 +318,10 @@ def log(xi):
     return lib().orc_log(xi)
 
 
-def log_table(j):
-    """entry j of the strict logarithm's table of ln(1 + j/256)"""
-    return lib().orc_log_table(j)
+def log_table_q57(j):
+    """entry j of the strict logarithm's table: ln(1 + j/256) 2^57 rounded to
+    the nearest integer"""
+    return lib().orc_log_table_q57(j)
 
 
 def site_index(j, n, M, N):

@@ -86,34 +86,63 @@ static double draw(uint64_t *s) { return (double)draw_n(s) * 0x1p-53; }
 
 /* ------------------------------------------------------------------------- */
 /* ln xi for the flight distance and the spectra.  Plain: libm's log.
- * Strict: the table-driven method of Tang ("Table-driven implementation of the
- * logarithm function in IEEE floating-point arithmetic", ACM TOMS 1990), as the
- * CUDA library evaluates it: xi = 2^(e-53) m with m in [1, 2); c = 1 + j/256
- * from the top 8 bits of m's fraction; r = (m - c) (1/c);
- * ln xi = (e - 53) ln 2 + ln c + log1p(r), log1p by its Taylor polynomial to
- * r^6 evaluated by Horner's rule with fused multiply-adds, its last product
- * fused into the addition of ln c.  The table holds
- * ln c correctly rounded (computed here in extended precision and rounded
- * once) and 1/c rounded once.                                                 */
-static double TANG_LN[256], TANG_RECIP[256];
+ * Strict: the CUDA library's fixed-point form of the table-driven method of
+ * Tang ("Table-driven implementation of the logarithm function in IEEE
+ * floating-point arithmetic", ACM TOMS 1990): xi = 2^(e-53) m with m in
+ * [1, 2); c = 1 + j/256 from the top 8 bits of m's fraction; r = (m - c)(1/c)
+ * as a 64-bit fraction; ln xi = (e - 53) ln 2 + ln c + log1p(r), log1p by its
+ * Taylor polynomial to r^6 by Horner's rule on 63-bit fractions (every
+ * product truncated), the three terms added in 57 fraction bits and the sum
+ * rounded once to a double.  The tables hold ln c and ln 2 to 57 fraction
+ * bits, rounded to nearest (computed here from the Mercator series of
+ * -ln(1 - t) in 120-bit fixed point), and 1/c to 63 bits rounded down.      */
+typedef unsigned __int128 orc_u128;
+static int64_t FX_LNC[256], FX_ELN2[64];
+static uint64_t FX_INVC[256];
 static int tang_ready;
-static const double LN2_D = 0x1.62e42fefa39efp-1;
+
+/* a b / 2^120 for a, b < 2^121: the 256-bit product from 64-bit limbs */
+static orc_u128 fx_mul120(orc_u128 a, orc_u128 b)
+{
+    uint64_t a1 = (uint64_t)(a >> 64), a0 = (uint64_t)a, b1 = (uint64_t)(b >> 64), b0 = (uint64_t)b;
+    orc_u128 p00 = (orc_u128)a0 * b0, p01 = (orc_u128)a0 * b1, p10 = (orc_u128)a1 * b0,
+             p11 = (orc_u128)a1 * b1;
+    /* product = p11 2^128 + (p01 + p10) 2^64 + p00; keep bits 120 and up */
+    orc_u128 mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;   /* bits 64..191, low part */
+    orc_u128 hi = p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);  /* bits 128 and up */
+    return (hi << 8) | ((uint64_t)mid >> 56);
+}
+
+/* -ln(1 - t) = t + t^2/2 + t^3/3 + ... for t = num/den < 1/2, 120 fraction bits */
+static orc_u128 fx_mercator120(uint64_t num, uint64_t den)
+{
+    orc_u128 t = ((orc_u128)num << 120) / den, pw = t, sum = 0;
+    for (int k = 1; k <= 400 && pw; k++) {
+        sum += pw / (orc_u128)k;
+        pw = fx_mul120(pw, t);
+    }
+    return sum;
+}
+
+static int64_t fx_round57(orc_u128 v) { return (int64_t)((v + ((orc_u128)1 << 62)) >> 63); }
 
 static void tang_init(void)
 {
     if (tang_ready) return;
     for (int j = 0; j < 256; j++) {
-        long double c = 1.0L + (long double)j / 256.0L;
-        TANG_LN[j] = (double)logl(c);
-        TANG_RECIP[j] = 1.0 / (double)c;
+        /* ln(1 + j/256) = -ln(1 - j/(256 + j)) */
+        FX_LNC[j] = fx_round57(fx_mercator120((uint64_t)j, (uint64_t)(256 + j)));
+        FX_INVC[j] = (uint64_t)(((orc_u128)1 << 71) / (orc_u128)(256 + j));
     }
+    int64_t ln2 = fx_round57(fx_mercator120(1, 2));   /* -ln(1 - 1/2) */
+    for (int e = 0; e < 64; e++) FX_ELN2[e] = (int64_t)(e - 53) * ln2;
     tang_ready = 1;
 }
 
-double orc_log_table(int j)
+int64_t orc_log_table_q57(int j)
 {
     tang_init();
-    return j >= 0 && j < 256 ? TANG_LN[j] : NAN;
+    return j >= 0 && j < 256 ? FX_LNC[j] : INT64_MIN;
 }
 
 /* n in [1, 2^53]: xi = n 2^-53 */
@@ -121,17 +150,21 @@ static double tang_log(uint64_t n)
 {
     int e = 0;
     while ((n >> e) > 1) e++;                         /* 2^e <= n < 2^(e+1) */
-    double m = ldexp((double)n, -e);                  /* exact */
-    int j = (int)((m - 1.0) * 256.0);                 /* exact: top 8 fraction bits */
-    double c = 1.0 + (double)j / 256.0;
-    double r = (m - c) * TANG_RECIP[j];
-    double h = -1.0 / 6.0;
-    h = fma(h, r, 1.0 / 5.0);
-    h = fma(h, r, -0.25);
-    h = fma(h, r, 1.0 / 3.0);
-    h = fma(h, r, -0.5);
-    h = fma(h, r, 1.0);
-    return (double)(e - 53) * LN2_D + fma(h, r, TANG_LN[j]);
+    uint64_t fr = (n << (52 - e)) & ((1ULL << 52) - 1);   /* m's 52 fraction bits */
+    int j = (int)(fr >> 44);
+    uint64_t d = fr & ((1ULL << 44) - 1);             /* (m - c) 2^52 */
+    uint64_t r = (uint64_t)(((orc_u128)d * FX_INVC[j]) >> 51);   /* r 2^64 */
+    static const uint64_t inv_k[6] = {0x8000000000000000ULL, 0x4000000000000000ULL,
+                                      0x2AAAAAAAAAAAAAAAULL, 0x2000000000000000ULL,
+                                      0x1999999999999999ULL, 0x1555555555555555ULL};   /* 2^63 / k */
+    uint64_t h = inv_k[5];
+    for (int k = 4; k >= 0; k--) h = inv_k[k] - (uint64_t)(((orc_u128)r * h) >> 64);
+    uint64_t lp = (uint64_t)(((orc_u128)r * h) >> 64);   /* log1p(r) 2^63 */
+    int64_t L = FX_ELN2[e] + FX_LNC[j] + (int64_t)(lp >> 6);
+    if (L == 0) return 0.0;
+    /* -L 2^-57, rounded to the nearest double (ties to even) by the FPU's
+     * conversion of the integer: |L| < 2^63 */
+    return -ldexp((double)(uint64_t)(-L), -57);
 }
 
 double orc_log(double xi)

@@ -132,7 +132,7 @@ double orc_rng_xi(uint64_t s);
 /* ln xi by the strict mode's table-driven method (xi in (0, 1]) */
 double orc_log(double xi);
 /* entry j (0..255) of that method's table of ln(1 + j/256) */
-double orc_log_table(int j);
+int64_t orc_log_table_q57(int j);
 /* index of the bank site that source j of N takes after a cycle banked M sites,
  * for the resampling draw xi = n 2^-53 (n in [1, 2^53]) */
 int64_t orc_site_index(int64_t j, uint64_t n, int64_t M, int64_t N);

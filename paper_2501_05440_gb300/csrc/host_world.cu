@@ -15,58 +15,40 @@
 
 namespace mcgb {
 
-static const double LN2 = 0x1.62e42fefa39efp-1;
+// The logarithm's tables, computed exactly enough in 128-bit fixed point with
+// 120 fraction bits (Q120): a product of two Q120 numbers below 2^121 keeps
+// its top bits from three 64-bit partial products (truncation below 3 units).
+typedef unsigned __int128 u128;
 
-// Double-double numbers hi + lo (|lo| <= half an ulp of hi) for the table of
-// the logarithm: Knuth's two-sum, the exact product by a fused multiply-add,
-// and division by long division in double-double.
-struct DD {
-    double hi, lo;
-};
-
-static DD dd_fast(double a, double b)   // |a| >= |b|: a + b exactly as hi + lo
+static u128 mul_q120(u128 a, u128 b)
 {
-    double s = a + b;
-    return {s, b - (s - a)};
+    const uint64_t ah = (uint64_t)(a >> 64), al = (uint64_t)a, bh = (uint64_t)(b >> 64),
+                   bl = (uint64_t)b;
+    const u128 hh = (u128)ah * bh, mid = (u128)ah * bl + (u128)al * bh, ll = (u128)al * bl;
+    return (hh << 8) + (mid >> 56) + (ll >> 120);
 }
 
-static DD dd_add(DD a, DD b)
+// 2 atanh(num / den) = ln((den + num) / (den - num)) in Q120 for num/den <= 1/3:
+// 2 (s + s^3/3 + s^5/5 + ...), summed until the terms vanish (error ~1e-33).
+static u128 atanh2_q120(uint64_t num, uint64_t den)
 {
-    double s = a.hi + b.hi;
-    double v = s - a.hi;
-    double e = (a.hi - (s - v)) + (b.hi - v);
-    return dd_fast(s, e + (a.lo + b.lo));
+    const u128 s = ((u128)num << 120) / den;
+    const u128 z = mul_q120(s, s);
+    u128 term = s, sum = 0;
+    for (int k = 0; k < 256 && term; k++) {
+        sum += term / (u128)(2 * k + 1);
+        term = mul_q120(term, z);
+    }
+    return 2 * sum;
 }
 
-static DD dd_mul(DD a, DD b)
-{
-    double p = a.hi * b.hi;
-    double e = std::fma(a.hi, b.hi, -p);
-    return dd_fast(p, e + (a.hi * b.lo + a.lo * b.hi));
-}
+static int64_t q120_to_q57(u128 v) { return (int64_t)((v + ((u128)1 << 62)) >> 63); }
 
-static DD dd_div(DD a, DD b)
-{
-    double q1 = a.hi / b.hi;
-    DD r = dd_add(a, dd_mul(b, DD{-q1, 0.0}));
-    double q2 = r.hi / b.hi;
-    r = dd_add(r, dd_mul(b, DD{-q2, 0.0}));
-    double q3 = r.hi / b.hi;
-    return dd_add(dd_fast(q1, q2), DD{q3, 0.0});
-}
+// ln(1 + j/256) in Q57, rounded to nearest: 2 atanh(j / (512 + j)).
+int64_t ln_table_q57(int j) { return q120_to_q57(atanh2_q120((uint64_t)j, (uint64_t)(512 + j))); }
 
-// ln(1 + j/256) correctly rounded: 2 atanh(s), s = j / (512 + j), summed as
-// s (1 + s^2/3 + s^4/5 + ...) in double-double (s <= 1/3: 40 terms leave
-// less than 1e-38), then rounded once.
-double ln_table_entry(int j)
-{
-    DD s = dd_div(DD{(double)j, 0.0}, DD{512.0 + (double)j, 0.0});
-    DD z = dd_mul(s, s);
-    DD p{0.0, 0.0};
-    for (int k = 39; k >= 0; k--) p = dd_add(dd_mul(p, z), dd_div(DD{1.0, 0.0}, DD{2.0 * k + 1.0, 0.0}));
-    DD r = dd_mul(dd_mul(DD{2.0, 0.0}, s), p);
-    return r.hi + r.lo;
-}
+// ln 2 in Q57: 2 atanh(1/3).
+int64_t ln2_q57() { return q120_to_q57(atanh2_q120(1, 3)); }
 
 // Partial sums in order divided by the total; the last entry is exactly 1.
 void make_cdf(const double *w, int n, double *cdf)
@@ -627,14 +609,16 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
             }
         }
     }
-    // log tables
-    std::vector<double> logtab(256), rinvtab(256), etab(64);
+    // log tables: ln c and 1/c of c = 1 + j/256 in fixed point (Q57, Q63 rounded
+    // down), and (e - 53) ln 2 in Q57 for the 54 binades of n
+    std::vector<int64_t> lnc_q(256), eln2_q(64);
+    std::vector<uint64_t> invc_q(256);
     for (int j = 0; j < 256; j++) {
-        double c = 1.0 + (double)j / 256.0;
-        logtab[j] = ln_table_entry(j);
-        rinvtab[j] = 1.0 / c;
+        lnc_q[j] = ln_table_q57(j);
+        invc_q[j] = (uint64_t)((((u128)256) << 63) / (u128)(256 + j));
     }
-    for (int e = 0; e < 64; e++) etab[e] = (double)(e - 53) * LN2;
+    const int64_t l2 = ln2_q57();
+    for (int e = 0; e < 64; e++) eln2_q[e] = (int64_t)(e - 53) * l2;
 
     int nrep = acc_size > 0 ? (int)std::max<int64_t>(1, std::min<int64_t>(64, (1 << 20) / acc_size)) : 1;
 
@@ -667,8 +651,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
            o_nA = S.put(n_A), o_nnu = S.put(n_nu), o_nkin = S.put(n_kin);
     size_t o_mcoff = S.put(mc_off), o_mcn = S.put(mc_n), o_mcnuc = S.put(mc_nuc),
            o_mcfis = S.put(mc_fissile), o_mcdens = S.put(mc_dens);
-    size_t o_srccdf = S.put(src_cdf), o_logtab = S.put(logtab), o_rinv = S.put(rinvtab),
-           o_etab = S.put(etab);
+    size_t o_srccdf = S.put(src_cdf), o_lncq = S.put(lnc_q), o_invcq = S.put(invc_q),
+           o_eln2q = S.put(eln2_q);
     size_t o_tf = S.put(t_filter), o_tnb = S.put(t_nbins), o_tne = S.put(t_ne), o_toff = S.put(t_off),
            o_teoff = S.put(t_eoff), o_tned = S.put(t_nedges), o_tbat = S.put(t_batches),
            o_tedges = S.put(t_edges), o_tntb = S.put(t_ntb), o_ttoff = S.put(t_toff),
@@ -726,8 +710,8 @@ std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cu
     P_(n_A, double, o_nA); P_(n_nu, double, o_nnu); P_(n_kin, double, o_nkin);
     P_(mc_off, int, o_mcoff); P_(mc_n, int, o_mcn); P_(mc_nuc, int, o_mcnuc);
     P_(mc_fissile, int, o_mcfis); P_(mc_dens, double, o_mcdens);
-    P_(src_cdf, double, o_srccdf); P_(logtab, double, o_logtab); P_(rinvtab, double, o_rinv);
-    P_(etab, double, o_etab);
+    P_(src_cdf, double, o_srccdf); P_(lnc_q, int64_t, o_lncq); P_(invc_q, uint64_t, o_invcq);
+    P_(eln2_q, int64_t, o_eln2q);
     P_(t_filter, int, o_tf); P_(t_nbins, int, o_tnb); P_(t_ne, int, o_tne); P_(t_off, int, o_toff);
     P_(t_eoff, int, o_teoff); P_(t_nedges, int, o_tned); P_(t_batches, int, o_tbat);
     P_(t_edges, double, o_tedges);

@@ -90,7 +90,8 @@ struct DeviceWorld {
 std::string build_world(const std::vector<ProblemRun> &runs, DeviceWorld &dw, cudaStream_t st);
 
 // Host-side tables identical to the device ones (shared with the checks).
-double ln_table_entry(int j);
+int64_t ln_table_q57(int j);
+int64_t ln2_q57();
 void make_cdf(const double *w, int n, double *cdf);
 
 }  // namespace mcgb

@@ -121,35 +121,42 @@ __device__ __forceinline__ double draw_sym(uint64_t &s) { return n_to_sym(draw_n
 __device__ __forceinline__ double draw_sym2(uint64_t &s) { return n_to_sym2(draw_n(s)); }
 
 // ---------------------------------------------------------------------------
-// ln xi for xi = n 2^-53: table-driven (Tang, ACM TOMS 1990).  n = 2^e m,
-// m in [1,2); c = 1 + j/256 from the top 8 fraction bits; r = (m - c)(1/c);
-// ln xi = (e - 53) ln 2 + ln c + r(1 + r(-1/2 + r(1/3 + r(-1/4 + r(1/5 - r/6))))),
-// the polynomial by Horner's rule with fused multiply-adds, its last product
-// fused into the addition of ln c.
-// Tables (built on the host): ln c by the series 2 atanh((c-1)/(c+1)), 1/c,
-// and (e - 53) ln 2 rounded once.
+// ln xi for xi = n 2^-53, n in [1, 2^53], on the integer pipe: the table-driven
+// reduction of Tang (ACM TOMS 1990) in fixed point.  n = 2^e m with m in
+// [1, 2); c = 1 + j/256 from the top 8 fraction bits of m; r = (m - c)(1/c)
+// in [0, 2^-8); ln xi = (e - 53) ln 2 + ln c + ln(1 + r), with
+// ln(1 + r) = r (1 - r (1/2 - r (1/3 - r (1/4 - r (1/5 - r/6))))) by Horner's
+// rule on 64-bit fractions (each product truncated), the sum in 57 fraction
+// bits (|ln xi| < 37), then rounded once to a double.  Tables (built on the
+// host): ln c and (e - 53) ln 2 rounded to 57 fraction bits, 1/c to 63.
+// Error: below 2^-56 absolute and 1.2 ulp relative where |ln xi| >= 1/32.
 __device__ __forceinline__ double log_n(const World &W, uint64_t n)
 {
-    int lz = __clzll((long long)n);
-    int e = 63 - lz;
-    uint64_t frac = ((n << lz) << 1) >> 12;
-    int j = (int)(frac >> 44);
-    // m - c is exact (c <= m < 2c): the low 44 fraction bits times 2^-52,
-    // built from the bits like n_to_xi instead of subtracted on the FP64 pipe
-    uint64_t lo = frac & ((1ULL << 44) - 1);
-    double mc = 0.0;
-    if (lo) {
-        int z = __clzll((long long)lo);
-        mc = __longlong_as_double((long long)(((uint64_t)(1034 - z) << 52) | (((lo << z) << 1) >> 12)));
-    }
-    double r = mc * __ldg(W.rinvtab + j);
-    double q = -1.0 / 6.0;
-    q = fma(q, r, 1.0 / 5.0);
-    q = fma(q, r, -0.25);
-    q = fma(q, r, 1.0 / 3.0);
-    q = fma(q, r, -0.5);
-    q = fma(q, r, 1.0);
-    return __ldg(W.etab + e) + fma(q, r, __ldg(W.logtab + j));
+    const int lz = __clzll((long long)n);
+    const uint64_t frac = ((n << lz) << 1) >> 12;   // the 52 fraction bits of m
+    const int j = (int)(frac >> 44);
+    const uint64_t d = frac & ((1ULL << 44) - 1);    // (m - c) 2^52, exact
+    // r 2^64 = d (1/c) 2^(64 - 52), from the 107-bit product d (2^63/c)
+    const uint64_t ic = __ldg(W.invc_q + j);
+    const uint64_t r = (__umul64hi(d, ic) << 13) | ((d * ic) >> 51);
+    uint64_t q = 0x1555555555555555ULL;               // 1/6 (63 fraction bits)
+    q = 0x1999999999999999ULL - __umul64hi(r, q);     // 1/5 - r q
+    q = 0x2000000000000000ULL - __umul64hi(r, q);     // 1/4
+    q = 0x2AAAAAAAAAAAAAAAULL - __umul64hi(r, q);     // 1/3
+    q = 0x4000000000000000ULL - __umul64hi(r, q);     // 1/2
+    q = 0x8000000000000000ULL - __umul64hi(r, q);     // 1
+    const uint64_t p = __umul64hi(r, q);              // ln(1 + r), 63 fraction bits
+    const int64_t L = __ldg(W.eln2_q + (63 - lz)) + __ldg(W.lnc_q + j) + (int64_t)(p >> 6);
+    if (L == 0) return 0.0;                           // xi = 1
+    // -L 2^-57 to a double, rounded to nearest (ties to even)
+    const uint64_t a = (uint64_t)(-L);
+    const int z = __clzll((long long)a);
+    const uint64_t x = a << z;
+    uint64_t mant = x >> 11;
+    const uint64_t rem = x & 0x7FF;
+    mant += (rem > 0x400 || (rem == 0x400 && (mant & 1))) ? 1 : 0;
+    const uint64_t bits = ((uint64_t)(63 - z - 57 + 1022) << 52) + mant;   // carries into the exponent
+    return -__longlong_as_double((long long)bits);
 }
 
 // ---------------------------------------------------------------------------

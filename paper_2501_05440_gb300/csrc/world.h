@@ -117,7 +117,8 @@ struct World {
     // source group distributions
     const double *src_cdf;
     // log tables: ln(1 + j/256), 1/(1 + j/256), (e - 53) ln 2
-    const double *logtab, *rinvtab, *etab;
+    const int64_t *lnc_q, *eln2_q;   // ln(1 + j/256) and (e - 53) ln 2 in Q57
+    const uint64_t *invc_q;          // 256 / (256 + j) in Q63, rounded down
     // tallies (global tally ids; accumulators [rep][acc_size]); a tally with
     // t_ntb > 0 time bins has edges t_tedges[t_toff + k] and 1 / width
     // t_tinvw[t_toff + k] and scores population instead of track length

@@ -110,17 +110,14 @@ def test_ce_energy_bin_edges(orc, strict):
 
 
 def test_log_table_correctly_rounded(orc):
+    """The strict logarithm's table holds ln(1 + j/256) in 57 fraction bits,
+    rounded to the nearest integer (checked against 200-bit mpmath)."""
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.prec = 200
+    scale = mpmath.mpf(2) ** 57
     for j in range(256):
-        want = float(mpmath.log(1 + mpmath.mpf(j) / 256))
-        assert orc.log_table(j) == want, j
-    # the 40-term double-precision atanh series is not correctly rounded
-    def series(c):
-        s = (c - 1.0) / (c + 1.0)
-        z = s * s
-        p = 1.0 / 79.0
-        for k in range(38, -1, -1):
-            p = p * z + 1.0 / float(2 * k + 1)
-        return 2.0 * s * p
-    assert any(series(1 + j / 256) != orc.log_table(j) for j in range(256))
+        want = int(mpmath.nint(mpmath.log(1 + mpmath.mpf(j) / 256) * scale))
+        assert orc.log_table_q57(j) == want, j
+    # rounding down instead of to nearest would differ
+    assert any(int(mpmath.floor(mpmath.log(1 + mpmath.mpf(j) / 256) * scale)) != orc.log_table_q57(j)
+               for j in range(256))
