@@ -60,15 +60,15 @@ HBM_PEAK_GBS = _hbm_peak()
 #   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum
 #   l2_hit_rate: lts__t_sector_hit_rate; warp_exec_efficiency: active lanes per
 #   issued instruction / 32; fp64_pipe_busy: FP64 pipe cycles / elapsed cycles
-NCU_SOURCES = "84c25240931993bc"
+NCU_SOURCES = "d7113fd32b7b2538"
 # k_source + k_pool of one cycle (2.233e7 events); DRAM bytes and rates of k_pool
-NCU_K_POOL = {"fp64_inst_per_event": (974839712 + 13809248) / 2.233e7,
-              "dram_bytes_per_launch": 130292224 + 73434624, "l2_hit_rate": 0.6472,
-              "warp_exec_efficiency": 20.29 / 32, "fp64_pipe_busy": 0.4371,
-              "births_kernel_dram_bytes": 59869440 + 100994816}
-NCU_K_ADVANCE = {"dram_bytes_per_launch": 124708608 + 23806720, "l2_hit_rate": 0.4811,
-                 "fp64_pipe_busy": 0.6543, "dram_throughput": 0.1979,
-                 "fp64_inst_per_particle": 36000000 / 1e6}
+NCU_K_POOL = {"fp64_inst_per_event": (818444256 + 13809952) / 2.233e7,
+              "dram_bytes_per_launch": 130676736 + 73460480, "l2_hit_rate": 0.6468,
+              "warp_exec_efficiency": 20.43 / 32, "fp64_pipe_busy": 0.3961,
+              "births_kernel_dram_bytes": 59829248 + 101268224}
+NCU_K_ADVANCE = {"dram_bytes_per_launch": 124738816 + 23476992, "l2_hit_rate": 0.4759,
+                 "fp64_pipe_busy": 0.6466, "dram_throughput": 0.2374,
+                 "fp64_inst_per_particle": 29000000 / 1e6}
 
 
 def ncu_counters(m):

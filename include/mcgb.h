@@ -76,7 +76,7 @@ enum { MCGB_MODE_EVENT = 0,       /* one kernel per event type, host-driven loop
 typedef struct {
     int device;             /* CUDA device ordinal (default 0) */
     int mode;               /* MCGB_MODE_* (default MCGB_MODE_EVENT) */
-    int block;              /* threads per block (default: autotuned or 256) */
+    int block;              /* threads per block (default: autotuned or 128) */
     int blocks_per_sm;      /* persistent mode: resident blocks per SM (default: occupancy) */
     int record_histories;   /* keep per-history records of the last cycle / generation 0 */
     double bank_factor;     /* fission bank capacity as a multiple of N (default 3) */

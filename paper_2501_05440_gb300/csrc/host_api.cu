@@ -277,7 +277,11 @@ static RunBufs run_bufs(mcgb_ctx *c, double *own, int own_cell, int own_G)
     return R;
 }
 
-static int block_size(mcgb_ctx *c) { return c->opts.block > 0 ? c->opts.block : 256; }
+// Threads per block of the launches over a generation's slots (births, the
+// event and segment kernels, the register-resident persistent variant): 128
+// by default, which ends the event form's flight launch sooner than 256
+// (finer blocks leave less of the last wave idle).
+static int block_size(mcgb_ctx *c) { return c->opts.block > 0 ? c->opts.block : 128; }
 
 // The default persistent pool by the physics the world holds (measured on the
 // lattice, the continuous-energy pin and the time benchmark): 256 particles per
