@@ -32,6 +32,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "histories/s on 1 GB300, batched vs plain event launch; % HBM roofline; grad/s"
 WORKLOAD = "mg-c5g7-like-lattice-51x51-7g-keff"
+# --workload: the headline problem (the lattice) or the continuous-energy pin
+WORKLOADS = {"lattice": WORKLOAD, "ce-pin": "ce-pin-cell-4nuclides-keff"}
 N_PER_CYCLE = 1_000_000
 # Algorithmic particle-state bytes an event moves in the event-based form:
 # advance reads position/direction/energy/RNG/cell path and writes position,
@@ -60,14 +62,14 @@ HBM_PEAK_GBS = _hbm_peak()
 #   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum
 #   l2_hit_rate: lts__t_sector_hit_rate; warp_exec_efficiency: active lanes per
 #   issued instruction / 32; fp64_pipe_busy: FP64 pipe cycles / elapsed cycles
-NCU_SOURCES = "d7113fd32b7b2538"
+NCU_SOURCES = "a6f4290a3d6c52a0"
 # k_source + k_pool of one cycle (2.233e7 events); DRAM bytes and rates of k_pool
-NCU_K_POOL = {"fp64_inst_per_event": (818444256 + 13809952) / 2.233e7,
-              "dram_bytes_per_launch": 130676736 + 73460480, "l2_hit_rate": 0.6468,
-              "warp_exec_efficiency": 20.43 / 32, "fp64_pipe_busy": 0.3961,
-              "births_kernel_dram_bytes": 59829248 + 101268224}
-NCU_K_ADVANCE = {"dram_bytes_per_launch": 124738816 + 23476992, "l2_hit_rate": 0.4759,
-                 "fp64_pipe_busy": 0.6466, "dram_throughput": 0.2374,
+NCU_K_POOL = {"fp64_inst_per_event": (818444544 + 13809472) / 2.233e7,
+              "dram_bytes_per_launch": 130064384 + 73324544, "l2_hit_rate": 0.6475,
+              "warp_exec_efficiency": 20.43 / 32, "fp64_pipe_busy": 0.3992,
+              "births_kernel_dram_bytes": 59924992 + 101296896}
+NCU_K_ADVANCE = {"dram_bytes_per_launch": 124726272 + 23420672, "l2_hit_rate": 0.4758,
+                 "fp64_pipe_busy": 0.6512, "dram_throughput": 0.2397,
                  "fp64_inst_per_particle": 29000000 / 1e6}
 
 
@@ -92,6 +94,9 @@ def parse():
     ap.add_argument("--graphs", type=int, default=0, help="0: cycles as CUDA graphs, -1: launches")
     ap.add_argument("--mode", default="persistent", choices=["persistent", "event", "segment"],
                     help="launch form of the headline leg (profiling the other forms)")
+    ap.add_argument("--workload", default="lattice", choices=sorted(WORKLOADS),
+                    help="problem of the headline leg: the lattice (the benchmark's) or, for "
+                         "profiling, the continuous-energy pin cell")
     return ap.parse_args()
 
 
@@ -133,9 +138,9 @@ def aggregate(pg, ms, units):
     return ms_max, total, total / (ms_max / 1e3)
 
 
-def replica_problem(W, n, rank):
+def replica_problem(W, n, rank, workload="lattice"):
     """The headline problem; replica `rank` draws from its own master seed."""
-    pb = W.c5g7_like_lattice(seed=1, n=n)
+    pb = W.ce_pin_cell(seed=1, n=n) if workload == "ce-pin" else W.c5g7_like_lattice(seed=1, n=n)
     return W.with_run(pb, seed=int(pb["run"]["seed"]) + 1000003 * rank)
 
 
@@ -203,7 +208,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def headline(m, W, torch, args, rank, pg):
     """Persistent form: K timed cycles after W warm-up cycles."""
-    pb = replica_problem(W, args.n, rank)
+    pb = replica_problem(W, args.n, rank, args.workload)
     mode = {"persistent": m.MODE_PERSISTENT, "event": m.MODE_EVENT,
             "segment": m.MODE_SEGMENT}[args.mode]
     c = m.Context(device=int(os.environ.get("LOCAL_RANK", "0")), mode=mode,
@@ -486,7 +491,8 @@ def run_mcgb(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles_per_cycle": h["n"], "step": "one power-iteration cycle",
+        "config": {"workload": WORKLOADS[args.workload], "particles_per_cycle": h["n"],
+                   "step": "one power-iteration cycle",
                    "mode": args.mode, "pool": args.pool, "graphs": args.graphs == 0, "l2": "inputs larger than L2 (particle state and fission "
                    "banks ~0.5 GB per GPU)", "parallelism": f"replicas x{world}"},
         "events_per_s": h["events_per_cycle"] * world / (ms_max / 1e3 / args.steps),
@@ -500,7 +506,7 @@ def run_mcgb(args):
     # event-based state traffic beside it
     ev = h["events_per_cycle"]
     t_kernel = max(h["transport_ms"], 1e-9) / 1e3
-    pool, _ = ncu_counters(m)
+    pool, _ = ncu_counters(m) if args.workload == "lattice" else (None, None)
     ipe = pool["fp64_inst_per_event"] if pool else None
     peak = h["fp64_ops_per_s"] / 1e9
     ach = ipe * ev / t_kernel / 1e9 if ipe else None

@@ -212,9 +212,10 @@ __device__ __forceinline__ int step_collide(const World &W, const ProblemDev &P,
         }
         int nuc = __ldg(W.mc_nuc + off + sel);
         double mu = div_rn(__ldg(W.n_nu + nuc) * sf, st);
-        double fl = floor(mu);
+        double fl;
+        const int nfl = floor_nonneg(mu, fl);
         double xi = draw(p.s);
-        int nf = (int)fl + (lt_mag(mu - fl, xi) ? 0 : 1);
+        int nf = nfl + (lt_mag(mu - fl, xi) ? 0 : 1);
         bank_append<TIME>(B, R.bank_n, R.err, p, slot, nf);
         xi = draw(p.s);
         if (!lt_mag(ss, xi * st)) {

@@ -39,6 +39,30 @@ __device__ __forceinline__ bool is_inf(double x)
 {
     return __double_as_longlong(x) == 0x7FF0000000000000LL;
 }
+// x > c for a positive constant c: exact for every non-NaN x (negative x have
+// negative bit patterns).
+__device__ __forceinline__ bool gt_pos(double x, double c)
+{
+    return __double_as_longlong(x) > __double_as_longlong(c);
+}
+
+// floor(mu) for a finite mu >= 0, as a double and as an integer, from the bits
+// (no FP64 instruction): the fraction bits below the units place cleared.
+__device__ __forceinline__ int floor_nonneg(double mu, double &fl)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(mu);
+    const int e = (int)(b >> 52) - 1023;
+    if (e < 0) {
+        fl = 0.0;
+        return 0;
+    }
+    if (e > 30) {   // beyond any fission yield; kept exact all the same
+        fl = floor(mu);
+        return (int)fl;
+    }
+    fl = __longlong_as_double((long long)(b & ~((1ULL << (52 - e)) - 1)));
+    return (int)((((b & ((1ULL << 52) - 1)) | (1ULL << 52)) >> (52 - e)));
+}
 
 // ---------------------------------------------------------------------------
 // Random numbers (Sec. 1: replicable on CPU and GPU).  63-bit LCG
@@ -220,7 +244,7 @@ __device__ __forceinline__ void rotate(double mu, uint64_t &s, double &u, double
     double st = sqrt_rn(is_pos(st2) ? st2 : 0.0);
     double u0 = u, v0 = v, w0 = w;
     double ww = fma(-w0, w0, 1.0);
-    if (ww > 1.0e-10) {
+    if (gt_pos(ww, 1.0e-10)) {
         double q = sqrt_rn(ww);
         double f = div_rn(st, q);
         u = fma(mu, u0, f * fma(u0 * w0, cphi, -(v0 * sphi)));
@@ -248,8 +272,7 @@ __device__ __forceinline__ double elastic(double E, const double *kin, uint64_t 
     double q = fma(k01.y, mucm, k23.x);
     double Ep = E * q * k23.y;
     double mul = div_rn(fma(k01.x, mucm, 1.0), sqrt_rn(q));
-    if (mul > 1.0) mul = 1.0;
-    if (mul < -1.0) mul = -1.0;
+    if (lt_mag(1.0, mul)) mul = is_neg(mul) ? -1.0 : 1.0;   // |mul| > 1: clamped
     rotate(mul, s, u, v, w);
     return lt_mag(Ep, E_MIN) ? E_MIN : Ep;
 }
