@@ -127,8 +127,9 @@ __device__ __forceinline__ void retire(const Pool &q, const Particles &G, int i,
 // bucket with a single shared-memory atomic; after one barrier every warp
 // scans the bucket counts itself and places its own slots, so a second barrier
 // ends the call.  Two count arrays are used in turn (hb selects), each zeroed
-// during the other's call.  REFILL: thread 0 also takes the block's share of
-// the device work counter (s_base, s_take; s_exhausted when it runs out).
+// during the other's call.  REFILL: bucket 0 holds the empty slots, and
+// thread 0 also takes the block's share of the device work counter for them
+// (s_base, s_take; s_exhausted when it runs out).
 template <int P, int T, bool REFILL = false, class KeyFn>
 __device__ __forceinline__ int build_list(const Pool &q, int *hist2, int &hb, int *cnt, KeyFn key,
                                           int *work = nullptr, int64_t total_work = 0,
@@ -181,13 +182,13 @@ __device__ __forceinline__ int build_list(const Pool &q, int *hist2, int &hb, in
             cnt[32] = last;
             cnt[NBUCKET] = total;
             other[32] = 0;
-            if (REFILL) {
+            if (REFILL) {   // bucket 0 holds the empty slots: v of lane 0
                 int take = 0, b = 0;
-                if (total > 0) {
-                    b = atomicAdd(work, total);
+                if (v > 0) {
+                    b = atomicAdd(work, v);
                     int64_t left = total_work - (int64_t)b;
-                    take = left <= 0 ? 0 : (left < total ? (int)left : total);
-                    if (take < total) *s_exhausted = 1;
+                    take = left <= 0 ? 0 : (left < v ? (int)left : v);
+                    if (take < v) *s_exhausted = 1;
                 }
                 *s_base = b;
                 *s_take = take;
@@ -232,12 +233,24 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, TIME, CE)) k_pool(Wor
             if (threadIdx.x == 0) atomicOr(R.err, ERR_ITER);
             break;
         }
-        // ---- refill empty slots from the work counter
-        if (!s_exhausted) {
-            build_list<P, T, true>(q, hist, hb, cnt,
-                                   [&](int i) { return q.fate[i] == SLOT_EMPTY ? 0 : -1; }, a.work,
-                                   total, &s_base, &s_take, &s_exhausted);
-            for (int k = threadIdx.x; k < s_take; k += T) {
+        // ---- one sorted list per pass: while histories are left to start, the
+        // empty slots (bucket 0, refilled from the work counter), then the live
+        // particles grouped by material; the newborn fly first, unsorted
+        const bool refill = !s_exhausted;   // block-uniform
+        int n_all;
+        if (refill)
+            n_all = build_list<P, T, true>(q, hist, hb, cnt, [&](int i) {
+                const int f = q.fate[i];
+                return f == SLOT_EMPTY ? 0 : (f == FATE_ALIVE ? 1 + (q.mat[i] & 31) : -1);
+            }, a.work, total, &s_base, &s_take, &s_exhausted);
+        else
+            n_all = build_list<P, T>(q, hist, hb, cnt, [&](int i) {
+                return q.fate[i] == FATE_ALIVE ? 1 + (q.mat[i] & 31) : -1;
+            });
+        const int n0 = refill ? cnt[0] : 0;   // empty slots, listed first
+        const int nb = refill ? s_take : 0;   // of which born this pass
+        if (refill) {
+            for (int k = threadIdx.x; k < nb; k += T) {
                 int i = q.list[k];
                 int64_t j = (int64_t)s_base + k;
                 int prob = 0;
@@ -270,17 +283,16 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, TIME, CE)) k_pool(Wor
             }
             __syncthreads();
         }
-        // ---- flights of every live particle, grouped by material
-        int n_adv = build_list<P, T>(q, hist, hb, cnt, [&](int i) {
-            return q.fate[i] == FATE_ALIVE ? 1 + (q.mat[i] & 31) : -1;
-        });
+        // ---- flights: the newborn (list entries below nb), then every live particle
+        const int n_adv = nb + (n_all - n0);
         if (n_adv == 0 && s_exhausted) break;
         if (s_exhausted && n_adv <= 32) {
             // the block's last few histories (no more to start, one warp's worth):
             // each runs to its end in a thread of warp 0, with no block barrier,
             // list building or shared-memory round trip between its events
-            if ((int)threadIdx.x < n_adv) {
-                int i = q.list[threadIdx.x];
+            const int t = threadIdx.x;
+            const int i = t < n_adv ? q.list[t < nb ? t : t - nb + n0] : 0;
+            if (t < n_adv && q.fate[i] == FATE_ALIVE) {
                 PS p;
                 pool_load<TIME, CE>(q, i, p);
                 const ProblemDev &Pd = W.prob[p.prob];
@@ -304,7 +316,8 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, TIME, CE)) k_pool(Wor
             break;
         }
         for (int k = threadIdx.x; k < n_adv; k += T) {
-            int i = q.list[k];
+            const int i = q.list[k < nb ? k : k - nb + n0];
+            if (q.fate[i] != FATE_ALIVE) continue;   // a birth the source could not place
             PS p;
             pool_load<TIME, CE>(q, i, p);
             int kind, which, uk = 0;
