@@ -5,10 +5,12 @@
 //
 // Each block keeps a pool of P particles in shared memory (structure of
 // arrays) and repeats: refill empty slots from the device work counter; run
-// the flight (advance) of every live particle; run the surface crossings, then
-// the collisions.  Before each phase the block builds a compacted list of the
-// slots that need it, collisions ordered by material, so that consecutive
-// threads -- whole warps -- run the same event on the same kind of data.  The
+// the flight (advance) of every newborn and live particle; run the surface
+// crossings, then the collisions.  Twice a pass the block builds a compacted
+// list: the empty slots, then the live particles by material, for the refill
+// and the flights; the crossings, then the collisions by material, for the
+// events -- so that consecutive threads, whole warps, run the same event on
+// the same kind of data.  The
 // grid stays resident for the whole cycle; no particle state goes through HBM
 // between events.  When no history is left to start and a block holds at most
 // a warp's worth of particles, each runs to its end in registers.  Results do
@@ -281,7 +283,8 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, TIME, CE)) k_pool(Wor
                     pool_store<TIME, CE>(q, i, p);
                 }
             }
-            __syncthreads();
+            // no barrier: list entry k below nb is born and then flown by the
+            // same thread (k mod T), and the births touch no other slot
         }
         // ---- flights: the newborn (list entries below nb), then every live particle
         const int n_adv = nb + (n_all - n0);
