@@ -306,20 +306,13 @@ static int transport_generation(mcgb_ctx *c, const RunBufs &R, int gen, int64_t 
     if (c->opts.mode == MCGB_MODE_PERSISTENT) {
         CK(cudaMemsetAsync(r.work, 0, sizeof(int), st));
         PersistentArgs a{};
-        a.gen = gen;
         a.total = total;
         a.gen_n = nullptr;
-        a.gen_base = gen_base;
-        a.src_idx = src_idx;
-        a.eigen = eigen;
         a.work = r.work;
-        a.chunk = 1;
-        a.gen_dev = gen_dev;
         a.max_passes = c->opts.max_iterations > 0 ? c->opts.max_iterations : 0;
         // every slot's birth made at once by a grid over the generation, so that
         // a block's refill copies a ready state instead of waiting on the bank
         // reads, the stream skip-ahead and the sampling of each birth
-        a.preborn = 1;
         launch_source(W, r.P, Bsrc, R, gen, total, gen_base, src_idx, eigen, block, st, gen_dev);
         c->launches += 1;
         int pool = c->opts.pool == 0 ? default_pool(W) : c->opts.pool;

@@ -31,20 +31,14 @@ void launch_segment(const World &W, const Particles &P, const Bank &Bdst, const 
 
 // ---- persistent event loop -------------------------------------------------
 struct PersistentArgs {
-    int gen;                 // cycle or generation index (stream ids gen 2^32 + local)
     int64_t total;           // work items (slots) when gen_n is null
     const int *gen_n;        // device total (bank size) when not null
-    const int64_t *gen_base; // [nprob + 1] first slot of each problem (device)
-    const int *src_idx;      // bank site of each slot, or null for the source definition
-    int eigen;
     int *work;               // device work counter (zeroed before the launch)
-    int chunk;               // slots taken per pop
-    const int *gen_dev;      // when not null: the cycle index is read here (graph replay)
     long long max_passes;    // > 0: a block (warp) stops after this many passes of its event
                              // loop and raises ERR_ITER (histories left unfinished)
-    int preborn;             // 1: slot j's birth was made by launch_source into the
-                             // particle arrays, and a refill copies it from there
 };
+// The persistent kernels take each slot's birth from the particle arrays, where
+// launch_source made it for the whole generation before their launch.
 // births read Bsrc (the previous cycle's bank), new sites are appended to Bdst
 void launch_persistent(const World &W, const Particles &P, const Bank &Bsrc, const Bank &Bdst,
                        const RunBufs &R, const PersistentArgs &a, int grid, int block,

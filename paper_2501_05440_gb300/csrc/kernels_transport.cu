@@ -357,7 +357,6 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
                                                     RunBufs R, PersistentArgs a)
 {
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
-    const int gen = a.gen_dev ? *a.gen_dev : a.gen;
     const int lane = threadIdx.x & 31;
     const int rep = accum_replica(W);
     PS p;
@@ -385,13 +384,10 @@ __global__ void __launch_bounds__(256) k_persistent(World W, Particles P, Bank B
                     done = true;
                 } else {
                     slot = (int)j;
-                    int prob = find_problem(a.gen_base, W.nprob, j);
-                    Pd = W.prob + prob;
                     kt = 0.0;
                     kc = 0.0;
-                    bool ok = a.preborn ? load_born<TIME, CE>(W, P, j, p)
-                                        : init_particle<CE>(W, *Pd, Bsrc, p, prob, j - a.gen_base[prob], gen,
-                                                            a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                    const bool ok = load_born<TIME, CE>(W, P, j, p);   // made by launch_source
+                    Pd = W.prob + p.prob;
                     if (ok) {
                         alive = true;
                     } else {

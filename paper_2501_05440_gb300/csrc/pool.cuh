@@ -224,7 +224,6 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, TIME, CE)) k_pool(Wor
     int hb = 0;
     for (int k = threadIdx.x; k < 2 * (NBUCKET + 1); k += T) hist[k] = 0;
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
-    const int gen = a.gen_dev ? *a.gen_dev : a.gen;
     const int rep = (int)(blockIdx.x % (unsigned)W.nrep);
     for (int i = threadIdx.x; i < P; i += T) q.fate[i] = SLOT_EMPTY;
     if (threadIdx.x == 0) s_exhausted = 0;
@@ -255,20 +254,8 @@ __global__ void __launch_bounds__(T, pool_min_blocks(P, T, TIME, CE)) k_pool(Wor
             for (int k = threadIdx.x; k < nb; k += T) {
                 int i = q.list[k];
                 int64_t j = (int64_t)s_base + k;
-                int prob = 0;
-                {
-                    int lo = 0, hi = W.nprob;
-                    while (hi - lo > 1) {
-                        int mid = (lo + hi) >> 1;
-                        if (a.gen_base[mid] <= j) lo = mid;
-                        else hi = mid;
-                    }
-                    prob = lo;
-                }
                 PS p;
-                bool ok = a.preborn ? load_born<TIME, CE>(W, G, j, p)
-                                    : init_particle<CE>(W, W.prob[prob], Bsrc, p, prob, j - a.gen_base[prob],
-                                                        gen, a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                const bool ok = load_born<TIME, CE>(W, G, j, p);   // made by launch_source
                 q.gslot[i] = (int)j;
                 q.kt[i] = 0.0;
                 q.kc[i] = 0.0;
@@ -410,7 +397,6 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Pool q = carve<TIME, CE>(smem + (size_t)warp * pool_bytes(PW, TIME, CE), PW);
     const int64_t total = a.gen_n ? (int64_t)*a.gen_n : a.total;
-    const int gen = a.gen_dev ? *a.gen_dev : a.gen;
     const int rep = (int)((blockIdx.x * (WPOOL_T / 32) + warp) % (unsigned)W.nrep);
     for (int i = lane; i < PW; i += 32) q.fate[i] = SLOT_EMPTY;
     __syncwarp();
@@ -435,16 +421,8 @@ __global__ void __launch_bounds__(WPOOL_T, WpoolMinBlocks<PW>::value) k_wpool(Wo
             for (int k = lane; k < take; k += 32) {
                 int i = q.list[k];
                 int64_t j = (int64_t)base + k;
-                int lo = 0, hi = W.nprob;
-                while (hi - lo > 1) {
-                    int mid = (lo + hi) >> 1;
-                    if (a.gen_base[mid] <= j) lo = mid;
-                    else hi = mid;
-                }
                 PS p;
-                bool ok = a.preborn ? load_born<TIME, CE>(W, G, j, p)
-                                    : init_particle<CE>(W, W.prob[lo], Bsrc, p, lo, j - a.gen_base[lo], gen,
-                                                        a.src_idx ? a.src_idx[j] : -1, a.eigen != 0);
+                const bool ok = load_born<TIME, CE>(W, G, j, p);   // made by launch_source
                 q.gslot[i] = (int)j;
                 q.kt[i] = 0.0;
                 q.kc[i] = 0.0;
