@@ -62,14 +62,14 @@ HBM_PEAK_GBS = _hbm_peak()
 #   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum
 #   l2_hit_rate: lts__t_sector_hit_rate; warp_exec_efficiency: active lanes per
 #   issued instruction / 32; fp64_pipe_busy: FP64 pipe cycles / elapsed cycles
-NCU_SOURCES = "a6f4290a3d6c52a0"
+NCU_SOURCES = "b73aadf790509d29"
 # k_source + k_pool of one cycle (2.233e7 events); DRAM bytes and rates of k_pool
-NCU_K_POOL = {"fp64_inst_per_event": (818444544 + 13809472) / 2.233e7,
-              "dram_bytes_per_launch": 130064384 + 73324544, "l2_hit_rate": 0.6475,
-              "warp_exec_efficiency": 20.43 / 32, "fp64_pipe_busy": 0.3992,
-              "births_kernel_dram_bytes": 59924992 + 101296896}
-NCU_K_ADVANCE = {"dram_bytes_per_launch": 124726272 + 23420672, "l2_hit_rate": 0.4758,
-                 "fp64_pipe_busy": 0.6512, "dram_throughput": 0.2397,
+NCU_K_POOL = {"fp64_inst_per_event": (818444992 + 13809344) / 2.233e7,
+              "dram_bytes_per_launch": 130011136 + 73101568, "l2_hit_rate": 0.6311,
+              "warp_exec_efficiency": 20.37 / 32, "fp64_pipe_busy": 0.4092,
+              "births_kernel_dram_bytes": 59837952 + 101257984}
+NCU_K_ADVANCE = {"dram_bytes_per_launch": 124719872 + 23557888, "l2_hit_rate": 0.4753,
+                 "fp64_pipe_busy": 0.6449, "dram_throughput": 0.2409,
                  "fp64_inst_per_particle": 29000000 / 1e6}
 
 
