@@ -122,3 +122,18 @@ def test_gpus_flag_starts_ranks_or_refuses():
     import json
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2
+
+
+def test_workload_option_selects_the_headline_problem():
+    """--workload picks the problem of the headline leg: the lattice by
+    default, the continuous-energy pin cell for profiling; replicas keep the
+    problem and take their own master seed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    lat = bench.replica_problem(W, 1000, 0)
+    ce = bench.replica_problem(W, 1000, 1, "ce-pin")
+    assert lat["name"] == bench.WORKLOADS["lattice"] and lat["lattices"]
+    assert ce["name"] == bench.WORKLOADS["ce-pin"] and not ce["lattices"]
+    assert ce["run"]["seed"] == bench.replica_problem(W, 1000, 0, "ce-pin")["run"]["seed"] + 1000003
+    assert set(bench.WORKLOADS) == {"lattice", "ce-pin"}
