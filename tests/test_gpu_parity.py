@@ -199,6 +199,24 @@ def test_ce_infinite_medium_eigen_parity(mcgb, mode, pool, graphs):
     _eigen_parity(mcgb, pb, mode, pool, graphs)
 
 
+@pytest.mark.parametrize("mode,pool,graphs", FEW + [(1, 64, 0), (1, 512, 0)])
+def test_ce_free_gas_eigen_parity(mcgb, mode, pool, graphs):
+    """Free-gas thermal scattering in a k-eigenvalue run without time
+    dependence (the pool instantiations without the particle clock; the
+    other free-gas cases are time dependent): a fissile nuclide in hydrogen
+    whose neutrons slow down into the thermal range."""
+    E = np.array([W.E_MIN, 1.0, W.E_MAX])
+    nuc = lambda A, sc, cc, sf, nu: {"A": A, "E": E, "sig_s": np.full(3, sc), "sig_c": np.full(3, cc),
+                                     "sig_f": np.full(3, sf), "nu": nu}
+    pb = W.ce_infinite_eigen([nuc(235.0, 4.0, 0.2, 0.4, 2.43), nuc(1.0, 20.0, 0.01, 0.0, 0.0)],
+                             [0.002, 0.06], n=2000, inactive=1, active=2)
+    pb["free_gas"] = {"kT": 0.0253}
+    c, o = _eigen_parity(mcgb, pb, mode, pool, graphs)
+    del pb["free_gas"]
+    cold = oracle_run(pb).histories()
+    assert np.any(cold["rng_end"] != c.get_histories()["rng_end"]), "free gas never sampled"
+
+
 @pytest.mark.parametrize("radius", [0.6299, 0.63])
 @pytest.mark.parametrize("mode,pool,graphs", [(0, 0, 0), (1, 0, 0)])
 def test_lattice_tight_pins_parity(mcgb, radius, mode, pool, graphs):
