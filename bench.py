@@ -350,10 +350,11 @@ def batched_leg(m, W, torch):
             "speedup": t_sep / t_batch, "tune": tune}
 
 
-def grad_leg(m, W, torch, n):
+def grad_leg(m, W, torch, n, reps=3):
     """Derivatives through the public torch API: DetectorTally on CUDA tensors
     (device-pointer calls, no host copies of any array), forward then backward
-    of sum(tally), 1e7 histories of the slab."""
+    of sum(tally), 1e7 histories of the slab; after one untimed pass at the
+    same size, the median of `reps` host-timed passes."""
     import numpy as np
 
     from paper_2501_05440_gb300.autograd import detector_tally
@@ -366,19 +367,24 @@ def grad_leg(m, W, torch, n):
         return [torch.tensor(np.array([mat[k] for mat in pb["materials"]]), device=dev,
                              requires_grad=True) for k in ("sigma_t", "sigma_s", "nu_sigma_f")]
 
-    st, ss, nf = xs()     # warm-up at a smaller size
-    detector_tally(pb, st, ss, nf, min(n, 10000), 1, det, engine=eng).sum().backward()
-    st, ss, nf = xs()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    y = detector_tally(pb, st, ss, nf, n, 1, det, engine=eng)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    y.sum().backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    return {"histories": n, "forward_s": t1 - t0, "backward_s": t2 - t1,
-            "grad_histories_per_s": n / (t2 - t1), "forward_histories_per_s": n / (t1 - t0),
+    st, ss, nf = xs()     # warm-up at the full size (the engine's buffers allocated)
+    detector_tally(pb, st, ss, nf, n, 1, det, engine=eng).sum().backward()
+    fwd, bwd = [], []
+    for _ in range(reps):
+        st, ss, nf = xs()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y = detector_tally(pb, st, ss, nf, n, 1, det, engine=eng)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        y.sum().backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        fwd.append(t1 - t0)
+        bwd.append(t2 - t1)
+    tf, tb = sorted(fwd)[reps // 2], sorted(bwd)[reps // 2]
+    return {"histories": n, "forward_s": tf, "backward_s": tb, "timing": f"median of {reps}",
+            "grad_histories_per_s": n / tb, "forward_histories_per_s": n / tf,
             "detector_tally": float(y.detach().sum().item()),
             "api": "paper_2501_05440_gb300.autograd.DetectorTally on CUDA tensors",
             "grad_norm_sigma_t": float(st.grad.norm().item())}

@@ -48,6 +48,12 @@ __device__ __forceinline__ float rcp_approx_f32(float x)
     return y;
 }
 
+// The hardware operations for the operands the integer paths leave out, kept
+// out of line: inlined at every call site, their code (taken practically
+// never) made the transport loops larger and slowed their instruction fetch.
+static __device__ __noinline__ double sqrt_hw(double x) { return sqrt(x); }
+static __device__ __noinline__ double div_hw(double n, double d) { return n / d; }
+
 constexpr uint64_t FP_FRAC = (1ULL << 52) - 1;
 constexpr uint64_t FP_HIDDEN = 1ULL << 52;
 constexpr uint64_t FP_SIGN = 0x8000000000000000ULL;
@@ -66,7 +72,7 @@ __device__ __forceinline__ double sqrt_rn(double x)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
     const uint32_t E = (uint32_t)(b >> 52);          // sign bit included: negatives fall back
-    if (E - 1u >= 2046u) return sqrt(x);
+    if (E - 1u >= 2046u) return sqrt_hw(x);
     const uint64_t F = b & FP_FRAC;
     const uint32_t odd = (~E) & 1u;                   // E even <=> E - 1075 odd
     const uint64_t M2 = (F | FP_HIDDEN) << odd;
@@ -107,7 +113,7 @@ __device__ __forceinline__ double div_rn(double n, double d)
     const uint64_t Mn = Fn | FP_HIDDEN, Md = Fd | FP_HIDDEN;
     const int lt = Mn < Md ? 1 : 0;
     const int Er = (int)En - (int)Ed + 1023 - lt;
-    if (En - 1u >= 2046u || Ed - 1u >= 2046u || (uint32_t)(Er - 1) >= 2046u) return n / d;
+    if (En - 1u >= 2046u || Ed - 1u >= 2046u || (uint32_t)(Er - 1) >= 2046u) return div_hw(n, d);
     const int K = 52 + lt;
     // significands in [1, 2) as floats built from the bits; y ~ 1 / d_m (Y = y 2^25);
     // n_m y ~ n_m / d_m with significand mq: Q0 = mq 2^sh ~ q
