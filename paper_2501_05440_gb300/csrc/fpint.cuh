@@ -51,8 +51,16 @@ __device__ __forceinline__ float rcp_approx_f32(float x)
 // The hardware operations for the operands the integer paths leave out, kept
 // out of line: inlined at every call site, their code (taken practically
 // never) made the transport loops larger and slowed their instruction fetch.
-static __device__ __noinline__ double sqrt_hw(double x) { return sqrt(x); }
-static __device__ __noinline__ double div_hw(double n, double d) { return n / d; }
+// A translation unit that defines MCGB_FALLBACK_INLINE before including this
+// header inlines them instead (the derivative replay's per-history loop ran
+// 25% slower with the calls).
+#ifdef MCGB_FALLBACK_INLINE
+#define MCGB_FALLBACK __forceinline__
+#else
+#define MCGB_FALLBACK __noinline__
+#endif
+static __device__ MCGB_FALLBACK double sqrt_hw(double x) { return sqrt(x); }
+static __device__ MCGB_FALLBACK double div_hw(double n, double d) { return n / d; }
 
 constexpr uint64_t FP_FRAC = (1ULL << 52) - 1;
 constexpr uint64_t FP_HIDDEN = 1ULL << 52;

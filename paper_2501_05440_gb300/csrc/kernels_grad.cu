@@ -19,6 +19,9 @@
 //   absorption (Sigma_a = Sigma_t - Sigma_s,tot > 0)
 //                                     dSigma_t: 1/Sigma_a - 1/Sigma_t, dSigma_s[g,*]: -1/Sigma_a
 // Parameters equal to 0 take no score.
+// the float64 fallbacks of the integer-pipe square root and division inlined
+// here: the replay loop is faster with them inline than with calls
+#define MCGB_FALLBACK_INLINE
 #include "kernels.h"
 #include "steps.cuh"
 
