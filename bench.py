@@ -62,14 +62,14 @@ HBM_PEAK_GBS = _hbm_peak()
 #   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum
 #   l2_hit_rate: lts__t_sector_hit_rate; warp_exec_efficiency: active lanes per
 #   issued instruction / 32; fp64_pipe_busy: FP64 pipe cycles / elapsed cycles
-NCU_SOURCES = "b73aadf790509d29"
+NCU_SOURCES = "8ef6620ef4fd8a01"
 # k_source + k_pool of one cycle (2.233e7 events); DRAM bytes and rates of k_pool
-NCU_K_POOL = {"fp64_inst_per_event": (818444992 + 13809344) / 2.233e7,
-              "dram_bytes_per_launch": 130011136 + 73101568, "l2_hit_rate": 0.6311,
-              "warp_exec_efficiency": 20.37 / 32, "fp64_pipe_busy": 0.4092,
-              "births_kernel_dram_bytes": 59837952 + 101257984}
-NCU_K_ADVANCE = {"dram_bytes_per_launch": 124719872 + 23557888, "l2_hit_rate": 0.4753,
-                 "fp64_pipe_busy": 0.6449, "dram_throughput": 0.2409,
+NCU_K_POOL = {"fp64_inst_per_event": (818444896 + 13809408) / 2.233e7,
+              "dram_bytes_per_launch": 129905408 + 72902144, "l2_hit_rate": 0.6307,
+              "warp_exec_efficiency": 20.37 / 32, "fp64_pipe_busy": 0.4202,
+              "births_kernel_dram_bytes": 59611392 + 101180416}
+NCU_K_ADVANCE = {"dram_bytes_per_launch": 124712704 + 23436032, "l2_hit_rate": 0.4754,
+                 "fp64_pipe_busy": 0.6500, "dram_throughput": 0.2374,
                  "fp64_inst_per_particle": 29000000 / 1e6}
 
 
