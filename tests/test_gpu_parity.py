@@ -217,6 +217,17 @@ def test_ce_free_gas_eigen_parity(mcgb, mode, pool, graphs):
     assert np.any(cold["rng_end"] != c.get_histories()["rng_end"]), "free gas never sampled"
 
 
+@pytest.mark.parametrize("mode,pool,graphs", FEW)
+def test_ce_fixed_energy_eigen_parity(mcgb, mode, pool, graphs):
+    """The problem of the oracle's fixed-energy closed form (nuclides of mass
+    ~1e9 with cross sections that vary over the fission spectrum's energies):
+    histories, banks, tallies and k equal to the oracle's."""
+    from tests.test_oracle_ce_fixed_energy import _nuclides
+    E = np.geomspace(W.E_MIN, W.E_MAX, 4001)
+    pb = W.ce_infinite_eigen(_nuclides(E), [0.02, 0.03], n=3000, inactive=1, active=2, seed=11)
+    _eigen_parity(mcgb, pb, mode, pool, graphs)
+
+
 @pytest.mark.parametrize("radius", [0.6299, 0.63])
 @pytest.mark.parametrize("mode,pool,graphs", [(0, 0, 0), (1, 0, 0)])
 def test_lattice_tight_pins_parity(mcgb, radius, mode, pool, graphs):
